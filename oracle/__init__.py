@@ -1,0 +1,67 @@
+"""Plain FP64 CPU oracle of F-AMS (Tene, Al Kobaisi, Hajibeygi; arXiv 1705.05784).
+
+TEST INFRASTRUCTURE ONLY: a slow, obviously-correct statement of the method,
+written from the paper, used by the tests, the smoke check and the CPU-baseline
+arm of the benchmark to check the CUDA library.  The library never imports,
+links or calls anything here, and nothing here imports the library.
+
+Modules:
+  geometry  - EDFM fracture cells, matrix-fracture connections, intersections
+  assemble  - the fine system A p = q (TPFA + NNC, Dirichlet faces)
+  coarsen   - primal/dual coarse grids, wirebasket ranks, Table 2 BFS
+  basis     - prolongation P by the staged rule and by Appendix A's formulas,
+              truncation
+  solver    - R, A_c = R A P, LU, ILU(0), Table 1 iteration, flux
+              reconstruction
+
+Parity unpinned: the paper's printed numbers (single-step error norms of
+Sec. 4.2, Table 3 timings) depend on permeability maps and fracture networks
+that are not published, so no function here is pinned to them.  Every other
+function is pinned by the tests in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import assemble as _asm
+from . import basis as _basis
+from . import coarsen as _coarsen
+from . import geometry as _geom
+from . import solver as _solver
+
+
+@dataclass
+class OracleResult:
+    geom: object
+    sysm: object
+    coarse: object
+    P: object
+    setup: object
+    p: np.ndarray
+    iters: int
+    rel_res: float
+    converged: bool
+    history: list
+
+
+def build(prob, route="staged"):
+    """Geometry, system, coarse grids, P (truncated) and the solver setup."""
+    g = _geom.build_geometry(prob)
+    sysm = _asm.assemble(prob, g)
+    c = _coarsen.build_coarse(prob, g)
+    if route == "staged":
+        P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis)
+    else:
+        P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis)
+    P = _basis.truncate(P, prob.alpha)
+    st = _solver.setup(sysm, P, c.primal, c.n_coarse, prob.restriction)
+    return g, sysm, c, P, st
+
+
+def run(prob, x0=None, history=True):
+    g, sysm, c, P, st = build(prob)
+    p, it, rr, ok, hist = _solver.two_stage_solve(st, x0=x0, tol=prob.tol,
+                                                   max_iter=prob.max_iter, history=history)
+    return OracleResult(g, sysm, c, P, st, p, it, rr, ok, hist)

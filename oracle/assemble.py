@@ -1,0 +1,137 @@
+"""Oracle: the fine-scale EDFM pressure system A p = q (Sec. 2, Eqs. 1-8).
+
+TEST INFRASTRUCTURE ONLY (see oracle/geometry.py).
+
+Incompressible single phase, mu = rho = 1, so lambda = k.  The system is
+integrated over each control volume, so every connection contributes one
+transmissibility T to both of its cells and A is symmetric:
+
+  row i:  sum_j T_ij (p_i - p_j) + T_D,i (p_i - p_D) = q_i
+
+* matrix-matrix: two-point flux, harmonic average of the half-cell
+  transmissibilities, T = A_face / (h/(2 k_i) + h/(2 k_j));
+* Dirichlet faces: half-cell transmissibility T_D = 2 k_i A_face / h;
+* matrix-fracture: T = CI_ij lambda^{f-m} with CI_ij = A_ij / <d>_ij (Eq. 7)
+  and lambda^{f-m} read as the matrix cell's k (the paper leaves it open);
+  eta^m V = eta^f A = CI lambda (Eqs. 4-6) makes the pair symmetric;
+* fracture-fracture: along strike k_f a_f depth / h_s, vertically
+  k_f a_f h_s / dz, intersections as built in geometry.py.
+
+Unknown order: matrix cells (x fastest, then y, then z) then fracture cells
+(Eq. 8 block order [m; f]).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .geometry import build_geometry
+
+
+class System:
+    pass
+
+
+def matrix_faces(prob):
+    """All interior matrix faces as (cell_lo, cell_hi, T, axis), ordered by axis
+    then by the low cell."""
+    nx, ny = prob.nx, prob.ny
+    nz = prob.nz if prob.dim == 3 else 1
+    k = np.asarray(prob.perm, np.float64).reshape(nz, ny, nx)
+    dx, dy, dz = prob.dx, prob.dy, prob.dz
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    out = []
+    # x faces
+    area, h = dy * dz, dx
+    kl, kr = k[:, :, :-1], k[:, :, 1:]
+    T = area / (h / (2 * kl) + h / (2 * kr))
+    out.append((idx[:, :, :-1].ravel(), idx[:, :, 1:].ravel(), T.ravel(), 0))
+    area, h = dx * dz, dy
+    kl, kr = k[:, :-1, :], k[:, 1:, :]
+    T = area / (h / (2 * kl) + h / (2 * kr))
+    out.append((idx[:, :-1, :].ravel(), idx[:, 1:, :].ravel(), T.ravel(), 1))
+    if prob.dim == 3:
+        area, h = dx * dy, dz
+        kl, kr = k[:-1, :, :], k[1:, :, :]
+        T = area / (h / (2 * kl) + h / (2 * kr))
+        out.append((idx[:-1, :, :].ravel(), idx[1:, :, :].ravel(), T.ravel(), 2))
+    return out
+
+
+def dirichlet_terms(prob):
+    """Half-cell transmissibility and value on each Dirichlet boundary face.
+    Returns (cell, T_D, p_D, face_id) arrays; face ids 0..5 = W,E,S,N,B,T."""
+    nx, ny = prob.nx, prob.ny
+    nz = prob.nz if prob.dim == 3 else 1
+    k = np.asarray(prob.perm, np.float64).reshape(nz, ny, nx)
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    dx, dy, dz = prob.dx, prob.dy, prob.dz
+    cells, tds, pds, fids = [], [], [], []
+    faces = [
+        (0, idx[:, :, 0], k[:, :, 0], dy * dz, dx),
+        (1, idx[:, :, -1], k[:, :, -1], dy * dz, dx),
+        (2, idx[:, 0, :], k[:, 0, :], dx * dz, dy),
+        (3, idx[:, -1, :], k[:, -1, :], dx * dz, dy),
+    ]
+    if prob.dim == 3:
+        faces += [(4, idx[0, :, :], k[0, :, :], dx * dy, dz),
+                  (5, idx[-1, :, :], k[-1, :, :], dx * dy, dz)]
+    for fid, cid, kk, area, h in faces:
+        if not (prob.bc_mask >> fid) & 1:
+            continue
+        cells.append(cid.ravel())
+        tds.append((2.0 * kk * area / h).ravel())
+        pds.append(np.full(cid.size, float(prob.bc_value[fid])))
+        fids.append(np.full(cid.size, fid))
+    if not cells:
+        return (np.zeros(0, np.int64), np.zeros(0), np.zeros(0), np.zeros(0, np.int64))
+    return (np.concatenate(cells), np.concatenate(tds), np.concatenate(pds),
+            np.concatenate(fids))
+
+
+def assemble(prob, geom=None):
+    """Build A (with Dirichlet terms), A0 (without them) and the total rhs."""
+    g = build_geometry(prob) if geom is None else geom
+    nm, nf = g.n_matrix, g.n_frac
+    n = nm + nf
+    perm = np.asarray(prob.perm, np.float64)
+    rows, cols, vals = [], [], []
+    conns = []  # (i, j, T) for every connection, i < j
+
+    for lo, hi, T, axis in matrix_faces(prob):
+        conns.append((lo, hi, T))
+    # matrix-fracture: T = CI * k_m  (Eqs. 4-7)
+    Tmf = g.nnc_area / g.nnc_dist * perm[g.nnc_m]
+    conns.append((g.nnc_m, nm + g.nnc_f, Tmf))
+    conns.append((nm + g.ff_a, nm + g.ff_b, g.ff_T))
+
+    for i, j, T in conns:
+        rows += [i, j, i, j]
+        cols += [j, i, i, j]
+        vals += [-T, -T, T, T]
+    A0 = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(n, n))
+    A0.sum_duplicates()
+    A0.sort_indices()
+    dc, dT, dp, dfid = dirichlet_terms(prob)
+    D = np.zeros(n)
+    np.add.at(D, dc, dT)
+    qD = np.zeros(n)
+    np.add.at(qD, dc, dT * dp)
+    A = (A0 + sp.diags(D)).tocsr()
+    A.sort_indices()
+    # A0's pattern must include the diagonal even where it is 0 (it never is here)
+    s = System()
+    s.geom = g
+    s.n = n
+    s.n_matrix = nm
+    s.n_frac = nf
+    s.A = A
+    s.A0 = A0
+    s.T_D = D
+    s.q_dirichlet = qD
+    src = np.zeros(n) if prob.rhs is None else np.asarray(prob.rhs, np.float64)
+    s.q = src + qD
+    s.dirichlet = (dc, dT, dp, dfid)
+    s.Tmf = Tmf
+    return s

@@ -1,0 +1,213 @@
+"""Oracle: restriction, coarse system, ILU(0) smoother and the two-stage
+iteration (Sec. 3.2, Table 1), and conservative flux reconstruction.
+
+TEST INFRASTRUCTURE ONLY (see oracle/geometry.py).
+
+* R^FV: R[I, i] = 1 when fine cell i lies in primal block I (Sec. 3.2);
+  R^FE = P^T (MSFE).
+* coarse operator A_c = R A P, solved by LU with partial pivoting (the paper
+  uses a direct LU solver, Sec. 4).
+* ILU(0) of the complete fine A in natural order (matrix cells then fracture
+  cells), no pivoting: the textbook IKJ variant restricted to the pattern of A.
+* Table 1, steps 3 and 5-8, with A and q fixed (incompressible, no step 2):
+    r = q - A p;  dp1 = P (R A P)^-1 R r;  r1 = r - A dp1;
+    dp2 = (LU)^-1 r1;  p = p + dp1 + dp2
+  iterated until ||q - A p||_2 <= tol ||q||_2 (q including Dirichlet terms).
+* flux reconstruction: one FV multiscale stage from x gives p', fluxes across
+  primal-block boundaries are T (p'_i - p'_j), and every primal block then
+  solves its own TPFA problem with those fluxes as Neumann data (pinned at its
+  coarse node when it has no Dirichlet face); fluxes inside a block come from
+  that local solution.  R^FV (q - A p') = 0 makes each local problem
+  consistent.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+R_FV, R_FE = 0, 1
+
+
+def restriction(P, primal, n_coarse, kind):
+    n = P.shape[0]
+    if kind == R_FE:
+        return sp.csr_matrix(P.T)
+    return sp.csr_matrix((np.ones(n), (primal, np.arange(n))), shape=(n_coarse, n))
+
+
+def coarse_operator(R, A, P):
+    Ac = (R @ A @ P).toarray()
+    return Ac
+
+
+def ilu0(A):
+    """ILU(0): returns a CSR matrix with the strict lower part of L (unit
+    diagonal implied) and the upper part of U in the pattern of A."""
+    A = sp.csr_matrix(A, copy=True)
+    A.sort_indices()
+    n = A.shape[0]
+    ip, ix, v = A.indptr, A.indices, A.data.astype(np.float64).copy()
+    diag = np.zeros(n, np.int64)
+    for i in range(n):
+        row = ix[ip[i]:ip[i + 1]]
+        k = np.searchsorted(row, i)
+        assert k < len(row) and row[k] == i, "missing diagonal"
+        diag[i] = ip[i] + k
+    for i in range(n):
+        a, b = ip[i], ip[i + 1]
+        pos = {ix[p]: p for p in range(a, b)}
+        for p in range(a, diag[i]):
+            k = ix[p]
+            v[p] = v[p] / v[diag[k]]
+            lik = v[p]
+            for q in range(diag[k] + 1, ip[k + 1]):
+                j = ix[q]
+                pj = pos.get(j)
+                if pj is not None:
+                    v[pj] -= lik * v[q]
+        if v[diag[i]] == 0.0:
+            raise ZeroDivisionError("zero pivot in ILU(0)")
+    F = sp.csr_matrix((v, ix.copy(), ip.copy()), shape=A.shape)
+    return F
+
+
+def ilu0_apply(F, r):
+    """Solve L U x = r with the factors from ilu0()."""
+    L = sp.tril(F, k=-1, format="csr") + sp.identity(F.shape[0], format="csr")
+    U = sp.triu(F, k=0, format="csr")
+    y = spla.spsolve_triangular(L, r, lower=True, unit_diagonal=True)
+    return spla.spsolve_triangular(U, y, lower=False)
+
+
+class Setup:
+    pass
+
+
+def setup(sysm, P, primal, n_coarse, kind):
+    s = Setup()
+    s.A = sysm.A
+    s.q = sysm.q
+    s.P = P
+    s.R = restriction(P, primal, n_coarse, kind)
+    s.Ac = coarse_operator(s.R, sysm.A, P)
+    s.lu = sla.lu_factor(s.Ac)
+    s.F = ilu0(sysm.A)
+    return s
+
+
+def two_stage_solve(s, x0=None, tol=1e-8, max_iter=200, smoother=True, history=False):
+    """Table 1 loop.  Returns (p, iterations, final relative residual, converged
+    flag, residual history)."""
+    A, q = s.A, s.q
+    p = np.zeros(A.shape[0]) if x0 is None else np.asarray(x0, np.float64).copy()
+    qn = np.linalg.norm(q)
+    qn = qn if qn > 0 else 1.0
+    r = q - A @ p
+    hist = [np.linalg.norm(r) / qn]
+    it = 0
+    while hist[-1] > tol and it < max_iter:
+        dp1 = s.P @ sla.lu_solve(s.lu, s.R @ r)          # step 5
+        p = p + dp1
+        if smoother:
+            r1 = r - A @ dp1                              # step 6
+            dp2 = ilu0_apply(s.F, r1)                     # step 7
+            p = p + dp2                                   # step 8
+        it += 1
+        r = q - A @ p                                     # step 3 of the next sweep
+        hist.append(np.linalg.norm(r) / qn)
+    return p, it, hist[-1], hist[-1] <= tol, (hist if history else None)
+
+
+def multiscale_stage(s, x):
+    """p' = x + P (R A P)^-1 R (q - A x)  (one multiscale stage)."""
+    r = s.q - s.A @ x
+    return x + s.P @ sla.lu_solve(s.lu, s.R @ r)
+
+
+def connections(sysm, prob):
+    """Every connection (i, j, T) with i < j, in a fixed order: matrix x, y, z
+    faces, then matrix-fracture, then fracture-fracture.  Also returns the
+    Dirichlet face list."""
+    from .assemble import matrix_faces
+    nm = sysm.n_matrix
+    g = sysm.geom
+    out = []
+    for lo, hi, T, axis in matrix_faces(prob):
+        out.append((lo, hi, T))
+    out.append((g.nnc_m, nm + g.nnc_f, sysm.Tmf))
+    out.append((nm + g.ff_a, nm + g.ff_b, g.ff_T))
+    ci = np.concatenate([o[0] for o in out]).astype(np.int64)
+    cj = np.concatenate([o[1] for o in out]).astype(np.int64)
+    cT = np.concatenate([o[2] for o in out]).astype(np.float64)
+    return ci, cj, cT
+
+
+def reconstruct_flux(sysm, prob, s_fv, x, primal, node_cell):
+    """Conservative flux field from an iterate x.  Returns (conn_flux for every
+    connection of connections(), dirichlet_flux for each Dirichlet face), flux
+    positive from the first to the second cell / out of the domain."""
+    pp = multiscale_stage(s_fv, x)
+    ci, cj, cT = connections(sysm, prob)
+    dc, dT, dp, _ = sysm.dirichlet
+    n = sysm.n
+    q_src = sysm.q - sysm.q_dirichlet
+    flux = cT * (pp[ci] - pp[cj])
+    dflux = np.zeros(len(dc))
+    nblk = int(primal.max()) + 1
+    members = [[] for _ in range(nblk)]
+    for i in range(n):
+        members[primal[i]].append(i)
+    internal = primal[ci] == primal[cj]
+    # boundary (cross-block) fluxes are final: accumulate them as Neumann data
+    bnd_out = np.zeros(n)
+    np.add.at(bnd_out, ci[~internal], flux[~internal])
+    np.subtract.at(bnd_out, cj[~internal], flux[~internal])
+    TD = np.zeros(n)
+    np.add.at(TD, dc, dT)
+    qD = np.zeros(n)
+    np.add.at(qD, dc, dT * dp)
+    int_idx = np.nonzero(internal)[0]
+    blk_of_conn = primal[ci[int_idx]]
+    conns_of_blk = [[] for _ in range(nblk)]
+    for k, b in zip(int_idx, blk_of_conn):
+        conns_of_blk[b].append(k)
+    ptil = pp.copy()
+    for b in range(nblk):
+        cells = members[b]
+        m = len(cells)
+        loc = {c: t for t, c in enumerate(cells)}
+        K = np.zeros((m, m))
+        rhs = np.zeros(m)
+        for k in conns_of_blk[b]:
+            a, c = loc[ci[k]], loc[cj[k]]
+            K[a, a] += cT[k]
+            K[c, c] += cT[k]
+            K[a, c] -= cT[k]
+            K[c, a] -= cT[k]
+        for t, c in enumerate(cells):
+            K[t, t] += TD[c]
+            rhs[t] = q_src[c] + qD[c] - bnd_out[c]
+        if not np.any(TD[cells] > 0):
+            v = loc[node_cell[b]]
+            K[v, :] = 0.0
+            K[v, v] = 1.0
+            rhs[v] = pp[node_cell[b]]
+        sol = np.linalg.solve(K, rhs)
+        for t, c in enumerate(cells):
+            ptil[c] = sol[t]
+    flux[internal] = cT[internal] * (ptil[ci[internal]] - ptil[cj[internal]])
+    dflux = dT * (ptil[dc] - dp)
+    return flux, dflux, pp, ptil
+
+
+def cell_balance(sysm, prob, flux, dflux):
+    """Net outflow minus source per cell (zero for a conservative field)."""
+    ci, cj, _ = connections(sysm, prob)
+    dc = sysm.dirichlet[0]
+    out = np.zeros(sysm.n)
+    np.add.at(out, ci, flux)
+    np.subtract.at(out, cj, flux)
+    np.add.at(out, dc, dflux)
+    return out - (sysm.q - sysm.q_dirichlet)

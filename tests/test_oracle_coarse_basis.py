@@ -1,0 +1,211 @@
+"""Pins of the oracle's coarse grids (Sec. 3, Table 2) and basis functions
+(Sec. 3.1, Appendix A)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import assemble, basis, coarsen, geometry
+from paper_1705_05784_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cases():
+    cases, cur = [], None
+    for line in open(os.path.join(GOLDEN, "bfs_networks.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, _, val = line.partition(" ")
+        if key == "case":
+            cur = {"name": val}
+        elif key == "end":
+            cases.append(cur)
+        elif key == "edges":
+            cur["edges"] = [tuple(int(t) for t in e.split("-")) for e in val.split()]
+        elif key in ("vertices", "primal"):
+            cur[key] = [int(t) for t in val.split()]
+        else:
+            cur[key] = int(val)
+    return cases
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c["name"])
+def test_bfs_golden(case):
+    n = case["n"]
+    adj = [set() for _ in range(n)]
+    for a, b in case["edges"]:
+        adj[a].add(b)
+        adj[b].add(a)
+    adj = [sorted(s) for s in adj]
+    verts, prim, level = coarsen.bfs_coarsen(list(range(n)), adj, case["dmin"])
+    assert verts == case["vertices"]
+    assert [prim[c] for c in range(n)] == case["primal"]
+
+
+def _bfs_dist(adj, src):
+    from collections import deque
+    d = {src: 0}
+    q = deque([src])
+    while q:
+        c = q.popleft()
+        for m in adj[c]:
+            if m not in d:
+                d[m] = d[c] + 1
+                q.append(m)
+    return d
+
+
+def test_bfs_spacing_and_coverage_random_networks():
+    for seed in range(6):
+        p = inputs.config_2d(48, 1.0, 4.0, 12, (10, 40), 1e2, 8, 6, seed=seed)
+        g = geometry.build_geometry(p)
+        lab, nets = coarsen.fracture_networks(g.strike_adj)
+        for cells in nets:
+            verts, prim, level = coarsen.bfs_coarsen(cells, g.strike_adj, 6)
+            # every cell assigned, each vertex owns its block
+            assert sorted(prim) == cells
+            for k, v in enumerate(verts):
+                assert prim[v] == k and level[v] == 0
+            # Table 2 guarantees at least d_min cells between coarse nodes
+            for v in verts:
+                d = _bfs_dist(g.strike_adj, v)
+                for w in verts:
+                    if w != v:
+                        assert d[w] >= 6
+            # each primal block is connected
+            for k in range(len(verts)):
+                blk = {c for c in cells if prim[c] == k}
+                d = _bfs_dist({c: [m for m in g.strike_adj[c] if m in blk] for c in blk},
+                              verts[k])
+                assert set(d) == blk
+
+
+def test_axis_blocks_nodes():
+    blk, node, nb = coarsen.axis_blocks(32, 4)
+    assert nb == 8 and list(node) == [0, 6, 10, 14, 18, 22, 26, 31]
+    blk, node, nb = coarsen.axis_blocks(10, 4)
+    assert list(node) == [0, 6, 9]
+    blk, node, nb = coarsen.axis_blocks(5, 8)
+    assert list(node) == [2]
+
+
+def _setup(p):
+    g = geometry.build_geometry(p)
+    s = assemble.assemble(p, g)
+    c = coarsen.build_coarse(p, g)
+    return g, s, c
+
+
+def test_matrix_rank_counts_2d():
+    p = inputs.config_2d(32, 1.0, 4.0, 0, (1, 2), 1.0, 4, 4, seed=1)
+    g, s, c = _setup(p)
+    rk = c.rank[: g.n_matrix]
+    nodes = 8
+    assert (rk == 3).sum() == nodes * nodes
+    assert (rk == 2).sum() == 2 * nodes * (32 - nodes)
+    assert (rk == 1).sum() == (32 - nodes) ** 2
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_staged_equals_appendix_formulas(variant, dim):
+    if dim == 2:
+        p = inputs.config_2d(24, 1.0, 4.0, 4, (6, 16), 1e3, 4, 4, seed=7, basis=variant)
+    else:
+        p = inputs.config_3d(12, 12, 8, 1.0, (4, 4, 2), 3, (4, 9), 1e3, (4, 4, 4), 4, 4,
+                             seed=3, basis=variant)
+        p.fracs[:, 4] = 0.0
+        p.fracs[:, 5] = 8.0
+    g, s, c = _setup(p)
+    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant)
+    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant)
+    assert abs(P1 - P2).max() < 1e-12
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_basis_invariants(variant):
+    p = inputs.config_2d(32, 1.5, 6.0, 6, (8, 20), 1e4, 4, 5, seed=9, basis=variant)
+    g, s, c = _setup(p)
+    P = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant)
+    nm = g.n_matrix
+    ncm = c.n_coarse_matrix
+    # partition of unity (end of Sec. 3.1)
+    assert np.abs(np.asarray(P.sum(axis=1)).ravel() - 1).max() < 1e-12
+    # vertex rows are the Kronecker delta (Eq. 16)
+    for j, v in enumerate(c.node_cell):
+        row = P.getrow(v)
+        assert row.nnz == 1 and row.indices[0] == j and row.data[0] == 1.0
+    # local SPD M-matrix problems: 0 <= P <= 1
+    assert P.data.min() > -1e-13 and P.data.max() < 1 + 1e-13
+    Pd = P.toarray()
+    Pmf, Pfm = Pd[:nm, ncm:], Pd[nm:, :ncm]
+    if variant == 0:
+        assert not Pmf.any() and not Pfm.any()
+    if variant == 1:
+        assert not Pfm.any() and Pmf.any()
+    if variant == 2:
+        assert not Pmf.any() and Pfm.any()
+    if variant == 3:
+        assert Pmf.any() and Pfm.any()
+    # truncation keeps partition of unity and drops small entries (Sec. 4.3)
+    Q = basis.truncate(P, 1e-2)
+    assert np.abs(np.asarray(Q.sum(axis=1)).ravel() - 1).max() < 1e-12
+    assert np.abs(Q.data).min() >= 1e-2 - 1e-15
+    assert Q.nnz < P.nnz
+
+
+def _hat(n, nodes, i, J):
+    """1D piecewise-linear hat of node J evaluated at cell i."""
+    x = nodes
+    if i <= x[0]:
+        return 1.0 if J == 0 else 0.0
+    if i >= x[-1]:
+        return 1.0 if J == len(x) - 1 else 0.0
+    k = np.searchsorted(x, i, side="right") - 1
+    w = (i - x[k]) / (x[k + 1] - x[k])
+    if J == k:
+        return 1 - w
+    if J == k + 1:
+        return w
+    return 0.0
+
+
+def test_homogeneous_basis_is_tensor_product_hat():
+    """In a homogeneous fracture-free medium the local problems are discrete
+    Laplace problems whose solutions are the bilinear (trilinear) interpolants
+    between node lines, so P is the tensor product of 1D hats."""
+    for dim, shape, C in ((2, (20, 13, 1), (4, 5, 1)), (3, (9, 10, 7), (4, 3, 3))):
+        nx, ny, nz = shape
+        p = inputs.Problem(dim=dim, nx=nx, ny=ny, nz=nz, perm=np.ones(nx * ny * nz),
+                           fracs=np.zeros((0, 4 if dim == 2 else 6)), kf=np.zeros(0),
+                           coarsen=C)
+        g, s, c = _setup(p)
+        P = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, 0).toarray()
+        _, ndx, nbx = coarsen.axis_blocks(nx, C[0])
+        _, ndy, nby = coarsen.axis_blocks(ny, C[1])
+        _, ndz, nbz = coarsen.axis_blocks(nz, C[2] if dim == 3 else 1)
+        want = np.zeros_like(P)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    for K in range(nbz):
+                        for J in range(nby):
+                            for I in range(nbx):
+                                want[x + nx * (y + ny * z), I + nbx * (J + nby * K)] = (
+                                    _hat(nx, ndx, x, I) * _hat(ny, ndy, y, J)
+                                    * (_hat(nz, ndz, z, K) if dim == 3 else 1.0))
+        np.testing.assert_allclose(P, want, rtol=0, atol=1e-13)
+
+
+def test_truncation_example():
+    P = sp.csr_matrix(np.array([[0.5, 0.495, 0.005], [0.004, 0.006, 0.99], [0.3, 0.3, 0.4]]))
+    Q = basis.truncate(P, 1e-2).toarray()
+    np.testing.assert_allclose(Q[0], [0.5 / 0.995, 0.495 / 0.995, 0.0])
+    np.testing.assert_allclose(Q[1], [0.0, 0.0, 1.0])
+    np.testing.assert_allclose(Q[2], [0.3, 0.3, 0.4])
+    # a row whose every entry is below alpha keeps its largest one
+    R = basis.truncate(sp.csr_matrix(np.array([[0.3, 0.3, 0.4]])), 0.5).toarray()
+    np.testing.assert_allclose(R, [[0.0, 0.0, 1.0]])

@@ -1,0 +1,135 @@
+"""Pins of the oracle's coarse system, ILU(0), Table 1 iteration and flux
+reconstruction (Sec. 3.2)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+from oracle import assemble, basis, coarsen, geometry, solver
+from paper_1705_05784_gb300 import inputs
+
+
+def _small(variant=0, restriction=1, **kw):
+    p = inputs.config_2d(24, 1.0, 4.0, 4, (6, 16), 1e2, 4, 4, seed=7, basis=variant,
+                         restriction=restriction, **kw)
+    return p
+
+
+def test_ilu0_reproduces_a_on_its_pattern():
+    p = _small()
+    s = assemble.assemble(p)
+    F = solver.ilu0(s.A)
+    L = sp.tril(F, -1) + sp.identity(s.n)
+    U = sp.triu(F)
+    LU = (L @ U).tocsr()
+    A = s.A.tocoo()
+    d = np.asarray(LU[A.row, A.col]).ravel() - A.data
+    assert np.abs(d).max() < 1e-12 * np.abs(A.data).max()
+
+
+def test_ilu0_is_exact_lu_without_fill():
+    n = 30
+    rng = np.random.default_rng(1)
+    off = -rng.uniform(0.5, 2, n - 1)
+    diag = rng.uniform(5, 6, n)
+    A = sp.diags([off, diag, off], [-1, 0, 1], format="csr")
+    F = solver.ilu0(A)
+    b = rng.standard_normal(n)
+    x = solver.ilu0_apply(F, b)
+    np.testing.assert_allclose(A @ x, b, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+def test_coarse_operator_properties(restriction):
+    p = _small(variant=3, restriction=restriction)
+    g = geometry.build_geometry(p)
+    s = assemble.assemble(p, g)
+    c = coarsen.build_coarse(p, g)
+    P = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, 3)
+    R = solver.restriction(P, c.primal, c.n_coarse, restriction)
+    # zero row sums of R A0 P: A0 1 = 0 and P 1 = 1
+    Ac0 = (R @ s.A0 @ P).toarray()
+    assert np.abs(Ac0.sum(axis=1)).max() < 1e-10 * np.abs(Ac0).max()
+    Ac = (R @ s.A @ P).toarray()
+    if restriction == 1:
+        assert np.abs(Ac - Ac.T).max() < 1e-12 * np.abs(Ac).max()
+        assert np.linalg.eigvalsh(0.5 * (Ac + Ac.T)).min() > 0
+    # after the multiscale stage the restricted residual vanishes:
+    # R (r - A P (R A P)^-1 R r) = 0
+    st = solver.setup(s, P, c.primal, c.n_coarse, restriction)
+    r = s.q - s.A @ np.zeros(s.n)
+    import scipy.linalg as sla
+    dp = P @ sla.lu_solve(st.lu, R @ r)
+    r1 = r - s.A @ dp
+    assert np.abs(R @ r1).max() < 1e-11 * np.abs(R @ r).max()
+
+
+def test_coarsening_ratio_one_is_a_direct_solve():
+    p = inputs.config_2d(12, 1.0, 3.0, 0, (1, 2), 1.0, 1, 1, seed=2)
+    r = oracle.run(p)
+    assert r.iters == 1 and r.rel_res < 1e-13
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+def test_homogeneous_one_multiscale_step_is_exact(restriction):
+    """With node lines on the boundary cells the coarse space contains the
+    linear pressure of a homogeneous fracture-free W/E problem."""
+    nx, ny = 40, 24
+    p = inputs.Problem(dim=2, nx=nx, ny=ny, nz=1, perm=np.ones(nx * ny),
+                       fracs=np.zeros((0, 4)), kf=np.zeros(0), coarsen=(8, 8, 1),
+                       restriction=restriction)
+    g, sysm, c, P, st = oracle.build(p)
+    x, it, rr, ok, _ = solver.two_stage_solve(st, max_iter=1, smoother=False)
+    np.testing.assert_allclose(x, np.tile(1 - (np.arange(nx) + 0.5) / nx, ny), atol=1e-13)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_converged_iterate_matches_direct_solve(variant):
+    p = _small(variant=variant)
+    r = oracle.run(p)
+    assert r.converged
+    x = spla.spsolve(r.sysm.A.tocsc(), r.sysm.q)
+    assert np.linalg.norm(r.p - x) / np.linalg.norm(x) < 1e-6
+    # the iteration count is the number of completed Table 1 sweeps
+    assert len(r.history) == r.iters + 1
+
+
+def test_zero_fracture_decoupled_is_plain_ams():
+    """Decoupled-AMS with no fractures reduces to AMS on the matrix alone:
+    every variant gives the same P and iterate."""
+    p = inputs.config_2d(24, 1.0, 4.0, 0, (1, 2), 1.0, 4, 4, seed=3)
+    res = []
+    for v in range(4):
+        p.basis = v
+        res.append(oracle.run(p))
+    for r in res[1:]:
+        assert abs(r.P - res[0].P).max() == 0.0
+        assert r.iters == res[0].iters
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_flux_reconstruction_is_conservative(variant):
+    p = _small(variant=variant, restriction=1)
+    p.tol = 1e-3          # stop early: the reconstruction works after any iteration
+    r = oracle.run(p)
+    g, sysm, c, P, st = oracle.build(p)
+    st_fv = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FV)
+    flux, dflux, pp, pt = solver.reconstruct_flux(sysm, p, st_fv, r.p, c.primal, c.node_cell)
+    bal = solver.cell_balance(sysm, p, flux, dflux)
+    scale = np.abs(flux).max()
+    assert np.abs(bal).max() < 1e-12 * max(scale, 1.0)
+    # the W/E problem: total inflow at the west face equals outflow at the east
+    dc, dT, dp, fid = sysm.dirichlet
+    assert abs(dflux[fid == 0].sum() + dflux[fid == 1].sum()) < 1e-10 * scale
+
+
+def test_flux_of_exact_solution_is_two_point_flux():
+    p = _small(variant=0, restriction=1)
+    g, sysm, c, P, st = oracle.build(p)
+    x = spla.spsolve(sysm.A.tocsc(), sysm.q)
+    st_fv = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FV)
+    flux, dflux, pp, pt = solver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
+    ci, cj, cT = solver.connections(sysm, p)
+    np.testing.assert_allclose(flux, cT * (x[ci] - x[cj]), rtol=0,
+                               atol=1e-9 * np.abs(flux).max())
