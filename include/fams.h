@@ -1,0 +1,187 @@
+/*
+ * fams.h - C ABI of libfams, a GB300 (sm_103a) implementation of the F-AMS
+ * two-stage pressure solver for heterogeneous porous media with embedded
+ * discrete fractures (Tene, Al Kobaisi, Hajibeygi, arXiv 1705.05784).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: FAMS_OK (0) or a negative FAMS_E*
+ *    code; fams_strerror() gives its text and fams_last_error() a one-line
+ *    detail of the most recent failure on the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Array arguments may be host or device pointers (detected with
+ *    cudaPointerGetAttributes).  Input arrays stay owned by the caller and are
+ *    copied during the call; output arrays are written during the call.
+ *  - Unknown ordering (Eq. 8, block order [m; f]): matrix cells first in
+ *    natural order (x fastest, then y, then z), then fracture cells: fractures
+ *    in input order, within a fracture along-strike index fastest, then layer.
+ *  - A context owns all device memory of its instances (fine system, coarse
+ *    grids, P, R, coarse factors, ILU(0) factors, work vectors); it is freed
+ *    by fams_destroy().  All work is issued on the context's own CUDA stream
+ *    and every call returns only after that work has finished.
+ *  - A batch context holds several independent instances (a block-diagonal
+ *    system): kernels process all instances together and one CTA per instance
+ *    runs the sequential parts, so results of an instance do not depend on
+ *    what else is in the batch.
+ */
+#ifndef FAMS_H
+#define FAMS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* coupling strategy of the basis functions (Sec. 3.1, Eqs. 19-22) */
+enum { FAMS_DECOUPLED = 0, FAMS_FRAC = 1, FAMS_ROCK = 2, FAMS_COUPLED = 3 };
+/* restriction operator (Sec. 3.2): finite volume (R^FV) or finite element (R^FE = P^T) */
+enum { FAMS_R_FV = 0, FAMS_R_FE = 1 };
+/* arithmetic of the iteration: FP64 throughout, or FP32 inner stages with
+   FP64 outer residual, coarse solve and refinement */
+enum { FAMS_FP64 = 0, FAMS_MIXED = 1 };
+
+enum {
+  FAMS_OK = 0,
+  FAMS_EINVAL = -1,      /* bad argument or an input the method cannot handle */
+  FAMS_ENOMEM = -2,      /* device allocation failed */
+  FAMS_ENOCONV = -3,     /* max_iter reached; x holds the last iterate */
+  FAMS_EBREAKDOWN = -4,  /* zero or non-finite pivot in a factorisation */
+  FAMS_ETIMEOUT = -5,    /* a bounded device wait gave up */
+  FAMS_ECUDA = -6,       /* a CUDA runtime call failed */
+  FAMS_ECAPACITY = -7    /* a local problem exceeds a compiled-in size limit */
+};
+
+/* Dirichlet face bits; faces not in the mask are no-flow */
+enum { FAMS_BC_WEST = 1, FAMS_BC_EAST = 2, FAMS_BC_SOUTH = 4, FAMS_BC_NORTH = 8,
+       FAMS_BC_BOTTOM = 16, FAMS_BC_TOP = 32 };
+
+typedef struct fams_ctx fams_ctx;   /* opaque, owned by the library */
+
+/* Structured matrix grid (Sec. 2).  dim = 2 or 3; in 2D nz must be 1 and dz is
+   the slab thickness.  bc_value[f] is the pressure on Dirichlet face f
+   (order W, E, S, N, B, T).  At least one Dirichlet face is required. */
+typedef struct {
+  int dim, nx, ny, nz;
+  double dx, dy, dz;
+  int bc_mask;
+  double bc_value[6];
+} fams_grid;
+
+/* Fractures (Sec. 2, Eqs. 4-7).  2D: n segments, xy[4i..4i+3] = x0,y0,x1,y1.
+   3D: n vertical plates, xy[6i..6i+5] = x0,y0,x1,y1,z0,z1 (layers whose centre
+   lies in [z0,z1)).  Coordinates are physical; segments are clipped to the
+   domain.  kf[i] is the fracture permeability (mu = 1), aperture the width a_f,
+   h_f the target fracture cell length. */
+typedef struct {
+  int n;
+  const double* xy;
+  const double* kf;
+  double aperture;
+  double h_f;
+} fams_fracs;
+
+/* Method options.  coarsen[] = matrix coarsening ratio per axis; frac_dmin =
+   d_min of the distance-based fracture coarsening (Table 2; <= 0 means
+   infinity, one coarse node per network); frac_cz = vertical coarsening of 3D
+   fracture plates; alpha = truncation threshold of P (Sec. 4.3, 0 = none);
+   max_iter bounds the Table 1 loop; precision = FAMS_FP64 or FAMS_MIXED. */
+typedef struct {
+  int coarsen[3];
+  int frac_dmin;
+  int frac_cz;
+  int basis;
+  int restriction;
+  double alpha;
+  int max_iter;
+  int precision;
+} fams_opts;
+
+/* Per-solve statistics (nullable argument). */
+typedef struct {
+  int iterations;        /* completed Table 1 sweeps */
+  double rel_residual;   /* ||q - A x||_2 / ||q||_2 after the last sweep */
+  int converged;
+  double solve_ms;       /* device time of the iteration */
+} fams_stats;
+
+/* fams_setup - build one instance: EDFM geometry and fine system (Sec. 2),
+   coarse grids (Sec. 3, Table 2), basis functions and P (Sec. 3.1, App. A),
+   truncation (Sec. 4.3), R and the coarse factor of R A P (Sec. 3.2), and the
+   ILU(0) smoother (Sec. 3.2).
+   perm: n_matrix permeabilities, x fastest.  On success *out owns the
+   context.  Errors: FAMS_EINVAL (bad sizes, no Dirichlet face, plates of one
+   network with different layer ranges), FAMS_ENOMEM, FAMS_EBREAKDOWN,
+   FAMS_ECAPACITY, FAMS_ECUDA. */
+int fams_setup(const fams_grid* grid, const double* perm, const fams_fracs* fracs,
+               const fams_opts* opts, fams_ctx** out);
+
+/* fams_setup_batch - n independent instances in one context (instance i uses
+   grids[i], perms[i], fracs[i], opts[i]).  Same errors as fams_setup. */
+int fams_setup_batch(int n, const fams_grid* grids, const double* const* perms,
+                     const fams_fracs* fracs, const fams_opts* opts, fams_ctx** out);
+
+/* fams_sizes - counts of instance `inst`: fine unknowns of the matrix and the
+   fractures, coarse unknowns, matrix faces (x, y then z faces including the
+   boundary faces), and fracture connections (matrix-fracture then
+   fracture-fracture).  Null pointers are skipped. */
+int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n_coarse,
+               int* n_faces, int* n_nnc);
+
+/* fams_solve - Table 1 (steps 3, 5-8) on instance 0 of ctx from the initial
+   guess in x until ||q - A x||_2 <= tol ||q||_2, q = rhs + Dirichlet terms.
+   rhs: n_matrix + n_frac sources (nullable = 0); x: in initial guess, out
+   pressure.  FAMS_ENOCONV leaves the last iterate in x. */
+int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st);
+
+/* fams_solve_batch - the same for every instance of a batch context; rhs[i]
+   (nullable) and x[i] per instance, st nullable or an array of n_instances.
+   Returns FAMS_ENOCONV if any instance did not converge. */
+int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
+                     fams_stats* st);
+
+/* fams_flux - conservative fine-scale flux field from an iterate x of
+   instance `inst`: one finite-volume multiscale stage, then a local TPFA
+   problem per primal block with the block-boundary fluxes as Neumann data
+   (Sec. 3.2; after any iteration, Sec. 1).  face_flux: n_faces values, x faces
+   ((nx+1) ny nz, x fastest), then y faces, then z faces, positive along +axis
+   (no-flow boundary faces are 0).  nnc_flux: n_nnc values, matrix-fracture
+   connections (positive matrix -> fracture) in fams_query(FAMS_Q_NNC_*) order,
+   then fracture-fracture connections (positive from the lower to the higher
+   fracture cell index). */
+int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, double* nnc_flux);
+
+/* fams_query - copy an internal array of instance `inst` into out (host or
+   device, capacity `cap` elements of the stated type).  Returns the element
+   count (>= 0) or a negative error; with out == NULL only the count.  For the
+   parity tests and for diagnostics. */
+enum {
+  FAMS_Q_NNC_FRAC = 1,     /* int32  matrix-fracture connections: fracture cell (local) */
+  FAMS_Q_NNC_MATRIX = 2,   /* int32  ... matrix cell */
+  FAMS_Q_NNC_AREA = 3,     /* double ... A_ij */
+  FAMS_Q_NNC_DIST = 4,     /* double ... <d>_ij */
+  FAMS_Q_FF_A = 5,         /* int32  fracture-fracture connections: lower cell */
+  FAMS_Q_FF_B = 6,         /* int32  ... higher cell */
+  FAMS_Q_FF_T = 7,         /* double ... transmissibility */
+  FAMS_Q_A_ROWPTR = 8,     /* int32  CSR of A (n+1) */
+  FAMS_Q_A_COL = 9,        /* int32 */
+  FAMS_Q_A_VAL = 10,       /* double */
+  FAMS_Q_Q = 11,           /* double total rhs q (sources + Dirichlet terms) */
+  FAMS_Q_RANK = 12,        /* int32  wirebasket rank per cell (V=3,E=2,F=1,I=0) */
+  FAMS_Q_PRIMAL = 13,      /* int32  primal block = coarse index per cell */
+  FAMS_Q_NODE_CELL = 14,   /* int32  node cell of each coarse unknown */
+  FAMS_Q_P_ROWPTR = 15,    /* int32  CSR of P (after truncation) */
+  FAMS_Q_P_COL = 16,       /* int32 */
+  FAMS_Q_P_VAL = 17,       /* double */
+  FAMS_Q_AC = 18,          /* double dense coarse operator R A P, row-major */
+  FAMS_Q_ILU_VAL = 19,     /* double ILU(0) factors in the pattern of A */
+  FAMS_Q_LEVELS = 20       /* int32  number of ILU(0) levels (1 value) */
+};
+int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap);
+
+int fams_num_instances(const fams_ctx* ctx);
+void fams_destroy(fams_ctx* ctx);
+const char* fams_strerror(int status);
+const char* fams_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FAMS_H */

@@ -23,7 +23,8 @@ Embedded discrete fractures on a structured matrix grid:
   (floored at 1e-3 h_f).
 
 All floating-point expressions that decide an integer (which cell a piece
-lies in) are written out in one fixed order so that another IEEE-754 double
+lies in, how many cells a fracture has) use only correctly rounded IEEE-754
+operations (+ - * / sqrt floor), written out in one fixed order so that another IEEE-754 double
 implementation without fused multiply-add reproduces them exactly.
 """
 from __future__ import annotations
@@ -66,12 +67,16 @@ def _floor_div(v, h):
     return int(math.floor(v / h))
 
 
-def piece_overlaps(ax, ay, bx, by, n, s, dx, dy, nx, ny):
+def _len(ex, ey):
+    return math.sqrt(ex * ex + ey * ey)
+
+
+def piece_overlaps(ax, ay, bx, by, n, s, dx, dy, nx, ny, hf=1.0):
     """Clip fracture cell s (parameter [s/n,(s+1)/n] of segment A->B) against
-    the matrix columns.  Returns a list of (ix, iy, length) in order along the
-    fracture, pieces in the same column merged."""
+    the matrix columns.  Returns a list of (ix, iy, length) sorted by column
+    index ix + nx iy, pieces in the same column merged."""
     ex, ey = bx - ax, by - ay
-    L = math.sqrt(ex * ex + ey * ey)
+    L = _len(ex, ey)
     ts = s / n
     te = (s + 1) / n
     brk = [ts, te]
@@ -94,25 +99,28 @@ def piece_overlaps(ax, ay, bx, by, n, s, dx, dy, nx, ny):
     for k in range(len(brk) - 1):
         t0, t1 = brk[k], brk[k + 1]
         ln = (t1 - t0) * L
-        if ln < ZERO_PIECE:
+        if ln < ZERO_PIECE * hf:
             continue
         tm = 0.5 * (t0 + t1)
         px = ax + tm * ex
         py = ay + tm * ey
         ix = min(max(_floor_div(px, dx), 0), nx - 1)
         iy = min(max(_floor_div(py, dy), 0), ny - 1)
-        if out and out[-1][0] == ix and out[-1][1] == iy:
-            out[-1][2] += ln
-        else:
-            out.append([ix, iy, ln])
-    return [tuple(o) for o in out]
+        out.append((ix, iy, ln))
+    # one connection per matrix column: pieces in the same column are summed
+    # (in the order they lie along the fracture), then sorted by column index
+    merged = {}
+    for ix, iy, ln in out:
+        key = ix + nx * iy
+        merged[key] = (ix, iy, merged[key][2] + ln) if key in merged else (ix, iy, ln)
+    return [merged[k] for k in sorted(merged)]
 
 
 def mean_distance(ax, ay, bx, by, ix, iy, dx, dy):
     """<d>: mean distance from matrix cell (ix,iy) to the infinite line through A,B
     (Eq. 7), by the 64 x 64 midpoint rule."""
     ex, ey = bx - ax, by - ay
-    L = math.sqrt(ex * ex + ey * ey)
+    L = _len(ex, ey)
     tx, ty = ex / L, ey / L
     m = MIDPOINT_N
     u = (np.arange(m, dtype=np.float64) + 0.5) / m
@@ -165,7 +173,7 @@ def build_geometry(prob):
         c = clip_segment(fr[f, 0], fr[f, 1], fr[f, 2], fr[f, 3], lx, ly)
         ns = 0
         if c is not None:
-            L = math.hypot(c[2] - c[0], c[3] - c[1])
+            L = _len(c[2] - c[0], c[3] - c[1])
             if L >= ZERO_PIECE * hf:
                 ns = max(1, int(math.floor(L / hf + 0.5)))
                 g.seg[f] = c
@@ -207,7 +215,7 @@ def build_geometry(prob):
             continue
         ax, ay, bx, by = g.seg[f]
         for s in range(ns):
-            ov = piece_overlaps(ax, ay, bx, by, ns, s, dx, dy, nx, ny)
+            ov = piece_overlaps(ax, ay, bx, by, ns, s, dx, dy, nx, ny, hf)
             for (ix, iy, ln) in ov:
                 dmean = mean_distance(ax, ay, bx, by, ix, iy, dx, dy)
                 if dim == 2:
@@ -230,7 +238,7 @@ def build_geometry(prob):
         if ns == 0:
             continue
         ax, ay, bx, by = g.seg[f]
-        h = math.hypot(bx - ax, by - ay) / ns
+        h = _len(bx - ax, by - ay) / ns
         nk = g.frac_nk[f] if dim == 3 else 1
         for kk in range(nk):
             for s in range(ns - 1):
@@ -255,8 +263,8 @@ def build_geometry(prob):
             na, nb = g.frac_ns[fa], g.frac_ns[fb]
             sa = min(int(math.floor(t * na)), na - 1)
             sb = min(int(math.floor(u * nb)), nb - 1)
-            La = math.hypot(g.seg[fa][2] - g.seg[fa][0], g.seg[fa][3] - g.seg[fa][1])
-            Lb = math.hypot(g.seg[fb][2] - g.seg[fb][0], g.seg[fb][3] - g.seg[fb][1])
+            La = _len(g.seg[fa][2] - g.seg[fa][0], g.seg[fa][3] - g.seg[fa][1])
+            Lb = _len(g.seg[fb][2] - g.seg[fb][0], g.seg[fb][3] - g.seg[fb][1])
             da = max(abs(t - (sa + 0.5) / na) * La, DIST_FLOOR * hf)
             db = max(abs(u - (sb + 0.5) / nb) * Lb, DIST_FLOOR * hf)
             Ta = kf[fa] * af * depth / da
@@ -315,8 +323,8 @@ def segment_intersection(sa, sb):
     d1x, d1y = bx - ax, by - ay
     d2x, d2y = ex - cx, ey - cy
     den = d1x * d2y - d1y * d2x
-    n1 = math.hypot(d1x, d1y)
-    n2 = math.hypot(d2x, d2y)
+    n1 = _len(d1x, d1y)
+    n2 = _len(d2x, d2y)
     if abs(den) <= 1e-14 * n1 * n2:
         return None
     wx, wy = cx - ax, cy - ay

@@ -1,0 +1,429 @@
+// C ABI of libfams (include/fams.h): argument checks, batch bookkeeping and
+// the order of the setup phases.  Every computation of the method runs in the
+// kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "batch.cuh"
+
+struct fams_ctx {
+  fams::Batch b;
+};
+
+namespace fams {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int Batch::upload_inst() {
+  std::vector<int> o(8 * (B + 1));
+  for (int i = 0; i <= B; ++i) {
+    bool last = i == B;
+    const Inst* I = last ? nullptr : &h[i];
+    o[0 * (B + 1) + i] = last ? (int)tot_m : I->m_off;
+    o[1 * (B + 1) + i] = last ? (int)tot_fr : I->fr_off;
+    o[2 * (B + 1) + i] = last ? (int)tot_fc : I->fc_off;
+    o[3 * (B + 1) + i] = last ? (int)tot_s : I->s_off;
+    o[4 * (B + 1) + i] = last ? (int)tot_row : I->row_off;
+    o[5 * (B + 1) + i] = last ? (int)tot_pair : I->inter_off;
+    o[6 * (B + 1) + i] = last ? (int)tot_nc : I->nc_off;
+    o[7 * (B + 1) + i] = last ? (int)tot_net : I->net_off;
+  }
+  FAMS_CUDA(cudaMemcpyAsync(off_m, o.data(), sizeof(int) * 8 * (B + 1), cudaMemcpyHostToDevice, stream));
+  FAMS_CUDA(cudaMemcpyAsync(d_inst, h.data(), sizeof(Inst) * B, cudaMemcpyHostToDevice, stream));
+  FAMS_CUDA(cudaStreamSynchronize(stream));
+  return FAMS_OK;
+}
+
+int Batch::check_err(const char* phase) {
+  int e = 0;
+  FAMS_CUDA(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  FAMS_CUDA(cudaStreamSynchronize(stream));
+  FAMS_CUDA(cudaGetLastError());
+  if (e == DERR_NONE) return FAMS_OK;
+  FAMS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
+  std::string p(phase);
+  switch (e) {
+    case DERR_BREAKDOWN: set_error(p + ": zero or non-finite pivot"); return FAMS_EBREAKDOWN;
+    case DERR_CAPACITY: set_error(p + ": a local problem exceeds a compiled-in size limit"); return FAMS_ECAPACITY;
+    case DERR_TIMEOUT: set_error(p + ": a bounded device wait gave up"); return FAMS_ETIMEOUT;
+    case DERR_FLOATING: set_error(p + ": a dual block has no link to known basis values"); return FAMS_EINVAL;
+    default: set_error(p + ": invalid input"); return FAMS_EINVAL;
+  }
+}
+
+namespace {
+
+int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
+  auto bad = [](const char* m) { set_error(m); return FAMS_EINVAL; };
+  if (g.dim != 2 && g.dim != 3) return bad("grid.dim must be 2 or 3");
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1) return bad("grid sizes must be >= 1");
+  if (g.dim == 2 && g.nz != 1) return bad("2D grids need nz = 1");
+  if (!(g.dx > 0) || !(g.dy > 0) || !(g.dz > 0)) return bad("cell sizes must be > 0");
+  int faces = g.dim == 3 ? 0x3f : 0x0f;
+  if ((g.bc_mask & faces) == 0) return bad("at least one Dirichlet face is required");
+  if ((long long)g.nx * g.ny * g.nz > 200000000LL) return bad("grid too large");
+  if (f && f->n < 0) return bad("fracs.n < 0");
+  if (f && f->n > 0 && (!f->xy || !f->kf)) return bad("fracture arrays missing");
+  if (f && f->n > 0 && (!(f->aperture > 0) || !(f->h_f > 0))) return bad("aperture and h_f must be > 0");
+  for (int a = 0; a < g.dim; ++a)
+    if (o.coarsen[a] < 1) return bad("coarsening ratios must be >= 1");
+  if (o.basis < 0 || o.basis > 3) return bad("basis must be 0..3");
+  if (o.restriction != FAMS_R_FV && o.restriction != FAMS_R_FE) return bad("restriction must be FV or FE");
+  if (!(o.alpha >= 0.0) || !(o.alpha < 1.0)) return bad("alpha must be in [0, 1)");
+  if (o.max_iter < 0) return bad("max_iter must be >= 0");
+  if (o.precision != FAMS_FP64) return bad("only FAMS_FP64 is available in this build");
+  if (g.dim == 3 && o.frac_cz < 1) return bad("frac_cz must be >= 1");
+  return FAMS_OK;
+}
+
+int setup_batch(int n, const fams_grid* grids, const double* const* perms, const fams_fracs* fracs,
+                const fams_opts* opts, Batch& b) {
+  b.B = n;
+  FAMS_CUDA(cudaGetDevice(&b.device));
+  FAMS_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+  b.h.assign(n, Inst{});
+  long long m = 0, fr = 0;
+  for (int i = 0; i < n; ++i) {
+    const fams_grid& g = grids[i];
+    const fams_opts& o = opts[i];
+    Inst& I = b.h[i];
+    I.dim = g.dim; I.nx = g.nx; I.ny = g.ny; I.nz = g.dim == 3 ? g.nz : 1;
+    I.dx = g.dx; I.dy = g.dy; I.dz = g.dz;
+    I.bc_mask = g.bc_mask & (g.dim == 3 ? 0x3f : 0x0f);
+    for (int k = 0; k < 6; ++k) I.bc_val[k] = g.bc_value[k];
+    int nf = fracs ? fracs[i].n : 0;
+    I.aperture = nf ? fracs[i].aperture : 1.0;
+    I.hf = nf ? fracs[i].h_f : 1.0;
+    I.cx = o.coarsen[0]; I.cy = o.coarsen[1]; I.cz = g.dim == 3 ? o.coarsen[2] : 1;
+    I.dmin = o.frac_dmin; I.fcz = std::max(1, o.frac_cz);
+    I.basis = o.basis; I.restriction = o.restriction; I.precision = o.precision;
+    I.max_iter = o.max_iter; I.alpha = o.alpha;
+    I.nm = g.nx * g.ny * I.nz;
+    I.m_off = (int)m;
+    I.nfr = nf;
+    I.fr_off = (int)fr;
+    m += I.nm;
+    fr += nf;
+  }
+  b.tot_m = m;
+  b.tot_fr = fr;
+  FAMS_TRY(b.alloc((void**)&b.off_m, sizeof(int) * 8 * (n + 1)));
+  b.off_fr = b.off_m + (n + 1);
+  b.off_fc = b.off_m + 2 * (n + 1);
+  b.off_s = b.off_m + 3 * (n + 1);
+  b.off_row = b.off_m + 4 * (n + 1);
+  b.off_pair = b.off_m + 5 * (n + 1);
+  b.off_nc = b.off_m + 6 * (n + 1);
+  b.off_net = b.off_m + 7 * (n + 1);
+  FAMS_TRY(b.alloc((void**)&b.d_inst, sizeof(Inst) * n));
+  FAMS_TRY(b.alloc((void**)&b.d_err, sizeof(int)));
+  FAMS_CUDA(cudaMemsetAsync(b.d_err, 0, sizeof(int), b.stream));
+  // inputs (host or device pointers: unified addressing picks the direction)
+  FAMS_TRY(b.alloc((void**)&b.perm, sizeof(double) * (m + 1)));
+  FAMS_TRY(b.alloc((void**)&b.fracs, sizeof(double) * 6 * (fr + 1)));
+  FAMS_TRY(b.alloc((void**)&b.kf, sizeof(double) * (fr + 1)));
+  std::vector<double> hfr(6 * (fr + 1), 0.0), hkf(fr + 1, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const Inst& I = b.h[i];
+    FAMS_CUDA(cudaMemcpyAsync(b.perm + I.m_off, perms[i], sizeof(double) * I.nm, cudaMemcpyDefault,
+                              b.stream));
+    if (I.nfr) {
+      int w = I.dim == 3 ? 6 : 4;
+      std::vector<double> xy((size_t)w * I.nfr);
+      FAMS_CUDA(cudaMemcpy(xy.data(), fracs[i].xy, sizeof(double) * w * I.nfr, cudaMemcpyDefault));
+      FAMS_CUDA(cudaMemcpy(hkf.data() + I.fr_off, fracs[i].kf, sizeof(double) * I.nfr,
+                           cudaMemcpyDefault));
+      for (int f = 0; f < I.nfr; ++f)
+        for (int k = 0; k < w; ++k) hfr[6 * (I.fr_off + f) + k] = xy[(size_t)w * f + k];
+    }
+  }
+  FAMS_CUDA(cudaMemcpyAsync(b.fracs, hfr.data(), sizeof(double) * hfr.size(), cudaMemcpyHostToDevice,
+                            b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.kf, hkf.data(), sizeof(double) * hkf.size(), cudaMemcpyHostToDevice,
+                            b.stream));
+  {
+    std::vector<double> hp(m);
+    FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.perm, sizeof(double) * m, cudaMemcpyDeviceToHost, b.stream));
+    FAMS_CUDA(cudaStreamSynchronize(b.stream));
+    for (double v : hp)
+      if (!(v > 0.0) || !std::isfinite(v)) {
+        set_error("permeability must be positive and finite");
+        return FAMS_EINVAL;
+      }
+    for (long long f = 0; f < fr; ++f)
+      if (!(hkf[f] > 0.0) || !std::isfinite(hkf[f])) {
+        set_error("fracture permeability must be positive and finite");
+        return FAMS_EINVAL;
+      }
+  }
+  FAMS_TRY(b.upload_inst());
+  FAMS_TRY(phase_geometry(b));
+  FAMS_TRY(phase_system(b));
+  FAMS_TRY(phase_coarse(b));
+  FAMS_TRY(phase_basis(b));
+  FAMS_TRY(phase_coarse_op(b, -1));
+  FAMS_TRY(phase_ilu(b));
+  FAMS_TRY(phase_alloc_work(b));
+  FAMS_CUDA(cudaMemcpyAsync(b.q, b.qD, sizeof(double) * b.tot_row, cudaMemcpyDeviceToDevice, b.stream));
+  FAMS_CUDA(cudaMemsetAsync(b.x, 0, sizeof(double) * b.tot_row, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  b.free_tmp();
+  return FAMS_OK;
+}
+
+void destroy_batch(Batch& b) {
+  if (b.stream) cudaStreamSynchronize(b.stream);
+  b.free_tmp();
+  for (void* p : b.owned) cudaFree(p);
+  b.owned.clear();
+  if (b.stream) cudaStreamDestroy(b.stream);
+  b.stream = nullptr;
+}
+
+template <class T>
+int fetch(const Batch& b, const T* src, long long n, std::vector<T>& out) {
+  out.resize(n);
+  if (n > 0) {
+    FAMS_CUDA(cudaMemcpyAsync(out.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost, b.stream));
+    FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  }
+  return FAMS_OK;
+}
+
+}  // namespace
+
+int make_q(Batch& b, const double* rhs_dev);
+
+}  // namespace fams
+
+using namespace fams;
+
+extern "C" {
+
+int fams_setup_batch(int n, const fams_grid* grids, const double* const* perms,
+                     const fams_fracs* fracs, const fams_opts* opts, fams_ctx** out) {
+  if (!out || n < 1 || !grids || !perms || !opts) {
+    set_error("null argument or n < 1");
+    return FAMS_EINVAL;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    FAMS_TRY(validate(grids[i], fracs ? &fracs[i] : nullptr, opts[i]));
+    if (!perms[i]) { set_error("perm is null"); return FAMS_EINVAL; }
+  }
+  fams_ctx* c = new fams_ctx();
+  int s = setup_batch(n, grids, perms, fracs, opts, c->b);
+  if (s != FAMS_OK) {
+    destroy_batch(c->b);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return FAMS_OK;
+}
+
+int fams_setup(const fams_grid* grid, const double* perm, const fams_fracs* fracs,
+               const fams_opts* opts, fams_ctx** out) {
+  if (!grid || !perm || !opts) {
+    set_error("null argument");
+    return FAMS_EINVAL;
+  }
+  const double* perms[1] = {perm};
+  return fams_setup_batch(1, grid, perms, fracs, opts, out);
+}
+
+int fams_num_instances(const fams_ctx* ctx) { return ctx ? ctx->b.B : 0; }
+
+int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n_coarse,
+               int* n_faces, int* n_nnc) {
+  if (!ctx || inst < 0 || inst >= ctx->b.B) { set_error("bad context or instance"); return FAMS_EINVAL; }
+  const Inst& I = ctx->b.h[inst];
+  int nz = I.dim == 3 ? I.nz : 1;
+  if (n_matrix) *n_matrix = I.nm;
+  if (n_frac) *n_frac = I.nf;
+  if (n_coarse) *n_coarse = I.nc;
+  if (n_faces)
+    *n_faces = (I.nx + 1) * I.ny * nz + I.nx * (I.ny + 1) * nz + (I.dim == 3 ? I.nx * I.ny * (nz + 1) : 0);
+  if (n_nnc) *n_nnc = I.nnc + I.nff;
+  return FAMS_OK;
+}
+
+int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
+                     fams_stats* st) {
+  if (!ctx || !x) { set_error("null argument"); return FAMS_EINVAL; }
+  if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return FAMS_EINVAL; }
+  Batch& b = ctx->b;
+  for (int i = 0; i < b.B; ++i)
+    if (!x[i]) { set_error("x is null"); return FAMS_EINVAL; }
+  // rhs staged in the dp work vector
+  FAMS_CUDA(cudaMemsetAsync(b.dp, 0, sizeof(double) * b.tot_row, b.stream));
+  for (int i = 0; i < b.B; ++i) {
+    const Inst& I = b.h[i];
+    if (rhs && rhs[i])
+      FAMS_CUDA(cudaMemcpyAsync(b.dp + I.row_off, rhs[i], sizeof(double) * I.n, cudaMemcpyDefault,
+                                b.stream));
+    FAMS_CUDA(cudaMemcpyAsync(b.x + I.row_off, x[i], sizeof(double) * I.n, cudaMemcpyDefault,
+                              b.stream));
+  }
+  FAMS_TRY(make_q(b, b.dp));
+  float ms = 0.f;
+  FAMS_TRY(run_solve(b, tol, &ms));
+  std::vector<double> stat;
+  FAMS_TRY(fetch(b, b.stat, 4LL * b.B, stat));
+  int status = FAMS_OK;
+  for (int i = 0; i < b.B; ++i) {
+    const Inst& I = b.h[i];
+    FAMS_CUDA(cudaMemcpyAsync(x[i], b.x + I.row_off, sizeof(double) * I.n, cudaMemcpyDefault,
+                              b.stream));
+    if (st) {
+      st[i].iterations = (int)stat[4 * i];
+      st[i].rel_residual = stat[4 * i + 1];
+      st[i].converged = stat[4 * i + 2] > 0.5;
+      st[i].solve_ms = ms;
+    }
+    if (!std::isfinite(stat[4 * i + 1])) {
+      set_error("the iteration produced a non-finite residual");
+      status = FAMS_EBREAKDOWN;
+    } else if (stat[4 * i + 2] < 0.5 && status == FAMS_OK) {
+      set_error("max_iter reached before the tolerance");
+      status = FAMS_ENOCONV;
+    }
+  }
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  return status;
+}
+
+int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st) {
+  if (!ctx || ctx->b.B != 1) { set_error("fams_solve needs a single-instance context"); return FAMS_EINVAL; }
+  const double* r[1] = {rhs};
+  double* xx[1] = {x};
+  return fams_solve_batch(ctx, r, xx, tol, st);
+}
+
+int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, double* nnc_flux) {
+  if (!ctx || !x || !face_flux || !nnc_flux || inst < 0 || inst >= ctx->b.B) {
+    set_error("null argument or bad instance");
+    return FAMS_EINVAL;
+  }
+  Batch& b = ctx->b;
+  int nf = 0, nn = 0;
+  fams_sizes(ctx, inst, nullptr, nullptr, nullptr, &nf, &nn);
+  const Inst& I = b.h[inst];
+  double *dx = nullptr, *df = nullptr, *dn = nullptr;
+  FAMS_CUDA(cudaMalloc(&dx, sizeof(double) * (I.n + 1)));
+  cudaError_t e1 = cudaMalloc(&df, sizeof(double) * (nf + 1));
+  cudaError_t e2 = cudaMalloc(&dn, sizeof(double) * (nn + 1));
+  int s = FAMS_OK;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    set_error("flux buffers");
+    s = FAMS_ENOMEM;
+  }
+  if (s == FAMS_OK && cudaMemcpy(dx, x, sizeof(double) * I.n, cudaMemcpyDefault) != cudaSuccess) {
+    set_error("copy of x");
+    s = FAMS_ECUDA;
+  }
+  if (s == FAMS_OK) s = run_flux(b, inst, dx, df, dn);
+  if (s == FAMS_OK) {
+    if (cudaMemcpy(face_flux, df, sizeof(double) * nf, cudaMemcpyDefault) != cudaSuccess ||
+        (nn > 0 && cudaMemcpy(nnc_flux, dn, sizeof(double) * nn, cudaMemcpyDefault) != cudaSuccess)) {
+      set_error("copy of the fluxes");
+      s = FAMS_ECUDA;
+    }
+  }
+  cudaFree(dx);
+  if (df) cudaFree(df);
+  if (dn) cudaFree(dn);
+  return s;
+}
+
+int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap) {
+  if (!ctx || inst < 0 || inst >= ctx->b.B) { set_error("bad context or instance"); return FAMS_EINVAL; }
+  const Batch& b = ctx->b;
+  const Inst& I = b.h[inst];
+  std::vector<int> vi;
+  std::vector<double> vd;
+  bool isint = true;
+  auto ints = [&](const int* src, long long n, long long sub) -> int {
+    FAMS_TRY(fetch(b, src, n, vi));
+    for (auto& v : vi) v -= (int)sub;
+    return FAMS_OK;
+  };
+  auto dbls = [&](const double* src, long long n) -> int {
+    isint = false;
+    return fetch(b, src, n, vd);
+  };
+  int pbeg = 0, pend = 0;
+  switch (what) {
+    case FAMS_Q_NNC_FRAC: FAMS_TRY(ints(b.nnc_row_f + I.nnc_off, I.nnc, I.row_off + I.nm)); break;
+    case FAMS_Q_NNC_MATRIX: FAMS_TRY(ints(b.nnc_row_m + I.nnc_off, I.nnc, I.row_off)); break;
+    case FAMS_Q_NNC_AREA: FAMS_TRY(dbls(b.nnc_area + I.nnc_off, I.nnc)); break;
+    case FAMS_Q_NNC_DIST: FAMS_TRY(dbls(b.nnc_dist + I.nnc_off, I.nnc)); break;
+    case FAMS_Q_FF_A: FAMS_TRY(ints(b.ff_a + I.ff_off, I.nff, I.row_off + I.nm)); break;
+    case FAMS_Q_FF_B: FAMS_TRY(ints(b.ff_b + I.ff_off, I.nff, I.row_off + I.nm)); break;
+    case FAMS_Q_FF_T: FAMS_TRY(dbls(b.ff_T + I.ff_off, I.nff)); break;
+    case FAMS_Q_A_ROWPTR: FAMS_TRY(ints(b.rowptr + I.row_off, I.n + 1, I.nnz_off)); break;
+    case FAMS_Q_A_COL: FAMS_TRY(ints(b.col + I.nnz_off, I.nnz, I.row_off)); break;
+    case FAMS_Q_A_VAL: FAMS_TRY(dbls(b.val + I.nnz_off, I.nnz)); break;
+    case FAMS_Q_Q: FAMS_TRY(dbls(b.q + I.row_off, I.n)); break;
+    case FAMS_Q_RANK: FAMS_TRY(ints(b.rank + I.row_off, I.n, 0)); break;
+    case FAMS_Q_PRIMAL: FAMS_TRY(ints(b.primal + I.row_off, I.n, 0)); break;
+    case FAMS_Q_NODE_CELL: FAMS_TRY(ints(b.node_cell + I.nc_off, I.nc, I.row_off)); break;
+    case FAMS_Q_P_ROWPTR:
+    case FAMS_Q_P_COL:
+    case FAMS_Q_P_VAL: {
+      std::vector<int> pp;
+      FAMS_TRY(fetch(b, b.p_ptr + I.row_off, I.n + 1, pp));
+      pbeg = pp[0];
+      pend = pp[I.n];
+      if (what == FAMS_Q_P_ROWPTR) {
+        vi = pp;
+        for (auto& v : vi) v -= pbeg;
+      } else if (what == FAMS_Q_P_COL) {
+        FAMS_TRY(ints(b.p_col + pbeg, pend - pbeg, 0));
+      } else {
+        FAMS_TRY(dbls(b.p_val + pbeg, pend - pbeg));
+      }
+      break;
+    }
+    case FAMS_Q_AC: FAMS_TRY(dbls(b.cs[0].Ac + b.csh[0].ac_off[inst], (long long)I.nc * I.nc)); break;
+    case FAMS_Q_ILU_VAL: FAMS_TRY(dbls(b.ilu + I.nnz_off, I.nnz)); break;
+    case FAMS_Q_LEVELS: vi.assign(1, I.nlev); break;
+    default: set_error("unknown query"); return FAMS_EINVAL;
+  }
+  long long n = isint ? (long long)vi.size() : (long long)vd.size();
+  if (!out) return (int)n;
+  if (cap < n) { set_error("output buffer too small"); return FAMS_EINVAL; }
+  size_t bytes = isint ? sizeof(int) * n : sizeof(double) * n;
+  const void* src = isint ? (const void*)vi.data() : (const void*)vd.data();
+  if (n > 0) FAMS_CUDA(cudaMemcpy(out, src, bytes, cudaMemcpyDefault));
+  return (int)n;
+}
+
+void fams_destroy(fams_ctx* ctx) {
+  if (!ctx) return;
+  destroy_batch(ctx->b);
+  delete ctx;
+}
+
+const char* fams_strerror(int s) {
+  switch (s) {
+    case FAMS_OK: return "ok";
+    case FAMS_EINVAL: return "invalid argument or unsupported input";
+    case FAMS_ENOMEM: return "device memory allocation failed";
+    case FAMS_ENOCONV: return "iteration did not reach the tolerance";
+    case FAMS_EBREAKDOWN: return "zero or non-finite pivot";
+    case FAMS_ETIMEOUT: return "bounded device wait timed out";
+    case FAMS_ECUDA: return "CUDA runtime error";
+    case FAMS_ECAPACITY: return "problem exceeds a compiled-in capacity";
+    default: return "unknown status";
+  }
+}
+
+const char* fams_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,613 @@
+// Basis functions and the prolongation P (Sec. 3.1, Eqs. 9-22; Appendix A)
+// and truncation (Sec. 4.3).
+//
+// Vertex rows of P are the Kronecker delta (Eq. 16).  Every other row is
+// built stage by stage in wirebasket order; in a stage, each dual block B (a
+// connected component of the stage's cells under the kept links) solves
+//     A'_BB P_B = sum over kept links to known rows c of T_rc P_c,
+// where A' is the fine matrix without Dirichlet terms with every dropped link
+// removed from the diagonal.  The coupling strategy decides which links are
+// kept (Appendix A):
+//   Decoupled: same medium and rank(c) >= rank(r)
+//   Frac-AMS : matrix rows also keep all fracture links (fracture rows first)
+//   Rock-AMS : fracture rows also keep all matrix links (matrix rows first)
+//   Coupled  : rank(c) >= rank(r) in either medium (merged dual blocks)
+// A'_BB is a symmetric, diagonally dominant M-matrix, solved by a dense
+// Cholesky factorisation in one CTA per dual block.
+#include <algorithm>
+
+#include "batch.cuh"
+
+namespace fams {
+
+namespace {
+
+constexpr int NSTAGE = 5;
+constexpr int HASH_CAP = 2048;      // distinct coarse columns one dual block may touch
+constexpr int MEMBER_SORT_MAX = 8192;
+constexpr int SOLVE_THREADS = 256;
+
+__device__ inline int stage_of(int variant, int med, int rank) {
+  if (rank == RANK_V) return -1;
+  switch (variant) {
+    case 0:  // Decoupled: [mE] [fE] [mF] [fF] [mI]
+      if (med == 0) return rank == RANK_E ? 0 : (rank == RANK_F ? 2 : 4);
+      return rank == RANK_E ? 1 : 3;
+    case 1:  // Frac-AMS: [fE] [fF] [mE] [mF] [mI]
+      if (med == 1) return rank == RANK_E ? 0 : 1;
+      return rank == RANK_E ? 2 : (rank == RANK_F ? 3 : 4);
+    case 2:  // Rock-AMS: [mE] [mF] [mI] [fE] [fF]
+      if (med == 0) return rank == RANK_E ? 0 : (rank == RANK_F ? 1 : 2);
+      return rank == RANK_E ? 3 : 4;
+    default:  // Coupled: [mE,fE] [mF,fF] [mI]
+      return rank == RANK_E ? 0 : (rank == RANK_F ? 1 : 2);
+  }
+}
+
+__device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc) {
+  switch (variant) {
+    case 0: return mr == mc && rc >= rr;
+    case 1: return (mr == 0) ? (mc == 1 || rc >= rr) : (mc == 1 && rc >= rr);
+    case 2: return (mr == 1) ? (mc == 0 || rc >= rr) : (mc == 0 && rc >= rr);
+    default: return rc >= rr;
+  }
+}
+
+struct RowCtx {
+  const Inst* inst;
+  int B;
+  const int* off_row;
+  const int* rank;
+};
+
+__device__ inline const Inst& inst_of(const Inst* inst, int B, const int* off_row, int r) {
+  return inst[find_segment(off_row, B + 1, r)];
+}
+
+__device__ inline int medium_of(const Inst& I, int r) { return (r - I.row_off) < I.nm ? 0 : 1; }
+
+// P staging: each known row points into the pool of the stage that built it
+struct Pool {
+  const int* col[NSTAGE + 1];
+  const double* val[NSTAGE + 1];
+};
+
+__global__ void k_vertex_rows(const Inst* inst, int B, const int* off_nc, long long nct,
+                              const int* node_cell, int* vcol, double* vval, int* pstage,
+                              int* poff, int* plen) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nct) return;
+  const Inst& I = inst[find_segment(off_nc, B + 1, g)];
+  int v = node_cell[g];
+  vcol[g] = (int)(g - I.nc_off);
+  vval[g] = 1.0;
+  pstage[v] = NSTAGE;
+  poff[v] = (int)g;
+  plen[v] = 1;
+}
+
+__global__ void k_stage_mark(const Inst* inst, int B, const int* off_row, long long nrow,
+                             const int* rank, int s, int* label, int* instage) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int in = stage_of(I.basis, medium_of(I, (int)r), rank[r]) == s;
+  instage[r] = in;
+  label[r] = in ? (int)r : -1;
+}
+
+__global__ void k_stage_relax(const Inst* inst, int B, const int* off_row, long long nrow,
+                              const int* rank, const int* rowptr, const int* col,
+                              const int* instage, int* label, int* changed) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow || !instage[r]) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int mr = medium_of(I, (int)r), rr = rank[r];
+  int m = label[r];
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+    int c = col[p];
+    if (c == r || !instage[c]) continue;
+    if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c])) continue;
+    m = min(m, label[c]);
+  }
+  m = min(m, label[m]);
+  if (m < label[r]) {
+    atomicMin(&label[r], m);
+    *changed = 1;
+  }
+}
+
+__global__ void k_root_flag(long long nrow, const int* label, int* flag) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrow) flag[r] = (label[r] == (int)r);
+}
+
+__global__ void k_comp_size(long long nrow, const int* label, const int* rscan, int* comp_of,
+                            int* size) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  int l = label[r];
+  if (l < 0) { comp_of[r] = -1; return; }
+  int c = rscan[l];
+  comp_of[r] = c;
+  atomicAdd(&size[c], 1);
+}
+
+__global__ void k_comp_place(long long nrow, const int* comp_of, const int* off, int* cursor,
+                             int* members) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  int c = comp_of[r];
+  if (c < 0) return;
+  members[off[c] + atomicAdd(&cursor[c], 1)] = (int)r;
+}
+
+__device__ void bitonic_sort_int(int* a, int m) {
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          if ((a[i] > a[l]) == up) { int t = a[i]; a[i] = a[l]; a[l] = t; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// one CTA per dual block: sort its members, then find the coarse columns its
+// known neighbours carry.  mode 0 counts them, mode 1 writes them sorted.
+__global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
+                            const int* rowptr, const int* col, const int* instage,
+                            const int* comp_off, int* members, int* pos, const int* pstage,
+                            const int* poff, const int* plen, Pool pool, int s, int mode,
+                            int* ncols, const int* colptr, int* colbuf, int* err) {
+  __shared__ int sm[MEMBER_SORT_MAX];
+  __shared__ int hs[HASH_CAP];
+  __shared__ int nuniq, known_links;
+  int c = blockIdx.x;
+  int a = comp_off[c], n = comp_off[c + 1] - a;
+  if (n > MEMBER_SORT_MAX) {
+    if (threadIdx.x == 0) atomicCAS(err, 0, DERR_CAPACITY);
+    return;
+  }
+  if (mode == 0) {
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sm[i] = i < n ? members[a + i] : 0x7fffffff;
+    __syncthreads();
+    bitonic_sort_int(sm, m);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      members[a + i] = sm[i];
+      pos[sm[i]] = i;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < HASH_CAP; i += blockDim.x) hs[i] = -1;
+  if (threadIdx.x == 0) { nuniq = 0; known_links = 0; }
+  __syncthreads();
+  const Inst& I = inst_of(inst, B, off_row, members[a]);
+  bool over = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = members[a + i];
+    int mr = medium_of(I, r), rr = rank[r];
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int cc = col[p];
+      if (cc == r || instage[cc]) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) continue;
+      atomicAdd(&known_links, 1);
+      int st = pstage[cc];
+      if (st < 0) { over = true; continue; }
+      const int* pc = pool.col[st] + poff[cc];
+      for (int q = 0; q < plen[cc]; ++q) {
+        int key = pc[q];
+        unsigned h = ((unsigned)key * 2654435761u) & (HASH_CAP - 1);
+        for (int probe = 0; probe < HASH_CAP; ++probe) {
+          int prev = atomicCAS(&hs[h], -1, key);
+          if (prev == -1) { atomicAdd(&nuniq, 1); break; }
+          if (prev == key) break;
+          h = (h + 1) & (HASH_CAP - 1);
+        }
+      }
+    }
+  }
+  if (over) atomicCAS(err, 0, DERR_INVAL);
+  __syncthreads();
+  if (threadIdx.x == 0 && known_links == 0) atomicCAS(err, 0, DERR_FLOATING);
+  if (nuniq > HASH_CAP / 2) {
+    if (threadIdx.x == 0) atomicCAS(err, 0, DERR_CAPACITY);
+    return;
+  }
+  if (mode == 0) {
+    if (threadIdx.x == 0) ncols[c] = nuniq;
+    return;
+  }
+  for (int i = threadIdx.x; i < HASH_CAP; i += blockDim.x)
+    if (hs[i] == -1) hs[i] = 0x7fffffff;
+  __syncthreads();
+  bitonic_sort_int(hs, HASH_CAP);
+  for (int i = threadIdx.x; i < nuniq; i += blockDim.x) colbuf[colptr[c] + i] = hs[i];
+}
+
+__device__ inline int find_col(const int* cols, int k, int key) {
+  int lo = 0, hi = k - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = cols[mid];
+    if (v == key) return mid;
+    if (v < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// one CTA per dual block: assemble A'_BB and the right-hand sides, dense
+// Cholesky, forward/back substitution, write the block's rows of P.
+__global__ void k_comp_solve(const Inst* inst, int B, const int* off_row, const int* rank,
+                             const int* rowptr, const int* col, const double* val,
+                             const double* TD, const int* instage, const int* comp_list,
+                             const int* comp_off, const int* members, const int* pos,
+                             const int* colptr, const int* colbuf, const long long* pool_off,
+                             int* pstage, int* poff, int* plen, Pool pool, int s, int* out_col,
+                             double* out_val, double* gwork, long long gstride, int* err) {
+  extern __shared__ double dsm[];
+  int c = comp_list[blockIdx.x];
+  int a = comp_off[c], n = comp_off[c + 1] - a;
+  int k = colptr[c + 1] - colptr[c];
+  const int* cols = colbuf + colptr[c];
+  double* M;
+  double* R;
+  if (gwork) {
+    M = gwork + (long long)blockIdx.x * gstride;
+  } else {
+    M = dsm;
+  }
+  R = M + (long long)n * n;
+  const Inst& I = inst_of(inst, B, off_row, members[a]);
+  for (long long i = threadIdx.x; i < (long long)n * n + (long long)n * k; i += blockDim.x) M[i] = 0.0;
+  __syncthreads();
+  // assemble: one thread per member row
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = members[a + i];
+    int mr = medium_of(I, r), rr = rank[r];
+    double d = 0.0;
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int cc = col[p];
+      double av = val[p];
+      if (cc == r) { d += av - TD[r]; continue; }
+      double T = -av;
+      if (keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) {
+        if (instage[cc]) {
+          int pc = pos[cc];
+          if (pc < 0 || pc >= n) { atomicCAS(err, 0, DERR_INVAL); continue; }
+          M[(long long)i * n + pc] = av;
+        } else {
+          int st = pstage[cc];
+          const int* pc = pool.col[st] + poff[cc];
+          const double* pv = pool.val[st] + poff[cc];
+          for (int q = 0; q < plen[cc]; ++q) {
+            int j = find_col(cols, k, pc[q]);
+            if (j < 0) { atomicCAS(err, 0, DERR_INVAL); continue; }
+            R[(long long)i * k + j] += T * pv[q];
+          }
+        }
+      } else {
+        d -= T;
+      }
+    }
+    M[(long long)i * n + i] = d;
+  }
+  __syncthreads();
+  // Cholesky, lower triangle in place (right-looking)
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    double djj = M[(long long)j * n + j];
+    if (!(djj > 0.0) || !isfinite(djj)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;
+    }
+    double l = sqrt(djj);
+    __syncthreads();
+    if (threadIdx.x == 0) M[(long long)j * n + j] = l;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(long long)i * n + j] /= l;
+    __syncthreads();
+    int m = n - j - 1;
+    long long tot = (long long)m * (m + 1) / 2;
+    for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+      // t -> (ii, jj) with jj <= ii, both in [0, m)
+      int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((long long)ii * (ii + 1) / 2 > t) --ii;
+      while ((long long)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      int jj = (int)(t - (long long)ii * (ii + 1) / 2);
+      int gi = j + 1 + ii, gj = j + 1 + jj;
+      M[(long long)gi * n + gj] -= M[(long long)gi * n + j] * M[(long long)gj * n + j];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicCAS(err, 0, DERR_BREAKDOWN);
+    return;
+  }
+  // forward: L Y = R
+  for (int j = 0; j < n; ++j) {
+    double l = M[(long long)j * n + j];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) R[(long long)j * k + q] /= l;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < (long long)(n - j - 1) * k; t += blockDim.x) {
+      int i = j + 1 + (int)(t / k), q = (int)(t % k);
+      R[(long long)i * k + q] -= M[(long long)i * n + j] * R[(long long)j * k + q];
+    }
+    __syncthreads();
+  }
+  // backward: L^T X = Y
+  for (int j = n - 1; j >= 0; --j) {
+    double l = M[(long long)j * n + j];
+    for (int q = threadIdx.x; q < k; q += blockDim.x) R[(long long)j * k + q] /= l;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < (long long)j * k; t += blockDim.x) {
+      int i = (int)(t / k), q = (int)(t % k);
+      R[(long long)i * k + q] -= M[(long long)j * n + i] * R[(long long)j * k + q];
+    }
+    __syncthreads();
+  }
+  long long base = pool_off[c];
+  for (long long t = threadIdx.x; t < (long long)n * k; t += blockDim.x) {
+    int i = (int)(t / k), q = (int)(t % k);
+    out_col[base + t] = cols[q];
+    out_val[base + t] = R[(long long)i * k + q];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = members[a + i];
+    pstage[r] = s;
+    poff[r] = (int)(base + (long long)i * k);
+    plen[r] = k;
+  }
+}
+
+// truncation (Sec. 4.3) and CSR of P
+__device__ inline void trunc_row(const int* pc, const double* pv, int len, double alpha,
+                                 int* cnt, double* sum, int* only) {
+  int c = 0, amax = -1;
+  double s = 0.0, vmax = -1.0;
+  for (int q = 0; q < len; ++q) {
+    double v = pv[q];
+    if (v == 0.0) continue;
+    if (fabs(v) > vmax) { vmax = fabs(v); amax = q; }
+    if (alpha <= 0.0 || fabs(v) >= alpha) { ++c; s += v; }
+  }
+  *only = -1;
+  if (c == 0 && amax >= 0) { c = 1; s = pv[amax]; *only = amax; }
+  *cnt = c;
+  *sum = s;
+}
+
+__global__ void k_p_count(const Inst* inst, int B, const int* off_row, long long nrow,
+                          const int* pstage, const int* poff, const int* plen, Pool pool,
+                          int* cnt) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int st = pstage[r];
+  int c = 0, only;
+  double s;
+  trunc_row(pool.col[st] + poff[r], pool.val[st] + poff[r], plen[r], I.alpha, &c, &s, &only);
+  cnt[r] = c;
+}
+
+__global__ void k_p_fill(const Inst* inst, int B, const int* off_row, long long nrow,
+                         const int* pstage, const int* poff, const int* plen, Pool pool,
+                         const int* p_ptr, int* p_col, double* p_val) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int st = pstage[r];
+  const int* pc = pool.col[st] + poff[r];
+  const double* pv = pool.val[st] + poff[r];
+  int c, only;
+  double s;
+  trunc_row(pc, pv, plen[r], I.alpha, &c, &s, &only);
+  int o = p_ptr[r];
+  if (only >= 0) {
+    p_col[o] = pc[only];
+    p_val[o] = 1.0;
+    return;
+  }
+  bool scale = I.alpha > 0.0;
+  for (int q = 0; q < plen[r]; ++q) {
+    double v = pv[q];
+    if (v == 0.0) continue;
+    if (I.alpha <= 0.0 || fabs(v) >= I.alpha) {
+      p_col[o] = pc[q];
+      p_val[o] = scale ? v / s : v;
+      ++o;
+    }
+  }
+}
+
+__global__ void k_p_global_cols(const Inst* inst, int B, const int* off_row, long long nrow,
+                                const int* p_ptr, const int* p_col, int* gcol) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  for (int p = p_ptr[r]; p < p_ptr[r + 1]; ++p) gcol[p] = I.nc_off + p_col[p];
+}
+
+}  // namespace
+
+int phase_basis(Batch& b) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  long long nrow = b.tot_row, nct = b.tot_nc;
+  int *pstage = nullptr, *poff = nullptr, *plen = nullptr;
+  FAMS_TRY(b.scratch((void**)&pstage, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&poff, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&plen, sizeof(int) * (nrow + 1)));
+  FAMS_CUDA(cudaMemsetAsync(pstage, 0xff, sizeof(int) * (nrow + 1), st));
+  FAMS_CUDA(cudaMemsetAsync(plen, 0, sizeof(int) * (nrow + 1), st));
+  Pool pool{};
+  int* vcol = nullptr;
+  double* vval = nullptr;
+  FAMS_TRY(b.scratch((void**)&vcol, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.scratch((void**)&vval, sizeof(double) * (nct + 1)));
+  pool.col[NSTAGE] = vcol;
+  pool.val[NSTAGE] = vval;
+  if (nct > 0)
+    k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
+                                                  vval, pstage, poff, plen);
+  int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr, *changed = nullptr;
+  int *comp_of = nullptr, *pos = nullptr;
+  FAMS_TRY(b.scratch((void**)&label, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&instage, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&flag, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&rscan, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&changed, sizeof(int)));
+  FAMS_TRY(b.scratch((void**)&comp_of, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&pos, sizeof(int) * (nrow + 1)));
+  int max_smem = 0;
+  FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem));
+  for (int s = 0; s < NSTAGE; ++s) {
+    k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
+                                                  instage);
+    for (int it = 0; it < 1000000; ++it) {
+      int h = 0;
+      FAMS_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
+      k_stage_relax<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
+                                                     b.rowptr, b.col, instage, label, changed);
+      FAMS_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FAMS_CUDA(cudaStreamSynchronize(st));
+      if (!h) break;
+    }
+    k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
+    long long ncomp = 0;
+    FAMS_TRY(exclusive_scan(b, flag, rscan, nrow, &ncomp));
+    if (ncomp == 0) continue;
+    int *size = nullptr, *coff = nullptr, *cursor = nullptr, *members = nullptr;
+    int *ncols = nullptr, *colptr = nullptr, *colbuf = nullptr;
+    FAMS_TRY(b.scratch((void**)&size, sizeof(int) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&coff, sizeof(int) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&cursor, sizeof(int) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&ncols, sizeof(int) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&colptr, sizeof(int) * (ncomp + 1)));
+    FAMS_CUDA(cudaMemsetAsync(size, 0, sizeof(int) * (ncomp + 1), st));
+    FAMS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (ncomp + 1), st));
+    k_comp_size<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, rscan, comp_of, size);
+    long long nmem = 0;
+    FAMS_TRY(exclusive_scan(b, size, coff, ncomp, &nmem));
+    FAMS_TRY(b.scratch((void**)&members, sizeof(int) * (nmem + 1)));
+    k_comp_place<<<grid_for(nrow, T), T, 0, st>>>(nrow, comp_of, coff, cursor, members);
+    k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+                                            instage, coff, members, pos, pstage, poff, plen, pool,
+                                            s, 0, ncols, nullptr, nullptr, b.d_err);
+    FAMS_CUDA(cudaGetLastError());
+    FAMS_TRY(b.check_err("dual-block columns"));
+    long long totc = 0;
+    FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
+    FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
+    k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+                                            instage, coff, members, pos, pstage, poff, plen, pool,
+                                            s, 1, ncols, colptr, colbuf, b.d_err);
+    // host plan: pool offsets and small/large split
+    std::vector<int> hs(ncomp), hk(ncomp);
+    FAMS_CUDA(cudaMemcpyAsync(hs.data(), size, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaMemcpyAsync(hk.data(), ncols, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    std::vector<long long> hpo(ncomp + 1, 0);
+    std::vector<int> small, large;
+    long long max_big = 0;
+    size_t small_smem = 0;
+    for (long long c = 0; c < ncomp; ++c) {
+      hpo[c + 1] = hpo[c] + (long long)hs[c] * hk[c];
+      long long need = ((long long)hs[c] * hs[c] + (long long)hs[c] * hk[c]) * 8;
+      if (need + 1024 <= max_smem) {
+        small.push_back((int)c);
+        small_smem = std::max(small_smem, (size_t)need);
+      } else {
+        large.push_back((int)c);
+        max_big = std::max(max_big, need / 8);
+      }
+    }
+    long long* pool_off = nullptr;
+    int* ocol = nullptr;
+    double* oval = nullptr;
+    int* clist = nullptr;
+    FAMS_TRY(b.scratch((void**)&pool_off, sizeof(long long) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&ocol, sizeof(int) * (hpo[ncomp] + 1)));
+    FAMS_TRY(b.scratch((void**)&oval, sizeof(double) * (hpo[ncomp] + 1)));
+    FAMS_TRY(b.scratch((void**)&clist, sizeof(int) * (ncomp + 1)));
+    FAMS_CUDA(cudaMemcpyAsync(pool_off, hpo.data(), sizeof(long long) * (ncomp + 1),
+                              cudaMemcpyHostToDevice, st));
+    if (hpo[ncomp] > 2147483647LL) {
+      set_error("basis stage pool exceeds the int32 index range");
+      return FAMS_ECAPACITY;
+    }
+    pool.col[s] = ocol;
+    pool.val[s] = oval;
+    if (!small.empty()) {
+      FAMS_CUDA(cudaMemcpyAsync(clist, small.data(), sizeof(int) * small.size(),
+                                cudaMemcpyHostToDevice, st));
+      k_comp_solve<<<(int)small.size(), SOLVE_THREADS, small_smem, st>>>(
+          b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val, b.TD, instage, clist, coff,
+          members, pos, colptr, colbuf, pool_off, pstage, poff, plen, pool, s, ocol, oval,
+          nullptr, 0, b.d_err);
+      FAMS_CUDA(cudaGetLastError());
+    }
+    if (!large.empty()) {
+      // bounded workspace: at most ~1 GiB of dense blocks per launch
+      long long per = std::max(1LL, (1LL << 27) / std::max(max_big, 1LL));
+      double* work = nullptr;
+      FAMS_TRY(b.scratch((void**)&work, sizeof(double) * max_big * std::min<long long>(per, large.size())));
+      int* lst = clist + small.size();
+      FAMS_CUDA(cudaMemcpyAsync(lst, large.data(), sizeof(int) * large.size(),
+                                cudaMemcpyHostToDevice, st));
+      for (size_t o = 0; o < large.size(); o += per) {
+        int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
+        k_comp_solve<<<cnt, 1024, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val,
+                                           b.TD, instage, lst + o, coff, members, pos, colptr,
+                                           colbuf, pool_off, pstage, poff, plen, pool, s, ocol,
+                                           oval, work, max_big, b.d_err);
+        FAMS_CUDA(cudaGetLastError());
+      }
+    }
+    FAMS_TRY(b.check_err("dual-block solves"));
+  }
+  // every row must have a basis row
+  // P CSR with truncation
+  int* cnt = nullptr;
+  FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.alloc((void**)&b.p_ptr, sizeof(int) * (nrow + 1)));
+  {
+    std::vector<int> hst(nrow);
+    FAMS_CUDA(cudaMemcpyAsync(hst.data(), pstage, sizeof(int) * nrow, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    for (long long r = 0; r < nrow; ++r)
+      if (hst[r] < 0) {
+        set_error("a cell was left without a basis row (it belongs to no stage)");
+        return FAMS_EINVAL;
+      }
+  }
+  k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
+                                             pool, cnt);
+  long long pnnz = 0;
+  FAMS_TRY(exclusive_scan(b, cnt, b.p_ptr, nrow, &pnnz));
+  FAMS_TRY(b.alloc((void**)&b.p_col, sizeof(int) * (pnnz + 1)));
+  FAMS_TRY(b.alloc((void**)&b.p_val, sizeof(double) * (pnnz + 1)));
+  k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
+                                            pool, b.p_ptr, b.p_col, b.p_val);
+  // P^T with global coarse rows (restriction R^FE and the coarse operator)
+  int* gcol = nullptr;
+  FAMS_TRY(b.scratch((void**)&gcol, sizeof(int) * (pnnz + 1)));
+  k_p_global_cols<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.p_ptr,
+                                                   b.p_col, gcol);
+  FAMS_TRY(transpose(b, b.p_ptr, gcol, b.p_val, (int)nrow, (int)nct, pnnz, &b.pt_ptr, &b.pt_col,
+                     &b.pt_val, true));
+  FAMS_CUDA(cudaGetLastError());
+  return b.check_err("prolongation");
+}
+
+}  // namespace fams

@@ -1,0 +1,177 @@
+// The device state of a batch of independent F-AMS instances.  Every array
+// is the concatenation of the instances' arrays (a block-diagonal system);
+// Inst::*_off give each instance's slice.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fams {
+
+// Coarse system of every instance of a batch (device pointers; per-instance
+// arrays have B entries, per-coarse-unknown arrays tot_nc).
+struct CoarseSys {
+  double* Ac = nullptr;         // dense R A P, row-major, at ac_off[i]
+  long long* ac_off = nullptr;
+  double* band = nullptr;       // band LU factors (column-major, ldab = 2kl+ku+1)
+  long long* band_off = nullptr;
+  int* kl = nullptr;            // lower / upper bandwidth after reordering
+  int* ku = nullptr;
+  int* ipiv = nullptr;          // pivot rows (band positions)
+  int* perm = nullptr;          // band position -> coarse index
+};
+
+struct CoarseHost {
+  std::vector<long long> ac_off, band_off;
+  std::vector<int> kl, ku;
+};
+
+struct Batch {
+  int B = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<Inst> h;          // host copy of the descriptors
+  Inst* d_inst = nullptr;       // device copy
+  int* d_err = nullptr;         // device status word
+  std::vector<void*> owned;     // freed by fams_destroy
+  std::vector<void*> tmp;       // freed at the end of setup
+
+  // per-item-kind instance offsets on the device (B+1 each)
+  int* off_m = nullptr;    // matrix cells
+  int* off_fr = nullptr;   // input fractures
+  int* off_fc = nullptr;   // fracture cells
+  int* off_s = nullptr;    // strike cells
+  int* off_row = nullptr;  // unknowns
+  int* off_pair = nullptr; // fracture pairs
+  int* off_nc = nullptr;   // coarse unknowns
+  int* off_net = nullptr;  // fracture networks
+
+  // totals
+  long long tot_m = 0, tot_fr = 0, tot_fc = 0, tot_s = 0, tot_row = 0, tot_pair = 0,
+            tot_nnc = 0, tot_ff = 0, tot_nc = 0, tot_net = 0, tot_nnz = 0;
+
+  // ---- inputs ----
+  double* perm = nullptr;      // tot_m
+  double* fracs = nullptr;     // 6 per input fracture
+  double* kf = nullptr;        // per input fracture
+  // ---- geometry ----
+  double* seg = nullptr;       // 4 per input fracture (clipped)
+  int* f_ns = nullptr;         // strike cells per fracture
+  int* f_k0 = nullptr;         // first layer (3D)
+  int* f_nk = nullptr;         // layers (3D), 1 in 2D
+  int* f_cfirst = nullptr;     // global fracture-cell index of the first cell
+  int* f_sfirst = nullptr;     // global strike index of the first strike cell
+  int* s_ovcnt = nullptr;      // overlaps per strike cell
+  int* s_ovcol = nullptr;      // MAX_OVERLAP per strike cell: 2D column index
+  double* s_ovlen = nullptr;   // overlap length
+  double* s_ovdist = nullptr;  // <d>
+  int* nnc_first = nullptr;    // per fracture cell: first connection (tot_fc+1)
+  int* ff_first = nullptr;     // per fracture cell: first link where it is the lower cell
+  int* nnc_row_f = nullptr;    // global row of the fracture cell
+  int* nnc_row_m = nullptr;    // global row of the matrix cell
+  double* nnc_T = nullptr;     // CI * k_m
+  double* nnc_area = nullptr;
+  double* nnc_dist = nullptr;
+  int* ff_a = nullptr;         // global rows, a < b
+  int* ff_b = nullptr;
+  double* ff_T = nullptr;
+  int* inter_hit = nullptr;    // per pair: 1 if the segments cross
+  int* inter_sa = nullptr;     // strike cell index within fracture a
+  int* inter_sb = nullptr;
+  double* inter_T = nullptr;
+  // ---- fine system ----
+  int* rowptr = nullptr;       // tot_row + 1
+  int* col = nullptr;          // global column indices
+  double* val = nullptr;
+  int* diag = nullptr;         // position of the diagonal in each row
+  double* TD = nullptr;        // Dirichlet half transmissibility per row
+  double* qD = nullptr;        // Dirichlet part of q
+  // ---- coarse grids ----
+  int* rank = nullptr;         // per row
+  int* primal = nullptr;       // per row: instance-local coarse index
+  int* node_cell = nullptr;    // per coarse unknown: global row
+  int* s_net = nullptr;        // per strike cell: global network index
+  int* s_prim = nullptr;       // per strike cell: network-local block
+  int* s_vert = nullptr;       // per strike cell: 1 if coarse node
+  int* net_nv = nullptr;       // vertices per network
+  int* net_k0 = nullptr;       // layer range of each network (3D)
+  int* net_nk = nullptr;
+  int* net_base = nullptr;     // instance-local coarse index of the network's first node
+  // ---- prolongation ----
+  int* p_ptr = nullptr;        // CSR of P, instance-local columns
+  int* p_col = nullptr;
+  double* p_val = nullptr;
+  int* pt_ptr = nullptr;       // CSR of P^T (rows = global coarse index)
+  int* pt_col = nullptr;       // global fine rows
+  double* pt_val = nullptr;
+  int* blk_ptr = nullptr;      // cells of each primal block (global coarse index)
+  int* blk_cell = nullptr;
+  // ---- coarse system: [0] the iteration's restriction, [1] R^FV for the
+  // flux reconstruction when the iteration uses R^FE ----
+  CoarseSys cs[2];
+  CoarseHost csh[2];
+  // ---- ILU(0) ----
+  double* ilu = nullptr;       // factors in the pattern of A
+  int* lev_ptr = nullptr;      // per instance: nlev+1 offsets (Inst-local slice)
+  int* lev_rows = nullptr;     // global rows grouped by level
+  int* lev_off = nullptr;      // per instance offset into lev_ptr
+  // ---- iteration work vectors ----
+  double* q = nullptr;
+  double* x = nullptr;
+  double* r = nullptr;
+  double* dp = nullptr;
+  double* y = nullptr;
+  double* rc = nullptr;
+  double* ec = nullptr;
+  double* stat = nullptr;      // per instance: 4 doubles (iters, relres, converged, qnorm)
+  // flux (FV coarse factor built on first use)
+  bool fv_ready = false;
+
+  int alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      return FAMS_ENOMEM;
+    }
+    owned.push_back(*p);
+    return FAMS_OK;
+  }
+  int scratch(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      return FAMS_ENOMEM;
+    }
+    tmp.push_back(*p);
+    return FAMS_OK;
+  }
+  void free_tmp() {
+    for (void* p : tmp) cudaFree(p);
+    tmp.clear();
+  }
+  int upload_inst();
+  int check_err(const char* phase);
+};
+
+// util.cu
+int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* total);
+int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict);
+int transpose(Batch& b, const int* rowptr, const int* col, const double* val, int nrows,
+              int ncols, long long nnz, int** tptr, int** tcol, double** tval, bool keep);
+
+// phases (each file)
+int phase_geometry(Batch& b);     // geometry.cu
+int phase_system(Batch& b);       // system.cu: CSR of A, q_D
+int phase_coarse(Batch& b);       // coarse.cu: matrix blocks, networks, BFS, ranks
+int phase_basis(Batch& b);        // basis.cu: P
+int phase_coarse_op(Batch& b, int restriction);  // coarseop.cu: R A P, band LU
+int build_coarse_system(Batch& b, CoarseSys& cs, int restriction, CoarseHost& ch);
+int phase_ilu(Batch& b);          // ilu.cu
+int phase_alloc_work(Batch& b);   // solve.cu
+int run_solve(Batch& b, double tol, float* ms);   // solve.cu
+int run_flux(Batch& b, int inst, const double* x_dev, double* face, double* nnc);  // flux.cu
+
+}  // namespace fams

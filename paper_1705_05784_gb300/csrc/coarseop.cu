@@ -1,0 +1,306 @@
+// Restriction and coarse system (Sec. 3.2): A_c = R A P with R^FV (the
+// indicator of the primal blocks) or R^FE = P^T, factorised by LU with
+// partial pivoting (the paper solves the coarse system with a direct LU).
+//
+// A_c is assembled densely per instance, reordered by reverse Cuthill-McKee
+// (one thread per instance) and stored as a band matrix; the band LU
+// (partial pivoting inside the band, the LAPACK gbtf2 scheme) runs in one CTA
+// per instance.  Any row permutation and pivot order gives the same solution
+// up to rounding.
+#include <algorithm>
+
+#include "batch.cuh"
+
+namespace fams {
+
+namespace {
+
+__device__ inline int row_of_nnz(const int* rowptr, int lo, int hi, long long p) {
+  // rowptr[lo] <= p < rowptr[hi]
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rowptr[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_rap(const Inst* inst, int B, const int* off_row, long long nnz_tot,
+                      const int* rowptr, const int* col, const double* val, long long nrow,
+                      const int* primal, const int* p_ptr, const int* p_col, const double* p_val,
+                      CoarseSys cs, int mode) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz_tot) return;
+  int i = row_of_nnz(rowptr, 0, (int)nrow - 1, p);
+  int ii = find_segment(off_row, B + 1, i);
+  const Inst& I = inst[ii];
+  int fe = mode < 0 ? (I.restriction == FAMS_R_FE) : mode;
+  int j = col[p];
+  double a = val[p];
+  double* Ac = cs.Ac + cs.ac_off[ii];
+  int nc = I.nc;
+  if (!fe) {
+    int Ib = primal[i];
+    for (int q = p_ptr[j]; q < p_ptr[j + 1]; ++q)
+      atomicAdd(&Ac[(long long)Ib * nc + p_col[q]], a * p_val[q]);
+  } else {
+    for (int t = p_ptr[i]; t < p_ptr[i + 1]; ++t) {
+      int Ib = p_col[t];
+      double u = p_val[t] * a;
+      for (int q = p_ptr[j]; q < p_ptr[j + 1]; ++q)
+        atomicAdd(&Ac[(long long)Ib * nc + p_col[q]], u * p_val[q]);
+    }
+  }
+}
+
+// nonzero pattern of each dense coarse row (warp per row)
+__global__ void k_ac_count(const Inst* inst, int B, const int* off_nc, long long nct, CoarseSys cs,
+                           int* cnt) {
+  long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= nct) return;
+  int ii = find_segment(off_nc, B + 1, w);
+  const Inst& I = inst[ii];
+  int r = (int)(w - I.nc_off);
+  const double* row = cs.Ac + cs.ac_off[ii] + (long long)r * I.nc;
+  int c = 0;
+  for (int j = lane; j < I.nc; j += 32) c += (row[j] != 0.0 && j != r);
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[w] = c;
+}
+
+__global__ void k_ac_cols(const Inst* inst, int B, const int* off_nc, long long nct, CoarseSys cs,
+                          const int* ptr, int* cols) {
+  long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nct) return;
+  int ii = find_segment(off_nc, B + 1, w);
+  const Inst& I = inst[ii];
+  int r = (int)(w - I.nc_off);
+  const double* row = cs.Ac + cs.ac_off[ii] + (long long)r * I.nc;
+  int o = ptr[w];
+  for (int j = 0; j < I.nc; ++j)
+    if (row[j] != 0.0 && j != r) cols[o++] = j;
+}
+
+// reverse Cuthill-McKee per instance (one thread each): BFS from a node of
+// minimum degree, neighbours in order of (degree, index), then reversed.
+__global__ void k_rcm(const Inst* inst, int B, const int* ptr, const int* cols, CoarseSys cs,
+                      int* visited, int* queue, int* kl_out, int* ku_out) {
+  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= B) return;
+  const Inst& I = inst[ii];
+  int n = I.nc, o = I.nc_off;
+  const int* rp = ptr + o;
+  int* vis = visited + o;
+  int* qu = queue + o;
+  int* perm = cs.perm + o;
+  for (int i = 0; i < n; ++i) vis[i] = 0;
+  int head = 0, tail = 0;
+  while (tail < n) {
+    int best = -1, bd = 0x7fffffff;
+    for (int i = 0; i < n; ++i)
+      if (!vis[i] && rp[i + 1] - rp[i] < bd) { bd = rp[i + 1] - rp[i]; best = i; }
+    vis[best] = 1;
+    qu[tail++] = best;
+    while (head < tail) {
+      int u = qu[head++];
+      int first = tail;
+      for (int p = rp[u]; p < rp[u + 1]; ++p) {
+        int v = cols[p];
+        if (!vis[v]) { vis[v] = 1; qu[tail++] = v; }
+      }
+      // insertion sort of the new entries by (degree, index)
+      for (int a = first + 1; a < tail; ++a) {
+        int v = qu[a], dv = rp[v + 1] - rp[v];
+        int b = a - 1;
+        while (b >= first) {
+          int w = qu[b], dw = rp[w + 1] - rp[w];
+          if (dw > dv || (dw == dv && w > v)) { qu[b + 1] = w; --b; } else break;
+        }
+        qu[b + 1] = v;
+      }
+    }
+  }
+  for (int k = 0; k < n; ++k) perm[k] = qu[n - 1 - k];
+  int* ip = vis;  // reuse as the inverse permutation
+  for (int k = 0; k < n; ++k) ip[perm[k]] = k;
+  int kl = 0, ku = 0;
+  for (int r = 0; r < n; ++r)
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+      int d = ip[r] - ip[cols[p]];
+      if (d > kl) kl = d;
+      if (-d > ku) ku = -d;
+    }
+  kl_out[ii] = kl;
+  ku_out[ii] = ku;
+}
+
+__global__ void k_band_fill(const Inst* inst, int B, const int* off_nc, long long nct,
+                            CoarseSys cs, const int* ip_all) {
+  long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nct) return;
+  int ii = find_segment(off_nc, B + 1, w);
+  const Inst& I = inst[ii];
+  int r = (int)(w - I.nc_off);
+  int kl = cs.kl[ii], ku = cs.ku[ii], ldab = 2 * kl + ku + 1;
+  const double* row = cs.Ac + cs.ac_off[ii] + (long long)r * I.nc;
+  double* AB = cs.band + cs.band_off[ii];
+  const int* ip = ip_all + I.nc_off;
+  int i = ip[r];
+  for (int c = 0; c < I.nc; ++c) {
+    double v = row[c];
+    if (v == 0.0 && c != r) continue;
+    int j = ip[c];
+    AB[(long long)(kl + ku + i - j) + (long long)ldab * j] = v;
+  }
+}
+
+__global__ void k_inverse_perm(const Inst* inst, int B, const int* off_nc, long long nct,
+                               CoarseSys cs, int* ip_all) {
+  long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nct) return;
+  int ii = find_segment(off_nc, B + 1, w);
+  const Inst& I = inst[ii];
+  int k = (int)(w - I.nc_off);
+  ip_all[I.nc_off + cs.perm[w]] = k;
+}
+
+// band LU with partial pivoting, one CTA per instance
+__global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
+  int ii = blockIdx.x;
+  const Inst& I = inst[ii];
+  int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
+  double* AB = cs.band + cs.band_off[ii];
+  int* ipiv = cs.ipiv + I.nc_off;
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_jp, s_ju, s_bad;
+  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; }
+  __syncthreads();
+#define AEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
+  for (int j = 0; j < n; ++j) {
+    int km = min(kl, n - 1 - j);
+    // pivot search (largest magnitude, lowest index on ties)
+    double best = -1.0;
+    int bi = 0;
+    for (int t = threadIdx.x; t <= km; t += blockDim.x) {
+      double v = fabs(AEL(j + t, j));
+      if (v > best) { best = v; bi = t; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (sv[w] > b0 || (sv[w] == b0 && si[w] < i0)) { b0 = sv[w]; i0 = si[w]; }
+      s_jp = i0;
+      ipiv[j] = j + i0;
+      if (!(b0 > 0.0) || !isfinite(b0)) s_bad = 1;
+      s_ju = max(s_ju, min(j + ku + i0, n - 1));
+    }
+    __syncthreads();
+    if (s_bad) break;
+    int jp = s_jp, ju = s_ju;
+    if (jp != 0) {
+      for (int c = j + threadIdx.x; c <= ju; c += blockDim.x) {
+        double t = AEL(j, c);
+        AEL(j, c) = AEL(j + jp, c);
+        AEL(j + jp, c) = t;
+      }
+      __syncthreads();
+    }
+    double piv = AEL(j, j);
+    for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) AEL(j + t, j) /= piv;
+    __syncthreads();
+    int w = ju - j;
+    for (int e = threadIdx.x; e < km * w; e += blockDim.x) {
+      int t = 1 + e % km, c = j + 1 + e / km;
+      AEL(j + t, c) -= AEL(j + t, j) * AEL(j, c);
+    }
+    __syncthreads();
+  }
+#undef AEL
+  if (threadIdx.x == 0 && s_bad) atomicCAS(err, 0, DERR_BREAKDOWN);
+}
+
+}  // namespace
+
+// mode < 0: each instance's own restriction; 0: R^FV for all; 1: R^FE for all
+int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  long long nct = b.tot_nc;
+  int B = b.B;
+  // dense A_c per instance
+  ch.ac_off.assign(B, 0);
+  long long tot = 0;
+  for (int i = 0; i < B; ++i) {
+    ch.ac_off[i] = tot;
+    tot += (long long)b.h[i].nc * b.h[i].nc;
+  }
+  FAMS_TRY(b.alloc((void**)&cs.Ac, sizeof(double) * (tot + 1)));
+  FAMS_TRY(b.alloc((void**)&cs.ac_off, sizeof(long long) * B));
+  FAMS_TRY(b.alloc((void**)&cs.kl, sizeof(int) * B));
+  FAMS_TRY(b.alloc((void**)&cs.ku, sizeof(int) * B));
+  FAMS_TRY(b.alloc((void**)&cs.band_off, sizeof(long long) * B));
+  FAMS_TRY(b.alloc((void**)&cs.ipiv, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.alloc((void**)&cs.perm, sizeof(int) * (nct + 1)));
+  FAMS_CUDA(cudaMemcpyAsync(cs.ac_off, ch.ac_off.data(), sizeof(long long) * B,
+                            cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (tot + 1), st));
+  if (b.tot_nnz > 0)
+    k_rap<<<grid_for(b.tot_nnz, T), T, 0, st>>>(b.d_inst, B, b.off_row, b.tot_nnz, b.rowptr, b.col,
+                                                b.val, b.tot_row, b.primal, b.p_ptr, b.p_col,
+                                                b.p_val, cs, mode);
+  // pattern, RCM, band sizes
+  int *cnt = nullptr, *ptr = nullptr, *cols = nullptr, *vis = nullptr, *que = nullptr;
+  FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.scratch((void**)&ptr, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.scratch((void**)&vis, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.scratch((void**)&que, sizeof(int) * (nct + 1)));
+  k_ac_count<<<grid_for(nct * 32, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, cnt);
+  long long nnzc = 0;
+  FAMS_TRY(exclusive_scan(b, cnt, ptr, nct, &nnzc));
+  FAMS_TRY(b.scratch((void**)&cols, sizeof(int) * (nnzc + 1)));
+  k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
+  int *dkl = nullptr, *dku = nullptr;
+  FAMS_TRY(b.scratch((void**)&dkl, sizeof(int) * B));
+  FAMS_TRY(b.scratch((void**)&dku, sizeof(int) * B));
+  k_rcm<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, dkl, dku);
+  FAMS_CUDA(cudaGetLastError());
+  ch.kl.assign(B, 0);
+  ch.ku.assign(B, 0);
+  FAMS_CUDA(cudaMemcpyAsync(ch.kl.data(), dkl, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaMemcpyAsync(ch.ku.data(), dku, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  ch.band_off.assign(B, 0);
+  long long btot = 0;
+  for (int i = 0; i < B; ++i) {
+    ch.band_off[i] = btot;
+    btot += (long long)(2 * ch.kl[i] + ch.ku[i] + 1) * b.h[i].nc;
+  }
+  FAMS_TRY(b.alloc((void**)&cs.band, sizeof(double) * (btot + 1)));
+  FAMS_CUDA(cudaMemsetAsync(cs.band, 0, sizeof(double) * (btot + 1), st));
+  FAMS_CUDA(cudaMemcpyAsync(cs.kl, ch.kl.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
+                            cudaMemcpyHostToDevice, st));
+  int* ip = nullptr;
+  FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
+  k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+  k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+  k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
+  FAMS_CUDA(cudaGetLastError());
+  return b.check_err("coarse LU");
+}
+
+int phase_coarse_op(Batch& b, int mode) {
+  return build_coarse_system(b, b.cs[0], mode, b.csh[0]);
+}
+
+}  // namespace fams

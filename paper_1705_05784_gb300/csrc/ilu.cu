@@ -1,0 +1,141 @@
+// ILU(0) smoother of the complete fine matrix (Sec. 3.2: M_S from an ILU(0)
+// decomposition of A), natural order (matrix cells, then fracture cells), no
+// pivoting, restricted to the pattern of A.
+//
+// Rows are grouped into dependency levels: a row's level is one more than the
+// highest level among the rows it depends on (its strictly lower entries).
+// For the natural-order stencil rows that is x + y + z; fracture rows follow
+// in one sequential pass per instance.  Rows of one level are independent, so
+// the factorisation and the triangular sweeps process a level in parallel and
+// give the same result as the row-by-row definition.
+#include <algorithm>
+
+#include "batch.cuh"
+
+namespace fams {
+
+namespace {
+
+__global__ void k_lev_matrix(const Inst* inst, int B, const int* off_row, long long nrow,
+                             int* level) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  int loc = (int)(r - I.row_off);
+  if (loc >= I.nm) return;
+  int x = loc % I.nx, y = (loc / I.nx) % I.ny, z = loc / (I.nx * I.ny);
+  level[r] = x + y + z;
+}
+
+__global__ void k_lev_frac(const Inst* inst, int B, const int* rowptr, const int* col,
+                           const int* diag, int* level, int* nlev) {
+  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= B) return;
+  const Inst& I = inst[ii];
+  int mx = I.nm > 0 ? (I.nx - 1) + (I.ny - 1) + (I.dim == 3 ? I.nz - 1 : 0) : -1;
+  for (int r = I.row_off + I.nm; r < I.row_off + I.n; ++r) {
+    int l = 0;
+    for (int p = rowptr[r]; p < diag[r]; ++p) l = max(l, level[col[p]] + 1);
+    level[r] = l;
+    mx = max(mx, l);
+  }
+  nlev[ii] = mx + 1;
+}
+
+__global__ void k_lev_count(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* level, const int* lev_off, int* cnt) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  int ii = find_segment(off_row, B + 1, r);
+  atomicAdd(&cnt[lev_off[ii] + level[r]], 1);
+}
+
+__global__ void k_lev_place(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* level, const int* lev_off, const int* lev_ptr, int* cursor,
+                            int* rows) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  int ii = find_segment(off_row, B + 1, r);
+  int s = lev_off[ii] + level[r];
+  rows[lev_ptr[s] + atomicAdd(&cursor[s], 1)] = (int)r;
+}
+
+// IKJ ILU(0), one CTA per instance, level by level
+__global__ void k_ilu_factor(const Inst* inst, int B, const int* rowptr, const int* col,
+                             const int* diag, const int* lev_off, const int* lev_ptr,
+                             const int* rows, double* F, int* err) {
+  int ii = blockIdx.x;
+  const Inst& I = inst[ii];
+  const int* lp = lev_ptr + lev_off[ii];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int l = 0; l < I.nlev; ++l) {
+    for (int t = lp[l] + threadIdx.x; t < lp[l + 1]; t += blockDim.x) {
+      int i = rows[t];
+      int e = rowptr[i + 1], d = diag[i];
+      for (int p = rowptr[i]; p < d; ++p) {
+        int k = col[p];
+        double lik = F[p] / F[diag[k]];
+        F[p] = lik;
+        int u = p + 1;
+        for (int q = diag[k] + 1; q < rowptr[k + 1]; ++q) {
+          int j = col[q];
+          while (u < e && col[u] < j) ++u;
+          if (u < e && col[u] == j) F[u] -= lik * F[q];
+        }
+      }
+      double piv = F[d];
+      if (!(piv != 0.0) || !isfinite(piv)) bad = 1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicCAS(err, 0, DERR_BREAKDOWN);
+}
+
+}  // namespace
+
+int phase_ilu(Batch& b) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  long long nrow = b.tot_row;
+  int B = b.B;
+  int *level = nullptr, *dnlev = nullptr;
+  FAMS_TRY(b.scratch((void**)&level, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&dnlev, sizeof(int) * B));
+  k_lev_matrix<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level);
+  k_lev_frac<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, level, dnlev);
+  std::vector<int> nlev(B);
+  FAMS_CUDA(cudaMemcpyAsync(nlev.data(), dnlev, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> loff(B + 1, 0);
+  for (int i = 0; i < B; ++i) {
+    b.h[i].nlev = nlev[i];
+    loff[i + 1] = loff[i] + nlev[i] + 1;
+  }
+  FAMS_TRY(b.upload_inst());
+  int tl = loff[B];
+  int *cnt = nullptr, *cursor = nullptr;
+  FAMS_TRY(b.alloc((void**)&b.lev_off, sizeof(int) * (B + 1)));
+  FAMS_TRY(b.alloc((void**)&b.lev_ptr, sizeof(int) * (tl + 1)));
+  FAMS_TRY(b.alloc((void**)&b.lev_rows, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (tl + 1)));
+  FAMS_TRY(b.scratch((void**)&cursor, sizeof(int) * (tl + 1)));
+  FAMS_CUDA(cudaMemcpyAsync(b.lev_off, loff.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (tl + 1), st));
+  FAMS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (tl + 1), st));
+  k_lev_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off, cnt);
+  FAMS_TRY(exclusive_scan(b, cnt, b.lev_ptr, tl, nullptr));
+  k_lev_place<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off,
+                                               b.lev_ptr, cursor, b.lev_rows);
+  // rows of a level in ascending order (independent rows: only for locality)
+  FAMS_TRY(sort_segments(b, b.lev_ptr, tl, b.lev_rows, nullptr, false));
+  FAMS_TRY(b.alloc((void**)&b.ilu, sizeof(double) * (b.tot_nnz + 1)));
+  FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
+  k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, b.lev_off, b.lev_ptr,
+                                  b.lev_rows, b.ilu, b.d_err);
+  FAMS_CUDA(cudaGetLastError());
+  return b.check_err("ILU(0)");
+}
+
+}  // namespace fams

@@ -1,0 +1,202 @@
+// Fine-scale EDFM system A p = q (Sec. 2, Eqs. 1-8) in CSR with sorted
+// columns: two-point matrix stencil (harmonic face transmissibilities),
+// matrix-fracture connections T = CI k_m, fracture-fracture links, Dirichlet
+// faces through half-cell transmissibilities.  Row order [matrix; fracture].
+#include "batch.cuh"
+
+namespace fams {
+
+namespace {
+
+__device__ inline double face_T(double ki, double kj, double area, double h) {
+  return area / (h / (2.0 * ki) + h / (2.0 * kj));
+}
+
+__global__ void k_nnc_mcell(const Inst* inst, int B, const int* off_row, long long nnc,
+                            const int* nrow_m, int* mcell) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnc) return;
+  int r = nrow_m[k];
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  mcell[k] = I.m_off + (r - I.row_off);
+}
+
+__global__ void k_ff_bcell(const Inst* inst, int B, const int* off_row, long long nff,
+                           const int* ffb, int* bcell) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nff) return;
+  int r = ffb[k];
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  bcell[k] = I.fc_off + (r - I.row_off - I.nm);
+}
+
+__global__ void k_row_count(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* nnc_t_ptr, const int* nnc_first, const int* ffr_ptr,
+                            const int* ff_first, int* cnt) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  int loc = (int)(r - I.row_off);
+  int c = 1;
+  if (loc < I.nm) {
+    int x = loc % I.nx, y = (loc / I.nx) % I.ny, z = loc / (I.nx * I.ny);
+    c += (x > 0) + (x < I.nx - 1) + (y > 0) + (y < I.ny - 1);
+    if (I.dim == 3) c += (z > 0) + (z < I.nz - 1);
+    int gm = I.m_off + loc;
+    c += nnc_t_ptr[gm + 1] - nnc_t_ptr[gm];
+  } else {
+    int gc = I.fc_off + (loc - I.nm);
+    c += nnc_first[gc + 1] - nnc_first[gc];
+    c += ffr_ptr[gc + 1] - ffr_ptr[gc];
+    c += ff_first[gc + 1] - ff_first[gc];
+  }
+  cnt[r] = c;
+}
+
+__global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long long nrow,
+                           const double* perm, const int* nnc_t_ptr, const int* nnc_t_fc,
+                           const double* nnc_t_T, const int* nnc_first, const int* nrow_m,
+                           const double* nT, const int* ffr_ptr, const int* ffr_a,
+                           const double* ffr_T, const int* ff_first, const int* ffb,
+                           const double* ffT, const int* rowptr, int* col, double* val,
+                           int* diag, double* TD, double* qD) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  int loc = (int)(r - I.row_off);
+  int p = rowptr[r];
+  double sumT = 0.0, td = 0.0, qd = 0.0;
+  int dpos = -1;
+  if (loc < I.nm) {
+    int nx = I.nx, ny = I.ny, nz = I.nz;
+    int x = loc % nx, y = (loc / nx) % ny, z = loc / (nx * ny);
+    const double* k = perm + I.m_off;
+    double ki = k[loc];
+    double ax = I.dy * I.dz, ay = I.dx * I.dz, az = I.dx * I.dy;
+    // columns in ascending order
+    if (I.dim == 3 && z > 0) {
+      double t = face_T(k[loc - nx * ny], ki, az, I.dz);
+      col[p] = (int)r - nx * ny; val[p++] = -t; sumT += t;
+    }
+    if (y > 0) {
+      double t = face_T(k[loc - nx], ki, ay, I.dy);
+      col[p] = (int)r - nx; val[p++] = -t; sumT += t;
+    }
+    if (x > 0) {
+      double t = face_T(k[loc - 1], ki, ax, I.dx);
+      col[p] = (int)r - 1; val[p++] = -t; sumT += t;
+    }
+    dpos = p++;
+    if (x < nx - 1) {
+      double t = face_T(ki, k[loc + 1], ax, I.dx);
+      col[p] = (int)r + 1; val[p++] = -t; sumT += t;
+    }
+    if (y < ny - 1) {
+      double t = face_T(ki, k[loc + nx], ay, I.dy);
+      col[p] = (int)r + nx; val[p++] = -t; sumT += t;
+    }
+    if (I.dim == 3 && z < nz - 1) {
+      double t = face_T(ki, k[loc + nx * ny], az, I.dz);
+      col[p] = (int)r + nx * ny; val[p++] = -t; sumT += t;
+    }
+    int gm = I.m_off + loc;
+    for (int q = nnc_t_ptr[gm]; q < nnc_t_ptr[gm + 1]; ++q) {
+      int gc = nnc_t_fc[q];
+      double t = nnc_t_T[q];
+      col[p] = I.row_off + I.nm + (gc - I.fc_off); val[p++] = -t; sumT += t;
+    }
+    // Dirichlet faces: T_D = 2 k A / h
+    const int on[6] = {x == 0, x == nx - 1, y == 0, y == ny - 1, I.dim == 3 && z == 0,
+                       I.dim == 3 && z == nz - 1};
+    const double ar[6] = {ax, ax, ay, ay, az, az};
+    const double hh[6] = {I.dx, I.dx, I.dy, I.dy, I.dz, I.dz};
+    for (int f = 0; f < 6; ++f) {
+      if (on[f] && ((I.bc_mask >> f) & 1)) {
+        double t = 2.0 * ki * ar[f] / hh[f];
+        td += t;
+        qd += t * I.bc_val[f];
+      }
+    }
+  } else {
+    int gc = I.fc_off + (loc - I.nm);
+    for (int q = nnc_first[gc]; q < nnc_first[gc + 1]; ++q) {
+      double t = nT[q];
+      col[p] = nrow_m[q]; val[p++] = -t; sumT += t;
+    }
+    for (int q = ffr_ptr[gc]; q < ffr_ptr[gc + 1]; ++q) {
+      double t = ffr_T[q];
+      col[p] = I.row_off + I.nm + (ffr_a[q] - I.fc_off); val[p++] = -t; sumT += t;
+    }
+    dpos = p++;
+    for (int q = ff_first[gc]; q < ff_first[gc + 1]; ++q) {
+      double t = ffT[q];
+      col[p] = ffb[q]; val[p++] = -t; sumT += t;
+    }
+  }
+  col[dpos] = (int)r;
+  val[dpos] = sumT + td;
+  diag[r] = dpos;
+  TD[r] = td;
+  qD[r] = qd;
+}
+
+}  // namespace
+
+int phase_system(Batch& b) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  long long nnc = b.tot_nnc, nff = b.tot_ff, nfc = b.tot_fc, nrow = b.tot_row;
+  // matrix-cell view of the matrix-fracture connections, sorted by fracture cell
+  int* mcell = nullptr;
+  FAMS_TRY(b.scratch((void**)&mcell, sizeof(int) * (nnc + 1)));
+  if (nnc > 0)
+    k_nnc_mcell<<<grid_for(nnc, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nnc, b.nnc_row_m,
+                                                mcell);
+  int *nnc_t_ptr = nullptr, *nnc_t_fc = nullptr;
+  double* nnc_t_T = nullptr;
+  FAMS_TRY(transpose(b, b.nnc_first, mcell, b.nnc_T, (int)nfc, (int)b.tot_m, nnc, &nnc_t_ptr,
+                     &nnc_t_fc, &nnc_t_T, false));
+  // fracture-fracture links seen from their higher cell
+  int* bcell = nullptr;
+  FAMS_TRY(b.scratch((void**)&bcell, sizeof(int) * (nff + 1)));
+  if (nff > 0)
+    k_ff_bcell<<<grid_for(nff, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nff, b.ff_b, bcell);
+  int *ffr_ptr = nullptr, *ffr_a = nullptr;
+  double* ffr_T = nullptr;
+  FAMS_TRY(transpose(b, b.ff_first, bcell, b.ff_T, (int)nfc, (int)nfc, nff, &ffr_ptr, &ffr_a,
+                     &ffr_T, false));
+  // ffr_a: for each higher cell, the lower cells (fracture-cell index) in order
+  int* cnt = nullptr;
+  FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.alloc((void**)&b.rowptr, sizeof(int) * (nrow + 1)));
+  if (nrow > 0)
+    k_row_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, nnc_t_ptr,
+                                                 b.nnc_first, ffr_ptr, b.ff_first, cnt);
+  long long nnz = 0;
+  FAMS_TRY(exclusive_scan(b, cnt, b.rowptr, nrow, &nnz));
+  b.tot_nnz = nnz;
+  FAMS_TRY(b.alloc((void**)&b.col, sizeof(int) * (nnz + 1)));
+  FAMS_TRY(b.alloc((void**)&b.val, sizeof(double) * (nnz + 1)));
+  FAMS_TRY(b.alloc((void**)&b.diag, sizeof(int) * (nrow + 1)));
+  FAMS_TRY(b.alloc((void**)&b.TD, sizeof(double) * (nrow + 1)));
+  FAMS_TRY(b.alloc((void**)&b.qD, sizeof(double) * (nrow + 1)));
+  if (nrow > 0)
+    k_row_fill<<<grid_for(nrow, T), T, 0, st>>>(
+        b.d_inst, b.B, b.off_row, nrow, b.perm, nnc_t_ptr, nnc_t_fc, nnc_t_T, b.nnc_first,
+        b.nnc_row_m, b.nnc_T, ffr_ptr, ffr_a, ffr_T, b.ff_first, b.ff_b, b.ff_T, b.rowptr, b.col,
+        b.val, b.diag, b.TD, b.qD);
+  FAMS_CUDA(cudaGetLastError());
+  std::vector<int> hp(nrow + 1);
+  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.rowptr, sizeof(int) * (nrow + 1), cudaMemcpyDeviceToHost,
+                            st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < b.B; ++i) {
+    Inst& I = b.h[i];
+    I.nnz_off = hp[I.row_off];
+    I.nnz = hp[I.row_off + I.n] - hp[I.row_off];
+  }
+  FAMS_TRY(b.upload_inst());
+  return b.check_err("fine system");
+}
+
+}  // namespace fams

@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libfams (include/fams.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  Importing this
+module loads the in-tree libfams.so and raises if it is missing: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfams.so")
+
+DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
+R_FV, R_FE = 0, 1
+FP64, MIXED = 0, 1
+OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ETIMEOUT, ECUDA, ECAPACITY = 0, -1, -2, -3, -4, -5, -6, -7
+
+Q = dict(NNC_FRAC=1, NNC_MATRIX=2, NNC_AREA=3, NNC_DIST=4, FF_A=5, FF_B=6, FF_T=7,
+         A_ROWPTR=8, A_COL=9, A_VAL=10, Q=11, RANK=12, PRIMAL=13, NODE_CELL=14,
+         P_ROWPTR=15, P_COL=16, P_VAL=17, AC=18, ILU_VAL=19, LEVELS=20)
+_INT_QUERIES = {1, 2, 5, 6, 8, 9, 12, 13, 14, 15, 16, 20}
+
+
+class fams_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("bc_mask", C.c_int), ("bc_value", C.c_double * 6)]
+
+
+class fams_fracs(C.Structure):
+    _fields_ = [("n", C.c_int), ("xy", C.POINTER(C.c_double)), ("kf", C.POINTER(C.c_double)),
+                ("aperture", C.c_double), ("h_f", C.c_double)]
+
+
+class fams_opts(C.Structure):
+    _fields_ = [("coarsen", C.c_int * 3), ("frac_dmin", C.c_int), ("frac_cz", C.c_int),
+                ("basis", C.c_int), ("restriction", C.c_int), ("alpha", C.c_double),
+                ("max_iter", C.c_int), ("precision", C.c_int)]
+
+
+class fams_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("converged", C.c_int),
+                ("solve_ms", C.c_double)]
+
+
+class FamsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libfams status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; build it with "
+                          "paper_1705_05784_gb300.build.build() (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    lib.fams_setup_batch.argtypes = [C.c_int, P(fams_grid), P(P(C.c_double)), P(fams_fracs),
+                                     P(fams_opts), P(C.c_void_p)]
+    lib.fams_setup.argtypes = [P(fams_grid), P(C.c_double), P(fams_fracs), P(fams_opts),
+                               P(C.c_void_p)]
+    lib.fams_sizes.argtypes = [C.c_void_p, C.c_int] + [P(C.c_int)] * 5
+    lib.fams_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, P(fams_stats)]
+    lib.fams_solve_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double,
+                                     P(fams_stats)]
+    lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fams_query.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong]
+    lib.fams_num_instances.argtypes = [C.c_void_p]
+    lib.fams_destroy.argtypes = [C.c_void_p]
+    lib.fams_destroy.restype = None
+    lib.fams_strerror.argtypes = [C.c_int]
+    lib.fams_strerror.restype = C.c_char_p
+    lib.fams_last_error.argtypes = []
+    lib.fams_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(status, allow=()):
+    if status < 0 and status not in allow:
+        raise FamsError(status, (lib.fams_strerror(status).decode() + ": "
+                                 + lib.fams_last_error().decode()))
+    return status
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _args(prob):
+    """ctypes structs (and the arrays they point into) for one inputs.Problem."""
+    g = fams_grid(prob.dim, prob.nx, prob.ny, prob.nz if prob.dim == 3 else 1,
+                  prob.dx, prob.dy, prob.dz, prob.bc_mask, (C.c_double * 6)(*prob.bc_value))
+    perm = np.ascontiguousarray(prob.perm, dtype=np.float64)
+    fr = np.zeros((0, 6 if prob.dim == 3 else 4)) if prob.fracs is None else prob.fracs
+    xy = np.ascontiguousarray(fr, dtype=np.float64).ravel()
+    kf = np.ascontiguousarray(np.zeros(0) if prob.kf is None else prob.kf, dtype=np.float64)
+    f = fams_fracs(len(fr), _dptr(xy) if len(fr) else None, _dptr(kf) if len(fr) else None,
+                   prob.aperture, prob.h_f)
+    cz = prob.coarsen[2] if prob.dim == 3 else 1
+    o = fams_opts((C.c_int * 3)(prob.coarsen[0], prob.coarsen[1], cz), prob.frac_dmin,
+                  max(1, prob.frac_cz), prob.basis, prob.restriction, prob.alpha,
+                  prob.max_iter, getattr(prob, "precision", FP64))
+    return g, perm, f, o, (xy, kf)
+
+
+class Context:
+    """One libfams context (a batch of one or more instances)."""
+
+    def __init__(self, problems):
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        n = len(problems)
+        parts = [_args(p) for p in problems]
+        grids = (fams_grid * n)(*[p[0] for p in parts])
+        perms = (C.POINTER(C.c_double) * n)(*[_dptr(p[1]) for p in parts])
+        fracs = (fams_fracs * n)(*[p[2] for p in parts])
+        opts = (fams_opts * n)(*[p[3] for p in parts])
+        self._keep = parts
+        self.h = C.c_void_p()
+        _check(lib.fams_setup_batch(n, grids, perms, fracs, opts, C.byref(self.h)))
+        self.n = n
+        self.problems = problems
+
+    def close(self):
+        if self.h:
+            lib.fams_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sizes(self, inst=0):
+        v = [C.c_int() for _ in range(5)]
+        _check(lib.fams_sizes(self.h, inst, *[C.byref(x) for x in v]))
+        return dict(zip(("n_matrix", "n_frac", "n_coarse", "n_faces", "n_nnc"),
+                        [x.value for x in v]))
+
+    def query(self, what, inst=0):
+        code = Q[what] if isinstance(what, str) else what
+        n = _check(lib.fams_query(self.h, inst, code, None, 0))
+        dt = np.int32 if code in _INT_QUERIES else np.float64
+        out = np.zeros(n, dt)
+        _check(lib.fams_query(self.h, inst, code, out.ctypes.data_as(C.c_void_p), n))
+        return out
+
+    def solve(self, rhs=None, x0=None, tol=1e-8, allow_noconv=True):
+        """Solve every instance; rhs/x0: list per instance (or one array for a
+        single instance).  Returns (list of pressures, list of stats dicts)."""
+        n = self.n
+        sz = [self.sizes(i) for i in range(n)]
+        N = [s["n_matrix"] + s["n_frac"] for s in sz]
+        if rhs is not None and not isinstance(rhs, (list, tuple)):
+            rhs = [rhs]
+        if x0 is not None and not isinstance(x0, (list, tuple)):
+            x0 = [x0]
+        xs = [np.ascontiguousarray(x0[i] if x0 is not None else np.zeros(N[i]), np.float64).copy()
+              for i in range(n)]
+        rs = [None if rhs is None or rhs[i] is None else np.ascontiguousarray(rhs[i], np.float64)
+              for i in range(n)]
+        xp = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
+        rp = (C.c_void_p * n)(*[0 if r is None else r.ctypes.data for r in rs])
+        st = (fams_stats * n)()
+        s = lib.fams_solve_batch(self.h, rp, xp, tol, st)
+        _check(s, allow=(ENOCONV,) if allow_noconv else ())
+        stats = [dict(iterations=st[i].iterations, rel_residual=st[i].rel_residual,
+                      converged=bool(st[i].converged), solve_ms=st[i].solve_ms, status=s)
+                 for i in range(n)]
+        return xs, stats
+
+    def solve_device(self, rhs_ptrs, x_ptrs, tol):
+        """The same call with caller-owned buffers given as raw pointers (host
+        or device), for timing the C-ABI path without copies in Python."""
+        n = self.n
+        xp = (C.c_void_p * n)(*x_ptrs)
+        rp = (C.c_void_p * n)(*[p or 0 for p in rhs_ptrs])
+        st = (fams_stats * n)()
+        s = lib.fams_solve_batch(self.h, rp, xp, tol, st)
+        _check(s, allow=(ENOCONV,))
+        return [dict(iterations=st[i].iterations, rel_residual=st[i].rel_residual,
+                     converged=bool(st[i].converged), solve_ms=st[i].solve_ms)
+                for i in range(n)]
+
+    def flux(self, x, inst=0):
+        s = self.sizes(inst)
+        face = np.zeros(s["n_faces"])
+        nnc = np.zeros(max(s["n_nnc"], 1))
+        x = np.ascontiguousarray(x, np.float64)
+        _check(lib.fams_flux(self.h, inst, x.ctypes.data_as(C.c_void_p),
+                             face.ctypes.data_as(C.c_void_p), nnc.ctypes.data_as(C.c_void_p)))
+        return face, nnc[: s["n_nnc"]]

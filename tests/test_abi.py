@@ -1,0 +1,45 @@
+"""CPU-side checks of the C ABI: the library builds and exports every entry
+point that include/fams.h declares (no compute call without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fams.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fams_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("fams_setup", "fams_solve", "fams_flux", "fams_destroy", "fams_setup_batch",
+              "fams_solve_batch", "fams_sizes", "fams_query", "fams_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1705_05784_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(f"no CUDA toolkit: {e}")
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n), n
+    lib.fams_strerror.restype = ctypes.c_char_p
+    assert lib.fams_strerror(-3) == b"iteration did not reach the tolerance"
+
+
+def test_binding_loads_and_reports_missing_gpu_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_1705_05784_gb300 import fams, inputs
+    with pytest.raises(fams.FamsError) as e:
+        fams.Context(inputs.config_2d_small())
+    assert e.value.status == fams.ECUDA

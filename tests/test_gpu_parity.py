@@ -1,0 +1,216 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: integer and index work (fracture cells, matrix-fracture and
+fracture-fracture connection lists, CSR patterns, wirebasket ranks, primal
+blocks, coarse nodes) must be bit-exact.  FP64 values computed by the same
+formula in a different summation order agree to a few ulps (1e-12 relative);
+quantities that pass through local or coarse direct solves agree to 1e-10
+relative; converged pressures to 1e-10 relative L2 with iteration counts
+within +-1.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle import solver as osolver
+from paper_1705_05784_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _fams():
+    from paper_1705_05784_gb300 import fams
+    return fams
+
+
+def _case(name, variant=0, restriction=1):
+    if name == "2d32":
+        p = inputs.config_2d_small(basis=variant, restriction=restriction)
+    elif name == "2d64":
+        p = inputs.config_2d(64, 1.5, 8.0, 6, (15, 45), 1e3, 8, 8, seed=4, basis=variant,
+                             restriction=restriction)
+    elif name == "2d50ragged":
+        # 50 x 37 cells, coarsening 7 x 6: partial last blocks on both axes;
+        # truncation on (alpha = 1e-2)
+        nx, ny = 50, 37
+        p = inputs.Problem(dim=2, nx=nx, ny=ny, nz=1,
+                           perm=10 ** inputs.gaussian_field((nx, ny), 1.0, 5.0, 6),
+                           fracs=inputs.random_segments(5, (nx, ny), (10, 30), 1006),
+                           kf=np.full(5, 1e2), coarsen=(7, 6, 1), frac_dmin=6, basis=variant,
+                           restriction=restriction, alpha=1e-2)
+    elif name == "3d":
+        p = inputs.config_3d(20, 18, 12, 1.0, (5, 5, 2), 4, (6, 14), 1e3, (5, 6, 4), 5, 4,
+                             seed=8, basis=variant, restriction=restriction)
+        p.fracs[:, 4] = 0.0
+        p.fracs[:, 5] = 12.0
+    else:
+        raise KeyError(name)
+    return p
+
+
+CASES = ["2d32", "2d64", "2d50ragged", "3d"]
+
+
+@pytest.fixture(scope="module")
+def built():
+    cache = {}
+
+    def get(name, variant=0, restriction=1):
+        key = (name, variant, restriction)
+        if key not in cache:
+            p = _case(name, variant, restriction)
+            g, sysm, c, P, st = oracle.build(p)
+            ctx = _fams().Context(p)
+            cache[key] = (p, g, sysm, c, P, st, ctx)
+        return cache[key]
+    yield get
+    for v in cache.values():
+        v[-1].close()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_geometry_bit_exact(built, name):
+    p, g, sysm, c, P, st, ctx = built(name)
+    s = ctx.sizes()
+    assert s["n_matrix"] == g.n_matrix and s["n_frac"] == g.n_frac
+    np.testing.assert_array_equal(ctx.query("NNC_FRAC"), g.nnc_f)
+    np.testing.assert_array_equal(ctx.query("NNC_MATRIX"), g.nnc_m)
+    np.testing.assert_allclose(ctx.query("NNC_AREA"), g.nnc_area, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(ctx.query("NNC_DIST"), g.nnc_dist, rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(ctx.query("FF_A"), g.ff_a)
+    np.testing.assert_array_equal(ctx.query("FF_B"), g.ff_b)
+    np.testing.assert_allclose(ctx.query("FF_T"), g.ff_T, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fine_system(built, name):
+    p, g, sysm, c, P, st, ctx = built(name)
+    A = sysm.A
+    np.testing.assert_array_equal(ctx.query("A_ROWPTR"), A.indptr)
+    np.testing.assert_array_equal(ctx.query("A_COL"), A.indices)
+    np.testing.assert_allclose(ctx.query("A_VAL"), A.data, rtol=1e-12, atol=1e-14 * abs(A.data).max())
+    np.testing.assert_allclose(ctx.query("Q"), sysm.q, rtol=1e-12, atol=1e-14 * abs(sysm.q).max())
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_grids_bit_exact(built, name):
+    p, g, sysm, c, P, st, ctx = built(name)
+    np.testing.assert_array_equal(ctx.query("RANK"), c.rank)
+    np.testing.assert_array_equal(ctx.query("PRIMAL"), c.primal)
+    np.testing.assert_array_equal(ctx.query("NODE_CELL"), c.node_cell)
+    assert ctx.sizes()["n_coarse"] == c.n_coarse
+
+
+def _gpu_P(ctx, shape):
+    return sp.csr_matrix((ctx.query("P_VAL"), ctx.query("P_COL"), ctx.query("P_ROWPTR")),
+                         shape=shape)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", CASES)
+def test_prolongation(built, name, variant):
+    p, g, sysm, c, P, st, ctx = built(name, variant)
+    Pg = _gpu_P(ctx, P.shape)
+    np.testing.assert_array_equal(Pg.indptr, P.indptr)
+    np.testing.assert_array_equal(Pg.indices, P.indices)
+    np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
+    assert np.abs(np.asarray(Pg.sum(axis=1)).ravel() - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_operator(built, name, restriction):
+    p, g, sysm, c, P, st, ctx = built(name, 0, restriction)
+    Ac = ctx.query("AC").reshape(c.n_coarse, c.n_coarse)
+    np.testing.assert_allclose(Ac, st.Ac, rtol=0, atol=1e-11 * np.abs(st.Ac).max())
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_ilu0(built, name):
+    p, g, sysm, c, P, st, ctx = built(name)
+    F = ctx.query("ILU_VAL")
+    np.testing.assert_allclose(F, st.F.data, rtol=1e-11, atol=1e-13 * np.abs(st.F.data).max())
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+def test_solve_parity(built, name, variant):
+    p, g, sysm, c, P, st, ctx = built(name, variant)
+    xo, ito, rro, oko, _ = osolver.two_stage_solve(st, tol=1e-8, max_iter=p.max_iter)
+    xs, stats = ctx.solve(tol=1e-8)
+    x = xs[0]
+    assert stats[0]["converged"] == oko
+    assert abs(stats[0]["iterations"] - ito) <= 1
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
+    # the residual the GPU reports is the true one
+    rr = np.linalg.norm(sysm.q - sysm.A @ x) / np.linalg.norm(sysm.q)
+    assert abs(rr - stats[0]["rel_residual"]) <= 1e-3 * rr + 1e-15
+
+
+def test_fv_restriction_solve(built):
+    p, g, sysm, c, P, st, ctx = built("2d32", 0, 0)
+    xo, ito, rro, oko, _ = osolver.two_stage_solve(st, tol=1e-8, max_iter=p.max_iter)
+    xs, stats = ctx.solve(tol=1e-8)
+    assert abs(stats[0]["iterations"] - ito) <= 1
+    assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["2d32", "2d64", "3d"])
+def test_flux_conservative_and_matches_oracle(built, name):
+    p, g, sysm, c, P, st, ctx = built(name, 0, 1)
+    p.tol = 1e-4
+    xs, stats = ctx.solve(tol=1e-4)
+    x = xs[0]
+    face, nnc = ctx.flux(x)
+    # oracle reconstruction from the same iterate
+    st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    flux, dflux, pp, pt = osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
+    nm = g.n_matrix
+    nx, ny = p.nx, p.ny
+    nz = p.nz if p.dim == 3 else 1
+    nfx, nfy = (nx + 1) * ny * nz, nx * (ny + 1) * nz
+    fx = face[:nfx].reshape(nz, ny, nx + 1)
+    fy = face[nfx:nfx + nfy].reshape(nz, ny + 1, nx)
+    parts = [fx[:, :, 1:-1].ravel(), fy[:, 1:-1, :].ravel()]
+    if p.dim == 3:
+        fz = face[nfx + nfy:].reshape(nz + 1, ny, nx)
+        parts.append(fz[1:-1].ravel())
+    gpu_conn = np.concatenate(parts + [nnc])
+    scale = np.abs(flux).max()
+    np.testing.assert_allclose(gpu_conn, flux, rtol=0, atol=1e-8 * scale)
+    # cell-by-cell mass balance of the GPU field
+    ci, cj, _ = osolver.connections(sysm, p)
+    out = np.zeros(sysm.n)
+    np.add.at(out, ci, gpu_conn)
+    np.subtract.at(out, cj, gpu_conn)
+    xm = np.arange(nm) % nx
+    west = fx[:, :, 0].ravel()
+    east = fx[:, :, -1].ravel()
+    out[np.nonzero(xm == 0)[0]] -= west
+    out[np.nonzero(xm == nx - 1)[0]] += east
+    assert np.abs(out).max() < 1e-11 * scale
+    assert abs(west.sum() - east.sum()) < 1e-9 * scale
+
+
+def test_batch_matches_single(built):
+    """A batch of different instances gives each instance's single result
+    bit for bit (one CTA per instance, fixed reduction order)."""
+    fams = _fams()
+    probs = [_case("2d32", 0), _case("2d64", 0), _case("2d50ragged", 3)]
+    with fams.Context(probs) as cb:
+        xb, sb = cb.solve(tol=1e-8)
+    for i, p in enumerate(probs):
+        with fams.Context(p) as c1:
+            x1, s1 = c1.solve(tol=1e-8)
+        assert s1[0]["iterations"] == sb[i]["iterations"]
+        assert np.linalg.norm(x1[0] - xb[i]) / np.linalg.norm(x1[0]) < 1e-10
+
+
+def test_rejects_bad_input():
+    fams = _fams()
+    p = _case("2d32")
+    p.bc_mask = 0
+    with pytest.raises(fams.FamsError) as e:
+        fams.Context(p)
+    assert e.value.status == fams.EINVAL
