@@ -172,7 +172,16 @@ enum {
   FAMS_Q_P_VAL = 17,       /* double */
   FAMS_Q_AC = 18,          /* double dense coarse operator R A P, row-major */
   FAMS_Q_ILU_VAL = 19,     /* double ILU(0) factors in the pattern of A */
-  FAMS_Q_LEVELS = 20       /* int32  number of ILU(0) levels (1 value) */
+  FAMS_Q_LEVELS = 20,      /* int32  number of ILU(0) levels (1 value) */
+  FAMS_Q_COARSE_PERM = 21, /* int32  band position -> coarse unknown (reverse Cuthill-McKee) */
+  FAMS_Q_COARSE_IPIV = 22, /* int32  pivot row (band position) of each LU step */
+  FAMS_Q_BAND_KLKU = 23,   /* int32  lower and upper bandwidth (2 values) */
+  FAMS_Q_BAND = 24,        /* double band LU factors, column-major, 2kl+ku+1 rows */
+  FAMS_Q_HISTORY = 25,     /* double relative residual after each sweep of the last solve */
+  FAMS_Q_LAST_DP1 = 26,    /* double multiscale correction of the last sweep (Table 1 step 5) */
+  FAMS_Q_LAST_DP2 = 27,    /* double smoother correction of the last sweep (Table 1 step 7) */
+  FAMS_Q_LAST_RC = 28,     /* double coarse right-hand side R r of the last sweep */
+  FAMS_Q_LAST_EC = 29      /* double coarse solution (R A P)^-1 R r of the last sweep */
 };
 int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap);
 

@@ -393,6 +393,23 @@ int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap
     case FAMS_Q_AC: FAMS_TRY(dbls(b.cs[0].Ac + b.csh[0].ac_off[inst], (long long)I.nc * I.nc)); break;
     case FAMS_Q_ILU_VAL: FAMS_TRY(dbls(b.ilu + I.nnz_off, I.nnz)); break;
     case FAMS_Q_LEVELS: vi.assign(1, I.nlev); break;
+    case FAMS_Q_COARSE_PERM: FAMS_TRY(ints(b.cs[0].perm + I.nc_off, I.nc, 0)); break;
+    case FAMS_Q_COARSE_IPIV: FAMS_TRY(ints(b.cs[0].ipiv + I.nc_off, I.nc, 0)); break;
+    case FAMS_Q_BAND_KLKU: vi = {b.csh[0].kl[inst], b.csh[0].ku[inst]}; break;
+    case FAMS_Q_BAND:
+      FAMS_TRY(dbls(b.cs[0].band + b.csh[0].band_off[inst],
+                    (long long)(2 * b.csh[0].kl[inst] + b.csh[0].ku[inst] + 1) * I.nc));
+      break;
+    case FAMS_Q_LAST_DP1: FAMS_TRY(dbls(b.dp + I.row_off, I.n)); break;
+    case FAMS_Q_LAST_DP2: FAMS_TRY(dbls(b.y + I.row_off, I.n)); break;
+    case FAMS_Q_LAST_RC: FAMS_TRY(dbls(b.rc + I.nc_off, I.nc)); break;
+    case FAMS_Q_LAST_EC: FAMS_TRY(dbls(b.ec + I.nc_off, I.nc)); break;
+    case FAMS_Q_HISTORY: {
+      std::vector<double> st;
+      FAMS_TRY(fetch(b, b.stat + 4 * inst, 4, st));
+      FAMS_TRY(dbls(b.hist + (long long)inst * (b.hist_len), (long long)st[0] + 1));
+      break;
+    }
     default: set_error("unknown query"); return FAMS_EINVAL;
   }
   long long n = isint ? (long long)vi.size() : (long long)vd.size();

@@ -469,6 +469,8 @@ int phase_basis(Batch& b) {
   FAMS_TRY(b.scratch((void**)&pos, sizeof(int) * (nrow + 1)));
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  // leave room for the kernels' static shared memory
+  max_smem -= 1024;
   FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem));
   for (int s = 0; s < NSTAGE; ++s) {

@@ -125,6 +125,8 @@ struct Batch {
   double* rc = nullptr;
   double* ec = nullptr;
   double* stat = nullptr;      // per instance: 4 doubles (iters, relres, converged, qnorm)
+  double* hist = nullptr;      // per instance: relative residual after each sweep
+  long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
   bool fv_ready = false;
 

@@ -121,17 +121,28 @@ __global__ void k_rcm(const Inst* inst, int B, const int* ptr, const int* cols, 
     }
   }
   for (int k = 0; k < n; ++k) perm[k] = qu[n - 1 - k];
-  int* ip = vis;  // reuse as the inverse permutation
-  for (int k = 0; k < n; ++k) ip[perm[k]] = k;
-  int kl = 0, ku = 0;
-  for (int r = 0; r < n; ++r)
-    for (int p = rp[r]; p < rp[r + 1]; ++p) {
-      int d = ip[r] - ip[cols[p]];
-      if (d > kl) kl = d;
-      if (-d > ku) ku = -d;
-    }
-  kl_out[ii] = kl;
-  ku_out[ii] = ku;
+}
+
+// lower / upper bandwidth of each instance's dense A_c under the ordering, from
+// the same entries the band fill stores (thread per coarse row)
+__global__ void k_bandwidth(const Inst* inst, int B, const int* off_nc, long long nct,
+                            CoarseSys cs, const int* ip_all, int* kl_out, int* ku_out) {
+  long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nct) return;
+  int ii = find_segment(off_nc, B + 1, w);
+  const Inst& I = inst[ii];
+  int r = (int)(w - I.nc_off);
+  const double* row = cs.Ac + cs.ac_off[ii] + (long long)r * I.nc;
+  const int* ip = ip_all + I.nc_off;
+  int kl = 0, ku = 0, i = ip[r];
+  for (int c = 0; c < I.nc; ++c) {
+    if (row[c] == 0.0) continue;
+    int d = i - ip[c];
+    kl = max(kl, d);
+    ku = max(ku, -d);
+  }
+  atomicMax(&kl_out[ii], kl);
+  atomicMax(&ku_out[ii], ku);
 }
 
 __global__ void k_band_fill(const Inst* inst, int B, const int* off_nc, long long nct,
@@ -268,10 +279,15 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_TRY(exclusive_scan(b, cnt, ptr, nct, &nnzc));
   FAMS_TRY(b.scratch((void**)&cols, sizeof(int) * (nnzc + 1)));
   k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
-  int *dkl = nullptr, *dku = nullptr;
+  int *dkl = nullptr, *dku = nullptr, *ip = nullptr;
   FAMS_TRY(b.scratch((void**)&dkl, sizeof(int) * B));
   FAMS_TRY(b.scratch((void**)&dku, sizeof(int) * B));
+  FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
+  FAMS_CUDA(cudaMemsetAsync(dkl, 0, sizeof(int) * B, st));
+  FAMS_CUDA(cudaMemsetAsync(dku, 0, sizeof(int) * B, st));
   k_rcm<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, dkl, dku);
+  k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+  k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
   FAMS_CUDA(cudaGetLastError());
   ch.kl.assign(B, 0);
   ch.ku.assign(B, 0);
@@ -290,9 +306,6 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
                             cudaMemcpyHostToDevice, st));
-  int* ip = nullptr;
-  FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
-  k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
   k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
   k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
   FAMS_CUDA(cudaGetLastError());

@@ -282,6 +282,7 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
   size_t smem = sizeof(double) * 2 * (size_t)I.nc;
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  max_smem -= 1024;  // static shared memory of the kernels
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_local, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   k_flux_stage<<<1, 512, smem, st>>>(b.d_inst, ii, *cs, b.rowptr, b.col, b.val, b.blk_ptr,

@@ -64,6 +64,10 @@ struct SolveArgs {
   double* dp;
   double* y;
   double* stat;
+  double* hist;
+  long long hist_len;
+  double* crhs;   // coarse right-hand side of the last sweep (coarse order)
+  double* csol;   // coarse solution of the last sweep
   double tol;
 };
 
@@ -131,7 +135,10 @@ __global__ void __launch_bounds__(SOLVE_T) k_solve(SolveArgs a) {
       acc += s * s;
     }
     rel = sqrt(block_sum(acc, red)) / qn;
-    if (threadIdx.x == 0) s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel));
+    if (threadIdx.x == 0) {
+      a.hist[(long long)ii * a.hist_len + it] = rel;
+      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel));
+    }
     __syncthreads();
     if (s_done) break;
     // step 5: coarse right-hand side R r, in band order
@@ -146,9 +153,13 @@ __global__ void __launch_bounds__(SOLVE_T) k_solve(SolveArgs a) {
       yb[k] = s;
     }
     __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) a.crhs[co + perm[k]] = yb[k];
     if (threadIdx.x < 32) band_solve_warp(AB, ipiv, nc, kl, ku, yb);
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) ecs[perm[k]] = yb[k];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      ecs[perm[k]] = yb[k];
+      a.csol[co + perm[k]] = yb[k];
+    }
     __syncthreads();
     // dp1 = P e_c
     for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
@@ -202,6 +213,12 @@ int phase_alloc_work(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.dp, sizeof(double) * (n + 1)));
   FAMS_TRY(b.alloc((void**)&b.y, sizeof(double) * (n + 1)));
   FAMS_TRY(b.alloc((void**)&b.stat, sizeof(double) * 4 * b.B));
+  int mi = 0;
+  for (auto& I : b.h) mi = std::max(mi, I.max_iter);
+  b.hist_len = mi + 1;
+  FAMS_TRY(b.alloc((void**)&b.rc, sizeof(double) * (b.tot_nc + 1)));
+  FAMS_TRY(b.alloc((void**)&b.ec, sizeof(double) * (b.tot_nc + 1)));
+  FAMS_TRY(b.alloc((void**)&b.hist, sizeof(double) * b.hist_len * b.B));
   return FAMS_OK;
 }
 
@@ -223,6 +240,8 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.blk_ptr = b.blk_ptr; a.blk_cell = b.blk_cell;
   a.F = b.ilu; a.lev_off = b.lev_off; a.lev_ptr = b.lev_ptr; a.lev_rows = b.lev_rows;
   a.q = b.q; a.x = b.x; a.r = b.r; a.dp = b.dp; a.y = b.y; a.stat = b.stat;
+  a.hist = b.hist; a.hist_len = b.hist_len;
+  a.crhs = b.rc; a.csol = b.ec;
   a.tol = tol;
   int maxnc = 0;
   for (auto& I : b.h) maxnc = std::max(maxnc, I.nc);
@@ -233,7 +252,8 @@ int run_solve(Batch& b, double tol, float* ms) {
     set_error("coarse system too large for the shared-memory coarse solve");
     return FAMS_ECAPACITY;
   }
-  FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - 1024));
   cudaEvent_t e0, e1;
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));
