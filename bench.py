@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Throughput of the F-AMS hot path on one GB300: solves/s to relative
+residual 1e-8.
+
+One step = one pass of the whole path over a batch of independent 2D
+256 x 256 instances shaped like the paper's 2D test (log10 k Gaussian field,
+std 2, correlation 16 cells; 30 random fractures of 20-120 cells; coarsening
+8 x 8, d_min = 8; the four coupling strategies and T_ratio 1e2 / 1e4 in
+rotation; R^FE, alpha = 1e-2): EDFM geometry, assembly, coarse grids, basis
+functions, truncation, R A P and its LU, ILU(0), the Table 1 iteration to
+1e-8 and the conservative flux reconstruction of every instance.
+
+value: inputs (permeability, initial guess, flux buffers) resident in GPU
+memory; e2e: the same through the C ABI with host buffers (host-to-device and
+device-to-host copies inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl fams|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rel. residual 1e-8 (served vs plain F-AMS, one GB300); p50/p99 ms"
+WORKLOAD = ("2D 256x256 (configs[1] shape): log10 k std 2 corr 16, 30 fractures L~U[20,120], "
+            "coarsening 8x8, d_min 8, 4 coupling strategies x T_ratio {1e2,1e4}, R^FE, alpha 1e-2, "
+            "ILU(0), tol 1e-8, + flux reconstruction")
+TOL = 1e-8
+
+
+def problems(batch, seed0):
+    from paper_1705_05784_gb300 import inputs
+    out = []
+    for i in range(batch):
+        p = inputs.config_2d_256(seed=seed0 + i, tratio=(1e2, 1e4)[(i // 4) % 2], basis=i % 4,
+                                 restriction=1, alpha=1e-2)
+        p.max_iter = 400
+        out.append(p)
+    return out
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def solve_bytes(s):
+    """Algorithmic HBM bytes of one Table 1 sweep of one instance in the
+    persistent solve kernel (FP64 values 8 B, int32 indices 4 B): two passes
+    over A (residual, r - A dp1), the lower and upper ILU(0) factors, P and P^T,
+    the band factors, and the vector streams."""
+    n, nnz, nnzp, nc, ldab = s["n"], s["nnz"], s["nnzp"], s["nc"], s["ldab"]
+    a_pass = 12 * nnz + 4 * (n + 1)
+    ilu = 8 * nnz + 4 * (nnz - n) // 2 + 8 * n       # L and U values, U indices, level lists
+    p_pass = 12 * nnzp + 4 * (n + 1)
+    pt_pass = 12 * nnzp + 4 * (nc + 1)
+    band = 8 * ldab * nc
+    vectors = 8 * n * 14                             # q, x (r/w x2), r (w, r x2), dp (w, r x2), y (w, r, w)
+    return 2 * a_pass + ilu + p_pass + pt_pass + band + vectors
+
+
+def sizes_of(ctx, i):
+    sz = ctx.sizes(i)
+    n = sz["n_matrix"] + sz["n_frac"]
+    kl, ku = ctx.query("BAND_KLKU", i)
+    return dict(n=n, nnz=int(ctx.query("A_ROWPTR", i)[-1]), nnzp=int(ctx.query("P_ROWPTR", i)[-1]),
+                nc=sz["n_coarse"], ldab=int(2 * kl + ku + 1), faces=sz["n_faces"], nnc=sz["n_nnc"])
+
+
+def cpu_baseline(sample):
+    """The FP64 oracle on `sample` instances of the same workload, one core."""
+    code = f"""
+import sys, time, json, numpy as np, warnings
+warnings.simplefilter('ignore')
+sys.path.insert(0, {ROOT!r})
+import bench, oracle
+from oracle import solver as osolver
+probs = bench.problems({sample}, 9000)
+t = time.perf_counter()
+for p in probs:
+    g, sysm, c, P, st = oracle.build(p)
+    x, it, rr, ok, _ = osolver.two_stage_solve(st, tol={TOL}, max_iter=p.max_iter)
+    st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
+print(json.dumps({{"seconds": time.perf_counter() - t}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {r.stderr[-300:]}"}
+    sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    return {"value": sample / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} instance(s) of the workload (setup + solve to 1e-8 + flux), "
+                      f"{sec:.1f} s single-threaded"}
+
+
+def run_reference(args, rank):
+    """--impl reference: the oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(1)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        cpu_baseline(1)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    v = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": 1},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "1 instance per step, single-threaded FP64 oracle"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=304)
+    ap.add_argument("--impl", default="fams", choices=["fams", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    # the oracle baseline runs first, in a spawned process, before any GPU work
+    cpu = None
+    if rank == 0 and not args.no_cpu and args.cpu_sample > 0:
+        cpu = cpu_baseline(args.cpu_sample)
+    from paper_1705_05784_gb300 import fams
+    probs = problems(args.batch, 1000 * (rank + 1))
+    dev = torch.device("cuda", local)
+    perm_d = [torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev) for p in probs]
+    # sizes from one setup (deterministic), device buffers for x and the fluxes
+    ctx = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+    S = [sizes_of(ctx, i) for i in range(len(probs))]
+    ctx.close()
+    x_d = [torch.zeros(s["n"], dtype=torch.float64, device=dev) for s in S]
+    f_d = [torch.zeros(s["faces"], dtype=torch.float64, device=dev) for s in S]
+    n_d = [torch.zeros(max(s["nnc"], 1), dtype=torch.float64, device=dev) for s in S]
+
+    def step_device():
+        for x in x_d:
+            x.zero_()
+        c = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+        st = c.solve_device([None] * len(probs), [x.data_ptr() for x in x_d], TOL)
+        for i in range(len(probs)):
+            c.flux_ptr(i, x_d[i].data_ptr(), f_d[i].data_ptr(), n_d[i].data_ptr())
+        c.close()
+        return st
+
+    x_h = [np.zeros(s["n"]) for s in S]
+    f_h = [np.zeros(s["faces"]) for s in S]
+    n_h = [np.zeros(max(s["nnc"], 1)) for s in S]
+
+    def step_host():
+        for x in x_h:
+            x[:] = 0.0
+        c = fams.Context(probs)
+        st = c.solve_device([None] * len(probs), [x.ctypes.data for x in x_h], TOL)
+        for i in range(len(probs)):
+            c.flux_ptr(i, x_h[i].ctypes.data, f_h[i].ctypes.data, n_h[i].ctypes.data)
+        c.close()
+        return st
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    l0 = fams.launch_count()
+    step_ms, solve_ms, stats = [], [], None
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            stats = step_device()
+            s1.record()
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            solve_ms.append(stats[0]["solve_ms"])
+        e1.record()
+        barrier()
+    launches = (fams.launch_count() - l0) // max(args.steps, 1)
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    converged = sum(1 for s in stats if s["converged"])
+    value = converged * world * args.steps / (total_ms / 1000.0)
+    # end to end with host buffers
+    barrier()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record()
+    for _ in range(args.steps):
+        step_host()
+    h1.record()
+    barrier()
+    e2e_ms = h0.elapsed_time(h1)
+    h2d = sum(8 * (len(p.perm) + s["n"] + 4 * len(p.fracs) + len(p.fracs)) for p, s in zip(probs, S))
+    d2h = sum(8 * (s["n"] + s["faces"] + s["nnc"]) for s in S)
+    # roofline of the dominant kernel: the persistent Table 1 solve kernel
+    iters = [s["iterations"] for s in stats]
+    byts = sum(solve_bytes(S[i]) * iters[i] for i in range(len(S)))
+    k_ms = statistics.median(solve_ms)
+    pk = peaks()
+    peak = pk.get("hbm_gbs", 6800.0)
+    achieved = byts / (k_ms / 1000.0) / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": len(probs), "cells_per_instance": S[0]["n"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
+                   f"({sum(s['nnz'] for s in S) * 12 / 1e9:.1f} GB of A alone per step)"},
+        "latency": {"p50_ms": statistics.median(step_ms),
+                    "p99_ms": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
+                    "note": "per batch step: every instance of the batch completes within it"},
+        "accuracy": {"converged": converged, "of": len(stats),
+                     "max_rel_residual": max(s["rel_residual"] for s in stats),
+                     "iterations_median": statistics.median(iters), "iterations_max": max(iters)},
+        "roofline": {"kernel": "k_solve (persistent Table 1 loop, one CTA per instance)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel_ms": k_ms, "algorithmic_bytes": byts,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else
+                                    "fallback 6800 GB/s"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": converged * args.steps / (e2e_ms / 1000.0), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

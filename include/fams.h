@@ -190,6 +190,10 @@ void fams_destroy(fams_ctx* ctx);
 const char* fams_strerror(int status);
 const char* fams_last_error(void);
 
+/* Number of CUDA kernels the library has launched since it was loaded (all
+   contexts, all threads); the difference across a call counts its launches. */
+long long fams_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

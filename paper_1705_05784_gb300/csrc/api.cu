@@ -2,6 +2,7 @@
 // the order of the setup phases.  Every computation of the method runs in the
 // kernels of the other translation units.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -15,9 +16,11 @@ namespace fams {
 
 namespace {
 thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
 }
 
 void set_error(const std::string& msg) { g_err = msg; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int Batch::upload_inst() {
   std::vector<int> o(8 * (B + 1));
@@ -442,5 +445,7 @@ const char* fams_strerror(int s) {
 }
 
 const char* fams_last_error(void) { return g_err.c_str(); }
+
+long long fams_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

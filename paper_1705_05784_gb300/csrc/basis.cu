@@ -456,7 +456,7 @@ int phase_basis(Batch& b) {
   pool.col[NSTAGE] = vcol;
   pool.val[NSTAGE] = vval;
   if (nct > 0)
-    k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
+    fams::note_launch(), k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
                                                   vval, pstage, poff, plen);
   int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr, *changed = nullptr;
   int *comp_of = nullptr, *pos = nullptr;
@@ -474,18 +474,18 @@ int phase_basis(Batch& b) {
   FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem));
   for (int s = 0; s < NSTAGE; ++s) {
-    k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
+    fams::note_launch(), k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
                                                   instage);
     for (int it = 0; it < 1000000; ++it) {
       int h = 0;
       FAMS_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
-      k_stage_relax<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
+      fams::note_launch(), k_stage_relax<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
                                                      b.rowptr, b.col, instage, label, changed);
       FAMS_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
       FAMS_CUDA(cudaStreamSynchronize(st));
       if (!h) break;
     }
-    k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
+    fams::note_launch(), k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
     long long ncomp = 0;
     FAMS_TRY(exclusive_scan(b, flag, rscan, nrow, &ncomp));
     if (ncomp == 0) continue;
@@ -498,12 +498,12 @@ int phase_basis(Batch& b) {
     FAMS_TRY(b.scratch((void**)&colptr, sizeof(int) * (ncomp + 1)));
     FAMS_CUDA(cudaMemsetAsync(size, 0, sizeof(int) * (ncomp + 1), st));
     FAMS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (ncomp + 1), st));
-    k_comp_size<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, rscan, comp_of, size);
+    fams::note_launch(), k_comp_size<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, rscan, comp_of, size);
     long long nmem = 0;
     FAMS_TRY(exclusive_scan(b, size, coff, ncomp, &nmem));
     FAMS_TRY(b.scratch((void**)&members, sizeof(int) * (nmem + 1)));
-    k_comp_place<<<grid_for(nrow, T), T, 0, st>>>(nrow, comp_of, coff, cursor, members);
-    k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    fams::note_launch(), k_comp_place<<<grid_for(nrow, T), T, 0, st>>>(nrow, comp_of, coff, cursor, members);
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 0, ncols, nullptr, nullptr, b.d_err);
     FAMS_CUDA(cudaGetLastError());
@@ -511,7 +511,7 @@ int phase_basis(Batch& b) {
     long long totc = 0;
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
-    k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 1, ncols, colptr, colbuf, b.d_err);
     // host plan: pool offsets and small/large split
@@ -553,7 +553,7 @@ int phase_basis(Batch& b) {
     if (!small.empty()) {
       FAMS_CUDA(cudaMemcpyAsync(clist, small.data(), sizeof(int) * small.size(),
                                 cudaMemcpyHostToDevice, st));
-      k_comp_solve<<<(int)small.size(), SOLVE_THREADS, small_smem, st>>>(
+      fams::note_launch(), k_comp_solve<<<(int)small.size(), SOLVE_THREADS, small_smem, st>>>(
           b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val, b.TD, instage, clist, coff,
           members, pos, colptr, colbuf, pool_off, pstage, poff, plen, pool, s, ocol, oval,
           nullptr, 0, b.d_err);
@@ -569,7 +569,7 @@ int phase_basis(Batch& b) {
                                 cudaMemcpyHostToDevice, st));
       for (size_t o = 0; o < large.size(); o += per) {
         int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
-        k_comp_solve<<<cnt, 1024, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val,
+        fams::note_launch(), k_comp_solve<<<cnt, 1024, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val,
                                            b.TD, instage, lst + o, coff, members, pos, colptr,
                                            colbuf, pool_off, pstage, poff, plen, pool, s, ocol,
                                            oval, work, max_big, b.d_err);
@@ -593,18 +593,18 @@ int phase_basis(Batch& b) {
         return FAMS_EINVAL;
       }
   }
-  k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
+  fams::note_launch(), k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
                                              pool, cnt);
   long long pnnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.p_ptr, nrow, &pnnz));
   FAMS_TRY(b.alloc((void**)&b.p_col, sizeof(int) * (pnnz + 1)));
   FAMS_TRY(b.alloc((void**)&b.p_val, sizeof(double) * (pnnz + 1)));
-  k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
+  fams::note_launch(), k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
                                             pool, b.p_ptr, b.p_col, b.p_val);
   // P^T with global coarse rows (restriction R^FE and the coarse operator)
   int* gcol = nullptr;
   FAMS_TRY(b.scratch((void**)&gcol, sizeof(int) * (pnnz + 1)));
-  k_p_global_cols<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.p_ptr,
+  fams::note_launch(), k_p_global_cols<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.p_ptr,
                                                    b.p_col, gcol);
   FAMS_TRY(transpose(b, b.p_ptr, gcol, b.p_val, (int)nrow, (int)nct, pnnz, &b.pt_ptr, &b.pt_col,
                      &b.pt_val, true));

@@ -311,24 +311,24 @@ int phase_coarse(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.rank, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.alloc((void**)&b.primal, sizeof(int) * (nrow + 1)));
   if (nrow > 0)
-    k_matrix_coarse<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
+    fams::note_launch(), k_matrix_coarse<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
                                                      b.primal);
   // strike graph
   int *deg = nullptr, *sptr = nullptr, *cursor = nullptr, *adj = nullptr;
   FAMS_TRY(b.scratch((void**)&deg, sizeof(int) * (ns + 1)));
   FAMS_TRY(b.scratch((void**)&sptr, sizeof(int) * (ns + 1)));
   FAMS_TRY(b.scratch((void**)&cursor, sizeof(int) * (ns + 1)));
-  if (ns > 0) k_strike_deg<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, deg);
+  if (ns > 0) fams::note_launch(), k_strike_deg<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, deg);
   if (np > 0)
-    k_strike_inter_deg<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
+    fams::note_launch(), k_strike_inter_deg<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
                                                       b.inter_sa, b.inter_sb, b.f_sfirst, deg);
   long long nadj = 0;
   FAMS_TRY(exclusive_scan(b, deg, sptr, ns, &nadj));
   FAMS_TRY(b.scratch((void**)&adj, sizeof(int) * (nadj + 1)));
   if (ns > 0)
-    k_strike_fill<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, sptr, cursor, adj);
+    fams::note_launch(), k_strike_fill<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, sptr, cursor, adj);
   if (np > 0)
-    k_strike_inter_fill<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
+    fams::note_launch(), k_strike_inter_fill<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
                                                        b.inter_sa, b.inter_sb, b.f_sfirst, sptr,
                                                        cursor, adj);
   FAMS_TRY(sort_segments(b, sptr, (int)ns, adj, nullptr, true));
@@ -340,16 +340,16 @@ int phase_coarse(Batch& b) {
   FAMS_TRY(b.scratch((void**)&changed, sizeof(int)));
   long long nnet = 0;
   if (ns > 0) {
-    k_label_init<<<grid_for(ns, T), T, 0, st>>>(ns, lab);
+    fams::note_launch(), k_label_init<<<grid_for(ns, T), T, 0, st>>>(ns, lab);
     for (int it = 0; it < 100000; ++it) {
       int h = 0;
       FAMS_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
-      k_label_relax<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, adj, lab, changed);
+      fams::note_launch(), k_label_relax<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, adj, lab, changed);
       FAMS_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
       FAMS_CUDA(cudaStreamSynchronize(st));
       if (!h) break;
     }
-    k_is_root<<<grid_for(ns, T), T, 0, st>>>(ns, lab, flag);
+    fams::note_launch(), k_is_root<<<grid_for(ns, T), T, 0, st>>>(ns, lab, flag);
     FAMS_TRY(exclusive_scan(b, flag, rscan, ns, &nnet));
   }
   b.tot_net = nnet;
@@ -387,9 +387,9 @@ int phase_coarse(Batch& b) {
     FAMS_CUDA(cudaMemsetAsync(b.net_nk, 0x7f, sizeof(int) * (nnet + 1), st));
     FAMS_CUDA(cudaMemsetAsync(k0max, 0, sizeof(int) * (nnet + 1), st));
     FAMS_CUDA(cudaMemsetAsync(nkmax, 0, sizeof(int) * (nnet + 1), st));
-    k_net_of<<<grid_for(ns, T), T, 0, st>>>(ns, lab, rscan, b.s_net, netcnt, nroot);
-    k_net_start<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, b.s_net, nstart);
-    k_net_layers<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_k0, b.f_nk, nfr, ns, b.s_net,
+    fams::note_launch(), k_net_of<<<grid_for(ns, T), T, 0, st>>>(ns, lab, rscan, b.s_net, netcnt, nroot);
+    fams::note_launch(), k_net_start<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, b.s_net, nstart);
+    fams::note_launch(), k_net_layers<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_k0, b.f_nk, nfr, ns, b.s_net,
                                                 b.net_k0, k0max, b.net_nk, nkmax);
     FAMS_CUDA(cudaMemcpyAsync(h_k0min.data(), b.net_k0, sizeof(int) * nnet, cudaMemcpyDeviceToHost, st));
     FAMS_CUDA(cudaMemcpyAsync(h_k0max.data(), k0max, sizeof(int) * nnet, cudaMemcpyDeviceToHost, st));
@@ -427,7 +427,7 @@ int phase_coarse(Batch& b) {
     FAMS_CUDA(cudaMemsetAsync(level, 0x7f, sizeof(int) * (ns + 1), st));
     FAMS_CUDA(cudaMemsetAsync(inqv, 0, sizeof(int) * (ns + 1), st));
     FAMS_CUDA(cudaMemsetAsync(b.s_prim, 0xff, sizeof(int) * (ns + 1), st));
-    k_bfs<<<grid_for(nnet, 32), 32, 0, st>>>(nnet, netoff, nstart, nroot, ndmin, sptr, adj, level,
+    fams::note_launch(), k_bfs<<<grid_for(nnet, 32), 32, 0, st>>>(nnet, netoff, nstart, nroot, ndmin, sptr, adj, level,
                                              b.s_prim, inqv, qv, q1, q2, vlist, b.net_nv);
     FAMS_CUDA(cudaGetLastError());
     FAMS_CUDA(cudaMemcpyAsync(h_nv.data(), b.net_nv, sizeof(int) * nnet, cudaMemcpyDeviceToHost, st));
@@ -472,14 +472,14 @@ int phase_coarse(Batch& b) {
   FAMS_TRY(b.upload_inst());
   FAMS_TRY(b.alloc((void**)&b.node_cell, sizeof(int) * (nc_tot + 1)));
   if (nc_tot > 0)
-    k_matrix_nodes<<<grid_for(nc_tot, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nc_tot, b.node_cell);
+    fams::note_launch(), k_matrix_nodes<<<grid_for(nc_tot, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nc_tot, b.node_cell);
   if (nfc > 0)
-    k_frac_rank<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_sfirst,
+    fams::note_launch(), k_frac_rank<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_sfirst,
                                                 b.f_ns, b.f_k0, nfr, nfc, b.s_net, b.s_prim,
                                                 b.s_vert, b.net_nv, b.net_k0, b.net_nk, b.net_base,
                                                 b.rank, b.primal);
   if (nnet > 0)
-    k_frac_nodes<<<grid_for(nnet, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_sfirst,
+    fams::note_launch(), k_frac_nodes<<<grid_for(nnet, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_sfirst,
                                                   b.f_ns, b.f_k0, nfr, nnet, netoff, ninst,
                                                   b.net_nv, b.net_k0, b.net_nk, b.net_base, vlist,
                                                   b.node_cell);
@@ -488,7 +488,7 @@ int phase_coarse(Batch& b) {
   int *gprim = nullptr, *iota = nullptr;
   FAMS_TRY(b.scratch((void**)&gprim, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&iota, sizeof(int) * (nrow + 2)));
-  k_primal_global<<<grid_for(nrow + 1, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.primal,
+  fams::note_launch(), k_primal_global<<<grid_for(nrow + 1, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.primal,
                                                        gprim, iota);
   FAMS_TRY(transpose(b, iota, gprim, nullptr, (int)nrow, (int)nc_tot, nrow, &b.blk_ptr,
                      &b.blk_cell, nullptr, true));

@@ -265,7 +265,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
                             cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (tot + 1), st));
   if (b.tot_nnz > 0)
-    k_rap<<<grid_for(b.tot_nnz, T), T, 0, st>>>(b.d_inst, B, b.off_row, b.tot_nnz, b.rowptr, b.col,
+    fams::note_launch(), k_rap<<<grid_for(b.tot_nnz, T), T, 0, st>>>(b.d_inst, B, b.off_row, b.tot_nnz, b.rowptr, b.col,
                                                 b.val, b.tot_row, b.primal, b.p_ptr, b.p_col,
                                                 b.p_val, cs, mode);
   // pattern, RCM, band sizes
@@ -274,20 +274,20 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_TRY(b.scratch((void**)&ptr, sizeof(int) * (nct + 1)));
   FAMS_TRY(b.scratch((void**)&vis, sizeof(int) * (nct + 1)));
   FAMS_TRY(b.scratch((void**)&que, sizeof(int) * (nct + 1)));
-  k_ac_count<<<grid_for(nct * 32, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, cnt);
+  fams::note_launch(), k_ac_count<<<grid_for(nct * 32, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, cnt);
   long long nnzc = 0;
   FAMS_TRY(exclusive_scan(b, cnt, ptr, nct, &nnzc));
   FAMS_TRY(b.scratch((void**)&cols, sizeof(int) * (nnzc + 1)));
-  k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
+  fams::note_launch(), k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
   int *dkl = nullptr, *dku = nullptr, *ip = nullptr;
   FAMS_TRY(b.scratch((void**)&dkl, sizeof(int) * B));
   FAMS_TRY(b.scratch((void**)&dku, sizeof(int) * B));
   FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
   FAMS_CUDA(cudaMemsetAsync(dkl, 0, sizeof(int) * B, st));
   FAMS_CUDA(cudaMemsetAsync(dku, 0, sizeof(int) * B, st));
-  k_rcm<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, dkl, dku);
-  k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
-  k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
+  fams::note_launch(), k_rcm<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, dkl, dku);
+  fams::note_launch(), k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+  fams::note_launch(), k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
   FAMS_CUDA(cudaGetLastError());
   ch.kl.assign(B, 0);
   ch.ku.assign(B, 0);
@@ -306,8 +306,8 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
                             cudaMemcpyHostToDevice, st));
-  k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
-  k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
+  fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+  fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
   FAMS_CUDA(cudaGetLastError());
   return b.check_err("coarse LU");
 }

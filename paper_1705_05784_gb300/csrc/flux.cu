@@ -285,7 +285,7 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
   max_smem -= 1024;  // static shared memory of the kernels
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_local, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-  k_flux_stage<<<1, 512, smem, st>>>(b.d_inst, ii, *cs, b.rowptr, b.col, b.val, b.blk_ptr,
+  fams::note_launch(), k_flux_stage<<<1, 512, smem, st>>>(b.d_inst, ii, *cs, b.rowptr, b.col, b.val, b.blk_ptr,
                                      b.blk_cell, b.p_ptr, b.p_col, b.p_val, b.q, x_dev, res, pp);
   FAMS_CUDA(cudaGetLastError());
   // local problems: split by size (shared memory or a bounded global workspace)
@@ -308,7 +308,7 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
   int status = FAMS_OK;
   if (!small.empty()) {
     cudaMemcpyAsync(lst, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice, st);
-    k_flux_local<<<(int)small.size(), 256, small_smem, st>>>(
+    fams::note_launch(), k_flux_local<<<(int)small.size(), 256, small_smem, st>>>(
         b.d_inst, ii, lst, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD, b.qD, b.q,
         b.primal, b.node_cell, pp, pt, nullptr, 0, b.d_err);
   }
@@ -323,7 +323,7 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
     cudaMemcpyAsync(l2, large.data(), sizeof(int) * large.size(), cudaMemcpyHostToDevice, st);
     for (size_t o = 0; o < large.size(); o += per) {
       int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
-      k_flux_local<<<cnt, 256, 0, st>>>(b.d_inst, ii, l2 + o, b.blk_ptr, b.blk_cell, b.rowptr,
+      fams::note_launch(), k_flux_local<<<cnt, 256, 0, st>>>(b.d_inst, ii, l2 + o, b.blk_ptr, b.blk_cell, b.rowptr,
                                         b.col, b.val, b.TD, b.qD, b.q, b.primal, b.node_cell, pp,
                                         pt, work, big, b.d_err);
     }
@@ -334,11 +334,11 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
                      (long long)I.nx * (I.ny + 1) * (I.dim == 3 ? I.nz : 1) +
                      (I.dim == 3 ? (long long)I.nx * I.ny * (I.nz + 1) : 0);
   if (status == FAMS_OK) {
-    k_flux_faces<<<grid_for(nfaces, 256), 256, 0, st>>>(b.d_inst, ii, b.perm, b.primal, pp, pt,
+    fams::note_launch(), k_flux_faces<<<grid_for(nfaces, 256), 256, 0, st>>>(b.d_inst, ii, b.perm, b.primal, pp, pt,
                                                         face);
     long long nn = (long long)I.nnc + I.nff;
     if (nn > 0)
-      k_flux_nnc<<<grid_for(nn, 256), 256, 0, st>>>(b.d_inst, ii, b.nnc_row_m, b.nnc_row_f,
+      fams::note_launch(), k_flux_nnc<<<grid_for(nn, 256), 256, 0, st>>>(b.d_inst, ii, b.nnc_row_m, b.nnc_row_f,
                                                     b.nnc_T, b.ff_a, b.ff_b, b.ff_T, b.primal, pp,
                                                     pt, nnc_out);
     e = cudaGetLastError();

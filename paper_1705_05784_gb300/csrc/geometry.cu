@@ -427,7 +427,7 @@ int phase_geometry(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.f_cfirst, sizeof(int) * (nfr + 1)));
   FAMS_TRY(b.alloc((void**)&b.f_sfirst, sizeof(int) * (nfr + 1)));
   if (nfr > 0)
-    k_frac_clip<<<grid_for(nfr, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, nfr, b.fracs, b.seg,
+    fams::note_launch(), k_frac_clip<<<grid_for(nfr, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, nfr, b.fracs, b.seg,
                                                 b.f_ns, b.f_k0, b.f_nk);
   FAMS_CUDA(cudaGetLastError());
   // per-fracture counts to the host: fracture-cell and strike offsets
@@ -483,10 +483,10 @@ int phase_geometry(Batch& b) {
   FAMS_TRY(b.scratch((void**)&b.s_ovlen, sizeof(double) * MAX_OVERLAP * (nsl + 1)));
   FAMS_TRY(b.scratch((void**)&b.s_ovdist, sizeof(double) * MAX_OVERLAP * (nsl + 1)));
   if (nsl > 0) {
-    k_strike_overlap<<<grid_for(nsl, 128), 128, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_sfirst, nfr,
+    fams::note_launch(), k_strike_overlap<<<grid_for(nsl, 128), 128, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_sfirst, nfr,
                                                          nsl, b.seg, b.f_ns, b.s_ovcnt, b.s_ovcol,
                                                          b.s_ovlen, b.d_err);
-    k_mean_dist<<<grid_for(nsl * MAX_OVERLAP, 128), 128, 0, st>>>(
+    fams::note_launch(), k_mean_dist<<<grid_for(nsl * MAX_OVERLAP, 128), 128, 0, st>>>(
         b.d_inst, b.B, b.off_fr, b.f_sfirst, nfr, nsl, b.seg, b.s_ovcnt, b.s_ovcol, b.s_ovdist);
   }
   FAMS_CUDA(cudaGetLastError());
@@ -499,7 +499,7 @@ int phase_geometry(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.nnc_first, sizeof(int) * (nfc + 1)));
   int* nnc_first = b.nnc_first;
   if (nfc > 0)
-    k_cell_nnc_count<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fc, b.off_fr,
+    fams::note_launch(), k_cell_nnc_count<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fc, b.off_fr,
                                                      b.f_cfirst, b.f_sfirst, b.f_ns, nfr, nfc,
                                                      b.s_ovcnt, cnt);
   long long nnc = 0;
@@ -511,7 +511,7 @@ int phase_geometry(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.nnc_area, sizeof(double) * (nnc + 1)));
   FAMS_TRY(b.alloc((void**)&b.nnc_dist, sizeof(double) * (nnc + 1)));
   if (nfc > 0)
-    k_cell_nnc_fill<<<grid_for(nfc, T), T, 0, st>>>(
+    fams::note_launch(), k_cell_nnc_fill<<<grid_for(nfc, T), T, 0, st>>>(
         b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_sfirst, b.f_ns, b.f_k0, nfr, nfc, b.s_ovcnt,
         b.s_ovcol, b.s_ovlen, b.s_ovdist, b.perm, nnc_first, b.nnc_row_f, b.nnc_row_m, b.nnc_T,
         b.nnc_area, b.nnc_dist);
@@ -538,7 +538,7 @@ int phase_geometry(Batch& b) {
   int* nlink = nullptr;
   FAMS_TRY(b.scratch((void**)&nlink, sizeof(int) * (np + 1)));
   if (np > 0)
-    k_intersect<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.seg, b.f_ns,
+    fams::note_launch(), k_intersect<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.seg, b.f_ns,
                                                b.f_k0, b.f_nk, b.kf, b.inter_hit, b.inter_sa,
                                                b.inter_sb, b.inter_T, nlink);
   // fracture-fracture links keyed by the lower cell
@@ -549,10 +549,10 @@ int phase_geometry(Batch& b) {
   int* ff_first = b.ff_first;
   FAMS_TRY(b.scratch((void**)&cursor, sizeof(int) * (nfc + 1)));
   if (nfc > 0)
-    k_ff_count<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_ns,
+    fams::note_launch(), k_ff_count<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_ns,
                                                b.f_nk, nfr, nfc, ffcnt);
   if (np > 0)
-    k_ff_inter_count<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
+    fams::note_launch(), k_ff_inter_count<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
                                                     b.inter_sa, b.f_cfirst, b.f_ns, b.f_k0,
                                                     b.f_nk, ffcnt);
   long long nff = 0;
@@ -562,15 +562,15 @@ int phase_geometry(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.ff_b, sizeof(int) * (nff + 1)));
   FAMS_TRY(b.alloc((void**)&b.ff_T, sizeof(double) * (nff + 1)));
   if (nfc > 0) {
-    k_ff_fill_fixed<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_ns,
+    fams::note_launch(), k_ff_fill_fixed<<<grid_for(nfc, T), T, 0, st>>>(b.d_inst, b.B, b.off_fr, b.f_cfirst, b.f_ns,
                                                     b.f_nk, b.seg, b.kf, nfr, nfc, ff_first,
                                                     cursor, b.ff_a, b.ff_b, b.ff_T);
     if (np > 0)
-      k_ff_fill_inter<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
+      fams::note_launch(), k_ff_fill_inter<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
                                                      b.inter_sa, b.inter_sb, b.inter_T,
                                                      b.f_cfirst, b.f_ns, b.f_k0, b.f_nk,
                                                      ff_first, cursor, b.ff_a, b.ff_b, b.ff_T);
-    k_ff_sort_cell<<<grid_for(nfc, T), T, 0, st>>>(ff_first, nfc, b.ff_b, b.ff_T);
+    fams::note_launch(), k_ff_sort_cell<<<grid_for(nfc, T), T, 0, st>>>(ff_first, nfc, b.ff_b, b.ff_T);
   }
   FAMS_CUDA(cudaGetLastError());
   {

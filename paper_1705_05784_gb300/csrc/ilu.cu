@@ -103,8 +103,8 @@ int phase_ilu(Batch& b) {
   int *level = nullptr, *dnlev = nullptr;
   FAMS_TRY(b.scratch((void**)&level, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&dnlev, sizeof(int) * B));
-  k_lev_matrix<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level);
-  k_lev_frac<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, level, dnlev);
+  fams::note_launch(), k_lev_matrix<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level);
+  fams::note_launch(), k_lev_frac<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, level, dnlev);
   std::vector<int> nlev(B);
   FAMS_CUDA(cudaMemcpyAsync(nlev.data(), dnlev, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   FAMS_CUDA(cudaStreamSynchronize(st));
@@ -124,15 +124,15 @@ int phase_ilu(Batch& b) {
   FAMS_CUDA(cudaMemcpyAsync(b.lev_off, loff.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (tl + 1), st));
   FAMS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (tl + 1), st));
-  k_lev_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off, cnt);
+  fams::note_launch(), k_lev_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off, cnt);
   FAMS_TRY(exclusive_scan(b, cnt, b.lev_ptr, tl, nullptr));
-  k_lev_place<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off,
+  fams::note_launch(), k_lev_place<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level, b.lev_off,
                                                b.lev_ptr, cursor, b.lev_rows);
   // rows of a level in ascending order (independent rows: only for locality)
   FAMS_TRY(sort_segments(b, b.lev_ptr, tl, b.lev_rows, nullptr, false));
   FAMS_TRY(b.alloc((void**)&b.ilu, sizeof(double) * (b.tot_nnz + 1)));
   FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
-  k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, b.lev_off, b.lev_ptr,
+  fams::note_launch(), k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, b.lev_off, b.lev_ptr,
                                   b.lev_rows, b.ilu, b.d_err);
   FAMS_CUDA(cudaGetLastError());
   return b.check_err("ILU(0)");

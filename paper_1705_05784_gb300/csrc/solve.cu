@@ -224,7 +224,7 @@ int phase_alloc_work(Batch& b) {
 
 int make_q(Batch& b, const double* rhs_dev) {
   long long n = b.tot_row;
-  k_make_q<<<grid_for(n, 256), 256, 0, b.stream>>>(n, rhs_dev, b.qD, b.q);
+  fams::note_launch(), k_make_q<<<grid_for(n, 256), 256, 0, b.stream>>>(n, rhs_dev, b.qD, b.q);
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }
@@ -258,7 +258,7 @@ int run_solve(Batch& b, double tol, float* ms) {
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));
   FAMS_CUDA(cudaEventRecord(e0, b.stream));
-  k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
+  fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
   FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaEventRecord(e1, b.stream));
   FAMS_CUDA(cudaEventSynchronize(e1));

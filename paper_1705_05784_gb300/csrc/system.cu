@@ -150,7 +150,7 @@ int phase_system(Batch& b) {
   int* mcell = nullptr;
   FAMS_TRY(b.scratch((void**)&mcell, sizeof(int) * (nnc + 1)));
   if (nnc > 0)
-    k_nnc_mcell<<<grid_for(nnc, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nnc, b.nnc_row_m,
+    fams::note_launch(), k_nnc_mcell<<<grid_for(nnc, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nnc, b.nnc_row_m,
                                                 mcell);
   int *nnc_t_ptr = nullptr, *nnc_t_fc = nullptr;
   double* nnc_t_T = nullptr;
@@ -160,7 +160,7 @@ int phase_system(Batch& b) {
   int* bcell = nullptr;
   FAMS_TRY(b.scratch((void**)&bcell, sizeof(int) * (nff + 1)));
   if (nff > 0)
-    k_ff_bcell<<<grid_for(nff, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nff, b.ff_b, bcell);
+    fams::note_launch(), k_ff_bcell<<<grid_for(nff, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nff, b.ff_b, bcell);
   int *ffr_ptr = nullptr, *ffr_a = nullptr;
   double* ffr_T = nullptr;
   FAMS_TRY(transpose(b, b.ff_first, bcell, b.ff_T, (int)nfc, (int)nfc, nff, &ffr_ptr, &ffr_a,
@@ -170,7 +170,7 @@ int phase_system(Batch& b) {
   FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.alloc((void**)&b.rowptr, sizeof(int) * (nrow + 1)));
   if (nrow > 0)
-    k_row_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, nnc_t_ptr,
+    fams::note_launch(), k_row_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, nnc_t_ptr,
                                                  b.nnc_first, ffr_ptr, b.ff_first, cnt);
   long long nnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.rowptr, nrow, &nnz));
@@ -181,7 +181,7 @@ int phase_system(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.TD, sizeof(double) * (nrow + 1)));
   FAMS_TRY(b.alloc((void**)&b.qD, sizeof(double) * (nrow + 1)));
   if (nrow > 0)
-    k_row_fill<<<grid_for(nrow, T), T, 0, st>>>(
+    fams::note_launch(), k_row_fill<<<grid_for(nrow, T), T, 0, st>>>(
         b.d_inst, b.B, b.off_row, nrow, b.perm, nnc_t_ptr, nnc_t_fc, nnc_t_T, b.nnc_first,
         b.nnc_row_m, b.nnc_T, ffr_ptr, ffr_a, ffr_T, b.ff_first, b.ff_b, b.ff_T, b.rowptr, b.col,
         b.val, b.diag, b.TD, b.qD);

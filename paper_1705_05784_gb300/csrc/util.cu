@@ -76,9 +76,9 @@ int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* to
   int nb = grid_for(n, SCAN_BLOCK);
   long long* sums = nullptr;
   FAMS_TRY(b.scratch((void**)&sums, sizeof(long long) * (nb + 1)));
-  k_scan_blocks<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums);
-  k_scan_sums<<<1, 32, 0, b.stream>>>(sums, nb);
-  k_scan_apply<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums, out);
+  fams::note_launch(), k_scan_blocks<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums);
+  fams::note_launch(), k_scan_sums<<<1, 32, 0, b.stream>>>(sums, nb);
+  fams::note_launch(), k_scan_apply<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums, out);
   FAMS_CUDA(cudaGetLastError());
   long long tot = 0;
   FAMS_CUDA(cudaMemcpyAsync(&tot, sums + nb, sizeof(long long), cudaMemcpyDeviceToHost, b.stream));
@@ -160,7 +160,7 @@ __global__ void k_seg_sort(const int* ptr, int nseg, int* key, double* val, int*
 
 int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict) {
   if (nseg <= 0) return FAMS_OK;
-  k_seg_sort<<<nseg, 256, 0, b.stream>>>(ptr, nseg, key, val, b.d_err, strict ? 1 : 0);
+  fams::note_launch(), k_seg_sort<<<nseg, 256, 0, b.stream>>>(ptr, nseg, key, val, b.d_err, strict ? 1 : 0);
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }
@@ -180,12 +180,12 @@ int transpose(Batch& b, const int* rowptr, const int* col, const double* val, in
   FAMS_TRY(alloc((void**)tcol, sizeof(int) * (nnz + 1)));
   if (tval) FAMS_TRY(alloc((void**)tval, sizeof(double) * (nnz + 1)));
   if (nnz > 0) {
-    k_count_cols<<<grid_for(nnz, 256), 256, 0, b.stream>>>(col, nnz, cnt);
-    k_row_of<<<grid_for(nrows, 256), 256, 0, b.stream>>>(rowptr, nrows, rowof);
+    fams::note_launch(), k_count_cols<<<grid_for(nnz, 256), 256, 0, b.stream>>>(col, nnz, cnt);
+    fams::note_launch(), k_row_of<<<grid_for(nrows, 256), 256, 0, b.stream>>>(rowptr, nrows, rowof);
   }
   FAMS_TRY(exclusive_scan(b, cnt, *tptr, ncols, nullptr));
   if (nnz > 0) {
-    k_place<<<grid_for(nnz, 256), 256, 0, b.stream>>>(rowof, col, val, nnz, *tptr, cursor, *tcol,
+    fams::note_launch(), k_place<<<grid_for(nnz, 256), 256, 0, b.stream>>>(rowof, col, val, nnz, *tptr, cursor, *tcol,
                                                       tval ? *tval : nullptr);
     FAMS_TRY(sort_segments(b, *tptr, ncols, *tcol, tval ? *tval : nullptr, true));
   }

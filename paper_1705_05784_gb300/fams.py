@@ -78,6 +78,8 @@ def _load():
     lib.fams_strerror.restype = C.c_char_p
     lib.fams_last_error.argtypes = []
     lib.fams_last_error.restype = C.c_char_p
+    lib.fams_launch_count.argtypes = []
+    lib.fams_launch_count.restype = C.c_longlong
     return lib
 
 
@@ -112,16 +114,29 @@ def _args(prob):
     return g, perm, f, o, (xy, kf)
 
 
-class Context:
-    """One libfams context (a batch of one or more instances)."""
+def launch_count():
+    """Kernels launched by the library since it was loaded."""
+    return int(lib.fams_launch_count())
 
-    def __init__(self, problems):
+
+class Context:
+    """One libfams context (a batch of one or more instances).
+
+    device_perm: optional list of device pointers (one per instance) holding
+    the permeability arrays already resident in GPU memory; the library then
+    copies device to device."""
+
+    def __init__(self, problems, device_perm=None):
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
         n = len(problems)
         parts = [_args(p) for p in problems]
         grids = (fams_grid * n)(*[p[0] for p in parts])
-        perms = (C.POINTER(C.c_double) * n)(*[_dptr(p[1]) for p in parts])
+        if device_perm is not None:
+            perms = (C.POINTER(C.c_double) * n)(
+                *[C.cast(C.c_void_p(int(d)), C.POINTER(C.c_double)) for d in device_perm])
+        else:
+            perms = (C.POINTER(C.c_double) * n)(*[_dptr(p[1]) for p in parts])
         fracs = (fams_fracs * n)(*[p[2] for p in parts])
         opts = (fams_opts * n)(*[p[3] for p in parts])
         self._keep = parts
@@ -197,6 +212,11 @@ class Context:
         return [dict(iterations=st[i].iterations, rel_residual=st[i].rel_residual,
                      converged=bool(st[i].converged), solve_ms=st[i].solve_ms)
                 for i in range(n)]
+
+    def flux_ptr(self, inst, x_ptr, face_ptr, nnc_ptr):
+        """fams_flux on caller-owned buffers given as raw pointers (host or device)."""
+        _check(lib.fams_flux(self.h, inst, C.c_void_p(int(x_ptr)), C.c_void_p(int(face_ptr)),
+                             C.c_void_p(int(nnc_ptr))))
 
     def flux(self, x, inst=0):
         s = self.sizes(inst)
