@@ -181,7 +181,9 @@ enum {
   FAMS_Q_LAST_DP1 = 26,    /* double multiscale correction of the last sweep (Table 1 step 5) */
   FAMS_Q_LAST_DP2 = 27,    /* double smoother correction of the last sweep (Table 1 step 7) */
   FAMS_Q_LAST_RC = 28,     /* double coarse right-hand side R r of the last sweep */
-  FAMS_Q_LAST_EC = 29      /* double coarse solution (R A P)^-1 R r of the last sweep */
+  FAMS_Q_LAST_EC = 29,     /* double coarse solution (R A P)^-1 R r of the last sweep */
+  FAMS_Q_STAGE_CYCLES = 30 /* double SM cycles of the last solve per phase: residual, coarse
+                              (restriction + band solve), prolongation + r1, L sweep, U sweep */
 };
 int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap);
 

@@ -43,13 +43,15 @@ int Batch::upload_inst() {
 }
 
 int Batch::check_err(const char* phase) {
-  int e = 0;
-  FAMS_CUDA(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  int w[3] = {0, 0, 0};
+  FAMS_CUDA(cudaMemcpyAsync(w, d_err, sizeof(int) * 3, cudaMemcpyDeviceToHost, stream));
   FAMS_CUDA(cudaStreamSynchronize(stream));
   FAMS_CUDA(cudaGetLastError());
+  int e = w[0];
   if (e == DERR_NONE) return FAMS_OK;
-  FAMS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
+  FAMS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int) * 3, stream));
   std::string p(phase);
+  if (w[1] > 0) p += " (instance " + std::to_string(w[1] - 1) + ", item " + std::to_string(w[2]) + ")";
   switch (e) {
     case DERR_BREAKDOWN: set_error(p + ": zero or non-finite pivot"); return FAMS_EBREAKDOWN;
     case DERR_CAPACITY: set_error(p + ": a local problem exceeds a compiled-in size limit"); return FAMS_ECAPACITY;
@@ -124,8 +126,8 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
   b.off_nc = b.off_m + 6 * (n + 1);
   b.off_net = b.off_m + 7 * (n + 1);
   FAMS_TRY(b.alloc((void**)&b.d_inst, sizeof(Inst) * n));
-  FAMS_TRY(b.alloc((void**)&b.d_err, sizeof(int)));
-  FAMS_CUDA(cudaMemsetAsync(b.d_err, 0, sizeof(int), b.stream));
+  FAMS_TRY(b.alloc((void**)&b.d_err, sizeof(int) * 3));
+  FAMS_CUDA(cudaMemsetAsync(b.d_err, 0, sizeof(int) * 3, b.stream));
   // inputs (host or device pointers: unified addressing picks the direction)
   FAMS_TRY(b.alloc((void**)&b.perm, sizeof(double) * (m + 1)));
   FAMS_TRY(b.alloc((void**)&b.fracs, sizeof(double) * 6 * (fr + 1)));
@@ -277,22 +279,27 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
   float ms = 0.f;
   FAMS_TRY(run_solve(b, tol, &ms));
   std::vector<double> stat;
-  FAMS_TRY(fetch(b, b.stat, 4LL * b.B, stat));
+  FAMS_TRY(fetch(b, b.stat, (long long)STAT_W * b.B, stat));
   int status = FAMS_OK;
   for (int i = 0; i < b.B; ++i) {
     const Inst& I = b.h[i];
     FAMS_CUDA(cudaMemcpyAsync(x[i], b.x + I.row_off, sizeof(double) * I.n, cudaMemcpyDefault,
                               b.stream));
     if (st) {
-      st[i].iterations = (int)stat[4 * i];
-      st[i].rel_residual = stat[4 * i + 1];
-      st[i].converged = stat[4 * i + 2] > 0.5;
+      st[i].iterations = (int)stat[STAT_W * i];
+      st[i].rel_residual = stat[STAT_W * i + 1];
+      st[i].converged = stat[STAT_W * i + 2] > 0.5;
       st[i].solve_ms = ms;
     }
-    if (!std::isfinite(stat[4 * i + 1])) {
+    if (stat[STAT_W * i + 9] > 0.5) {
+      if (status != FAMS_EBREAKDOWN)
+        set_error("instance " + std::to_string(i) + ": numerically singular coarse system "
+                  "(zero pivot at LU step " + std::to_string(b.csh[0].bad[i] - 1) + ")");
+      status = FAMS_EBREAKDOWN;
+    } else if (!std::isfinite(stat[STAT_W * i + 1])) {
       set_error("the iteration produced a non-finite residual");
       status = FAMS_EBREAKDOWN;
-    } else if (stat[4 * i + 2] < 0.5 && status == FAMS_OK) {
+    } else if (stat[STAT_W * i + 2] < 0.5 && status == FAMS_OK) {
       set_error("max_iter reached before the tolerance");
       status = FAMS_ENOCONV;
     }
@@ -403,13 +410,14 @@ int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap
       FAMS_TRY(dbls(b.cs[0].band + b.csh[0].band_off[inst],
                     (long long)(2 * b.csh[0].kl[inst] + b.csh[0].ku[inst] + 1) * I.nc));
       break;
+    case FAMS_Q_STAGE_CYCLES: FAMS_TRY(dbls(b.stat + STAT_W * inst + 4, 5)); break;
     case FAMS_Q_LAST_DP1: FAMS_TRY(dbls(b.dp + I.row_off, I.n)); break;
     case FAMS_Q_LAST_DP2: FAMS_TRY(dbls(b.y + I.row_off, I.n)); break;
     case FAMS_Q_LAST_RC: FAMS_TRY(dbls(b.rc + I.nc_off, I.nc)); break;
     case FAMS_Q_LAST_EC: FAMS_TRY(dbls(b.ec + I.nc_off, I.nc)); break;
     case FAMS_Q_HISTORY: {
       std::vector<double> st;
-      FAMS_TRY(fetch(b, b.stat + 4 * inst, 4, st));
+      FAMS_TRY(fetch(b, b.stat + STAT_W * inst, STAT_W, st));
       FAMS_TRY(dbls(b.hist + (long long)inst * (b.hist_len), (long long)st[0] + 1));
       break;
     }

@@ -20,11 +20,13 @@ struct CoarseSys {
   int* ku = nullptr;
   int* ipiv = nullptr;          // pivot rows (band positions)
   int* perm = nullptr;          // band position -> coarse index
+  int* bad = nullptr;           // per instance: 0, or 1 + the LU step with a zero pivot
 };
 
 struct CoarseHost {
   std::vector<long long> ac_off, band_off;
   std::vector<int> kl, ku;
+  std::vector<int> bad;         // host copy of CoarseSys::bad
 };
 
 struct Batch {
@@ -116,6 +118,18 @@ struct Batch {
   int* lev_ptr = nullptr;      // per instance: nlev+1 offsets (Inst-local slice)
   int* lev_rows = nullptr;     // global rows grouped by level
   int* lev_off = nullptr;      // per instance offset into lev_ptr
+  // the factors again in level order (position t of lev_rows), structure of
+  // arrays, PK entries of each triangle inline, for the sweeps
+  int* pk_pos = nullptr;       // row -> position t
+  int* pk_nl = nullptr;        // L entries of the row
+  int* pk_lp = nullptr;        // first L entry in the CSR (for entries beyond PK)
+  int* pk_lc = nullptr;        // PK x tot_row columns
+  double* pk_lv = nullptr;     // PK x tot_row values
+  int* pk_nu = nullptr;        // U entries right of the diagonal
+  int* pk_uc = nullptr;
+  double* pk_uv = nullptr;
+  double* pk_ud = nullptr;     // U diagonal
+  double* ylev = nullptr;      // sweep right-hand side in level order
   // ---- iteration work vectors ----
   double* q = nullptr;
   double* x = nullptr;

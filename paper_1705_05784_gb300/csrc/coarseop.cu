@@ -184,8 +184,8 @@ __global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
   int* ipiv = cs.ipiv + I.nc_off;
   __shared__ double sv[32];
   __shared__ int si[32];
-  __shared__ int s_jp, s_ju, s_bad;
-  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; }
+  __shared__ int s_jp, s_ju, s_bad, s_badcol;
+  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
   __syncthreads();
 #define AEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
   for (int j = 0; j < n; ++j) {
@@ -211,7 +211,10 @@ __global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
         if (sv[w] > b0 || (sv[w] == b0 && si[w] < i0)) { b0 = sv[w]; i0 = si[w]; }
       s_jp = i0;
       ipiv[j] = j + i0;
-      if (!(b0 > 0.0) || !isfinite(b0)) s_bad = 1;
+      if (!(b0 > 0.0) || !isfinite(b0)) {
+        s_bad = 1;
+        s_badcol = j;
+      }
       s_ju = max(s_ju, min(j + ku + i0, n - 1));
     }
     __syncthreads();
@@ -236,7 +239,8 @@ __global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
     __syncthreads();
   }
 #undef AEL
-  if (threadIdx.x == 0 && s_bad) atomicCAS(err, 0, DERR_BREAKDOWN);
+  // a numerically singular coarse system fails this instance only
+  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
 }
 
 }  // namespace
@@ -261,6 +265,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_TRY(b.alloc((void**)&cs.band_off, sizeof(long long) * B));
   FAMS_TRY(b.alloc((void**)&cs.ipiv, sizeof(int) * (nct + 1)));
   FAMS_TRY(b.alloc((void**)&cs.perm, sizeof(int) * (nct + 1)));
+  FAMS_TRY(b.alloc((void**)&cs.bad, sizeof(int) * B));
   FAMS_CUDA(cudaMemcpyAsync(cs.ac_off, ch.ac_off.data(), sizeof(long long) * B,
                             cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (tot + 1), st));
@@ -309,6 +314,9 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
   fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
   FAMS_CUDA(cudaGetLastError());
+  ch.bad.assign(B, 0);
+  FAMS_CUDA(cudaMemcpyAsync(ch.bad.data(), cs.bad, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
   return b.check_err("coarse LU");
 }
 

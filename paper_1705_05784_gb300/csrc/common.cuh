@@ -22,6 +22,11 @@ enum DevErr {
 };
 
 constexpr int RANK_I = 0, RANK_F = 1, RANK_E = 2, RANK_V = 3;
+// per-instance solve statistics: iterations, relative residual, converged,
+// ||q||, then SM cycles of the five phases of a sweep (residual, coarse,
+// prolongation + r1, L sweep, U sweep), one spare
+constexpr int STAT_W = 10;
+constexpr int PK = 4;  // factor entries per row kept inline in the level-ordered layout
 constexpr int MAX_OVERLAP = 8;        // matrix columns one fracture cell may cross
 constexpr int MIDPOINT_N = 64;        // points per axis of the <d> midpoint rule
 constexpr double ZERO_PIECE = 1e-12;  // x h_f

@@ -276,6 +276,13 @@ int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_ou
     cs = &b.cs[1];
   }
   const Inst& I = b.h[ii];
+  const CoarseHost& chh = all_fv ? b.csh[0] : b.csh[1];
+  if (chh.bad[ii]) {
+    set_error("instance " + std::to_string(ii) + ": the finite-volume coarse system is "
+              "numerically singular (zero pivot at LU step " + std::to_string(chh.bad[ii] - 1) +
+              "); no conservative reconstruction");
+    return FAMS_EBREAKDOWN;
+  }
   double* pp = b.r;   // work vectors: r = residual, dp = p', y = p~
   double* pt = b.y;
   double* res = b.dp;

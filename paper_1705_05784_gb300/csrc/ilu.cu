@@ -93,6 +93,28 @@ __global__ void k_ilu_factor(const Inst* inst, int B, const int* rowptr, const i
   if (threadIdx.x == 0 && bad) atomicCAS(err, 0, DERR_BREAKDOWN);
 }
 
+// level-ordered structure-of-arrays copy of the factors (position t)
+__global__ void k_pack(long long nrow, const int* rows, const int* rowptr, const int* col,
+                       const int* diag, const double* F, int* pos, int* nl, int* lp, int* lc,
+                       double* lv, int* nu, int* uc, double* uv, double* ud) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrow) return;
+  int i = rows[t];
+  int a = rowptr[i], d = diag[i], e = rowptr[i + 1];
+  pos[i] = (int)t;
+  nl[t] = d - a;
+  lp[t] = a;
+  nu[t] = e - d - 1;
+  ud[t] = F[d];
+  for (int k = 0; k < PK; ++k) {
+    long long o = (long long)k * nrow + t;
+    lc[o] = (a + k < d) ? col[a + k] : 0;
+    lv[o] = (a + k < d) ? F[a + k] : 0.0;
+    uc[o] = (d + 1 + k < e) ? col[d + 1 + k] : 0;
+    uv[o] = (d + 1 + k < e) ? F[d + 1 + k] : 0.0;
+  }
+}
+
 }  // namespace
 
 int phase_ilu(Batch& b) {
@@ -135,7 +157,24 @@ int phase_ilu(Batch& b) {
   fams::note_launch(), k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, b.lev_off, b.lev_ptr,
                                   b.lev_rows, b.ilu, b.d_err);
   FAMS_CUDA(cudaGetLastError());
-  return b.check_err("ILU(0)");
+  FAMS_TRY(b.check_err("ILU(0)"));
+  long long n1 = nrow + 1;
+  FAMS_TRY(b.alloc((void**)&b.pk_pos, sizeof(int) * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_nl, sizeof(int) * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_lp, sizeof(int) * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_nu, sizeof(int) * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_lc, sizeof(int) * PK * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_uc, sizeof(int) * PK * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_lv, sizeof(double) * PK * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_uv, sizeof(double) * PK * n1));
+  FAMS_TRY(b.alloc((void**)&b.pk_ud, sizeof(double) * n1));
+  FAMS_TRY(b.alloc((void**)&b.ylev, sizeof(double) * n1));
+  if (nrow > 0)
+    fams::note_launch(), k_pack<<<grid_for(nrow, T), T, 0, st>>>(
+        nrow, b.lev_rows, b.rowptr, b.col, b.diag, b.ilu, b.pk_pos, b.pk_nl, b.pk_lp, b.pk_lc,
+        b.pk_lv, b.pk_nu, b.pk_uc, b.pk_uv, b.pk_ud);
+  FAMS_CUDA(cudaGetLastError());
+  return FAMS_OK;
 }
 
 }  // namespace fams

@@ -5,8 +5,16 @@
 //
 // One persistent CTA per instance runs the whole loop, so instances of a
 // batch never wait for each other and each result is independent of the
-// batch it ran in (every reduction has a fixed order).  The coarse vectors
-// live in shared memory; the band triangular solves run in one warp.
+// batch it ran in (every reduction has a fixed order).  Everything on the
+// loop's critical path is arranged so that a step waits for at most one
+// memory round trip:
+//  * row-parallel passes (residual, r1, P e_c) keep four rows per thread in
+//    flight;
+//  * the coarse band solve runs in warp 0 on factor columns that the other
+//    warps stage into shared memory one chunk ahead (double buffer);
+//  * the ILU(0) sweeps go level by level; the row data of the next level
+//    (indices, factors, right-hand side) is loaded before the barrier, so a
+//    level costs one gather of the previous level's results.
 #include <algorithm>
 
 #include "batch.cuh"
@@ -16,6 +24,9 @@ namespace fams {
 namespace {
 
 constexpr int SOLVE_T = 512;
+constexpr int ROWS_ILP = 4;
+constexpr int BAND_BUF = 3072;   // doubles per staged chunk of band columns (24 KiB)
+constexpr int CH_MAX = 64;       // band columns per chunk
 
 __device__ inline double block_sum(double v, double* red) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -41,7 +52,6 @@ __global__ void k_make_q(long long n, const double* rhs, const double* qD, doubl
 struct SolveArgs {
   const Inst* inst;
   CoarseSys cs;
-  int fe;
   const int* rowptr;
   const int* col;
   const double* val;
@@ -68,138 +78,330 @@ struct SolveArgs {
   long long hist_len;
   double* crhs;   // coarse right-hand side of the last sweep (coarse order)
   double* csol;   // coarse solution of the last sweep
+  // level-ordered factors (position t) and right-hand side
+  const int* pk_pos;
+  const int* pk_nl;
+  const int* pk_lp;
+  const int* pk_lc;
+  const double* pk_lv;
+  const int* pk_nu;
+  const int* pk_uc;
+  const double* pk_uv;
+  const double* pk_ud;
+  double* ylev;
+  long long ntot;  // rows of the batch (stride of the PK arrays)
   double tol;
 };
 
-// coarse solve of the band LU (gbtrs scheme) by warp 0, vector in shared memory
-__device__ void band_solve_warp(const double* AB, const int* ipiv, int n, int kl, int ku,
-                                double* yb) {
-  int lane = threadIdx.x & 31;
-  int kv = kl + ku, ldab = 2 * kl + ku + 1;
-  // L: forward with row interchanges
-  for (int j = 0; j < n; ++j) {
-    int km = min(kl, n - 1 - j);
-    int pj = ipiv[j];
-    if (lane == 0 && pj != j) {
-      double t = yb[j];
-      yb[j] = yb[pj];
-      yb[pj] = t;
+// y[i] = b[i] - sum_p val[p] v[col[p]] for the instance's rows, four rows per
+// thread in flight; returns this thread's sum of y^2 when `norm`
+__device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const double* b,
+                                       const double* v, double* y, bool norm,
+                                       double* ylev = nullptr) {
+  double acc = 0.0;
+  const int T = blockDim.x;
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+    int rs[ROWS_ILP], re[ROWS_ILP];
+    double s[ROWS_ILP];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * T;
+      bool ok = i < ro + n;
+      rs[k] = ok ? a.rowptr[i] : 0;
+      re[k] = ok ? a.rowptr[i + 1] : 0;
+      s[k] = ok ? b[i] : 0.0;
+      m = max(m, re[k] - rs[k]);
     }
-    __syncwarp();
-    double yj = yb[j];
-    for (int t = 1 + lane; t <= km; t += 32)
-      yb[j + t] -= AB[(long long)(kv + t) + (long long)ldab * j] * yj;
-    __syncwarp();
+    for (int e = 0; e < m; ++e) {
+#pragma unroll
+      for (int k = 0; k < ROWS_ILP; ++k) {
+        int p = rs[k] + e;
+        if (p < re[k]) s[k] -= a.val[p] * v[a.col[p]];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * T;
+      if (i < ro + n) {
+        y[i] = s[k];
+        if (ylev) ylev[a.pk_pos[i]] = s[k];
+        if (norm) acc += s[k] * s[k];
+      }
+    }
   }
-  // U: backward, kv superdiagonals
-  for (int j = n - 1; j >= 0; --j) {
-    double yj = yb[j] / AB[(long long)kv + (long long)ldab * j];
-    __syncwarp();
-    if (lane == 0) yb[j] = yj;
-    int lo = max(0, j - kv);
-    for (int i = lo + lane; i < j; i += 32)
-      yb[i] -= AB[(long long)(kv + i - j) + (long long)ldab * j] * yj;
-    __syncwarp();
+  return acc;
+}
+
+// coarse band solve: warp 0 runs the recurrences on columns staged in shared
+// memory, the other warps stage the next chunk meanwhile
+__device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, int ku, double* yb,
+                             double* buf, int* pbuf) {
+  const int kv = kl + ku, ldab = 2 * kl + ku + 1, stride = kv + 1;
+  int ch = BAND_BUF / stride;
+  ch = max(1, min(CH_MAX, ch));
+  const int nch = (n + ch - 1) / ch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int T = blockDim.x;
+  // forward (L with row interchanges), chunk c holds columns [c ch, (c+1) ch)
+  auto load_fwd = [&](int c, double* dst, int* pdst, int t0, int nt) {
+    int j0 = c * ch;
+    for (int idx = t0; idx < ch * kl; idx += nt) {
+      int jj = idx / kl, t = idx % kl + 1, j = j0 + jj;
+      dst[jj * stride + t - 1] = (j < n && t <= n - 1 - j) ? AB[(long long)(kv + t) + (long long)ldab * j] : 0.0;
+    }
+    for (int jj = t0; jj < ch; jj += nt) pdst[jj] = (j0 + jj < n) ? ipiv[j0 + jj] : 0;
+  };
+  load_fwd(0, buf, pbuf, threadIdx.x, T);
+  __syncthreads();
+  for (int c = 0; c < nch; ++c) {
+    double* cur = buf + (c & 1) * BAND_BUF;
+    int* pcur = pbuf + (c & 1) * CH_MAX;
+    if (warp == 0) {
+      int j0 = c * ch;
+      for (int jj = 0; jj < ch && j0 + jj < n; ++jj) {
+        int j = j0 + jj;
+        int km = min(kl, n - 1 - j);
+        int pj = pcur[jj];
+        if (lane == 0 && pj != j) {
+          double t = yb[j];
+          yb[j] = yb[pj];
+          yb[pj] = t;
+        }
+        __syncwarp();
+        double yj = yb[j];
+        for (int t = 1 + lane; t <= km; t += 32) yb[j + t] -= cur[jj * stride + t - 1] * yj;
+        __syncwarp();
+      }
+    } else if (c + 1 < nch) {
+      load_fwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, pbuf + ((c + 1) & 1) * CH_MAX,
+               threadIdx.x - 32, T - 32);
+    }
+    __syncthreads();
+  }
+  // backward (U, kv superdiagonals); chunk c holds columns [n-(c+1)ch, n-c ch)
+  auto load_bwd = [&](int c, double* dst, int t0, int nt) {
+    int jhi = n - c * ch, jlo = max(0, jhi - ch);
+    for (int idx = t0; idx < (jhi - jlo) * stride; idx += nt) {
+      int jj = idx / stride, rr = idx % stride, j = jlo + jj;
+      int i = j - kv + rr;
+      dst[jj * stride + rr] = (i >= 0) ? AB[(long long)rr + (long long)ldab * j] : 0.0;
+    }
+  };
+  load_bwd(0, buf, threadIdx.x, T);
+  __syncthreads();
+  for (int c = 0; c < nch; ++c) {
+    double* cur = buf + (c & 1) * BAND_BUF;
+    if (warp == 0) {
+      int jhi = n - c * ch, jlo = max(0, jhi - ch);
+      for (int j = jhi - 1; j >= jlo; --j) {
+        const double* colj = cur + (j - jlo) * stride;
+        double yj = yb[j] / colj[kv];
+        __syncwarp();
+        if (lane == 0) yb[j] = yj;
+        for (int i = max(0, j - kv) + lane; i < j; i += 32) yb[i] -= colj[kv + i - j] * yj;
+        __syncwarp();
+      }
+    } else if (c + 1 < nch) {
+      load_bwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, threadIdx.x - 32, T - 32);
+    }
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(SOLVE_T) k_solve(SolveArgs a) {
+// one row of a triangular sweep, loaded from the level-ordered layout: every
+// address depends only on the position t, so the loads of a whole level are
+// coalesced and independent of the sweep's results
+struct SweepRow {
+  int t, i, cnt, p;
+  double base, diag;
+  int c[PK];
+  double f[PK];
+};
+
+__device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int nlev, bool lower,
+                                  SweepRow& s) {
+  s.t = -1;
+  if (l < 0 || l >= nlev) return;
+  int t = lp[l] + threadIdx.x;
+  if (t >= lp[l + 1]) return;
+  s.t = t;
+  s.i = a.lev_rows[t];
+  s.base = a.ylev[t];
+  if (lower) {
+    s.cnt = a.pk_nl[t];
+    s.p = a.pk_lp[t];
+    s.diag = 1.0;
+  } else {
+    s.cnt = a.pk_nu[t];
+    s.diag = a.pk_ud[t];
+  }
+  const int* pc = lower ? a.pk_lc : a.pk_uc;
+  const double* pv = lower ? a.pk_lv : a.pk_uv;
+#pragma unroll
+  for (int k = 0; k < PK; ++k) {
+    s.c[k] = pc[(long long)k * a.ntot + t];
+    s.f[k] = pv[(long long)k * a.ntot + t];
+  }
+}
+
+__global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   extern __shared__ double sm[];
   __shared__ double red[40];
   __shared__ int s_done;
+  __shared__ int pbuf[2 * CH_MAX];
   int ii = blockIdx.x;
   const Inst& I = a.inst[ii];
-  int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
-  double* yb = sm;        // coarse vector in band order
-  double* ecs = sm + nc;  // coarse correction in coarse order
+  const int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
+  double* yb = sm;            // coarse vector in band order
+  double* ecs = sm + nc;      // coarse correction in coarse order
+  double* buf = sm + 2 * nc;  // two staged chunks of band columns
   const double* AB = a.cs.band + a.cs.band_off[ii];
   const int* ipiv = a.cs.ipiv + co;
   const int* perm = a.cs.perm + co;
-  int kl = a.cs.kl[ii], ku = a.cs.ku[ii];
+  const int kl = a.cs.kl[ii], ku = a.cs.ku[ii];
   const int* lp = a.lev_ptr + a.lev_off[ii];
-  int nlev = I.nlev;
+  const int nlev = I.nlev;
+  const int T = blockDim.x;
   // ||q||
   double acc = 0.0;
-  for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) acc += a.q[i] * a.q[i];
+  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
   double qn = sqrt(block_sum(acc, red));
   if (!(qn > 0.0)) qn = 1.0;
   int it = 0;
   double rel = 0.0;
+  // SM cycles per phase (thread 0, between barriers): residual, coarse
+  // (restriction + band solve), prolongation + r1, L sweep, U sweep
+  long long cyc[5] = {0, 0, 0, 0, 0};
+  long long t0 = clock64();
   for (;;) {
     // step 3: r = q - A p
-    acc = 0.0;
-    for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
-      double s = a.q[i];
-      for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) s -= a.val[p] * a.x[a.col[p]];
-      a.r[i] = s;
-      acc += s * s;
-    }
+    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
     rel = sqrt(block_sum(acc, red)) / qn;
     if (threadIdx.x == 0) {
       a.hist[(long long)ii * a.hist_len + it] = rel;
-      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel));
+      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii]);
     }
     __syncthreads();
+    long long t1 = clock64();
+    cyc[0] += t1 - t0;
     if (s_done) break;
     // step 5: coarse right-hand side R r, in band order
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    for (int k = threadIdx.x; k < nc; k += T) {
       int c = co + perm[k];
-      double s = 0.0;
+      double s0 = 0.0, s1 = 0.0;
       if (I.restriction == FAMS_R_FE) {
-        for (int p = a.pt_ptr[c]; p < a.pt_ptr[c + 1]; ++p) s += a.pt_val[p] * a.r[a.pt_col[p]];
+        int p = a.pt_ptr[c], e = a.pt_ptr[c + 1];
+        for (; p + 1 < e; p += 2) {
+          s0 += a.pt_val[p] * a.r[a.pt_col[p]];
+          s1 += a.pt_val[p + 1] * a.r[a.pt_col[p + 1]];
+        }
+        if (p < e) s0 += a.pt_val[p] * a.r[a.pt_col[p]];
       } else {
-        for (int p = a.blk_ptr[c]; p < a.blk_ptr[c + 1]; ++p) s += a.r[a.blk_cell[p]];
+        int p = a.blk_ptr[c], e = a.blk_ptr[c + 1];
+        for (; p + 1 < e; p += 2) {
+          s0 += a.r[a.blk_cell[p]];
+          s1 += a.r[a.blk_cell[p + 1]];
+        }
+        if (p < e) s0 += a.r[a.blk_cell[p]];
       }
-      yb[k] = s;
+      yb[k] = s0 + s1;
+      a.crhs[co + perm[k]] = s0 + s1;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) a.crhs[co + perm[k]] = yb[k];
-    if (threadIdx.x < 32) band_solve_warp(AB, ipiv, nc, kl, ku, yb);
-    __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    coarse_solve(AB, ipiv, nc, kl, ku, yb, buf, pbuf);
+    for (int k = threadIdx.x; k < nc; k += T) {
       ecs[perm[k]] = yb[k];
       a.csol[co + perm[k]] = yb[k];
     }
     __syncthreads();
+    long long t2 = clock64();
+    cyc[1] += t2 - t1;
     // dp1 = P e_c
-    for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
-      double s = 0.0;
-      for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += a.p_val[p] * ecs[a.p_col[p]];
-      a.dp[i] = s;
+    for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+#pragma unroll
+      for (int k = 0; k < ROWS_ILP; ++k) {
+        int i = i0 + k * T;
+        if (i < ro + n) {
+          double s = 0.0;
+          for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += a.p_val[p] * ecs[a.p_col[p]];
+          a.dp[i] = s;
+        }
+      }
     }
     __syncthreads();
-    // steps 6-7, L sweep: y = L^-1 (r - A dp1)
+    // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
+    rows_residual(a, ro, n, a.r, a.dp, a.y, false, a.ylev);
+    __syncthreads();
+    long long t3 = clock64();
+    cyc[2] += t3 - t2;
+    // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
+    SweepRow cur, nxt;
+    sweep_load(a, lp, 0, nlev, true, cur);
     for (int l = 0; l < nlev; ++l) {
-      for (int t = lp[l] + threadIdx.x; t < lp[l + 1]; t += blockDim.x) {
+      sweep_load(a, lp, l + 1, nlev, true, nxt);
+      if (cur.t >= 0) {
+        double s = cur.base;
+#pragma unroll
+        for (int k = 0; k < PK; ++k)
+          if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
+        for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
+        a.y[cur.i] = s;
+        a.ylev[cur.t] = s;
+      }
+      for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
         int i = a.lev_rows[t];
-        double s = a.r[i];
-        int d = a.diag[i];
-        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) s -= a.val[p] * a.dp[a.col[p]];
-        for (int p = a.rowptr[i]; p < d; ++p) s -= a.F[p] * a.y[a.col[p]];
+        double s = a.ylev[t];
+        for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= a.F[p] * a.y[a.col[p]];
         a.y[i] = s;
+        a.ylev[t] = s;
       }
       __syncthreads();
+      cur = nxt;
     }
+    long long t4 = clock64();
+    cyc[3] += t4 - t3;
     // U sweep and step 8: p = p + dp1 + dp2
+    sweep_load(a, lp, nlev - 1, nlev, false, cur);
     for (int l = nlev - 1; l >= 0; --l) {
-      for (int t = lp[l] + threadIdx.x; t < lp[l + 1]; t += blockDim.x) {
+      sweep_load(a, lp, l - 1, nlev, false, nxt);
+      if (cur.t >= 0) {
+        double s = cur.base;
+        double xo = a.x[cur.i], dpo = a.dp[cur.i];
+#pragma unroll
+        for (int k = 0; k < PK; ++k)
+          if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
+        if (cur.cnt > PK) {
+          int d = a.diag[cur.i];
+          for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
+        }
+        double xi = s / cur.diag;
+        a.y[cur.i] = xi;
+        a.x[cur.i] = (xo + dpo) + xi;
+      }
+      for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
         int i = a.lev_rows[t];
         int d = a.diag[i];
-        double s = a.y[i];
+        double s = a.ylev[t];
         for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= a.F[p] * a.y[a.col[p]];
         double xi = s / a.F[d];
         a.y[i] = xi;
         a.x[i] = (a.x[i] + a.dp[i]) + xi;
       }
       __syncthreads();
+      cur = nxt;
     }
+    t0 = clock64();
+    cyc[4] += t0 - t4;
     ++it;
   }
   if (threadIdx.x == 0) {
-    a.stat[4 * ii + 0] = it;
-    a.stat[4 * ii + 1] = rel;
-    a.stat[4 * ii + 2] = (rel <= a.tol) ? 1.0 : 0.0;
-    a.stat[4 * ii + 3] = qn;
+    a.stat[STAT_W * ii + 0] = it;
+    a.stat[STAT_W * ii + 1] = rel;
+    a.stat[STAT_W * ii + 2] = (rel <= a.tol) ? 1.0 : 0.0;
+    a.stat[STAT_W * ii + 3] = qn;
+    for (int k = 0; k < 5; ++k) a.stat[STAT_W * ii + 4 + k] = (double)cyc[k];
+    a.stat[STAT_W * ii + 9] = a.cs.bad[ii] ? 1.0 : 0.0;  // singular coarse system
   }
 }
 
@@ -212,7 +414,7 @@ int phase_alloc_work(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.r, sizeof(double) * (n + 1)));
   FAMS_TRY(b.alloc((void**)&b.dp, sizeof(double) * (n + 1)));
   FAMS_TRY(b.alloc((void**)&b.y, sizeof(double) * (n + 1)));
-  FAMS_TRY(b.alloc((void**)&b.stat, sizeof(double) * 4 * b.B));
+  FAMS_TRY(b.alloc((void**)&b.stat, sizeof(double) * STAT_W * b.B));
   int mi = 0;
   for (auto& I : b.h) mi = std::max(mi, I.max_iter);
   b.hist_len = mi + 1;
@@ -233,7 +435,6 @@ int run_solve(Batch& b, double tol, float* ms) {
   SolveArgs a;
   a.inst = b.d_inst;
   a.cs = b.cs[0];
-  a.fe = b.h[0].restriction == FAMS_R_FE;
   a.rowptr = b.rowptr; a.col = b.col; a.val = b.val; a.diag = b.diag;
   a.p_ptr = b.p_ptr; a.p_col = b.p_col; a.p_val = b.p_val;
   a.pt_ptr = b.pt_ptr; a.pt_col = b.pt_col; a.pt_val = b.pt_val;
@@ -242,18 +443,27 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.q = b.q; a.x = b.x; a.r = b.r; a.dp = b.dp; a.y = b.y; a.stat = b.stat;
   a.hist = b.hist; a.hist_len = b.hist_len;
   a.crhs = b.rc; a.csol = b.ec;
+  a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
+  a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
+  a.ylev = b.ylev;
+  a.ntot = b.tot_row;
   a.tol = tol;
   int maxnc = 0;
   for (auto& I : b.h) maxnc = std::max(maxnc, I.nc);
-  size_t smem = sizeof(double) * 2 * (size_t)maxnc;
+  for (int i = 0; i < b.B; ++i)
+    if (b.csh[0].kl[i] + b.csh[0].ku[i] + 1 > BAND_BUF) {
+      set_error("coarse band wider than the staged band buffer");
+      return FAMS_ECAPACITY;
+    }
+  size_t smem = sizeof(double) * (2 * (size_t)maxnc + 2 * BAND_BUF);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
-  if ((long long)smem + 1024 > max_smem) {
+  if ((long long)smem + 2048 > max_smem) {
     set_error("coarse system too large for the shared-memory coarse solve");
     return FAMS_ECAPACITY;
   }
   FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - 1024));
+                                 max_smem - 2048));
   cudaEvent_t e0, e1;
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));
