@@ -148,6 +148,16 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
    fracture cell index). */
 int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, double* nnc_flux);
 
+/* fams_flux_batch - the same reconstruction for every instance of a batch
+   context in one pass (x[i], face_flux[i], nnc_flux[i] per instance, host or
+   device).  status (nullable, n_instances entries) receives each instance's
+   result; an instance whose finite-volume coarse system R^FV A P is
+   numerically singular gets FAMS_EBREAKDOWN and its buffers are left
+   untouched while the others are reconstructed.  Returns FAMS_EBREAKDOWN if
+   any instance failed that way. */
+int fams_flux_batch(fams_ctx* ctx, const double* const* x, double* const* face_flux,
+                    double* const* nnc_flux, int* status);
+
 /* fams_query - copy an internal array of instance `inst` into out (host or
    device, capacity `cap` elements of the stated type).  Returns the element
    count (>= 0) or a negative error; with out == NULL only the count.  For the
@@ -182,8 +192,11 @@ enum {
   FAMS_Q_LAST_DP2 = 27,    /* double smoother correction of the last sweep (Table 1 step 7) */
   FAMS_Q_LAST_RC = 28,     /* double coarse right-hand side R r of the last sweep */
   FAMS_Q_LAST_EC = 29,     /* double coarse solution (R A P)^-1 R r of the last sweep */
-  FAMS_Q_STAGE_CYCLES = 30 /* double SM cycles of the last solve per phase: residual, coarse
-                              (restriction + band solve), prolongation + r1, L sweep, U sweep */
+  FAMS_Q_STAGE_CYCLES = 30, /* double SM cycles of the last solve per phase: residual,
+                               restriction, band solve, prolongation + r1, L sweep, U sweep */
+  FAMS_Q_SETUP_MS = 31     /* double wall ms of the setup phases of the whole context:
+                              geometry, fine system, coarse grids, basis, coarse operator,
+                              ILU(0) */
 };
 int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap);
 

@@ -3,6 +3,7 @@
 // kernels of the other translation units.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 
@@ -167,12 +168,31 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
       }
   }
   FAMS_TRY(b.upload_inst());
+  // wall time of each setup phase (every phase ends synchronised with the
+  // device): geometry, system, coarse grids, basis, coarse operator, ILU(0)
+  auto tick = [&](int k, double t0) {
+    b.setup_ms[k] = 1e3 * (std::chrono::duration<double>(
+                               std::chrono::steady_clock::now().time_since_epoch()).count() - t0);
+  };
+  auto now = [] {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+  };
+  double t0 = now();
   FAMS_TRY(phase_geometry(b));
+  tick(0, t0), t0 = now();
   FAMS_TRY(phase_system(b));
+  tick(1, t0), t0 = now();
   FAMS_TRY(phase_coarse(b));
+  tick(2, t0), t0 = now();
   FAMS_TRY(phase_basis(b));
+  tick(3, t0), t0 = now();
   FAMS_TRY(phase_coarse_op(b, -1));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  tick(4, t0), t0 = now();
   FAMS_TRY(phase_ilu(b));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  tick(5, t0);
   FAMS_TRY(phase_alloc_work(b));
   FAMS_CUDA(cudaMemcpyAsync(b.q, b.qD, sizeof(double) * b.tot_row, cudaMemcpyDeviceToDevice, b.stream));
   FAMS_CUDA(cudaMemsetAsync(b.x, 0, sizeof(double) * b.tot_row, b.stream));
@@ -203,6 +223,73 @@ int fetch(const Batch& b, const T* src, long long n, std::vector<T>& out) {
 }  // namespace
 
 int make_q(Batch& b, const double* rhs_dev);
+
+namespace {
+
+long long faces_host(const Inst& I) {
+  long long nz = I.dim == 3 ? I.nz : 1;
+  return (long long)(I.nx + 1) * I.ny * nz + (long long)I.nx * (I.ny + 1) * nz +
+         (I.dim == 3 ? (long long)I.nx * I.ny * (nz + 1) : 0);
+}
+
+// reconstruction of the listed instances; per-instance status (nullable)
+int flux_some(Batch& b, const std::vector<int>& want, const double* const* x,
+              double* const* face, double* const* nnc, int* status) {
+  for (int ii : want)
+    if (ii < 0 || ii >= b.B) {
+      set_error("bad instance");
+      return FAMS_EINVAL;
+    }
+  if (!b.fx) {
+    long long nf = 0, nn = 0;
+    for (auto& I : b.h) nf += faces_host(I), nn += (long long)I.nnc + I.nff;
+    FAMS_TRY(b.alloc((void**)&b.fx, sizeof(double) * (b.tot_row + 1)));
+    FAMS_TRY(b.alloc((void**)&b.fface, sizeof(double) * (nf + 1)));
+    FAMS_TRY(b.alloc((void**)&b.fnnc, sizeof(double) * (nn + 1)));
+  }
+  const CoarseHost* ch = nullptr;
+  FAMS_TRY(flux_prepare(b, &ch));
+  std::vector<int> list;
+  std::vector<int> slot;  // position of each wanted instance in the call's arrays
+  int result = FAMS_OK;
+  for (size_t k = 0; k < want.size(); ++k) {
+    int ii = want[k];
+    if (ch->bad[ii]) {
+      if (status) status[k] = FAMS_EBREAKDOWN;
+      if (result == FAMS_OK)
+        set_error("instance " + std::to_string(ii) + ": the finite-volume coarse system is "
+                  "numerically singular (zero pivot at LU step " + std::to_string(ch->bad[ii] - 1) +
+                  "); no conservative reconstruction");
+      result = FAMS_EBREAKDOWN;
+      continue;
+    }
+    if (status) status[k] = FAMS_OK;
+    list.push_back(ii);
+    slot.push_back((int)k);
+  }
+  std::vector<long long> foff(list.size() + 1, 0), noff(list.size() + 1, 0);
+  for (size_t k = 0; k < list.size(); ++k) {
+    const Inst& I = b.h[list[k]];
+    foff[k + 1] = foff[k] + faces_host(I);
+    noff[k + 1] = noff[k] + I.nnc + I.nff;
+    FAMS_CUDA(cudaMemcpyAsync(b.fx + I.row_off, x[slot[k]], sizeof(double) * I.n,
+                              cudaMemcpyDefault, b.stream));
+  }
+  int s = run_flux(b, list, b.fx, b.fface, foff, b.fnnc, noff);
+  if (s != FAMS_OK) return s;
+  for (size_t k = 0; k < list.size(); ++k) {
+    long long nf = foff[k + 1] - foff[k], nn = noff[k + 1] - noff[k];
+    FAMS_CUDA(cudaMemcpyAsync(face[slot[k]], b.fface + foff[k], sizeof(double) * nf,
+                              cudaMemcpyDefault, b.stream));
+    if (nn > 0)
+      FAMS_CUDA(cudaMemcpyAsync(nnc[slot[k]], b.fnnc + noff[k], sizeof(double) * nn,
+                                cudaMemcpyDefault, b.stream));
+  }
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  return result;
+}
+
+}  // namespace
 
 }  // namespace fams
 
@@ -291,7 +378,7 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
       st[i].converged = stat[STAT_W * i + 2] > 0.5;
       st[i].solve_ms = ms;
     }
-    if (stat[STAT_W * i + 9] > 0.5) {
+    if (stat[STAT_W * i + STAT_BAD] > 0.5) {
       if (status != FAMS_EBREAKDOWN)
         set_error("instance " + std::to_string(i) + ": numerically singular coarse system "
                   "(zero pivot at LU step " + std::to_string(b.csh[0].bad[i] - 1) + ")");
@@ -320,35 +407,27 @@ int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, doubl
     set_error("null argument or bad instance");
     return FAMS_EINVAL;
   }
-  Batch& b = ctx->b;
-  int nf = 0, nn = 0;
-  fams_sizes(ctx, inst, nullptr, nullptr, nullptr, &nf, &nn);
-  const Inst& I = b.h[inst];
-  double *dx = nullptr, *df = nullptr, *dn = nullptr;
-  FAMS_CUDA(cudaMalloc(&dx, sizeof(double) * (I.n + 1)));
-  cudaError_t e1 = cudaMalloc(&df, sizeof(double) * (nf + 1));
-  cudaError_t e2 = cudaMalloc(&dn, sizeof(double) * (nn + 1));
-  int s = FAMS_OK;
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    set_error("flux buffers");
-    s = FAMS_ENOMEM;
+  const double* xs[1] = {x};
+  double* fs[1] = {face_flux};
+  double* ns[1] = {nnc_flux};
+  return flux_some(ctx->b, std::vector<int>{inst}, xs, fs, ns, nullptr);
+}
+
+int fams_flux_batch(fams_ctx* ctx, const double* const* x, double* const* face_flux,
+                    double* const* nnc_flux, int* status) {
+  if (!ctx || !x || !face_flux || !nnc_flux) {
+    set_error("null argument");
+    return FAMS_EINVAL;
   }
-  if (s == FAMS_OK && cudaMemcpy(dx, x, sizeof(double) * I.n, cudaMemcpyDefault) != cudaSuccess) {
-    set_error("copy of x");
-    s = FAMS_ECUDA;
-  }
-  if (s == FAMS_OK) s = run_flux(b, inst, dx, df, dn);
-  if (s == FAMS_OK) {
-    if (cudaMemcpy(face_flux, df, sizeof(double) * nf, cudaMemcpyDefault) != cudaSuccess ||
-        (nn > 0 && cudaMemcpy(nnc_flux, dn, sizeof(double) * nn, cudaMemcpyDefault) != cudaSuccess)) {
-      set_error("copy of the fluxes");
-      s = FAMS_ECUDA;
+  std::vector<int> all(ctx->b.B);
+  for (int i = 0; i < ctx->b.B; ++i) {
+    if (!x[i] || !face_flux[i] || !nnc_flux[i]) {
+      set_error("null buffer");
+      return FAMS_EINVAL;
     }
+    all[i] = i;
   }
-  cudaFree(dx);
-  if (df) cudaFree(df);
-  if (dn) cudaFree(dn);
-  return s;
+  return flux_some(ctx->b, all, x, face_flux, nnc_flux, status);
 }
 
 int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap) {
@@ -410,7 +489,8 @@ int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap
       FAMS_TRY(dbls(b.cs[0].band + b.csh[0].band_off[inst],
                     (long long)(2 * b.csh[0].kl[inst] + b.csh[0].ku[inst] + 1) * I.nc));
       break;
-    case FAMS_Q_STAGE_CYCLES: FAMS_TRY(dbls(b.stat + STAT_W * inst + 4, 5)); break;
+    case FAMS_Q_STAGE_CYCLES: FAMS_TRY(dbls(b.stat + STAT_W * inst + 4, 6)); break;
+    case FAMS_Q_SETUP_MS: isint = false; vd.assign(b.setup_ms, b.setup_ms + 6); break;
     case FAMS_Q_LAST_DP1: FAMS_TRY(dbls(b.dp + I.row_off, I.n)); break;
     case FAMS_Q_LAST_DP2: FAMS_TRY(dbls(b.y + I.row_off, I.n)); break;
     case FAMS_Q_LAST_RC: FAMS_TRY(dbls(b.rc + I.nc_off, I.nc)); break;

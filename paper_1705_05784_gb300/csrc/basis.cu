@@ -314,16 +314,17 @@ __global__ void k_comp_solve(const Inst* inst, int B, const int* off_row, const 
     if (threadIdx.x == 0) M[(long long)j * n + j] = l;
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(long long)i * n + j] /= l;
     __syncthreads();
+    // trailing update of the lower triangle: warp w takes rows j+1+w, j+1+w+NW, ...
+    // and its lanes the columns of that row
     int m = n - j - 1;
-    long long tot = (long long)m * (m + 1) / 2;
-    for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
-      // t -> (ii, jj) with jj <= ii, both in [0, m)
-      int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-      while ((long long)ii * (ii + 1) / 2 > t) --ii;
-      while ((long long)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      int jj = (int)(t - (long long)ii * (ii + 1) / 2);
-      int gi = j + 1 + ii, gj = j + 1 + jj;
-      M[(long long)gi * n + gj] -= M[(long long)gi * n + j] * M[(long long)gj * n + j];
+    int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int ii = threadIdx.x >> 5; ii < m; ii += nw) {
+      int gi = j + 1 + ii;
+      double lij = M[(long long)gi * n + j];
+      for (int jj = lane; jj <= ii; jj += 32) {
+        int gj = j + 1 + jj;
+        M[(long long)gi * n + gj] -= lij * M[(long long)gj * n + j];
+      }
     }
     __syncthreads();
   }

@@ -143,6 +143,11 @@ struct Batch {
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
   bool fv_ready = false;
+  double setup_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per setup phase, wall time
+  // flux reconstruction buffers (allocated on first use): iterates and outputs
+  double* fx = nullptr;
+  double* fface = nullptr;
+  double* fnnc = nullptr;
 
   int alloc(void** p, size_t bytes) {
     if (bytes == 0) bytes = 8;
@@ -188,6 +193,9 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int restriction, CoarseHost& ch
 int phase_ilu(Batch& b);          // ilu.cu
 int phase_alloc_work(Batch& b);   // solve.cu
 int run_solve(Batch& b, double tol, float* ms);   // solve.cu
-int run_flux(Batch& b, int inst, const double* x_dev, double* face, double* nnc);  // flux.cu
+// flux.cu
+int flux_prepare(Batch& b, const CoarseHost** ch);
+int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* face,
+             const std::vector<long long>& foff, double* nnc, const std::vector<long long>& noff);
 
 }  // namespace fams

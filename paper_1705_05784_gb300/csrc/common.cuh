@@ -23,9 +23,10 @@ enum DevErr {
 
 constexpr int RANK_I = 0, RANK_F = 1, RANK_E = 2, RANK_V = 3;
 // per-instance solve statistics: iterations, relative residual, converged,
-// ||q||, then SM cycles of the five phases of a sweep (residual, coarse,
-// prolongation + r1, L sweep, U sweep), one spare
-constexpr int STAT_W = 10;
+// ||q||, SM cycles of the six phases of a sweep (residual, restriction, band
+// solve, prolongation + r1, L sweep, U sweep), singular-coarse flag, spare
+constexpr int STAT_W = 12;
+constexpr int STAT_BAD = 10;
 constexpr int PK = 4;  // factor entries per row kept inline in the level-ordered layout
 constexpr int MAX_OVERLAP = 8;        // matrix columns one fracture cell may cross
 constexpr int MIDPOINT_N = 64;        // points per axis of the <d> midpoint rule

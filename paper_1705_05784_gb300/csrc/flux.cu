@@ -7,7 +7,9 @@
 //      pinned to p' at its coarse node) -> p~;
 //   4. connections inside a block carry T (p~_i - p~_j).
 // R^FV (q - A p') = 0 makes every local problem consistent, so the result is
-// mass conservative cell by cell.
+// mass conservative cell by cell.  All requested instances are processed
+// together: one CTA per instance for step 1, one CTA per primal block for
+// step 3, one thread per face or connection for steps 2 and 4.
 #include <algorithm>
 
 #include "batch.cuh"
@@ -16,36 +18,21 @@ namespace fams {
 
 namespace {
 
-__device__ inline double block_sum_f(double v, double* red) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[32] = s;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-// step 1 for one instance (one CTA)
-__global__ void k_flux_stage(const Inst* inst, int ii, CoarseSys cs, const int* rowptr,
+// step 1, one CTA per listed instance
+__global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, const int* rowptr,
                              const int* col, const double* val, const int* blk_ptr,
                              const int* blk_cell, const int* p_ptr, const int* p_col,
                              const double* p_val, const double* q, const double* x, double* r,
                              double* pp) {
   extern __shared__ double sm[];
+  int ii = list[blockIdx.x];
   const Inst& I = inst[ii];
   int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
   double* yb = sm;
   double* ecs = sm + nc;
   for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
     double s = q[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s -= val[p] * x[col[p] - ro];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s -= val[p] * x[col[p]];
     r[i] = s;
   }
   __syncthreads();
@@ -87,21 +74,20 @@ __global__ void k_flux_stage(const Inst* inst, int ii, CoarseSys cs, const int* 
   for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
     double s = 0.0;
     for (int p = p_ptr[i]; p < p_ptr[i + 1]; ++p) s += p_val[p] * ecs[p_col[p]];
-    pp[i] = x[i - ro] + s;
+    pp[i] = x[i] + s;
   }
 }
 
-// steps 2-3: one CTA per primal block, dense Gaussian elimination with
-// partial pivoting on the block's local TPFA matrix
-__global__ void k_flux_local(const Inst* inst, int ii, const int* blk_list, const int* blk_ptr,
-                             const int* blk_cell, const int* rowptr, const int* col,
-                             const double* val, const double* TD, const double* qD,
-                             const double* q, const int* primal, const int* node_cell,
-                             const double* pp, double* pt, double* gwork, long long gstride,
-                             int* err) {
+// step 3: one CTA per listed primal block (global coarse index), dense
+// Gaussian elimination with partial pivoting of the block's local TPFA matrix
+__global__ void k_flux_local(const Inst* inst, int B, const int* off_nc, const int* blk_list,
+                             const int* blk_ptr, const int* blk_cell, const int* rowptr,
+                             const int* col, const double* val, const double* TD, const double* q,
+                             const int* primal, const int* node_cell, const double* pp,
+                             double* pt, double* gwork, long long gstride, int* err) {
   extern __shared__ double dsm[];
-  const Inst& I = inst[ii];
-  int c = I.nc_off + blk_list[blockIdx.x];
+  int c = blk_list[blockIdx.x];
+  const Inst& I = inst[find_segment(off_nc, B + 1, c)];
   int a = blk_ptr[c], m = blk_ptr[c + 1] - a;
   double* K = gwork ? gwork + (long long)blockIdx.x * gstride : dsm;
   double* rhs = K + (long long)m * m;
@@ -120,7 +106,6 @@ __global__ void k_flux_local(const Inst* inst, int ii, const int* blk_list, cons
       if (j == i) continue;
       double T = -val[p];
       if (primal[j] == myblk) {
-        // position of j in the sorted member list
         int lo = 0, hi = m - 1, pos = -1;
         while (lo <= hi) {
           int mid = (lo + hi) >> 1;
@@ -153,7 +138,6 @@ __global__ void k_flux_local(const Inst* inst, int ii, const int* blk_list, cons
     rhs[pos] = pp[v];
   }
   __syncthreads();
-  // Gaussian elimination with partial pivoting
   for (int j = 0; j < m; ++j) {
     if (threadIdx.x == 0) {
       int pr = j;
@@ -204,22 +188,35 @@ __global__ void k_flux_local(const Inst* inst, int ii, const int* blk_list, cons
   for (int t = threadIdx.x; t < m; t += blockDim.x) pt[blk_cell[a + t]] = rhs[t];
 }
 
-// step 4: face and connection fluxes of one instance
-__global__ void k_flux_faces(const Inst* inst, int ii, const double* perm, const int* primal,
+__device__ inline long long faces_of(const Inst& I) {
+  long long nz = I.dim == 3 ? I.nz : 1;
+  return (long long)(I.nx + 1) * I.ny * nz + (long long)I.nx * (I.ny + 1) * nz +
+         (I.dim == 3 ? (long long)I.nx * I.ny * (nz + 1) : 0);
+}
+
+// steps 2 and 4 on the matrix faces of every listed instance: x faces
+// ((nx+1) ny nz, x fastest), then y faces, then z faces; positive along +axis
+__global__ void k_flux_faces(const Inst* inst, const int* list, int nlist, const long long* foff,
+                             long long ftot, const double* perm, const int* primal,
                              const double* pp, const double* pt, double* face) {
-  const Inst& I = inst[ii];
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ftot) return;
+  int li = 0, hi = nlist - 1;
+  while (li < hi) {
+    int mid = (li + hi + 1) >> 1;
+    if (foff[mid] <= g) li = mid; else hi = mid - 1;
+  }
+  const Inst& I = inst[list[li]];
+  long long f = g - foff[li];
   int nx = I.nx, ny = I.ny, nz = I.dim == 3 ? I.nz : 1;
   long long nfx = (long long)(nx + 1) * ny * nz, nfy = (long long)nx * (ny + 1) * nz;
-  long long nfz = I.dim == 3 ? (long long)nx * ny * (nz + 1) : 0;
-  long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nfx + nfy + nfz) return;
   const double* k = perm + I.m_off;
   int ro = I.row_off;
   int axis, i, j, l;
-  long long g = f;
-  if (g < nfx) { axis = 0; i = (int)(g % (nx + 1)); j = (int)((g / (nx + 1)) % ny); l = (int)(g / ((long long)(nx + 1) * ny)); }
-  else if ((g -= nfx) < nfy) { axis = 1; i = (int)(g % nx); j = (int)((g / nx) % (ny + 1)); l = (int)(g / ((long long)nx * (ny + 1))); }
-  else { g -= nfy; axis = 2; i = (int)(g % nx); j = (int)((g / nx) % ny); l = (int)(g / ((long long)nx * ny)); }
+  long long e = f;
+  if (e < nfx) { axis = 0; i = (int)(e % (nx + 1)); j = (int)((e / (nx + 1)) % ny); l = (int)(e / ((long long)(nx + 1) * ny)); }
+  else if ((e -= nfx) < nfy) { axis = 1; i = (int)(e % nx); j = (int)((e / nx) % (ny + 1)); l = (int)(e / ((long long)nx * (ny + 1))); }
+  else { e -= nfy; axis = 2; i = (int)(e % nx); j = (int)((e / nx) % ny); l = (int)(e / ((long long)nx * ny)); }
   int n_ax = axis == 0 ? nx : (axis == 1 ? ny : nz);
   int c_ax = axis == 0 ? i : (axis == 1 ? j : l);
   double area = axis == 0 ? I.dy * I.dz : (axis == 1 ? I.dx * I.dz : I.dx * I.dy);
@@ -242,122 +239,139 @@ __global__ void k_flux_faces(const Inst* inst, int ii, const double* perm, const
     const double* p = same ? pt : pp;
     out = T * (p[ro + lo_cell] - p[ro + hi_cell]);
   }
-  face[f] = out;
+  face[g] = out;
 }
 
-__global__ void k_flux_nnc(const Inst* inst, int ii, const int* nrow_m, const int* nrow_f,
-                           const double* nT, const int* ffa, const int* ffb, const double* ffT,
-                           const int* primal, const double* pp, const double* pt, double* out) {
-  const Inst& I = inst[ii];
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// steps 2 and 4 on the fracture connections: matrix-fracture (positive
+// matrix -> fracture), then fracture-fracture (positive lower -> higher cell)
+__global__ void k_flux_nnc(const Inst* inst, const int* list, int nlist, const long long* noff,
+                           long long ntot, const int* nrow_m, const int* nrow_f, const double* nT,
+                           const int* ffa, const int* ffb, const double* ffT, const int* primal,
+                           const double* pp, const double* pt, double* out) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ntot) return;
+  int li = 0, hi = nlist - 1;
+  while (li < hi) {
+    int mid = (li + hi + 1) >> 1;
+    if (noff[mid] <= g) li = mid; else hi = mid - 1;
+  }
+  const Inst& I = inst[list[li]];
+  long long t = g - noff[li];
   if (t < I.nnc) {
     long long k = I.nnc_off + t;
-    out[t] = nT[k] * (pp[nrow_m[k]] - pp[nrow_f[k]]);
-  } else if (t < (long long)I.nnc + I.nff) {
+    out[g] = nT[k] * (pp[nrow_m[k]] - pp[nrow_f[k]]);
+  } else {
     long long k = I.ff_off + (t - I.nnc);
     int a = ffa[k], b = ffb[k];
     const double* p = primal[a] == primal[b] ? pt : pp;
-    out[t] = ffT[k] * (p[a] - p[b]);
+    out[g] = ffT[k] * (p[a] - p[b]);
   }
 }
 
 }  // namespace
 
-int run_flux(Batch& b, int ii, const double* x_dev, double* face, double* nnc_out) {
-  cudaStream_t st = b.stream;
+// The R^FV coarse system of the reconstruction: the iteration's own when every
+// instance iterates with R^FV, otherwise a second one built on first use.
+int flux_prepare(Batch& b, const CoarseHost** ch) {
   bool all_fv = true;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
-  CoarseSys* cs = &b.cs[0];
-  if (!all_fv) {
-    if (!b.fv_ready) {
-      FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1]));
-      b.fv_ready = true;
-    }
-    cs = &b.cs[1];
+  if (all_fv) {
+    *ch = &b.csh[0];
+    return FAMS_OK;
   }
-  const Inst& I = b.h[ii];
-  const CoarseHost& chh = all_fv ? b.csh[0] : b.csh[1];
-  if (chh.bad[ii]) {
-    set_error("instance " + std::to_string(ii) + ": the finite-volume coarse system is "
-              "numerically singular (zero pivot at LU step " + std::to_string(chh.bad[ii] - 1) +
-              "); no conservative reconstruction");
-    return FAMS_EBREAKDOWN;
+  if (!b.fv_ready) {
+    FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1]));
+    b.fv_ready = true;
+    b.free_tmp();
   }
-  double* pp = b.r;   // work vectors: r = residual, dp = p', y = p~
+  *ch = &b.csh[1];
+  return FAMS_OK;
+}
+
+// Flux of the listed instances.  x: concatenated iterates (global rows);
+// face / nnc: concatenated outputs at foff / noff (per listed instance).
+int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* face,
+             const std::vector<long long>& foff, double* nnc, const std::vector<long long>& noff) {
+  cudaStream_t st = b.stream;
+  const CoarseHost* chh = nullptr;
+  FAMS_TRY(flux_prepare(b, &chh));
+  CoarseSys* cs = (chh == &b.csh[0]) ? &b.cs[0] : &b.cs[1];
+  int nl = (int)list.size();
+  if (nl == 0) return FAMS_OK;
+  double* pp = b.r;   // work vectors: r = p', y = p~, dp = residual
   double* pt = b.y;
   double* res = b.dp;
-  size_t smem = sizeof(double) * 2 * (size_t)I.nc;
+  int maxnc = 0;
+  for (int ii : list) maxnc = std::max(maxnc, b.h[ii].nc);
+  size_t smem = sizeof(double) * 2 * (size_t)maxnc;
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;  // static shared memory of the kernels
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_local, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-  fams::note_launch(), k_flux_stage<<<1, 512, smem, st>>>(b.d_inst, ii, *cs, b.rowptr, b.col, b.val, b.blk_ptr,
-                                     b.blk_cell, b.p_ptr, b.p_col, b.p_val, b.q, x_dev, res, pp);
+  int* dlist = nullptr;
+  FAMS_TRY(b.scratch((void**)&dlist, sizeof(int) * nl));
+  FAMS_CUDA(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+  fams::note_launch(), k_flux_stage<<<nl, 512, smem, st>>>(
+      b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.p_ptr, b.p_col,
+      b.p_val, b.q, x, res, pp);
   FAMS_CUDA(cudaGetLastError());
-  // local problems: split by size (shared memory or a bounded global workspace)
-  std::vector<int> hp(I.nc + 1);
-  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.blk_ptr + I.nc_off, sizeof(int) * (I.nc + 1),
+  // local problems of every primal block of the listed instances, split by
+  // size (shared memory or a bounded global workspace)
+  std::vector<int> hp(b.tot_nc + 1);
+  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
                             cudaMemcpyDeviceToHost, st));
   FAMS_CUDA(cudaStreamSynchronize(st));
   std::vector<int> small, large;
   size_t small_smem = 0;
   long long big = 0;
-  for (int c = 0; c < I.nc; ++c) {
-    long long m = hp[c + 1] - hp[c];
-    long long need = (m * m + m) * 8;
-    if (need + 1024 <= max_smem) { small.push_back(c); small_smem = std::max(small_smem, (size_t)need); }
-    else { large.push_back(c); big = std::max(big, m * m + m); }
+  for (int ii : list) {
+    const Inst& I = b.h[ii];
+    for (int c = I.nc_off; c < I.nc_off + I.nc; ++c) {
+      long long m = hp[c + 1] - hp[c];
+      long long need = (m * m + m) * 8;
+      if (need <= max_smem) { small.push_back(c); small_smem = std::max(small_smem, (size_t)need); }
+      else { large.push_back(c); big = std::max(big, m * m + m); }
+    }
   }
   int* lst = nullptr;
-  FAMS_CUDA(cudaMalloc(&lst, sizeof(int) * (I.nc + 1)));
-  double* work = nullptr;
-  int status = FAMS_OK;
+  FAMS_TRY(b.scratch((void**)&lst, sizeof(int) * (small.size() + large.size() + 1)));
   if (!small.empty()) {
-    cudaMemcpyAsync(lst, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice, st);
+    FAMS_CUDA(cudaMemcpyAsync(lst, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice, st));
     fams::note_launch(), k_flux_local<<<(int)small.size(), 256, small_smem, st>>>(
-        b.d_inst, ii, lst, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD, b.qD, b.q,
+        b.d_inst, b.B, b.off_nc, lst, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD, b.q,
         b.primal, b.node_cell, pp, pt, nullptr, 0, b.d_err);
   }
   if (!large.empty()) {
     long long per = std::max(1LL, (1LL << 26) / std::max(big, 1LL));
-    if (cudaMalloc(&work, sizeof(double) * big * std::min<long long>(per, large.size())) != cudaSuccess) {
-      cudaFree(lst);
-      set_error("flux workspace allocation failed");
-      return FAMS_ENOMEM;
-    }
+    double* work = nullptr;
+    FAMS_TRY(b.scratch((void**)&work, sizeof(double) * big * std::min<long long>(per, large.size())));
     int* l2 = lst + small.size();
-    cudaMemcpyAsync(l2, large.data(), sizeof(int) * large.size(), cudaMemcpyHostToDevice, st);
+    FAMS_CUDA(cudaMemcpyAsync(l2, large.data(), sizeof(int) * large.size(), cudaMemcpyHostToDevice, st));
     for (size_t o = 0; o < large.size(); o += per) {
       int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
-      fams::note_launch(), k_flux_local<<<cnt, 256, 0, st>>>(b.d_inst, ii, l2 + o, b.blk_ptr, b.blk_cell, b.rowptr,
-                                        b.col, b.val, b.TD, b.qD, b.q, b.primal, b.node_cell, pp,
-                                        pt, work, big, b.d_err);
+      fams::note_launch(), k_flux_local<<<cnt, 256, 0, st>>>(
+          b.d_inst, b.B, b.off_nc, l2 + o, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD,
+          b.q, b.primal, b.node_cell, pp, pt, work, big, b.d_err);
     }
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) status = FAMS_ECUDA;
-  long long nfaces = (long long)(I.nx + 1) * I.ny * (I.dim == 3 ? I.nz : 1) +
-                     (long long)I.nx * (I.ny + 1) * (I.dim == 3 ? I.nz : 1) +
-                     (I.dim == 3 ? (long long)I.nx * I.ny * (I.nz + 1) : 0);
-  if (status == FAMS_OK) {
-    fams::note_launch(), k_flux_faces<<<grid_for(nfaces, 256), 256, 0, st>>>(b.d_inst, ii, b.perm, b.primal, pp, pt,
-                                                        face);
-    long long nn = (long long)I.nnc + I.nff;
-    if (nn > 0)
-      fams::note_launch(), k_flux_nnc<<<grid_for(nn, 256), 256, 0, st>>>(b.d_inst, ii, b.nnc_row_m, b.nnc_row_f,
-                                                    b.nnc_T, b.ff_a, b.ff_b, b.ff_T, b.primal, pp,
-                                                    pt, nnc_out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) status = FAMS_ECUDA;
-  }
-  cudaStreamSynchronize(st);
-  cudaFree(lst);
-  if (work) cudaFree(work);
-  if (status != FAMS_OK) {
-    set_error(std::string("flux kernels: ") + cudaGetErrorString(e));
-    return status;
-  }
+  FAMS_CUDA(cudaGetLastError());
+  long long* dfo = nullptr;
+  long long* dno = nullptr;
+  FAMS_TRY(b.scratch((void**)&dfo, sizeof(long long) * (nl + 1)));
+  FAMS_TRY(b.scratch((void**)&dno, sizeof(long long) * (nl + 1)));
+  FAMS_CUDA(cudaMemcpyAsync(dfo, foff.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemcpyAsync(dno, noff.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, st));
+  if (foff[nl] > 0)
+    fams::note_launch(), k_flux_faces<<<grid_for(foff[nl], 256), 256, 0, st>>>(
+        b.d_inst, dlist, nl, dfo, foff[nl], b.perm, b.primal, pp, pt, face);
+  if (noff[nl] > 0)
+    fams::note_launch(), k_flux_nnc<<<grid_for(noff[nl], 256), 256, 0, st>>>(
+        b.d_inst, dlist, nl, dno, noff[nl], b.nnc_row_m, b.nnc_row_f, b.nnc_T, b.ff_a, b.ff_b,
+        b.ff_T, b.primal, pp, pt, nnc);
+  FAMS_CUDA(cudaGetLastError());
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  b.free_tmp();
   return b.check_err("flux reconstruction");
 }
 

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   double rel = 0.0;
   // SM cycles per phase (thread 0, between barriers): residual, coarse
   // (restriction + band solve), prolongation + r1, L sweep, U sweep
-  long long cyc[5] = {0, 0, 0, 0, 0};
+  long long cyc[6] = {0, 0, 0, 0, 0, 0};
   long long t0 = clock64();
   for (;;) {
     // step 3: r = q - A p
@@ -309,6 +309,8 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
       a.crhs[co + perm[k]] = s0 + s1;
     }
     __syncthreads();
+    long long t1b = clock64();
+    cyc[1] += t1b - t1;
     coarse_solve(AB, ipiv, nc, kl, ku, yb, buf, pbuf);
     for (int k = threadIdx.x; k < nc; k += T) {
       ecs[perm[k]] = yb[k];
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     }
     __syncthreads();
     long long t2 = clock64();
-    cyc[1] += t2 - t1;
+    cyc[2] += t2 - t1b;
     // dp1 = P e_c
     for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
 #pragma unroll
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     rows_residual(a, ro, n, a.r, a.dp, a.y, false, a.ylev);
     __syncthreads();
     long long t3 = clock64();
-    cyc[2] += t3 - t2;
+    cyc[3] += t3 - t2;
     // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
     SweepRow cur, nxt;
     sweep_load(a, lp, 0, nlev, true, cur);
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
       cur = nxt;
     }
     long long t4 = clock64();
-    cyc[3] += t4 - t3;
+    cyc[4] += t4 - t3;
     // U sweep and step 8: p = p + dp1 + dp2
     sweep_load(a, lp, nlev - 1, nlev, false, cur);
     for (int l = nlev - 1; l >= 0; --l) {
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
       cur = nxt;
     }
     t0 = clock64();
-    cyc[4] += t0 - t4;
+    cyc[5] += t0 - t4;
     ++it;
   }
   if (threadIdx.x == 0) {
@@ -400,8 +402,8 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     a.stat[STAT_W * ii + 1] = rel;
     a.stat[STAT_W * ii + 2] = (rel <= a.tol) ? 1.0 : 0.0;
     a.stat[STAT_W * ii + 3] = qn;
-    for (int k = 0; k < 5; ++k) a.stat[STAT_W * ii + 4 + k] = (double)cyc[k];
-    a.stat[STAT_W * ii + 9] = a.cs.bad[ii] ? 1.0 : 0.0;  // singular coarse system
+    for (int k = 0; k < 6; ++k) a.stat[STAT_W * ii + 4 + k] = (double)cyc[k];
+    a.stat[STAT_W * ii + STAT_BAD] = a.cs.bad[ii] ? 1.0 : 0.0;  // singular coarse system
   }
 }
 

@@ -23,7 +23,7 @@ Q = dict(NNC_FRAC=1, NNC_MATRIX=2, NNC_AREA=3, NNC_DIST=4, FF_A=5, FF_B=6, FF_T=
          A_ROWPTR=8, A_COL=9, A_VAL=10, Q=11, RANK=12, PRIMAL=13, NODE_CELL=14,
          P_ROWPTR=15, P_COL=16, P_VAL=17, AC=18, ILU_VAL=19, LEVELS=20,
          COARSE_PERM=21, COARSE_IPIV=22, BAND_KLKU=23, BAND=24, HISTORY=25,
-         LAST_DP1=26, LAST_DP2=27, LAST_RC=28, LAST_EC=29, STAGE_CYCLES=30)
+         LAST_DP1=26, LAST_DP2=27, LAST_RC=28, LAST_EC=29, STAGE_CYCLES=30, SETUP_MS=31)
 _INT_QUERIES = {1, 2, 5, 6, 8, 9, 12, 13, 14, 15, 16, 20, 21, 22, 23}
 
 
@@ -70,6 +70,8 @@ def _load():
     lib.fams_solve_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double,
                                      P(fams_stats)]
     lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fams_flux_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p),
+                                    P(C.c_int)]
     lib.fams_query.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong]
     lib.fams_num_instances.argtypes = [C.c_void_p]
     lib.fams_destroy.argtypes = [C.c_void_p]
@@ -212,6 +214,17 @@ class Context:
         return [dict(iterations=st[i].iterations, rel_residual=st[i].rel_residual,
                      converged=bool(st[i].converged), solve_ms=st[i].solve_ms)
                 for i in range(n)]
+
+    def flux_batch_ptr(self, x_ptrs, face_ptrs, nnc_ptrs):
+        """fams_flux_batch on caller-owned buffers (raw pointers, host or
+        device); returns the per-instance status list."""
+        n = self.n
+        st = (C.c_int * n)()
+        xp = (C.c_void_p * n)(*[int(p) for p in x_ptrs])
+        fp = (C.c_void_p * n)(*[int(p) for p in face_ptrs])
+        npp = (C.c_void_p * n)(*[int(p) for p in nnc_ptrs])
+        _check(lib.fams_flux_batch(self.h, xp, fp, npp, st), allow=(EBREAKDOWN,))
+        return list(st)
 
     def flux_ptr(self, inst, x_ptr, face_ptr, nnc_ptr):
         """fams_flux on caller-owned buffers given as raw pointers (host or device)."""

@@ -230,6 +230,24 @@ def test_batch_matches_single(built):
         assert np.linalg.norm(x1[0] - xb[i]) / np.linalg.norm(x1[0]) < 1e-10
 
 
+def test_flux_batch_matches_single():
+    """fams_flux_batch over a batch equals fams_flux of each instance alone."""
+    fams = _fams()
+    probs = [_case("2d32", 0, 1), _case("2d64", 3, 1), _case("3d", 1, 1)]
+    with fams.Context(probs) as cb:
+        xs, _ = cb.solve(tol=1e-6)
+        S = [cb.sizes(i) for i in range(len(probs))]
+        F = [np.zeros(s["n_faces"]) for s in S]
+        N = [np.zeros(max(1, s["n_nnc"])) for s in S]
+        st = cb.flux_batch_ptr([x.ctypes.data for x in xs], [f.ctypes.data for f in F],
+                               [m.ctypes.data for m in N])
+        assert st == [0, 0, 0]
+        for i in range(len(probs)):
+            f1, n1 = cb.flux(xs[i], i)
+            np.testing.assert_array_equal(F[i], f1)
+            np.testing.assert_array_equal(N[i][: S[i]["n_nnc"]], n1)
+
+
 def test_rejects_bad_input():
     fams = _fams()
     p = _case("2d32")
