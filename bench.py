@@ -29,6 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s to rel. residual 1e-8 (served vs plain F-AMS, one GB300); p50/p99 ms"
+# DRAM bytes / algorithmic bytes of k_solve from the ncu capture in
+# profiles/k_solve_2d256_batch8_10sweeps.md (None once the kernel changes)
+TRAFFIC_RATIO = 2230.4 / 2262.2
 WORKLOAD = ("2D 256x256 (configs[1] shape): log10 k std 2 corr 16, 30 fractures L~U[20,120], "
             "coarsening 8x8, d_min 8, 4 coupling strategies x T_ratio {1e2,1e4}, R^FE, alpha 1e-2, "
             "ILU(0), tol 1e-8, + flux reconstruction")
@@ -320,7 +323,8 @@ def main():
                      "iterations_median": statistics.median(iters), "iterations_max": max(iters)},
         "roofline": {"kernel": "k_solve (persistent Table 1 loop, one CTA per instance)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": None if TRAFFIC_RATIO is None else byts * TRAFFIC_RATIO,
                      "kernel_ms": k_ms, "algorithmic_bytes": byts,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else
                                     "fallback 6800 GB/s"},
