@@ -137,6 +137,37 @@ int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_sta
 int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
                      fams_stats* st);
 
+/* Limits of fams_solve_static (its fixed work array, about 13 MB per GPU). */
+#define FAMS_STATIC_MAX_ROWS 262144   /* n_matrix + n_frac of the instance */
+#define FAMS_STATIC_MAX_COARSE 16384  /* n_coarse of the instance */
+#define FAMS_STATIC_MAX_ITER 16383    /* the instance's max_iter */
+
+/* fams_solve_static - the solve of fams_solve (same arguments, same result)
+   for callers that cannot allocate device memory when they solve: a code
+   that hands the free device memory to its own pool allocator and leaves
+   none to libraries, or a time-step loop that must not enter cudaMalloc or
+   cudaFree (both can synchronise the device, and can fail under memory
+   pressure mid-run).  The paper has no counterpart; it is a deployment
+   variant of the same iteration.
+   It allocates nothing, on any call: the iteration's work vectors (the
+   right-hand side with its Dirichlet terms, iterate, residual, multiscale
+   and ILU corrections, the coarse vectors, status words and residual
+   history) live in one device array compiled into the library, of fixed size
+   (the FAMS_STATIC_MAX_* limits; every GPU that loads the library holds it
+   until the process exits).  The first call on a device looks up that
+   array's address on the context's device (which also loads the library's
+   kernels there): make the first call on each device before any stream
+   capture starts.
+   ctx must be a single-instance context; x (in initial guess, out pressure)
+   and rhs (nullable) may be host or device memory.  Instances above a limit
+   are rejected with FAMS_ECAPACITY before anything runs.  Every call, from any
+   context, shares the one array per device and it keeps the last call's
+   contents; each call clears the status words and writes every other value
+   it reads.  Calls that overlap on the GPU (other threads, other streams)
+   race on the array: serialise them.  stats.solve_ms is host wall time of the
+   launch and its completion. */
+int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st);
+
 /* fams_flux - conservative fine-scale flux field from an iterate x of
    instance `inst`: one finite-volume multiscale stage, then a local TPFA
    problem per primal block with the block-boundary fluxes as Neumann data

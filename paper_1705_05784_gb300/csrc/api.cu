@@ -223,6 +223,7 @@ int fetch(const Batch& b, const T* src, long long n, std::vector<T>& out) {
 }  // namespace
 
 int make_q(Batch& b, const double* rhs_dev);
+int solve_static(Batch& b, const double* rhs, double* x, double tol, fams_stats* st);
 
 namespace {
 
@@ -400,6 +401,16 @@ int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_sta
   const double* r[1] = {rhs};
   double* xx[1] = {x};
   return fams_solve_batch(ctx, r, xx, tol, st);
+}
+
+int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st) {
+  if (!ctx || ctx->b.B != 1) {
+    set_error("fams_solve_static needs a single-instance context");
+    return FAMS_EINVAL;
+  }
+  if (!x) { set_error("x is null"); return FAMS_EINVAL; }
+  if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return FAMS_EINVAL; }
+  return solve_static(ctx->b, rhs, x, tol, st);
 }
 
 int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, double* nnc_flux) {

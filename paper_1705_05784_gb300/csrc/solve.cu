@@ -16,6 +16,9 @@
 //    (indices, factors, right-hand side) is loaded before the barrier, so a
 //    level costs one gather of the previous level's results.
 #include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <mutex>
 
 #include "batch.cuh"
 
@@ -480,6 +483,161 @@ int run_solve(Batch& b, double tol, float* ms) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return FAMS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The same iteration with its work vectors in a fixed device array, for
+// callers that cannot allocate device memory when they solve.  Layout in
+// doubles, every part starting on a 256-byte boundary:
+//   q, x, r, dp, y, ylev   STATIC_ROWS each
+//   crhs, csol             STATIC_COARSE each
+//   stat                   STATIC_STAT (STAT_W used)
+//   hist                   STATIC_HIST
+namespace {
+constexpr long long STATIC_ROWS = FAMS_STATIC_MAX_ROWS;
+constexpr long long STATIC_COARSE = FAMS_STATIC_MAX_COARSE;
+constexpr long long STATIC_STAT = 32;
+constexpr long long STATIC_HIST = (long long)FAMS_STATIC_MAX_ITER + 1;
+constexpr long long STATIC_DOUBLES = 6 * STATIC_ROWS + 2 * STATIC_COARSE + STATIC_STAT + STATIC_HIST;
+static_assert(STATIC_ROWS % 32 == 0 && STATIC_COARSE % 32 == 0 && STATIC_STAT % 32 == 0,
+              "parts of the static work array must stay 256-byte aligned");
+static_assert(STATIC_STAT >= STAT_W, "status words do not fit");
+constexpr int MAX_DEVICES = 64;
+}  // namespace
+
+// In host code this name only stands for the device array: its device address
+// comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) double g_solve_static_work[STATIC_DOUBLES];
+
+namespace {
+std::mutex g_static_mu;
+double* g_static_ptr[MAX_DEVICES] = {};
+
+// device address of the work array on `dev` (current device); looked up on
+// the first call on each device
+int static_work(int dev, double** out) {
+  if (dev < 0 || dev >= MAX_DEVICES) {
+    set_error("device ordinal beyond the static work table");
+    return FAMS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_solve_static_work);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress of the static work array: ") +
+                cudaGetErrorString(e));
+      return FAMS_ECUDA;
+    }
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return FAMS_OK;
+}
+
+int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, fams_stats* st) {
+  const Inst& I = b.h[0];
+  if (I.n > STATIC_ROWS) {
+    set_error("instance has " + std::to_string(I.n) + " unknowns; fams_solve_static holds at most " +
+              std::to_string(STATIC_ROWS));
+    return FAMS_ECAPACITY;
+  }
+  if (I.nc > STATIC_COARSE) {
+    set_error("instance has " + std::to_string(I.nc) + " coarse unknowns; fams_solve_static holds "
+              "at most " + std::to_string(STATIC_COARSE));
+    return FAMS_ECAPACITY;
+  }
+  if ((long long)I.max_iter + 1 > STATIC_HIST) {
+    set_error("max_iter " + std::to_string(I.max_iter) + " above fams_solve_static's limit " +
+              std::to_string(STATIC_HIST - 1));
+    return FAMS_ECAPACITY;
+  }
+  if (b.csh[0].kl[0] + b.csh[0].ku[0] + 1 > BAND_BUF) {
+    set_error("coarse band wider than the staged band buffer");
+    return FAMS_ECAPACITY;
+  }
+  size_t smem = sizeof(double) * (2 * (size_t)I.nc + 2 * BAND_BUF);
+  int max_smem = 0;
+  FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  if ((long long)smem + 2048 > max_smem) {
+    set_error("coarse system too large for the shared-memory coarse solve");
+    return FAMS_ECAPACITY;
+  }
+  double* w = nullptr;
+  FAMS_TRY(static_work(b.device, &w));
+  double* q = w;
+  double* xs = w + STATIC_ROWS;
+  double* dp = w + 3 * STATIC_ROWS;
+  double* stat = w + 6 * STATIC_ROWS + 2 * STATIC_COARSE;
+
+  SolveArgs a;
+  a.inst = b.d_inst;
+  a.cs = b.cs[0];
+  a.rowptr = b.rowptr; a.col = b.col; a.val = b.val; a.diag = b.diag;
+  a.p_ptr = b.p_ptr; a.p_col = b.p_col; a.p_val = b.p_val;
+  a.pt_ptr = b.pt_ptr; a.pt_col = b.pt_col; a.pt_val = b.pt_val;
+  a.blk_ptr = b.blk_ptr; a.blk_cell = b.blk_cell;
+  a.F = b.ilu; a.lev_off = b.lev_off; a.lev_ptr = b.lev_ptr; a.lev_rows = b.lev_rows;
+  a.q = q; a.x = xs; a.r = w + 2 * STATIC_ROWS; a.dp = dp; a.y = w + 4 * STATIC_ROWS;
+  a.ylev = w + 5 * STATIC_ROWS;
+  a.crhs = w + 6 * STATIC_ROWS; a.csol = w + 6 * STATIC_ROWS + STATIC_COARSE;
+  a.stat = stat;
+  a.hist = stat + STATIC_STAT; a.hist_len = STATIC_HIST;
+  a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
+  a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
+  a.ntot = b.tot_row;
+  a.tol = tol;
+
+  // the array keeps the previous call's values: clear the status words; q,
+  // the iterate and the staged rhs are written below, every other vector is
+  // written by the kernel before it is read
+  FAMS_CUDA(cudaMemsetAsync(stat, 0, sizeof(double) * STATIC_STAT, b.stream));
+  if (rhs)
+    FAMS_CUDA(cudaMemcpyAsync(dp, rhs, sizeof(double) * I.n, cudaMemcpyDefault, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(xs, x, sizeof(double) * I.n, cudaMemcpyDefault, b.stream));
+  fams::note_launch(),
+      k_make_q<<<grid_for(I.n, 256), 256, 0, b.stream>>>(I.n, rhs ? dp : nullptr, b.qD, q);
+  FAMS_CUDA(cudaGetLastError());
+  FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - 2048));
+  auto t0 = std::chrono::steady_clock::now();
+  fams::note_launch(), k_solve<<<1, SOLVE_T, smem, b.stream>>>(a);
+  FAMS_CUDA(cudaGetLastError());
+  double hs[STAT_W];
+  FAMS_CUDA(cudaMemcpyAsync(hs, stat, sizeof(double) * STAT_W, cudaMemcpyDeviceToHost, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(x, xs, sizeof(double) * I.n, cudaMemcpyDefault, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (st) {
+    st->iterations = (int)hs[0];
+    st->rel_residual = hs[1];
+    st->converged = hs[2] > 0.5;
+    st->solve_ms = ms;
+  }
+  if (hs[STAT_BAD] > 0.5) {
+    set_error("numerically singular coarse system (zero pivot at LU step " +
+              std::to_string(b.csh[0].bad[0] - 1) + ")");
+    return FAMS_EBREAKDOWN;
+  }
+  if (!std::isfinite(hs[1])) {
+    set_error("the iteration produced a non-finite residual");
+    return FAMS_EBREAKDOWN;
+  }
+  if (hs[2] < 0.5) {
+    set_error("max_iter reached before the tolerance");
+    return FAMS_ENOCONV;
+  }
+  return FAMS_OK;
+}
+}  // namespace
+
+int solve_static(Batch& b, const double* rhs, double* x, double tol, fams_stats* st) {
+  int prev = -1;
+  FAMS_CUDA(cudaGetDevice(&prev));
+  if (prev != b.device) FAMS_CUDA(cudaSetDevice(b.device));
+  int s = solve_static_on_device(b, rhs, x, tol, st);
+  if (prev != b.device) cudaSetDevice(prev);
+  return s;
 }
 
 }  // namespace fams

@@ -69,6 +69,8 @@ def _load():
     lib.fams_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, P(fams_stats)]
     lib.fams_solve_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double,
                                      P(fams_stats)]
+    lib.fams_solve_static.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                      P(fams_stats)]
     lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fams_flux_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p),
                                     P(C.c_int)]
@@ -214,6 +216,20 @@ class Context:
         return [dict(iterations=st[i].iterations, rel_residual=st[i].rel_residual,
                      converged=bool(st[i].converged), solve_ms=st[i].solve_ms)
                 for i in range(n)]
+
+    def solve_static(self, rhs=None, x0=None, tol=1e-8):
+        """fams_solve_static on this single-instance context: the solve of
+        fams_solve with the library's fixed work array instead of any
+        allocation.  Returns (pressure, stats dict)."""
+        N = self.sizes(0)["n_matrix"] + self.sizes(0)["n_frac"]
+        x = np.ascontiguousarray(x0 if x0 is not None else np.zeros(N), np.float64).copy()
+        r = None if rhs is None else np.ascontiguousarray(rhs, np.float64)
+        st = fams_stats()
+        s = lib.fams_solve_static(self.h, None if r is None else r.ctypes.data_as(C.c_void_p),
+                                  x.ctypes.data_as(C.c_void_p), tol, C.byref(st))
+        _check(s, allow=(ENOCONV,))
+        return x, dict(iterations=st.iterations, rel_residual=st.rel_residual,
+                       converged=bool(st.converged), solve_ms=st.solve_ms, status=s)
 
     def flux_batch_ptr(self, x_ptrs, face_ptrs, nnc_ptrs):
         """fams_flux_batch on caller-owned buffers (raw pointers, host or
