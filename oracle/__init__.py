@@ -11,8 +11,8 @@ Modules:
   coarsen   - primal/dual coarse grids, wirebasket ranks, Table 2 BFS
   basis     - prolongation P by the staged rule and by Appendix A's formulas,
               truncation
-  solver    - R, A_c = R A P, LU, ILU(0), Table 1 iteration, flux
-              reconstruction
+  solver    - R, A_c = R A P, LU, ILU(0), Table 1 iteration, GMRES with the
+              two-stage step as preconditioner, flux reconstruction
 
 Parity unpinned: the paper's printed numbers (single-step error norms of
 Sec. 4.2, Table 3 timings) depend on permeability maps and fracture networks
@@ -62,6 +62,10 @@ def build(prob, route="staged"):
 
 def run(prob, x0=None, history=True):
     g, sysm, c, P, st = build(prob)
-    p, it, rr, ok, hist = _solver.two_stage_solve(st, x0=x0, tol=prob.tol,
-                                                   max_iter=prob.max_iter, history=history)
+    if getattr(prob, "krylov", 0) == 1:
+        p, it, rr, ok, hist = _solver.gmres_solve(st, x0=x0, tol=prob.tol, max_iter=prob.max_iter,
+                                                  restart=prob.restart, history=history)
+    else:
+        p, it, rr, ok, hist = _solver.two_stage_solve(st, x0=x0, tol=prob.tol,
+                                                       max_iter=prob.max_iter, history=history)
     return OracleResult(g, sysm, c, P, st, p, it, rr, ok, hist)

@@ -120,6 +120,82 @@ def two_stage_solve(s, x0=None, tol=1e-8, max_iter=200, smoother=True, history=F
     return p, it, hist[-1], hist[-1] <= tol, (hist if history else None)
 
 
+def precondition(s, r, smoother=True):
+    """The two-stage step of Table 1 as an operator on a residual r (steps 5-7
+    with p = 0): z = dp1 + dp2, dp1 = P A_c^-1 R r, dp2 = (LU)^-1 (r - A dp1).
+    Linear in r, so it can precondition a Krylov method (Sec. 4.5, 4.6)."""
+    dp1 = s.P @ sla.lu_solve(s.lu, s.R @ r)
+    if not smoother:
+        return dp1
+    return dp1 + ilu0_apply(s.F, r - s.A @ dp1)
+
+
+def gmres_solve(s, x0=None, tol=1e-8, max_iter=200, restart=30, history=False):
+    """GMRES(m) with the two-stage step as right preconditioner: F-AMS as a
+    preconditioner for GMRES, the paper's benchmark mode (Sec. 4.5, 4.6, the
+    method of Saad's "Iterative Methods for Sparse Linear Systems", right
+    preconditioning, Arnoldi by modified Gram-Schmidt, least-squares problem
+    by Givens rotations).
+
+    Every Arnoldi step is one iteration (one preconditioner application).
+    history[k] is the relative residual after k iterations: the true one at
+    the start of each cycle, the least-squares one |g_{j+1}| / ||q|| inside a
+    cycle.  A cycle ends when that estimate reaches tol, after `restart`
+    steps, or at max_iter; then x = x0 + M^-1 V y and the true residual
+    decides whether to stop.  Returns (p, iterations, final true relative
+    residual, converged flag, history)."""
+    A, q = s.A, s.q
+    n = A.shape[0]
+    m = int(restart)
+    x = np.zeros(n) if x0 is None else np.asarray(x0, np.float64).copy()
+    qn = np.linalg.norm(q)
+    qn = qn if qn > 0 else 1.0
+    r = q - A @ x
+    beta = np.linalg.norm(r)
+    hist = [beta / qn]
+    it = 0
+    while hist[-1] > tol and it < max_iter and beta > 0.0:
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        V[0] = r / beta
+        g[0] = beta
+        k = 0
+        while k < m and it < max_iter:
+            w = A @ precondition(s, V[k])
+            for i in range(k + 1):                     # modified Gram-Schmidt
+                H[i, k] = V[i] @ w
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = np.linalg.norm(w)
+            if H[k + 1, k] > 0.0:
+                V[k + 1] = w / H[k + 1, k]
+            for i in range(k):                         # previous rotations
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t
+            d = np.hypot(H[k, k], H[k + 1, k])         # new rotation
+            cs[k], sn[k] = H[k, k] / d, H[k + 1, k] / d
+            H[k, k] = d
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            k += 1
+            it += 1
+            hist.append(abs(g[k]) / qn)
+            if hist[-1] <= tol:
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):                 # back substitution
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + precondition(s, V[:k].T @ y)
+        r = q - A @ x
+        beta = np.linalg.norm(r)
+        hist[-1] = beta / qn                           # the true residual ends a cycle
+    return x, it, hist[-1], hist[-1] <= tol, (hist if history else None)
+
+
 def multiscale_stage(s, x):
     """p' = x + P (R A P)^-1 R (q - A x)  (one multiscale stage)."""
     r = s.q - s.A @ x

@@ -52,6 +52,9 @@ class Problem:
     alpha: float = 0.0
     tol: float = 1e-8
     max_iter: int = 200
+    krylov: int = 0                  # 0 the Table 1 loop, 1 GMRES(restart)
+    restart: int = 30
+    precision: int = 0               # 0 FP64, 1 FP32 inner stages
     rhs: np.ndarray = None           # sources, length N (matrix then fracture); None = 0
     name: str = ""
     meta: dict = field(default_factory=dict)
@@ -144,14 +147,15 @@ def config_2d_256(seed=2, tratio=1e4, basis=0, restriction=0, n_fracs=30, alpha=
 
 
 def config_2d(n, sigma, corr, n_fracs, flen, tratio, coarsen, dmin, seed, basis=0,
-              restriction=0, alpha=0.0):
-    """Generic 2D instance of the same family at any size (tests use small ones)."""
+              restriction=0, alpha=0.0, **solver_opts):
+    """Generic 2D instance of the same family at any size (tests use small ones);
+    solver_opts sets further Problem fields (krylov, restart, precision, ...)."""
     perm = 10.0 ** gaussian_field((n, n), sigma, corr, seed)
     fr = random_segments(n_fracs, (n, n), flen, seed + 1000) if n_fracs else np.zeros((0, 4))
     return Problem(dim=2, nx=n, ny=n, nz=1, perm=perm, fracs=fr,
                    kf=np.full(len(fr), float(tratio)), coarsen=(coarsen, coarsen, 1),
                    frac_dmin=dmin, basis=basis, restriction=restriction, alpha=alpha,
-                   name=f"2d-{n}-{n_fracs}frac-s{seed}")
+                   name=f"2d-{n}-{n_fracs}frac-s{seed}", **solver_opts)
 
 
 def config_3d(nx, ny, nz, sigma, corr, n_plates, side, tratio, coarsen, dmin, cz, seed,

@@ -133,3 +133,77 @@ def test_flux_of_exact_solution_is_two_point_flux():
     ci, cj, cT = solver.connections(sysm, p)
     np.testing.assert_allclose(flux, cT * (x[ci] - x[cj]), rtol=0,
                                atol=1e-9 * np.abs(flux).max())
+
+
+# --- GMRES with the two-stage step as right preconditioner (Sec. 4.5, 4.6) ---
+
+def _minres_over_krylov(st, x0, k):
+    """Brute force: min ||q - A (x0 + M^-1 K c)|| over the k-dimensional Krylov
+    space K = span{r0, (A M^-1) r0, ...} (the defining property of GMRES),
+    from explicit power vectors and an SVD least-squares solve."""
+    A, q = st.A, st.q
+    r0 = q - A @ x0
+    cols, v = [], r0 / np.linalg.norm(r0)
+    for _ in range(k):
+        cols.append(v)
+        v = A @ solver.precondition(st, v)
+        v = v / np.linalg.norm(v)
+    Z = np.stack([solver.precondition(st, c) for c in cols], axis=1)
+    AZ = A @ Z
+    c, *_ = np.linalg.lstsq(AZ, r0, rcond=None)
+    return np.linalg.norm(r0 - AZ @ c)
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_gmres_minimises_the_residual_over_the_krylov_space(variant):
+    p = _small(variant=variant)
+    g, sysm, c, P, st = oracle.build(p)
+    x0 = np.random.default_rng(3).uniform(0, 1, sysm.n)
+    qn = np.linalg.norm(sysm.q)
+    for k in range(1, 6):
+        x, it, rr, ok, hist = solver.gmres_solve(st, x0=x0, tol=0.0, max_iter=k, restart=30,
+                                                 history=True)
+        assert it == k and len(hist) == k + 1
+        best = _minres_over_krylov(st, x0, k)
+        assert abs(rr * qn - best) <= 1e-7 * best
+        # the least-squares estimate inside the cycle is the true residual too
+        assert abs(np.linalg.norm(sysm.q - sysm.A @ x) / qn - rr) <= 1e-12
+
+
+def test_gmres_residuals_do_not_increase_within_a_cycle():
+    p = _small(variant=1)
+    g, sysm, c, P, st = oracle.build(p)
+    x, it, rr, ok, hist = solver.gmres_solve(st, tol=1e-10, max_iter=25, restart=25, history=True)
+    assert np.all(np.diff(hist) <= 1e-14)
+
+
+def test_gmres_with_exact_preconditioner_takes_one_iteration():
+    # coarsening ratio 1: P = I and the coarse solve is a direct solve of A
+    p = inputs.config_2d(12, 1.0, 3.0, 0, (1, 2), 1.0, 1, 1, seed=2, krylov=1)
+    r = oracle.run(p)
+    assert r.iters == 1 and r.rel_res < 1e-13
+
+
+def test_gmres_terminates_on_a_tiny_system():
+    """Without restarts GMRES finds the solution in at most n steps."""
+    p = inputs.config_2d(6, 1.0, 2.0, 1, (2, 4), 1e2, 3, 3, seed=5)
+    g, sysm, c, P, st = oracle.build(p)
+    n = sysm.n
+    x, it, rr, ok, hist = solver.gmres_solve(st, tol=1e-11, max_iter=n, restart=n, history=True)
+    assert ok and it <= n
+    xd = spla.spsolve(sysm.A.tocsc(), sysm.q)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+
+
+@pytest.mark.parametrize("restart", [5, 30])
+def test_gmres_converges_to_the_direct_solution_with_restarts(restart):
+    p = _small(variant=2, krylov=1, restart=restart)
+    r = oracle.run(p)
+    assert r.converged
+    # every cycle ends on a true residual, so the history's last entry is one
+    assert abs(np.linalg.norm(r.sysm.q - r.sysm.A @ r.p) / np.linalg.norm(r.sysm.q)
+               - r.rel_res) < 1e-14
+    x = spla.spsolve(r.sysm.A.tocsc(), r.sysm.q)
+    assert np.linalg.norm(r.p - x) / np.linalg.norm(x) < 1e-6
+    rich = oracle.run(_small(variant=2))
+    assert r.iters < rich.iters
