@@ -32,19 +32,23 @@ METRIC = "solves/s to rel. residual 1e-8 (served vs plain F-AMS, one GB300); p50
 # DRAM bytes / algorithmic bytes of k_solve from the ncu capture in
 # profiles/k_solve_2d256_batch8_10sweeps.md (None once the kernel changes)
 TRAFFIC_RATIO = 2230.4 / 2262.2
-WORKLOAD = ("2D 256x256 (configs[1] shape): log10 k std 2 corr 16, 30 fractures L~U[20,120], "
-            "coarsening 8x8, d_min 8, 4 coupling strategies x T_ratio {1e2,1e4}, R^FE, alpha 1e-2, "
-            "ILU(0), tol 1e-8, + flux reconstruction")
+WORKLOAD = ("2D 256x256: log10 k std 2 corr 16, 30 fractures L~U[20,120], coarsening 8x8, "
+            "d_min 8, 4 coupling strategies x T_ratio {1e2,1e4,1e6,1e8}, R^FE, alpha 1e-2, "
+            "ILU(0), GMRES(30) with the two-stage preconditioner, tol 1e-8, + flux reconstruction")
 TOL = 1e-8
+TRATIOS = (1e2, 1e4, 1e6, 1e8)
 
 
-def problems(batch, seed0, max_iter=400):
+def problems(batch, seed0, max_iter=400, krylov=1, restart=30):
+    """The bench workload: instance i has coupling strategy i % 4 and
+    T_ratio 1e2..1e8 by (i // 4) % 4, seeds seed0 + i."""
     from paper_1705_05784_gb300 import inputs
     out = []
     for i in range(batch):
-        p = inputs.config_2d_256(seed=seed0 + i, tratio=(1e2, 1e4)[(i // 4) % 2], basis=i % 4,
-                                 restriction=1, alpha=1e-2)
+        p = inputs.config_2d_256(seed=seed0 + i, tratio=TRATIOS[(i // 4) % len(TRATIOS)],
+                                 basis=i % 4, restriction=1, alpha=1e-2)
         p.max_iter = max_iter
+        p.krylov, p.restart = krylov, restart
         out.append(p)
     return out
 
@@ -138,7 +142,11 @@ probs = bench.problems({sample}, 9000)
 t = time.perf_counter()
 for p in probs:
     g, sysm, c, P, st = oracle.build(p)
-    x, it, rr, ok, _ = osolver.two_stage_solve(st, tol={TOL}, max_iter=p.max_iter)
+    if p.krylov == 1:
+        x, it, rr, ok, _ = osolver.gmres_solve(st, tol={TOL}, max_iter=p.max_iter,
+                                               restart=p.restart)
+    else:
+        x, it, rr, ok, _ = osolver.two_stage_solve(st, tol={TOL}, max_iter=p.max_iter)
     st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
     osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
 print(json.dumps({{"seconds": time.perf_counter() - t}}))

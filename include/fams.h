@@ -21,7 +21,8 @@
  *  - A batch context holds several independent instances (a block-diagonal
  *    system): kernels process all instances together and one CTA per instance
  *    runs the sequential parts, so results of an instance do not depend on
- *    what else is in the batch.
+ *    what else is in the batch (beyond rounding: the coarse operator is
+ *    summed with atomic additions).
  */
 #ifndef FAMS_H
 #define FAMS_H
@@ -37,6 +38,10 @@ enum { FAMS_R_FV = 0, FAMS_R_FE = 1 };
 /* arithmetic of the iteration: FP64 throughout, or FP32 inner stages with
    FP64 outer residual, coarse solve and refinement */
 enum { FAMS_FP64 = 0, FAMS_MIXED = 1 };
+/* outer iteration: the Table 1 loop, or GMRES with the two-stage step as
+   right preconditioner (Sec. 4.5, 4.6) */
+enum { FAMS_KRYLOV_NONE = 0, FAMS_KRYLOV_GMRES = 1 };
+#define FAMS_MAX_RESTART 64
 
 enum {
   FAMS_OK = 0,
@@ -82,7 +87,12 @@ typedef struct {
    d_min of the distance-based fracture coarsening (Table 2; <= 0 means
    infinity, one coarse node per network); frac_cz = vertical coarsening of 3D
    fracture plates; alpha = truncation threshold of P (Sec. 4.3, 0 = none);
-   max_iter bounds the Table 1 loop; precision = FAMS_FP64 or FAMS_MIXED. */
+   max_iter bounds the Table 1 loop (or the GMRES iterations); precision =
+   FAMS_FP64 or FAMS_MIXED.  krylov = FAMS_KRYLOV_GMRES runs the two-stage
+   step as the right preconditioner of GMRES(restart), the paper's benchmark
+   mode (Sec. 4.5, 4.6): every iteration is one preconditioner application,
+   and a cycle ends when the least-squares residual estimate reaches tol, after
+   `restart` iterations, or at max_iter; the true residual then decides. */
 typedef struct {
   int coarsen[3];
   int frac_dmin;
@@ -92,12 +102,14 @@ typedef struct {
   double alpha;
   int max_iter;
   int precision;
+  int krylov;    /* FAMS_KRYLOV_NONE: the Table 1 loop; FAMS_KRYLOV_GMRES: GMRES(restart) */
+  int restart;   /* GMRES cycle length, 1..FAMS_MAX_RESTART (ignored otherwise) */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */
 typedef struct {
-  int iterations;        /* completed Table 1 sweeps */
-  double rel_residual;   /* ||q - A x||_2 / ||q||_2 after the last sweep */
+  int iterations;        /* completed Table 1 sweeps (GMRES: preconditioner applications) */
+  double rel_residual;   /* ||q - A x||_2 / ||q||_2 of the returned x */
   int converged;
   double solve_ms;       /* device time of the iteration */
 } fams_stats;

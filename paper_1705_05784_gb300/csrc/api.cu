@@ -84,6 +84,10 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   if (o.max_iter < 0) return bad("max_iter must be >= 0");
   if (o.precision != FAMS_FP64) return bad("only FAMS_FP64 is available in this build");
   if (g.dim == 3 && o.frac_cz < 1) return bad("frac_cz must be >= 1");
+  if (o.krylov != FAMS_KRYLOV_NONE && o.krylov != FAMS_KRYLOV_GMRES)
+    return bad("krylov must be FAMS_KRYLOV_NONE or FAMS_KRYLOV_GMRES");
+  if (o.krylov == FAMS_KRYLOV_GMRES && (o.restart < 1 || o.restart > FAMS_MAX_RESTART))
+    return bad("GMRES restart must be in 1..FAMS_MAX_RESTART");
   return FAMS_OK;
 }
 
@@ -109,6 +113,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.dmin = o.frac_dmin; I.fcz = std::max(1, o.frac_cz);
     I.basis = o.basis; I.restriction = o.restriction; I.precision = o.precision;
     I.max_iter = o.max_iter; I.alpha = o.alpha;
+    I.krylov = o.krylov; I.restart = o.krylov == FAMS_KRYLOV_GMRES ? o.restart : 0;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;
     I.nfr = nf;
@@ -406,6 +411,10 @@ int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_sta
 int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st) {
   if (!ctx || ctx->b.B != 1) {
     set_error("fams_solve_static needs a single-instance context");
+    return FAMS_EINVAL;
+  }
+  if (ctx->b.h[0].krylov != FAMS_KRYLOV_NONE) {
+    set_error("fams_solve_static runs the Table 1 loop only (krylov = FAMS_KRYLOV_NONE)");
     return FAMS_EINVAL;
   }
   if (!x) { set_error("x is null"); return FAMS_EINVAL; }

@@ -12,11 +12,13 @@
 //   Frac-AMS : matrix rows also keep all fracture links (fracture rows first)
 //   Rock-AMS : fracture rows also keep all matrix links (matrix rows first)
 //   Coupled  : rank(c) >= rank(r) in either medium (merged dual blocks)
-// A'_BB is a symmetric, diagonally dominant M-matrix, solved by a dense
-// Cholesky factorisation in one CTA per dual block.
+// A'_BB is a symmetric, diagonally dominant M-matrix, solved densely by
+// elimination without pivoting: one warp per small dual block, one CTA per
+// larger one.
 #include <algorithm>
 
 #include "batch.cuh"
+#include "dense.cuh"
 
 namespace fams {
 
@@ -25,7 +27,9 @@ namespace {
 constexpr int NSTAGE = 5;
 constexpr int HASH_CAP = 2048;      // distinct coarse columns one dual block may touch
 constexpr int MEMBER_SORT_MAX = 8192;
-constexpr int SOLVE_THREADS = 256;
+constexpr int CTA_WARPS = 4;            // warp-per-block launches: blocks per CTA
+constexpr long long WARP_NEED = 1024;   // doubles: largest block solved by one warp
+constexpr long long MID_NEED = 6144;    // doubles: largest block on a 128-thread CTA
 
 __device__ inline int stage_of(int variant, int med, int rank) {
   if (rank == RANK_V) return -1;
@@ -159,14 +163,16 @@ __device__ void bitonic_sort_int(int* a, int m) {
 
 // one CTA per dual block: sort its members, then find the coarse columns its
 // known neighbours carry.  mode 0 counts them, mode 1 writes them sorted.
+// Mode 0 needs a power of two >= the largest block of ints of dynamic shared
+// memory.
 __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
                             const int* rowptr, const int* col, const int* instage,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
                             int* ncols, const int* colptr, int* colbuf, int* err) {
-  __shared__ int sm[MEMBER_SORT_MAX];
+  extern __shared__ int sm[];   // member sort buffer (mode 0), sized by the launch
   __shared__ int hs[HASH_CAP];
-  __shared__ int nuniq, known_links;
+  __shared__ int nuniq, known_links, ncand;
   int c = blockIdx.x;
   int a = comp_off[c], n = comp_off[c + 1] - a;
   if (n > MEMBER_SORT_MAX) {
@@ -185,11 +191,32 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < HASH_CAP; i += blockDim.x) hs[i] = -1;
-  if (threadIdx.x == 0) { nuniq = 0; known_links = 0; }
+  if (threadIdx.x == 0) { nuniq = 0; known_links = 0; ncand = 0; }
   __syncthreads();
   const Inst& I = inst_of(inst, B, off_row, members[a]);
+  // candidate columns (with repeats): the hash table gets twice as many slots
   bool over = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = members[a + i];
+    int mr = medium_of(I, r), rr = rank[r];
+    int cand = 0, links = 0;
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int cc = col[p];
+      if (cc == r || instage[cc]) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) continue;
+      ++links;
+      if (pstage[cc] < 0) { over = true; continue; }
+      cand += plen[cc];
+    }
+    if (links) atomicAdd(&known_links, links);
+    if (cand) atomicAdd(&ncand, cand);
+  }
+  if (over) atomicCAS(err, 0, DERR_INVAL);
+  __syncthreads();
+  int H = 32;
+  while (H < 2 * ncand && H < HASH_CAP) H <<= 1;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) hs[i] = -1;
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int r = members[a + i];
     int mr = medium_of(I, r), rr = rank[r];
@@ -197,26 +224,24 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
       int cc = col[p];
       if (cc == r || instage[cc]) continue;
       if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) continue;
-      atomicAdd(&known_links, 1);
       int st = pstage[cc];
-      if (st < 0) { over = true; continue; }
+      if (st < 0) continue;
       const int* pc = pool.col[st] + poff[cc];
       for (int q = 0; q < plen[cc]; ++q) {
         int key = pc[q];
-        unsigned h = ((unsigned)key * 2654435761u) & (HASH_CAP - 1);
-        for (int probe = 0; probe < HASH_CAP; ++probe) {
+        unsigned h = ((unsigned)key * 2654435761u) & (H - 1);
+        for (int probe = 0; probe < H; ++probe) {
           int prev = atomicCAS(&hs[h], -1, key);
           if (prev == -1) { atomicAdd(&nuniq, 1); break; }
           if (prev == key) break;
-          h = (h + 1) & (HASH_CAP - 1);
+          h = (h + 1) & (H - 1);
         }
       }
     }
   }
-  if (over) atomicCAS(err, 0, DERR_INVAL);
   __syncthreads();
   if (threadIdx.x == 0 && known_links == 0) atomicCAS(err, 0, DERR_FLOATING);
-  if (nuniq > HASH_CAP / 2) {
+  if (nuniq > H / 2) {
     if (threadIdx.x == 0) atomicCAS(err, 0, DERR_CAPACITY);
     return;
   }
@@ -224,10 +249,10 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     if (threadIdx.x == 0) ncols[c] = nuniq;
     return;
   }
-  for (int i = threadIdx.x; i < HASH_CAP; i += blockDim.x)
+  for (int i = threadIdx.x; i < H; i += blockDim.x)
     if (hs[i] == -1) hs[i] = 0x7fffffff;
   __syncthreads();
-  bitonic_sort_int(hs, HASH_CAP);
+  bitonic_sort_int(hs, H);
   for (int i = threadIdx.x; i < nuniq; i += blockDim.x) colbuf[colptr[c] + i] = hs[i];
 }
 
@@ -242,131 +267,107 @@ __device__ inline int find_col(const int* cols, int k, int key) {
   return -1;
 }
 
-// one CTA per dual block: assemble A'_BB and the right-hand sides, dense
-// Cholesky, forward/back substitution, write the block's rows of P.
-__global__ void k_comp_solve(const Inst* inst, int B, const int* off_row, const int* rank,
-                             const int* rowptr, const int* col, const double* val,
-                             const double* TD, const int* instage, const int* comp_list,
-                             const int* comp_off, const int* members, const int* pos,
-                             const int* colptr, const int* colbuf, const long long* pool_off,
-                             int* pstage, int* poff, int* plen, Pool pool, int s, int* out_col,
-                             double* out_val, double* gwork, long long gstride, int* err) {
-  extern __shared__ double dsm[];
-  int c = comp_list[blockIdx.x];
-  int a = comp_off[c], n = comp_off[c + 1] - a;
-  int k = colptr[c + 1] - colptr[c];
-  const int* cols = colbuf + colptr[c];
-  double* M;
-  double* R;
-  if (gwork) {
-    M = gwork + (long long)blockIdx.x * gstride;
-  } else {
-    M = dsm;
-  }
-  R = M + (long long)n * n;
-  const Inst& I = inst_of(inst, B, off_row, members[a]);
-  for (long long i = threadIdx.x; i < (long long)n * n + (long long)n * k; i += blockDim.x) M[i] = 0.0;
-  __syncthreads();
-  // assemble: one thread per member row
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int r = members[a + i];
-    int mr = medium_of(I, r), rr = rank[r];
+struct CompArgs {
+  const Inst* inst;
+  int B;
+  const int* off_row;
+  const int* rank;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const double* TD;
+  const int* instage;
+  const int* comp_list;
+  long long ncomp;
+  const int* comp_off;
+  const int* members;
+  const int* pos;
+  const int* colptr;
+  const int* colbuf;
+  const long long* pool_off;
+  int* pstage;
+  int* poff;
+  int* plen;
+  Pool pool;
+  int s;
+  int* out_col;
+  double* out_val;
+  int* err;
+};
+
+// one dual block on a thread group: assemble [A'_BB | right-hand sides] with
+// leading dimension n + k, eliminate, write the block's rows of P
+template <class G>
+__device__ void comp_solve(const CompArgs& a, int c, double* M) {
+  const int gr = G::rank(), gs = G::size();
+  const int a0 = a.comp_off[c], n = a.comp_off[c + 1] - a0;
+  const int k = a.colptr[c + 1] - a.colptr[c];
+  const int ld = n + k;
+  const int* cols = a.colbuf + a.colptr[c];
+  const Inst& I = inst_of(a.inst, a.B, a.off_row, a.members[a0]);
+  for (long long t = gr; t < (long long)n * ld; t += gs) M[t] = 0.0;
+  G::sync();
+  for (int i = gr; i < n; i += gs) {
+    int r = a.members[a0 + i];
+    int mr = medium_of(I, r), rr = a.rank[r];
+    double* Mi = M + (long long)i * ld;
     double d = 0.0;
-    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
-      int cc = col[p];
-      double av = val[p];
-      if (cc == r) { d += av - TD[r]; continue; }
+    for (int p = a.rowptr[r]; p < a.rowptr[r + 1]; ++p) {
+      int cc = a.col[p];
+      double av = a.val[p];
+      if (cc == r) { d += av - a.TD[r]; continue; }
       double T = -av;
-      if (keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) {
-        if (instage[cc]) {
-          int pc = pos[cc];
-          if (pc < 0 || pc >= n) { atomicCAS(err, 0, DERR_INVAL); continue; }
-          M[(long long)i * n + pc] = av;
+      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc])) {
+        if (a.instage[cc]) {
+          int pc = a.pos[cc];
+          if (pc < 0 || pc >= n) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
+          Mi[pc] = av;
         } else {
-          int st = pstage[cc];
-          const int* pc = pool.col[st] + poff[cc];
-          const double* pv = pool.val[st] + poff[cc];
-          for (int q = 0; q < plen[cc]; ++q) {
+          int st = a.pstage[cc];
+          const int* pc = a.pool.col[st] + a.poff[cc];
+          const double* pv = a.pool.val[st] + a.poff[cc];
+          for (int q = 0; q < a.plen[cc]; ++q) {
             int j = find_col(cols, k, pc[q]);
-            if (j < 0) { atomicCAS(err, 0, DERR_INVAL); continue; }
-            R[(long long)i * k + j] += T * pv[q];
+            if (j < 0) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
+            Mi[n + j] += T * pv[q];
           }
         }
       } else {
         d -= T;
       }
     }
-    M[(long long)i * n + i] = d;
+    Mi[i] = d;
   }
-  __syncthreads();
-  // Cholesky, lower triangle in place (right-looking)
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    double djj = M[(long long)j * n + j];
-    if (!(djj > 0.0) || !isfinite(djj)) {
-      if (threadIdx.x == 0) bad = 1;
-      break;
-    }
-    double l = sqrt(djj);
-    __syncthreads();
-    if (threadIdx.x == 0) M[(long long)j * n + j] = l;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[(long long)i * n + j] /= l;
-    __syncthreads();
-    // trailing update of the lower triangle: warp w takes rows j+1+w, j+1+w+NW, ...
-    // and its lanes the columns of that row
-    int m = n - j - 1;
-    int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
-    for (int ii = threadIdx.x >> 5; ii < m; ii += nw) {
-      int gi = j + 1 + ii;
-      double lij = M[(long long)gi * n + j];
-      for (int jj = lane; jj <= ii; jj += 32) {
-        int gj = j + 1 + jj;
-        M[(long long)gi * n + gj] -= lij * M[(long long)gj * n + j];
-      }
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  if (bad) {
-    if (threadIdx.x == 0) atomicCAS(err, 0, DERR_BREAKDOWN);
+  G::sync();
+  if (!ge_solve<G>(M, ld, n, k)) {
+    if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
     return;
   }
-  // forward: L Y = R
-  for (int j = 0; j < n; ++j) {
-    double l = M[(long long)j * n + j];
-    for (int q = threadIdx.x; q < k; q += blockDim.x) R[(long long)j * k + q] /= l;
-    __syncthreads();
-    for (long long t = threadIdx.x; t < (long long)(n - j - 1) * k; t += blockDim.x) {
-      int i = j + 1 + (int)(t / k), q = (int)(t % k);
-      R[(long long)i * k + q] -= M[(long long)i * n + j] * R[(long long)j * k + q];
-    }
-    __syncthreads();
+  long long base = a.pool_off[c];
+  for (int t = gr; t < n * k; t += gs) {
+    int i = t / k, q = t - i * k;
+    a.out_col[base + t] = cols[q];
+    a.out_val[base + t] = M[(long long)i * ld + n + q];
   }
-  // backward: L^T X = Y
-  for (int j = n - 1; j >= 0; --j) {
-    double l = M[(long long)j * n + j];
-    for (int q = threadIdx.x; q < k; q += blockDim.x) R[(long long)j * k + q] /= l;
-    __syncthreads();
-    for (long long t = threadIdx.x; t < (long long)j * k; t += blockDim.x) {
-      int i = (int)(t / k), q = (int)(t % k);
-      R[(long long)i * k + q] -= M[(long long)j * n + i] * R[(long long)j * k + q];
-    }
-    __syncthreads();
+  for (int i = gr; i < n; i += gs) {
+    int r = a.members[a0 + i];
+    a.pstage[r] = a.s;
+    a.poff[r] = (int)(base + (long long)i * k);
+    a.plen[r] = k;
   }
-  long long base = pool_off[c];
-  for (long long t = threadIdx.x; t < (long long)n * k; t += blockDim.x) {
-    int i = (int)(t / k), q = (int)(t % k);
-    out_col[base + t] = cols[q];
-    out_val[base + t] = R[(long long)i * k + q];
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int r = members[a + i];
-    pstage[r] = s;
-    poff[r] = (int)(base + (long long)i * k);
-    plen[r] = k;
-  }
+}
+
+// dual blocks of the stage: one warp each (WarpGroup: CTA_WARPS blocks per
+// CTA, `slice` doubles of shared memory each) or one CTA each (CtaGroup; in
+// shared memory, or in `gwork` with `slice` doubles per CTA)
+template <class G>
+__global__ void k_comp_solve(CompArgs a, long long slice, double* gwork) {
+  extern __shared__ double dsm[];
+  const int sub = G::per_warp ? (threadIdx.x >> 5) : 0;
+  const long long idx = (long long)blockIdx.x * (G::per_warp ? (blockDim.x >> 5) : 1) + sub;
+  if (idx >= a.ncomp) return;
+  double* M = gwork ? gwork + (long long)blockIdx.x * slice : dsm + (long long)sub * slice;
+  comp_solve<G>(a, a.comp_list[idx], M);
 }
 
 // truncation (Sec. 4.3) and CSR of P
@@ -472,8 +473,10 @@ int phase_basis(Batch& b) {
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   // leave room for the kernels' static shared memory
   max_smem -= 1024;
-  FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem));
+  FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve<CtaGroup>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  FAMS_CUDA(cudaFuncSetAttribute(k_comp_solve<WarpGroup>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   for (int s = 0; s < NSTAGE; ++s) {
     fams::note_launch(), k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
                                                   instage);
@@ -504,7 +507,19 @@ int phase_basis(Batch& b) {
     FAMS_TRY(exclusive_scan(b, size, coff, ncomp, &nmem));
     FAMS_TRY(b.scratch((void**)&members, sizeof(int) * (nmem + 1)));
     fams::note_launch(), k_comp_place<<<grid_for(nrow, T), T, 0, st>>>(nrow, comp_of, coff, cursor, members);
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    // block sizes on the host: sort buffer of the column search, size classes
+    std::vector<int> hs(ncomp), hk(ncomp);
+    FAMS_CUDA(cudaMemcpyAsync(hs.data(), size, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    int sort_cap = 1, maxn = 0;
+    for (int v : hs) maxn = std::max(maxn, v);
+    while (sort_cap < maxn) sort_cap <<= 1;
+    if (maxn > MEMBER_SORT_MAX) {
+      set_error("a dual block has " + std::to_string(maxn) + " cells; at most " +
+                std::to_string(MEMBER_SORT_MAX) + " are supported");
+      return FAMS_ECAPACITY;
+    }
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 0, ncols, nullptr, nullptr, b.d_err);
     FAMS_CUDA(cudaGetLastError());
@@ -512,28 +527,23 @@ int phase_basis(Batch& b) {
     long long totc = 0;
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 256, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 1, ncols, colptr, colbuf, b.d_err);
-    // host plan: pool offsets and small/large split
-    std::vector<int> hs(ncomp), hk(ncomp);
-    FAMS_CUDA(cudaMemcpyAsync(hs.data(), size, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+    // host plan: pool offsets, and the blocks by size class (doubles of
+    // [A'_BB | R]): one warp, a 128-thread CTA, a 256-thread CTA in shared
+    // memory, or a 512-thread CTA on a bounded global workspace
     FAMS_CUDA(cudaMemcpyAsync(hk.data(), ncols, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
     FAMS_CUDA(cudaStreamSynchronize(st));
     std::vector<long long> hpo(ncomp + 1, 0);
-    std::vector<int> small, large;
-    long long max_big = 0;
-    size_t small_smem = 0;
+    std::vector<int> cls[4];
+    long long cmax[4] = {0, 0, 0, 0};
     for (long long c = 0; c < ncomp; ++c) {
       hpo[c + 1] = hpo[c] + (long long)hs[c] * hk[c];
-      long long need = ((long long)hs[c] * hs[c] + (long long)hs[c] * hk[c]) * 8;
-      if (need + 1024 <= max_smem) {
-        small.push_back((int)c);
-        small_smem = std::max(small_smem, (size_t)need);
-      } else {
-        large.push_back((int)c);
-        max_big = std::max(max_big, need / 8);
-      }
+      long long need = (long long)hs[c] * ((long long)hs[c] + hk[c]);
+      int q = need <= WARP_NEED ? 0 : need <= MID_NEED ? 1 : need * 8 + 1024 <= max_smem ? 2 : 3;
+      cls[q].push_back((int)c);
+      cmax[q] = std::max(cmax[q], need);
     }
     long long* pool_off = nullptr;
     int* ocol = nullptr;
@@ -551,31 +561,43 @@ int phase_basis(Batch& b) {
     }
     pool.col[s] = ocol;
     pool.val[s] = oval;
-    if (!small.empty()) {
-      FAMS_CUDA(cudaMemcpyAsync(clist, small.data(), sizeof(int) * small.size(),
+    CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val, b.TD, instage,
+                nullptr, 0, coff, members, pos, colptr, colbuf, pool_off, pstage, poff, plen,
+                pool, s, ocol, oval, b.d_err};
+    long long lo = 0;
+    for (int q = 0; q < 4; ++q) {
+      if (cls[q].empty()) continue;
+      int* lst = clist + lo;
+      FAMS_CUDA(cudaMemcpyAsync(lst, cls[q].data(), sizeof(int) * cls[q].size(),
                                 cudaMemcpyHostToDevice, st));
-      fams::note_launch(), k_comp_solve<<<(int)small.size(), SOLVE_THREADS, small_smem, st>>>(
-          b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val, b.TD, instage, clist, coff,
-          members, pos, colptr, colbuf, pool_off, pstage, poff, plen, pool, s, ocol, oval,
-          nullptr, 0, b.d_err);
-      FAMS_CUDA(cudaGetLastError());
-    }
-    if (!large.empty()) {
-      // bounded workspace: at most ~1 GiB of dense blocks per launch
-      long long per = std::max(1LL, (1LL << 27) / std::max(max_big, 1LL));
-      double* work = nullptr;
-      FAMS_TRY(b.scratch((void**)&work, sizeof(double) * max_big * std::min<long long>(per, large.size())));
-      int* lst = clist + small.size();
-      FAMS_CUDA(cudaMemcpyAsync(lst, large.data(), sizeof(int) * large.size(),
-                                cudaMemcpyHostToDevice, st));
-      for (size_t o = 0; o < large.size(); o += per) {
-        int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
-        fams::note_launch(), k_comp_solve<<<cnt, 1024, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val,
-                                           b.TD, instage, lst + o, coff, members, pos, colptr,
-                                           colbuf, pool_off, pstage, poff, plen, pool, s, ocol,
-                                           oval, work, max_big, b.d_err);
-        FAMS_CUDA(cudaGetLastError());
+      lo += (long long)cls[q].size();
+      long long cnt = (long long)cls[q].size();
+      if (q == 0) {
+        long long slice = (cmax[0] + 3) & ~3LL;
+        ca.comp_list = lst;
+        ca.ncomp = cnt;
+        fams::note_launch(),
+            k_comp_solve<WarpGroup><<<(int)((cnt + CTA_WARPS - 1) / CTA_WARPS), 32 * CTA_WARPS,
+                                      sizeof(double) * slice * CTA_WARPS, st>>>(ca, slice, nullptr);
+      } else if (q < 3) {
+        ca.comp_list = lst;
+        ca.ncomp = cnt;
+        fams::note_launch(),
+            k_comp_solve<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], st>>>(
+                ca, cmax[q], nullptr);
+      } else {
+        // bounded workspace: at most ~1 GiB of dense blocks per launch
+        long long per = std::max(1LL, (1LL << 27) / std::max(cmax[3], 1LL));
+        double* work = nullptr;
+        FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] * std::min(per, cnt)));
+        for (long long o = 0; o < cnt; o += per) {
+          ca.comp_list = lst + o;
+          ca.ncomp = std::min(per, cnt - o);
+          fams::note_launch(),
+              k_comp_solve<CtaGroup><<<(int)ca.ncomp, 512, 0, st>>>(ca, cmax[3], work);
+        }
       }
+      FAMS_CUDA(cudaGetLastError());
     }
     FAMS_TRY(b.check_err("dual-block solves"));
   }

@@ -140,6 +140,7 @@ struct Batch {
   double* ec = nullptr;
   double* stat = nullptr;      // per instance: 4 doubles (iters, relres, converged, qnorm)
   double* hist = nullptr;      // per instance: relative residual after each sweep
+  double* krylov = nullptr;    // GMRES bases of the instances that use GMRES
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
   bool fv_ready = false;

@@ -42,6 +42,7 @@ struct Inst {
   double bc_val[6];
   double aperture, hf;
   int cx, cy, cz, dmin, fcz, basis, restriction, precision, max_iter;
+  int krylov, restart;  // outer iteration; GMRES cycle length
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells

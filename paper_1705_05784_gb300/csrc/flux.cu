@@ -8,15 +8,21 @@
 //   4. connections inside a block carry T (p~_i - p~_j).
 // R^FV (q - A p') = 0 makes every local problem consistent, so the result is
 // mass conservative cell by cell.  All requested instances are processed
-// together: one CTA per instance for step 1, one CTA per primal block for
-// step 3, one thread per face or connection for steps 2 and 4.
+// together: one CTA per instance for step 1, one warp (small blocks) or one
+// CTA per primal block for step 3, one thread per face or connection for
+// steps 2 and 4.
 #include <algorithm>
 
 #include "batch.cuh"
+#include "dense.cuh"
 
 namespace fams {
 
 namespace {
+
+constexpr int LOCAL_CTA_WARPS = 4;            // warp-per-block launches: blocks per CTA
+constexpr long long LOCAL_WARP_NEED = 1024;   // doubles: largest block solved by one warp
+constexpr long long LOCAL_MID_NEED = 6144;    // doubles: largest block on a 128-thread CTA
 
 // step 1, one CTA per listed instance
 __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, const int* rowptr,
@@ -78,114 +84,102 @@ __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, co
   }
 }
 
-// step 3: one CTA per listed primal block (global coarse index), dense
-// Gaussian elimination with partial pivoting of the block's local TPFA matrix
-__global__ void k_flux_local(const Inst* inst, int B, const int* off_nc, const int* blk_list,
-                             const int* blk_ptr, const int* blk_cell, const int* rowptr,
-                             const int* col, const double* val, const double* TD, const double* q,
-                             const int* primal, const int* node_cell, const double* pp,
-                             double* pt, double* gwork, long long gstride, int* err) {
-  extern __shared__ double dsm[];
-  int c = blk_list[blockIdx.x];
-  const Inst& I = inst[find_segment(off_nc, B + 1, c)];
-  int a = blk_ptr[c], m = blk_ptr[c + 1] - a;
-  double* K = gwork ? gwork + (long long)blockIdx.x * gstride : dsm;
-  double* rhs = K + (long long)m * m;
-  __shared__ int s_hasD, s_piv, s_bad;
-  if (threadIdx.x == 0) { s_hasD = 0; s_bad = 0; }
-  for (long long t = threadIdx.x; t < (long long)m * m + m; t += blockDim.x) K[t] = 0.0;
-  __syncthreads();
-  int myblk = c - I.nc_off;
-  for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    int i = blk_cell[a + t];
-    double b = q[i];  // sources + Dirichlet terms
-    double d = TD[i];
-    if (TD[i] > 0.0) s_hasD = 1;
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      int j = col[p];
+// step 3: the local TPFA problem of one primal block (global coarse index)
+// on a thread group: [K | rhs] with leading dimension m + 1, Neumann data
+// from p' on the block boundary, pinned to p' at the block's coarse node when
+// no Dirichlet face closes it; dense elimination without pivoting
+struct LocalArgs {
+  const Inst* inst;
+  int B;
+  const int* off_nc;
+  const int* blk_list;
+  long long nblk;
+  const int* blk_ptr;
+  const int* blk_cell;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const double* TD;
+  const double* q;
+  const int* primal;
+  const int* node_cell;
+  const double* pp;
+  double* pt;
+  int* err;
+};
+
+template <class G>
+__device__ void flux_local(const LocalArgs& a, int c, double* K) {
+  const int gr = G::rank(), gs = G::size();
+  const Inst& I = a.inst[find_segment(a.off_nc, a.B + 1, c)];
+  const int a0 = a.blk_ptr[c], m = a.blk_ptr[c + 1] - a0;
+  const int ld = m + 1;
+  for (long long t = gr; t < (long long)m * ld; t += gs) K[t] = 0.0;
+  G::sync();
+  const int myblk = c - I.nc_off;
+  bool hasD = false;
+  for (int t = gr; t < m; t += gs) {
+    int i = a.blk_cell[a0 + t];
+    double* Kt = K + (long long)t * ld;
+    double b = a.q[i];  // sources + Dirichlet terms
+    double d = a.TD[i];
+    if (a.TD[i] > 0.0) hasD = true;
+    for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
+      int j = a.col[p];
       if (j == i) continue;
-      double T = -val[p];
-      if (primal[j] == myblk) {
+      double T = -a.val[p];
+      if (a.primal[j] == myblk) {
         int lo = 0, hi = m - 1, pos = -1;
         while (lo <= hi) {
           int mid = (lo + hi) >> 1;
-          int v = blk_cell[a + mid];
+          int v = a.blk_cell[a0 + mid];
           if (v == j) { pos = mid; break; }
           if (v < j) lo = mid + 1; else hi = mid - 1;
         }
-        if (pos < 0) { atomicCAS(err, 0, DERR_INVAL); continue; }
-        K[(long long)t * m + pos] -= T;
+        if (pos < 0) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
+        Kt[pos] -= T;
         d += T;
       } else {
-        b -= T * (pp[i] - pp[j]);
+        b -= T * (a.pp[i] - a.pp[j]);
       }
     }
-    K[(long long)t * m + t] += d;
-    rhs[t] = b;
+    Kt[t] += d;
+    Kt[m] = b;
   }
-  __syncthreads();
-  if (!s_hasD && threadIdx.x == 0) {
-    int v = node_cell[c];
+  // pin the coarse node unless a Dirichlet face closes the block
+  bool anyD = G::per_warp ? __any_sync(0xffffffffu, hasD) : __syncthreads_or(hasD);
+  if (!anyD) {
+    int v = a.node_cell[c];
     int lo = 0, hi = m - 1, pos = 0;
     while (lo <= hi) {
       int mid = (lo + hi) >> 1;
-      int w = blk_cell[a + mid];
+      int w = a.blk_cell[a0 + mid];
       if (w == v) { pos = mid; break; }
       if (w < v) lo = mid + 1; else hi = mid - 1;
     }
-    for (int j = 0; j < m; ++j) K[(long long)pos * m + j] = 0.0;
-    K[(long long)pos * m + pos] = 1.0;
-    rhs[pos] = pp[v];
+    G::sync();
+    double* Kp = K + (long long)pos * ld;
+    for (int j = gr; j <= m; j += gs) Kp[j] = j == pos ? 1.0 : (j == m ? a.pp[v] : 0.0);
   }
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) {
-      int pr = j;
-      double best = fabs(K[(long long)j * m + j]);
-      for (int i = j + 1; i < m; ++i) {
-        double v = fabs(K[(long long)i * m + j]);
-        if (v > best) { best = v; pr = i; }
-      }
-      if (!(best > 0.0)) s_bad = 1;
-      s_piv = pr;
-    }
-    __syncthreads();
-    if (s_bad) break;
-    int pr = s_piv;
-    if (pr != j) {
-      for (int t = threadIdx.x; t <= m; t += blockDim.x) {
-        if (t < m) {
-          double u = K[(long long)j * m + t];
-          K[(long long)j * m + t] = K[(long long)pr * m + t];
-          K[(long long)pr * m + t] = u;
-        } else {
-          double u = rhs[j]; rhs[j] = rhs[pr]; rhs[pr] = u;
-        }
-      }
-      __syncthreads();
-    }
-    double piv = K[(long long)j * m + j];
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-      double f = K[(long long)i * m + j] / piv;
-      K[(long long)i * m + j] = f;
-      for (int t = j + 1; t < m; ++t) K[(long long)i * m + t] -= f * K[(long long)j * m + t];
-      rhs[i] -= f * rhs[j];
-    }
-    __syncthreads();
-  }
-  if (s_bad) {
-    if (threadIdx.x == 0) atomicCAS(err, 0, DERR_BREAKDOWN);
+  G::sync();
+  if (!ge_solve<G>(K, ld, m, 1)) {
+    if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
     return;
   }
-  if (threadIdx.x == 0) {
-    for (int j = m - 1; j >= 0; --j) {
-      double s = rhs[j];
-      for (int t = j + 1; t < m; ++t) s -= K[(long long)j * m + t] * rhs[t];
-      rhs[j] = s / K[(long long)j * m + j];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < m; t += blockDim.x) pt[blk_cell[a + t]] = rhs[t];
+  for (int t = gr; t < m; t += gs) a.pt[a.blk_cell[a0 + t]] = K[(long long)t * ld + m];
+}
+
+// primal blocks of the listed instances: one warp each (WarpGroup, several
+// per CTA, `slice` doubles of shared memory each) or one CTA each (CtaGroup;
+// in shared memory, or in `gwork` with `slice` doubles per CTA)
+template <class G>
+__global__ void k_flux_local(LocalArgs a, long long slice, double* gwork) {
+  extern __shared__ double dsm[];
+  const int sub = G::per_warp ? (threadIdx.x >> 5) : 0;
+  const long long idx = (long long)blockIdx.x * (G::per_warp ? (blockDim.x >> 5) : 1) + sub;
+  if (idx >= a.nblk) return;
+  double* K = gwork ? gwork + (long long)blockIdx.x * slice : dsm + (long long)sub * slice;
+  flux_local<G>(a, a.blk_list[idx], K);
 }
 
 __device__ inline long long faces_of(const Inst& I) {
@@ -308,7 +302,10 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;  // static shared memory of the kernels
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-  FAMS_CUDA(cudaFuncSetAttribute(k_flux_local, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  FAMS_CUDA(cudaFuncSetAttribute(k_flux_local<CtaGroup>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  FAMS_CUDA(cudaFuncSetAttribute(k_flux_local<WarpGroup>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   int* dlist = nullptr;
   FAMS_TRY(b.scratch((void**)&dlist, sizeof(int) * nl));
   FAMS_CUDA(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
@@ -316,44 +313,62 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
       b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.p_ptr, b.p_col,
       b.p_val, b.q, x, res, pp);
   FAMS_CUDA(cudaGetLastError());
-  // local problems of every primal block of the listed instances, split by
-  // size (shared memory or a bounded global workspace)
+  // local problems of every primal block of the listed instances, by size
+  // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread
+  // CTA in shared memory, or a 512-thread CTA on a bounded global workspace
   std::vector<int> hp(b.tot_nc + 1);
   FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
                             cudaMemcpyDeviceToHost, st));
   FAMS_CUDA(cudaStreamSynchronize(st));
-  std::vector<int> small, large;
-  size_t small_smem = 0;
-  long long big = 0;
+  std::vector<int> cls[4];
+  long long cmax[4] = {0, 0, 0, 0};
   for (int ii : list) {
     const Inst& I = b.h[ii];
     for (int c = I.nc_off; c < I.nc_off + I.nc; ++c) {
       long long m = hp[c + 1] - hp[c];
-      long long need = (m * m + m) * 8;
-      if (need <= max_smem) { small.push_back(c); small_smem = std::max(small_smem, (size_t)need); }
-      else { large.push_back(c); big = std::max(big, m * m + m); }
+      long long need = m * (m + 1);
+      int q = need <= LOCAL_WARP_NEED ? 0 : need <= LOCAL_MID_NEED ? 1
+            : need * 8 <= max_smem ? 2 : 3;
+      cls[q].push_back(c);
+      cmax[q] = std::max(cmax[q], need);
     }
   }
   int* lst = nullptr;
-  FAMS_TRY(b.scratch((void**)&lst, sizeof(int) * (small.size() + large.size() + 1)));
-  if (!small.empty()) {
-    FAMS_CUDA(cudaMemcpyAsync(lst, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice, st));
-    fams::note_launch(), k_flux_local<<<(int)small.size(), 256, small_smem, st>>>(
-        b.d_inst, b.B, b.off_nc, lst, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD, b.q,
-        b.primal, b.node_cell, pp, pt, nullptr, 0, b.d_err);
-  }
-  if (!large.empty()) {
-    long long per = std::max(1LL, (1LL << 26) / std::max(big, 1LL));
-    double* work = nullptr;
-    FAMS_TRY(b.scratch((void**)&work, sizeof(double) * big * std::min<long long>(per, large.size())));
-    int* l2 = lst + small.size();
-    FAMS_CUDA(cudaMemcpyAsync(l2, large.data(), sizeof(int) * large.size(), cudaMemcpyHostToDevice, st));
-    for (size_t o = 0; o < large.size(); o += per) {
-      int cnt = (int)std::min<long long>(per, (long long)(large.size() - o));
-      fams::note_launch(), k_flux_local<<<cnt, 256, 0, st>>>(
-          b.d_inst, b.B, b.off_nc, l2 + o, b.blk_ptr, b.blk_cell, b.rowptr, b.col, b.val, b.TD,
-          b.q, b.primal, b.node_cell, pp, pt, work, big, b.d_err);
+  FAMS_TRY(b.scratch((void**)&lst, sizeof(int) * (b.tot_nc + 1)));
+  LocalArgs la{b.d_inst, b.B, b.off_nc, nullptr, 0, b.blk_ptr, b.blk_cell, b.rowptr, b.col,
+               b.val, b.TD, b.q, b.primal, b.node_cell, pp, pt, b.d_err};
+  long long lo = 0;
+  for (int q = 0; q < 4; ++q) {
+    if (cls[q].empty()) continue;
+    long long cnt = (long long)cls[q].size();
+    int* l = lst + lo;
+    lo += cnt;
+    FAMS_CUDA(cudaMemcpyAsync(l, cls[q].data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
+    la.blk_list = l;
+    la.nblk = cnt;
+    if (q == 0) {
+      long long slice = (cmax[0] + 3) & ~3LL;
+      fams::note_launch(),
+          k_flux_local<WarpGroup><<<(int)((cnt + LOCAL_CTA_WARPS - 1) / LOCAL_CTA_WARPS),
+                                    32 * LOCAL_CTA_WARPS,
+                                    sizeof(double) * slice * LOCAL_CTA_WARPS, st>>>(la, slice,
+                                                                                  nullptr);
+    } else if (q < 3) {
+      fams::note_launch(),
+          k_flux_local<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], st>>>(
+              la, cmax[q], nullptr);
+    } else {
+      long long per = std::max(1LL, (1LL << 26) / std::max(cmax[3], 1LL));
+      double* work = nullptr;
+      FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] * std::min(per, cnt)));
+      for (long long o = 0; o < cnt; o += per) {
+        la.blk_list = l + o;
+        la.nblk = std::min(per, cnt - o);
+        fams::note_launch(),
+            k_flux_local<CtaGroup><<<(int)la.nblk, 512, 0, st>>>(la, cmax[3], work);
+      }
     }
+    FAMS_CUDA(cudaGetLastError());
   }
   FAMS_CUDA(cudaGetLastError());
   long long* dfo = nullptr;

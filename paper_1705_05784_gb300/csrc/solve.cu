@@ -248,17 +248,24 @@ __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int 
   }
 }
 
-__global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
-  extern __shared__ double sm[];
-  __shared__ double red[40];
-  __shared__ int s_done;
-  __shared__ int pbuf[2 * CH_MAX];
-  int ii = blockIdx.x;
-  const Inst& I = a.inst[ii];
+// shared-memory layout of the solve kernels (doubles): the coarse vector in
+// band order, the coarse correction in coarse order, two staged chunks of
+// band columns; the GMRES kernel adds its small dense arrays after them
+struct SolveSmem {
+  double* yb;
+  double* ecs;
+  double* buf;
+  int* pbuf;
+};
+
+// Steps 5-7 of Table 1 on a residual r (SM cycles of the phases added to cyc
+// by thread 0):
+//   dp = P A_c^-1 R r;  y = r - A dp (also in level order);
+//   out = (base + dp) + (LU)^-1 y   (base null: out = dp + (LU)^-1 y)
+// out may alias base; r, dp and out must not alias y or ylev.
+__device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const double* r, double* dp,
+                          double* out, const double* base, const SolveSmem& S, long long* cyc) {
   const int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
-  double* yb = sm;            // coarse vector in band order
-  double* ecs = sm + nc;      // coarse correction in coarse order
-  double* buf = sm + 2 * nc;  // two staged chunks of band columns
   const double* AB = a.cs.band + a.cs.band_off[ii];
   const int* ipiv = a.cs.ipiv + co;
   const int* perm = a.cs.perm + co;
@@ -266,140 +273,126 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   const int* lp = a.lev_ptr + a.lev_off[ii];
   const int nlev = I.nlev;
   const int T = blockDim.x;
-  // ||q||
-  double acc = 0.0;
-  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
-  double qn = sqrt(block_sum(acc, red));
-  if (!(qn > 0.0)) qn = 1.0;
-  int it = 0;
-  double rel = 0.0;
-  // SM cycles per phase (thread 0, between barriers): residual, coarse
-  // (restriction + band solve), prolongation + r1, L sweep, U sweep
-  long long cyc[6] = {0, 0, 0, 0, 0, 0};
-  long long t0 = clock64();
-  for (;;) {
-    // step 3: r = q - A p
-    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
-    rel = sqrt(block_sum(acc, red)) / qn;
-    if (threadIdx.x == 0) {
-      a.hist[(long long)ii * a.hist_len + it] = rel;
-      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii]);
-    }
-    __syncthreads();
-    long long t1 = clock64();
-    cyc[0] += t1 - t0;
-    if (s_done) break;
-    // step 5: coarse right-hand side R r, in band order
-    for (int k = threadIdx.x; k < nc; k += T) {
-      int c = co + perm[k];
-      double s0 = 0.0, s1 = 0.0;
-      if (I.restriction == FAMS_R_FE) {
-        int p = a.pt_ptr[c], e = a.pt_ptr[c + 1];
-        for (; p + 1 < e; p += 2) {
-          s0 += a.pt_val[p] * a.r[a.pt_col[p]];
-          s1 += a.pt_val[p + 1] * a.r[a.pt_col[p + 1]];
-        }
-        if (p < e) s0 += a.pt_val[p] * a.r[a.pt_col[p]];
-      } else {
-        int p = a.blk_ptr[c], e = a.blk_ptr[c + 1];
-        for (; p + 1 < e; p += 2) {
-          s0 += a.r[a.blk_cell[p]];
-          s1 += a.r[a.blk_cell[p + 1]];
-        }
-        if (p < e) s0 += a.r[a.blk_cell[p]];
+  long long t1 = clock64();
+  // step 5: coarse right-hand side R r, in band order
+  for (int k = threadIdx.x; k < nc; k += T) {
+    int c = co + perm[k];
+    double s0 = 0.0, s1 = 0.0;
+    if (I.restriction == FAMS_R_FE) {
+      int p = a.pt_ptr[c], e = a.pt_ptr[c + 1];
+      for (; p + 1 < e; p += 2) {
+        s0 += a.pt_val[p] * r[a.pt_col[p]];
+        s1 += a.pt_val[p + 1] * r[a.pt_col[p + 1]];
       }
-      yb[k] = s0 + s1;
-      a.crhs[co + perm[k]] = s0 + s1;
-    }
-    __syncthreads();
-    long long t1b = clock64();
-    cyc[1] += t1b - t1;
-    coarse_solve(AB, ipiv, nc, kl, ku, yb, buf, pbuf);
-    for (int k = threadIdx.x; k < nc; k += T) {
-      ecs[perm[k]] = yb[k];
-      a.csol[co + perm[k]] = yb[k];
-    }
-    __syncthreads();
-    long long t2 = clock64();
-    cyc[2] += t2 - t1b;
-    // dp1 = P e_c
-    for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
-#pragma unroll
-      for (int k = 0; k < ROWS_ILP; ++k) {
-        int i = i0 + k * T;
-        if (i < ro + n) {
-          double s = 0.0;
-          for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += a.p_val[p] * ecs[a.p_col[p]];
-          a.dp[i] = s;
-        }
+      if (p < e) s0 += a.pt_val[p] * r[a.pt_col[p]];
+    } else {
+      int p = a.blk_ptr[c], e = a.blk_ptr[c + 1];
+      for (; p + 1 < e; p += 2) {
+        s0 += r[a.blk_cell[p]];
+        s1 += r[a.blk_cell[p + 1]];
       }
+      if (p < e) s0 += r[a.blk_cell[p]];
     }
-    __syncthreads();
-    // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
-    rows_residual(a, ro, n, a.r, a.dp, a.y, false, a.ylev);
-    __syncthreads();
-    long long t3 = clock64();
-    cyc[3] += t3 - t2;
-    // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
-    SweepRow cur, nxt;
-    sweep_load(a, lp, 0, nlev, true, cur);
-    for (int l = 0; l < nlev; ++l) {
-      sweep_load(a, lp, l + 1, nlev, true, nxt);
-      if (cur.t >= 0) {
-        double s = cur.base;
-#pragma unroll
-        for (int k = 0; k < PK; ++k)
-          if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
-        for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
-        a.y[cur.i] = s;
-        a.ylev[cur.t] = s;
-      }
-      for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
-        int i = a.lev_rows[t];
-        double s = a.ylev[t];
-        for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= a.F[p] * a.y[a.col[p]];
-        a.y[i] = s;
-        a.ylev[t] = s;
-      }
-      __syncthreads();
-      cur = nxt;
-    }
-    long long t4 = clock64();
-    cyc[4] += t4 - t3;
-    // U sweep and step 8: p = p + dp1 + dp2
-    sweep_load(a, lp, nlev - 1, nlev, false, cur);
-    for (int l = nlev - 1; l >= 0; --l) {
-      sweep_load(a, lp, l - 1, nlev, false, nxt);
-      if (cur.t >= 0) {
-        double s = cur.base;
-        double xo = a.x[cur.i], dpo = a.dp[cur.i];
-#pragma unroll
-        for (int k = 0; k < PK; ++k)
-          if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
-        if (cur.cnt > PK) {
-          int d = a.diag[cur.i];
-          for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
-        }
-        double xi = s / cur.diag;
-        a.y[cur.i] = xi;
-        a.x[cur.i] = (xo + dpo) + xi;
-      }
-      for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
-        int i = a.lev_rows[t];
-        int d = a.diag[i];
-        double s = a.ylev[t];
-        for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= a.F[p] * a.y[a.col[p]];
-        double xi = s / a.F[d];
-        a.y[i] = xi;
-        a.x[i] = (a.x[i] + a.dp[i]) + xi;
-      }
-      __syncthreads();
-      cur = nxt;
-    }
-    t0 = clock64();
-    cyc[5] += t0 - t4;
-    ++it;
+    S.yb[k] = s0 + s1;
+    a.crhs[co + perm[k]] = s0 + s1;
   }
+  __syncthreads();
+  long long t1b = clock64();
+  coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf);
+  for (int k = threadIdx.x; k < nc; k += T) {
+    S.ecs[perm[k]] = S.yb[k];
+    a.csol[co + perm[k]] = S.yb[k];
+  }
+  __syncthreads();
+  long long t2 = clock64();
+  // dp1 = P e_c
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * T;
+      if (i < ro + n) {
+        double s = 0.0;
+        for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += a.p_val[p] * S.ecs[a.p_col[p]];
+        dp[i] = s;
+      }
+    }
+  }
+  __syncthreads();
+  // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
+  rows_residual(a, ro, n, r, dp, a.y, false, a.ylev);
+  __syncthreads();
+  long long t3 = clock64();
+  // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
+  SweepRow cur, nxt;
+  sweep_load(a, lp, 0, nlev, true, cur);
+  for (int l = 0; l < nlev; ++l) {
+    sweep_load(a, lp, l + 1, nlev, true, nxt);
+    if (cur.t >= 0) {
+      double s = cur.base;
+#pragma unroll
+      for (int k = 0; k < PK; ++k)
+        if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
+      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
+      a.y[cur.i] = s;
+      a.ylev[cur.t] = s;
+    }
+    for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
+      int i = a.lev_rows[t];
+      double s = a.ylev[t];
+      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= a.F[p] * a.y[a.col[p]];
+      a.y[i] = s;
+      a.ylev[t] = s;
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+  long long t4 = clock64();
+  // U sweep and step 8: out = (base + dp1) + dp2
+  sweep_load(a, lp, nlev - 1, nlev, false, cur);
+  for (int l = nlev - 1; l >= 0; --l) {
+    sweep_load(a, lp, l - 1, nlev, false, nxt);
+    if (cur.t >= 0) {
+      double s = cur.base;
+      double xo = base ? base[cur.i] : 0.0, dpo = dp[cur.i];
+#pragma unroll
+      for (int k = 0; k < PK; ++k)
+        if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
+      if (cur.cnt > PK) {
+        int d = a.diag[cur.i];
+        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
+      }
+      double xi = s / cur.diag;
+      a.y[cur.i] = xi;
+      out[cur.i] = (xo + dpo) + xi;
+    }
+    for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
+      int i = a.lev_rows[t];
+      int d = a.diag[i];
+      double s = a.ylev[t];
+      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= a.F[p] * a.y[a.col[p]];
+      double xi = s / a.F[d];
+      a.y[i] = xi;
+      out[i] = ((base ? base[i] : 0.0) + dp[i]) + xi;
+    }
+    __syncthreads();
+    cur = nxt;
+  }
+  long long t5 = clock64();
+  if (cyc) {
+    cyc[1] += t1b - t1;
+    cyc[2] += t2 - t1b;
+    cyc[3] += t3 - t2;
+    cyc[4] += t4 - t3;
+    cyc[5] += t5 - t4;
+  }
+}
+
+__device__ inline SolveSmem solve_smem(double* sm, int nc, int* pbuf) {
+  return SolveSmem{sm, sm + nc, sm + 2 * nc, pbuf};
+}
+
+__device__ inline void write_stats(const SolveArgs& a, int ii, int it, double rel, double qn,
+                                   const long long* cyc) {
   if (threadIdx.x == 0) {
     a.stat[STAT_W * ii + 0] = it;
     a.stat[STAT_W * ii + 1] = rel;
@@ -408,6 +401,259 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     for (int k = 0; k < 6; ++k) a.stat[STAT_W * ii + 4 + k] = (double)cyc[k];
     a.stat[STAT_W * ii + STAT_BAD] = a.cs.bad[ii] ? 1.0 : 0.0;  // singular coarse system
   }
+}
+
+__global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double red[40];
+  __shared__ int s_done;
+  __shared__ int pbuf[2 * CH_MAX];
+  int ii = blockIdx.x;
+  const Inst& I = a.inst[ii];
+  if (I.krylov != FAMS_KRYLOV_NONE) return;
+  const int n = I.n, ro = I.row_off;
+  const SolveSmem S = solve_smem(sm, I.nc, pbuf);
+  const int T = blockDim.x;
+  // ||q||
+  double acc = 0.0;
+  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
+  double qn = sqrt(block_sum(acc, red));
+  if (!(qn > 0.0)) qn = 1.0;
+  int it = 0;
+  double rel = 0.0;
+  // SM cycles per phase (thread 0, between barriers): residual, restriction,
+  // band solve, prolongation + r1, L sweep, U sweep
+  long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  for (;;) {
+    long long t0 = clock64();
+    // step 3: r = q - A p
+    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
+    rel = sqrt(block_sum(acc, red)) / qn;
+    if (threadIdx.x == 0) {
+      a.hist[(long long)ii * a.hist_len + it] = rel;
+      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii]);
+    }
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+    if (s_done) break;
+    // steps 5-8: p = p + dp1 + dp2
+    two_stage(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
+    ++it;
+  }
+  write_stats(a, ii, it, rel, qn, cyc);
+}
+
+// GMRES helpers on the vectors of one instance (rows [ro, ro + n)); every
+// reduction has a fixed order, so results do not depend on the batch
+
+// y = A v; returns this thread's sum of y^2
+__device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const double* v, double* y) {
+  double acc = 0.0;
+  const int T = blockDim.x;
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+    int rs[ROWS_ILP], re[ROWS_ILP];
+    double s[ROWS_ILP];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * T;
+      bool ok = i < ro + n;
+      rs[k] = ok ? a.rowptr[i] : 0;
+      re[k] = ok ? a.rowptr[i + 1] : 0;
+      s[k] = 0.0;
+      m = max(m, re[k] - rs[k]);
+    }
+    for (int e = 0; e < m; ++e) {
+#pragma unroll
+      for (int k = 0; k < ROWS_ILP; ++k) {
+        int p = rs[k] + e;
+        if (p < re[k]) s[k] += a.val[p] * v[a.col[p]];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * T;
+      if (i < ro + n) {
+        y[i] = s[k];
+        acc += s[k] * s[k];
+      }
+    }
+  }
+  return acc;
+}
+
+constexpr int GS_CHUNK = 8;   // basis vectors per pass of the Gram-Schmidt dot products
+
+// h[0..k] = V[0..k]^T w over rows [ro, ro + n), reduced over the CTA into h
+// (shared memory); V_c at V + c ld
+__device__ void block_dots(const double* V, long long ld, int k1, int ro, int n, const double* w,
+                           double* h, double* red8) {
+  const int T = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  for (int c0 = 0; c0 < k1; c0 += GS_CHUNK) {
+    double s[GS_CHUNK];
+#pragma unroll
+    for (int c = 0; c < GS_CHUNK; ++c) s[c] = 0.0;
+    for (int i = ro + threadIdx.x; i < ro + n; i += T) {
+      double wi = w[i];
+#pragma unroll
+      for (int c = 0; c < GS_CHUNK; ++c)
+        if (c0 + c < k1) s[c] += V[(long long)(c0 + c) * ld + i] * wi;
+    }
+#pragma unroll
+    for (int c = 0; c < GS_CHUNK; ++c) {
+      double v = s[c];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red8[warp * GS_CHUNK + c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < GS_CHUNK && c0 + threadIdx.x < k1) {
+      double v = 0.0;
+      for (int q = 0; q < nw; ++q) v += red8[q * GS_CHUNK + threadIdx.x];
+      h[c0 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= V[0..k] h; returns this thread's sum of w^2
+__device__ inline double block_update(const double* V, long long ld, int k1, int ro, int n, double* w,
+                                      const double* h) {
+  double acc = 0.0;
+  for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
+    double wi = w[i];
+    for (int c = 0; c < k1; ++c) wi -= h[c] * V[(long long)c * ld + i];
+    w[i] = wi;
+    acc += wi * wi;
+  }
+  return acc;
+}
+
+// GMRES(m) with the two-stage step as right preconditioner (Sec. 4.5, 4.6;
+// Saad's right-preconditioned GMRES, Givens rotations).  The Arnoldi vectors
+// are orthogonalised by classical Gram-Schmidt applied twice, whose two
+// passes over the basis replace the k + 1 dependent reductions of modified
+// Gram-Schmidt (same result in exact arithmetic, orthogonality to working
+// precision).  Iterations count preconditioner applications; the history
+// holds the least-squares residual estimate inside a cycle and the true
+// residual at each cycle's end.
+__global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* krylov) {
+  extern __shared__ double sm[];
+  __shared__ double red[40];
+  __shared__ double red8[(SOLVE_T / 32) * GS_CHUNK];
+  __shared__ int s_done;
+  __shared__ int pbuf[2 * CH_MAX];
+  int ii = blockIdx.x;
+  const Inst& I = a.inst[ii];
+  if (I.krylov != FAMS_KRYLOV_GMRES) return;
+  const int n = I.n, ro = I.row_off, m = I.restart;
+  const SolveSmem S = solve_smem(sm, I.nc, pbuf);
+  // dense arrays after the coarse buffers: H ((m+1) x m, column k at
+  // H + k (m+1)), g (m+1), cs, sn, hv (m+1 scratch dot products), y (m)
+  double* H = sm + 2 * I.nc + 2 * BAND_BUF;
+  double* g = H + (m + 1) * m;
+  double* cs = g + (m + 1);
+  double* sn = cs + m;
+  double* hv = sn + m;
+  double* yv = hv + (m + 1);
+  double* V = krylov;   // V_k at V + k ntot, rows indexed like every batch vector
+  const long long ld = a.ntot;
+  const int T = blockDim.x;
+  double acc = 0.0;
+  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
+  double qn = sqrt(block_sum(acc, red));
+  if (!(qn > 0.0)) qn = 1.0;
+  long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  long long t0 = clock64();
+  int it = 0;
+  acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
+  double beta = sqrt(block_sum(acc, red));
+  double rel = beta / qn;
+  if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len] = rel;
+  cyc[0] += clock64() - t0;
+  for (;;) {
+    if (threadIdx.x == 0)
+      s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii] || !(beta > 0.0));
+    __syncthreads();
+    if (s_done) break;
+    // V_0 = r / beta, g = beta e_1
+    t0 = clock64();
+    for (int i = ro + threadIdx.x; i < ro + n; i += T) V[i] = a.r[i] / beta;
+    for (int k = threadIdx.x; k <= m; k += T) g[k] = k == 0 ? beta : 0.0;
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+    int k = 0;
+    for (;;) {
+      // z = M^-1 V_k (in r), w = A z (in V_{k+1})
+      double* Vk = V + (long long)k * ld;
+      double* w = V + (long long)(k + 1) * ld;
+      two_stage(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
+      t0 = clock64();
+      rows_apply(a, ro, n, a.r, w);
+      __syncthreads();
+      // classical Gram-Schmidt, twice: H(0..k, k) = V^T w, w -= V H(0..k, k)
+      double* Hk = H + (long long)k * (m + 1);
+      block_dots(V, ld, k + 1, ro, n, w, Hk, red8);
+      block_update(V, ld, k + 1, ro, n, w, Hk);
+      __syncthreads();
+      block_dots(V, ld, k + 1, ro, n, w, hv, red8);
+      acc = block_update(V, ld, k + 1, ro, n, w, hv);
+      double hn = sqrt(block_sum(acc, red));
+      if (threadIdx.x <= k) Hk[threadIdx.x] += hv[threadIdx.x];
+      if (hn > 0.0)
+        for (int i = ro + threadIdx.x; i < ro + n; i += T) w[i] /= hn;
+      __syncthreads();
+      // Givens rotations on column k and the right-hand side g
+      if (threadIdx.x == 0) {
+        Hk[k + 1] = hn;
+        for (int i = 0; i < k; ++i) {
+          double t = cs[i] * Hk[i] + sn[i] * Hk[i + 1];
+          Hk[i + 1] = -sn[i] * Hk[i] + cs[i] * Hk[i + 1];
+          Hk[i] = t;
+        }
+        double d = hypot(Hk[k], Hk[k + 1]);
+        cs[k] = Hk[k] / d;
+        sn[k] = Hk[k + 1] / d;
+        Hk[k] = d;
+        Hk[k + 1] = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        double est = fabs(g[k + 1]) / qn;
+        a.hist[(long long)ii * a.hist_len + it + 1] = est;
+        s_done = (est <= a.tol || k + 1 >= m || it + 1 >= I.max_iter || !isfinite(est));
+      }
+      __syncthreads();
+      cyc[0] += clock64() - t0;
+      ++k;
+      ++it;
+      if (s_done) break;
+    }
+    // y = H^-1 g (upper triangular k x k), u = V y (in V_k), x += M^-1 u
+    t0 = clock64();
+    if (threadIdx.x == 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k; ++j) s -= H[(long long)j * (m + 1) + i] * yv[j];
+        yv[i] = s / H[(long long)i * (m + 1) + i];
+      }
+    }
+    __syncthreads();
+    double* u = V + (long long)k * ld;
+    for (int i = ro + threadIdx.x; i < ro + n; i += T) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += yv[j] * V[(long long)j * ld + i];
+      u[i] = s;
+    }
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+    two_stage(a, I, ii, u, a.dp, a.x, a.x, S, cyc);
+    t0 = clock64();
+    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
+    beta = sqrt(block_sum(acc, red));
+    rel = beta / qn;
+    if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len + it] = rel;
+    cyc[0] += clock64() - t0;
+  }
+  write_stats(a, ii, it, rel, qn, cyc);
 }
 
 }  // namespace
@@ -426,6 +672,11 @@ int phase_alloc_work(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.rc, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.ec, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.hist, sizeof(double) * b.hist_len * b.B));
+  // GMRES bases: (restart + 1) vectors indexed like the batch rows
+  int mr = 0;
+  for (auto& I : b.h) mr = std::max(mr, I.restart);
+  if (mr > 0)
+    FAMS_TRY(b.alloc((void**)&b.krylov, sizeof(double) * (size_t)(mr + 1) * (size_t)(n + 1)));
   return FAMS_OK;
 }
 
@@ -461,20 +712,35 @@ int run_solve(Batch& b, double tol, float* ms) {
       return FAMS_ECAPACITY;
     }
   size_t smem = sizeof(double) * (2 * (size_t)maxnc + 2 * BAND_BUF);
+  int mr = 0, nrich = 0;
+  for (auto& I : b.h) {
+    mr = std::max(mr, I.restart);
+    nrich += I.krylov == FAMS_KRYLOV_NONE;
+  }
+  size_t smem_g = smem + sizeof(double) * ((size_t)mr * mr + 6 * (size_t)mr + 2);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
-  if ((long long)smem + 2048 > max_smem) {
+  if ((long long)(mr > 0 ? smem_g : smem) + 2048 > max_smem) {
     set_error("coarse system too large for the shared-memory coarse solve");
     return FAMS_ECAPACITY;
   }
   FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem - 2048));
+  FAMS_CUDA(cudaFuncSetAttribute(k_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - 3072));
   cudaEvent_t e0, e1;
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));
   FAMS_CUDA(cudaEventRecord(e0, b.stream));
-  fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
-  FAMS_CUDA(cudaGetLastError());
+  // each kernel leaves the other kind of instance alone
+  if (nrich > 0) {
+    fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
+    FAMS_CUDA(cudaGetLastError());
+  }
+  if (mr > 0) {
+    fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov);
+    FAMS_CUDA(cudaGetLastError());
+  }
   FAMS_CUDA(cudaEventRecord(e1, b.stream));
   FAMS_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;

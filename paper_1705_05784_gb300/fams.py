@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libfams.so")
 DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
 R_FV, R_FE = 0, 1
 FP64, MIXED = 0, 1
+KRYLOV_NONE, KRYLOV_GMRES = 0, 1
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ETIMEOUT, ECUDA, ECAPACITY = 0, -1, -2, -3, -4, -5, -6, -7
 
 Q = dict(NNC_FRAC=1, NNC_MATRIX=2, NNC_AREA=3, NNC_DIST=4, FF_A=5, FF_B=6, FF_T=7,
@@ -41,7 +42,8 @@ class fams_fracs(C.Structure):
 class fams_opts(C.Structure):
     _fields_ = [("coarsen", C.c_int * 3), ("frac_dmin", C.c_int), ("frac_cz", C.c_int),
                 ("basis", C.c_int), ("restriction", C.c_int), ("alpha", C.c_double),
-                ("max_iter", C.c_int), ("precision", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
+                ("restart", C.c_int)]
 
 
 class fams_stats(C.Structure):
@@ -114,7 +116,8 @@ def _args(prob):
     cz = prob.coarsen[2] if prob.dim == 3 else 1
     o = fams_opts((C.c_int * 3)(prob.coarsen[0], prob.coarsen[1], cz), prob.frac_dmin,
                   max(1, prob.frac_cz), prob.basis, prob.restriction, prob.alpha,
-                  prob.max_iter, getattr(prob, "precision", FP64))
+                  prob.max_iter, getattr(prob, "precision", FP64), getattr(prob, "krylov", 0),
+                  getattr(prob, "restart", 30))
     return g, perm, f, o, (xy, kf)
 
 

@@ -8,6 +8,8 @@ quantities that pass through local or coarse direct solves agree to 1e-10
 relative; converged pressures to 1e-10 relative L2 with iteration counts
 within +-1.
 """
+import copy
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -173,6 +175,63 @@ def test_solve_to_tolerance(built, name, variant):
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
 
 
+def _gmres(p, restart, max_iter):
+    q = copy.copy(p)
+    q.krylov, q.restart, q.max_iter = 1, restart, max_iter
+    return q
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+def test_gmres_trajectory(built, name, variant, restriction):
+    """GMRES(8) for 13 iterations (one restart): the GPU iterate and residual
+    history equal the oracle's (modified Gram-Schmidt there, classical
+    Gram-Schmidt twice here: the same Krylov space, rounding apart)."""
+    p, g, sysm, c, P, st, ctx = built(name, variant, restriction)
+    K, m = 13, 8
+    xo, ito, rro, _, ho = osolver.gmres_solve(st, tol=0.0, max_iter=K, restart=m, history=True)
+    with _fams().Context(_gmres(p, m, K)) as ck:
+        xs, stats = ck.solve(tol=0.0)
+        hg = ck.query("HISTORY")
+    assert stats[0]["iterations"] == K == ito
+    assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+    # entries that end a cycle are true residuals ||q - A x|| / ||q||: their
+    # rounding is absolute, about eps ||A|| ||x|| / ||q||
+    np.testing.assert_allclose(hg[:K + 1], ho, rtol=1e-8, atol=1e-12)
+    assert abs(stats[0]["rel_residual"] - rro) <= 1e-8 * rro + 1e-12
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+def test_gmres_solve_to_tolerance(built, name, variant):
+    p, g, sysm, c, P, st, ctx = built(name, variant)
+    xo, ito, rro, oko, _ = osolver.gmres_solve(st, tol=1e-8, max_iter=p.max_iter, restart=30)
+    with _fams().Context(_gmres(p, 30, p.max_iter)) as ck:
+        xs, stats = ck.solve(tol=1e-8)
+    x = xs[0]
+    assert stats[0]["converged"] and oko
+    assert abs(stats[0]["iterations"] - ito) <= 1
+    rr = np.linalg.norm(sysm.q - sysm.A @ x) / np.linalg.norm(sysm.q)
+    assert rr <= 1e-8
+    assert abs(rr - stats[0]["rel_residual"]) <= 1e-6 * rr + 1e-13
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+
+
+def test_gmres_and_richardson_instances_share_a_batch(built):
+    """A batch mixing both outer iterations gives each instance its own result."""
+    pa = _gmres(built("2d32", 0)[0], 30, 200)
+    pb = built("2d64", 3)[0]
+    with _fams().Context([pa, pb]) as cab, _fams().Context(pa) as ca, \
+            _fams().Context(pb) as cb:
+        xs, st = cab.solve(tol=1e-8)
+        xa, sa = ca.solve(tol=1e-8)
+        xb, sb = cb.solve(tol=1e-8)
+    assert st[0]["iterations"] == sa[0]["iterations"] and st[1]["iterations"] == sb[0]["iterations"]
+    assert np.linalg.norm(xs[0] - xa[0]) / np.linalg.norm(xa[0]) < 1e-10
+    assert np.linalg.norm(xs[1] - xb[0]) / np.linalg.norm(xb[0]) < 1e-10
+
+
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("name", ["2d32", "2d64", "3d"])
 def test_flux_conservative_and_matches_oracle(built, name, restriction):
@@ -218,7 +277,8 @@ def test_flux_conservative_and_matches_oracle(built, name, restriction):
 
 def test_batch_matches_single(built):
     """A batch of different instances gives each instance's single result
-    bit for bit (one CTA per instance, fixed reduction order)."""
+    (one CTA per instance, fixed reduction order in the iteration; the coarse
+    operator is summed with atomic additions, so results agree to rounding)."""
     fams = _fams()
     probs = [_case("2d32", 0), _case("2d64", 0), _case("2d50ragged", 3)]
     with fams.Context(probs) as cb:
