@@ -296,9 +296,10 @@ struct CompArgs {
 };
 
 // one dual block on a thread group: assemble [A'_BB | right-hand sides] with
-// leading dimension n + k, eliminate, write the block's rows of P
+// leading dimension n + k (then n doubles of pivot reciprocals), eliminate,
+// write the block's rows of P
 template <class G>
-__device__ void comp_solve(const CompArgs& a, int c, double* M) {
+__device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
   const int gr = G::rank(), gs = G::size();
   const int a0 = a.comp_off[c], n = a.comp_off[c + 1] - a0;
   const int k = a.colptr[c + 1] - a.colptr[c];
@@ -307,6 +308,7 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M) {
   const Inst& I = inst_of(a.inst, a.B, a.off_row, a.members[a0]);
   for (long long t = gr; t < (long long)n * ld; t += gs) M[t] = 0.0;
   G::sync();
+  int bl = 0, bu = 0;   // bandwidths of A'_BB in member order
   for (int i = gr; i < n; i += gs) {
     int r = a.members[a0 + i];
     int mr = medium_of(I, r), rr = a.rank[r];
@@ -322,6 +324,8 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M) {
           int pc = a.pos[cc];
           if (pc < 0 || pc >= n) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
           Mi[pc] = av;
+          bl = max(bl, i - pc);
+          bu = max(bu, pc - i);
         } else {
           int st = a.pstage[cc];
           const int* pc = a.pool.col[st] + a.poff[cc];
@@ -338,8 +342,10 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M) {
     }
     Mi[i] = d;
   }
+  bl = G::max(bl, red);
+  bu = G::max(bu, red);
   G::sync();
-  if (!ge_solve<G>(M, ld, n, k)) {
+  if (!ge_solve<G>(M, ld, n, k, bl, bu, M + (long long)n * ld)) {
     if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
     return;
   }
@@ -363,11 +369,12 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M) {
 template <class G>
 __global__ void k_comp_solve(CompArgs a, long long slice, double* gwork) {
   extern __shared__ double dsm[];
+  __shared__ int red[32];
   const int sub = G::per_warp ? (threadIdx.x >> 5) : 0;
   const long long idx = (long long)blockIdx.x * (G::per_warp ? (blockDim.x >> 5) : 1) + sub;
   if (idx >= a.ncomp) return;
   double* M = gwork ? gwork + (long long)blockIdx.x * slice : dsm + (long long)sub * slice;
-  comp_solve<G>(a, a.comp_list[idx], M);
+  comp_solve<G>(a, a.comp_list[idx], M, red);
 }
 
 // truncation (Sec. 4.3) and CSR of P
@@ -540,7 +547,7 @@ int phase_basis(Batch& b) {
     long long cmax[4] = {0, 0, 0, 0};
     for (long long c = 0; c < ncomp; ++c) {
       hpo[c + 1] = hpo[c] + (long long)hs[c] * hk[c];
-      long long need = (long long)hs[c] * ((long long)hs[c] + hk[c]);
+      long long need = (long long)hs[c] * ((long long)hs[c] + hk[c] + 1);   // [A'_BB | R], pivots
       int q = need <= WARP_NEED ? 0 : need <= MID_NEED ? 1 : need * 8 + 1024 <= max_smem ? 2 : 3;
       cls[q].push_back((int)c);
       cmax[q] = std::max(cmax[q], need);

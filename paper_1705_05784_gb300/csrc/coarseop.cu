@@ -243,6 +243,97 @@ __global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
   if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
 }
 
+// The same factorisation with the active columns in shared memory: step j
+// touches only columns j..j+kv, so a ring of kv + 1 band columns (column c in
+// slot c mod (kv + 1)) holds everything it reads or writes.  After step j,
+// column j goes back to global memory, its multipliers scaled by the pivot's
+// reciprocal as in LAPACK's gbtf2, and column j + kv + 1 takes its slot.
+__global__ void k_band_lu_win(const Inst* inst, int B, CoarseSys cs, int* err) {
+  extern __shared__ double win[];
+  int ii = blockIdx.x;
+  const Inst& I = inst[ii];
+  const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
+  const int W = kv + 1, T = blockDim.x;
+  double* AB = cs.band + cs.band_off[ii];
+  int* ipiv = cs.ipiv + I.nc_off;
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_jp, s_ju, s_bad, s_badcol;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
+  for (int idx = threadIdx.x; idx < min(W, n) * ldab; idx += T) win[idx] = AB[idx];
+  __syncthreads();
+#define WEL(i, c) win[((c) % W) * ldab + (kv + (i) - (c))]
+  for (int j = 0; j < n; ++j) {
+    const int km = min(kl, n - 1 - j);
+    // pivot search (largest magnitude, lowest index on ties)
+    double best = -1.0;
+    int bi = 0;
+    for (int t = threadIdx.x; t <= km; t += T) {
+      double v = fabs(WEL(j + t, j));
+      if (v > best) { best = v; bi = t; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = 0;
+      for (int w = 0; w < (int)(T >> 5); ++w)
+        if (sv[w] > b0 || (sv[w] == b0 && si[w] < i0)) { b0 = sv[w]; i0 = si[w]; }
+      s_jp = i0;
+      ipiv[j] = j + i0;
+      if (!(b0 > 0.0) || !isfinite(b0)) {
+        s_bad = 1;
+        s_badcol = j;
+      } else {
+        s_inv = 1.0 / WEL(j + i0, j);
+      }
+      s_ju = max(s_ju, min(j + ku + i0, n - 1));
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int jp = s_jp, ju = s_ju;
+    if (jp != 0) {
+      for (int c = j + threadIdx.x; c <= ju; c += T) {
+        double t = WEL(j, c);
+        WEL(j, c) = WEL(j + jp, c);
+        WEL(j + jp, c) = t;
+      }
+      __syncthreads();
+    }
+    // rank-1 update of rows j+1..j+km, columns j+1..ju (multipliers from the
+    // unscaled column j; it is scaled on its way back to global memory)
+    const double inv = s_inv;
+    const int w = ju - j;
+    for (int e = threadIdx.x; e < km * w; e += T) {
+      int c = j + 1 + e / km, t = 1 + e % km;
+      WEL(j + t, c) -= (WEL(j + t, j) * inv) * WEL(j, c);
+    }
+    __syncthreads();
+    // column j back to global (each thread its own rows), column j + W in
+    const int slot = (j % W) * ldab;
+    for (int r = threadIdx.x; r < ldab; r += T) {
+      double v = win[slot + r];
+      if (r > kv && r <= kv + km) v *= inv;
+      AB[(long long)ldab * j + r] = v;
+      if (j + W < n) win[slot + r] = AB[(long long)ldab * (j + W) + r];
+    }
+    __syncthreads();
+  }
+#undef WEL
+  if (s_bad) {
+    // columns still in the window go back unfactored from the failing step on
+    for (int c = max(0, s_badcol); c < min(n, s_badcol + W); ++c)
+      for (int r = threadIdx.x; r < ldab; r += T) AB[(long long)ldab * c + r] = win[(c % W) * ldab + r];
+  }
+  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
+}
+
 }  // namespace
 
 // mode < 0: each instance's own restriction; 0: R^FV for all; 1: R^FE for all
@@ -312,7 +403,20 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
                             cudaMemcpyHostToDevice, st));
   fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
-  fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
+  // shared-memory window of kv + 1 band columns when every instance's fits
+  size_t win = 0;
+  for (int i = 0; i < B; ++i)
+    win = std::max(win, sizeof(double) * (size_t)(ch.kl[i] + ch.ku[i] + 1) *
+                            (size_t)(2 * ch.kl[i] + ch.ku[i] + 1));
+  int max_smem = 0;
+  FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  if ((long long)win + 1024 <= max_smem) {
+    FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   max_smem - 1024));
+    fams::note_launch(), k_band_lu_win<<<B, 256, win, st>>>(b.d_inst, B, cs, b.d_err);
+  } else {
+    fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
+  }
   FAMS_CUDA(cudaGetLastError());
   ch.bad.assign(B, 0);
   FAMS_CUDA(cudaMemcpyAsync(ch.bad.data(), cs.bad, sizeof(int) * B, cudaMemcpyDeviceToHost, st));

@@ -85,7 +85,8 @@ __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, co
 }
 
 // step 3: the local TPFA problem of one primal block (global coarse index)
-// on a thread group: [K | rhs] with leading dimension m + 1, Neumann data
+// on a thread group: [K | rhs] with leading dimension m + 1 (then m doubles
+// of pivot reciprocals), Neumann data
 // from p' on the block boundary, pinned to p' at the block's coarse node when
 // no Dirichlet face closes it; dense elimination without pivoting
 struct LocalArgs {
@@ -109,7 +110,7 @@ struct LocalArgs {
 };
 
 template <class G>
-__device__ void flux_local(const LocalArgs& a, int c, double* K) {
+__device__ void flux_local(const LocalArgs& a, int c, double* K, int* red) {
   const int gr = G::rank(), gs = G::size();
   const Inst& I = a.inst[find_segment(a.off_nc, a.B + 1, c)];
   const int a0 = a.blk_ptr[c], m = a.blk_ptr[c + 1] - a0;
@@ -118,6 +119,7 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K) {
   G::sync();
   const int myblk = c - I.nc_off;
   bool hasD = false;
+  int bl = 0, bu = 0;   // bandwidths of K in block order
   for (int t = gr; t < m; t += gs) {
     int i = a.blk_cell[a0 + t];
     double* Kt = K + (long long)t * ld;
@@ -139,6 +141,8 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K) {
         if (pos < 0) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
         Kt[pos] -= T;
         d += T;
+        bl = max(bl, t - pos);
+        bu = max(bu, pos - t);
       } else {
         b -= T * (a.pp[i] - a.pp[j]);
       }
@@ -161,8 +165,10 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K) {
     double* Kp = K + (long long)pos * ld;
     for (int j = gr; j <= m; j += gs) Kp[j] = j == pos ? 1.0 : (j == m ? a.pp[v] : 0.0);
   }
+  bl = G::max(bl, red);
+  bu = G::max(bu, red);
   G::sync();
-  if (!ge_solve<G>(K, ld, m, 1)) {
+  if (!ge_solve<G>(K, ld, m, 1, bl, bu, K + (long long)m * ld)) {
     if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
     return;
   }
@@ -175,11 +181,12 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K) {
 template <class G>
 __global__ void k_flux_local(LocalArgs a, long long slice, double* gwork) {
   extern __shared__ double dsm[];
+  __shared__ int red[32];
   const int sub = G::per_warp ? (threadIdx.x >> 5) : 0;
   const long long idx = (long long)blockIdx.x * (G::per_warp ? (blockDim.x >> 5) : 1) + sub;
   if (idx >= a.nblk) return;
   double* K = gwork ? gwork + (long long)blockIdx.x * slice : dsm + (long long)sub * slice;
-  flux_local<G>(a, a.blk_list[idx], K);
+  flux_local<G>(a, a.blk_list[idx], K, red);
 }
 
 __device__ inline long long faces_of(const Inst& I) {
@@ -326,7 +333,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
     const Inst& I = b.h[ii];
     for (int c = I.nc_off; c < I.nc_off + I.nc; ++c) {
       long long m = hp[c + 1] - hp[c];
-      long long need = m * (m + 1);
+      long long need = m * (m + 2);   // [K | rhs], pivot reciprocals
       int q = need <= LOCAL_WARP_NEED ? 0 : need <= LOCAL_MID_NEED ? 1
             : need * 8 <= max_smem ? 2 : 3;
       cls[q].push_back(c);
