@@ -145,11 +145,13 @@ __global__ void k_bandwidth(const Inst* inst, int B, const int* off_nc, long lon
   atomicMax(&ku_out[ii], ku);
 }
 
+// only (nullable): instances to fill
 __global__ void k_band_fill(const Inst* inst, int B, const int* off_nc, long long nct,
-                            CoarseSys cs, const int* ip_all) {
+                            CoarseSys cs, const int* ip_all, const int* only) {
   long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nct) return;
   int ii = find_segment(off_nc, B + 1, w);
+  if (only && !only[ii]) return;
   const Inst& I = inst[ii];
   int r = (int)(w - I.nc_off);
   int kl = cs.kl[ii], ku = cs.ku[ii], ldab = 2 * kl + ku + 1;
@@ -176,8 +178,9 @@ __global__ void k_inverse_perm(const Inst* inst, int B, const int* off_nc, long 
 }
 
 // band LU with partial pivoting, one CTA per instance
-__global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
+__global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, const int* only, int* err) {
   int ii = blockIdx.x;
+  if (only && !only[ii]) return;
   const Inst& I = inst[ii];
   int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
   double* AB = cs.band + cs.band_off[ii];
@@ -248,9 +251,10 @@ __global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, int* err) {
 // slot c mod (kv + 1)) holds everything it reads or writes.  After step j,
 // column j goes back to global memory, its multipliers scaled by the pivot's
 // reciprocal as in LAPACK's gbtf2, and column j + kv + 1 takes its slot.
-__global__ void k_band_lu_win(const Inst* inst, int B, CoarseSys cs, int* err) {
+__global__ void k_band_lu_win(const Inst* inst, int B, CoarseSys cs, const int* only, int* err) {
   extern __shared__ double win[];
   int ii = blockIdx.x;
+  if (only && !only[ii]) return;
   const Inst& I = inst[ii];
   const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
   const int W = kv + 1, T = blockDim.x;
@@ -334,6 +338,72 @@ __global__ void k_band_lu_win(const Inst* inst, int B, CoarseSys cs, int* err) {
   if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
 }
 
+// Symmetric positive definite coarse systems (R^FE = P^T: A_c = P^T A P):
+// band LDL^T without pivoting, about a quarter of the band LU's work.  The
+// active lower triangle (rows and columns j..j+kl) lives in a shared-memory
+// ring of K = kl + 1 rows and columns, element (i, c) at slot
+// (i mod K, c mod K).  The factors are written in the band LU's layout, so
+// the solves need no second code path: unit lower multipliers
+// L'(i,j) = S(i,j) / d_j, upper row U(j,c) = S(c,j) (= d_j L'(c,j)), pivot
+// rows ipiv[j] = j.  A non-positive or non-finite pivot sets failed[ii]; the
+// host then refactors that instance with the band LU.
+__global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* only, int* failed) {
+  extern __shared__ double S[];
+  int ii = blockIdx.x;
+  if (!only[ii]) return;
+  const Inst& I = inst[ii];
+  const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
+  const int K = kl + 1, T = blockDim.x;
+  double* AB = cs.band + cs.band_off[ii];
+  int* ipiv = cs.ipiv + I.nc_off;
+  double* lj = S + (long long)K * K;   // multipliers of the current column
+#define SEL(i, c) S[((i) % K) * K + ((c) % K)]
+#define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
+  // rows 0..K-1 of the lower triangle
+  for (int e = threadIdx.x; e < K * K; e += T) {
+    int i = e / K, c = e - i * K;
+    if (i < n && c <= i && i - c <= kl) SEL(i, c) = BEL(i, c);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int km = min(kl, n - 1 - j);
+    const double d = SEL(j, j);
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) failed[ii] = 1;
+      return;
+    }
+    const double inv = 1.0 / d;
+    for (int t = threadIdx.x; t < km; t += T) lj[t] = SEL(j + 1 + t, j) * inv;
+    __syncthreads();
+    // S(i, c) -= L'(i, j) S(c, j) for j < c <= i <= j + km
+    for (int e = threadIdx.x; e < km * km; e += T) {
+      int r = e / km, q = e - r * km;
+      if (q <= r) SEL(j + 1 + r, j + 1 + q) -= lj[r] * SEL(j + 1 + q, j);
+    }
+    __syncthreads();
+    // column j of the factors back to the band: pivot, multipliers, and the
+    // upper row U(j, c) = S(c, j) stored in column c
+    for (int t = threadIdx.x; t <= km; t += T) {
+      if (t == 0) {
+        BEL(j, j) = d;
+        ipiv[j] = j;
+      } else {
+        BEL(j + t, j) = lj[t - 1];
+        BEL(j, j + t) = SEL(j + t, j);
+      }
+    }
+    __syncthreads();
+    // row j + K of the original matrix takes row j's slot
+    const int i = j + K;
+    if (i < n)
+      for (int c = i - kl + threadIdx.x; c <= i; c += T) SEL(i, c) = BEL(i, c);
+    __syncthreads();
+  }
+#undef SEL
+#undef BEL
+  if (threadIdx.x == 0) cs.bad[ii] = 0;
+}
+
 }  // namespace
 
 // mode < 0: each instance's own restriction; 0: R^FV for all; 1: R^FE for all
@@ -402,20 +472,70 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
                             cudaMemcpyHostToDevice, st));
-  fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
-  // shared-memory window of kv + 1 band columns when every instance's fits
-  size_t win = 0;
-  for (int i = 0; i < B; ++i)
-    win = std::max(win, sizeof(double) * (size_t)(ch.kl[i] + ch.ku[i] + 1) *
-                            (size_t)(2 * ch.kl[i] + ch.ku[i] + 1));
+  fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip,
+                                                                   nullptr);
+  // factorisation: LDL^T for the symmetric positive definite (R^FE) systems
+  // whose active triangle fits in shared memory, band LU for the others and
+  // for any LDL^T that meets a non-positive pivot
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
-  if ((long long)win + 1024 <= max_smem) {
-    FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   max_smem - 1024));
-    fams::note_launch(), k_band_lu_win<<<B, 256, win, st>>>(b.d_inst, B, cs, b.d_err);
-  } else {
-    fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, b.d_err);
+  max_smem -= 1024;   // static shared memory of the kernels
+  std::vector<int> spd(B, 0), lu(B, 0);
+  size_t ldl_smem = 0;
+  for (int i = 0; i < B; ++i) {
+    bool fe = mode == 1 || (mode < 0 && b.h[i].restriction == FAMS_R_FE);
+    size_t need = sizeof(double) * ((size_t)(ch.kl[i] + 1) * (ch.kl[i] + 1) + ch.kl[i] + 1);
+    if (fe && ch.kl[i] == ch.ku[i] && need <= (size_t)max_smem) {
+      spd[i] = 1;
+      ldl_smem = std::max(ldl_smem, need);
+    } else {
+      lu[i] = 1;
+    }
+  }
+  int *d_spd = nullptr, *d_lu = nullptr;
+  FAMS_TRY(b.scratch((void**)&d_spd, sizeof(int) * B));
+  FAMS_TRY(b.scratch((void**)&d_lu, sizeof(int) * B));
+  FAMS_CUDA(cudaMemcpyAsync(d_spd, spd.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemsetAsync(d_lu, 0, sizeof(int) * B, st));
+  FAMS_CUDA(cudaMemsetAsync(cs.bad, 0, sizeof(int) * B, st));
+  if (ldl_smem > 0) {
+    FAMS_CUDA(cudaFuncSetAttribute(k_band_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   max_smem));
+    fams::note_launch(), k_band_ldl<<<B, 256, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu);
+    FAMS_CUDA(cudaGetLastError());
+    std::vector<int> failed(B, 0);
+    FAMS_CUDA(cudaMemcpyAsync(failed.data(), d_lu, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int i = 0; i < B; ++i) any |= failed[i] != 0;
+    if (any) {   // back to the assembled matrix for the band LU
+      for (int i = 0; i < B; ++i)
+        if (failed[i])
+          FAMS_CUDA(cudaMemsetAsync(cs.band + ch.band_off[i], 0,
+                                    sizeof(double) * (2 * ch.kl[i] + ch.ku[i] + 1) * b.h[i].nc, st));
+      fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct,
+                                                                         cs, ip, d_lu);
+    }
+    for (int i = 0; i < B; ++i) lu[i] |= failed[i];
+  }
+  // band LU: the shared-memory window of kv + 1 band columns when it fits
+  size_t win = 0;
+  bool any_lu = false;
+  for (int i = 0; i < B; ++i)
+    if (lu[i]) {
+      any_lu = true;
+      win = std::max(win, sizeof(double) * (size_t)(ch.kl[i] + ch.ku[i] + 1) *
+                              (size_t)(2 * ch.kl[i] + ch.ku[i] + 1));
+    }
+  if (any_lu) {
+    FAMS_CUDA(cudaMemcpyAsync(d_lu, lu.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    if (win <= (size_t)max_smem) {
+      FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     max_smem));
+      fams::note_launch(), k_band_lu_win<<<B, 256, win, st>>>(b.d_inst, B, cs, d_lu, b.d_err);
+    } else {
+      fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, d_lu, b.d_err);
+    }
   }
   FAMS_CUDA(cudaGetLastError());
   ch.bad.assign(B, 0);

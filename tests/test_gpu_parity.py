@@ -128,6 +128,46 @@ def test_coarse_operator(built, name, restriction):
     np.testing.assert_allclose(Ac, st.Ac, rtol=0, atol=1e-11 * np.abs(st.Ac).max())
 
 
+def _band_solve(AB, ipiv, kl, ku, b):
+    """LAPACK gbtrs on band factors (column-major, ldab = 2 kl + ku + 1):
+    row interchanges and unit lower multipliers, then the upper band."""
+    n = len(b)
+    kv = kl + ku
+    y = b.astype(np.float64).copy()
+    for j in range(n):
+        p = ipiv[j]
+        if p != j:
+            y[j], y[p] = y[p], y[j]
+        km = min(kl, n - 1 - j)
+        y[j + 1:j + 1 + km] -= AB[kv + 1:kv + 1 + km, j] * y[j]
+    for j in range(n - 1, -1, -1):
+        y[j] /= AB[kv, j]
+        i0 = max(0, j - kv)
+        y[i0:j] -= AB[kv - (j - i0):kv, j] * y[j]
+    return y
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_factors_solve_the_coarse_system(built, name, restriction):
+    """The band factors (LDL^T written as LU for R^FE, partial-pivoting band LU
+    for R^FV) solve the reordered coarse system: backward error at rounding."""
+    p, g, sysm, c, P, st, ctx = built(name, 0, restriction)
+    nc = c.n_coarse
+    Ac = ctx.query("AC").reshape(nc, nc)
+    perm = ctx.query("COARSE_PERM")
+    ipiv = ctx.query("COARSE_IPIV")
+    kl, ku = ctx.query("BAND_KLKU")
+    AB = ctx.query("BAND").reshape(nc, 2 * kl + ku + 1).T
+    Ab = Ac[np.ix_(perm, perm)]
+    rhs = np.random.default_rng(11).standard_normal(nc)
+    x = _band_solve(AB, ipiv, kl, ku, rhs)
+    berr = np.linalg.norm(Ab @ x - rhs) / (np.linalg.norm(Ab, np.inf) * np.linalg.norm(x, np.inf) + np.linalg.norm(rhs, np.inf))
+    assert berr < 1e-13
+    if restriction == 1:
+        assert np.array_equal(ipiv, np.arange(nc))   # symmetric positive definite: no pivoting
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_ilu0(built, name):
     p, g, sysm, c, P, st, ctx = built(name)
