@@ -177,166 +177,7 @@ __global__ void k_inverse_perm(const Inst* inst, int B, const int* off_nc, long 
   ip_all[I.nc_off + cs.perm[w]] = k;
 }
 
-// band LU with partial pivoting, one CTA per instance
-__global__ void k_band_lu(const Inst* inst, int B, CoarseSys cs, const int* only, int* err) {
-  int ii = blockIdx.x;
-  if (only && !only[ii]) return;
-  const Inst& I = inst[ii];
-  int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
-  double* AB = cs.band + cs.band_off[ii];
-  int* ipiv = cs.ipiv + I.nc_off;
-  __shared__ double sv[32];
-  __shared__ int si[32];
-  __shared__ int s_jp, s_ju, s_bad, s_badcol;
-  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
-  __syncthreads();
-#define AEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
-  for (int j = 0; j < n; ++j) {
-    int km = min(kl, n - 1 - j);
-    // pivot search (largest magnitude, lowest index on ties)
-    double best = -1.0;
-    int bi = 0;
-    for (int t = threadIdx.x; t <= km; t += blockDim.x) {
-      double v = fabs(AEL(j + t, j));
-      if (v > best) { best = v; bi = t; }
-    }
-    for (int o = 16; o; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b0 = -1.0;
-      int i0 = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-        if (sv[w] > b0 || (sv[w] == b0 && si[w] < i0)) { b0 = sv[w]; i0 = si[w]; }
-      s_jp = i0;
-      ipiv[j] = j + i0;
-      if (!(b0 > 0.0) || !isfinite(b0)) {
-        s_bad = 1;
-        s_badcol = j;
-      }
-      s_ju = max(s_ju, min(j + ku + i0, n - 1));
-    }
-    __syncthreads();
-    if (s_bad) break;
-    int jp = s_jp, ju = s_ju;
-    if (jp != 0) {
-      for (int c = j + threadIdx.x; c <= ju; c += blockDim.x) {
-        double t = AEL(j, c);
-        AEL(j, c) = AEL(j + jp, c);
-        AEL(j + jp, c) = t;
-      }
-      __syncthreads();
-    }
-    double piv = AEL(j, j);
-    for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) AEL(j + t, j) /= piv;
-    __syncthreads();
-    int w = ju - j;
-    for (int e = threadIdx.x; e < km * w; e += blockDim.x) {
-      int t = 1 + e % km, c = j + 1 + e / km;
-      AEL(j + t, c) -= AEL(j + t, j) * AEL(j, c);
-    }
-    __syncthreads();
-  }
-#undef AEL
-  // a numerically singular coarse system fails this instance only
-  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
-}
-
-// The same factorisation with the active columns in shared memory: step j
-// touches only columns j..j+kv, so a ring of kv + 1 band columns (column c in
-// slot c mod (kv + 1)) holds everything it reads or writes.  After step j,
-// column j goes back to global memory, its multipliers scaled by the pivot's
-// reciprocal as in LAPACK's gbtf2, and column j + kv + 1 takes its slot.
-__global__ void k_band_lu_win(const Inst* inst, int B, CoarseSys cs, const int* only, int* err) {
-  extern __shared__ double win[];
-  int ii = blockIdx.x;
-  if (only && !only[ii]) return;
-  const Inst& I = inst[ii];
-  const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
-  const int W = kv + 1, T = blockDim.x;
-  double* AB = cs.band + cs.band_off[ii];
-  int* ipiv = cs.ipiv + I.nc_off;
-  __shared__ double sv[32];
-  __shared__ int si[32];
-  __shared__ int s_jp, s_ju, s_bad, s_badcol;
-  __shared__ double s_inv;
-  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
-  for (int idx = threadIdx.x; idx < min(W, n) * ldab; idx += T) win[idx] = AB[idx];
-  __syncthreads();
-#define WEL(i, c) win[((c) % W) * ldab + (kv + (i) - (c))]
-  for (int j = 0; j < n; ++j) {
-    const int km = min(kl, n - 1 - j);
-    // pivot search (largest magnitude, lowest index on ties)
-    double best = -1.0;
-    int bi = 0;
-    for (int t = threadIdx.x; t <= km; t += T) {
-      double v = fabs(WEL(j + t, j));
-      if (v > best) { best = v; bi = t; }
-    }
-    for (int o = 16; o; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b0 = -1.0;
-      int i0 = 0;
-      for (int w = 0; w < (int)(T >> 5); ++w)
-        if (sv[w] > b0 || (sv[w] == b0 && si[w] < i0)) { b0 = sv[w]; i0 = si[w]; }
-      s_jp = i0;
-      ipiv[j] = j + i0;
-      if (!(b0 > 0.0) || !isfinite(b0)) {
-        s_bad = 1;
-        s_badcol = j;
-      } else {
-        s_inv = 1.0 / WEL(j + i0, j);
-      }
-      s_ju = max(s_ju, min(j + ku + i0, n - 1));
-    }
-    __syncthreads();
-    if (s_bad) break;
-    const int jp = s_jp, ju = s_ju;
-    if (jp != 0) {
-      for (int c = j + threadIdx.x; c <= ju; c += T) {
-        double t = WEL(j, c);
-        WEL(j, c) = WEL(j + jp, c);
-        WEL(j + jp, c) = t;
-      }
-      __syncthreads();
-    }
-    // rank-1 update of rows j+1..j+km, columns j+1..ju (multipliers from the
-    // unscaled column j; it is scaled on its way back to global memory)
-    const double inv = s_inv;
-    const int w = ju - j;
-    for (int e = threadIdx.x; e < km * w; e += T) {
-      int c = j + 1 + e / km, t = 1 + e % km;
-      WEL(j + t, c) -= (WEL(j + t, j) * inv) * WEL(j, c);
-    }
-    __syncthreads();
-    // column j back to global (each thread its own rows), column j + W in
-    const int slot = (j % W) * ldab;
-    for (int r = threadIdx.x; r < ldab; r += T) {
-      double v = win[slot + r];
-      if (r > kv && r <= kv + km) v *= inv;
-      AB[(long long)ldab * j + r] = v;
-      if (j + W < n) win[slot + r] = AB[(long long)ldab * (j + W) + r];
-    }
-    __syncthreads();
-  }
-#undef WEL
-  if (s_bad) {
-    // columns still in the window go back unfactored from the failing step on
-    for (int c = max(0, s_badcol); c < min(n, s_badcol + W); ++c)
-      for (int r = threadIdx.x; r < ldab; r += T) AB[(long long)ldab * c + r] = win[(c % W) * ldab + r];
-  }
-  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
-}
+__device__ inline int wrap(int x, int k) { return x >= k ? x - k : x; }
 
 // Symmetric positive definite coarse systems (R^FE = P^T: A_c = P^T A P):
 // band LDL^T without pivoting, about a quarter of the band LU's work.  The
@@ -354,54 +195,161 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
   const Inst& I = inst[ii];
   const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
   const int K = kl + 1, T = blockDim.x;
+  const int nw = T >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* AB = cs.band + cs.band_off[ii];
   int* ipiv = cs.ipiv + I.nc_off;
-  double* lj = S + (long long)K * K;   // multipliers of the current column
-#define SEL(i, c) S[((i) % K) * K + ((c) % K)]
+  double* colj = S + (long long)K * K;   // column j below the pivot
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
-  // rows 0..K-1 of the lower triangle
   for (int e = threadIdx.x; e < K * K; e += T) {
     int i = e / K, c = e - i * K;
-    if (i < n && c <= i && i - c <= kl) SEL(i, c) = BEL(i, c);
+    S[e] = (i < n && c <= i && i - c <= kl) ? BEL(i, c) : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const int km = min(kl, n - 1 - j);
-    const double d = SEL(j, j);
+    const int js = j % K, base = wrap(js + 1, K);
+    const double d = S[js * K + js];
     if (!(d > 0.0) || !isfinite(d)) {
       if (threadIdx.x == 0) failed[ii] = 1;
       return;
     }
     const double inv = 1.0 / d;
-    for (int t = threadIdx.x; t < km; t += T) lj[t] = SEL(j + 1 + t, j) * inv;
+    for (int t = threadIdx.x; t < km; t += T) colj[t] = S[wrap(base + t, K) * K + js];
     __syncthreads();
-    // S(i, c) -= L'(i, j) S(c, j) for j < c <= i <= j + km
-    for (int e = threadIdx.x; e < km * km; e += T) {
-      int r = e / km, q = e - r * km;
-      if (q <= r) SEL(j + 1 + r, j + 1 + q) -= lj[r] * SEL(j + 1 + q, j);
+    // S(i, c) -= L'(i, j) S(c, j) for j < c <= i <= j + km: a warp per row
+    for (int r = w; r < km; r += nw) {
+      double* row = S + wrap(base + r, K) * K;
+      const double lr = colj[r] * inv;
+      for (int q = lane; q <= r; q += 32) row[wrap(base + q, K)] -= lr * colj[q];
     }
-    __syncthreads();
     // column j of the factors back to the band: pivot, multipliers, and the
-    // upper row U(j, c) = S(c, j) stored in column c
+    // upper row U(j, c) = S(c, j) stored in column c (from colj: no ring
+    // reads, so this overlaps the update)
     for (int t = threadIdx.x; t <= km; t += T) {
       if (t == 0) {
         BEL(j, j) = d;
         ipiv[j] = j;
       } else {
-        BEL(j + t, j) = lj[t - 1];
-        BEL(j, j + t) = SEL(j + t, j);
+        BEL(j + t, j) = colj[t - 1] * inv;
+        BEL(j, j + t) = colj[t - 1];
       }
     }
     __syncthreads();
     // row j + K of the original matrix takes row j's slot
     const int i = j + K;
     if (i < n)
-      for (int c = i - kl + threadIdx.x; c <= i; c += T) SEL(i, c) = BEL(i, c);
+      for (int c = i - kl + threadIdx.x; c <= i; c += T) S[js * K + c % K] = BEL(i, c);
+    __syncthreads();
+  }
+#undef BEL
+  if (threadIdx.x == 0) cs.bad[ii] = 0;
+}
+
+// Band LU with partial pivoting (LAPACK gbtf2 steps) on the active block
+// only: rows j..j+kl and columns j..j+kv, a ring of (kl+1) x (kv+1) doubles,
+// element (i, c) at (i mod (kl+1), c mod (kv+1)), in shared memory or, when
+// it does not fit, in a per-CTA slice of global memory (`gws`, `gstride`
+// doubles per CTA).  Each finished pivot row and multiplier column goes
+// back to the band; row j + kl + 1 and column j + kv + 1 enter the ring in
+// their place.
+__global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* only, int* err,
+                              double* gws, long long gstride) {
+  extern __shared__ double dyn[];
+  int ii = blockIdx.x;
+  if (!only[ii]) return;
+  const Inst& I = inst[ii];
+  const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
+  const int K1 = kl + 1, K2 = kv + 1, T = blockDim.x;
+  const int nw = T >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* S = gws ? gws + (long long)blockIdx.x * gstride : dyn;
+  double* lj = gws ? dyn : dyn + (long long)K1 * K2;   // multipliers of column j
+  double* ur = lj + K1;                                // pivot row j
+  double* AB = cs.band + cs.band_off[ii];
+  int* ipiv = cs.ipiv + I.nc_off;
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_jp, s_ju, s_bad, s_badcol;
+  __shared__ double s_piv;
+#define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
+#define SEL(rs, c) S[(long long)(rs) * K2 + (c)]
+  if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
+  for (int e = threadIdx.x; e < K1 * K2; e += T) {
+    int i = e / K2, c = e - i * K2;
+    S[e] = (i < n && c < n && c - i <= ku && i - c <= kl) ? BEL(i, c) : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int km = min(kl, n - 1 - j);
+    const int jr = j % K1, jc = j % K2;
+    double best = -1.0;
+    int bi = 0;
+    for (int t = threadIdx.x; t <= km; t += T) {
+      double v = fabs(SEL(wrap(jr + t, K1), jc));
+      if (v > best) { best = v; bi = t; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[w] = best; si[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = 0;
+      for (int q = 0; q < nw; ++q)
+        if (sv[q] > b0 || (sv[q] == b0 && si[q] < i0)) { b0 = sv[q]; i0 = si[q]; }
+      s_jp = i0;
+      ipiv[j] = j + i0;
+      if (!(b0 > 0.0) || !isfinite(b0)) {
+        s_bad = 1;
+        s_badcol = j;
+      } else {
+        s_piv = SEL(wrap(jr + i0, K1), jc);
+      }
+      s_ju = max(s_ju, min(j + ku + i0, n - 1));
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int jp = s_jp, ju = s_ju, wd = ju - j;
+    const double piv = s_piv, inv = 1.0 / piv;
+    if (jp != 0) {
+      const int pr = wrap(jr + jp, K1);
+      for (int cc = threadIdx.x; cc <= wd; cc += T) {
+        int c = wrap(jc + cc, K2);
+        double t = SEL(jr, c);
+        SEL(jr, c) = SEL(pr, c);
+        SEL(pr, c) = t;
+      }
+      __syncthreads();
+    }
+    for (int t = 1 + threadIdx.x; t <= km; t += T) lj[t] = SEL(wrap(jr + t, K1), jc) * inv;
+    for (int cc = 1 + threadIdx.x; cc <= wd; cc += T) ur[cc] = SEL(jr, wrap(jc + cc, K2));
+    __syncthreads();
+    // rank-1 update: a warp per row, lanes along the pivot row
+    for (int t = 1 + w; t <= km; t += nw) {
+      const int rs = wrap(jr + t, K1);
+      const double l = lj[t];
+      for (int cc = 1 + lane; cc <= wd; cc += 32) SEL(rs, wrap(jc + cc, K2)) -= l * ur[cc];
+    }
+    // finished pivot row and multipliers back to the band (temporaries only)
+    for (int cc = threadIdx.x; cc <= wd; cc += T) BEL(j, j + cc) = cc == 0 ? piv : ur[cc];
+    for (int t = 1 + threadIdx.x; t <= km; t += T) BEL(j + t, j) = lj[t];
+    __syncthreads();
+    // column slot jc becomes column j + K2 (zero in the active rows), row
+    // slot jr becomes row j + K1 of the original matrix
+    const int inew = j + K1;
+    for (int rs = threadIdx.x; rs < K1; rs += T)
+      if (rs != jr) SEL(rs, jc) = 0.0;
+    for (int cc = 1 + threadIdx.x; cc <= K2; cc += T) {
+      int c = j + cc;
+      SEL(jr, wrap(jc + cc, K2)) = (inew < n && c < n) ? BEL(inew, c) : 0.0;
+    }
     __syncthreads();
   }
 #undef SEL
 #undef BEL
-  if (threadIdx.x == 0) cs.bad[ii] = 0;
+  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
 }
 
 }  // namespace
@@ -518,24 +466,38 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
     }
     for (int i = 0; i < B; ++i) lu[i] |= failed[i];
   }
-  // band LU: the shared-memory window of kv + 1 band columns when it fits
-  size_t win = 0;
-  bool any_lu = false;
-  for (int i = 0; i < B; ++i)
-    if (lu[i]) {
-      any_lu = true;
-      win = std::max(win, sizeof(double) * (size_t)(ch.kl[i] + ch.ku[i] + 1) *
-                              (size_t)(2 * ch.kl[i] + ch.ku[i] + 1));
-    }
-  if (any_lu) {
-    FAMS_CUDA(cudaMemcpyAsync(d_lu, lu.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-    if (win <= (size_t)max_smem) {
-      FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     max_smem));
-      fams::note_launch(), k_band_lu_win<<<B, 256, win, st>>>(b.d_inst, B, cs, d_lu, b.d_err);
+  // band LU on the active block: in shared memory where it fits, else in a
+  // global workspace per CTA
+  std::vector<int> lu_s(B, 0), lu_g(B, 0);
+  size_t act_s = 0, act_g = 0, temps = 0;
+  for (int i = 0; i < B; ++i)   // multipliers and pivot row of the widest band
+    if (lu[i]) temps = std::max(temps, sizeof(double) * (size_t)(2 * ch.kl[i] + ch.ku[i] + 2));
+  for (int i = 0; i < B; ++i) {
+    if (!lu[i]) continue;
+    size_t act = (size_t)(ch.kl[i] + 1) * (size_t)(ch.kl[i] + ch.ku[i] + 1);
+    if (sizeof(double) * act + temps <= (size_t)max_smem) {
+      lu_s[i] = 1;
+      act_s = std::max(act_s, act);
     } else {
-      fams::note_launch(), k_band_lu<<<B, 512, 0, st>>>(b.d_inst, B, cs, d_lu, b.d_err);
+      lu_g[i] = 1;
+      act_g = std::max(act_g, act);
     }
+  }
+  FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem));
+  if (act_s > 0) {
+    FAMS_CUDA(cudaMemcpyAsync(d_lu, lu_s.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_s + temps, st>>>(
+        b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0);
+  }
+  if (act_g > 0) {
+    int* d_lg = nullptr;
+    double* gws = nullptr;
+    FAMS_TRY(b.scratch((void**)&d_lg, sizeof(int) * B));
+    FAMS_TRY(b.scratch((void**)&gws, sizeof(double) * act_g * (size_t)B));
+    FAMS_CUDA(cudaMemcpyAsync(d_lg, lu_g.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    fams::note_launch(), k_band_lu_act<<<B, 256, temps, st>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
+                                                                (long long)act_g);
   }
   FAMS_CUDA(cudaGetLastError());
   ch.bad.assign(B, 0);

@@ -168,6 +168,43 @@ def test_coarse_factors_solve_the_coarse_system(built, name, restriction):
         assert np.array_equal(ipiv, np.arange(nc))   # symmetric positive definite: no pivoting
 
 
+def _check_band_factors(ctx, i):
+    nc = ctx.sizes(i)["n_coarse"]
+    Ac = ctx.query("AC", i).reshape(nc, nc)
+    perm = ctx.query("COARSE_PERM", i)
+    ipiv = ctx.query("COARSE_IPIV", i)
+    kl, ku = ctx.query("BAND_KLKU", i)
+    AB = ctx.query("BAND", i).reshape(nc, 2 * kl + ku + 1).T
+    Ab = Ac[np.ix_(perm, perm)]
+    rhs = np.random.default_rng(i).standard_normal(nc)
+    x = _band_solve(AB, ipiv, kl, ku, rhs)
+    berr = np.linalg.norm(Ab @ x - rhs) / (np.linalg.norm(Ab, np.inf) * np.linalg.norm(x, np.inf)
+                                         + np.linalg.norm(rhs, np.inf))
+    assert berr < 1e-13, (i, berr)
+    return kl
+
+
+def test_coarse_factors_at_bench_size():
+    """256x256 instances, R^FV (band LU) and R^FE (LDL^T), bandwidths ~60-150."""
+    fams = _fams()
+    probs = [inputs.config_2d_256(seed=500 + i, tratio=1e4, basis=i % 4, restriction=i % 2,
+                                  alpha=1e-2) for i in range(16)]
+    with fams.Context(probs) as cb:
+        for i in range(len(probs)):
+            _check_band_factors(cb, i)
+
+
+def test_coarse_factors_of_wide_bands():
+    """3D 64x64x32 with 4x4x4 coarsening and R^FV: a coarse bandwidth beyond
+    what shared memory holds ((kl+1)(2kl+1) doubles > 227 KB for kl > 118),
+    so the band LU runs on its global-memory active block."""
+    fams = _fams()
+    p = inputs.config_3d(64, 64, 32, 1.0, (8, 8, 4), 6, (8, 24), 1e3, (4, 4, 4), 6, 4, seed=21,
+                         basis=0, restriction=0)
+    with fams.Context(p) as c1:
+        assert _check_band_factors(c1, 0) > 118
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_ilu0(built, name):
     p, g, sysm, c, P, st, ctx = built(name)
