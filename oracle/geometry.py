@@ -14,8 +14,8 @@ Embedded discrete fractures on a structured matrix grid:
   overlap gives one matrix-fracture connection with area A_ij (overlap length
   x depth) and average distance <d>_ij (Eq. 7, CI_ij = A_ij/<d>_ij);
 * <d>_ij is the mean distance from the matrix cell to the fracture's line,
-  evaluated with a fixed 64 x 64 midpoint rule (a vertical plate gives the 2D
-  value in every layer);
+  integrated exactly (the cell clipped by the line; a vertical plate gives
+  the 2D value in every layer);
 * fracture-fracture intersections (Sec. 4.1: an explicit intersection
   pressure with a flux balance) are eliminated exactly: for the two cells that
   meet at the intersection point, T_ab = T_a T_b / (T_a + T_b) with
@@ -33,7 +33,6 @@ import math
 
 import numpy as np
 
-MIDPOINT_N = 64          # points per axis of the <d> midpoint rule
 ZERO_PIECE = 1e-12       # pieces shorter than this x h_f are dropped
 DIST_FLOOR = 1e-3        # intersection distance floor, x h_f
 
@@ -117,18 +116,41 @@ def piece_overlaps(ax, ay, bx, by, n, s, dx, dy, nx, ny, hf=1.0):
 
 
 def mean_distance(ax, ay, bx, by, ix, iy, dx, dy):
-    """<d>: mean distance from matrix cell (ix,iy) to the infinite line through A,B
-    (Eq. 7), by the 64 x 64 midpoint rule."""
+    """<d> (Eq. 7): mean distance from matrix cell (ix, iy) to the infinite
+    line through A, B.
+
+    The signed distance f(x) = n . (x - A) is linear, so its integral over a
+    triangle is the area times the mean of f at the three corners.  With P+
+    the part of the cell where f >= 0 (the cell rectangle clipped by that
+    half-plane, a convex polygon), int_cell |f| = 2 int_{P+} f - int_cell f,
+    and int_cell f = area * f(centre).  Coordinates are taken relative to the
+    cell's lower-left corner."""
     ex, ey = bx - ax, by - ay
     L = _len(ex, ey)
-    tx, ty = ex / L, ey / L
-    m = MIDPOINT_N
-    u = (np.arange(m, dtype=np.float64) + 0.5) / m
-    px = ix * dx + u * dx
-    py = iy * dy + u * dy
-    X, Y = np.meshgrid(px, py, indexing="ij")
-    d = np.abs(tx * (Y - ay) - ty * (X - ax))
-    return float(d.sum() / (m * m))
+    nx, ny = -ey / L, ex / L
+    x0, y0 = ix * dx, iy * dy
+    ox, oy = ax - x0, ay - y0          # A relative to the corner
+
+    def f(x, y):
+        return nx * (x - ox) + ny * (y - oy)
+
+    rect = [(0.0, 0.0), (dx, 0.0), (dx, dy), (0.0, dy)]
+    poly = []
+    for k in range(4):                 # clip by f >= 0 (Sutherland-Hodgman)
+        p, q = rect[k], rect[(k + 1) % 4]
+        fp, fq = f(*p), f(*q)
+        if fp >= 0.0:
+            poly.append(p)
+        if (fp >= 0.0) != (fq >= 0.0):
+            t = fp / (fp - fq)
+            poly.append((p[0] + t * (q[0] - p[0]), p[1] + t * (q[1] - p[1])))
+    pos = 0.0                          # int over P+ of f, by a fan of triangles
+    for k in range(1, len(poly) - 1):
+        (x1, y1), (x2, y2), (x3, y3) = poly[0], poly[k], poly[k + 1]
+        area = 0.5 * ((x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1))
+        pos += area * (f(x1, y1) + f(x2, y2) + f(x3, y3)) / 3.0
+    A = dx * dy
+    return float((2.0 * pos - A * f(0.5 * dx, 0.5 * dy)) / A)
 
 
 class Geometry:

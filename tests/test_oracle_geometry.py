@@ -34,8 +34,7 @@ def test_axis_aligned_fracture_cells_and_overlaps():
     assert list(g.nnc_f) == list(range(10))
     assert list(g.nnc_m) == [2 + s + 16 * 5 for s in range(10)]
     np.testing.assert_allclose(g.nnc_area, 1.0, rtol=0, atol=1e-14)
-    # the line runs through the cell middle: <d> = 1/4 exactly (midpoint rule
-    # is exact for a kink on a quadrature cell boundary)
+    # the line runs through the cell middle: <d> = 1/4 exactly
     np.testing.assert_allclose(g.nnc_dist, 0.25, rtol=0, atol=1e-15)
 
 
@@ -55,13 +54,41 @@ def test_overlap_lengths_sum_to_fracture_length():
 
 
 def test_mean_distance_closed_forms():
-    # a line far from the cell: the distance is linear over the cell, so the
-    # midpoint rule is exact and equals the distance to the cell centre
+    # a line clear of the cell: the distance is linear over the cell, so its
+    # mean is the distance to the cell centre
     d = geometry.mean_distance(0, 10.0, 20, 10.0, 3, 2, 1.0, 1.0)
-    assert abs(d - (10.0 - 2.5)) < 1e-13
-    # the diagonal through a unit cell: exact mean |x - y| / sqrt(2) = 1/(3 sqrt 2)
+    assert abs(d - (10.0 - 2.5)) < 1e-14
+    d = geometry.mean_distance(0, -4.0, 20, -4.0, 3, 2, 1.0, 1.0)
+    assert abs(d - (2.5 + 4.0)) < 1e-14
+    # the diagonal through a unit cell: mean |x - y| / sqrt(2) = 1 / (3 sqrt 2)
     d = geometry.mean_distance(0, 0, 8, 8, 3, 3, 1.0, 1.0)
-    assert abs(d - 1.0 / (3 * math.sqrt(2))) < 1e-4
+    assert abs(d - 1.0 / (3 * math.sqrt(2))) < 1e-15
+    # an axis-parallel line through the centre of a dx x dy cell: dx / 4
+    d = geometry.mean_distance(3.5 * 2.0, -5.0, 3.5 * 2.0, 30.0, 3, 1, 2.0, 0.5)
+    assert abs(d - 0.5) < 1e-15
+    # a line at distance a < dx/2 from the centre, parallel to y:
+    # mean |x - c| over [0, dx] = ((dx/2 + a)^2 + (dx/2 - a)^2) / (2 dx)
+    a, w = 0.3, 2.0
+    d = geometry.mean_distance(3 * w + w / 2 + a, 0.0, 3 * w + w / 2 + a, 9.0, 3, 1, w, 1.0)
+    assert abs(d - ((w / 2 + a) ** 2 + (w / 2 - a) ** 2) / (2 * w)) < 1e-15
+
+
+def test_mean_distance_against_brute_force_sampling():
+    """A fine midpoint rule (1024^2 points) on random lines and cells: the
+    exact mean differs from it by the rule's O(h^2) error only."""
+    rng = np.random.default_rng(4)
+    m = 1024
+    u = (np.arange(m) + 0.5) / m
+    for _ in range(20):
+        ax, ay, bx, by = rng.uniform(0, 8, 4)
+        ix, iy = rng.integers(0, 8, 2)
+        dx, dy = rng.uniform(0.5, 2.0, 2)
+        X, Y = np.meshgrid(ix * dx + u * dx, iy * dy + u * dy, indexing="ij")
+        ex, ey = bx - ax, by - ay
+        L = math.hypot(ex, ey)
+        ref = np.abs((ex * (Y - ay) - ey * (X - ax)) / L).mean()
+        d = geometry.mean_distance(ax, ay, bx, by, ix, iy, dx, dy)
+        assert abs(d - ref) < 1e-6 * max(dx, dy)
 
 
 def test_segment_intersection():
