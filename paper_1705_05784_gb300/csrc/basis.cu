@@ -100,25 +100,53 @@ __global__ void k_stage_mark(const Inst* inst, int B, const int* off_row, long l
   label[r] = in ? (int)r : -1;
 }
 
-__global__ void k_stage_relax(const Inst* inst, int B, const int* off_row, long long nrow,
+// Dual blocks of a stage = connected components of its kept links, by
+// union-find on `label` used as the parent array (label[r] = r or -1 from
+// k_stage_mark).  A union links the larger root under the smaller, so every
+// parent is <= its child and each component ends with its smallest row as
+// root: the same labels as propagating minima, in two launches.
+__device__ inline int uf_find(volatile int* parent, int x) {
+  int cur = parent[x];
+  if (cur == x) return x;
+  int prev = x, next;
+  while (cur > (next = parent[cur])) {   // path halving on the way up
+    parent[prev] = next;
+    prev = cur;
+    cur = next;
+  }
+  return cur;
+}
+
+__global__ void k_stage_union(const Inst* inst, int B, const int* off_row, long long nrow,
                               const int* rank, const int* rowptr, const int* col,
-                              const int* instage, int* label, int* changed) {
+                              const int* instage, int* label) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow || !instage[r]) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
   int mr = medium_of(I, (int)r), rr = rank[r];
-  int m = label[r];
+  volatile int* parent = label;
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
     int c = col[p];
-    if (c == r || !instage[c]) continue;
+    if (c <= r || !instage[c]) continue;
     if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c])) continue;
-    m = min(m, label[c]);
+    int a = uf_find(parent, (int)r), b = uf_find(parent, c);
+    while (a != b) {
+      if (a < b) { int t = a; a = b; b = t; }   // link the larger root a under b
+      int old = atomicCAS(&label[a], a, b);
+      if (old == a) break;
+      a = uf_find(parent, old);                 // a was no longer a root
+      b = uf_find(parent, b);
+    }
   }
-  m = min(m, label[m]);
-  if (m < label[r]) {
-    atomicMin(&label[r], m);
-    *changed = 1;
-  }
+}
+
+__global__ void k_stage_flatten(long long nrow, const int* instage, int* label) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow || !instage[r]) return;
+  volatile int* parent = label;
+  int x = (int)r;
+  while (parent[x] != x) x = parent[x];
+  label[r] = x;
 }
 
 __global__ void k_root_flag(long long nrow, const int* label, int* flag) {
@@ -467,13 +495,12 @@ int phase_basis(Batch& b) {
   if (nct > 0)
     fams::note_launch(), k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
                                                   vval, pstage, poff, plen);
-  int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr, *changed = nullptr;
+  int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr;
   int *comp_of = nullptr, *pos = nullptr;
   FAMS_TRY(b.scratch((void**)&label, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&instage, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&flag, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&rscan, sizeof(int) * (nrow + 1)));
-  FAMS_TRY(b.scratch((void**)&changed, sizeof(int)));
   FAMS_TRY(b.scratch((void**)&comp_of, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&pos, sizeof(int) * (nrow + 1)));
   int max_smem = 0;
@@ -487,15 +514,9 @@ int phase_basis(Batch& b) {
   for (int s = 0; s < NSTAGE; ++s) {
     fams::note_launch(), k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
                                                   instage);
-    for (int it = 0; it < 1000000; ++it) {
-      int h = 0;
-      FAMS_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
-      fams::note_launch(), k_stage_relax<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank,
-                                                     b.rowptr, b.col, instage, label, changed);
-      FAMS_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
-      FAMS_CUDA(cudaStreamSynchronize(st));
-      if (!h) break;
-    }
+    fams::note_launch(), k_stage_union<<<grid_for(nrow, T), T, 0, st>>>(
+        b.d_inst, b.B, b.off_row, nrow, b.rank, b.rowptr, b.col, instage, label);
+    fams::note_launch(), k_stage_flatten<<<grid_for(nrow, T), T, 0, st>>>(nrow, instage, label);
     fams::note_launch(), k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
     long long ncomp = 0;
     FAMS_TRY(exclusive_scan(b, flag, rscan, nrow, &ncomp));

@@ -115,22 +115,51 @@ __global__ void k_strike_inter_fill(const Inst* inst, int B, const int* off_pair
   adj[ptr[v] + atomicAdd(&cursor[v], 1)] = u;
 }
 
-// connected components by min-label propagation with pointer jumping
+// connected components by union-find on lab (the parent array): a union
+// links the larger root under the smaller, so each component ends with its
+// smallest index as label
 __global__ void k_label_init(long long n, int* lab) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) lab[i] = (int)i;
 }
 
-__global__ void k_label_relax(long long n, const int* ptr, const int* adj, int* lab, int* changed) {
+__device__ inline int lab_find(volatile int* parent, int x) {
+  int cur = parent[x];
+  if (cur == x) return x;
+  int prev = x, next;
+  while (cur > (next = parent[cur])) {   // path halving on the way up
+    parent[prev] = next;
+    prev = cur;
+    cur = next;
+  }
+  return cur;
+}
+
+__global__ void k_label_union(long long n, const int* ptr, const int* adj, int* lab) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int m = lab[i];
-  for (int p = ptr[i]; p < ptr[i + 1]; ++p) m = min(m, lab[adj[p]]);
-  m = min(m, lab[m]);
-  if (m < lab[i]) {
-    atomicMin(&lab[i], m);
-    *changed = 1;
+  volatile int* parent = lab;
+  for (int p = ptr[i]; p < ptr[i + 1]; ++p) {
+    int c = adj[p];
+    if (c <= i) continue;
+    int a = lab_find(parent, (int)i), b = lab_find(parent, c);
+    while (a != b) {
+      if (a < b) { int t = a; a = b; b = t; }
+      int old = atomicCAS(&lab[a], a, b);
+      if (old == a) break;
+      a = lab_find(parent, old);
+      b = lab_find(parent, b);
+    }
   }
+}
+
+__global__ void k_label_flatten(long long n, int* lab) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  volatile int* parent = lab;
+  int x = (int)i;
+  while (parent[x] != x) x = parent[x];
+  lab[i] = x;
 }
 
 __global__ void k_is_root(long long n, const int* lab, int* flag) {
@@ -333,22 +362,15 @@ int phase_coarse(Batch& b) {
                                                        cursor, adj);
   FAMS_TRY(sort_segments(b, sptr, (int)ns, adj, nullptr, true));
   // networks
-  int *lab = nullptr, *flag = nullptr, *rscan = nullptr, *changed = nullptr;
+  int *lab = nullptr, *flag = nullptr, *rscan = nullptr;
   FAMS_TRY(b.scratch((void**)&lab, sizeof(int) * (ns + 1)));
   FAMS_TRY(b.scratch((void**)&flag, sizeof(int) * (ns + 1)));
   FAMS_TRY(b.scratch((void**)&rscan, sizeof(int) * (ns + 1)));
-  FAMS_TRY(b.scratch((void**)&changed, sizeof(int)));
   long long nnet = 0;
   if (ns > 0) {
     fams::note_launch(), k_label_init<<<grid_for(ns, T), T, 0, st>>>(ns, lab);
-    for (int it = 0; it < 100000; ++it) {
-      int h = 0;
-      FAMS_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), st));
-      fams::note_launch(), k_label_relax<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, adj, lab, changed);
-      FAMS_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
-      FAMS_CUDA(cudaStreamSynchronize(st));
-      if (!h) break;
-    }
+    fams::note_launch(), k_label_union<<<grid_for(ns, T), T, 0, st>>>(ns, sptr, adj, lab);
+    fams::note_launch(), k_label_flatten<<<grid_for(ns, T), T, 0, st>>>(ns, lab);
     fams::note_launch(), k_is_root<<<grid_for(ns, T), T, 0, st>>>(ns, lab, flag);
     FAMS_TRY(exclusive_scan(b, flag, rscan, ns, &nnet));
   }

@@ -29,7 +29,6 @@ constexpr int STAT_W = 12;
 constexpr int STAT_BAD = 10;
 constexpr int PK = 4;  // factor entries per row kept inline in the level-ordered layout
 constexpr int MAX_OVERLAP = 8;        // matrix columns one fracture cell may cross
-constexpr int MIDPOINT_N = 64;        // points per axis of the <d> midpoint rule
 constexpr double ZERO_PIECE = 1e-12;  // x h_f
 constexpr double DIST_FLOOR = 1e-3;   // x h_f
 

@@ -12,7 +12,7 @@
 //  * every fracture cell is split at the grid lines it crosses; each piece
 //    lies in the matrix column of its midpoint; pieces in one column are
 //    summed; the connection's area is length x depth and its <d> the mean
-//    distance from the matrix cell to the fracture line (64 x 64 midpoints);
+//    distance from the matrix cell to the fracture line (exact, by clipping);
 //  * two crossing fractures get one connection per shared layer between the
 //    cells that hold the crossing, T_ab = T_a T_b / (T_a + T_b) with
 //    T_a = k_f a_f depth / d_a (the intersection pressure eliminated exactly).
@@ -179,7 +179,42 @@ __global__ void k_strike_overlap(const Inst* inst, int B, const int* off_fr, con
   }
 }
 
-// <d>: mean distance from the matrix cell to the fracture line (Eq. 7)
+// <d>: mean distance from the matrix cell to the fracture line (Eq. 7).  The
+// signed distance f = n . (x - A) is linear: over a triangle its integral is
+// the area times the mean of f at the corners.  With P+ the part of the cell
+// where f >= 0 (the rectangle clipped by that half-plane),
+// int |f| = 2 int_{P+} f - area f(centre).  Coordinates relative to the
+// cell's lower-left corner; one thread per (strike piece, matrix cell).
+__device__ inline double mean_dist_cell(double nx, double ny, double ox, double oy, double dx,
+                                        double dy) {
+  const double rx[4] = {0.0, dx, dx, 0.0}, ry[4] = {0.0, 0.0, dy, dy};
+  double px[5], py[5];
+  int m = 0;
+  for (int k = 0; k < 4; ++k) {
+    int k1 = (k + 1) & 3;
+    double fp = nx * (rx[k] - ox) + ny * (ry[k] - oy);
+    double fq = nx * (rx[k1] - ox) + ny * (ry[k1] - oy);
+    if (fp >= 0.0) { px[m] = rx[k]; py[m] = ry[k]; ++m; }
+    if ((fp >= 0.0) != (fq >= 0.0)) {
+      double t = fp / (fp - fq);
+      px[m] = rx[k] + t * (rx[k1] - rx[k]);
+      py[m] = ry[k] + t * (ry[k1] - ry[k]);
+      ++m;
+    }
+  }
+  double pos = 0.0;
+  for (int k = 1; k + 1 < m; ++k) {
+    double area = 0.5 * ((px[k] - px[0]) * (py[k + 1] - py[0]) - (px[k + 1] - px[0]) * (py[k] - py[0]));
+    double f1 = nx * (px[0] - ox) + ny * (py[0] - oy);
+    double f2 = nx * (px[k] - ox) + ny * (py[k] - oy);
+    double f3 = nx * (px[k + 1] - ox) + ny * (py[k + 1] - oy);
+    pos += area * (f1 + f2 + f3) / 3.0;
+  }
+  double A = dx * dy;
+  double fc = nx * (0.5 * dx - ox) + ny * (0.5 * dy - oy);
+  return (2.0 * pos - A * fc) / A;
+}
+
 __global__ void k_mean_dist(const Inst* inst, int B, const int* off_fr, const int* f_sfirst,
                             long long nfr, long long ns_tot, const double* seg,
                             const int* ovcnt, const int* ovcol, double* ovdist) {
@@ -192,22 +227,11 @@ __global__ void k_mean_dist(const Inst* inst, int B, const int* off_fr, const in
   double ax = seg[4 * gf], ay = seg[4 * gf + 1], bx = seg[4 * gf + 2], by = seg[4 * gf + 3];
   double ex = bx - ax, ey = by - ay;
   double L = sqrt(ex * ex + ey * ey);
-  double tx = ex / L, ty = ey / L;
+  double nx = -ey / L, ny = ex / L;
   int key = ovcol[gs * MAX_OVERLAP + q];
   int ix = key % I.nx, iy = key / I.nx;
-  double sum = 0.0;
-  for (int a = 0; a < MIDPOINT_N; ++a) {
-    double u = ((double)a + 0.5) / MIDPOINT_N;
-    double X = (double)ix * I.dx + u * I.dx;
-    double rowsum = 0.0;
-    for (int c = 0; c < MIDPOINT_N; ++c) {
-      double w = ((double)c + 0.5) / MIDPOINT_N;
-      double Y = (double)iy * I.dy + w * I.dy;
-      rowsum += fabs(tx * (Y - ay) - ty * (X - ax));
-    }
-    sum += rowsum;
-  }
-  ovdist[gs * MAX_OVERLAP + q] = sum / (double)(MIDPOINT_N * MIDPOINT_N);
+  double x0 = (double)ix * I.dx, y0 = (double)iy * I.dy;
+  ovdist[gs * MAX_OVERLAP + q] = mean_dist_cell(nx, ny, ax - x0, ay - y0, I.dx, I.dy);
 }
 
 // per fracture cell: number of matrix-fracture connections
