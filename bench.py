@@ -29,9 +29,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s to rel. residual 1e-8 (served vs plain F-AMS, one GB300); p50/p99 ms"
-# DRAM bytes / algorithmic bytes of k_solve from the ncu capture in
-# profiles/k_solve_2d256_batch8_10sweeps.md (None once the kernel changes)
-TRAFFIC_RATIO = 2230.4 / 2262.2
+# DRAM bytes / algorithmic bytes of the solve kernel from its ncu capture
+# under profiles/ (None until the current kernel has been captured)
+TRAFFIC_RATIO = None
 WORKLOAD = ("2D 256x256: log10 k std 2 corr 16, 30 fractures L~U[20,120], coarsening 8x8, "
             "d_min 8, 4 coupling strategies x T_ratio {1e2,1e4,1e6,1e8}, R^FE, alpha 1e-2, "
             "ILU(0), GMRES(30) with the two-stage preconditioner, tol 1e-8, + flux reconstruction")
@@ -39,7 +39,7 @@ TOL = 1e-8
 TRATIOS = (1e2, 1e4, 1e6, 1e8)
 
 
-def problems(batch, seed0, max_iter=400, krylov=1, restart=30):
+def problems(batch, seed0, max_iter=400, krylov=1, restart=30, precision=1):
     """The bench workload: instance i has coupling strategy i % 4 and
     T_ratio 1e2..1e8 by (i // 4) % 4, seeds seed0 + i."""
     from paper_1705_05784_gb300 import inputs
@@ -48,7 +48,7 @@ def problems(batch, seed0, max_iter=400, krylov=1, restart=30):
         p = inputs.config_2d_256(seed=seed0 + i, tratio=TRATIOS[(i // 4) % len(TRATIOS)],
                                  basis=i % 4, restriction=1, alpha=1e-2)
         p.max_iter = max_iter
-        p.krylov, p.restart = krylov, restart
+        p.krylov, p.restart, p.precision = krylov, restart, precision
         out.append(p)
     return out
 
@@ -107,19 +107,41 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def solve_bytes(s):
-    """Algorithmic HBM bytes of one Table 1 sweep of one instance in the
-    persistent solve kernel (FP64 values 8 B, int32 indices 4 B): two passes
-    over A (residual, r - A dp1), the lower and upper ILU(0) factors, P and P^T,
-    the band factors, and the vector streams."""
+def _passes(s):
     n, nnz, nnzp, nc, ldab = s["n"], s["nnz"], s["nnzp"], s["nc"], s["ldab"]
-    a_pass = 12 * nnz + 4 * (n + 1)
-    ilu = 8 * nnz + 4 * (nnz - n) // 2 + 8 * n       # L and U values, U indices, level lists
-    p_pass = 12 * nnzp + 4 * (n + 1)
-    pt_pass = 12 * nnzp + 4 * (nc + 1)
-    band = 8 * ldab * nc
-    vectors = 8 * n * 14                             # q, x (r/w x2), r (w, r x2), dp (w, r x2), y (w, r, w)
-    return 2 * a_pass + ilu + p_pass + pt_pass + band + vectors
+    a_pass = 12 * nnz + 4 * (n + 1)                     # values, columns, row pointers
+    ilu = 8 * nnz + 4 * (nnz - n) // 2 + 8 * n          # L and U values, U indices, level lists
+    two_stage = (a_pass + ilu + (12 * nnzp + 4 * (n + 1)) + (12 * nnzp + 4 * (nc + 1))
+                 + 8 * ldab * nc + 8 * n * 10)          # P, P^T, band factors, vector streams
+    return a_pass, two_stage, 8 * n
+
+
+def solve_bytes(s):
+    """Algorithmic HBM bytes of one Table 1 sweep of one instance (FP64 values
+    8 B, int32 indices 4 B): the residual's pass over A, then the two-stage
+    step (restriction by P^T, band factors, prolongation by P, r - A dp1, the
+    lower and upper ILU(0) factors, vector streams)."""
+    a_pass, two_stage, vec = _passes(s)
+    return a_pass + 2 * vec + two_stage
+
+
+def gmres_bytes(s, iters, restart):
+    """Algorithmic HBM bytes of `iters` GMRES(restart) iterations of one
+    instance: per Arnoldi step k (0-based in its cycle) the two-stage step,
+    w = A z, classical Gram-Schmidt twice (each a dot pass over V_0..V_k and
+    w, and an update pass over V_0..V_k reading and writing w) and the
+    scaling of w; per cycle of K steps V_0 = r / beta, u = V y, the final
+    two-stage step and the true residual."""
+    a_pass, two_stage, vec = _passes(s)
+    total, left = 0, iters
+    while left > 0:
+        K = min(restart, left)
+        for k in range(K):
+            total += (two_stage + a_pass + 2 * vec + 2 * ((k + 2) * vec) + 2 * ((k + 3) * vec)
+                      + 2 * vec)
+        total += 2 * vec + (K + 1) * vec + two_stage + a_pass + 2 * vec
+        left -= K
+    return total
 
 
 def sizes_of(ctx, i):
@@ -197,7 +219,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-iter", type=int, default=400,
-                    help="cap on Table 1 sweeps (lower it only for profiler captures)")
+                    help="cap on iterations (lower it only for profiler captures)")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="mixed: FP32 inner stages with FP64 residuals and refinement")
+    ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,7 +242,9 @@ def main():
     if rank == 0 and not args.no_cpu and args.cpu_sample > 0:
         cpu = cpu_baseline(args.cpu_sample)
     from paper_1705_05784_gb300 import fams
-    probs = problems(args.batch, 1000 * (rank + 1), args.max_iter)
+    probs = problems(args.batch, 1000 * (rank + 1), args.max_iter,
+                     krylov=1 if args.krylov == "gmres" else 0,
+                     precision=1 if args.precision == "mixed" else 0)
     dev = torch.device("cuda", local)
     perm_d = [torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev) for p in probs]
     # sizes from one setup (deterministic), device buffers for x and the fluxes
@@ -305,9 +332,10 @@ def main():
     e2e_ms = h0.elapsed_time(h1)
     h2d = sum(8 * (len(p.perm) + s["n"] + 4 * len(p.fracs) + len(p.fracs)) for p, s in zip(probs, S))
     d2h = sum(8 * (s["n"] + s["faces"] + s["nnc"]) for s in S)
-    # roofline of the dominant kernel: the persistent Table 1 solve kernel
+    # roofline of the dominant kernel: the persistent solve kernel
     iters = [s["iterations"] for s in stats]
-    byts = sum(solve_bytes(S[i]) * iters[i] for i in range(len(S)))
+    byts = sum(gmres_bytes(S[i], iters[i], probs[i].restart) if probs[i].krylov == 1
+               else solve_bytes(S[i]) * iters[i] for i in range(len(S)))
     k_ms = statistics.median(solve_ms)
     pk = peaks()
     peak = pk.get("hbm_gbs", 6800.0)
@@ -317,9 +345,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": len(probs), "cells_per_instance": S[0]["n"],
+                   "solver": ("GMRES(30)" if args.krylov == "gmres" else "Table 1 loop") + ", " +
+                             ("FP32 inner stages, FP64 residual/coarse solve/refinement"
+                              if args.precision == "mixed" else "FP64"),
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
                    f"({sum(s['nnz'] for s in S) * 12 / 1e9:.1f} GB of A alone per step)"},
         "latency": {"p50_ms": statistics.median(step_ms),
@@ -329,7 +361,8 @@ def main():
                      "flux_singular_fv_coarse": flux_failed[0],
                      "max_rel_residual": max(s["rel_residual"] for s in stats),
                      "iterations_median": statistics.median(iters), "iterations_max": max(iters)},
-        "roofline": {"kernel": "k_solve (persistent Table 1 loop, one CTA per instance)",
+        "roofline": {"kernel": "k_gmres (persistent GMRES(30) with the two-stage step, one CTA "
+                               "per instance)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": None if TRAFFIC_RATIO is None else byts * TRAFFIC_RATIO,

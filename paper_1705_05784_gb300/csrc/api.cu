@@ -82,7 +82,8 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   if (o.restriction != FAMS_R_FV && o.restriction != FAMS_R_FE) return bad("restriction must be FV or FE");
   if (!(o.alpha >= 0.0) || !(o.alpha < 1.0)) return bad("alpha must be in [0, 1)");
   if (o.max_iter < 0) return bad("max_iter must be >= 0");
-  if (o.precision != FAMS_FP64) return bad("only FAMS_FP64 is available in this build");
+  if (o.precision != FAMS_FP64 && o.precision != FAMS_MIXED)
+    return bad("precision must be FAMS_FP64 or FAMS_MIXED");
   if (g.dim == 3 && o.frac_cz < 1) return bad("frac_cz must be >= 1");
   if (o.krylov != FAMS_KRYLOV_NONE && o.krylov != FAMS_KRYLOV_GMRES)
     return bad("krylov must be FAMS_KRYLOV_NONE or FAMS_KRYLOV_GMRES");
@@ -413,8 +414,9 @@ int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, f
     set_error("fams_solve_static needs a single-instance context");
     return FAMS_EINVAL;
   }
-  if (ctx->b.h[0].krylov != FAMS_KRYLOV_NONE) {
-    set_error("fams_solve_static runs the Table 1 loop only (krylov = FAMS_KRYLOV_NONE)");
+  if (ctx->b.h[0].krylov != FAMS_KRYLOV_NONE || ctx->b.h[0].precision != FAMS_FP64) {
+    set_error("fams_solve_static runs the FP64 Table 1 loop only (krylov = FAMS_KRYLOV_NONE, "
+              "precision = FAMS_FP64)");
     return FAMS_EINVAL;
   }
   if (!x) { set_error("x is null"); return FAMS_EINVAL; }

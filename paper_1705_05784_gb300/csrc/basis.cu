@@ -648,6 +648,7 @@ int phase_basis(Batch& b) {
                                              pool, cnt);
   long long pnnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.p_ptr, nrow, &pnnz));
+  b.tot_pnnz = pnnz;
   FAMS_TRY(b.alloc((void**)&b.p_col, sizeof(int) * (pnnz + 1)));
   FAMS_TRY(b.alloc((void**)&b.p_val, sizeof(double) * (pnnz + 1)));
   fams::note_launch(), k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,

@@ -51,7 +51,7 @@ struct Batch {
 
   // totals
   long long tot_m = 0, tot_fr = 0, tot_fc = 0, tot_s = 0, tot_row = 0, tot_pair = 0,
-            tot_nnc = 0, tot_ff = 0, tot_nc = 0, tot_net = 0, tot_nnz = 0;
+            tot_nnc = 0, tot_ff = 0, tot_nc = 0, tot_net = 0, tot_nnz = 0, tot_pnnz = 0;
 
   // ---- inputs ----
   double* perm = nullptr;      // tot_m
@@ -141,6 +141,22 @@ struct Batch {
   double* stat = nullptr;      // per instance: 4 doubles (iters, relres, converged, qnorm)
   double* hist = nullptr;      // per instance: relative residual after each sweep
   double* krylov = nullptr;    // GMRES bases of the instances that use GMRES
+  // mixed precision: FP32 copies of A, P, P^T and the ILU(0) factors (plain
+  // and level-ordered), FP32 work vectors and GMRES bases
+  float* val32 = nullptr;
+  float* p_val32 = nullptr;
+  float* pt_val32 = nullptr;
+  float* ilu32 = nullptr;
+  float* pk_lv32 = nullptr;
+  float* pk_uv32 = nullptr;
+  float* pk_ud32 = nullptr;
+  double* xs = nullptr;
+  float* rf = nullptr;
+  float* zf = nullptr;
+  float* dpf = nullptr;
+  float* yf = nullptr;
+  float* ylevf = nullptr;
+  float* krylov32 = nullptr;
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
   bool fv_ready = false;

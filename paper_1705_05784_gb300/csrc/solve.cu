@@ -47,6 +47,11 @@ __device__ inline double block_sum(double v, double* red) {
   return red[32];
 }
 
+__global__ void k_round(long long n, const double* src, float* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
 __global__ void k_make_q(long long n, const double* rhs, const double* qD, double* q) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) q[i] = (rhs ? rhs[i] : 0.0) + qD[i];
@@ -94,38 +99,82 @@ struct SolveArgs {
   double* ylev;
   long long ntot;  // rows of the batch (stride of the PK arrays)
   double tol;
+  // FP32 copies and work vectors of the mixed-precision inner stages
+  const float* val32;
+  const float* p_val32;
+  const float* pt_val32;
+  const float* F32;
+  const float* pk_lv32;
+  const float* pk_uv32;
+  const float* pk_ud32;
+  double* xs;     // iterate saved before an FP32 cycle
+  float* rf;      // residual rounded to FP32
+  float* zf;      // preconditioned vector
+  float* dpf;
+  float* yf;
+  float* ylevf;
+};
+
+// the arrays of one arithmetic: FP64 throughout, or the FP32 copies
+template <class T> struct Prec;
+template <> struct Prec<double> {
+  static __device__ const double* val(const SolveArgs& a) { return a.val; }
+  static __device__ const double* pv(const SolveArgs& a) { return a.p_val; }
+  static __device__ const double* ptv(const SolveArgs& a) { return a.pt_val; }
+  static __device__ const double* F(const SolveArgs& a) { return a.F; }
+  static __device__ const double* lv(const SolveArgs& a) { return a.pk_lv; }
+  static __device__ const double* uv(const SolveArgs& a) { return a.pk_uv; }
+  static __device__ const double* ud(const SolveArgs& a) { return a.pk_ud; }
+  static __device__ double* y(const SolveArgs& a) { return a.y; }
+  static __device__ double* ylev(const SolveArgs& a) { return a.ylev; }
+  static __device__ double* dp(const SolveArgs& a) { return a.dp; }
+  static __device__ double* z(const SolveArgs& a) { return a.r; }
+};
+template <> struct Prec<float> {
+  static __device__ const float* val(const SolveArgs& a) { return a.val32; }
+  static __device__ const float* pv(const SolveArgs& a) { return a.p_val32; }
+  static __device__ const float* ptv(const SolveArgs& a) { return a.pt_val32; }
+  static __device__ const float* F(const SolveArgs& a) { return a.F32; }
+  static __device__ const float* lv(const SolveArgs& a) { return a.pk_lv32; }
+  static __device__ const float* uv(const SolveArgs& a) { return a.pk_uv32; }
+  static __device__ const float* ud(const SolveArgs& a) { return a.pk_ud32; }
+  static __device__ float* y(const SolveArgs& a) { return a.yf; }
+  static __device__ float* ylev(const SolveArgs& a) { return a.ylevf; }
+  static __device__ float* dp(const SolveArgs& a) { return a.dpf; }
+  static __device__ float* z(const SolveArgs& a) { return a.zf; }
 };
 
 // y[i] = b[i] - sum_p val[p] v[col[p]] for the instance's rows, four rows per
 // thread in flight; returns this thread's sum of y^2 when `norm`
-__device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const double* b,
-                                       const double* v, double* y, bool norm,
-                                       double* ylev = nullptr) {
-  double acc = 0.0;
-  const int T = blockDim.x;
-  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+template <class T>
+__device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const T* b, const T* v,
+                                       T* y, bool norm, T* ylev = nullptr) {
+  const T* val = Prec<T>::val(a);
+  T acc = 0;
+  const int NT = blockDim.x;
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
     int rs[ROWS_ILP], re[ROWS_ILP];
-    double s[ROWS_ILP];
+    T s[ROWS_ILP];
     int m = 0;
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * T;
+      int i = i0 + k * NT;
       bool ok = i < ro + n;
       rs[k] = ok ? a.rowptr[i] : 0;
       re[k] = ok ? a.rowptr[i + 1] : 0;
-      s[k] = ok ? b[i] : 0.0;
+      s[k] = ok ? b[i] : T(0);
       m = max(m, re[k] - rs[k]);
     }
     for (int e = 0; e < m; ++e) {
 #pragma unroll
       for (int k = 0; k < ROWS_ILP; ++k) {
         int p = rs[k] + e;
-        if (p < re[k]) s[k] -= a.val[p] * v[a.col[p]];
+        if (p < re[k]) s[k] -= val[p] * v[a.col[p]];
       }
     }
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * T;
+      int i = i0 + k * NT;
       if (i < ro + n) {
         y[i] = s[k];
         if (ylev) ylev[a.pk_pos[i]] = s[k];
@@ -133,7 +182,7 @@ __device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const 
       }
     }
   }
-  return acc;
+  return (double)acc;
 }
 
 // coarse band solve: warp 0 runs the recurrences on columns staged in shared
@@ -215,32 +264,34 @@ __device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, i
 // one row of a triangular sweep, loaded from the level-ordered layout: every
 // address depends only on the position t, so the loads of a whole level are
 // coalesced and independent of the sweep's results
+template <class T>
 struct SweepRow {
   int t, i, cnt, p;
-  double base, diag;
+  T base, diag;
   int c[PK];
-  double f[PK];
+  T f[PK];
 };
 
+template <class T>
 __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int nlev, bool lower,
-                                  SweepRow& s) {
+                                  SweepRow<T>& s) {
   s.t = -1;
   if (l < 0 || l >= nlev) return;
   int t = lp[l] + threadIdx.x;
   if (t >= lp[l + 1]) return;
   s.t = t;
   s.i = a.lev_rows[t];
-  s.base = a.ylev[t];
+  s.base = Prec<T>::ylev(a)[t];
   if (lower) {
     s.cnt = a.pk_nl[t];
     s.p = a.pk_lp[t];
-    s.diag = 1.0;
+    s.diag = T(1);
   } else {
     s.cnt = a.pk_nu[t];
-    s.diag = a.pk_ud[t];
+    s.diag = Prec<T>::ud(a)[t];
   }
   const int* pc = lower ? a.pk_lc : a.pk_uc;
-  const double* pv = lower ? a.pk_lv : a.pk_uv;
+  const T* pv = lower ? Prec<T>::lv(a) : Prec<T>::uv(a);
 #pragma unroll
   for (int k = 0; k < PK; ++k) {
     s.c[k] = pc[(long long)k * a.ntot + t];
@@ -258,13 +309,16 @@ struct SolveSmem {
   int* pbuf;
 };
 
-// Steps 5-7 of Table 1 on a residual r (SM cycles of the phases added to cyc
-// by thread 0):
+// Steps 5-7 of Table 1 on a residual r, in the arithmetic T of the vectors
+// (the coarse solve is FP64 in both; SM cycles of the phases are added to
+// cyc by thread 0):
 //   dp = P A_c^-1 R r;  y = r - A dp (also in level order);
 //   out = (base + dp) + (LU)^-1 y   (base null: out = dp + (LU)^-1 y)
 // out may alias base; r, dp and out must not alias y or ylev.
-__device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const double* r, double* dp,
-                          double* out, const double* base, const SolveSmem& S, long long* cyc) {
+template <class T>
+__device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const T* r,
+                                          T* dp, T* out, const T* base, const SolveSmem& S,
+                                          long long* cyc) {
   const int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
   const double* AB = a.cs.band + a.cs.band_off[ii];
   const int* ipiv = a.cs.ipiv + co;
@@ -272,19 +326,24 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   const int kl = a.cs.kl[ii], ku = a.cs.ku[ii];
   const int* lp = a.lev_ptr + a.lev_off[ii];
   const int nlev = I.nlev;
-  const int T = blockDim.x;
+  const int NT = blockDim.x;
+  const T* ptv = Prec<T>::ptv(a);
+  const T* pv = Prec<T>::pv(a);
+  const T* F = Prec<T>::F(a);
+  T* y = Prec<T>::y(a);
+  T* ylev = Prec<T>::ylev(a);
   long long t1 = clock64();
   // step 5: coarse right-hand side R r, in band order
-  for (int k = threadIdx.x; k < nc; k += T) {
+  for (int k = threadIdx.x; k < nc; k += NT) {
     int c = co + perm[k];
-    double s0 = 0.0, s1 = 0.0;
+    T s0 = 0, s1 = 0;
     if (I.restriction == FAMS_R_FE) {
       int p = a.pt_ptr[c], e = a.pt_ptr[c + 1];
       for (; p + 1 < e; p += 2) {
-        s0 += a.pt_val[p] * r[a.pt_col[p]];
-        s1 += a.pt_val[p + 1] * r[a.pt_col[p + 1]];
+        s0 += ptv[p] * r[a.pt_col[p]];
+        s1 += ptv[p + 1] * r[a.pt_col[p + 1]];
       }
-      if (p < e) s0 += a.pt_val[p] * r[a.pt_col[p]];
+      if (p < e) s0 += ptv[p] * r[a.pt_col[p]];
     } else {
       int p = a.blk_ptr[c], e = a.blk_ptr[c + 1];
       for (; p + 1 < e; p += 2) {
@@ -293,86 +352,86 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       }
       if (p < e) s0 += r[a.blk_cell[p]];
     }
-    S.yb[k] = s0 + s1;
-    a.crhs[co + perm[k]] = s0 + s1;
+    S.yb[k] = (double)(s0 + s1);
+    a.crhs[co + perm[k]] = (double)(s0 + s1);
   }
   __syncthreads();
   long long t1b = clock64();
   coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf);
-  for (int k = threadIdx.x; k < nc; k += T) {
+  for (int k = threadIdx.x; k < nc; k += NT) {
     S.ecs[perm[k]] = S.yb[k];
     a.csol[co + perm[k]] = S.yb[k];
   }
   __syncthreads();
   long long t2 = clock64();
   // dp1 = P e_c
-  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * T;
+      int i = i0 + k * NT;
       if (i < ro + n) {
-        double s = 0.0;
-        for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += a.p_val[p] * S.ecs[a.p_col[p]];
+        T s = 0;
+        for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += pv[p] * (T)S.ecs[a.p_col[p]];
         dp[i] = s;
       }
     }
   }
   __syncthreads();
   // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
-  rows_residual(a, ro, n, r, dp, a.y, false, a.ylev);
+  rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
   __syncthreads();
   long long t3 = clock64();
   // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
-  SweepRow cur, nxt;
-  sweep_load(a, lp, 0, nlev, true, cur);
+  SweepRow<T> cur, nxt;
+  sweep_load<T>(a, lp, 0, nlev, true, cur);
   for (int l = 0; l < nlev; ++l) {
-    sweep_load(a, lp, l + 1, nlev, true, nxt);
+    sweep_load<T>(a, lp, l + 1, nlev, true, nxt);
     if (cur.t >= 0) {
-      double s = cur.base;
+      T s = cur.base;
 #pragma unroll
       for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
-      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
-      a.y[cur.i] = s;
-      a.ylev[cur.t] = s;
+        if (k < cur.cnt) s -= cur.f[k] * y[cur.c[k]];
+      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= F[p] * y[a.col[p]];
+      y[cur.i] = s;
+      ylev[cur.t] = s;
     }
-    for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
+    for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
       int i = a.lev_rows[t];
-      double s = a.ylev[t];
-      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= a.F[p] * a.y[a.col[p]];
-      a.y[i] = s;
-      a.ylev[t] = s;
+      T s = ylev[t];
+      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= F[p] * y[a.col[p]];
+      y[i] = s;
+      ylev[t] = s;
     }
     __syncthreads();
     cur = nxt;
   }
   long long t4 = clock64();
   // U sweep and step 8: out = (base + dp1) + dp2
-  sweep_load(a, lp, nlev - 1, nlev, false, cur);
+  sweep_load<T>(a, lp, nlev - 1, nlev, false, cur);
   for (int l = nlev - 1; l >= 0; --l) {
-    sweep_load(a, lp, l - 1, nlev, false, nxt);
+    sweep_load<T>(a, lp, l - 1, nlev, false, nxt);
     if (cur.t >= 0) {
-      double s = cur.base;
-      double xo = base ? base[cur.i] : 0.0, dpo = dp[cur.i];
+      T s = cur.base;
+      T xo = base ? base[cur.i] : T(0), dpo = dp[cur.i];
 #pragma unroll
       for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * a.y[cur.c[k]];
+        if (k < cur.cnt) s -= cur.f[k] * y[cur.c[k]];
       if (cur.cnt > PK) {
         int d = a.diag[cur.i];
-        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= a.F[p] * a.y[a.col[p]];
+        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= F[p] * y[a.col[p]];
       }
-      double xi = s / cur.diag;
-      a.y[cur.i] = xi;
+      T xi = s / cur.diag;
+      y[cur.i] = xi;
       out[cur.i] = (xo + dpo) + xi;
     }
-    for (int t = lp[l] + threadIdx.x + T; t < lp[l + 1]; t += T) {
+    for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
       int i = a.lev_rows[t];
       int d = a.diag[i];
-      double s = a.ylev[t];
-      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= a.F[p] * a.y[a.col[p]];
-      double xi = s / a.F[d];
-      a.y[i] = xi;
-      out[i] = ((base ? base[i] : 0.0) + dp[i]) + xi;
+      T s = ylev[t];
+      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= F[p] * y[a.col[p]];
+      T xi = s / F[d];
+      y[i] = xi;
+      out[i] = ((base ? base[i] : T(0)) + dp[i]) + xi;
     }
     __syncthreads();
     cur = nxt;
@@ -403,6 +462,13 @@ __device__ inline void write_stats(const SolveArgs& a, int ii, int it, double re
   }
 }
 
+// The Table 1 loop.  FP64: every step in FP64.  Mixed precision: the
+// residual and the iterate stay FP64, the two-stage step runs on the residual
+// rounded to FP32 with the FP32 copies of P, A and the ILU(0) factors (the
+// coarse solve stays FP64), and its correction is added to the FP64 iterate
+// -- iterative refinement with the two-stage step as the inner solver.  A
+// sweep that does not reduce the FP64 residual switches the instance to FP64
+// sweeps for the rest of the solve.
 __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   extern __shared__ double sm[];
   __shared__ double red[40];
@@ -413,22 +479,25 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   if (I.krylov != FAMS_KRYLOV_NONE) return;
   const int n = I.n, ro = I.row_off;
   const SolveSmem S = solve_smem(sm, I.nc, pbuf);
-  const int T = blockDim.x;
+  const int NT = blockDim.x;
+  bool use32 = I.precision == FAMS_MIXED;
   // ||q||
   double acc = 0.0;
-  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
+  for (int i = ro + threadIdx.x; i < ro + n; i += NT) acc += a.q[i] * a.q[i];
   double qn = sqrt(block_sum(acc, red));
   if (!(qn > 0.0)) qn = 1.0;
   int it = 0;
-  double rel = 0.0;
+  double rel = 0.0, prev = INFINITY;
   // SM cycles per phase (thread 0, between barriers): residual, restriction,
   // band solve, prolongation + r1, L sweep, U sweep
   long long cyc[6] = {0, 0, 0, 0, 0, 0};
   for (;;) {
     long long t0 = clock64();
-    // step 3: r = q - A p
-    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
+    // step 3: r = q - A p (FP64)
+    acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
     rel = sqrt(block_sum(acc, red)) / qn;
+    if (use32 && !(rel < prev)) use32 = false;   // FP32 no longer makes progress
+    prev = rel;
     if (threadIdx.x == 0) {
       a.hist[(long long)ii * a.hist_len + it] = rel;
       s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii]);
@@ -437,7 +506,15 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     cyc[0] += clock64() - t0;
     if (s_done) break;
     // steps 5-8: p = p + dp1 + dp2
-    two_stage(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
+    if (!use32) {
+      two_stage<double>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
+    } else {
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)a.r[i];
+      __syncthreads();
+      two_stage<float>(a, I, ii, a.rf, a.dpf, a.zf, nullptr, S, cyc);
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.x[i] += (double)a.zf[i];
+      __syncthreads();
+    }
     ++it;
   }
   write_stats(a, ii, it, rel, qn, cyc);
@@ -447,16 +524,56 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
 // reduction has a fixed order, so results do not depend on the batch
 
 // y = A v; returns this thread's sum of y^2
-__device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const double* v, double* y) {
+template <class T>
+__device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const T* v, T* y) {
+  const T* val = Prec<T>::val(a);
+  T acc = 0;
+  const int NT = blockDim.x;
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
+    int rs[ROWS_ILP], re[ROWS_ILP];
+    T s[ROWS_ILP];
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * NT;
+      bool ok = i < ro + n;
+      rs[k] = ok ? a.rowptr[i] : 0;
+      re[k] = ok ? a.rowptr[i + 1] : 0;
+      s[k] = 0;
+      m = max(m, re[k] - rs[k]);
+    }
+    for (int e = 0; e < m; ++e) {
+#pragma unroll
+      for (int k = 0; k < ROWS_ILP; ++k) {
+        int p = rs[k] + e;
+        if (p < re[k]) s[k] += val[p] * v[a.col[p]];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ROWS_ILP; ++k) {
+      int i = i0 + k * NT;
+      if (i < ro + n) {
+        y[i] = s[k];
+        acc += s[k] * s[k];
+      }
+    }
+  }
+  return (double)acc;
+}
+
+// y = A z for an FP32 vector z, in FP64 (z is widened exactly); returns this
+// thread's sum of y^2
+__device__ inline double rows_apply_wide(const SolveArgs& a, int ro, int n, const float* z,
+                                         double* y) {
   double acc = 0.0;
-  const int T = blockDim.x;
-  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * T) {
+  const int NT = blockDim.x;
+  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
     int rs[ROWS_ILP], re[ROWS_ILP];
     double s[ROWS_ILP];
     int m = 0;
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * T;
+      int i = i0 + k * NT;
       bool ok = i < ro + n;
       rs[k] = ok ? a.rowptr[i] : 0;
       re[k] = ok ? a.rowptr[i + 1] : 0;
@@ -467,12 +584,12 @@ __device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const dou
 #pragma unroll
       for (int k = 0; k < ROWS_ILP; ++k) {
         int p = rs[k] + e;
-        if (p < re[k]) s[k] += a.val[p] * v[a.col[p]];
+        if (p < re[k]) s[k] += a.val[p] * (double)z[a.col[p]];
       }
     }
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * T;
+      int i = i0 + k * NT;
       if (i < ro + n) {
         y[i] = s[k];
         acc += s[k] * s[k];
@@ -485,25 +602,26 @@ __device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const dou
 constexpr int GS_CHUNK = 8;   // basis vectors per pass of the Gram-Schmidt dot products
 
 // h[0..k] = V[0..k]^T w over rows [ro, ro + n), reduced over the CTA into h
-// (shared memory); V_c at V + c ld
-__device__ void block_dots(const double* V, long long ld, int k1, int ro, int n, const double* w,
-                           double* h, double* red8) {
-  const int T = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+// (shared memory, FP64); V_c at V + c ld
+template <class T>
+__device__ void block_dots(const T* V, long long ld, int k1, int ro, int n, const T* w, double* h,
+                           double* red8) {
+  const int NT = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = NT >> 5;
   for (int c0 = 0; c0 < k1; c0 += GS_CHUNK) {
-    double s[GS_CHUNK];
+    T s[GS_CHUNK];
 #pragma unroll
-    for (int c = 0; c < GS_CHUNK; ++c) s[c] = 0.0;
-    for (int i = ro + threadIdx.x; i < ro + n; i += T) {
-      double wi = w[i];
+    for (int c = 0; c < GS_CHUNK; ++c) s[c] = 0;
+    for (int i = ro + threadIdx.x; i < ro + n; i += NT) {
+      T wi = w[i];
 #pragma unroll
       for (int c = 0; c < GS_CHUNK; ++c)
         if (c0 + c < k1) s[c] += V[(long long)(c0 + c) * ld + i] * wi;
     }
 #pragma unroll
     for (int c = 0; c < GS_CHUNK; ++c) {
-      double v = s[c];
+      T v = s[c];
       for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red8[warp * GS_CHUNK + c] = v;
+      if (lane == 0) red8[warp * GS_CHUNK + c] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < GS_CHUNK && c0 + threadIdx.x < k1) {
@@ -516,16 +634,147 @@ __device__ void block_dots(const double* V, long long ld, int k1, int ro, int n,
 }
 
 // w -= V[0..k] h; returns this thread's sum of w^2
-__device__ inline double block_update(const double* V, long long ld, int k1, int ro, int n, double* w,
+template <class T>
+__device__ inline double block_update(const T* V, long long ld, int k1, int ro, int n, T* w,
                                       const double* h) {
-  double acc = 0.0;
+  T acc = 0;
   for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
-    double wi = w[i];
-    for (int c = 0; c < k1; ++c) wi -= h[c] * V[(long long)c * ld + i];
+    T wi = w[i];
+    for (int c = 0; c < k1; ++c) wi -= (T)h[c] * V[(long long)c * ld + i];
     w[i] = wi;
     acc += wi * wi;
   }
-  return acc;
+  return (double)acc;
+}
+
+constexpr double MIXED_MIN_GAIN = 0.1;   // FP32 cycle: least FP64 residual reduction kept
+
+// shared state of one GMRES CTA
+struct GmresSmem {
+  double* H;     // (m+1) x m Hessenberg matrix, column k at H + k (m+1)
+  double* g;     // m+1 rotated right-hand side
+  double* cs;    // m Givens cosines
+  double* sn;    // m Givens sines
+  double* hv;    // m+1 second Gram-Schmidt pass
+  double* yv;    // m least-squares solution
+  double* red;   // block_sum scratch
+  double* red8;  // block_dots scratch
+  int* done;
+};
+
+// One GMRES(m) cycle from the residual in a.r (norm beta), ending with
+// x += M^-1 V y.  `it` counts preconditioner applications.
+//
+// mixed = true: flexible GMRES with the two-stage step in FP32.  The basis V,
+// w = A z and the Gram-Schmidt passes stay FP64; each V_k is rounded to FP32
+// for the two-stage step and its output z_k is kept (Z, FP32), so that
+// A Z = V H holds in FP64 whatever the FP32 rounding did to the
+// preconditioner, and the cycle ends with x += Z y (no further
+// preconditioner application).  FP32 vectors cannot hold smooth pressure
+// fields to more than a few digits of their cell-to-cell differences, which
+// is why only the preconditioner, whose output the residual never depends on
+// through FP32 arithmetic, runs there.
+template <bool mixed>
+__device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V, float* Z,
+                            double beta, double qn, int& it, const SolveSmem& S,
+                            const GmresSmem& G, long long* cyc) {
+  const int n = I.n, ro = I.row_off, m = I.restart;
+  const long long ld = a.ntot;
+  const int NT = blockDim.x;
+  // V_0 = r / beta, g = beta e_1
+  long long t0 = clock64();
+  for (int i = ro + threadIdx.x; i < ro + n; i += NT) V[i] = a.r[i] / beta;
+  for (int k = threadIdx.x; k <= m; k += NT) G.g[k] = k == 0 ? beta : 0.0;
+  __syncthreads();
+  cyc[0] += clock64() - t0;
+  int k = 0;
+  for (;;) {
+    // z = M^-1 V_k, w = A z (in V_{k+1})
+    double* Vk = V + (long long)k * ld;
+    double* w = V + (long long)(k + 1) * ld;
+    if constexpr (mixed) {
+      float* Zk = Z + (long long)k * ld;
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)Vk[i];
+      __syncthreads();
+      two_stage<float>(a, I, ii, a.rf, a.dpf, Zk, nullptr, S, cyc);
+      t0 = clock64();
+      rows_apply_wide(a, ro, n, Zk, w);
+    } else {
+      two_stage<double>(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
+      t0 = clock64();
+      rows_apply<double>(a, ro, n, a.r, w);
+    }
+    __syncthreads();
+    // classical Gram-Schmidt, twice: H(0..k, k) = V^T w, w -= V H(0..k, k)
+    double* Hk = G.H + (long long)k * (m + 1);
+    block_dots<double>(V, ld, k + 1, ro, n, w, Hk, G.red8);
+    block_update<double>(V, ld, k + 1, ro, n, w, Hk);
+    __syncthreads();
+    block_dots<double>(V, ld, k + 1, ro, n, w, G.hv, G.red8);
+    double acc = block_update<double>(V, ld, k + 1, ro, n, w, G.hv);
+    double hn = sqrt(block_sum(acc, G.red));
+    if (threadIdx.x <= k) Hk[threadIdx.x] += G.hv[threadIdx.x];
+    if (hn > 0.0) {
+      const double inv = 1.0 / hn;
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) w[i] *= inv;
+    }
+    __syncthreads();
+    // Givens rotations on column k and the right-hand side g
+    if (threadIdx.x == 0) {
+      Hk[k + 1] = hn;
+      for (int i = 0; i < k; ++i) {
+        double t = G.cs[i] * Hk[i] + G.sn[i] * Hk[i + 1];
+        Hk[i + 1] = -G.sn[i] * Hk[i] + G.cs[i] * Hk[i + 1];
+        Hk[i] = t;
+      }
+      double d = hypot(Hk[k], Hk[k + 1]);
+      G.cs[k] = Hk[k] / d;
+      G.sn[k] = Hk[k + 1] / d;
+      Hk[k] = d;
+      Hk[k + 1] = 0.0;
+      G.g[k + 1] = -G.sn[k] * G.g[k];
+      G.g[k] = G.cs[k] * G.g[k];
+      double est = fabs(G.g[k + 1]) / qn;
+      a.hist[(long long)ii * a.hist_len + it + 1] = est;
+      *G.done = (est <= a.tol || k + 1 >= m || it + 1 >= I.max_iter || !isfinite(est));
+    }
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+    ++k;
+    ++it;
+    if (*G.done) break;
+  }
+  // y = H^-1 g (upper triangular k x k)
+  t0 = clock64();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double s = G.g[i];
+      for (int j = i + 1; j < k; ++j) s -= G.H[(long long)j * (m + 1) + i] * G.yv[j];
+      G.yv[i] = s / G.H[(long long)i * (m + 1) + i];
+    }
+  }
+  __syncthreads();
+  if constexpr (mixed) {
+    // x += Z y
+    for (int i = ro + threadIdx.x; i < ro + n; i += NT) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += G.yv[j] * (double)Z[(long long)j * ld + i];
+      a.x[i] += s;
+    }
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+  } else {
+    // u = V y (in V_k), x += M^-1 u
+    double* u = V + (long long)k * ld;
+    for (int i = ro + threadIdx.x; i < ro + n; i += NT) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += G.yv[j] * V[(long long)j * ld + i];
+      u[i] = s;
+    }
+    __syncthreads();
+    cyc[0] += clock64() - t0;
+    two_stage<double>(a, I, ii, u, a.dp, a.x, a.x, S, cyc);
+  }
 }
 
 // GMRES(m) with the two-stage step as right preconditioner (Sec. 4.5, 4.6;
@@ -536,7 +785,13 @@ __device__ inline double block_update(const double* V, long long ld, int k1, int
 // precision).  Iterations count preconditioner applications; the history
 // holds the least-squares residual estimate inside a cycle and the true
 // residual at each cycle's end.
-__global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* krylov) {
+//
+// Mixed precision: flexible GMRES with the two-stage step in FP32 (see
+// gmres_cycle).  A cycle that does not cut the FP64 residual by
+// MIXED_MIN_GAIN marks FP32 as too coarse for this instance: the cycle is
+// undone if the residual grew, and the instance continues with the FP64
+// two-stage step.
+__global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64, float* kry32) {
   extern __shared__ double sm[];
   __shared__ double red[40];
   __shared__ double red8[(SOLVE_T / 32) * GS_CHUNK];
@@ -547,25 +802,26 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* krylo
   if (I.krylov != FAMS_KRYLOV_GMRES) return;
   const int n = I.n, ro = I.row_off, m = I.restart;
   const SolveSmem S = solve_smem(sm, I.nc, pbuf);
-  // dense arrays after the coarse buffers: H ((m+1) x m, column k at
-  // H + k (m+1)), g (m+1), cs, sn, hv (m+1 scratch dot products), y (m)
-  double* H = sm + 2 * I.nc + 2 * BAND_BUF;
-  double* g = H + (m + 1) * m;
-  double* cs = g + (m + 1);
-  double* sn = cs + m;
-  double* hv = sn + m;
-  double* yv = hv + (m + 1);
-  double* V = krylov;   // V_k at V + k ntot, rows indexed like every batch vector
-  const long long ld = a.ntot;
-  const int T = blockDim.x;
+  GmresSmem G;
+  G.H = sm + 2 * I.nc + 2 * BAND_BUF;
+  G.g = G.H + (m + 1) * m;
+  G.cs = G.g + (m + 1);
+  G.sn = G.cs + m;
+  G.hv = G.sn + m;
+  G.yv = G.hv + (m + 1);
+  G.red = red;
+  G.red8 = red8;
+  G.done = &s_done;
+  const int NT = blockDim.x;
+  bool use32 = I.precision == FAMS_MIXED;
   double acc = 0.0;
-  for (int i = ro + threadIdx.x; i < ro + n; i += T) acc += a.q[i] * a.q[i];
+  for (int i = ro + threadIdx.x; i < ro + n; i += NT) acc += a.q[i] * a.q[i];
   double qn = sqrt(block_sum(acc, red));
   if (!(qn > 0.0)) qn = 1.0;
   long long cyc[6] = {0, 0, 0, 0, 0, 0};
   long long t0 = clock64();
   int it = 0;
-  acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
+  acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
   double beta = sqrt(block_sum(acc, red));
   double rel = beta / qn;
   if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len] = rel;
@@ -575,80 +831,26 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* krylo
       s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii] || !(beta > 0.0));
     __syncthreads();
     if (s_done) break;
-    // V_0 = r / beta, g = beta e_1
-    t0 = clock64();
-    for (int i = ro + threadIdx.x; i < ro + n; i += T) V[i] = a.r[i] / beta;
-    for (int k = threadIdx.x; k <= m; k += T) g[k] = k == 0 ? beta : 0.0;
-    __syncthreads();
-    cyc[0] += clock64() - t0;
-    int k = 0;
-    for (;;) {
-      // z = M^-1 V_k (in r), w = A z (in V_{k+1})
-      double* Vk = V + (long long)k * ld;
-      double* w = V + (long long)(k + 1) * ld;
-      two_stage(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
-      t0 = clock64();
-      rows_apply(a, ro, n, a.r, w);
+    if (use32) {
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.xs[i] = a.x[i];
       __syncthreads();
-      // classical Gram-Schmidt, twice: H(0..k, k) = V^T w, w -= V H(0..k, k)
-      double* Hk = H + (long long)k * (m + 1);
-      block_dots(V, ld, k + 1, ro, n, w, Hk, red8);
-      block_update(V, ld, k + 1, ro, n, w, Hk);
-      __syncthreads();
-      block_dots(V, ld, k + 1, ro, n, w, hv, red8);
-      acc = block_update(V, ld, k + 1, ro, n, w, hv);
-      double hn = sqrt(block_sum(acc, red));
-      if (threadIdx.x <= k) Hk[threadIdx.x] += hv[threadIdx.x];
-      if (hn > 0.0)
-        for (int i = ro + threadIdx.x; i < ro + n; i += T) w[i] /= hn;
-      __syncthreads();
-      // Givens rotations on column k and the right-hand side g
-      if (threadIdx.x == 0) {
-        Hk[k + 1] = hn;
-        for (int i = 0; i < k; ++i) {
-          double t = cs[i] * Hk[i] + sn[i] * Hk[i + 1];
-          Hk[i + 1] = -sn[i] * Hk[i] + cs[i] * Hk[i + 1];
-          Hk[i] = t;
-        }
-        double d = hypot(Hk[k], Hk[k + 1]);
-        cs[k] = Hk[k] / d;
-        sn[k] = Hk[k + 1] / d;
-        Hk[k] = d;
-        Hk[k + 1] = 0.0;
-        g[k + 1] = -sn[k] * g[k];
-        g[k] = cs[k] * g[k];
-        double est = fabs(g[k + 1]) / qn;
-        a.hist[(long long)ii * a.hist_len + it + 1] = est;
-        s_done = (est <= a.tol || k + 1 >= m || it + 1 >= I.max_iter || !isfinite(est));
-      }
-      __syncthreads();
-      cyc[0] += clock64() - t0;
-      ++k;
-      ++it;
-      if (s_done) break;
+      gmres_cycle<true>(a, I, ii, kry64, kry32, beta, qn, it, S, G, cyc);
+    } else {
+      gmres_cycle<false>(a, I, ii, kry64, nullptr, beta, qn, it, S, G, cyc);
     }
-    // y = H^-1 g (upper triangular k x k), u = V y (in V_k), x += M^-1 u
     t0 = clock64();
-    if (threadIdx.x == 0) {
-      for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int j = i + 1; j < k; ++j) s -= H[(long long)j * (m + 1) + i] * yv[j];
-        yv[i] = s / H[(long long)i * (m + 1) + i];
+    acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
+    double beta1 = sqrt(block_sum(acc, red));
+    if (use32 && !(beta1 <= MIXED_MIN_GAIN * beta)) {
+      use32 = false;
+      if (!(beta1 < beta)) {   // undo the cycle
+        for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.x[i] = a.xs[i];
+        __syncthreads();
+        acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
+        beta1 = sqrt(block_sum(acc, red));
       }
     }
-    __syncthreads();
-    double* u = V + (long long)k * ld;
-    for (int i = ro + threadIdx.x; i < ro + n; i += T) {
-      double s = 0.0;
-      for (int j = 0; j < k; ++j) s += yv[j] * V[(long long)j * ld + i];
-      u[i] = s;
-    }
-    __syncthreads();
-    cyc[0] += clock64() - t0;
-    two_stage(a, I, ii, u, a.dp, a.x, a.x, S, cyc);
-    t0 = clock64();
-    acc = rows_residual(a, ro, n, a.q, a.x, a.r, true);
-    beta = sqrt(block_sum(acc, red));
+    beta = beta1;
     rel = beta / qn;
     if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len + it] = rel;
     cyc[0] += clock64() - t0;
@@ -672,11 +874,45 @@ int phase_alloc_work(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.rc, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.ec, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.hist, sizeof(double) * b.hist_len * b.B));
-  // GMRES bases: (restart + 1) vectors indexed like the batch rows
-  int mr = 0;
-  for (auto& I : b.h) mr = std::max(mr, I.restart);
-  if (mr > 0)
-    FAMS_TRY(b.alloc((void**)&b.krylov, sizeof(double) * (size_t)(mr + 1) * (size_t)(n + 1)));
+  // GMRES bases: (restart + 1) vectors indexed like the batch rows, in the
+  // arithmetic of the instances that use them
+  // (a mixed-precision instance may fall back to FP64 GMRES)
+  int mr64 = 0, mr32 = 0;
+  bool mixed = false;
+  for (auto& I : b.h) {
+    bool m32 = I.precision == FAMS_MIXED;
+    mixed |= m32;
+    mr64 = std::max(mr64, I.restart);
+    if (m32) mr32 = std::max(mr32, I.restart);
+  }
+  if (mr64 > 0)
+    FAMS_TRY(b.alloc((void**)&b.krylov, sizeof(double) * (size_t)(mr64 + 1) * (size_t)(n + 1)));
+  if (mr32 > 0)
+    FAMS_TRY(b.alloc((void**)&b.krylov32, sizeof(float) * (size_t)(mr32 + 1) * (size_t)(n + 1)));
+  if (mixed) {
+    const long long n1 = n + 1, nnz = b.tot_nnz, pn = b.tot_pnnz;
+    FAMS_TRY(b.alloc((void**)&b.val32, sizeof(float) * (nnz + 1)));
+    FAMS_TRY(b.alloc((void**)&b.ilu32, sizeof(float) * (nnz + 1)));
+    FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (pn + 1)));
+    FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (pn + 1)));
+    FAMS_TRY(b.alloc((void**)&b.pk_lv32, sizeof(float) * PK * n1));
+    FAMS_TRY(b.alloc((void**)&b.pk_uv32, sizeof(float) * PK * n1));
+    FAMS_TRY(b.alloc((void**)&b.pk_ud32, sizeof(float) * n1));
+    for (float** v : {&b.rf, &b.zf, &b.dpf, &b.yf, &b.ylevf})
+      FAMS_TRY(b.alloc((void**)v, sizeof(float) * n1));
+    FAMS_TRY(b.alloc((void**)&b.xs, sizeof(double) * n1));
+    auto round = [&](const double* src, float* dst, long long cnt) {
+      if (cnt > 0) fams::note_launch(), k_round<<<grid_for(cnt, 256), 256, 0, b.stream>>>(cnt, src, dst);
+    };
+    round(b.val, b.val32, nnz);
+    round(b.ilu, b.ilu32, nnz);
+    round(b.p_val, b.p_val32, pn);
+    round(b.pt_val, b.pt_val32, pn);
+    round(b.pk_lv, b.pk_lv32, PK * n1);
+    round(b.pk_uv, b.pk_uv32, PK * n1);
+    round(b.pk_ud, b.pk_ud32, n1);
+    FAMS_CUDA(cudaGetLastError());
+  }
   return FAMS_OK;
 }
 
@@ -688,7 +924,7 @@ int make_q(Batch& b, const double* rhs_dev) {
 }
 
 int run_solve(Batch& b, double tol, float* ms) {
-  SolveArgs a;
+  SolveArgs a{};
   a.inst = b.d_inst;
   a.cs = b.cs[0];
   a.rowptr = b.rowptr; a.col = b.col; a.val = b.val; a.diag = b.diag;
@@ -704,6 +940,9 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.ylev = b.ylev;
   a.ntot = b.tot_row;
   a.tol = tol;
+  a.val32 = b.val32; a.p_val32 = b.p_val32; a.pt_val32 = b.pt_val32; a.F32 = b.ilu32;
+  a.pk_lv32 = b.pk_lv32; a.pk_uv32 = b.pk_uv32; a.pk_ud32 = b.pk_ud32;
+  a.xs = b.xs; a.rf = b.rf; a.zf = b.zf; a.dpf = b.dpf; a.yf = b.yf; a.ylevf = b.ylevf;
   int maxnc = 0;
   for (auto& I : b.h) maxnc = std::max(maxnc, I.nc);
   for (int i = 0; i < b.B; ++i)
@@ -712,35 +951,29 @@ int run_solve(Batch& b, double tol, float* ms) {
       return FAMS_ECAPACITY;
     }
   size_t smem = sizeof(double) * (2 * (size_t)maxnc + 2 * BAND_BUF);
-  int mr = 0, nrich = 0;
+  int mr = 0, nrich = 0, ngm = 0;
   for (auto& I : b.h) {
     mr = std::max(mr, I.restart);
-    nrich += I.krylov == FAMS_KRYLOV_NONE;
+    (I.krylov == FAMS_KRYLOV_NONE ? nrich : ngm)++;
   }
   size_t smem_g = smem + sizeof(double) * ((size_t)mr * mr + 6 * (size_t)mr + 2);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
-  if ((long long)(mr > 0 ? smem_g : smem) + 2048 > max_smem) {
+  if ((long long)(mr > 0 ? smem_g : smem) + 3072 > max_smem) {
     set_error("coarse system too large for the shared-memory coarse solve");
     return FAMS_ECAPACITY;
   }
-  FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - 2048));
-  FAMS_CUDA(cudaFuncSetAttribute(k_gmres, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - 3072));
+  for (const void* k : {(const void*)k_solve, (const void*)k_gmres})
+    FAMS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 3072));
   cudaEvent_t e0, e1;
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));
   FAMS_CUDA(cudaEventRecord(e0, b.stream));
   // each kernel leaves the other kind of instance alone
-  if (nrich > 0) {
-    fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
-    FAMS_CUDA(cudaGetLastError());
-  }
-  if (mr > 0) {
-    fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov);
-    FAMS_CUDA(cudaGetLastError());
-  }
+  if (nrich > 0) fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
+  if (ngm > 0)
+    fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov, b.krylov32);
+  FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaEventRecord(e1, b.stream));
   FAMS_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -825,7 +1058,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
   size_t smem = sizeof(double) * (2 * (size_t)I.nc + 2 * BAND_BUF);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
-  if ((long long)smem + 2048 > max_smem) {
+  if ((long long)smem + 3072 > max_smem) {
     set_error("coarse system too large for the shared-memory coarse solve");
     return FAMS_ECAPACITY;
   }
@@ -836,7 +1069,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
   double* dp = w + 3 * STATIC_ROWS;
   double* stat = w + 6 * STATIC_ROWS + 2 * STATIC_COARSE;
 
-  SolveArgs a;
+  SolveArgs a{};
   a.inst = b.d_inst;
   a.cs = b.cs[0];
   a.rowptr = b.rowptr; a.col = b.col; a.val = b.val; a.diag = b.diag;
@@ -865,7 +1098,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
       k_make_q<<<grid_for(I.n, 256), 256, 0, b.stream>>>(I.n, rhs ? dp : nullptr, b.qD, q);
   FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - 2048));
+                                 max_smem - 3072));
   auto t0 = std::chrono::steady_clock::now();
   fams::note_launch(), k_solve<<<1, SOLVE_T, smem, b.stream>>>(a);
   FAMS_CUDA(cudaGetLastError());

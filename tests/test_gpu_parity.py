@@ -295,6 +295,34 @@ def test_gmres_solve_to_tolerance(built, name, variant):
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
 
 
+def _mixed(p, krylov, restart=30):
+    q = copy.copy(p)
+    q.precision, q.krylov, q.restart = 1, krylov, restart
+    return q
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+def test_mixed_precision_reaches_the_fp64_tolerance(built, name, variant, krylov):
+    """FP32 inner stages with FP64 residuals and refinement: the true FP64
+    residual reaches tol, the solution matches the FP64 oracle's to tol x
+    cond, and the iteration count stays close to the FP64 path's."""
+    p, g, sysm, c, P, st, ctx = built(name, variant)
+    if krylov:
+        xo, ito, _, oko, _ = osolver.gmres_solve(st, tol=1e-8, max_iter=p.max_iter, restart=30)
+    else:
+        xo, ito, _, oko, _ = osolver.two_stage_solve(st, tol=1e-8, max_iter=p.max_iter)
+    with _fams().Context(_mixed(p, krylov)) as cm:
+        xs, stats = cm.solve(tol=1e-8)
+    x = xs[0]
+    rr = np.linalg.norm(sysm.q - sysm.A @ x) / np.linalg.norm(sysm.q)
+    assert oko and stats[0]["converged"] and rr <= 1e-8
+    assert abs(rr - stats[0]["rel_residual"]) <= 1e-6 * rr + 1e-13
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+    assert stats[0]["iterations"] <= ito + max(3, ito // 4)
+
+
 def test_gmres_and_richardson_instances_share_a_batch(built):
     """A batch mixing both outer iterations gives each instance its own result."""
     pa = _gmres(built("2d32", 0)[0], 30, 200)
