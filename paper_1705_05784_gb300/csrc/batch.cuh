@@ -128,7 +128,7 @@ struct Batch {
   int* pk_nu = nullptr;        // U entries right of the diagonal
   int* pk_uc = nullptr;
   double* pk_uv = nullptr;
-  double* pk_ud = nullptr;     // U diagonal
+  double* pk_ud = nullptr;     // reciprocal of the U diagonal
   double* ylev = nullptr;      // sweep right-hand side in level order
   // ---- iteration work vectors ----
   double* q = nullptr;

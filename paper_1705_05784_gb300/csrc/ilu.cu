@@ -105,7 +105,7 @@ __global__ void k_pack(long long nrow, const int* rows, const int* rowptr, const
   nl[t] = d - a;
   lp[t] = a;
   nu[t] = e - d - 1;
-  ud[t] = F[d];
+  ud[t] = 1.0 / F[d];   // reciprocal: the sweep multiplies
   for (int k = 0; k < PK; ++k) {
     long long o = (long long)k * nrow + t;
     lc[o] = (a + k < d) ? col[a + k] : 0;

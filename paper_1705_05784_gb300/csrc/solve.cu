@@ -185,15 +185,25 @@ __device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const 
   return (double)acc;
 }
 
-// coarse band solve: warp 0 runs the recurrences on columns staged in shared
-// memory, the other warps stage the next chunk meanwhile
+// Coarse band solve (LAPACK gbtrs steps on the band factors).  Warps
+// 0..CS_WARPS-1 run the recurrences column by column, splitting each
+// column's rows among them and meeting at a named barrier; the other warps
+// stage the next chunk of band columns into shared memory meanwhile (double
+// buffer, one CTA barrier per chunk).  The staging warps also turn U's
+// diagonal into its reciprocal, so the recurrences never divide.
+constexpr int CS_WARPS = 4;
+constexpr int CS_T = 32 * CS_WARPS;
+
+__device__ inline void cs_sync() { asm volatile("bar.sync 1, %0;" ::"n"(CS_T) : "memory"); }
+
 __device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, int ku, double* yb,
                              double* buf, int* pbuf) {
   const int kv = kl + ku, ldab = 2 * kl + ku + 1, stride = kv + 1;
   int ch = BAND_BUF / stride;
   ch = max(1, min(CH_MAX, ch));
   const int nch = (n + ch - 1) / ch;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x;
+  const bool comp = tid < CS_T;
   const int T = blockDim.x;
   // forward (L with row interchanges), chunk c holds columns [c ch, (c+1) ch)
   auto load_fwd = [&](int c, double* dst, int* pdst, int t0, int nt) {
@@ -204,61 +214,71 @@ __device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, i
     }
     for (int jj = t0; jj < ch; jj += nt) pdst[jj] = (j0 + jj < n) ? ipiv[j0 + jj] : 0;
   };
-  load_fwd(0, buf, pbuf, threadIdx.x, T);
+  load_fwd(0, buf, pbuf, tid, T);
   __syncthreads();
   for (int c = 0; c < nch; ++c) {
     double* cur = buf + (c & 1) * BAND_BUF;
     int* pcur = pbuf + (c & 1) * CH_MAX;
-    if (warp == 0) {
+    if (comp) {
       int j0 = c * ch;
       for (int jj = 0; jj < ch && j0 + jj < n; ++jj) {
         int j = j0 + jj;
         int km = min(kl, n - 1 - j);
         int pj = pcur[jj];
-        if (lane == 0 && pj != j) {
-          double t = yb[j];
-          yb[j] = yb[pj];
-          yb[pj] = t;
+        if (pj != j) {
+          if (tid == 0) {
+            double t = yb[j];
+            yb[j] = yb[pj];
+            yb[pj] = t;
+          }
+          cs_sync();
         }
-        __syncwarp();
         double yj = yb[j];
-        for (int t = 1 + lane; t <= km; t += 32) yb[j + t] -= cur[jj * stride + t - 1] * yj;
-        __syncwarp();
+        for (int t = 1 + tid; t <= km; t += CS_T) yb[j + t] -= cur[jj * stride + t - 1] * yj;
+        cs_sync();
       }
     } else if (c + 1 < nch) {
-      load_fwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, pbuf + ((c + 1) & 1) * CH_MAX,
-               threadIdx.x - 32, T - 32);
+      load_fwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, pbuf + ((c + 1) & 1) * CH_MAX, tid - CS_T,
+               T - CS_T);
     }
     __syncthreads();
   }
-  // backward (U, kv superdiagonals); chunk c holds columns [n-(c+1)ch, n-c ch)
+  // backward (U, kv superdiagonals, reciprocal diagonal); chunk c holds
+  // columns [n-(c+1)ch, n-c ch).  Rows are updated with x_j = y_j / U_jj
+  // while y_j itself is overwritten one column later, when nothing reads it.
   auto load_bwd = [&](int c, double* dst, int t0, int nt) {
     int jhi = n - c * ch, jlo = max(0, jhi - ch);
     for (int idx = t0; idx < (jhi - jlo) * stride; idx += nt) {
       int jj = idx / stride, rr = idx % stride, j = jlo + jj;
       int i = j - kv + rr;
-      dst[jj * stride + rr] = (i >= 0) ? AB[(long long)rr + (long long)ldab * j] : 0.0;
+      double v = (i >= 0) ? AB[(long long)rr + (long long)ldab * j] : 0.0;
+      dst[jj * stride + rr] = rr == kv ? 1.0 / v : v;
     }
   };
-  load_bwd(0, buf, threadIdx.x, T);
+  load_bwd(0, buf, tid, T);
   __syncthreads();
+  int prev = -1;
+  double xprev = 0.0;
   for (int c = 0; c < nch; ++c) {
     double* cur = buf + (c & 1) * BAND_BUF;
-    if (warp == 0) {
+    if (comp) {
       int jhi = n - c * ch, jlo = max(0, jhi - ch);
       for (int j = jhi - 1; j >= jlo; --j) {
         const double* colj = cur + (j - jlo) * stride;
-        double yj = yb[j] / colj[kv];
-        __syncwarp();
-        if (lane == 0) yb[j] = yj;
-        for (int i = max(0, j - kv) + lane; i < j; i += 32) yb[i] -= colj[kv + i - j] * yj;
-        __syncwarp();
+        double xj = yb[j] * colj[kv];
+        if (tid == 0 && prev >= 0) yb[prev] = xprev;
+        for (int i = max(0, j - kv) + tid; i < j; i += CS_T) yb[i] -= colj[kv + i - j] * xj;
+        prev = j;
+        xprev = xj;
+        cs_sync();
       }
     } else if (c + 1 < nch) {
-      load_bwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, threadIdx.x - 32, T - 32);
+      load_bwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, tid - CS_T, T - CS_T);
     }
     __syncthreads();
   }
+  if (tid == 0 && prev >= 0) yb[prev] = xprev;
+  __syncthreads();
 }
 
 // one row of a triangular sweep, loaded from the level-ordered layout: every
@@ -420,7 +440,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
         int d = a.diag[cur.i];
         for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= F[p] * y[a.col[p]];
       }
-      T xi = s / cur.diag;
+      T xi = s * cur.diag;   // reciprocal of U's diagonal
       y[cur.i] = xi;
       out[cur.i] = (xo + dpo) + xi;
     }
@@ -429,7 +449,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       int d = a.diag[i];
       T s = ylev[t];
       for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= F[p] * y[a.col[p]];
-      T xi = s / F[d];
+      T xi = s * Prec<T>::ud(a)[t];
       y[i] = xi;
       out[i] = ((base ? base[i] : T(0)) + dp[i]) + xi;
     }
@@ -600,6 +620,7 @@ __device__ inline double rows_apply_wide(const SolveArgs& a, int ro, int n, cons
 }
 
 constexpr int GS_CHUNK = 8;   // basis vectors per pass of the Gram-Schmidt dot products
+constexpr double REORTH_RATIO = 0.70710678118654752;   // 1/sqrt(2): reorthogonalise below it
 
 // h[0..k] = V[0..k]^T w over rows [ro, ro + n), reduced over the CTA into h
 // (shared memory, FP64); V_c at V + c ld
@@ -692,28 +713,33 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
     // z = M^-1 V_k, w = A z (in V_{k+1})
     double* Vk = V + (long long)k * ld;
     double* w = V + (long long)(k + 1) * ld;
+    double acc;
     if constexpr (mixed) {
       float* Zk = Z + (long long)k * ld;
       for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)Vk[i];
       __syncthreads();
       two_stage<float>(a, I, ii, a.rf, a.dpf, Zk, nullptr, S, cyc);
       t0 = clock64();
-      rows_apply_wide(a, ro, n, Zk, w);
+      acc = rows_apply_wide(a, ro, n, Zk, w);
     } else {
       two_stage<double>(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
       t0 = clock64();
-      rows_apply<double>(a, ro, n, a.r, w);
+      acc = rows_apply<double>(a, ro, n, a.r, w);
     }
-    __syncthreads();
-    // classical Gram-Schmidt, twice: H(0..k, k) = V^T w, w -= V H(0..k, k)
+    const double wn = sqrt(block_sum(acc, G.red));
+    // classical Gram-Schmidt: H(0..k, k) = V^T w, w -= V H(0..k, k); a second
+    // pass only when the first removed most of w (||w|| fell below ||w_0|| /
+    // sqrt 2), where the first pass alone can lose orthogonality
     double* Hk = G.H + (long long)k * (m + 1);
     block_dots<double>(V, ld, k + 1, ro, n, w, Hk, G.red8);
-    block_update<double>(V, ld, k + 1, ro, n, w, Hk);
-    __syncthreads();
-    block_dots<double>(V, ld, k + 1, ro, n, w, G.hv, G.red8);
-    double acc = block_update<double>(V, ld, k + 1, ro, n, w, G.hv);
+    acc = block_update<double>(V, ld, k + 1, ro, n, w, Hk);
     double hn = sqrt(block_sum(acc, G.red));
-    if (threadIdx.x <= k) Hk[threadIdx.x] += G.hv[threadIdx.x];
+    if (hn < REORTH_RATIO * wn) {
+      block_dots<double>(V, ld, k + 1, ro, n, w, G.hv, G.red8);
+      acc = block_update<double>(V, ld, k + 1, ro, n, w, G.hv);
+      hn = sqrt(block_sum(acc, G.red));
+      if (threadIdx.x <= k) Hk[threadIdx.x] += G.hv[threadIdx.x];
+    }
     if (hn > 0.0) {
       const double inv = 1.0 / hn;
       for (int i = ro + threadIdx.x; i < ro + n; i += NT) w[i] *= inv;
@@ -779,10 +805,11 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
 
 // GMRES(m) with the two-stage step as right preconditioner (Sec. 4.5, 4.6;
 // Saad's right-preconditioned GMRES, Givens rotations).  The Arnoldi vectors
-// are orthogonalised by classical Gram-Schmidt applied twice, whose two
-// passes over the basis replace the k + 1 dependent reductions of modified
-// Gram-Schmidt (same result in exact arithmetic, orthogonality to working
-// precision).  Iterations count preconditioner applications; the history
+// are orthogonalised by classical Gram-Schmidt, repeated once when the first
+// pass cancels most of the vector (Kahan's "twice is enough" test); its one
+// or two passes over the basis replace the k + 1 dependent reductions of
+// modified Gram-Schmidt (same result in exact arithmetic, orthogonality to
+// working precision).  Iterations count preconditioner applications; the history
 // holds the least-squares residual estimate inside a cycle and the true
 // residual at each cycle's end.
 //
