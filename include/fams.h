@@ -248,6 +248,47 @@ void fams_destroy(fams_ctx* ctx);
 const char* fams_strerror(int status);
 const char* fams_last_error(void);
 
+/* Request server: continuous batching of independent solves (setup, solve
+   to tol and, optionally, the flux reconstruction).  The paper has no
+   counterpart; it is the deployment layer around the solver.  Problems are
+   copied at submission.  `pipelines` worker threads, each with its own
+   context and CUDA stream, repeatedly take up to `max_batch` waiting
+   requests in arrival order -- as many as fit in `hbm_budget` bytes of
+   device memory (an estimate from the problem sizes) next to the
+   micro-batches already in flight, and always at least one on an idle
+   device -- and process them as one batch; requests that arrive meanwhile
+   go to the next free worker.  A result does not depend on what the request
+   was batched with (up to the rounding of the coarse operator's atomic
+   sums).  rhs, if given, holds n_matrix matrix-cell sources (fracture sources
+   are zero).  Calls are thread-safe. */
+typedef struct fams_server fams_server;
+typedef struct {
+  int max_batch;         /* instances per micro-batch, >= 1 */
+  int pipelines;         /* micro-batches in flight, 1..16 */
+  long long hbm_budget;  /* bytes the in-flight micro-batches may use */
+  double tol;            /* relative residual of every solve */
+  int with_flux;         /* also reconstruct the conservative fluxes */
+} fams_server_opts;
+
+int fams_server_create(const fams_server_opts* opts, fams_server** out);
+/* ticket: identifies the request in the calls below */
+int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm,
+                       const fams_fracs* fracs, const fams_opts* opts, const double* rhs,
+                       long long* ticket);
+/* waits up to timeout_ms (<= 0: no wait); *done = 1 once the result is ready */
+int fams_server_wait(fams_server* s, long long ticket, double timeout_ms, int* done);
+/* copies a finished request's pressure (n_matrix + n_frac values), fluxes (as
+   fams_flux; with_flux only) and statistics; latency_ms = completion minus
+   submission time.  Returns the request's status.  Null outputs are skipped;
+   a capacity below the result's size is FAMS_EINVAL. */
+int fams_server_result(fams_server* s, long long ticket, double* x, long long x_cap,
+                       double* face_flux, long long face_cap, double* nnc_flux, long long nnc_cap,
+                       fams_stats* st, double* latency_ms);
+/* frees a finished request */
+int fams_server_release(fams_server* s, long long ticket);
+/* finishes every submitted request, then stops the workers and frees all */
+void fams_server_destroy(fams_server* s);
+
 /* Number of CUDA kernels the library has launched since it was loaded (all
    contexts, all threads); the difference across a call counts its launches. */
 long long fams_launch_count(void);

@@ -17,7 +17,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libfams.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["util", "geometry", "system", "coarse", "basis", "coarseop", "ilu", "solve", "flux", "api"]
+UNITS = ["util", "geometry", "system", "coarse", "basis", "coarseop", "ilu", "solve", "flux", "api",
+         "server"]
 NOFMA = {"geometry"}
 
 

@@ -51,6 +51,11 @@ class fams_stats(C.Structure):
                 ("solve_ms", C.c_double)]
 
 
+class fams_server_opts(C.Structure):
+    _fields_ = [("max_batch", C.c_int), ("pipelines", C.c_int), ("hbm_budget", C.c_longlong),
+                ("tol", C.c_double), ("with_flux", C.c_int)]
+
+
 class FamsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libfams status {status}: {msg}")
@@ -86,6 +91,16 @@ def _load():
     lib.fams_last_error.restype = C.c_char_p
     lib.fams_launch_count.argtypes = []
     lib.fams_launch_count.restype = C.c_longlong
+    lib.fams_server_create.argtypes = [P(fams_server_opts), P(C.c_void_p)]
+    lib.fams_server_submit.argtypes = [C.c_void_p, P(fams_grid), P(C.c_double), P(fams_fracs),
+                                       P(fams_opts), P(C.c_double), P(C.c_longlong)]
+    lib.fams_server_wait.argtypes = [C.c_void_p, C.c_longlong, C.c_double, P(C.c_int)]
+    lib.fams_server_result.argtypes = [C.c_void_p, C.c_longlong, P(C.c_double), C.c_longlong,
+                                       P(C.c_double), C.c_longlong, P(C.c_double), C.c_longlong,
+                                       P(fams_stats), P(C.c_double)]
+    lib.fams_server_release.argtypes = [C.c_void_p, C.c_longlong]
+    lib.fams_server_destroy.argtypes = [C.c_void_p]
+    lib.fams_server_destroy.restype = None
     return lib
 
 
@@ -258,3 +273,67 @@ class Context:
         _check(lib.fams_flux(self.h, inst, x.ctypes.data_as(C.c_void_p),
                              face.ctypes.data_as(C.c_void_p), nnc.ctypes.data_as(C.c_void_p)))
         return face, nnc[: s["n_nnc"]]
+
+
+class Server:
+    """fams_server_*: continuous batching of independent solves."""
+
+    def __init__(self, max_batch=64, pipelines=2, hbm_budget=64 << 30, tol=1e-8, with_flux=True):
+        o = fams_server_opts(max_batch, pipelines, hbm_budget, tol, 1 if with_flux else 0)
+        self.h = C.c_void_p()
+        _check(lib.fams_server_create(C.byref(o), C.byref(self.h)))
+        self.with_flux = with_flux
+        self._sizes = {}
+
+    def submit(self, prob, rhs=None):
+        g, perm, f, o, keep = _args(prob)
+        t = C.c_longlong()
+        r = None if rhs is None else np.ascontiguousarray(rhs, np.float64)
+        _check(lib.fams_server_submit(self.h, C.byref(g), _dptr(perm), C.byref(f), C.byref(o),
+                                      None if r is None else _dptr(r), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        d = C.c_int()
+        _check(lib.fams_server_wait(self.h, ticket, timeout_ms, C.byref(d)))
+        return bool(d.value)
+
+    def result(self, ticket, n, n_faces=0, n_nnc=0):
+        """Pressure (n values), face and NNC fluxes (if the server makes them),
+        stats dict with latency_ms, and the request's status."""
+        x = np.zeros(n)
+        face = np.zeros(max(n_faces, 1))
+        nnc = np.zeros(max(n_nnc, 1))
+        st = fams_stats()
+        lat = C.c_double()
+        s = lib.fams_server_result(self.h, ticket, _dptr(x), n, _dptr(face), len(face), _dptr(nnc),
+                                   len(nnc), C.byref(st), C.byref(lat))
+        if s not in (OK, ENOCONV, EBREAKDOWN):
+            _check(s)
+        return x, face[:n_faces], nnc[:n_nnc], dict(iterations=st.iterations,
+                                                    rel_residual=st.rel_residual,
+                                                    converged=bool(st.converged),
+                                                    latency_ms=lat.value, status=s)
+
+    def status(self, ticket):
+        return lib.fams_server_result(self.h, ticket, None, 0, None, 0, None, 0, None, None)
+
+    def release(self, ticket):
+        _check(lib.fams_server_release(self.h, ticket))
+
+    def close(self):
+        if self.h:
+            lib.fams_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
