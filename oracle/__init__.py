@@ -51,10 +51,12 @@ def build(prob, route="staged"):
     g = _geom.build_geometry(prob)
     sysm = _asm.assemble(prob, g)
     c = _coarsen.build_coarse(prob, g)
+    plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
     if route == "staged":
-        P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis)
+        P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate)
     else:
-        P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis)
+        P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
+                                         plate)
     P = _basis.truncate(P, prob.alpha)
     st = _solver.setup(sysm, P, c.primal, c.n_coarse, prob.restriction)
     return g, sysm, c, P, st

@@ -41,7 +41,12 @@ DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
 M, F = 0, 1
 
 
-def keep_link(variant, med_r, rank_r, med_c, rank_c):
+def keep_link(variant, med_r, rank_r, med_c, rank_c, cross=False):
+    """cross: the link joins cells of two different fractures (a crossing).
+    Two fracture faces never share a link: faces of different fractures meet
+    only along edges, so a face-face link across a crossing is dropped."""
+    if cross and med_r == F and med_c == F and rank_r == RANK_F and rank_c == RANK_F:
+        return False
     if variant == DECOUPLED:
         return med_r == med_c and rank_c >= rank_r
     if variant == FRAC:
@@ -68,10 +73,59 @@ def stage_list(variant):
     return [[mE, fE], [mF, fF], [mI]]
 
 
-def prolongation_staged(A0, rank, medium, node_cell, variant):
-    """P (CSR, n x n_coarse) by the staged wirebasket rule."""
+def _plate_of(n, plate):
+    return np.full(n, -1, np.int64) if plate is None else np.asarray(plate, np.int64)
+
+
+def stage_blocks(A0, rank, medium, node_cell, variant, plate=None):
+    """The dual blocks of every stage (lists of rows), in solve order."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
+    plate = _plate_of(n, plate)
+    known = np.zeros(n, bool)
+    known[np.asarray(node_cell)] = True
+    ip, ix = A0.indptr, A0.indices
+    out = []
+    for stage in stage_list(variant):
+        in_stage = np.zeros(n, bool)
+        for (med, rk) in stage:
+            in_stage |= (medium == med) & (rank == rk)
+        in_stage &= ~known
+        S = np.nonzero(in_stage)[0]
+        if S.size == 0:
+            continue
+        loc = -np.ones(n, np.int64)
+        loc[S] = np.arange(S.size)
+        er, ec = [], []
+        for r in S:
+            for p in range(ip[r], ip[r + 1]):
+                c = ix[p]
+                cross = plate[r] >= 0 and plate[c] >= 0 and plate[r] != plate[c]
+                if c != r and in_stage[c] and keep_link(variant, medium[r], rank[r], medium[c],
+                                                        rank[c], cross):
+                    er.append(loc[r])
+                    ec.append(loc[c])
+        G = sp.csr_matrix((np.ones(len(er)), (er, ec)), shape=(S.size, S.size))
+        ncomp, lab = csg.connected_components(G, directed=False)
+        members = [[] for _ in range(ncomp)]
+        for li, r in enumerate(S):
+            members[lab[li]].append(int(r))
+        out.extend(members)
+        known |= in_stage
+    return out
+
+
+def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None):
+    """P (CSR, n x n_coarse) by the staged wirebasket rule.  plate[r]: input
+    fracture of fracture row r (-1 for matrix rows; None: no crossings)."""
+    A0 = sp.csr_matrix(A0)
+    n = A0.shape[0]
+    plate = _plate_of(n, plate)
+
+    def keep(r, c):
+        cross = plate[r] >= 0 and plate[c] >= 0 and plate[r] != plate[c]
+        return keep_link(variant, medium[r], rank[r], medium[c], rank[c], cross)
+
     nc = len(node_cell)
     rows = [dict() for _ in range(n)]
     known = np.zeros(n, bool)
@@ -94,8 +148,7 @@ def prolongation_staged(A0, rank, medium, node_cell, variant):
         for r in S:
             for p in range(ip[r], ip[r + 1]):
                 c = ix[p]
-                if c != r and in_stage[c] and keep_link(variant, medium[r], rank[r],
-                                                        medium[c], rank[c]):
+                if c != r and in_stage[c] and keep(r, c):
                     er.append(loc[r])
                     ec.append(loc[c])
         G = sp.csr_matrix((np.ones(len(er)), (er, ec)), shape=(S.size, S.size))
@@ -118,7 +171,7 @@ def prolongation_staged(A0, rank, medium, node_cell, variant):
                         diag += a
                         continue
                     T = -a
-                    if keep_link(variant, medium[r], rank[r], medium[c], rank[c]):
+                    if keep(r, c):
                         if c in bl:
                             Ab[i, bl[c]] = a
                         else:
@@ -168,11 +221,23 @@ def _solve(Ablk, R):
     return sp.csr_matrix(lu.solve(Rd))
 
 
-def prolongation_appendix(A0, rank, medium, node_cell, variant):
+def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None):
     """P from the printed block formulas of Appendix A (regular wirebasket:
-    the blocks that the TPFA stencil makes zero are taken as zero)."""
+    the blocks that the TPFA stencil makes zero are taken as zero).  Face-face
+    links across fracture crossings are dropped from A0 first (removed from
+    the diagonal), as in keep_link."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
+    plate = _plate_of(n, plate)
+    A0 = A0.tolil()
+    ff = np.nonzero((medium == F) & (rank == RANK_F))[0]
+    for r in ff:
+        for c in list(A0.rows[r]):
+            if c != r and medium[c] == F and rank[c] == RANK_F and plate[c] != plate[r]:
+                A0[r, r] = A0[r, r] + A0[r, c]
+                A0[r, c] = 0.0
+    A0 = sp.csr_matrix(A0)
+    A0.eliminate_zeros()
     nc = len(node_cell)
     cls = {}
     for med in (M, F):

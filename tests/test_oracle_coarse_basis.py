@@ -120,9 +120,43 @@ def test_staged_equals_appendix_formulas(variant, dim):
         p.fracs[:, 4] = 0.0
         p.fracs[:, 5] = 8.0
     g, s, c = _setup(p)
-    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant)
-    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant)
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
+    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
     assert abs(P1 - P2).max() < 1e-12
+
+
+def _crossing_plates(variant):
+    """Two full-height plates crossing at right angles in a 16x16x8 box."""
+    p = inputs.config_3d(16, 16, 8, 1.0, (4, 4, 2), 0, (4, 9), 1e3, (4, 4, 4), 4, 4, seed=5,
+                         basis=variant)
+    p.fracs = np.array([[1.5, 8.3, 14.5, 8.3, 0.0, 8.0], [8.3, 1.5, 8.3, 14.5, 0.0, 8.0]])
+    p.kf = np.array([1e3, 1e3])
+    return p
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_fracture_faces_do_not_merge_across_a_crossing(variant):
+    """Faces of two crossing plates meet only along the crossing: no dual
+    block of the face stage holds face cells of both plates, the staged and
+    Appendix A routes agree with the crossing links dropped, and the rows of
+    P still sum to one."""
+    p = _crossing_plates(variant)
+    g, s, c = _setup(p)
+    assert (g.ff_kind == 2).any()
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
+    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
+    assert abs(P1 - P2).max() < 1e-12
+    assert np.abs(np.asarray(P1.sum(axis=1)).ravel() - 1).max() < 1e-12
+    blocks = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
+    faces = (c.medium == 1) & (c.rank == basis.RANK_F)
+    for cells in blocks:
+        owners = {int(plate[r]) for r in cells if faces[r]}
+        assert len(owners) <= 1
+    # without the rule the two plates' faces would share a block
+    merged = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, variant, None)
+    assert any(len({int(plate[r]) for r in cells if faces[r]}) > 1 for cells in merged)
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
