@@ -107,6 +107,106 @@ class Clocks:
                 "samples": len(sm)}
 
 
+SERVE_WORKLOAD = ("stream of independent requests, arrivals Poisson at 80% of the served "
+                  "sustained rate: half 2D (side U{64..256}, 0-30 fractures L~U[20,120], "
+                  "log10 k std 2 corr 16, coarsening 8x8), half 3D (cube side U{24..48}, 0-10 "
+                  "full-height plates, log10 k std 1.5, coarsening U{4..8}^3); T_ratio "
+                  "1e2..1e8, the four coupling strategies, R^FE, GMRES(30), tol 1e-8, + flux")
+
+
+def serve_problems(n, seed):
+    """The served stream's requests (see SERVE_WORKLOAD), seeded."""
+    import numpy as np
+    from paper_1705_05784_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        basis = int(rng.integers(0, 4))
+        tr = float(TRATIOS[int(rng.integers(0, len(TRATIOS)))])
+        if rng.random() < 0.5:
+            side = 8 * int(rng.integers(8, 33))
+            p = inputs.config_2d(side, 2.0, 16.0, int(rng.integers(0, 31)), (20.0, 120.0), tr, 8, 8,
+                                 seed=seed + i, basis=basis, restriction=1, alpha=1e-2)
+        else:
+            side = int(rng.integers(24, 49))
+            cr = int(rng.integers(4, 9))
+            npl = int(rng.integers(0, 11))
+            p = inputs.config_3d(side, side, side, 1.5, (8.0, 8.0, 4.0), npl, (4, max(5, side // 2)),
+                                 tr, (cr, cr, cr), cr, cr, seed=seed + i, basis=basis,
+                                 restriction=1, alpha=1e-2)
+            if npl:
+                p.fracs[:, 4] = 0.0
+                p.fracs[:, 5] = float(side)
+        p.krylov, p.restart, p.max_iter = 1, 30, 400
+        out.append(p)
+    return out
+
+
+def serving(fams, n_req, n_plain, seed):
+    """Served stream (continuous batching through fams_server_*) against the
+    plain path (one context per request, solved one after another)."""
+    import numpy as np
+    probs = serve_problems(n_req, seed)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+    def run(rate):
+        lat, ok, fails = [], 0, {}
+        with fams.Server(max_batch=64, pipelines=3, hbm_budget=96 << 30, tol=TOL) as srv:
+            rng = np.random.default_rng(seed + 1)
+            arrive = np.cumsum(rng.exponential(1.0 / rate, len(probs))) if rate else None
+            t0 = time.perf_counter()
+            tickets = []
+            for k, p in enumerate(probs):
+                if arrive is not None:
+                    dt = arrive[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                tickets.append(srv.submit(p))
+            for t in tickets:
+                srv.wait(t, 600000.0)
+            elapsed = time.perf_counter() - t0
+            for t in tickets:
+                x, face, nnc, st = srv.fetch(t)
+                ok += st["status"] == 0 and st["converged"]
+                if st["status"] != 0:
+                    key = st["error"][:90]
+                    fails[key] = fails.get(key, 0) + 1
+                lat.append(st["latency_ms"])
+                srv.release(t)
+        return ok, elapsed, lat, fails
+
+    run(None)                                    # warm-up of the stream's code paths
+    ok_c, el_c, _, _ = run(None)                 # closed loop: sustained served rate
+    rate = 0.8 * len(probs) / el_c
+    ok_s, el_s, lat, fails = run(rate)
+    # plain: the first n_plain requests, each alone, one after another
+    times = []
+    ok_p = 0
+    for p in probs[:n_plain]:
+        t = time.perf_counter()
+        try:
+            with fams.Context(p) as c:
+                xs, st = c.solve(tol=TOL)
+                if st[0]["converged"]:
+                    c.flux(xs[0])
+                    ok_p += 1
+        except fams.FamsError:
+            pass                                 # counted as not solved, as in the stream
+        times.append(1000.0 * (time.perf_counter() - t))
+    plain_rate = ok_p / (sum(times) / 1000.0) if times else None
+    return {"workload": SERVE_WORKLOAD, "requests": len(probs),
+            "sustained_solves_per_s": ok_c / el_c, "arrival_rate_per_s": rate,
+            "served_solves_per_s": ok_s / el_s, "converged": ok_s, "failed": fails,
+            "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99),
+            "plain": {"requests": len(times), "solves_per_s": plain_rate,
+                      "p50_ms": pct(times, 0.50), "p99_ms": pct(times, 0.99),
+                      "note": "one context per request, setup + solve + flux, sequential"},
+            "served_vs_plain": (ok_s / el_s) / plain_rate if plain_rate else None}
+
+
 def _passes(s):
     n, nnz, nnzp, nc, ldab = s["n"], s["nnz"], s["nnzp"], s["nc"], s["ldab"]
     a_pass = 12 * nnz + 4 * (n + 1)                     # values, columns, row pointers
@@ -220,9 +320,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-iter", type=int, default=400,
                     help="cap on iterations (lower it only for profiler captures)")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64",
                     help="mixed: FP32 inner stages with FP64 residuals and refinement")
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
+    ap.add_argument("--serve", type=int, default=400,
+                    help="requests in the served stream (0: skip the serving measurement)")
+    ap.add_argument("--plain", type=int, default=32,
+                    help="requests of the stream solved one by one for the plain comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -375,6 +479,12 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if args.serve > 0:
+        sv = serving(fams, args.serve, args.plain, 7000)
+        line["serving"] = sv
+        line["latency"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
+                           "note": "served stream, submission to completion per request; "
+                                   "the batched step above takes ms_per_step"}
     print(json.dumps(line))
 
 

@@ -284,6 +284,10 @@ int fams_server_wait(fams_server* s, long long ticket, double timeout_ms, int* d
 int fams_server_result(fams_server* s, long long ticket, double* x, long long x_cap,
                        double* face_flux, long long face_cap, double* nnc_flux, long long nnc_cap,
                        fams_stats* st, double* latency_ms);
+/* sizes of a finished request's results: unknowns, face fluxes, NNC fluxes
+   (0 without fluxes; one placeholder value when the instance has no NNC) */
+int fams_server_sizes(fams_server* s, long long ticket, long long* n, long long* n_faces,
+                      long long* n_nnc);
 /* frees a finished request */
 int fams_server_release(fams_server* s, long long ticket);
 /* finishes every submitted request, then stops the workers and frees all */

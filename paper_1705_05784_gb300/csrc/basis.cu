@@ -48,13 +48,32 @@ __device__ inline int stage_of(int variant, int med, int rank) {
   }
 }
 
-__device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc) {
+// cross: the link joins fracture cells of two different input fractures.
+// Faces of different fractures meet only along edges: a face-face link across
+// a crossing is never kept.
+__device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc, bool cross) {
+  if (cross && mr == 1 && mc == 1 && rr == RANK_F && rc == RANK_F) return false;
   switch (variant) {
     case 0: return mr == mc && rc >= rr;
     case 1: return (mr == 0) ? (mc == 1 || rc >= rr) : (mc == 1 && rc >= rr);
     case 2: return (mr == 1) ? (mc == 0 || rc >= rr) : (mc == 0 && rc >= rr);
     default: return rc >= rr;
   }
+}
+
+__device__ inline bool crossing(const int* plate, int r, int c) {
+  int a = plate[r], b = plate[c];
+  return a >= 0 && b >= 0 && a != b;
+}
+
+// input fracture of every unknown (-1 for matrix cells)
+__global__ void k_row_plate(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* f_cfirst, long long nfr, int* plate) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  long long loc = r - I.row_off;
+  plate[r] = loc < I.nm ? -1 : find_segment(f_cfirst, (int)nfr + 1, I.fc_off + (loc - I.nm));
 }
 
 struct RowCtx {
@@ -118,8 +137,8 @@ __device__ inline int uf_find(volatile int* parent, int x) {
 }
 
 __global__ void k_stage_union(const Inst* inst, int B, const int* off_row, long long nrow,
-                              const int* rank, const int* rowptr, const int* col,
-                              const int* instage, int* label) {
+                              const int* rank, const int* plate, const int* rowptr,
+                              const int* col, const int* instage, int* label) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow || !instage[r]) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
@@ -128,7 +147,7 @@ __global__ void k_stage_union(const Inst* inst, int B, const int* off_row, long 
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
     int c = col[p];
     if (c <= r || !instage[c]) continue;
-    if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c])) continue;
+    if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, (int)r, c))) continue;
     int a = uf_find(parent, (int)r), b = uf_find(parent, c);
     while (a != b) {
       if (a < b) { int t = a; a = b; b = t; }   // link the larger root a under b
@@ -194,7 +213,8 @@ __device__ void bitonic_sort_int(int* a, int m) {
 // Mode 0 needs a power of two >= the largest block of ints of dynamic shared
 // memory.
 __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
-                            const int* rowptr, const int* col, const int* instage,
+                            const int* plate, const int* rowptr, const int* col,
+                            const int* instage,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
                             int* ncols, const int* colptr, int* colbuf, int* err) {
@@ -231,7 +251,7 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
       int cc = col[p];
       if (cc == r || instage[cc]) continue;
-      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) continue;
       ++links;
       if (pstage[cc] < 0) { over = true; continue; }
       cand += plen[cc];
@@ -251,7 +271,7 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
       int cc = col[p];
       if (cc == r || instage[cc]) continue;
-      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc])) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) continue;
       int st = pstage[cc];
       if (st < 0) continue;
       const int* pc = pool.col[st] + poff[cc];
@@ -300,6 +320,7 @@ struct CompArgs {
   int B;
   const int* off_row;
   const int* rank;
+  const int* plate;
   const int* rowptr;
   const int* col;
   const double* val;
@@ -347,7 +368,7 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
       double av = a.val[p];
       if (cc == r) { d += av - a.TD[r]; continue; }
       double T = -av;
-      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc])) {
+      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, r, cc))) {
         if (a.instage[cc]) {
           int pc = a.pos[cc];
           if (pc < 0 || pc >= n) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
@@ -495,6 +516,10 @@ int phase_basis(Batch& b) {
   if (nct > 0)
     fams::note_launch(), k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
                                                   vval, pstage, poff, plen);
+  int* plate = nullptr;
+  FAMS_TRY(b.scratch((void**)&plate, sizeof(int) * (nrow + 1)));
+  fams::note_launch(), k_row_plate<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow,
+                                                                     b.f_cfirst, b.tot_fr, plate);
   int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr;
   int *comp_of = nullptr, *pos = nullptr;
   FAMS_TRY(b.scratch((void**)&label, sizeof(int) * (nrow + 1)));
@@ -515,7 +540,7 @@ int phase_basis(Batch& b) {
     fams::note_launch(), k_stage_mark<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, b.rank, s, label,
                                                   instage);
     fams::note_launch(), k_stage_union<<<grid_for(nrow, T), T, 0, st>>>(
-        b.d_inst, b.B, b.off_row, nrow, b.rank, b.rowptr, b.col, instage, label);
+        b.d_inst, b.B, b.off_row, nrow, b.rank, plate, b.rowptr, b.col, instage, label);
     fams::note_launch(), k_stage_flatten<<<grid_for(nrow, T), T, 0, st>>>(nrow, instage, label);
     fams::note_launch(), k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
     long long ncomp = 0;
@@ -547,7 +572,7 @@ int phase_basis(Batch& b) {
                 std::to_string(MEMBER_SORT_MAX) + " are supported");
       return FAMS_ECAPACITY;
     }
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 0, ncols, nullptr, nullptr, b.d_err);
     FAMS_CUDA(cudaGetLastError());
@@ -555,7 +580,7 @@ int phase_basis(Batch& b) {
     long long totc = 0;
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 1, ncols, colptr, colbuf, b.d_err);
     // host plan: pool offsets, and the blocks by size class (doubles of
@@ -589,7 +614,7 @@ int phase_basis(Batch& b) {
     }
     pool.col[s] = ocol;
     pool.val[s] = oval;
-    CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, b.rowptr, b.col, b.val, b.TD, instage,
+    CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col, b.val, b.TD, instage,
                 nullptr, 0, coff, members, pos, colptr, colbuf, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};
     long long lo = 0;

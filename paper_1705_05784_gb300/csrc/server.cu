@@ -42,6 +42,7 @@ struct Request {
   std::vector<double> x, face, nnc;
   fams_stats st{};
   int status = FAMS_OK;
+  std::string err;   // detail of a failure
   bool done = false;
   double t_submit = 0, t_start = 0, t_done = 0;
 };
@@ -109,6 +110,7 @@ void run_batch(fams_server* s, std::vector<Request*>& batch) {
       }
     } else {
       batch[0]->status = st;
+      batch[0]->err = fams_last_error();
     }
     return;
   }
@@ -131,6 +133,7 @@ void run_batch(fams_server* s, std::vector<Request*>& batch) {
   }
   std::vector<fams_stats> stats(n);
   int ss = fams_solve_batch(ctx, rhs.data(), xs.data(), s->o.tol, stats.data());
+  std::string serr = ss == FAMS_OK ? "" : fams_last_error();
   std::vector<int> fst(n, FAMS_OK);
   if (s->o.with_flux && ss != FAMS_ECUDA && ss != FAMS_EINVAL)
     fams_flux_batch(ctx, xs.data(), faces.data(), nncs.data(), fst.data());
@@ -141,6 +144,7 @@ void run_batch(fams_server* s, std::vector<Request*>& batch) {
     else if (!stats[i].converged) r->status = std::isfinite(stats[i].rel_residual) ? FAMS_ENOCONV
                                                                                    : FAMS_EBREAKDOWN;
     else r->status = fst[i];
+    if (r->status != FAMS_OK) r->err = r->status == fst[i] ? "flux reconstruction failed" : serr;
   }
   fams_destroy(ctx);
 }
@@ -298,8 +302,21 @@ int fams_server_result(fams_server* s, long long ticket, double* x, long long x_
   }
   if (st) *st = r->st;
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;
-  if (r->status != FAMS_OK) set_error("request failed");
+  if (r->status != FAMS_OK) set_error("request failed: " + r->err);
   return r->status;
+}
+
+int fams_server_sizes(fams_server* s, long long ticket, long long* n, long long* n_faces,
+                      long long* n_nnc) {
+  if (!s) { set_error("null argument"); return FAMS_EINVAL; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) { set_error("unknown ticket"); return FAMS_EINVAL; }
+  if (!r->done) { set_error("request not finished"); return FAMS_EINVAL; }
+  if (n) *n = (long long)r->x.size();
+  if (n_faces) *n_faces = (long long)r->face.size();
+  if (n_nnc) *n_nnc = (long long)r->nnc.size();
+  return FAMS_OK;
 }
 
 int fams_server_release(fams_server* s, long long ticket) {

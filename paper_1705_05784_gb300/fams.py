@@ -99,6 +99,7 @@ def _load():
                                        P(C.c_double), C.c_longlong, P(C.c_double), C.c_longlong,
                                        P(fams_stats), P(C.c_double)]
     lib.fams_server_release.argtypes = [C.c_void_p, C.c_longlong]
+    lib.fams_server_sizes.argtypes = [C.c_void_p, C.c_longlong] + [P(C.c_longlong)] * 3
     lib.fams_server_destroy.argtypes = [C.c_void_p]
     lib.fams_server_destroy.restype = None
     return lib
@@ -308,12 +309,23 @@ class Server:
         lat = C.c_double()
         s = lib.fams_server_result(self.h, ticket, _dptr(x), n, _dptr(face), len(face), _dptr(nnc),
                                    len(nnc), C.byref(st), C.byref(lat))
-        if s not in (OK, ENOCONV, EBREAKDOWN):
-            _check(s)
+        # a failed request reports its status (and fams_last_error its reason)
         return x, face[:n_faces], nnc[:n_nnc], dict(iterations=st.iterations,
                                                     rel_residual=st.rel_residual,
                                                     converged=bool(st.converged),
-                                                    latency_ms=lat.value, status=s)
+                                                    latency_ms=lat.value, status=s,
+                                                    error=lib.fams_last_error().decode()
+                                                    if s != OK else "")
+
+    def sizes(self, ticket):
+        v = [C.c_longlong() for _ in range(3)]
+        _check(lib.fams_server_sizes(self.h, ticket, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def fetch(self, ticket):
+        """result() with buffers sized by the finished request itself."""
+        n, nf, nn = self.sizes(ticket)
+        return self.result(ticket, n, nf, nn)
 
     def status(self, ticket):
         return lib.fams_server_result(self.h, ticket, None, 0, None, 0, None, 0, None, None)

@@ -46,12 +46,19 @@ def _case(name, variant=0, restriction=1):
                              seed=8, basis=variant, restriction=restriction)
         p.fracs[:, 4] = 0.0
         p.fracs[:, 5] = 12.0
+    elif name == "3dcross":
+        # two full-height plates crossing at right angles plus an oblique one
+        p = inputs.config_3d(16, 16, 8, 1.0, (4, 4, 2), 0, (4, 9), 1e3, (4, 4, 4), 4, 4, seed=5,
+                             basis=variant, restriction=restriction)
+        p.fracs = np.array([[1.5, 8.3, 14.5, 8.3, 0.0, 8.0], [8.3, 1.5, 8.3, 14.5, 0.0, 8.0],
+                            [2.2, 2.7, 13.6, 12.9, 0.0, 8.0]])
+        p.kf = np.array([1e3, 1e4, 1e3])
     else:
         raise KeyError(name)
     return p
 
 
-CASES = ["2d32", "2d64", "2d50ragged", "3d"]
+CASES = ["2d32", "2d64", "2d50ragged", "3d", "3dcross"]
 
 
 @pytest.fixture(scope="module")
@@ -222,7 +229,7 @@ def _fixed_k(p, k):
 
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d", "3dcross"])
 def test_iteration_trajectory(built, name, variant, restriction):
     """After the same number of sweeps the GPU iterate equals the oracle's."""
     p, g, sysm, c, P, st, ctx = built(name, variant, restriction)
@@ -260,7 +267,7 @@ def _gmres(p, restart, max_iter):
 
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("variant", [0, 3])
-@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d"])
+@pytest.mark.parametrize("name", ["2d32", "2d64", "2d50ragged", "3d", "3dcross"])
 def test_gmres_trajectory(built, name, variant, restriction):
     """GMRES(8) for 13 iterations (one restart): the GPU iterate and residual
     history equal the oracle's (modified Gram-Schmidt there, classical
