@@ -1,6 +1,8 @@
 // Device-wide helpers used by the setup phases: exclusive scan and a CSR
 // transpose whose segments come out sorted (deterministic, no atomics in the
 // final order).
+#include <algorithm>
+
 #include "batch.cuh"
 
 namespace fams {
@@ -114,27 +116,9 @@ __global__ void k_place(const int* rowof, const int* col, const double* val, lon
   if (val) tval[pos] = val[i];
 }
 
-// sort each segment by key (one CTA per segment, in shared memory)
-constexpr int SEG_SORT_MAX = 4096;
-__global__ void k_seg_sort(const int* ptr, int nseg, int* key, double* val, int* err,
-                           int strict) {
-  __shared__ int sk[SEG_SORT_MAX];
-  __shared__ double sv[SEG_SORT_MAX];
-  int s = blockIdx.x;
-  if (s >= nseg) return;
-  int a = ptr[s], n = ptr[s + 1] - a;
-  if (n <= 1) return;
-  if (n > SEG_SORT_MAX) {
-    if (strict && threadIdx.x == 0) atomicCAS(err, 0, DERR_CAPACITY);
-    return;
-  }
-  int m = 1;
-  while (m < n) m <<= 1;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    sk[i] = (i < n) ? key[a + i] : 0x7fffffff;
-    sv[i] = (i < n && val) ? val[a + i] : 0.0;
-  }
-  __syncthreads();
+// bitonic sort of keys (and values) in place, m a power of two, one CTA
+template <class K, class V>
+__device__ void bitonic(K* sk, V* sv, int m) {
   for (int k = 2; k <= m; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -142,25 +126,90 @@ __global__ void k_seg_sort(const int* ptr, int nseg, int* key, double* val, int*
         if (l > i) {
           bool up = (i & k) == 0;
           if ((sk[i] > sk[l]) == up) {
-            int tk = sk[i]; sk[i] = sk[l]; sk[l] = tk;
-            double tv = sv[i]; sv[i] = sv[l]; sv[l] = tv;
+            K tk = sk[i]; sk[i] = sk[l]; sk[l] = tk;
+            if (sv) { V tv = sv[i]; sv[i] = sv[l]; sv[l] = tv; }
           }
         }
       }
       __syncthreads();
     }
   }
+}
+
+// sort the segments with lo < length <= hi by key, one CTA per segment: in
+// dynamic shared memory (gtmp null; room for the power of two above hi) or
+// in a global scratch slice of `stride` keys (and values) per CTA
+__global__ void k_seg_sort(const int* ptr, int nseg, int* key, double* val, int lo, int hi,
+                           int* gk, double* gv, long long stride) {
+  extern __shared__ double dyn[];
+  int s = blockIdx.x;
+  if (s >= nseg) return;
+  int a = ptr[s], n = ptr[s + 1] - a;
+  if (n <= lo || n > hi || n <= 1) return;
+  int m = 1;
+  while (m < n) m <<= 1;
+  double* sv = gk ? (val ? gv + (long long)blockIdx.x * stride : nullptr) : (val ? dyn : nullptr);
+  int* sk = gk ? gk + (long long)blockIdx.x * stride : (int*)(val ? dyn + m : dyn);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sk[i] = (i < n) ? key[a + i] : 0x7fffffff;
+    if (sv) sv[i] = (i < n) ? val[a + i] : 0.0;
+  }
+  __syncthreads();
+  bitonic(sk, sv, m);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     key[a + i] = sk[i];
     if (val) val[a + i] = sv[i];
   }
 }
 
+__global__ void k_seg_max(const int* ptr, int nseg, int* out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nseg) atomicMax(out, ptr[s + 1] - ptr[s]);
+}
+
+constexpr int SEG_SMALL = 1024;   // segments sorted with a small shared-memory footprint
+
 }  // namespace
 
+// sort each segment of `key` (and `val`) ascending: short segments in shared
+// memory, longer ones in shared memory sized to the longest (up to what a CTA
+// holds), the rest in global scratch.  `strict` is kept for the callers'
+// intent: every segment is sorted.
 int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict) {
+  (void)strict;
   if (nseg <= 0) return FAMS_OK;
-  fams::note_launch(), k_seg_sort<<<nseg, 256, 0, b.stream>>>(ptr, nseg, key, val, b.d_err, strict ? 1 : 0);
+  int* dmax = nullptr;
+  FAMS_TRY(b.scratch((void**)&dmax, sizeof(int)));
+  FAMS_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), b.stream));
+  fams::note_launch(), k_seg_max<<<grid_for(nseg, 256), 256, 0, b.stream>>>(ptr, nseg, dmax);
+  int mx = 0;
+  FAMS_CUDA(cudaMemcpyAsync(&mx, dmax, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  if (mx <= 1) return FAMS_OK;
+  const size_t per = sizeof(int) + (val ? sizeof(double) : 0);
+  auto pow2 = [](int v) { int m = 1; while (m < v) m <<= 1; return m; };
+  int max_smem = 0;
+  FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  FAMS_CUDA(cudaFuncSetAttribute(k_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  int small = std::min(mx, SEG_SMALL);
+  fams::note_launch(), k_seg_sort<<<nseg, 256, per * pow2(small), b.stream>>>(
+      ptr, nseg, key, val, 0, SEG_SMALL, nullptr, nullptr, 0);
+  if (mx > SEG_SMALL) {
+    int cap = SEG_SMALL;
+    while ((size_t)cap * 2 * per <= (size_t)max_smem && cap * 2 <= pow2(mx)) cap *= 2;
+    if (cap > SEG_SMALL)
+      fams::note_launch(), k_seg_sort<<<nseg, 512, per * cap, b.stream>>>(
+          ptr, nseg, key, val, SEG_SMALL, cap, nullptr, nullptr, 0);
+    if (mx > cap) {
+      long long stride = pow2(mx);
+      int *gk = nullptr;
+      double* gv = nullptr;
+      FAMS_TRY(b.scratch((void**)&gk, sizeof(int) * stride * (size_t)nseg));
+      if (val) FAMS_TRY(b.scratch((void**)&gv, sizeof(double) * stride * (size_t)nseg));
+      fams::note_launch(), k_seg_sort<<<nseg, 1024, 0, b.stream>>>(ptr, nseg, key, val, cap, 1 << 30,
+                                                                  gk, gv, stride);
+    }
+  }
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }
