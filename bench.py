@@ -142,7 +142,7 @@ def serve_problems(n, seed):
     return out
 
 
-def serving(fams, n_req, n_plain, seed):
+def serving(fams, n_req, n_plain, seed, pipelines=6, max_batch=64):
     """Served stream (continuous batching through fams_server_*) against the
     plain path (one context per request, solved one after another)."""
     import numpy as np
@@ -153,8 +153,9 @@ def serving(fams, n_req, n_plain, seed):
         return v[min(len(v) - 1, int(q * len(v)))] if v else None
 
     def run(rate):
-        lat, ok, fails = [], 0, {}
-        with fams.Server(max_batch=64, pipelines=3, hbm_budget=96 << 30, tol=TOL) as srv:
+        lat, svc, ok, fails = [], [], 0, {}
+        with fams.Server(max_batch=max_batch, pipelines=pipelines, hbm_budget=96 << 30,
+                         tol=TOL) as srv:
             rng = np.random.default_rng(seed + 1)
             arrive = np.cumsum(rng.exponential(1.0 / rate, len(probs))) if rate else None
             t0 = time.perf_counter()
@@ -175,13 +176,15 @@ def serving(fams, n_req, n_plain, seed):
                     key = st["error"][:90]
                     fails[key] = fails.get(key, 0) + 1
                 lat.append(st["latency_ms"])
+                svc.append(st["service_ms"])
                 srv.release(t)
-        return ok, elapsed, lat, fails
+        return ok, elapsed, lat, fails, svc
 
     run(None)                                    # warm-up of the stream's code paths
-    ok_c, el_c, _, _ = run(None)                 # closed loop: sustained served rate
+
+    ok_c, el_c, _, _, _ = run(None)              # closed loop: sustained served rate
     rate = 0.8 * len(probs) / el_c
-    ok_s, el_s, lat, fails = run(rate)
+    ok_s, el_s, lat, fails, svc = run(rate)
     # plain: the first n_plain requests, each alone, one after another
     times = []
     ok_p = 0
@@ -197,10 +200,12 @@ def serving(fams, n_req, n_plain, seed):
             pass                                 # counted as not solved, as in the stream
         times.append(1000.0 * (time.perf_counter() - t))
     plain_rate = ok_p / (sum(times) / 1000.0) if times else None
-    return {"workload": SERVE_WORKLOAD, "requests": len(probs),
+    return {"workload": SERVE_WORKLOAD, "requests": len(probs), "pipelines": pipelines,
+            "max_batch": max_batch,
             "sustained_solves_per_s": ok_c / el_c, "arrival_rate_per_s": rate,
             "served_solves_per_s": ok_s / el_s, "converged": ok_s, "failed": fails,
             "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99),
+            "service_p50_ms": pct(svc, 0.50), "service_p99_ms": pct(svc, 0.99),
             "plain": {"requests": len(times), "solves_per_s": plain_rate,
                       "p50_ms": pct(times, 0.50), "p99_ms": pct(times, 0.99),
                       "note": "one context per request, setup + solve + flux, sequential"},
@@ -325,6 +330,8 @@ def main():
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
     ap.add_argument("--serve", type=int, default=400,
                     help="requests in the served stream (0: skip the serving measurement)")
+    ap.add_argument("--pipelines", type=int, default=6, help="server: micro-batches in flight")
+    ap.add_argument("--max-batch", type=int, default=64, help="server: requests per micro-batch")
     ap.add_argument("--plain", type=int, default=32,
                     help="requests of the stream solved one by one for the plain comparison")
     args = ap.parse_args()
@@ -480,7 +487,7 @@ def main():
         "clocks": clk.summary(),
     }
     if args.serve > 0:
-        sv = serving(fams, args.serve, args.plain, 7000)
+        sv = serving(fams, args.serve, args.plain, 7000, args.pipelines, args.max_batch)
         line["serving"] = sv
         line["latency"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
                            "note": "served stream, submission to completion per request; "

@@ -253,7 +253,9 @@ const char* fams_last_error(void);
    counterpart; it is the deployment layer around the solver.  Problems are
    copied at submission.  `pipelines` worker threads, each with its own
    context and CUDA stream, repeatedly take up to `max_batch` waiting
-   requests in arrival order -- as many as fit in `hbm_budget` bytes of
+   requests in arrival order -- of the oldest one's kind (whether its coarse
+   band factorisation is estimated to be large), as many as fit in
+   `hbm_budget` bytes of
    device memory (an estimate from the problem sizes) next to the
    micro-batches already in flight, and always at least one on an idle
    device -- and process them as one batch; requests that arrive meanwhile
@@ -278,7 +280,8 @@ int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm
 /* waits up to timeout_ms (<= 0: no wait); *done = 1 once the result is ready */
 int fams_server_wait(fams_server* s, long long ticket, double timeout_ms, int* done);
 /* copies a finished request's pressure (n_matrix + n_frac values), fluxes (as
-   fams_flux; with_flux only) and statistics; latency_ms = completion minus
+   fams_flux; with_flux only) and statistics (st->solve_ms: from the start of
+   the request's micro-batch to its completion); latency_ms = completion minus
    submission time.  Returns the request's status.  Null outputs are skipped;
    a capacity below the result's size is FAMS_EINVAL. */
 int fams_server_result(fams_server* s, long long ticket, double* x, long long x_cap,

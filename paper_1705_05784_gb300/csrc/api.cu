@@ -15,6 +15,8 @@ struct fams_ctx {
 
 namespace fams {
 
+constexpr uint64_t POOL_KEEP = 32ull << 30;   // bytes of freed device memory the pool keeps
+
 namespace {
 thread_local std::string g_err;
 std::atomic<long long> g_launches{0};
@@ -97,6 +99,18 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
   b.B = n;
   FAMS_CUDA(cudaGetDevice(&b.device));
   FAMS_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+  {
+    // keep freed blocks in this process's pool for the next context (up to
+    // POOL_KEEP bytes) instead of returning them at every synchronisation
+    cudaMemPool_t pool;
+    FAMS_CUDA(cudaDeviceGetDefaultMemPool(&pool, b.device));
+    uint64_t keep = POOL_KEEP;
+    FAMS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    // reuse across streams only once the free has completed: the pool then
+    // never makes one context's stream wait for another's
+    int no = 0;
+    FAMS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no));
+  }
   b.h.assign(n, Inst{});
   long long m = 0, fr = 0;
   for (int i = 0; i < n; ++i) {
@@ -210,8 +224,9 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
 void destroy_batch(Batch& b) {
   if (b.stream) cudaStreamSynchronize(b.stream);
   b.free_tmp();
-  for (void* p : b.owned) cudaFree(p);
+  for (void* p : b.owned) cudaFreeAsync(p, b.stream);
   b.owned.clear();
+  if (b.stream) cudaStreamSynchronize(b.stream);
   if (b.stream) cudaStreamDestroy(b.stream);
   b.stream = nullptr;
 }

@@ -166,11 +166,15 @@ struct Batch {
   double* fface = nullptr;
   double* fnnc = nullptr;
 
+  // Device memory is stream-ordered (cudaMallocAsync on the context's
+  // stream, from the device's memory pool): unlike cudaMalloc/cudaFree it
+  // never synchronises the device, so contexts on other streams (the
+  // request server's micro-batches) keep running.
   int alloc(void** p, size_t bytes) {
     if (bytes == 0) bytes = 8;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, stream);
     if (e != cudaSuccess) {
-      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       return FAMS_ENOMEM;
     }
     owned.push_back(*p);
@@ -178,16 +182,16 @@ struct Batch {
   }
   int scratch(void** p, size_t bytes) {
     if (bytes == 0) bytes = 8;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, stream);
     if (e != cudaSuccess) {
-      set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       return FAMS_ENOMEM;
     }
     tmp.push_back(*p);
     return FAMS_OK;
   }
   void free_tmp() {
-    for (void* p : tmp) cudaFree(p);
+    for (void* p : tmp) cudaFreeAsync(p, stream);
     tmp.clear();
   }
   int upload_inst();

@@ -81,46 +81,82 @@ __global__ void k_ac_cols(const Inst* inst, int B, const int* off_nc, long long 
     if (row[j] != 0.0 && j != r) cols[o++] = j;
 }
 
-// reverse Cuthill-McKee per instance (one thread each): BFS from a node of
-// minimum degree, neighbours in order of (degree, index), then reversed.
+// reverse Cuthill-McKee per instance, one warp each: BFS from a node of
+// minimum degree (lowest index on ties), each node's unvisited neighbours
+// appended in order of (degree, index), components in turn, then reversed.
+// The warp gathers a node's new neighbours with a ballot and orders them with
+// a bitonic sort in shared memory.
+constexpr int RCM_DEG_MAX = 2048;   // neighbours of one coarse node
+
 __global__ void k_rcm(const Inst* inst, int B, const int* ptr, const int* cols, CoarseSys cs,
-                      int* visited, int* queue, int* kl_out, int* ku_out) {
-  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+                      int* visited, int* queue, int* err) {
+  __shared__ long long key[RCM_DEG_MAX];
+  int ii = blockIdx.x;
   if (ii >= B) return;
+  const int lane = threadIdx.x;
   const Inst& I = inst[ii];
-  int n = I.nc, o = I.nc_off;
+  const int n = I.nc, o = I.nc_off;
   const int* rp = ptr + o;
   int* vis = visited + o;
   int* qu = queue + o;
   int* perm = cs.perm + o;
-  for (int i = 0; i < n; ++i) vis[i] = 0;
+  for (int i = lane; i < n; i += 32) vis[i] = 0;
+  __syncwarp();
   int head = 0, tail = 0;
   while (tail < n) {
-    int best = -1, bd = 0x7fffffff;
-    for (int i = 0; i < n; ++i)
-      if (!vis[i] && rp[i + 1] - rp[i] < bd) { bd = rp[i + 1] - rp[i]; best = i; }
-    vis[best] = 1;
-    qu[tail++] = best;
+    // unvisited node of minimum (degree, index)
+    long long best = 0x7fffffffffffffffLL;
+    for (int i = lane; i < n; i += 32)
+      if (!vis[i]) best = min(best, ((long long)(rp[i + 1] - rp[i]) << 32) | i);
+    for (int s = 16; s; s >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, s));
+    int start = (int)(best & 0xffffffff);
+    if (lane == 0) {
+      vis[start] = 1;
+      qu[tail] = start;
+    }
+    ++tail;
+    __syncwarp();
     while (head < tail) {
       int u = qu[head++];
-      int first = tail;
-      for (int p = rp[u]; p < rp[u + 1]; ++p) {
-        int v = cols[p];
-        if (!vis[v]) { vis[v] = 1; qu[tail++] = v; }
-      }
-      // insertion sort of the new entries by (degree, index)
-      for (int a = first + 1; a < tail; ++a) {
-        int v = qu[a], dv = rp[v + 1] - rp[v];
-        int b = a - 1;
-        while (b >= first) {
-          int w = qu[b], dw = rp[w + 1] - rp[w];
-          if (dw > dv || (dw == dv && w > v)) { qu[b + 1] = w; --b; } else break;
+      int cnt = 0;
+      for (int p0 = rp[u]; p0 < rp[u + 1]; p0 += 32) {
+        int p = p0 + lane;
+        int v = p < rp[u + 1] ? cols[p] : -1;
+        bool fresh = v >= 0 && !vis[v];
+        unsigned m = __ballot_sync(0xffffffffu, fresh);
+        if (fresh) {
+          int at = cnt + __popc(m & ((1u << lane) - 1));
+          if (at < RCM_DEG_MAX) key[at] = ((long long)(rp[v + 1] - rp[v]) << 32) | v;
+          vis[v] = 1;
         }
-        qu[b + 1] = v;
+        cnt += __popc(m);
       }
+      if (cnt > RCM_DEG_MAX) {
+        if (lane == 0) atomicCAS(err, 0, DERR_CAPACITY);
+        return;
+      }
+      __syncwarp();
+      int m = 1;
+      while (m < cnt) m <<= 1;
+      for (int i = cnt + lane; i < m; i += 32) key[i] = 0x7fffffffffffffffLL;
+      __syncwarp();
+      for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < m; i += 32) {
+            int l = i ^ j;
+            if (l > i) {
+              bool up = (i & k) == 0;
+              if ((key[i] > key[l]) == up) { long long t = key[i]; key[i] = key[l]; key[l] = t; }
+            }
+          }
+          __syncwarp();
+        }
+      for (int i = lane; i < cnt; i += 32) qu[tail + i] = (int)(key[i] & 0xffffffff);
+      tail += cnt;
+      __syncwarp();
     }
   }
-  for (int k = 0; k < n; ++k) perm[k] = qu[n - 1 - k];
+  for (int k = lane; k < n; k += 32) perm[k] = qu[n - 1 - k];
 }
 
 // lower / upper bandwidth of each instance's dense A_c under the ordering, from
@@ -399,7 +435,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
   FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
   FAMS_CUDA(cudaMemsetAsync(dkl, 0, sizeof(int) * B, st));
   FAMS_CUDA(cudaMemsetAsync(dku, 0, sizeof(int) * B, st));
-  fams::note_launch(), k_rcm<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, dkl, dku);
+  fams::note_launch(), k_rcm<<<B, 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, b.d_err);
   fams::note_launch(), k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
   fams::note_launch(), k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
   FAMS_CUDA(cudaGetLastError());

@@ -2,7 +2,8 @@
 //
 // Callers submit problems (copied at submission) and collect results by
 // ticket.  Worker threads, each with its own context and CUDA stream, take
-// whatever has arrived -- up to max_batch requests, and no more than the
+// whatever has arrived -- up to max_batch requests of the oldest request's
+// kind (a wide coarse band to factor, or not), and no more than the
 // device-memory budget allows next to the micro-batches already in flight --
 // set the micro-batch up, solve it and reconstruct its fluxes, while the
 // other workers do the same with the requests that arrived in the meantime.
@@ -38,6 +39,7 @@ struct Request {
   fams_fracs fr{};
   fams_opts opts{};
   size_t mem = 0;
+  bool heavy = false;   // large coarse factorisation: batched only with its own kind
   // results
   std::vector<double> x, face, nnc;
   fams_stats st{};
@@ -64,6 +66,18 @@ size_t estimate_bytes(const Request& r) {
   long long nc = cells / cr + nfc / std::max(1, r.opts.frac_dmin > 0 ? r.opts.frac_dmin : 8) + 8;
   long long kry = r.opts.krylov == FAMS_KRYLOV_GMRES ? (long long)(r.opts.restart + 1) * 8 : 0;
   return (size_t)(n * (1200 + kry) + nc * nc * 16);
+}
+
+// work of the coarse band factorisation, nc kl^2 with kl about three planes
+// (3D) or three lines (2D) of coarse nodes: a few requests with wide coarse
+// bands would otherwise hold a whole micro-batch of small ones
+bool estimate_heavy(const Request& r) {
+  auto nodes = [](int n, int c) { return (double)std::max(1, (n + std::max(1, c) - 1) / std::max(1, c)); };
+  double cx = nodes(r.grid.nx, r.opts.coarsen[0]), cy = nodes(r.grid.ny, r.opts.coarsen[1]);
+  double cz = r.grid.dim == 3 ? nodes(r.grid.nz, r.opts.coarsen[2]) : 1.0;
+  double nc = cx * cy * cz;
+  double kl = 3.0 * (r.grid.dim == 3 ? cx * cy : cx);
+  return nc * kl * kl > 2e7;
 }
 
 }  // namespace
@@ -163,14 +177,18 @@ void worker(fams_server* s) {
         return s->inflight == 0 || s->inflight + s->pending.front()->mem <= (size_t)s->o.hbm_budget;
       });
       if (s->stop && s->pending.empty()) return;
-      while (!s->pending.empty() && (int)batch.size() < s->o.max_batch) {
-        Request* r = s->pending.front();
+      // the oldest request, then later ones of the same kind (light or
+      // heavy) in arrival order, while they fit
+      const bool kind = s->pending.front()->heavy;
+      for (auto it = s->pending.begin(); it != s->pending.end() && (int)batch.size() < s->o.max_batch;) {
+        Request* r = *it;
+        if (r->heavy != kind) { ++it; continue; }
         if (!(s->inflight == 0 && batch.empty()) &&
             s->inflight + mem + r->mem > (size_t)s->o.hbm_budget)
           break;
         batch.push_back(r);
         mem += r->mem;
-        s->pending.pop_front();
+        it = s->pending.erase(it);
       }
       s->inflight += mem;
     }
@@ -251,6 +269,7 @@ int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm
   r->opts = *opts;
   if (rhs) r->rhs.assign(rhs, rhs + cells);   // matrix sources; fracture sources default to 0
   r->mem = estimate_bytes(*r);
+  r->heavy = estimate_heavy(*r);
   r->t_submit = now_ms();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -300,7 +319,10 @@ int fams_server_result(fams_server* s, long long ticket, double* x, long long x_
     if (nnc_cap < (long long)r->nnc.size()) { set_error("nnc buffer too small"); return FAMS_EINVAL; }
     std::copy(r->nnc.begin(), r->nnc.end(), nnc_flux);
   }
-  if (st) *st = r->st;
+  if (st) {
+    *st = r->st;
+    st->solve_ms = r->t_done - r->t_start;   // service time of its micro-batch
+  }
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;
   if (r->status != FAMS_OK) set_error("request failed: " + r->err);
   return r->status;

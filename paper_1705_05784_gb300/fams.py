@@ -314,6 +314,7 @@ class Server:
                                                     rel_residual=st.rel_residual,
                                                     converged=bool(st.converged),
                                                     latency_ms=lat.value, status=s,
+                                                    service_ms=st.solve_ms,
                                                     error=lib.fams_last_error().decode()
                                                     if s != OK else "")
 
