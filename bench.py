@@ -39,7 +39,7 @@ TOL = 1e-8
 TRATIOS = (1e2, 1e4, 1e6, 1e8)
 
 
-def problems(batch, seed0, max_iter=400, krylov=1, restart=30, precision=1):
+def problems(batch, seed0, max_iter=400, krylov=1, restart=30, precision=0):
     """The bench workload: instance i has coupling strategy i % 4 and
     T_ratio 1e2..1e8 by (i // 4) % 4, seeds seed0 + i."""
     from paper_1705_05784_gb300 import inputs

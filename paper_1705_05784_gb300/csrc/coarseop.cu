@@ -215,6 +215,9 @@ __global__ void k_inverse_perm(const Inst* inst, int B, const int* off_nc, long 
 
 __device__ inline int wrap(int x, int k) { return x >= k ? x - k : x; }
 
+constexpr int LU_EXTRA = 32;      // narrow LU ring: columns of fill past the upper band
+constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choice
+
 // Symmetric positive definite coarse systems (R^FE = P^T: A_c = P^T A P):
 // band LDL^T without pivoting, about a quarter of the band LU's work.  The
 // active lower triangle (rows and columns j..j+kl) lives in a shared-memory
@@ -281,21 +284,28 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
   if (threadIdx.x == 0) cs.bad[ii] = 0;
 }
 
-// Band LU with partial pivoting (LAPACK gbtf2 steps) on the active block
-// only: rows j..j+kl and columns j..j+kv, a ring of (kl+1) x (kv+1) doubles,
-// element (i, c) at (i mod (kl+1), c mod (kv+1)), in shared memory or, when
-// it does not fit, in a per-CTA slice of global memory (`gws`, `gstride`
-// doubles per CTA).  Each finished pivot row and multiplier column goes
-// back to the band; row j + kl + 1 and column j + kv + 1 enter the ring in
-// their place.
+// Band LU (LAPACK gbtf2 steps) on the active block only: rows j..j+kl and a
+// ring of K2 columns from j on, element (i, c) at (i mod (kl+1), c mod K2), in
+// shared memory or, when it does not fit, in a per-CTA slice of global memory
+// (`gws`, `gstride` doubles per CTA).  Each finished pivot row and multiplier
+// column goes back to the band; row j + kl + 1 and column j + K2 enter the
+// ring in their place.
+//
+// With K2 = kl + ku + 1 (extra < 0) the ring holds every fill that partial
+// pivoting can cause.  With K2 = ku + 1 + extra the factorisation pivots by
+// threshold -- the diagonal stays unless it is below tau times the column's
+// largest entry -- and an instance whose row interchanges would spread fill
+// beyond the ring sets failed[ii] and leaves its band to be refactored with
+// the full ring.
 __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* only, int* err,
-                              double* gws, long long gstride) {
+                              double* gws, long long gstride, int extra, double tau, int* failed) {
   extern __shared__ double dyn[];
   int ii = blockIdx.x;
   if (!only[ii]) return;
   const Inst& I = inst[ii];
   const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
-  const int K1 = kl + 1, K2 = kv + 1, T = blockDim.x;
+  const int K1 = kl + 1, K2 = extra < 0 ? kv + 1 : min(kv + 1, ku + 1 + extra);
+  const int T = blockDim.x;
   const int nw = T >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* S = gws ? gws + (long long)blockIdx.x * gstride : dyn;
   double* lj = gws ? dyn : dyn + (long long)K1 * K2;   // multipliers of column j
@@ -308,10 +318,11 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   __shared__ double s_piv;
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
 #define SEL(rs, c) S[(long long)(rs) * K2 + (c)]
+#define INBAND(i, c) ((i) < n && (c) < n && (c) - (i) <= ku && (i) - (c) <= kl)
   if (threadIdx.x == 0) { s_ju = 0; s_bad = 0; s_badcol = -1; }
   for (int e = threadIdx.x; e < K1 * K2; e += T) {
     int i = e / K2, c = e - i * K2;
-    S[e] = (i < n && c < n && c - i <= ku && i - c <= kl) ? BEL(i, c) : 0.0;
+    S[e] = INBAND(i, c) ? BEL(i, c) : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -335,6 +346,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
       int i0 = 0;
       for (int q = 0; q < nw; ++q)
         if (sv[q] > b0 || (sv[q] == b0 && si[q] < i0)) { b0 = sv[q]; i0 = si[q]; }
+      if (fabs(SEL(jr, jc)) >= tau * b0) i0 = 0;   // threshold: keep the diagonal
       s_jp = i0;
       ipiv[j] = j + i0;
       if (!(b0 > 0.0) || !isfinite(b0)) {
@@ -344,6 +356,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
         s_piv = SEL(wrap(jr + i0, K1), jc);
       }
       s_ju = max(s_ju, min(j + ku + i0, n - 1));
+      if (s_ju - j + 1 > K2) s_bad = 2;   // fill beyond the ring
     }
     __syncthreads();
     if (s_bad) break;
@@ -362,30 +375,52 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
     for (int t = 1 + threadIdx.x; t <= km; t += T) lj[t] = SEL(wrap(jr + t, K1), jc) * inv;
     for (int cc = 1 + threadIdx.x; cc <= wd; cc += T) ur[cc] = SEL(jr, wrap(jc + cc, K2));
     __syncthreads();
-    // rank-1 update: a warp per row, lanes along the pivot row
+    // rank-1 update: a warp per row, lanes along the pivot row, four
+    // independent loads in flight per lane (the ring may sit in global memory)
     for (int t = 1 + w; t <= km; t += nw) {
       const int rs = wrap(jr + t, K1);
       const double l = lj[t];
-      for (int cc = 1 + lane; cc <= wd; cc += 32) SEL(rs, wrap(jc + cc, K2)) -= l * ur[cc];
+      for (int c0 = 1 + lane; c0 <= wd; c0 += 128) {
+        double v[4];
+        int cs_[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int cc = c0 + 32 * u;
+          cs_[u] = cc <= wd ? wrap(jc + cc, K2) : -1;
+          v[u] = cs_[u] >= 0 ? SEL(rs, cs_[u]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cs_[u] >= 0) SEL(rs, cs_[u]) = v[u] - l * ur[c0 + 32 * u];
+      }
     }
     // finished pivot row and multipliers back to the band (temporaries only)
     for (int cc = threadIdx.x; cc <= wd; cc += T) BEL(j, j + cc) = cc == 0 ? piv : ur[cc];
     for (int t = 1 + threadIdx.x; t <= km; t += T) BEL(j + t, j) = lj[t];
     __syncthreads();
-    // column slot jc becomes column j + K2 (zero in the active rows), row
-    // slot jr becomes row j + K1 of the original matrix
-    const int inew = j + K1;
-    for (int rs = threadIdx.x; rs < K1; rs += T)
-      if (rs != jr) SEL(rs, jc) = 0.0;
+    // column slot jc becomes column j + K2 (still original in the band: no
+    // step so far reached it), row slot jr becomes row j + K1
+    const int inew = j + K1, cnew = j + K2;
+    for (int t = 1 + threadIdx.x; t < K1; t += T) {
+      int i = j + t;
+      SEL(wrap(jr + t, K1), jc) = INBAND(i, cnew) ? BEL(i, cnew) : 0.0;
+    }
     for (int cc = 1 + threadIdx.x; cc <= K2; cc += T) {
       int c = j + cc;
-      SEL(jr, wrap(jc + cc, K2)) = (inew < n && c < n) ? BEL(inew, c) : 0.0;
+      SEL(jr, wrap(jc + cc, K2)) = INBAND(inew, c) ? BEL(inew, c) : 0.0;
     }
     __syncthreads();
   }
+#undef INBAND
 #undef SEL
 #undef BEL
-  if (threadIdx.x == 0) cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
+  if (threadIdx.x == 0) {
+    if (s_bad == 2) {
+      failed[ii] = 1;
+    } else {
+      cs.bad[ii] = s_bad ? s_badcol + 1 : 0;
+    }
+  }
 }
 
 }  // namespace
@@ -502,12 +537,58 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
     }
     for (int i = 0; i < B; ++i) lu[i] |= failed[i];
   }
-  // band LU on the active block: in shared memory where it fits, else in a
-  // global workspace per CTA
-  std::vector<int> lu_s(B, 0), lu_g(B, 0);
-  size_t act_s = 0, act_g = 0, temps = 0;
+  // band LU on the active block.  First a narrow ring (threshold pivoting,
+  // fill up to LU_EXTRA columns past the upper band) in shared memory; then
+  // the full ring of partial pivoting for the instances that did not fit it
+  // or pivoted beyond it: in shared memory where it fits, else in global
+  // scratch
+  FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem));
+  size_t temps = 0;
   for (int i = 0; i < B; ++i)   // multipliers and pivot row of the widest band
     if (lu[i]) temps = std::max(temps, sizeof(double) * (size_t)(2 * ch.kl[i] + ch.ku[i] + 2));
+  {
+    std::vector<int> lu_n(B, 0);
+    size_t act_n = 0;
+    for (int i = 0; i < B; ++i) {
+      if (!lu[i]) continue;
+      size_t k2 = (size_t)std::min(ch.kl[i] + ch.ku[i] + 1, ch.ku[i] + 1 + LU_EXTRA);
+      size_t act = (size_t)(ch.kl[i] + 1) * k2;
+      if (sizeof(double) * act + temps <= (size_t)max_smem) {
+        lu_n[i] = 1;
+        act_n = std::max(act_n, act);
+      }
+    }
+    if (act_n > 0) {
+      int *d_n = nullptr, *d_f = nullptr;
+      FAMS_TRY(b.scratch((void**)&d_n, sizeof(int) * B));
+      FAMS_TRY(b.scratch((void**)&d_f, sizeof(int) * B));
+      FAMS_CUDA(cudaMemcpyAsync(d_n, lu_n.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+      FAMS_CUDA(cudaMemsetAsync(d_f, 0, sizeof(int) * B, st));
+      fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_n + temps, st>>>(
+          b.d_inst, B, cs, d_n, b.d_err, nullptr, 0, LU_EXTRA, LU_TAU, d_f);
+      FAMS_CUDA(cudaGetLastError());
+      std::vector<int> failed(B, 0);
+      FAMS_CUDA(cudaMemcpyAsync(failed.data(), d_f, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+      FAMS_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int i = 0; i < B; ++i) {
+        if (lu_n[i] && !failed[i]) lu[i] = 0;   // done
+        if (failed[i]) {
+          any = true;
+          FAMS_CUDA(cudaMemsetAsync(cs.band + ch.band_off[i], 0,
+                                    sizeof(double) * (2 * ch.kl[i] + ch.ku[i] + 1) * b.h[i].nc, st));
+        }
+      }
+      if (any) {
+        FAMS_CUDA(cudaMemcpyAsync(d_f, failed.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct,
+                                                                           cs, ip, d_f);
+      }
+    }
+  }
+  std::vector<int> lu_s(B, 0), lu_g(B, 0);
+  size_t act_s = 0, act_g = 0;
   for (int i = 0; i < B; ++i) {
     if (!lu[i]) continue;
     size_t act = (size_t)(ch.kl[i] + 1) * (size_t)(ch.kl[i] + ch.ku[i] + 1);
@@ -519,12 +600,10 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
       act_g = std::max(act_g, act);
     }
   }
-  FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem));
   if (act_s > 0) {
     FAMS_CUDA(cudaMemcpyAsync(d_lu, lu_s.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
     fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_s + temps, st>>>(
-        b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0);
+        b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0, -1, 1.0, nullptr);
   }
   if (act_g > 0) {
     int* d_lg = nullptr;
@@ -532,8 +611,8 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
     FAMS_TRY(b.scratch((void**)&d_lg, sizeof(int) * B));
     FAMS_TRY(b.scratch((void**)&gws, sizeof(double) * act_g * (size_t)B));
     FAMS_CUDA(cudaMemcpyAsync(d_lg, lu_g.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-    fams::note_launch(), k_band_lu_act<<<B, 256, temps, st>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
-                                                                (long long)act_g);
+    fams::note_launch(), k_band_lu_act<<<B, 1024, temps, st>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
+                                                                 (long long)act_g, -1, 1.0, nullptr);
   }
   FAMS_CUDA(cudaGetLastError());
   ch.bad.assign(B, 0);
