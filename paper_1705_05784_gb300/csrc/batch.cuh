@@ -123,7 +123,7 @@ struct Batch {
   int* pk_pos = nullptr;       // row -> position t
   int* pk_nl = nullptr;        // L entries of the row
   int* pk_lp = nullptr;        // first L entry in the CSR (for entries beyond PK)
-  int* pk_lc = nullptr;        // PK x tot_row columns
+  int* pk_lc = nullptr;        // PK x tot_row neighbours, as level positions
   double* pk_lv = nullptr;     // PK x tot_row values
   int* pk_nu = nullptr;        // U entries right of the diagonal
   int* pk_uc = nullptr;

@@ -93,24 +93,30 @@ __global__ void k_ilu_factor(const Inst* inst, int B, const int* rowptr, const i
   if (threadIdx.x == 0 && bad) atomicCAS(err, 0, DERR_BREAKDOWN);
 }
 
-// level-ordered structure-of-arrays copy of the factors (position t)
+__global__ void k_pos(long long nrow, const int* rows, int* pos) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nrow) pos[rows[t]] = (int)t;
+}
+
+// level-ordered structure-of-arrays copy of the factors (position t); the
+// first PK neighbours of each triangle are stored by their level positions,
+// so the sweeps can find recent results in shared memory
 __global__ void k_pack(long long nrow, const int* rows, const int* rowptr, const int* col,
-                       const int* diag, const double* F, int* pos, int* nl, int* lp, int* lc,
+                       const int* diag, const double* F, const int* pos, int* nl, int* lp, int* lc,
                        double* lv, int* nu, int* uc, double* uv, double* ud) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nrow) return;
   int i = rows[t];
   int a = rowptr[i], d = diag[i], e = rowptr[i + 1];
-  pos[i] = (int)t;
   nl[t] = d - a;
   lp[t] = a;
   nu[t] = e - d - 1;
   ud[t] = 1.0 / F[d];   // reciprocal: the sweep multiplies
   for (int k = 0; k < PK; ++k) {
     long long o = (long long)k * nrow + t;
-    lc[o] = (a + k < d) ? col[a + k] : 0;
+    lc[o] = (a + k < d) ? pos[col[a + k]] : 0;
     lv[o] = (a + k < d) ? F[a + k] : 0.0;
-    uc[o] = (d + 1 + k < e) ? col[d + 1 + k] : 0;
+    uc[o] = (d + 1 + k < e) ? pos[col[d + 1 + k]] : 0;
     uv[o] = (d + 1 + k < e) ? F[d + 1 + k] : 0.0;
   }
 }
@@ -169,10 +175,12 @@ int phase_ilu(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.pk_uv, sizeof(double) * PK * n1));
   FAMS_TRY(b.alloc((void**)&b.pk_ud, sizeof(double) * n1));
   FAMS_TRY(b.alloc((void**)&b.ylev, sizeof(double) * n1));
-  if (nrow > 0)
+  if (nrow > 0) {
+    fams::note_launch(), k_pos<<<grid_for(nrow, T), T, 0, st>>>(nrow, b.lev_rows, b.pk_pos);
     fams::note_launch(), k_pack<<<grid_for(nrow, T), T, 0, st>>>(
         nrow, b.lev_rows, b.rowptr, b.col, b.diag, b.ilu, b.pk_pos, b.pk_nl, b.pk_lp, b.pk_lc,
         b.pk_lv, b.pk_nu, b.pk_uc, b.pk_uv, b.pk_ud);
+  }
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }

@@ -30,6 +30,8 @@ constexpr int SOLVE_T = 512;
 constexpr int ROWS_ILP = 4;
 constexpr int BAND_BUF = 3072;   // doubles per staged chunk of band columns (24 KiB)
 constexpr int CH_MAX = 64;       // band columns per chunk
+constexpr int SWEEP_RING = 4096; // level positions of recent sweep results kept in shared memory
+static_assert(SWEEP_RING <= 2 * BAND_BUF, "the sweep ring lives in the band buffer");
 
 __device__ inline double block_sum(double v, double* red) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -401,46 +403,59 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
   __syncthreads();
   long long t3 = clock64();
-  // step 7, L sweep in place: y_i = r1_i - sum_{j<i} L_ij y_j
+  // step 7, L sweep: y_i = r1_i - sum_{j<i} L_ij y_j, by level position t.
+  // Results also go to a shared-memory ring of the last SWEEP_RING
+  // positions (the band buffer, idle during the sweeps): a neighbour from a
+  // recent level is read there, older ones from ylev.  The current level
+  // writes positions [lp[l], lp[l+1]), so a position tc is still in the ring
+  // while tc >= lp[l+1] - SWEEP_RING.
+  T* ring = reinterpret_cast<T*>(S.buf);
   SweepRow<T> cur, nxt;
   sweep_load<T>(a, lp, 0, nlev, true, cur);
   for (int l = 0; l < nlev; ++l) {
     sweep_load<T>(a, lp, l + 1, nlev, true, nxt);
+    const int lim = lp[l + 1] - SWEEP_RING;
+    auto yv = [&](int tc) { return tc >= lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
     if (cur.t >= 0) {
       T s = cur.base;
 #pragma unroll
       for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * y[cur.c[k]];
-      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= F[p] * y[a.col[p]];
-      y[cur.i] = s;
+        if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
+      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
+      ring[cur.t & (SWEEP_RING - 1)] = s;
       ylev[cur.t] = s;
     }
     for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
       int i = a.lev_rows[t];
       T s = ylev[t];
-      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= F[p] * y[a.col[p]];
-      y[i] = s;
+      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
+      ring[t & (SWEEP_RING - 1)] = s;
       ylev[t] = s;
     }
     __syncthreads();
     cur = nxt;
   }
   long long t4 = clock64();
-  // U sweep and step 8: out = (base + dp1) + dp2
+  // U sweep and step 8: out = (base + dp1) + dp2; the ring now holds the
+  // upper neighbours, valid while tc < lp[l] + SWEEP_RING
   sweep_load<T>(a, lp, nlev - 1, nlev, false, cur);
   for (int l = nlev - 1; l >= 0; --l) {
     sweep_load<T>(a, lp, l - 1, nlev, false, nxt);
+    const int lim = lp[l] + SWEEP_RING;
+    auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
     if (cur.t >= 0) {
       T s = cur.base;
       T xo = base ? base[cur.i] : T(0), dpo = dp[cur.i];
 #pragma unroll
       for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * y[cur.c[k]];
+        if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
       if (cur.cnt > PK) {
         int d = a.diag[cur.i];
-        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= F[p] * y[a.col[p]];
+        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
       }
       T xi = s * cur.diag;   // reciprocal of U's diagonal
+      ring[cur.t & (SWEEP_RING - 1)] = xi;
+      ylev[cur.t] = xi;
       y[cur.i] = xi;
       out[cur.i] = (xo + dpo) + xi;
     }
@@ -448,8 +463,10 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       int i = a.lev_rows[t];
       int d = a.diag[i];
       T s = ylev[t];
-      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= F[p] * y[a.col[p]];
+      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
       T xi = s * Prec<T>::ud(a)[t];
+      ring[t & (SWEEP_RING - 1)] = xi;
+      ylev[t] = xi;
       y[i] = xi;
       out[i] = ((base ? base[i] : T(0)) + dp[i]) + xi;
     }
