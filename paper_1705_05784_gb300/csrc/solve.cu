@@ -636,54 +636,6 @@ __device__ inline double rows_apply_wide(const SolveArgs& a, int ro, int n, cons
   return acc;
 }
 
-constexpr int GS_CHUNK = 8;   // basis vectors per pass of the Gram-Schmidt dot products
-constexpr double REORTH_RATIO = 0.70710678118654752;   // 1/sqrt(2): reorthogonalise below it
-
-// h[0..k] = V[0..k]^T w over rows [ro, ro + n), reduced over the CTA into h
-// (shared memory, FP64); V_c at V + c ld
-template <class T>
-__device__ void block_dots(const T* V, long long ld, int k1, int ro, int n, const T* w, double* h,
-                           double* red8) {
-  const int NT = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = NT >> 5;
-  for (int c0 = 0; c0 < k1; c0 += GS_CHUNK) {
-    T s[GS_CHUNK];
-#pragma unroll
-    for (int c = 0; c < GS_CHUNK; ++c) s[c] = 0;
-    for (int i = ro + threadIdx.x; i < ro + n; i += NT) {
-      T wi = w[i];
-#pragma unroll
-      for (int c = 0; c < GS_CHUNK; ++c)
-        if (c0 + c < k1) s[c] += V[(long long)(c0 + c) * ld + i] * wi;
-    }
-#pragma unroll
-    for (int c = 0; c < GS_CHUNK; ++c) {
-      T v = s[c];
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red8[warp * GS_CHUNK + c] = (double)v;
-    }
-    __syncthreads();
-    if (threadIdx.x < GS_CHUNK && c0 + threadIdx.x < k1) {
-      double v = 0.0;
-      for (int q = 0; q < nw; ++q) v += red8[q * GS_CHUNK + threadIdx.x];
-      h[c0 + threadIdx.x] = v;
-    }
-    __syncthreads();
-  }
-}
-
-// w -= V[0..k] h; returns this thread's sum of w^2
-template <class T>
-__device__ inline double block_update(const T* V, long long ld, int k1, int ro, int n, T* w,
-                                      const double* h) {
-  T acc = 0;
-  for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
-    T wi = w[i];
-    for (int c = 0; c < k1; ++c) wi -= (T)h[c] * V[(long long)c * ld + i];
-    w[i] = wi;
-    acc += wi * wi;
-  }
-  return (double)acc;
-}
 
 constexpr double MIXED_MIN_GAIN = 0.1;   // FP32 cycle: least FP64 residual reduction kept
 
@@ -693,10 +645,8 @@ struct GmresSmem {
   double* g;     // m+1 rotated right-hand side
   double* cs;    // m Givens cosines
   double* sn;    // m Givens sines
-  double* hv;    // m+1 second Gram-Schmidt pass
   double* yv;    // m least-squares solution
   double* red;   // block_sum scratch
-  double* red8;  // block_dots scratch
   int* done;
 };
 
@@ -743,20 +693,34 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
       t0 = clock64();
       acc = rows_apply<double>(a, ro, n, a.r, w);
     }
-    const double wn = sqrt(block_sum(acc, G.red));
-    // classical Gram-Schmidt: H(0..k, k) = V^T w, w -= V H(0..k, k); a second
-    // pass only when the first removed most of w (||w|| fell below ||w_0|| /
-    // sqrt 2), where the first pass alone can lose orthogonality
+    (void)acc;
+    // modified Gram-Schmidt, as in the oracle: for i = 0..k, h_i = V_i . w,
+    // then w -= h_i V_i.  Pass i applies the previous projection and forms
+    // the next dot product in one sweep over the rows, so each step costs
+    // 2 (k+1) n FMAs and k + 2 block reductions.
     double* Hk = G.H + (long long)k * (m + 1);
-    block_dots<double>(V, ld, k + 1, ro, n, w, Hk, G.red8);
-    acc = block_update<double>(V, ld, k + 1, ro, n, w, Hk);
-    double hn = sqrt(block_sum(acc, G.red));
-    if (hn < REORTH_RATIO * wn) {
-      block_dots<double>(V, ld, k + 1, ro, n, w, G.hv, G.red8);
-      acc = block_update<double>(V, ld, k + 1, ro, n, w, G.hv);
-      hn = sqrt(block_sum(acc, G.red));
-      if (threadIdx.x <= k) Hk[threadIdx.x] += G.hv[threadIdx.x];
+    double hprev = 0.0;
+    for (int i = 0; i <= k + 1; ++i) {
+      const double* Vp = i > 0 ? V + (long long)(i - 1) * ld : nullptr;
+      const double* Vi = i <= k ? V + (long long)i * ld : nullptr;
+      double s = 0.0;
+      for (int r = ro + threadIdx.x; r < ro + n; r += NT) {
+        double wr = w[r];
+        if (Vp) {
+          wr -= hprev * Vp[r];
+          w[r] = wr;
+        }
+        s += Vi ? Vi[r] * wr : wr * wr;
+      }
+      double h = block_sum(s, G.red);
+      if (i <= k) {
+        if (threadIdx.x == 0) Hk[i] = h;
+        hprev = h;
+      } else {
+        hprev = sqrt(h);
+      }
     }
+    const double hn = hprev;
     if (hn > 0.0) {
       const double inv = 1.0 / hn;
       for (int i = ro + threadIdx.x; i < ro + n; i += NT) w[i] *= inv;
@@ -822,11 +786,8 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
 
 // GMRES(m) with the two-stage step as right preconditioner (Sec. 4.5, 4.6;
 // Saad's right-preconditioned GMRES, Givens rotations).  The Arnoldi vectors
-// are orthogonalised by classical Gram-Schmidt, repeated once when the first
-// pass cancels most of the vector (Kahan's "twice is enough" test); its one
-// or two passes over the basis replace the k + 1 dependent reductions of
-// modified Gram-Schmidt (same result in exact arithmetic, orthogonality to
-// working precision).  Iterations count preconditioner applications; the history
+// are orthogonalised by modified Gram-Schmidt, each projection fused with
+// the next dot product in one pass over the rows.  Iterations count preconditioner applications; the history
 // holds the least-squares residual estimate inside a cycle and the true
 // residual at each cycle's end.
 //
@@ -838,7 +799,6 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
 __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64, float* kry32) {
   extern __shared__ double sm[];
   __shared__ double red[40];
-  __shared__ double red8[(SOLVE_T / 32) * GS_CHUNK];
   __shared__ int s_done;
   __shared__ int pbuf[2 * CH_MAX];
   int ii = blockIdx.x;
@@ -851,10 +811,8 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
   G.g = G.H + (m + 1) * m;
   G.cs = G.g + (m + 1);
   G.sn = G.cs + m;
-  G.hv = G.sn + m;
-  G.yv = G.hv + (m + 1);
+  G.yv = G.sn + m;
   G.red = red;
-  G.red8 = red8;
   G.done = &s_done;
   const int NT = blockDim.x;
   bool use32 = I.precision == FAMS_MIXED;
@@ -1000,7 +958,7 @@ int run_solve(Batch& b, double tol, float* ms) {
     mr = std::max(mr, I.restart);
     (I.krylov == FAMS_KRYLOV_NONE ? nrich : ngm)++;
   }
-  size_t smem_g = smem + sizeof(double) * ((size_t)mr * mr + 6 * (size_t)mr + 2);
+  size_t smem_g = smem + sizeof(double) * ((size_t)mr * mr + 5 * (size_t)mr + 1);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   if ((long long)(mr > 0 ? smem_g : smem) + 3072 > max_smem) {
