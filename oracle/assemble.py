@@ -135,3 +135,41 @@ def assemble(prob, geom=None):
     s.dirichlet = (dc, dT, dp, dfid)
     s.Tmf = Tmf
     return s
+
+
+def update_mobility(sysm, scale):
+    """Time-step update of the fine system (the reading of a mobility change
+    between time steps, where the basis functions are kept): every
+    connection's transmissibility is multiplied by the harmonic mean
+    2 s_i s_j / (s_i + s_j) of its two cells' mobility scales, a Dirichlet
+    half-cell transmissibility by its cell's scale.  The pattern does not
+    change; A0, A, the Dirichlet terms and q follow.  Returns a new System
+    carrying `scale` (the flux reconstruction applies it to the connections)."""
+    import copy
+    sc = np.asarray(scale, np.float64)
+    out = copy.copy(sysm)
+    C = sp.coo_matrix(sysm.A0)
+    off = C.row != C.col
+    r, c, v = C.row[off], C.col[off], C.data[off]
+    hm = 2.0 * sc[r] * sc[c] / (sc[r] + sc[c])
+    v = v * hm
+    n = sysm.n
+    diag = np.zeros(n)
+    np.subtract.at(diag, r, v)
+    A0 = sp.csr_matrix((np.concatenate([v, diag]), (np.concatenate([r, np.arange(n)]),
+                                                   np.concatenate([c, np.arange(n)]))),
+                       shape=(n, n))
+    A0.sort_indices()
+    out.A0 = A0
+    out.T_D = sysm.T_D * sc
+    src = sysm.q - sysm.q_dirichlet
+    out.q_dirichlet = sysm.q_dirichlet * sc
+    out.q = src + out.q_dirichlet
+    out.A = (A0 + sp.diags(out.T_D)).tocsr()
+    out.A.sort_indices()
+    dc, dT, dp, dfid = sysm.dirichlet
+    out.dirichlet = (dc, dT * sc[dc], dp, dfid)
+    out.Tmf = sysm.Tmf * (2.0 * sc[sysm.geom.nnc_m] * sc[sysm.n_matrix + sysm.geom.nnc_f]
+                          / (sc[sysm.geom.nnc_m] + sc[sysm.n_matrix + sysm.geom.nnc_f]))
+    out.scale = sc
+    return out

@@ -217,6 +217,15 @@ def connections(sysm, prob):
     ci = np.concatenate([o[0] for o in out]).astype(np.int64)
     cj = np.concatenate([o[1] for o in out]).astype(np.int64)
     cT = np.concatenate([o[2] for o in out]).astype(np.float64)
+    sc = getattr(sysm, "scale", None)
+    if sc is not None:
+        # a time-step update scaled every connection by the harmonic mean of
+        # its cells' mobility scales (Tmf is stored scaled already)
+        nmf = len(sysm.Tmf)
+        nmat = len(cT) - nmf - len(g.ff_T)
+        hm = 2.0 * sc[ci] * sc[cj] / (sc[ci] + sc[cj])
+        cT[:nmat] *= hm[:nmat]
+        cT[nmat + nmf:] *= hm[nmat + nmf:]
     return ci, cj, cT
 
 

@@ -207,3 +207,41 @@ def test_gmres_converges_to_the_direct_solution_with_restarts(restart):
     assert np.linalg.norm(r.p - x) / np.linalg.norm(x) < 1e-6
     rich = oracle.run(_small(variant=2))
     assert r.iters < rich.iters
+
+
+# --- time-step update: mobility scales on the transmissibilities, P reused ---
+
+def test_mobility_update_pins():
+    p = _small(variant=1)
+    g, sysm, c, P, st = oracle.build(p)
+    n = sysm.n
+    # scale 1: the same system
+    u1 = assemble.update_mobility(sysm, np.ones(n))
+    assert abs(u1.A - sysm.A).max() <= 1e-12 * abs(sysm.A).max()
+    # a uniform scale c: A and the Dirichlet terms scale by c, the solution is
+    # unchanged (no sources)
+    uc = assemble.update_mobility(sysm, np.full(n, 3.0))
+    assert abs(uc.A - 3.0 * sysm.A).max() <= 1e-12 * abs(sysm.A).max()
+    x0 = spla.spsolve(sysm.A.tocsc(), sysm.q)
+    x3 = spla.spsolve(uc.A.tocsc(), uc.q)
+    assert np.linalg.norm(x3 - x0) <= 1e-10 * np.linalg.norm(x0)
+    # a random scale: symmetric, zero row sums of A0, and one connection by hand
+    sc = np.random.default_rng(2).uniform(0.5, 2.0, n)
+    ur = assemble.update_mobility(sysm, sc)
+    assert abs(ur.A - ur.A.T).max() <= 1e-14 * abs(ur.A).max()
+    assert np.abs(np.asarray(ur.A0.sum(axis=1)).ravel()).max() <= 1e-12 * abs(ur.A0).max()
+    i, j = 5, 6                                   # x-neighbours in the first row
+    hm = 2 * sc[i] * sc[j] / (sc[i] + sc[j])
+    assert abs(ur.A[i, j] - sysm.A[i, j] * hm) <= 1e-14 * abs(sysm.A[i, j])
+    # the updated system with the old P: converges to its own direct solution,
+    # and its flux field stays conservative
+    su = solver.setup(ur, P, c.primal, c.n_coarse, solver.R_FE)
+    x, it, rr, ok, _ = solver.gmres_solve(su, tol=1e-10, max_iter=200)
+    xd = spla.spsolve(ur.A.tocsc(), ur.q)
+    assert ok and np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+    sfv = solver.setup(ur, P, c.primal, c.n_coarse, solver.R_FV)
+    flux, dflux, _, _ = solver.reconstruct_flux(ur, p, sfv, x, c.primal, c.node_cell)
+    bal = solver.cell_balance(ur, p, flux, dflux)
+    # each cell sums a few fluxes T (p_i - p_j) of up to max T |p| in size
+    bound = 64 * np.finfo(float).eps * abs(ur.A).max() * np.abs(x).max()
+    assert np.abs(bal).max() <= bound
