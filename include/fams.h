@@ -149,6 +149,19 @@ int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_sta
 int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
                      fams_stats* st);
 
+/* fams_update - time-step update of instance 0: every connection's
+   transmissibility (matrix faces, matrix-fracture and fracture-fracture) is
+   the setup-time value times the harmonic mean 2 s_i s_j / (s_i + s_j) of its
+   two cells' mobility scales, a Dirichlet half-cell's the setup-time value
+   times its cell's scale.  The coarse grids and P (Sec. 3.1) are kept; R A P
+   and its factors, the ILU(0) smoother and the fluxes' transmissibilities
+   follow.  mobility_scale: n_matrix + n_frac positive values, relative to
+   the setup (nullable: all 1, i.e. back to the setup values); host or
+   device. */
+int fams_update(fams_ctx* ctx, const double* mobility_scale);
+/* the same for every instance of a batch context (scale[i] nullable) */
+int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);
+
 /* Limits of fams_solve_static (its fixed work array, about 13 MB per GPU). */
 #define FAMS_STATIC_MAX_ROWS 262144   /* n_matrix + n_frac of the instance */
 #define FAMS_STATIC_MAX_COARSE 16384  /* n_coarse of the instance */

@@ -439,6 +439,17 @@ int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, f
   return solve_static(ctx->b, rhs, x, tol, st);
 }
 
+int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale) {
+  if (!ctx) { set_error("null argument"); return FAMS_EINVAL; }
+  return phase_update(ctx->b, mobility_scale);
+}
+
+int fams_update(fams_ctx* ctx, const double* mobility_scale) {
+  if (!ctx || ctx->b.B != 1) { set_error("fams_update needs a single-instance context"); return FAMS_EINVAL; }
+  const double* s[1] = {mobility_scale};
+  return phase_update(ctx->b, s);
+}
+
 int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, double* nnc_flux) {
   if (!ctx || !x || !face_flux || !nnc_flux || inst < 0 || inst >= ctx->b.B) {
     set_error("null argument or bad instance");

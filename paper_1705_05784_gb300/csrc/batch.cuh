@@ -25,6 +25,7 @@ struct CoarseSys {
 
 struct CoarseHost {
   std::vector<long long> ac_off, band_off;
+  long long band_tot = 0;
   std::vector<int> kl, ku;
   std::vector<int> bad;         // host copy of CoarseSys::bad
 };
@@ -89,6 +90,14 @@ struct Batch {
   int* diag = nullptr;         // position of the diagonal in each row
   double* TD = nullptr;        // Dirichlet half transmissibility per row
   double* qD = nullptr;        // Dirichlet part of q
+  // time-step update: mobility scale per row and the setup-time values it
+  // scales (allocated by the first update)
+  double* mob = nullptr;
+  double* val0 = nullptr;
+  double* TD0 = nullptr;
+  double* qD0 = nullptr;
+  double* nnc_T0 = nullptr;
+  double* ff_T0 = nullptr;
   // ---- coarse grids ----
   int* rank = nullptr;         // per row
   int* primal = nullptr;       // per row: instance-local coarse index
@@ -159,7 +168,8 @@ struct Batch {
   float* krylov32 = nullptr;
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
-  bool fv_ready = false;
+  bool fv_ready = false;       // R^FV coarse system current
+  bool fv_built = false;       // ... and allocated (a time-step update only refactors it)
   double setup_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per setup phase, wall time
   // flux reconstruction buffers (allocated on first use): iterates and outputs
   double* fx = nullptr;
@@ -210,7 +220,10 @@ int phase_system(Batch& b);       // system.cu: CSR of A, q_D
 int phase_coarse(Batch& b);       // coarse.cu: matrix blocks, networks, BFS, ranks
 int phase_basis(Batch& b);        // basis.cu: P
 int phase_coarse_op(Batch& b, int restriction);  // coarseop.cu: R A P, band LU
-int build_coarse_system(Batch& b, CoarseSys& cs, int restriction, CoarseHost& ch);
+int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse);
+int phase_update(Batch& b, const double* const* scale);   // system.cu
+int ilu_refactor(Batch& b);                               // ilu.cu
+int refresh_mixed(Batch& b);                              // solve.cu
 int phase_ilu(Batch& b);          // ilu.cu
 int phase_alloc_work(Batch& b);   // solve.cu
 int run_solve(Batch& b, double tol, float* ms);   // solve.cu

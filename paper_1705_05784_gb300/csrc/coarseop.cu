@@ -426,71 +426,84 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
 }  // namespace
 
 // mode < 0: each instance's own restriction; 0: R^FV for all; 1: R^FE for all
-int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
+// reuse: the system was built before and the fine operator kept its pattern
+// (a time-step update): A_c is summed again and refactored with the same
+// ordering, bandwidths and band layout
+int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse) {
   const int T = 256;
   cudaStream_t st = b.stream;
   long long nct = b.tot_nc;
   int B = b.B;
-  // dense A_c per instance
-  ch.ac_off.assign(B, 0);
   long long tot = 0;
-  for (int i = 0; i < B; ++i) {
-    ch.ac_off[i] = tot;
-    tot += (long long)b.h[i].nc * b.h[i].nc;
+  for (int i = 0; i < B; ++i) tot += (long long)b.h[i].nc * b.h[i].nc;
+  if (!reuse) {
+    // dense A_c per instance
+    ch.ac_off.assign(B, 0);
+    long long o = 0;
+    for (int i = 0; i < B; ++i) {
+      ch.ac_off[i] = o;
+      o += (long long)b.h[i].nc * b.h[i].nc;
+    }
+    FAMS_TRY(b.alloc((void**)&cs.Ac, sizeof(double) * (tot + 1)));
+    FAMS_TRY(b.alloc((void**)&cs.ac_off, sizeof(long long) * B));
+    FAMS_TRY(b.alloc((void**)&cs.kl, sizeof(int) * B));
+    FAMS_TRY(b.alloc((void**)&cs.ku, sizeof(int) * B));
+    FAMS_TRY(b.alloc((void**)&cs.band_off, sizeof(long long) * B));
+    FAMS_TRY(b.alloc((void**)&cs.ipiv, sizeof(int) * (nct + 1)));
+    FAMS_TRY(b.alloc((void**)&cs.perm, sizeof(int) * (nct + 1)));
+    FAMS_TRY(b.alloc((void**)&cs.bad, sizeof(int) * B));
+    FAMS_CUDA(cudaMemcpyAsync(cs.ac_off, ch.ac_off.data(), sizeof(long long) * B,
+                              cudaMemcpyHostToDevice, st));
   }
-  FAMS_TRY(b.alloc((void**)&cs.Ac, sizeof(double) * (tot + 1)));
-  FAMS_TRY(b.alloc((void**)&cs.ac_off, sizeof(long long) * B));
-  FAMS_TRY(b.alloc((void**)&cs.kl, sizeof(int) * B));
-  FAMS_TRY(b.alloc((void**)&cs.ku, sizeof(int) * B));
-  FAMS_TRY(b.alloc((void**)&cs.band_off, sizeof(long long) * B));
-  FAMS_TRY(b.alloc((void**)&cs.ipiv, sizeof(int) * (nct + 1)));
-  FAMS_TRY(b.alloc((void**)&cs.perm, sizeof(int) * (nct + 1)));
-  FAMS_TRY(b.alloc((void**)&cs.bad, sizeof(int) * B));
-  FAMS_CUDA(cudaMemcpyAsync(cs.ac_off, ch.ac_off.data(), sizeof(long long) * B,
-                            cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (tot + 1), st));
   if (b.tot_nnz > 0)
     fams::note_launch(), k_rap<<<grid_for(b.tot_nnz, T), T, 0, st>>>(b.d_inst, B, b.off_row, b.tot_nnz, b.rowptr, b.col,
                                                 b.val, b.tot_row, b.primal, b.p_ptr, b.p_col,
                                                 b.p_val, cs, mode);
-  // pattern, RCM, band sizes
-  int *cnt = nullptr, *ptr = nullptr, *cols = nullptr, *vis = nullptr, *que = nullptr;
-  FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nct + 1)));
-  FAMS_TRY(b.scratch((void**)&ptr, sizeof(int) * (nct + 1)));
-  FAMS_TRY(b.scratch((void**)&vis, sizeof(int) * (nct + 1)));
-  FAMS_TRY(b.scratch((void**)&que, sizeof(int) * (nct + 1)));
-  fams::note_launch(), k_ac_count<<<grid_for(nct * 32, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, cnt);
-  long long nnzc = 0;
-  FAMS_TRY(exclusive_scan(b, cnt, ptr, nct, &nnzc));
-  FAMS_TRY(b.scratch((void**)&cols, sizeof(int) * (nnzc + 1)));
-  fams::note_launch(), k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
-  int *dkl = nullptr, *dku = nullptr, *ip = nullptr;
-  FAMS_TRY(b.scratch((void**)&dkl, sizeof(int) * B));
-  FAMS_TRY(b.scratch((void**)&dku, sizeof(int) * B));
+  int* ip = nullptr;
   FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
-  FAMS_CUDA(cudaMemsetAsync(dkl, 0, sizeof(int) * B, st));
-  FAMS_CUDA(cudaMemsetAsync(dku, 0, sizeof(int) * B, st));
-  fams::note_launch(), k_rcm<<<B, 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, b.d_err);
-  fams::note_launch(), k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
-  fams::note_launch(), k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
-  FAMS_CUDA(cudaGetLastError());
-  ch.kl.assign(B, 0);
-  ch.ku.assign(B, 0);
-  FAMS_CUDA(cudaMemcpyAsync(ch.kl.data(), dkl, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
-  FAMS_CUDA(cudaMemcpyAsync(ch.ku.data(), dku, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
-  FAMS_CUDA(cudaStreamSynchronize(st));
-  ch.band_off.assign(B, 0);
-  long long btot = 0;
-  for (int i = 0; i < B; ++i) {
-    ch.band_off[i] = btot;
-    btot += (long long)(2 * ch.kl[i] + ch.ku[i] + 1) * b.h[i].nc;
+  if (!reuse) {
+    // pattern, RCM, band sizes
+    int *cnt = nullptr, *ptr = nullptr, *cols = nullptr, *vis = nullptr, *que = nullptr;
+    FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nct + 1)));
+    FAMS_TRY(b.scratch((void**)&ptr, sizeof(int) * (nct + 1)));
+    FAMS_TRY(b.scratch((void**)&vis, sizeof(int) * (nct + 1)));
+    FAMS_TRY(b.scratch((void**)&que, sizeof(int) * (nct + 1)));
+    fams::note_launch(), k_ac_count<<<grid_for(nct * 32, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, cnt);
+    long long nnzc = 0;
+    FAMS_TRY(exclusive_scan(b, cnt, ptr, nct, &nnzc));
+    FAMS_TRY(b.scratch((void**)&cols, sizeof(int) * (nnzc + 1)));
+    fams::note_launch(), k_ac_cols<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ptr, cols);
+    int *dkl = nullptr, *dku = nullptr;
+    FAMS_TRY(b.scratch((void**)&dkl, sizeof(int) * B));
+    FAMS_TRY(b.scratch((void**)&dku, sizeof(int) * B));
+    FAMS_CUDA(cudaMemsetAsync(dkl, 0, sizeof(int) * B, st));
+    FAMS_CUDA(cudaMemsetAsync(dku, 0, sizeof(int) * B, st));
+    fams::note_launch(), k_rcm<<<B, 32, 0, st>>>(b.d_inst, B, ptr, cols, cs, vis, que, b.d_err);
+    fams::note_launch(), k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
+    fams::note_launch(), k_bandwidth<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip, dkl, dku);
+    FAMS_CUDA(cudaGetLastError());
+    ch.kl.assign(B, 0);
+    ch.ku.assign(B, 0);
+    FAMS_CUDA(cudaMemcpyAsync(ch.kl.data(), dkl, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaMemcpyAsync(ch.ku.data(), dku, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    ch.band_off.assign(B, 0);
+    long long bt = 0;
+    for (int i = 0; i < B; ++i) {
+      ch.band_off[i] = bt;
+      bt += (long long)(2 * ch.kl[i] + ch.ku[i] + 1) * b.h[i].nc;
+    }
+    ch.band_tot = bt;
+    FAMS_TRY(b.alloc((void**)&cs.band, sizeof(double) * (bt + 1)));
+    FAMS_CUDA(cudaMemcpyAsync(cs.kl, ch.kl.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
+                              cudaMemcpyHostToDevice, st));
+  } else {
+    fams::note_launch(), k_inverse_perm<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip);
   }
-  FAMS_TRY(b.alloc((void**)&cs.band, sizeof(double) * (btot + 1)));
-  FAMS_CUDA(cudaMemsetAsync(cs.band, 0, sizeof(double) * (btot + 1), st));
-  FAMS_CUDA(cudaMemcpyAsync(cs.kl, ch.kl.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-  FAMS_CUDA(cudaMemcpyAsync(cs.ku, ch.ku.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-  FAMS_CUDA(cudaMemcpyAsync(cs.band_off, ch.band_off.data(), sizeof(long long) * B,
-                            cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemsetAsync(cs.band, 0, sizeof(double) * (ch.band_tot + 1), st));
   fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip,
                                                                    nullptr);
   // factorisation: LDL^T for the symmetric positive definite (R^FE) systems
@@ -622,7 +635,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch) {
 }
 
 int phase_coarse_op(Batch& b, int mode) {
-  return build_coarse_system(b, b.cs[0], mode, b.csh[0]);
+  return build_coarse_system(b, b.cs[0], mode, b.csh[0], false);
 }
 
 }  // namespace fams

@@ -197,9 +197,11 @@ __device__ inline long long faces_of(const Inst& I) {
 
 // steps 2 and 4 on the matrix faces of every listed instance: x faces
 // ((nx+1) ny nz, x fastest), then y faces, then z faces; positive along +axis
+// mob (nullable): mobility scales of a time-step update, applied as the
+// harmonic mean of the two cells' scales (a Dirichlet face: the cell's)
 __global__ void k_flux_faces(const Inst* inst, const int* list, int nlist, const long long* foff,
-                             long long ftot, const double* perm, const int* primal,
-                             const double* pp, const double* pt, double* face) {
+                             long long ftot, const double* perm, const double* mob,
+                             const int* primal, const double* pp, const double* pt, double* face) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ftot) return;
   int li = 0, hi = nlist - 1;
@@ -230,12 +232,17 @@ __global__ void k_flux_faces(const Inst* inst, const int* list, int nlist, const
     if ((I.bc_mask >> fid) & 1) {
       long long cell = (c_ax == 0) ? hi_cell : hi_cell - stride;
       double TDf = 2.0 * k[cell] * area / h;
+      if (mob) TDf *= mob[ro + cell];
       double pc = pt[ro + cell];
       out = (c_ax == 0) ? TDf * (I.bc_val[fid] - pc) : TDf * (pc - I.bc_val[fid]);
     }
   } else {
     long long lo_cell = hi_cell - stride;
     double T = area / (h / (2.0 * k[lo_cell]) + h / (2.0 * k[hi_cell]));
+    if (mob) {
+      double a = mob[ro + lo_cell], c = mob[ro + hi_cell];
+      T *= 2.0 * a * c / (a + c);
+    }
     bool same = primal[ro + lo_cell] == primal[ro + hi_cell];
     const double* p = same ? pt : pp;
     out = T * (p[ro + lo_cell] - p[ro + hi_cell]);
@@ -281,8 +288,10 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
     return FAMS_OK;
   }
   if (!b.fv_ready) {
-    FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1]));
+    // built once; a time-step update (fv_built, !fv_ready) refactors it in place
+    FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1], b.fv_built));
     b.fv_ready = true;
+    b.fv_built = true;
     b.free_tmp();
   }
   *ch = &b.csh[1];
@@ -386,7 +395,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_CUDA(cudaMemcpyAsync(dno, noff.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, st));
   if (foff[nl] > 0)
     fams::note_launch(), k_flux_faces<<<grid_for(foff[nl], 256), 256, 0, st>>>(
-        b.d_inst, dlist, nl, dfo, foff[nl], b.perm, b.primal, pp, pt, face);
+        b.d_inst, dlist, nl, dfo, foff[nl], b.perm, b.mob, b.primal, pp, pt, face);
   if (noff[nl] > 0)
     fams::note_launch(), k_flux_nnc<<<grid_for(noff[nl], 256), 256, 0, st>>>(
         b.d_inst, dlist, nl, dno, noff[nl], b.nnc_row_m, b.nnc_row_f, b.nnc_T, b.ff_a, b.ff_b,

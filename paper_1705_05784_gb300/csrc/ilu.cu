@@ -185,4 +185,23 @@ int phase_ilu(Batch& b) {
   return FAMS_OK;
 }
 
+// new values, same pattern and levels (a time-step update)
+int ilu_refactor(Batch& b) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  long long nrow = b.tot_row;
+  FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
+  fams::note_launch(), k_ilu_factor<<<b.B, 512, 0, st>>>(b.d_inst, b.B, b.rowptr, b.col, b.diag,
+                                                          b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
+                                                          b.d_err);
+  FAMS_CUDA(cudaGetLastError());
+  FAMS_TRY(b.check_err("ILU(0)"));
+  if (nrow > 0)
+    fams::note_launch(), k_pack<<<grid_for(nrow, T), T, 0, st>>>(
+        nrow, b.lev_rows, b.rowptr, b.col, b.diag, b.ilu, b.pk_pos, b.pk_nl, b.pk_lp, b.pk_lc,
+        b.pk_lv, b.pk_nu, b.pk_uc, b.pk_uv, b.pk_ud);
+  FAMS_CUDA(cudaGetLastError());
+  return FAMS_OK;
+}
+
 }  // namespace fams

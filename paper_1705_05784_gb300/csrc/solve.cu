@@ -918,6 +918,22 @@ int phase_alloc_work(Batch& b) {
   return FAMS_OK;
 }
 
+// FP32 copies of the operators after their FP64 values changed
+int refresh_mixed(Batch& b) {
+  if (!b.val32) return FAMS_OK;
+  const long long n1 = b.tot_row + 1, nnz = b.tot_nnz;
+  auto round = [&](const double* src, float* dst, long long cnt) {
+    if (cnt > 0) fams::note_launch(), k_round<<<grid_for(cnt, 256), 256, 0, b.stream>>>(cnt, src, dst);
+  };
+  round(b.val, b.val32, nnz);
+  round(b.ilu, b.ilu32, nnz);
+  round(b.pk_lv, b.pk_lv32, PK * n1);
+  round(b.pk_uv, b.pk_uv32, PK * n1);
+  round(b.pk_ud, b.pk_ud32, n1);
+  FAMS_CUDA(cudaGetLastError());
+  return FAMS_OK;
+}
+
 int make_q(Batch& b, const double* rhs_dev) {
   long long n = b.tot_row;
   fams::note_launch(), k_make_q<<<grid_for(n, 256), 256, 0, b.stream>>>(n, rhs_dev, b.qD, b.q);

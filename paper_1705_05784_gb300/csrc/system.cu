@@ -140,7 +140,91 @@ __global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long lon
   qD[r] = qd;
 }
 
+// time-step update (the harmonic mean of the two cells' mobility scales on
+// every connection, the cell's scale on a Dirichlet half-cell): the rows of A
+// and their Dirichlet terms, with q keeping its sources
+__device__ inline double hmean(double a, double b) { return 2.0 * a * b / (a + b); }
+
+__global__ void k_update_rows(long long nrow, const int* rowptr, const int* col, const int* diag,
+                              const double* val0, const double* TD0, const double* qD0,
+                              const double* mob, double* val, double* TD, double* qD, double* q) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const double sr = mob[r];
+  double dsum = 0.0;
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+    int c = col[p];
+    if (c == r) continue;
+    double v = val0[p] * hmean(sr, mob[c]);
+    val[p] = v;
+    dsum -= v;
+  }
+  const double td = TD0[r] * sr, qd = qD0[r] * sr;
+  val[diag[r]] = dsum + td;
+  q[r] += qd - qD[r];
+  TD[r] = td;
+  qD[r] = qd;
+}
+
+__global__ void k_update_conn(long long nnc, const int* row_m, const int* row_f, const double* T0,
+                              long long nff, const int* fa, const int* fb, const double* F0,
+                              const double* mob, double* T, double* FT) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnc) T[k] = T0[k] * hmean(mob[row_m[k]], mob[row_f[k]]);
+  else if (k < nnc + nff) {
+    long long e = k - nnc;
+    FT[e] = F0[e] * hmean(mob[fa[e]], mob[fb[e]]);
+  }
+}
+
+__global__ void k_fill(long long n, double v, double* x) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
 }  // namespace
+
+// scale[i]: n_matrix + n_frac mobility scales of instance i relative to the
+// setup-time values (null: 1 everywhere, i.e. back to them)
+int phase_update(Batch& b, const double* const* scale) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  const long long n = b.tot_row, nnz = b.tot_nnz, nnc = b.tot_nnc, nff = b.tot_ff;
+  auto keep = [&](double** dst, const double* src, long long cnt) -> int {
+    FAMS_TRY(b.alloc((void**)dst, sizeof(double) * (cnt + 1)));
+    if (cnt > 0) FAMS_CUDA(cudaMemcpyAsync(*dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+    return FAMS_OK;
+  };
+  if (!b.mob) {
+    FAMS_TRY(b.alloc((void**)&b.mob, sizeof(double) * (n + 1)));
+    FAMS_TRY(keep(&b.val0, b.val, nnz));
+    FAMS_TRY(keep(&b.TD0, b.TD, n));
+    FAMS_TRY(keep(&b.qD0, b.qD, n));
+    FAMS_TRY(keep(&b.nnc_T0, b.nnc_T, nnc));
+    FAMS_TRY(keep(&b.ff_T0, b.ff_T, nff));
+  }
+  if (n > 0) fams::note_launch(), k_fill<<<grid_for(n, T), T, 0, st>>>(n, 1.0, b.mob);
+  for (int i = 0; i < b.B; ++i)
+    if (scale && scale[i])
+      FAMS_CUDA(cudaMemcpyAsync(b.mob + b.h[i].row_off, scale[i], sizeof(double) * b.h[i].n,
+                                cudaMemcpyDefault, st));
+  if (n > 0)
+    fams::note_launch(), k_update_rows<<<grid_for(n, T), T, 0, st>>>(
+        n, b.rowptr, b.col, b.diag, b.val0, b.TD0, b.qD0, b.mob, b.val, b.TD, b.qD, b.q);
+  if (nnc + nff > 0)
+    fams::note_launch(), k_update_conn<<<grid_for(nnc + nff, T), T, 0, st>>>(
+        nnc, b.nnc_row_m, b.nnc_row_f, b.nnc_T0, nff, b.ff_a, b.ff_b, b.ff_T0, b.mob, b.nnc_T,
+        b.ff_T);
+  FAMS_CUDA(cudaGetLastError());
+  // P stays; R A P, its factors, ILU(0) and the FP32 copies follow A
+  FAMS_TRY(build_coarse_system(b, b.cs[0], -1, b.csh[0], true));
+  b.fv_ready = false;
+  FAMS_TRY(ilu_refactor(b));
+  FAMS_TRY(refresh_mixed(b));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  b.free_tmp();
+  return b.check_err("time-step update");
+}
 
 int phase_system(Batch& b) {
   const int T = 256;

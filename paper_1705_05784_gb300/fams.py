@@ -79,6 +79,8 @@ def _load():
     lib.fams_solve_static.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       P(fams_stats)]
     lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fams_update.argtypes = [C.c_void_p, C.c_void_p]
+    lib.fams_update_batch.argtypes = [C.c_void_p, P(C.c_void_p)]
     lib.fams_flux_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p),
                                     P(C.c_int)]
     lib.fams_query.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong]
@@ -222,6 +224,15 @@ class Context:
                       converged=bool(st[i].converged), solve_ms=st[i].solve_ms, status=s)
                  for i in range(n)]
         return xs, stats
+
+    def update(self, scales):
+        """fams_update_batch: scales is a list per instance (None: all 1) or
+        one array for a single instance."""
+        if not isinstance(scales, (list, tuple)):
+            scales = [scales]
+        arrs = [None if sc is None else np.ascontiguousarray(sc, np.float64) for sc in scales]
+        ptrs = (C.c_void_p * self.n)(*[0 if a is None else a.ctypes.data for a in arrs])
+        _check(lib.fams_update_batch(self.h, ptrs))
 
     def solve_device(self, rhs_ptrs, x_ptrs, tol):
         """The same call with caller-owned buffers given as raw pointers (host

@@ -427,3 +427,50 @@ def test_rejects_bad_input():
     with pytest.raises(fams.FamsError) as e:
         fams.Context(p)
     assert e.value.status == fams.EINVAL
+
+
+# --- time-step update (fams_update): mobility scales, P reused ---
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3dcross"])
+def test_time_step_update_matches_oracle(name, restriction):
+    """After fams_update the fine system, the coarse operator, ILU(0), a
+    GMRES trajectory and the conservative fluxes equal the oracle's for the
+    scaled system with the setup-time P; a second update replaces the first
+    (scales are relative to the setup), and no scale restores the setup."""
+    from oracle import assemble as oasm
+    fams = _fams()
+    p = _gmres(_case(name, 0, restriction), 8, 13)
+    g, sysm, c, P, st0 = oracle.build(p)
+    n = sysm.n
+    with fams.Context(p) as ctx:
+        for seed in (3, 4):
+            sc = np.random.default_rng(seed).uniform(0.25, 4.0, n)
+            ur = oasm.update_mobility(sysm, sc)
+            su = osolver.setup(ur, P, c.primal, c.n_coarse, p.restriction)
+            ctx.update(sc)
+            np.testing.assert_allclose(ctx.query("A_VAL"), ur.A.data, rtol=1e-13,
+                                       atol=1e-15 * abs(ur.A).max())
+            Ac = ctx.query("AC").reshape(c.n_coarse, c.n_coarse)
+            np.testing.assert_allclose(Ac, su.Ac, rtol=0, atol=1e-11 * np.abs(su.Ac).max())
+            F = ctx.query("ILU_VAL")
+            np.testing.assert_allclose(F, su.F.data, rtol=1e-11, atol=1e-13 * np.abs(su.F.data).max())
+            xo, ito, _, _, _ = osolver.gmres_solve(su, tol=0.0, max_iter=13, restart=8)
+            xs, stats = ctx.solve(tol=0.0)
+            assert stats[0]["iterations"] == 13 == ito
+            assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+            face, nnc = ctx.flux(xs[0])
+            sfv = osolver.setup(ur, P, c.primal, c.n_coarse, osolver.R_FV)
+            flux, dflux, _, _ = osolver.reconstruct_flux(ur, p, sfv, xs[0], c.primal, c.node_cell)
+            nz = p.nz if p.dim == 3 else 1
+            nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
+            fx = face[:nfx].reshape(nz, p.ny, p.nx + 1)
+            fy = face[nfx:nfx + nfy].reshape(nz, p.ny + 1, p.nx)
+            parts = [fx[:, :, 1:-1].ravel(), fy[:, 1:-1, :].ravel()]
+            if p.dim == 3:
+                parts.append(face[nfx + nfy:].reshape(nz + 1, p.ny, p.nx)[1:-1].ravel())
+            conn = np.concatenate(parts + [nnc])
+            np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
+        ctx.update(None)
+        np.testing.assert_allclose(ctx.query("A_VAL"), sysm.A.data, rtol=1e-13,
+                                   atol=1e-15 * abs(sysm.A).max())
