@@ -49,6 +49,7 @@ def problems(batch, seed0, max_iter=400, krylov=1, restart=30, precision=0):
                                  basis=i % 4, restriction=1, alpha=1e-2)
         p.max_iter = max_iter
         p.krylov, p.restart, p.precision = krylov, restart, precision
+        p.prepare_flux = 1   # every step reconstructs the fluxes of every instance
         out.append(p)
     return out
 

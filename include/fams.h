@@ -92,7 +92,8 @@ typedef struct {
    step as the right preconditioner of GMRES(restart), the paper's benchmark
    mode (Sec. 4.5, 4.6): every iteration is one preconditioner application,
    and a cycle ends when the least-squares residual estimate reaches tol, after
-   `restart` iterations, or at max_iter; the true residual then decides. */
+   `restart` iterations, or at max_iter; the true residual then decides.
+   Zero-initialise the struct: fields added later default to 0. */
 typedef struct {
   int coarsen[3];
   int frac_dmin;
@@ -104,6 +105,12 @@ typedef struct {
   int precision;
   int krylov;    /* FAMS_KRYLOV_NONE: the Table 1 loop; FAMS_KRYLOV_GMRES: GMRES(restart) */
   int restart;   /* GMRES cycle length, 1..FAMS_MAX_RESTART (ignored otherwise) */
+  int prepare_flux;  /* 1: the caller will reconstruct fluxes (fams_flux*).  The
+                        R^FV coarse system of the reconstruction (Sec. 3.2) is then
+                        built on a second stream while the first solve runs,
+                        filling the SMs that early-converging instances leave
+                        idle; 0: built on the first fams_flux* call.  Results are
+                        the same either way. */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */
@@ -140,7 +147,8 @@ int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n
 /* fams_solve - Table 1 (steps 3, 5-8) on instance 0 of ctx from the initial
    guess in x until ||q - A x||_2 <= tol ||q||_2, q = rhs + Dirichlet terms.
    rhs: n_matrix + n_frac sources (nullable = 0); x: in initial guess, out
-   pressure.  FAMS_ENOCONV leaves the last iterate in x. */
+   pressure.  FAMS_ENOCONV leaves the last iterate in x; FAMS_EBREAKDOWN
+   reports a numerically singular coarse system (the test of fams_flux_batch). */
 int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st);
 
 /* fams_solve_batch - the same for every instance of a batch context; rhs[i]
@@ -209,8 +217,11 @@ int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, doubl
    device).  status (nullable, n_instances entries) receives each instance's
    result; an instance whose finite-volume coarse system R^FV A P is
    numerically singular gets FAMS_EBREAKDOWN and its buffers are left
-   untouched while the others are reconstructed.  Returns FAMS_EBREAKDOWN if
-   any instance failed that way. */
+   untouched while the others are reconstructed.  Numerically singular: a
+   pivot of its band LU is at most 1e-13 times the largest entry of its row as
+   assembled (e.g. a coarse node whose truncated basis function is its own
+   cell inside its own primal block: its R^FV column sums to zero).  Returns
+   FAMS_EBREAKDOWN if any instance failed that way. */
 int fams_flux_batch(fams_ctx* ctx, const double* const* x, double* const* face_flux,
                     double* const* nnc_flux, int* status);
 

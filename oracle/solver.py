@@ -13,6 +13,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/geometry.py).
     r = q - A p;  dp1 = P (R A P)^-1 R r;  r1 = r - A dp1;
     dp2 = (LU)^-1 r1;  p = p + dp1 + dp2
   iterated until ||q - A p||_2 <= tol ||q||_2 (q including Dirichlet terms).
+* numerically singular coarse system (a reading; the paper is silent):
+  Gaussian elimination with partial pivoting meets a pivot at most SING_EPS
+  times the largest entry of its row as assembled (`singular_step`).
 * flux reconstruction: one FV multiscale stage from x gives p', fluxes across
   primal-block boundaries are T (p'_i - p'_j), and every primal block then
   solves its own TPFA problem with those fluxes as Neumann data (pinned at its
@@ -83,6 +86,34 @@ def ilu0_apply(F, r):
 
 class Setup:
     pass
+
+
+# a pivot at most this fraction of the largest entry of its row (as assembled)
+# is numerically zero
+SING_EPS = 1e-13
+
+
+def singular_step(M):
+    """First step at which Gaussian elimination with partial pivoting on M
+    meets a numerically zero pivot, |u_kk| <= SING_EPS max_j |m_ij| for the
+    original row i that became pivot row k; -1 if none.  Invariant under row
+    scaling.  An exactly zero column is the extreme case: a coarse node whose
+    truncated basis function is its own cell, inside its own primal block, has
+    an R^FV column R^FV A e_node that sums A's column over the block, i.e. to
+    zero."""
+    U = np.array(M, dtype=np.float64, copy=True)
+    n = U.shape[0]
+    scale = np.abs(U).max(axis=1) if n else np.zeros(0)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(U[k:, k])))
+        if p != k:
+            U[[k, p]] = U[[p, k]]
+            scale[[k, p]] = scale[[p, k]]
+        if not abs(U[k, k]) > SING_EPS * scale[k]:
+            return k
+        lk = U[k + 1:, k] / U[k, k]
+        U[k + 1:, k:] -= np.outer(lk, U[k, k:])
+    return -1
 
 
 def setup(sysm, P, primal, n_coarse, kind):

@@ -91,6 +91,7 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
     return bad("krylov must be FAMS_KRYLOV_NONE or FAMS_KRYLOV_GMRES");
   if (o.krylov == FAMS_KRYLOV_GMRES && (o.restart < 1 || o.restart > FAMS_MAX_RESTART))
     return bad("GMRES restart must be in 1..FAMS_MAX_RESTART");
+  if (o.prepare_flux != 0 && o.prepare_flux != 1) return bad("prepare_flux must be 0 or 1");
   return FAMS_OK;
 }
 
@@ -129,6 +130,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.basis = o.basis; I.restriction = o.restriction; I.precision = o.precision;
     I.max_iter = o.max_iter; I.alpha = o.alpha;
     I.krylov = o.krylov; I.restart = o.krylov == FAMS_KRYLOV_GMRES ? o.restart : 0;
+    b.prepare_flux = b.prepare_flux || o.prepare_flux == 1;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;
     I.nfr = nf;
@@ -229,6 +231,10 @@ void destroy_batch(Batch& b) {
   if (b.stream) cudaStreamSynchronize(b.stream);
   if (b.stream) cudaStreamDestroy(b.stream);
   b.stream = nullptr;
+  if (b.side) cudaStreamDestroy(b.side);
+  if (b.side_done) cudaEventDestroy(b.side_done);
+  b.side = nullptr;
+  b.side_done = nullptr;
 }
 
 template <class T>

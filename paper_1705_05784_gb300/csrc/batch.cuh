@@ -33,6 +33,9 @@ struct CoarseHost {
 struct Batch {
   int B = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;        // second stream: the R^FV system built beside a solve
+  cudaEvent_t side_done = nullptr;
+  bool prepare_flux = false;          // some instance asked for it (fams_opts.prepare_flux)
   int device = 0;
   std::vector<Inst> h;          // host copy of the descriptors
   Inst* d_inst = nullptr;       // device copy
@@ -229,6 +232,7 @@ int phase_alloc_work(Batch& b);   // solve.cu
 int run_solve(Batch& b, double tol, float* ms);   // solve.cu
 // flux.cu
 int flux_prepare(Batch& b, const CoarseHost** ch);
+int flux_beside(Batch& b, cudaEvent_t ready);   // flux.cu: flux_prepare on the side stream
 int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* face,
              const std::vector<long long>& foff, double* nnc, const std::vector<long long>& noff);
 

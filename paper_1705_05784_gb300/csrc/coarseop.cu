@@ -217,6 +217,10 @@ __device__ inline int wrap(int x, int k) { return x >= k ? x - k : x; }
 
 constexpr int LU_EXTRA = 32;      // narrow LU ring: columns of fill past the upper band
 constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choice
+// a pivot at most this fraction of the largest entry of its row (as assembled)
+// is numerically zero: the rounding the elimination leaves in that row, a few
+// eps times its scale, is then within three decimal digits of the pivot
+constexpr double SING_EPS = 1e-13;
 
 // Symmetric positive definite coarse systems (R^FE = P^T: A_c = P^T A P):
 // band LDL^T without pivoting, about a quarter of the band LU's work.  The
@@ -297,6 +301,12 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
 // largest entry -- and an instance whose row interchanges would spread fill
 // beyond the ring sets failed[ii] and leaves its band to be refactored with
 // the full ring.
+//
+// The system is numerically singular (cs.bad) when the chosen pivot is at most
+// SING_EPS times the largest entry of its row as assembled (rows keep their
+// scale in `sc` through the interchanges); an exactly zero column is the
+// extreme case.  A coarse node whose truncated basis function is a single
+// cell inside its own primal block has an R^FV column that sums to zero.
 __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* only, int* err,
                               double* gws, long long gstride, int extra, double tau, int* failed) {
   extern __shared__ double dyn[];
@@ -310,6 +320,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   double* S = gws ? gws + (long long)blockIdx.x * gstride : dyn;
   double* lj = gws ? dyn : dyn + (long long)K1 * K2;   // multipliers of column j
   double* ur = lj + K1;                                // pivot row j
+  double* sc = ur + kv + 1;                            // scale of the row in each slot
   double* AB = cs.band + cs.band_off[ii];
   int* ipiv = cs.ipiv + I.nc_off;
   __shared__ double sv[32];
@@ -323,6 +334,13 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   for (int e = threadIdx.x; e < K1 * K2; e += T) {
     int i = e / K2, c = e - i * K2;
     S[e] = INBAND(i, c) ? BEL(i, c) : 0.0;
+  }
+  for (int i = w; i < K1; i += nw) {   // rows 0..kl sit in slots 0..kl
+    double m = 0.0;
+    if (i < n)
+      for (int c = max(0, i - kl) + lane; c <= min(n - 1, i + ku); c += 32) m = fmax(m, fabs(BEL(i, c)));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sc[i] = m;
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -349,11 +367,12 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
       if (fabs(SEL(jr, jc)) >= tau * b0) i0 = 0;   // threshold: keep the diagonal
       s_jp = i0;
       ipiv[j] = j + i0;
-      if (!(b0 > 0.0) || !isfinite(b0)) {
+      const double p0 = SEL(wrap(jr + i0, K1), jc);
+      if (!(b0 > 0.0) || !isfinite(b0) || !(fabs(p0) > SING_EPS * sc[wrap(jr + i0, K1)])) {
         s_bad = 1;
         s_badcol = j;
       } else {
-        s_piv = SEL(wrap(jr + i0, K1), jc);
+        s_piv = p0;
       }
       s_ju = max(s_ju, min(j + ku + i0, n - 1));
       if (s_ju - j + 1 > K2) s_bad = 2;   // fill beyond the ring
@@ -369,6 +388,11 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
         double t = SEL(jr, c);
         SEL(jr, c) = SEL(pr, c);
         SEL(pr, c) = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = sc[jr];
+        sc[jr] = sc[pr];
+        sc[pr] = t;
       }
       __syncthreads();
     }
@@ -408,6 +432,13 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
     for (int cc = 1 + threadIdx.x; cc <= K2; cc += T) {
       int c = j + cc;
       SEL(jr, wrap(jc + cc, K2)) = INBAND(inew, c) ? BEL(inew, c) : 0.0;
+    }
+    if (w == nw - 1) {   // scale of the entering row, still as assembled in the band
+      double m = 0.0;
+      if (inew < n)
+        for (int c = inew - kl + lane; c <= min(n - 1, inew + ku); c += 32) m = fmax(m, fabs(BEL(inew, c)));
+      for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) sc[jr] = m;
     }
     __syncthreads();
   }
@@ -558,8 +589,8 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem));
   size_t temps = 0;
-  for (int i = 0; i < B; ++i)   // multipliers and pivot row of the widest band
-    if (lu[i]) temps = std::max(temps, sizeof(double) * (size_t)(2 * ch.kl[i] + ch.ku[i] + 2));
+  for (int i = 0; i < B; ++i)   // multipliers, pivot row and row scales of the widest band
+    if (lu[i]) temps = std::max(temps, sizeof(double) * (size_t)(3 * ch.kl[i] + ch.ku[i] + 3));
   {
     std::vector<int> lu_n(B, 0);
     size_t act_n = 0;

@@ -298,6 +298,36 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
   return FAMS_OK;
 }
 
+// flux_prepare on the side stream, started while the iteration kernels run on
+// the context's stream: the R^FV system reads only A and P (complete at
+// `ready`, recorded before the iteration), and its one-CTA-per-instance
+// kernels take the SM slots of instances that converge early.  The context's
+// stream then waits for it.  A failure here does not fail the solve: the
+// system stays unbuilt and the reconstruction builds it (and reports the
+// error) on its first call.
+int flux_beside(Batch& b, cudaEvent_t ready) {
+  bool all_fv = true;
+  for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
+  if (all_fv || b.fv_ready) return FAMS_OK;
+  if (!b.side) {
+    FAMS_CUDA(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
+    FAMS_CUDA(cudaEventCreateWithFlags(&b.side_done, cudaEventDisableTiming));
+  }
+  FAMS_CUDA(cudaStreamWaitEvent(b.side, ready, 0));
+  std::vector<void*> keep;
+  keep.swap(b.tmp);   // scratch of the running solve stays out of this build's frees
+  std::swap(b.stream, b.side);
+  const CoarseHost* ch = nullptr;
+  int rc = flux_prepare(b, &ch);
+  b.free_tmp();
+  std::swap(b.stream, b.side);
+  b.tmp.swap(keep);
+  FAMS_CUDA(cudaEventRecord(b.side_done, b.side));
+  FAMS_CUDA(cudaStreamWaitEvent(b.stream, b.side_done, 0));
+  (void)rc;
+  return FAMS_OK;
+}
+
 // Flux of the listed instances.  x: concatenated iterates (global rows);
 // face / nnc: concatenated outputs at foff / noff (per listed instance).
 int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* face,

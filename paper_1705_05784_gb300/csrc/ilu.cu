@@ -27,19 +27,46 @@ __global__ void k_lev_matrix(const Inst* inst, int B, const int* off_row, long l
   level[r] = x + y + z;
 }
 
+constexpr int LEV_WIN = 8192;   // fracture rows whose levels stay in shared memory
+
+// Fracture rows of one instance in order, one warp: lanes take a row's lower
+// entries (matrix levels from the cell index, fracture levels from shared
+// memory for the first LEV_WIN fracture rows), row bounds fetched 32 rows at
+// a time.
 __global__ void k_lev_frac(const Inst* inst, int B, const int* rowptr, const int* col,
                            const int* diag, int* level, int* nlev) {
-  int ii = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ii >= B) return;
-  const Inst& I = inst[ii];
+  __shared__ int win[LEV_WIN];
+  const Inst& I = inst[blockIdx.x];
+  int lane = threadIdx.x;
   int mx = I.nm > 0 ? (I.nx - 1) + (I.ny - 1) + (I.dim == 3 ? I.nz - 1 : 0) : -1;
-  for (int r = I.row_off + I.nm; r < I.row_off + I.n; ++r) {
-    int l = 0;
-    for (int p = rowptr[r]; p < diag[r]; ++p) l = max(l, level[col[p]] + 1);
-    level[r] = l;
-    mx = max(mx, l);
+  int f0 = I.row_off + I.nm, end = I.row_off + I.n;
+  for (int r0 = f0; r0 < end; r0 += 32) {
+    int rr = r0 + lane;
+    int ra = rr < end ? rowptr[rr] : 0, rd = rr < end ? diag[rr] : 0;
+    int nr = min(32, end - r0);
+    for (int j = 0; j < nr; ++j) {
+      int a = __shfl_sync(0xffffffffu, ra, j), d = __shfl_sync(0xffffffffu, rd, j);
+      int l = 0;
+      for (int p = a + lane; p < d; p += 32) {
+        int c = col[p];
+        int loc = c - I.row_off, lc;
+        if (loc < I.nm) {
+          lc = loc % I.nx + (loc / I.nx) % I.ny + loc / (I.nx * I.ny);
+        } else {
+          lc = c - f0 < LEV_WIN ? win[c - f0] : level[c];
+        }
+        l = max(l, lc + 1);
+      }
+      for (int o = 16; o > 0; o >>= 1) l = max(l, __shfl_xor_sync(0xffffffffu, l, o));
+      if (lane == 0) {
+        level[r0 + j] = l;
+        if (r0 + j - f0 < LEV_WIN) win[r0 + j - f0] = l;
+      }
+      __syncwarp();
+      mx = max(mx, l);
+    }
   }
-  nlev[ii] = mx + 1;
+  if (lane == 0) nlev[blockIdx.x] = mx + 1;
 }
 
 __global__ void k_lev_count(const Inst* inst, int B, const int* off_row, long long nrow,
@@ -132,7 +159,7 @@ int phase_ilu(Batch& b) {
   FAMS_TRY(b.scratch((void**)&level, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&dnlev, sizeof(int) * B));
   fams::note_launch(), k_lev_matrix<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, B, b.off_row, nrow, level);
-  fams::note_launch(), k_lev_frac<<<grid_for(B, 32), 32, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, level, dnlev);
+  fams::note_launch(), k_lev_frac<<<B, 32, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, level, dnlev);
   std::vector<int> nlev(B);
   FAMS_CUDA(cudaMemcpyAsync(nlev.data(), dnlev, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   FAMS_CUDA(cudaStreamSynchronize(st));

@@ -112,6 +112,7 @@ void run_batch(fams_server* s, std::vector<Request*>& batch) {
     fracs[i].xy = batch[i]->xy.empty() ? nullptr : batch[i]->xy.data();
     fracs[i].kf = batch[i]->kf.empty() ? nullptr : batch[i]->kf.data();
     opts[i] = batch[i]->opts;
+    opts[i].prepare_flux = s->o.with_flux ? 1 : 0;
     batch[i]->t_start = now_ms();
   }
   fams_ctx* ctx = nullptr;

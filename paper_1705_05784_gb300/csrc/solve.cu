@@ -993,6 +993,7 @@ int run_solve(Batch& b, double tol, float* ms) {
     fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov, b.krylov32);
   FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaEventRecord(e1, b.stream));
+  if (b.prepare_flux) FAMS_TRY(flux_beside(b, e0));
   FAMS_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
   FAMS_CUDA(cudaEventElapsedTime(&t, e0, e1));

@@ -44,17 +44,41 @@ __global__ void k_scan_blocks(const int* in, long long n, long long* block_sums)
   if (threadIdx.x == SCAN_BLOCK - 1) block_sums[blockIdx.x] = s;
 }
 
+// exclusive scan of the nb block sums in place, total at sums[nb]: one CTA of
+// SCAN_BLOCK threads walks them in chunks with a running carry
 __global__ void k_scan_sums(long long* sums, int nb) {
-  // single thread: block counts are small (n / 1024)
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    long long acc = 0;
-    for (int b = 0; b < nb; ++b) {
-      long long t = sums[b];
-      sums[b] = acc;
-      acc += t;
+  __shared__ long long sh[SCAN_BLOCK / 32];
+  __shared__ long long carry;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += SCAN_BLOCK) {
+    int b = base + threadIdx.x;
+    long long v = b < nb ? sums[b] : 0;
+    long long s = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
     }
-    sums[nb] = acc;
+    if (lane == 31) sh[w] = s;
+    __syncthreads();
+    if (w == 0) {
+      long long t = sh[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        long long u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
+      }
+      sh[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) s += sh[w - 1];
+    long long c = carry;
+    if (b < nb) sums[b] = c + s - v;
+    __syncthreads();
+    if (threadIdx.x == SCAN_BLOCK - 1) carry = c + s;
+    __syncthreads();
   }
+  if (threadIdx.x == 0) sums[nb] = carry;
 }
 
 __global__ void k_scan_apply(const int* in, long long n, const long long* block_off, int* out) {
@@ -79,7 +103,7 @@ int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* to
   long long* sums = nullptr;
   FAMS_TRY(b.scratch((void**)&sums, sizeof(long long) * (nb + 1)));
   fams::note_launch(), k_scan_blocks<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums);
-  fams::note_launch(), k_scan_sums<<<1, 32, 0, b.stream>>>(sums, nb);
+  fams::note_launch(), k_scan_sums<<<1, SCAN_BLOCK, 0, b.stream>>>(sums, nb);
   fams::note_launch(), k_scan_apply<<<nb, SCAN_BLOCK, 0, b.stream>>>(in, n, sums, out);
   FAMS_CUDA(cudaGetLastError());
   long long tot = 0;

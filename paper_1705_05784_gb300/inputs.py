@@ -54,6 +54,7 @@ class Problem:
     max_iter: int = 200
     krylov: int = 0                  # 0 the Table 1 loop, 1 GMRES(restart)
     restart: int = 30
+    prepare_flux: int = 0            # 1: build the reconstruction's coarse system beside the solve
     precision: int = 0               # 0 FP64, 1 FP32 inner stages
     rhs: np.ndarray = None           # sources, length N (matrix then fracture); None = 0
     name: str = ""
@@ -132,6 +133,17 @@ def config_2d_small(seed=1, basis=0, restriction=0):
     return Problem(dim=2, nx=nx, ny=ny, nz=1, perm=perm, fracs=fr, kf=np.array([1e4]),
                    coarsen=(4, 4, 1), frac_dmin=5, basis=basis, restriction=restriction,
                    alpha=0.0, name="2d-32x32-1frac")
+
+
+def config_2d_sealed_node(basis=0, restriction=1):
+    """config_2d_small with truncation (alpha 1e-2) and the cell at (22, 6), the
+    coarse node of primal block (5, 1), 1e-10 times as permeable as before."""
+    p = config_2d_small(basis=basis, restriction=restriction)
+    p.perm = p.perm.copy()
+    p.perm[22 + 32 * 6] *= 1e-10
+    p.alpha = 1e-2
+    p.name = "2d-32x32-sealed-node"
+    return p
 
 
 def config_2d_256(seed=2, tratio=1e4, basis=0, restriction=0, n_fracs=30, alpha=0.0):

@@ -420,6 +420,79 @@ def test_flux_batch_matches_single():
             np.testing.assert_array_equal(N[i][: S[i]["n_nnc"]], n1)
 
 
+def _rows(ctx, i):
+    s = ctx.sizes(i)
+    return s["n_matrix"] + s["n_frac"]
+
+
+def test_flux_prepared_beside_the_solve():
+    """prepare_flux = 1 builds the R^FV coarse system on a second stream while
+    the solve runs; the fluxes equal those of the system built on the first
+    fams_flux call (to the rounding of the atomically summed coarse operator),
+    also after a time-step update, which rebuilds it beside the next solve."""
+    fams = _fams()
+
+    def run(prep):
+        probs = [_gmres(_case("2d64", 0, 1), 30, 200), _gmres(_case("3dcross", 1, 1), 30, 200),
+                 _gmres(_case("2d50ragged", 2, 0), 30, 200)]
+        for q in probs:
+            q.prepare_flux = prep
+        out = []
+        with fams.Context(probs) as c:
+            for sc_seed in (None, 5):
+                if sc_seed is not None:
+                    c.update([np.random.default_rng(sc_seed + i).uniform(0.5, 2.0, _rows(c, i))
+                              for i in range(len(probs))])
+                xs, st = c.solve(tol=1e-8)
+                assert all(s["converged"] for s in st)
+                out.append([(x,) + tuple(c.flux(x, i)) for i, x in enumerate(xs)])
+        return out
+
+    a, b = run(1), run(0)
+    for ra, rb in zip(a, b):
+        for (xa, fa, na), (xb, fb, nb) in zip(ra, rb):
+            assert np.linalg.norm(xa - xb) / np.linalg.norm(xb) < 1e-10
+            sc = max(np.abs(fb).max(), np.abs(nb).max() if len(nb) else 0.0)
+            np.testing.assert_allclose(fa, fb, rtol=0, atol=1e-9 * sc)
+            np.testing.assert_allclose(na, nb, rtol=0, atol=1e-9 * sc)
+
+
+def test_flux_reports_a_singular_fv_coarse_system():
+    """The sealed-node instance's R^FV A P is singular by the oracle's scaled
+    pivot test: its reconstruction reports FAMS_EBREAKDOWN, the regular
+    instance of the same batch is reconstructed as alone, and both R^FE
+    solves converge; an R^FV iteration on the sealed instance reports
+    FAMS_EBREAKDOWN from the solve."""
+    fams = _fams()
+    sealed = inputs.config_2d_sealed_node(restriction=0)
+    plain = inputs.config_2d_small(restriction=0)
+    plain.alpha = 1e-2
+    assert osolver.singular_step(oracle.build(sealed)[4].Ac) >= 0
+    assert osolver.singular_step(oracle.build(plain)[4].Ac) == -1
+    probs = []
+    for q in (sealed, plain):
+        q = _gmres(copy.copy(q), 30, 200)
+        q.restriction = 1
+        probs.append(q)
+    with fams.Context(probs) as c:
+        xs, st = c.solve(tol=1e-8)
+        assert all(s["converged"] for s in st)
+        S = [c.sizes(i) for i in range(2)]
+        F = [np.full(s["n_faces"], 7.0) for s in S]
+        N = [np.full(max(1, s["n_nnc"]), 7.0) for s in S]
+        status = c.flux_batch_ptr([x.ctypes.data for x in xs], [f.ctypes.data for f in F],
+                                  [m.ctypes.data for m in N])
+        assert status == [fams.EBREAKDOWN, 0]
+        assert (F[0] == 7.0).all() and (N[0] == 7.0).all()
+        f1, n1 = c.flux(xs[1], 1)
+        np.testing.assert_array_equal(F[1], f1)
+        np.testing.assert_array_equal(N[1][: S[1]["n_nnc"]], n1)
+    with fams.Context(sealed) as c:
+        with pytest.raises(fams.FamsError) as e:
+            c.solve(tol=1e-8)
+        assert e.value.status == fams.EBREAKDOWN
+
+
 def test_rejects_bad_input():
     fams = _fams()
     p = _case("2d32")

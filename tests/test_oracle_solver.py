@@ -245,3 +245,49 @@ def test_mobility_update_pins():
     # each cell sums a few fluxes T (p_i - p_j) of up to max T |p| in size
     bound = 64 * np.finfo(float).eps * abs(ur.A).max() * np.abs(x).max()
     assert np.abs(bal).max() <= bound
+
+
+# --- numerically singular coarse systems (reading: scaled pivot test) ---
+
+def test_singular_step_pins():
+    rng = np.random.default_rng(11)
+    M = rng.standard_normal((7, 7)) + 7 * np.eye(7)
+    assert solver.singular_step(M) == -1
+    Z = M.copy()
+    Z[:, 3] = 0.0                                   # zero column
+    assert solver.singular_step(Z) >= 0
+    R = M.copy()
+    R[4] = -2.5 * R[1]                              # dependent rows
+    assert solver.singular_step(R) >= 0
+    # invariant under row scaling: entries over 16 decades stay regular
+    D = np.diag(10.0 ** np.linspace(-8, 8, 7))
+    assert solver.singular_step(D) == -1
+    assert solver.singular_step(D @ M) == -1
+    assert solver.singular_step(D @ R) >= 0
+    # nearly dependent rows (1e-6 apart) are ill-conditioned, not singular
+    N = M.copy()
+    N[4] = N[1] * (1 + 1e-6 * rng.standard_normal(7))
+    assert solver.singular_step(N) == -1
+    assert solver.singular_step(np.zeros((0, 0))) == -1
+
+
+def test_sealed_node_makes_the_fv_coarse_system_singular():
+    """A node cell 1e-10 times less permeable than its neighbours: its basis
+    function truncates to the node cell alone, so its R^FV column sums A's
+    column over its own primal block (zero); the R^FE system stays regular."""
+    p = inputs.config_2d_sealed_node(restriction=solver.R_FV)
+    g, sysm, c, P, st = oracle.build(p)
+    node = 22 + 32 * 6
+    J = int(np.nonzero(c.node_cell == node)[0][0])
+    col = P.tocsc()[:, J]
+    assert col.nnz == 1 and col.indices[0] == node and col.data[0] == 1.0
+    Afv = st.Ac
+    assert np.abs(Afv[:, J]).max() <= 1e-14 * np.abs(Afv).max()
+    assert solver.singular_step(Afv) >= 0
+    sfe = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FE)
+    assert solver.singular_step(sfe.Ac) == -1
+    # the same inputs without the sealed cell: both regular
+    q = inputs.config_2d_small(restriction=solver.R_FV)
+    q.alpha = 1e-2
+    _, _, _, _, sq = oracle.build(q)
+    assert solver.singular_step(sq.Ac) == -1
