@@ -234,17 +234,16 @@ def solve_bytes(s):
 def gmres_bytes(s, iters, restart):
     """Algorithmic HBM bytes of `iters` GMRES(restart) iterations of one
     instance: per Arnoldi step k (0-based in its cycle) the two-stage step,
-    w = A z, classical Gram-Schmidt twice (each a dot pass over V_0..V_k and
-    w, and an update pass over V_0..V_k reading and writing w) and the
-    scaling of w; per cycle of K steps V_0 = r / beta, u = V y, the final
-    two-stage step and the true residual."""
+    w = A z, modified Gram-Schmidt with each projection fused into the next
+    dot product (k + 2 passes: V_0..V_k read twice, w read k + 2 and written
+    k + 1 times) and the scaling of w; per cycle of K steps V_0 = r / beta,
+    u = V y, the final two-stage step and the true residual."""
     a_pass, two_stage, vec = _passes(s)
     total, left = 0, iters
     while left > 0:
         K = min(restart, left)
         for k in range(K):
-            total += (two_stage + a_pass + 2 * vec + 2 * ((k + 2) * vec) + 2 * ((k + 3) * vec)
-                      + 2 * vec)
+            total += (two_stage + a_pass + 2 * vec + (4 * k + 5) * vec + 2 * vec)
         total += 2 * vec + (K + 1) * vec + two_stage + a_pass + 2 * vec
         left -= K
     return total

@@ -21,13 +21,22 @@ struct CoarseSys {
   int* ipiv = nullptr;          // pivot rows (band positions)
   int* perm = nullptr;          // band position -> coarse index
   int* bad = nullptr;           // per instance: 0, or 1 + the LU step with a zero pivot
+  // factors without row interchanges (LDL^T): inverses of the diagonal
+  // blocks of COARSE_NB band positions, L_bb^-1 then U_bb^-1 per block,
+  // column-major, for the blocked band solve
+  int* nopiv = nullptr;         // per instance: 1 if factored without interchanges
+  double* binv = nullptr;
+  long long* binv_off = nullptr;
 };
+
+constexpr int COARSE_NB = 32;   // band positions per block of the blocked band solve
 
 struct CoarseHost {
   std::vector<long long> ac_off, band_off;
   long long band_tot = 0;
   std::vector<int> kl, ku;
   std::vector<int> bad;         // host copy of CoarseSys::bad
+  std::vector<long long> binv_off;
 };
 
 struct Batch {

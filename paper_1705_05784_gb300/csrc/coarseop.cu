@@ -288,6 +288,64 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
   if (threadIdx.x == 0) cs.bad[ii] = 0;
 }
 
+// Inverses of the diagonal blocks of factors without row interchanges, for
+// the blocked band solve: block b covers band positions [b NB, b NB + NB),
+// L_bb^-1 (unit lower) and U_bb^-1 (U = D L^T as stored), column-major, the
+// identity beyond n.  One warp per (block, triangle); lane c forms column c
+// of the inverse by substitution in shared memory.
+constexpr int BINV_WARPS = 4;
+
+__global__ void k_band_binv(const Inst* inst, int B, CoarseSys cs) {
+  constexpr int NB = COARSE_NB, LD = NB + 1;
+  extern __shared__ double dyn[];
+  const int ii = blockIdx.x;
+  if (!cs.nopiv[ii]) return;
+  const Inst& I = inst[ii];
+  const int n = I.nc, kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
+  const double* AB = cs.band + cs.band_off[ii];
+  double* out = cs.binv + cs.binv_off[ii];
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
+  double* M = dyn + (long long)w * 2 * NB * LD;
+  double* X = M + NB * LD;
+  const int nb = (n + NB - 1) / NB;
+  for (int task = w; task < 2 * nb; task += BINV_WARPS) {
+    const int b = task >> 1, j0 = b * NB, m = min(NB, n - j0);
+    const bool upper = task & 1;
+    for (int i = 0; i < NB; ++i) {   // lane c loads column c of the block
+      double v = i == c ? 1.0 : 0.0;
+      if (i < m && c < m) {
+        const int d = i - c;
+        if (upper ? (d <= 0 && -d <= ku) : (d > 0 && d <= kl))
+          v = AB[(long long)(kv + d) + (long long)ldab * (j0 + c)];
+      }
+      M[i * LD + c] = v;
+    }
+    __syncwarp();
+    if (!upper) {
+      for (int i = 0; i < NB; ++i) {
+        double s = i == c ? 1.0 : 0.0;
+        if (i > c)
+          for (int k = c; k < i; ++k) s -= M[i * LD + k] * X[k * LD + c];
+        X[i * LD + c] = s;
+      }
+    } else {
+      for (int i = NB - 1; i >= 0; --i) {
+        double s = 0.0;
+        if (i <= c) {
+          s = i == c ? 1.0 : 0.0;
+          for (int k = i + 1; k <= c; ++k) s -= M[i * LD + k] * X[k * LD + c];
+          s /= M[i * LD + i];
+        }
+        X[i * LD + c] = s;
+      }
+    }
+    __syncwarp();
+    double* o = out + (long long)b * 2 * NB * NB + (upper ? NB * NB : 0);
+    for (int cc = 0; cc < NB; ++cc) o[cc * NB + c] = X[c * LD + cc];
+    __syncwarp();
+  }
+}
+
 // Band LU (LAPACK gbtf2 steps) on the active block only: rows j..j+kl and a
 // ring of K2 columns from j on, element (i, c) at (i mod (kl+1), c mod K2), in
 // shared memory or, when it does not fit, in a per-CTA slice of global memory
@@ -483,6 +541,8 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
     FAMS_TRY(b.alloc((void**)&cs.ipiv, sizeof(int) * (nct + 1)));
     FAMS_TRY(b.alloc((void**)&cs.perm, sizeof(int) * (nct + 1)));
     FAMS_TRY(b.alloc((void**)&cs.bad, sizeof(int) * B));
+    FAMS_TRY(b.alloc((void**)&cs.nopiv, sizeof(int) * B));
+    FAMS_TRY(b.alloc((void**)&cs.binv_off, sizeof(long long) * B));
     FAMS_CUDA(cudaMemcpyAsync(cs.ac_off, ch.ac_off.data(), sizeof(long long) * B,
                               cudaMemcpyHostToDevice, st));
   }
@@ -543,7 +603,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;   // static shared memory of the kernels
-  std::vector<int> spd(B, 0), lu(B, 0);
+  std::vector<int> spd(B, 0), lu(B, 0), ldl_ok(B, 0);
   size_t ldl_smem = 0;
   for (int i = 0; i < B; ++i) {
     bool fe = mode == 1 || (mode < 0 && b.h[i].restriction == FAMS_R_FE);
@@ -579,7 +639,10 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
       fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct,
                                                                          cs, ip, d_lu);
     }
-    for (int i = 0; i < B; ++i) lu[i] |= failed[i];
+    for (int i = 0; i < B; ++i) {
+      lu[i] |= failed[i];
+      ldl_ok[i] = spd[i] && !failed[i];
+    }
   }
   // band LU on the active block.  First a narrow ring (threshold pivoting,
   // fill up to LU_EXTRA columns past the upper band) in shared memory; then
@@ -659,6 +722,29 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
                                                                  (long long)act_g, -1, 1.0, nullptr);
   }
   FAMS_CUDA(cudaGetLastError());
+  // inverse diagonal blocks of the LDL^T factors (room for every instance that
+  // tries LDL^T, which the same bandwidths decide again on a refactorisation)
+  if (!reuse) {
+    ch.binv_off.assign(B, 0);
+    long long tot_binv = 0;
+    for (int i = 0; i < B; ++i) {
+      ch.binv_off[i] = tot_binv;
+      if (spd[i])
+        tot_binv += (long long)((b.h[i].nc + COARSE_NB - 1) / COARSE_NB) * 2 * COARSE_NB * COARSE_NB;
+    }
+    FAMS_TRY(b.alloc((void**)&cs.binv, sizeof(double) * (tot_binv + 1)));
+    FAMS_CUDA(cudaMemcpyAsync(cs.binv_off, ch.binv_off.data(), sizeof(long long) * B,
+                              cudaMemcpyHostToDevice, st));
+  }
+  FAMS_CUDA(cudaMemcpyAsync(cs.nopiv, ldl_ok.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  bool any_ldl = false;
+  for (int i = 0; i < B; ++i) any_ldl |= ldl_ok[i] != 0;
+  if (any_ldl) {
+    const size_t sm = sizeof(double) * BINV_WARPS * 2 * COARSE_NB * (COARSE_NB + 1);
+    FAMS_CUDA(cudaFuncSetAttribute(k_band_binv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    fams::note_launch(), k_band_binv<<<B, 32 * BINV_WARPS, sm, st>>>(b.d_inst, B, cs);
+    FAMS_CUDA(cudaGetLastError());
+  }
   ch.bad.assign(B, 0);
   FAMS_CUDA(cudaMemcpyAsync(ch.bad.data(), cs.bad, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   FAMS_CUDA(cudaStreamSynchronize(st));

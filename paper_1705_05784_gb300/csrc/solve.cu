@@ -283,6 +283,59 @@ __device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, i
   __syncthreads();
 }
 
+// Band solve of factors without row interchanges (LDL^T, stored as unit L and
+// U = D L^T) in blocks of COARSE_NB band positions: a block's unknowns come
+// from its precomputed inverse diagonal block (a small dense product instead
+// of COARSE_NB dependent steps), then the rows the block couples to are
+// updated.  Forward with L, then backward with U.  Every thread takes part;
+// partial sums are combined in a fixed order.  part: 4 (COARSE_NB + kl)
+// doubles of shared memory.
+__device__ void coarse_solve_blocked(const double* AB, const double* binv, int n, int kl, int ku,
+                                     double* yb, double* part) {
+  constexpr int NB = COARSE_NB;
+  const int kv = kl + ku, ldab = 2 * kl + ku + 1;
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int nb = (n + NB - 1) / NB;
+  double* pd = part;            // 4 x NB partial sums of the diagonal block
+  double* pr = part + 4 * NB;   // 4 x (coupled rows) partial sums
+  for (int s = 0; s < 2 * nb; ++s) {
+    const bool fwd = s < nb;
+    const int b = fwd ? s : 2 * nb - 1 - s;
+    const int j0 = b * NB, m = min(NB, n - j0);
+    const double* X = binv + (long long)b * 2 * NB * NB + (fwd ? 0 : NB * NB);
+    if (tid < 4 * NB) {
+      const int i = tid & (NB - 1), q = tid / NB;
+      double acc = 0.0;
+      const int c0 = 8 * q, c1 = min(c0 + 8, m);
+      if (i < m)
+        for (int c = c0; c < c1; ++c)
+          if (fwd ? c <= i : c >= i) acc += X[c * NB + i] * yb[j0 + c];
+      pd[q * NB + i] = acc;
+    }
+    __syncthreads();
+    if (tid < m) yb[j0 + tid] = (pd[tid] + pd[NB + tid]) + (pd[2 * NB + tid] + pd[3 * NB + tid]);
+    __syncthreads();
+    // rows coupled to the block: below it within kl (forward), above it within ku (backward)
+    const int r0 = fwd ? j0 + NB : max(0, j0 - ku);
+    const int r1 = fwd ? min(n, j0 + m + kl) : j0;
+    const int nr = max(0, r1 - r0);
+    for (int e = tid; e < 4 * nr; e += T) {
+      const int q = e / nr, i = r0 + e - q * nr;
+      const int c0 = j0 + 8 * q, c1 = min(c0 + 8, j0 + m);
+      double acc = 0.0;
+      for (int c = c0; c < c1; ++c) {
+        const int d = i - c;
+        if (fwd ? d <= kl : -d <= ku) acc += AB[(long long)(kv + d) + (long long)ldab * c] * yb[c];
+      }
+      pr[e] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < nr; t += T)
+      yb[r0 + t] -= (pr[t] + pr[nr + t]) + (pr[2 * nr + t] + pr[3 * nr + t]);
+    __syncthreads();
+  }
+}
+
 // one row of a triangular sweep, loaded from the level-ordered layout: every
 // address depends only on the position t, so the loads of a whole level are
 // coalesced and independent of the sweep's results
@@ -379,7 +432,10 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   }
   __syncthreads();
   long long t1b = clock64();
-  coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf);
+  if (a.cs.nopiv[ii] && 4 * (COARSE_NB + kl) <= 2 * BAND_BUF)
+    coarse_solve_blocked(AB, a.cs.binv + a.cs.binv_off[ii], nc, kl, ku, S.yb, S.buf);
+  else
+    coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf);
   for (int k = threadIdx.x; k < nc; k += NT) {
     S.ecs[perm[k]] = S.yb[k];
     a.csol[co + perm[k]] = S.yb[k];

@@ -160,14 +160,47 @@ __device__ void bitonic(K* sk, V* sv, int m) {
   }
 }
 
-// sort the segments with lo < length <= hi by key, one CTA per segment: in
-// dynamic shared memory (gtmp null; room for the power of two above hi) or
-// in a global scratch slice of `stride` keys (and values) per CTA
-__global__ void k_seg_sort(const int* ptr, int nseg, int* key, double* val, int lo, int hi,
-                           int* gk, double* gv, long long stride) {
-  extern __shared__ double dyn[];
-  int s = blockIdx.x;
+constexpr int SEG_TINY = 16;   // segments sorted by one thread in registers
+
+// one thread per segment: segments of at most SEG_TINY entries are sorted in
+// place by insertion; longer ones are listed for the CTA-per-segment sort
+__global__ void k_seg_tiny(const int* ptr, int nseg, int* key, double* val, int* list, int* nlist) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
+  int a = ptr[s], n = ptr[s + 1] - a;
+  if (n <= 1) return;
+  if (n > SEG_TINY) {
+    list[atomicAdd(nlist, 1)] = s;
+    return;
+  }
+  int k[SEG_TINY];
+  double v[SEG_TINY];
+  for (int i = 0; i < n; ++i) {
+    int ki = key[a + i];
+    double vi = val ? val[a + i] : 0.0;
+    int j = i;
+    while (j > 0 && k[j - 1] > ki) {
+      k[j] = k[j - 1];
+      v[j] = v[j - 1];
+      --j;
+    }
+    k[j] = ki;
+    v[j] = vi;
+  }
+  for (int i = 0; i < n; ++i) {
+    key[a + i] = k[i];
+    if (val) val[a + i] = v[i];
+  }
+}
+
+// sort the listed segments with lo < length <= hi by key, one CTA per
+// segment: in dynamic shared memory (gk null; room for the power of two above
+// hi) or in a global scratch slice of `stride` keys (and values) per CTA
+__global__ void k_seg_sort(const int* ptr, const int* list, int nseg, int* key, double* val,
+                           int lo, int hi, int* gk, double* gv, long long stride) {
+  extern __shared__ double dyn[];
+  if ((int)blockIdx.x >= nseg) return;
+  int s = list[blockIdx.x];
   int a = ptr[s], n = ptr[s + 1] - a;
   if (n <= lo || n > hi || n <= 1) return;
   int m = 1;
@@ -202,36 +235,41 @@ constexpr int SEG_SMALL = 1024;   // segments sorted with a small shared-memory 
 int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict) {
   (void)strict;
   if (nseg <= 0) return FAMS_OK;
-  int* dmax = nullptr;
-  FAMS_TRY(b.scratch((void**)&dmax, sizeof(int)));
-  FAMS_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), b.stream));
+  int* dmax = nullptr;   // [0] longest segment, [1] listed segments
+  int* list = nullptr;
+  FAMS_TRY(b.scratch((void**)&dmax, sizeof(int) * 2));
+  FAMS_TRY(b.scratch((void**)&list, sizeof(int) * nseg));
+  FAMS_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int) * 2, b.stream));
   fams::note_launch(), k_seg_max<<<grid_for(nseg, 256), 256, 0, b.stream>>>(ptr, nseg, dmax);
-  int mx = 0;
-  FAMS_CUDA(cudaMemcpyAsync(&mx, dmax, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  fams::note_launch(), k_seg_tiny<<<grid_for(nseg, 256), 256, 0, b.stream>>>(ptr, nseg, key, val,
+                                                                           list, dmax + 1);
+  int hm[2] = {0, 0};
+  FAMS_CUDA(cudaMemcpyAsync(hm, dmax, sizeof(int) * 2, cudaMemcpyDeviceToHost, b.stream));
   FAMS_CUDA(cudaStreamSynchronize(b.stream));
-  if (mx <= 1) return FAMS_OK;
+  const int mx = hm[0], nl = hm[1];
+  if (mx <= SEG_TINY || nl == 0) return FAMS_OK;
   const size_t per = sizeof(int) + (val ? sizeof(double) : 0);
   auto pow2 = [](int v) { int m = 1; while (m < v) m <<= 1; return m; };
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   FAMS_CUDA(cudaFuncSetAttribute(k_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   int small = std::min(mx, SEG_SMALL);
-  fams::note_launch(), k_seg_sort<<<nseg, 256, per * pow2(small), b.stream>>>(
-      ptr, nseg, key, val, 0, SEG_SMALL, nullptr, nullptr, 0);
+  fams::note_launch(), k_seg_sort<<<nl, 256, per * pow2(small), b.stream>>>(
+      ptr, list, nl, key, val, SEG_TINY, SEG_SMALL, nullptr, nullptr, 0);
   if (mx > SEG_SMALL) {
     int cap = SEG_SMALL;
     while ((size_t)cap * 2 * per <= (size_t)max_smem && cap * 2 <= pow2(mx)) cap *= 2;
     if (cap > SEG_SMALL)
-      fams::note_launch(), k_seg_sort<<<nseg, 512, per * cap, b.stream>>>(
-          ptr, nseg, key, val, SEG_SMALL, cap, nullptr, nullptr, 0);
+      fams::note_launch(), k_seg_sort<<<nl, 512, per * cap, b.stream>>>(
+          ptr, list, nl, key, val, SEG_SMALL, cap, nullptr, nullptr, 0);
     if (mx > cap) {
       long long stride = pow2(mx);
       int *gk = nullptr;
       double* gv = nullptr;
-      FAMS_TRY(b.scratch((void**)&gk, sizeof(int) * stride * (size_t)nseg));
-      if (val) FAMS_TRY(b.scratch((void**)&gv, sizeof(double) * stride * (size_t)nseg));
-      fams::note_launch(), k_seg_sort<<<nseg, 1024, 0, b.stream>>>(ptr, nseg, key, val, cap, 1 << 30,
-                                                                  gk, gv, stride);
+      FAMS_TRY(b.scratch((void**)&gk, sizeof(int) * stride * (size_t)nl));
+      if (val) FAMS_TRY(b.scratch((void**)&gv, sizeof(double) * stride * (size_t)nl));
+      fams::note_launch(), k_seg_sort<<<nl, 1024, 0, b.stream>>>(ptr, list, nl, key, val, cap, 1 << 30,
+                                                                gk, gv, stride);
     }
   }
   FAMS_CUDA(cudaGetLastError());

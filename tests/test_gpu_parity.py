@@ -212,6 +212,40 @@ def test_coarse_factors_of_wide_bands():
         assert _check_band_factors(c1, 0) > 118
 
 
+def _coarse_solve_berr(ctx, i):
+    nc = ctx.sizes(i)["n_coarse"]
+    Ac = ctx.query("AC", i).reshape(nc, nc)
+    rc, ec = ctx.query("LAST_RC", i), ctx.query("LAST_EC", i)
+    return np.linalg.norm(Ac @ ec - rc, np.inf) / (np.linalg.norm(Ac, np.inf) * np.linalg.norm(ec, np.inf)
+                                                   + np.linalg.norm(rc, np.inf))
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", CASES)
+def test_device_coarse_solve(built, name, restriction):
+    """The coarse solve inside the iteration -- blocks of 32 through inverse
+    diagonal blocks for LDL^T factors, column by column with interchanges for
+    the band LU -- solves the last application's R A P e = R r to rounding."""
+    p, g, sysm, c, P, st, ctx = built(name, 0, restriction)
+    ctx.solve(tol=1e-8)
+    assert _coarse_solve_berr(ctx, 0) < 1e-13
+
+
+def test_device_coarse_solve_at_bench_size():
+    """256x256 R^FE instances (coarse sizes ~1100-1300, not multiples of 32;
+    bandwidths 40-150) through the blocked solve."""
+    fams = _fams()
+    probs = []
+    for i in range(8):
+        q = _gmres(inputs.config_2d_256(seed=700 + i, tratio=10.0 ** (2 + 2 * (i % 4)), basis=i % 4,
+                                        restriction=1, alpha=1e-2), 30, 3)
+        probs.append(q)
+    with fams.Context(probs) as cb:
+        cb.solve(tol=0.0)
+        for i in range(len(probs)):
+            assert _coarse_solve_berr(cb, i) < 1e-13, i
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_ilu0(built, name):
     p, g, sysm, c, P, st, ctx = built(name)
