@@ -304,12 +304,19 @@ __device__ void coarse_solve_blocked(const double* AB, const double* binv, int n
     const int j0 = b * NB, m = min(NB, n - j0);
     const double* X = binv + (long long)b * 2 * NB * NB + (fwd ? 0 : NB * NB);
     if (tid < 4 * NB) {
+      // eight independent loads in flight, then the products
       const int i = tid & (NB - 1), q = tid / NB;
+      double xv[8], yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = 8 * q + u;
+        const bool ok = i < m && c < m && (fwd ? c <= i : c >= i);
+        xv[u] = ok ? X[c * NB + i] : 0.0;
+        yv[u] = ok ? yb[j0 + c] : 0.0;
+      }
       double acc = 0.0;
-      const int c0 = 8 * q, c1 = min(c0 + 8, m);
-      if (i < m)
-        for (int c = c0; c < c1; ++c)
-          if (fwd ? c <= i : c >= i) acc += X[c * NB + i] * yb[j0 + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += xv[u] * yv[u];
       pd[q * NB + i] = acc;
     }
     __syncthreads();
@@ -321,12 +328,17 @@ __device__ void coarse_solve_blocked(const double* AB, const double* binv, int n
     const int nr = max(0, r1 - r0);
     for (int e = tid; e < 4 * nr; e += T) {
       const int q = e / nr, i = r0 + e - q * nr;
-      const int c0 = j0 + 8 * q, c1 = min(c0 + 8, j0 + m);
-      double acc = 0.0;
-      for (int c = c0; c < c1; ++c) {
-        const int d = i - c;
-        if (fwd ? d <= kl : -d <= ku) acc += AB[(long long)(kv + d) + (long long)ldab * c] * yb[c];
+      double av[8], yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = j0 + 8 * q + u, d = i - c;
+        const bool ok = c < j0 + m && (fwd ? d <= kl : -d <= ku);
+        av[u] = ok ? AB[(long long)(kv + d) + (long long)ldab * c] : 0.0;
+        yv[u] = ok ? yb[c] : 0.0;
       }
+      double acc = 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += av[u] * yv[u];
       pr[e] = acc;
     }
     __syncthreads();
