@@ -108,8 +108,8 @@ class Clocks:
                 "samples": len(sm)}
 
 
-SERVE_WORKLOAD = ("stream of independent requests, arrivals Poisson at 80% of the served "
-                  "sustained rate: half 2D (side U{64..256}, 0-30 fractures L~U[20,120], "
+SERVE_WORKLOAD = ("stream of independent requests, arrivals Poisson at 80% of the "
+                  "closed-loop rate: half 2D (side U{64..256}, 0-30 fractures L~U[20,120], "
                   "log10 k std 2 corr 16, coarsening 8x8), half 3D (cube side U{24..48}, 0-10 "
                   "full-height plates, log10 k std 1.5, coarsening U{4..8}^3); T_ratio "
                   "1e2..1e8, the four coupling strategies, R^FE, GMRES(30), tol 1e-8, + flux")
@@ -143,7 +143,7 @@ def serve_problems(n, seed):
     return out
 
 
-def serving(fams, n_req, n_plain, seed, pipelines=6, max_batch=64):
+def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
     """Served stream (continuous batching through fams_server_*) against the
     plain path (one context per request, solved one after another)."""
     import numpy as np
@@ -154,38 +154,47 @@ def serving(fams, n_req, n_plain, seed, pipelines=6, max_batch=64):
         return v[min(len(v) - 1, int(q * len(v)))] if v else None
 
     def run(rate):
-        lat, svc, ok, fails = [], [], 0, {}
+        lat, svc, ok, fails, done = [], [], 0, {}, []
         with fams.Server(max_batch=max_batch, pipelines=pipelines, hbm_budget=96 << 30,
                          tol=TOL) as srv:
             rng = np.random.default_rng(seed + 1)
             arrive = np.cumsum(rng.exponential(1.0 / rate, len(probs))) if rate else None
             t0 = time.perf_counter()
-            tickets = []
+            tickets, t_sub = [], []
             for k, p in enumerate(probs):
                 if arrive is not None:
                     dt = arrive[k] - (time.perf_counter() - t0)
                     if dt > 0:
                         time.sleep(dt)
+                t_sub.append(time.perf_counter() - t0)
                 tickets.append(srv.submit(p))
             for t in tickets:
                 srv.wait(t, 600000.0)
             elapsed = time.perf_counter() - t0
-            for t in tickets:
+            for t, ts in zip(tickets, t_sub):
                 x, face, nnc, st = srv.fetch(t)
-                ok += st["status"] == 0 and st["converged"]
+                good = st["status"] == 0 and st["converged"]
+                ok += good
                 if st["status"] != 0:
                     key = st["error"][:90]
                     fails[key] = fails.get(key, 0) + 1
                 lat.append(st["latency_ms"])
                 svc.append(st["service_ms"])
+                if good:
+                    done.append(ts + st["latency_ms"] / 1000.0)
                 srv.release(t)
-        return ok, elapsed, lat, fails, svc
+        # steady-state rate: completions between the 10th and 90th percentile
+        # completion times (no ramp-up at the start, no drain at the end)
+        done.sort()
+        i10, i90 = int(0.1 * len(done)), int(0.9 * len(done))
+        steady = (i90 - i10) / (done[i90] - done[i10]) if i90 > i10 and done[i90] > done[i10] else None
+        return ok, elapsed, lat, fails, svc, steady
 
     run(None)                                    # warm-up of the stream's code paths
 
-    ok_c, el_c, _, _, _ = run(None)              # closed loop: sustained served rate
+    ok_c, el_c, _, _, _, _ = run(None)           # closed loop: sustained served rate
     rate = 0.8 * len(probs) / el_c
-    ok_s, el_s, lat, fails, svc = run(rate)
+    ok_s, el_s, lat, fails, svc, steady = run(rate)
     # plain: the first n_plain requests, each alone, one after another
     times = []
     ok_p = 0
@@ -204,13 +213,15 @@ def serving(fams, n_req, n_plain, seed, pipelines=6, max_batch=64):
     return {"workload": SERVE_WORKLOAD, "requests": len(probs), "pipelines": pipelines,
             "max_batch": max_batch,
             "sustained_solves_per_s": ok_c / el_c, "arrival_rate_per_s": rate,
-            "served_solves_per_s": ok_s / el_s, "converged": ok_s, "failed": fails,
+            "served_solves_per_s": steady, "served_over_whole_run_per_s": ok_s / el_s,
+            "converged": ok_s, "failed": fails,
             "p50_ms": pct(lat, 0.50), "p99_ms": pct(lat, 0.99),
             "service_p50_ms": pct(svc, 0.50), "service_p99_ms": pct(svc, 0.99),
+            "queue_p50_ms": pct([l - s for l, s in zip(lat, svc)], 0.50),
             "plain": {"requests": len(times), "solves_per_s": plain_rate,
                       "p50_ms": pct(times, 0.50), "p99_ms": pct(times, 0.99),
                       "note": "one context per request, setup + solve + flux, sequential"},
-            "served_vs_plain": (ok_s / el_s) / plain_rate if plain_rate else None}
+            "served_vs_plain": steady / plain_rate if plain_rate and steady else None}
 
 
 def _passes(s):
@@ -330,7 +341,7 @@ def main():
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
     ap.add_argument("--serve", type=int, default=400,
                     help="requests in the served stream (0: skip the serving measurement)")
-    ap.add_argument("--pipelines", type=int, default=6, help="server: micro-batches in flight")
+    ap.add_argument("--pipelines", type=int, default=4, help="server: micro-batches in flight")
     ap.add_argument("--max-batch", type=int, default=64, help="server: requests per micro-batch")
     ap.add_argument("--plain", type=int, default=32,
                     help="requests of the stream solved one by one for the plain comparison")
