@@ -771,14 +771,33 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
     for (int i = 0; i <= k + 1; ++i) {
       const double* Vp = i > 0 ? V + (long long)(i - 1) * ld : nullptr;
       const double* Vi = i <= k ? V + (long long)i * ld : nullptr;
+      // ROWS_ILP rows per thread in flight: all loads first (the compiler
+      // cannot prove that w does not alias the basis vectors, so it would not
+      // move a row's loads above the previous row's store), then the
+      // arithmetic in the same row order as one row at a time
       double s = 0.0;
-      for (int r = ro + threadIdx.x; r < ro + n; r += NT) {
-        double wr = w[r];
-        if (Vp) {
-          wr -= hprev * Vp[r];
-          w[r] = wr;
+      for (int r0 = ro + threadIdx.x; r0 < ro + n; r0 += ROWS_ILP * NT) {
+        double wv[ROWS_ILP], pv[ROWS_ILP], iv[ROWS_ILP];
+#pragma unroll
+        for (int u = 0; u < ROWS_ILP; ++u) {
+          const int r = r0 + u * NT;
+          const bool ok = r < ro + n;
+          wv[u] = ok ? w[r] : 0.0;
+          pv[u] = ok && Vp ? Vp[r] : 0.0;
+          iv[u] = ok && Vi ? Vi[r] : 0.0;
         }
-        s += Vi ? Vi[r] * wr : wr * wr;
+#pragma unroll
+        for (int u = 0; u < ROWS_ILP; ++u) {
+          const int r = r0 + u * NT;
+          if (r < ro + n) {
+            double wr = wv[u];
+            if (Vp) {
+              wr -= hprev * pv[u];
+              w[r] = wr;
+            }
+            s += Vi ? iv[u] * wr : wr * wr;
+          }
+        }
       }
       double h = block_sum(s, G.red);
       if (i <= k) {
