@@ -420,27 +420,26 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   T* y = Prec<T>::y(a);
   T* ylev = Prec<T>::ylev(a);
   long long t1 = clock64();
-  // step 5: coarse right-hand side R r, in band order
-  for (int k = threadIdx.x; k < nc; k += NT) {
-    int c = co + perm[k];
-    T s0 = 0, s1 = 0;
-    if (I.restriction == FAMS_R_FE) {
-      int p = a.pt_ptr[c], e = a.pt_ptr[c + 1];
-      for (; p + 1 < e; p += 2) {
-        s0 += ptv[p] * r[a.pt_col[p]];
-        s1 += ptv[p + 1] * r[a.pt_col[p + 1]];
+  // step 5: coarse right-hand side R r, in band order: one warp per coarse
+  // row (a row of P^T or a primal block holds hundreds of cells), lanes
+  // along the row, then a fixed butterfly sum
+  {
+    const int lane = threadIdx.x & 31, nw = NT >> 5;
+    for (int k = threadIdx.x >> 5; k < nc; k += nw) {
+      const int c = co + perm[k];
+      T s = 0;
+      if (I.restriction == FAMS_R_FE) {
+        for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += ptv[p] * r[a.pt_col[p]];
+      } else {
+        for (int p = a.blk_ptr[c] + lane; p < a.blk_ptr[c + 1]; p += 32) s += r[a.blk_cell[p]];
       }
-      if (p < e) s0 += ptv[p] * r[a.pt_col[p]];
-    } else {
-      int p = a.blk_ptr[c], e = a.blk_ptr[c + 1];
-      for (; p + 1 < e; p += 2) {
-        s0 += r[a.blk_cell[p]];
-        s1 += r[a.blk_cell[p + 1]];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        S.yb[k] = (double)s;
+        a.crhs[c] = (double)s;
       }
-      if (p < e) s0 += r[a.blk_cell[p]];
     }
-    S.yb[k] = (double)(s0 + s1);
-    a.crhs[co + perm[k]] = (double)(s0 + s1);
   }
   __syncthreads();
   long long t1b = clock64();
