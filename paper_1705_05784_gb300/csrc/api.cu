@@ -95,6 +95,33 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   return FAMS_OK;
 }
 
+// flags an entry that is not positive and finite (integer test on the bits:
+// the sign bit makes negatives negative, NaN and infinity lie above the
+// largest finite pattern)
+__global__ void k_check_positive(const double* v, long long n, int* bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long b = __double_as_longlong(v[i]);
+  if (!(b > 0 && b < 0x7ff0000000000000LL)) atomicExch(bad, 1);
+}
+
+// copy a small caller array (host or device memory) into host memory
+int copy_to_host(void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return FAMS_OK;
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, src);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    FAMS_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return FAMS_OK;
+}
+
 int setup_batch(int n, const fams_grid* grids, const double* const* perms, const fams_fracs* fracs,
                 const fams_opts* opts, Batch& b) {
   b.B = n;
@@ -163,9 +190,8 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     if (I.nfr) {
       int w = I.dim == 3 ? 6 : 4;
       std::vector<double> xy((size_t)w * I.nfr);
-      FAMS_CUDA(cudaMemcpy(xy.data(), fracs[i].xy, sizeof(double) * w * I.nfr, cudaMemcpyDefault));
-      FAMS_CUDA(cudaMemcpy(hkf.data() + I.fr_off, fracs[i].kf, sizeof(double) * I.nfr,
-                           cudaMemcpyDefault));
+      FAMS_TRY(copy_to_host(xy.data(), fracs[i].xy, sizeof(double) * w * I.nfr));
+      FAMS_TRY(copy_to_host(hkf.data() + I.fr_off, fracs[i].kf, sizeof(double) * I.nfr));
       for (int f = 0; f < I.nfr; ++f)
         for (int k = 0; k < w; ++k) hfr[6 * (I.fr_off + f) + k] = xy[(size_t)w * f + k];
     }
@@ -175,14 +201,18 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
   FAMS_CUDA(cudaMemcpyAsync(b.kf, hkf.data(), sizeof(double) * hkf.size(), cudaMemcpyHostToDevice,
                             b.stream));
   {
-    std::vector<double> hp(m);
-    FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.perm, sizeof(double) * m, cudaMemcpyDeviceToHost, b.stream));
+    int* dbad = nullptr;
+    FAMS_TRY(b.scratch((void**)&dbad, sizeof(int)));
+    FAMS_CUDA(cudaMemsetAsync(dbad, 0, sizeof(int), b.stream));
+    if (m > 0)
+      fams::note_launch(), k_check_positive<<<grid_for(m, 256), 256, 0, b.stream>>>(b.perm, m, dbad);
+    int hbad = 0;
+    FAMS_CUDA(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
     FAMS_CUDA(cudaStreamSynchronize(b.stream));
-    for (double v : hp)
-      if (!(v > 0.0) || !std::isfinite(v)) {
-        set_error("permeability must be positive and finite");
-        return FAMS_EINVAL;
-      }
+    if (hbad) {
+      set_error("permeability must be positive and finite");
+      return FAMS_EINVAL;
+    }
     for (long long f = 0; f < fr; ++f)
       if (!(hkf[f] > 0.0) || !std::isfinite(hkf[f])) {
         set_error("fracture permeability must be positive and finite");
@@ -235,6 +265,11 @@ void destroy_batch(Batch& b) {
   if (b.side_done) cudaEventDestroy(b.side_done);
   b.side = nullptr;
   b.side_done = nullptr;
+  if (b.aux) cudaStreamDestroy(b.aux);
+  if (b.aux_ev) cudaEventDestroy(b.aux_ev);
+  if (b.aux_done) cudaEventDestroy(b.aux_done);
+  b.aux = nullptr;
+  b.aux_ev = b.aux_done = nullptr;
 }
 
 template <class T>

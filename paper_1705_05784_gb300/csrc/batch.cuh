@@ -44,6 +44,8 @@ struct Batch {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;        // second stream: the R^FV system built beside a solve
   cudaEvent_t side_done = nullptr;
+  cudaStream_t aux = nullptr;         // concurrent band LU passes of disjoint instance sets
+  cudaEvent_t aux_ev = nullptr, aux_done = nullptr;
   bool prepare_flux = false;          // some instance asked for it (fams_opts.prepare_flux)
   int device = 0;
   std::vector<Inst> h;          // host copy of the descriptors

@@ -644,9 +644,10 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
       ldl_ok[i] = spd[i] && !failed[i];
     }
   }
-  // band LU on the active block.  First a narrow ring (threshold pivoting,
-  // fill up to LU_EXTRA columns past the upper band) in shared memory; then
-  // the full ring of partial pivoting for the instances that did not fit it
+  // band LU on the active block.  R^FE systems whose LDL^T failed first try
+  // a narrow ring (threshold pivoting, fill up to LU_EXTRA columns past the
+  // upper band) in shared memory; then the full ring of partial pivoting for
+  // the R^FV systems and for the instances that did not fit the narrow ring
   // or pivoted beyond it: in shared memory where it fits, else in global
   // scratch
   FAMS_CUDA(cudaFuncSetAttribute(k_band_lu_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -658,7 +659,10 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
     std::vector<int> lu_n(B, 0);
     size_t act_n = 0;
     for (int i = 0; i < B; ++i) {
-      if (!lu[i]) continue;
+      // R^FV systems (high contrast, often pivoting across the whole lower
+      // band) fail the narrow ring too often to gain from it: full ring first
+      const bool fe = mode == 1 || (mode < 0 && b.h[i].restriction == FAMS_R_FE);
+      if (!lu[i] || !fe) continue;
       size_t k2 = (size_t)std::min(ch.kl[i] + ch.ku[i] + 1, ch.ku[i] + 1 + LU_EXTRA);
       size_t act = (size_t)(ch.kl[i] + 1) * k2;
       if (sizeof(double) * act + temps <= (size_t)max_smem) {
@@ -707,21 +711,39 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
       act_g = std::max(act_g, act);
     }
   }
-  if (act_s > 0) {
-    FAMS_CUDA(cudaMemcpyAsync(d_lu, lu_s.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-    fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_s + temps, st>>>(
-        b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0, -1, 1.0, nullptr);
-  }
+  // the shared-memory and the global-memory passes factor disjoint sets of
+  // instances: when both run, the global one goes on a second stream so that
+  // the two overlap (each keeps only a few CTAs busy)
+  int* d_lg = nullptr;
+  double* gws = nullptr;
   if (act_g > 0) {
-    int* d_lg = nullptr;
-    double* gws = nullptr;
     FAMS_TRY(b.scratch((void**)&d_lg, sizeof(int) * B));
     FAMS_TRY(b.scratch((void**)&gws, sizeof(double) * act_g * (size_t)B));
     FAMS_CUDA(cudaMemcpyAsync(d_lg, lu_g.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-    fams::note_launch(), k_band_lu_act<<<B, 1024, temps, st>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
-                                                                 (long long)act_g, -1, 1.0, nullptr);
   }
+  if (act_s > 0) FAMS_CUDA(cudaMemcpyAsync(d_lu, lu_s.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  cudaStream_t gst = st;
+  if (act_s > 0 && act_g > 0) {
+    if (!b.aux) {
+      FAMS_CUDA(cudaStreamCreateWithFlags(&b.aux, cudaStreamNonBlocking));
+      FAMS_CUDA(cudaEventCreateWithFlags(&b.aux_ev, cudaEventDisableTiming));
+      FAMS_CUDA(cudaEventCreateWithFlags(&b.aux_done, cudaEventDisableTiming));
+    }
+    FAMS_CUDA(cudaEventRecord(b.aux_ev, st));
+    FAMS_CUDA(cudaStreamWaitEvent(b.aux, b.aux_ev, 0));
+    gst = b.aux;
+  }
+  if (act_s > 0)
+    fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_s + temps, st>>>(
+        b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0, -1, 1.0, nullptr);
+  if (act_g > 0)
+    fams::note_launch(), k_band_lu_act<<<B, 1024, temps, gst>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
+                                                                  (long long)act_g, -1, 1.0, nullptr);
   FAMS_CUDA(cudaGetLastError());
+  if (gst != st) {
+    FAMS_CUDA(cudaEventRecord(b.aux_done, gst));
+    FAMS_CUDA(cudaStreamWaitEvent(st, b.aux_done, 0));
+  }
   // inverse diagonal blocks of the LDL^T factors (room for every instance that
   // tries LDL^T, which the same bandwidths decide again on a refactorisation)
   if (!reuse) {

@@ -534,6 +534,14 @@ def test_rejects_bad_input():
     with pytest.raises(fams.FamsError) as e:
         fams.Context(p)
     assert e.value.status == fams.EINVAL
+    # permeability not positive and finite (checked on the device)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        q = _case("2d32")
+        q.perm = q.perm.copy()
+        q.perm[37] = bad
+        with pytest.raises(fams.FamsError) as e:
+            fams.Context([_case("2d64"), q])
+        assert e.value.status == fams.EINVAL and "permeability" in str(e.value)
 
 
 # --- time-step update (fams_update): mobility scales, P reused ---
