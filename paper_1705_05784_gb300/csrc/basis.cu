@@ -660,14 +660,12 @@ int phase_basis(Batch& b) {
   FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.alloc((void**)&b.p_ptr, sizeof(int) * (nrow + 1)));
   {
-    std::vector<int> hst(nrow);
-    FAMS_CUDA(cudaMemcpyAsync(hst.data(), pstage, sizeof(int) * nrow, cudaMemcpyDeviceToHost, st));
-    FAMS_CUDA(cudaStreamSynchronize(st));
-    for (long long r = 0; r < nrow; ++r)
-      if (hst[r] < 0) {
-        set_error("a cell was left without a basis row (it belongs to no stage)");
-        return FAMS_EINVAL;
-      }
+    bool missing = false;
+    FAMS_TRY(any_negative(b, pstage, nrow, &missing));
+    if (missing) {
+      set_error("a cell was left without a basis row (it belongs to no stage)");
+      return FAMS_EINVAL;
+    }
   }
   fams::note_launch(), k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
                                              pool, cnt);

@@ -132,6 +132,7 @@ struct Batch {
   double* pt_val = nullptr;
   int* blk_ptr = nullptr;      // cells of each primal block (global coarse index)
   int* blk_cell = nullptr;
+  std::vector<int> h_blk_ptr;  // host copy of blk_ptr (taken on the first reconstruction)
   // ---- coarse system: [0] the iteration's restriction, [1] R^FV for the
   // flux reconstruction when the iteration uses R^FE ----
   CoarseSys cs[2];
@@ -224,6 +225,10 @@ struct Batch {
 
 // util.cu
 int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* total);
+// out[i] = src[idx[i]] for i < n, on the host (idx in device memory)
+int take_ints(Batch& b, const int* src, const int* idx, int n, std::vector<int>& out);
+// whether any of v[0..n) is negative
+int any_negative(Batch& b, const int* v, long long n, bool* res);
 int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict);
 int transpose(Batch& b, const int* rowptr, const int* col, const double* val, int nrows,
               int ncols, long long nnz, int** tptr, int** tcol, double** tval, bool keep);

@@ -242,6 +242,7 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
   double* AB = cs.band + cs.band_off[ii];
   int* ipiv = cs.ipiv + I.nc_off;
   double* colj = S + (long long)K * K;   // column j below the pivot
+  __shared__ double s_inv;
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
   for (int e = threadIdx.x; e < K * K; e += T) {
     int i = e / K, c = e - i * K;
@@ -252,13 +253,15 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
     const int km = min(kl, n - 1 - j);
     const int js = j % K, base = wrap(js + 1, K);
     const double d = S[js * K + js];
-    if (!(d > 0.0) || !isfinite(d)) {
+    const long long db = __double_as_longlong(d);   // positive and finite, tested on the bits
+    if (!(db > 0 && db < 0x7ff0000000000000LL)) {
       if (threadIdx.x == 0) failed[ii] = 1;
       return;
     }
-    const double inv = 1.0 / d;
+    if (threadIdx.x == 0) s_inv = 1.0 / d;   // one division per step, not one per thread
     for (int t = threadIdx.x; t < km; t += T) colj[t] = S[wrap(base + t, K) * K + js];
     __syncthreads();
+    const double inv = s_inv;
     // S(i, c) -= L'(i, j) S(c, j) for j < c <= i <= j + km: a warp per row
     for (int r = w; r < km; r += nw) {
       double* row = S + wrap(base + r, K) * K;
@@ -384,7 +387,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   __shared__ double sv[32];
   __shared__ int si[32];
   __shared__ int s_jp, s_ju, s_bad, s_badcol;
-  __shared__ double s_piv;
+  __shared__ double s_piv, s_inv;
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
 #define SEL(rs, c) S[(long long)(rs) * K2 + (c)]
 #define INBAND(i, c) ((i) < n && (c) < n && (c) - (i) <= ku && (i) - (c) <= kl)
@@ -431,6 +434,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
         s_badcol = j;
       } else {
         s_piv = p0;
+        s_inv = 1.0 / p0;   // one division per step, not one per thread
       }
       s_ju = max(s_ju, min(j + ku + i0, n - 1));
       if (s_ju - j + 1 > K2) s_bad = 2;   // fill beyond the ring
@@ -438,7 +442,7 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
     __syncthreads();
     if (s_bad) break;
     const int jp = s_jp, ju = s_ju, wd = ju - j;
-    const double piv = s_piv, inv = 1.0 / piv;
+    const double piv = s_piv, inv = s_inv;
     if (jp != 0) {
       const int pr = wrap(jr + jp, K1);
       for (int cc = threadIdx.x; cc <= wd; cc += T) {

@@ -362,10 +362,13 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread
   // CTA in shared memory, or a 512-thread CTA on a bounded global workspace
-  std::vector<int> hp(b.tot_nc + 1);
-  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
-                            cudaMemcpyDeviceToHost, st));
-  FAMS_CUDA(cudaStreamSynchronize(st));
+  if (b.h_blk_ptr.empty()) {   // primal-block sizes, fixed after setup: fetched once
+    b.h_blk_ptr.resize(b.tot_nc + 1);
+    FAMS_CUDA(cudaMemcpyAsync(b.h_blk_ptr.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
+                              cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+  }
+  const std::vector<int>& hp = b.h_blk_ptr;
   std::vector<int> cls[4];
   long long cmax[4] = {0, 0, 0, 0};
   for (int ii : list) {

@@ -270,14 +270,13 @@ int phase_system(Batch& b) {
         b.nnc_row_m, b.nnc_T, ffr_ptr, ffr_a, ffr_T, b.ff_first, b.ff_b, b.ff_T, b.rowptr, b.col,
         b.val, b.diag, b.TD, b.qD);
   FAMS_CUDA(cudaGetLastError());
-  std::vector<int> hp(nrow + 1);
-  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.rowptr, sizeof(int) * (nrow + 1), cudaMemcpyDeviceToHost,
-                            st));
-  FAMS_CUDA(cudaStreamSynchronize(st));
+  // row pointers at the instance boundaries (off_row: B + 1 row offsets)
+  std::vector<int> hp;
+  FAMS_TRY(take_ints(b, b.rowptr, b.off_row, b.B + 1, hp));
   for (int i = 0; i < b.B; ++i) {
     Inst& I = b.h[i];
-    I.nnz_off = hp[I.row_off];
-    I.nnz = hp[I.row_off + I.n] - hp[I.row_off];
+    I.nnz_off = hp[i];
+    I.nnz = hp[i + 1] - hp[i];
   }
   FAMS_TRY(b.upload_inst());
   return b.check_err("fine system");

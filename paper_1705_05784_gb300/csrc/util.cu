@@ -93,6 +93,45 @@ __global__ void k_scan_apply(const int* in, long long n, const long long* block_
 
 }  // namespace
 
+namespace {
+
+__global__ void k_take(const int* src, const int* idx, int n, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[idx[i]];
+}
+
+__global__ void k_any_negative(const int* v, long long n, int* flag) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && v[i] < 0) atomicExch(flag, 1);
+}
+
+}  // namespace
+
+int take_ints(Batch& b, const int* src, const int* idx, int n, std::vector<int>& out) {
+  out.assign(n, 0);
+  if (n <= 0) return FAMS_OK;
+  int* d = nullptr;
+  FAMS_TRY(b.scratch((void**)&d, sizeof(int) * n));
+  fams::note_launch(), k_take<<<grid_for(n, 256), 256, 0, b.stream>>>(src, idx, n, d);
+  FAMS_CUDA(cudaMemcpyAsync(out.data(), d, sizeof(int) * n, cudaMemcpyDeviceToHost, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  return FAMS_OK;
+}
+
+int any_negative(Batch& b, const int* v, long long n, bool* res) {
+  *res = false;
+  if (n <= 0) return FAMS_OK;
+  int* d = nullptr;
+  FAMS_TRY(b.scratch((void**)&d, sizeof(int)));
+  FAMS_CUDA(cudaMemsetAsync(d, 0, sizeof(int), b.stream));
+  fams::note_launch(), k_any_negative<<<grid_for(n, 256), 256, 0, b.stream>>>(v, n, d);
+  int h = 0;
+  FAMS_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));
+  *res = h != 0;
+  return FAMS_OK;
+}
+
 int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* total) {
   if (n <= 0) {
     FAMS_CUDA(cudaMemsetAsync(out, 0, sizeof(int), b.stream));
