@@ -339,6 +339,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64",
                     help="mixed: FP32 inner stages with FP64 residuals and refinement")
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
+    ap.add_argument("--restart", type=int, default=30, help="GMRES cycle length")
     ap.add_argument("--serve", type=int, default=400,
                     help="requests in the served stream (0: skip the serving measurement)")
     ap.add_argument("--pipelines", type=int, default=4, help="server: micro-batches in flight")
@@ -365,7 +366,7 @@ def main():
         cpu = cpu_baseline(args.cpu_sample)
     from paper_1705_05784_gb300 import fams
     probs = problems(args.batch, 1000 * (rank + 1), args.max_iter,
-                     krylov=1 if args.krylov == "gmres" else 0,
+                     krylov=1 if args.krylov == "gmres" else 0, restart=args.restart,
                      precision=1 if args.precision == "mixed" else 0)
     dev = torch.device("cuda", local)
     perm_d = [torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev) for p in probs]
@@ -471,7 +472,7 @@ def main():
         "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": len(probs), "cells_per_instance": S[0]["n"],
-                   "solver": ("GMRES(30)" if args.krylov == "gmres" else "Table 1 loop") + ", " +
+                   "solver": (f"GMRES({args.restart})" if args.krylov == "gmres" else "Table 1 loop") + ", " +
                              ("FP32 inner stages, FP64 residual/coarse solve/refinement"
                               if args.precision == "mixed" else "FP64"),
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 "
@@ -483,7 +484,7 @@ def main():
                      "flux_singular_fv_coarse": flux_failed[0],
                      "max_rel_residual": max(s["rel_residual"] for s in stats),
                      "iterations_median": statistics.median(iters), "iterations_max": max(iters)},
-        "roofline": {"kernel": "k_gmres (persistent GMRES(30) with the two-stage step, one CTA "
+        "roofline": {"kernel": f"k_gmres (persistent GMRES({args.restart}) with the two-stage step, one CTA "
                                "per instance)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
