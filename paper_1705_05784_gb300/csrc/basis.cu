@@ -217,10 +217,10 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
                             const int* instage,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
-                            int* ncols, const int* colptr, int* colbuf, int* err) {
+                            int* ncols, const int* colptr, int* colbuf, int* bw, int* err) {
   extern __shared__ int sm[];   // member sort buffer (mode 0), sized by the launch
   __shared__ int hs[HASH_CAP];
-  __shared__ int nuniq, known_links, ncand;
+  __shared__ int nuniq, known_links, ncand, s_bl, s_bu;
   int c = blockIdx.x;
   int a = comp_off[c], n = comp_off[c + 1] - a;
   if (n > MEMBER_SORT_MAX) {
@@ -239,18 +239,28 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { nuniq = 0; known_links = 0; ncand = 0; }
+  if (threadIdx.x == 0) { nuniq = 0; known_links = 0; ncand = 0; s_bl = 0; s_bu = 0; }
   __syncthreads();
   const Inst& I = inst_of(inst, B, off_row, members[a]);
-  // candidate columns (with repeats): the hash table gets twice as many slots
+  // candidate columns (with repeats): the hash table gets twice as many slots;
+  // mode 0 also measures the block matrix's bandwidths in member order
   bool over = false;
+  int bl = 0, bu = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int r = members[a + i];
     int mr = medium_of(I, r), rr = rank[r];
     int cand = 0, links = 0;
     for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
       int cc = col[p];
-      if (cc == r || instage[cc]) continue;
+      if (cc == r) continue;
+      if (instage[cc]) {
+        if (mode == 0 &&
+            keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) {
+          bl = max(bl, i - pos[cc]);
+          bu = max(bu, pos[cc] - i);
+        }
+        continue;
+      }
       if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) continue;
       ++links;
       if (pstage[cc] < 0) { over = true; continue; }
@@ -260,7 +270,15 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     if (cand) atomicAdd(&ncand, cand);
   }
   if (over) atomicCAS(err, 0, DERR_INVAL);
+  if (mode == 0) {
+    atomicMax(&s_bl, bl);
+    atomicMax(&s_bu, bu);
+  }
   __syncthreads();
+  if (mode == 0 && threadIdx.x == 0) {
+    bw[2 * c] = s_bl;
+    bw[2 * c + 1] = s_bu;
+  }
   int H = 32;
   while (H < 2 * ncand && H < HASH_CAP) H <<= 1;
   for (int i = threadIdx.x; i < H; i += blockDim.x) hs[i] = -1;
@@ -333,6 +351,7 @@ struct CompArgs {
   const int* pos;
   const int* colptr;
   const int* colbuf;
+  const int* bw;             // per block: lower and upper bandwidth in member order
   const long long* pool_off;
   int* pstage;
   int* poff;
@@ -344,20 +363,21 @@ struct CompArgs {
   int* err;
 };
 
-// one dual block on a thread group: assemble [A'_BB | right-hand sides] with
-// leading dimension n + k (then n doubles of pivot reciprocals), eliminate,
-// write the block's rows of P
+// one dual block on a thread group: assemble [A'_BB | right-hand sides] in
+// band storage, W = bl + bu + 1 band entries then k right-hand sides per row
+// (then n doubles of pivot reciprocals), eliminate, write the block's rows of P
 template <class G>
 __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
+  (void)red;
   const int gr = G::rank(), gs = G::size();
   const int a0 = a.comp_off[c], n = a.comp_off[c + 1] - a0;
   const int k = a.colptr[c + 1] - a.colptr[c];
-  const int ld = n + k;
+  const int bl = a.bw[2 * c], bu = a.bw[2 * c + 1], W = bl + bu + 1;
+  const int ld = W + k;
   const int* cols = a.colbuf + a.colptr[c];
   const Inst& I = inst_of(a.inst, a.B, a.off_row, a.members[a0]);
   for (long long t = gr; t < (long long)n * ld; t += gs) M[t] = 0.0;
   G::sync();
-  int bl = 0, bu = 0;   // bandwidths of A'_BB in member order
   for (int i = gr; i < n; i += gs) {
     int r = a.members[a0 + i];
     int mr = medium_of(I, r), rr = a.rank[r];
@@ -371,10 +391,8 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
       if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, r, cc))) {
         if (a.instage[cc]) {
           int pc = a.pos[cc];
-          if (pc < 0 || pc >= n) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
-          Mi[pc] = av;
-          bl = max(bl, i - pc);
-          bu = max(bu, pc - i);
+          if (pc < 0 || pc >= n || i - pc > bl || pc - i > bu) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
+          Mi[pc - i + bl] = av;
         } else {
           int st = a.pstage[cc];
           const int* pc = a.pool.col[st] + a.poff[cc];
@@ -382,17 +400,15 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
           for (int q = 0; q < a.plen[cc]; ++q) {
             int j = find_col(cols, k, pc[q]);
             if (j < 0) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
-            Mi[n + j] += T * pv[q];
+            Mi[W + j] += T * pv[q];
           }
         }
       } else {
         d -= T;
       }
     }
-    Mi[i] = d;
+    Mi[bl] = d;
   }
-  bl = G::max(bl, red);
-  bu = G::max(bu, red);
   G::sync();
   if (!ge_solve<G>(M, ld, n, k, bl, bu, M + (long long)n * ld)) {
     if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
@@ -402,7 +418,7 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
   for (int t = gr; t < n * k; t += gs) {
     int i = t / k, q = t - i * k;
     a.out_col[base + t] = cols[q];
-    a.out_val[base + t] = M[(long long)i * ld + n + q];
+    a.out_val[base + t] = M[(long long)i * ld + W + q];
   }
   for (int i = gr; i < n; i += gs) {
     int r = a.members[a0 + i];
@@ -552,6 +568,8 @@ int phase_basis(Batch& b) {
     FAMS_TRY(b.scratch((void**)&coff, sizeof(int) * (ncomp + 1)));
     FAMS_TRY(b.scratch((void**)&cursor, sizeof(int) * (ncomp + 1)));
     FAMS_TRY(b.scratch((void**)&ncols, sizeof(int) * (ncomp + 1)));
+    int* bw = nullptr;
+    FAMS_TRY(b.scratch((void**)&bw, sizeof(int) * 2 * (ncomp + 1)));
     FAMS_TRY(b.scratch((void**)&colptr, sizeof(int) * (ncomp + 1)));
     FAMS_CUDA(cudaMemsetAsync(size, 0, sizeof(int) * (ncomp + 1), st));
     FAMS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (ncomp + 1), st));
@@ -574,7 +592,7 @@ int phase_basis(Batch& b) {
     }
     fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
-                                            s, 0, ncols, nullptr, nullptr, b.d_err);
+                                            s, 0, ncols, nullptr, nullptr, bw, b.d_err);
     FAMS_CUDA(cudaGetLastError());
     FAMS_TRY(b.check_err("dual-block columns"));
     long long totc = 0;
@@ -582,18 +600,21 @@ int phase_basis(Batch& b) {
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
     fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
-                                            s, 1, ncols, colptr, colbuf, b.d_err);
+                                            s, 1, ncols, colptr, colbuf, nullptr, b.d_err);
     // host plan: pool offsets, and the blocks by size class (doubles of
     // [A'_BB | R]): one warp, a 128-thread CTA, a 256-thread CTA in shared
     // memory, or a 512-thread CTA on a bounded global workspace
+    std::vector<int> hbw(2 * ncomp);
     FAMS_CUDA(cudaMemcpyAsync(hk.data(), ncols, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaMemcpyAsync(hbw.data(), bw, sizeof(int) * 2 * ncomp, cudaMemcpyDeviceToHost, st));
     FAMS_CUDA(cudaStreamSynchronize(st));
     std::vector<long long> hpo(ncomp + 1, 0);
     std::vector<int> cls[4];
     long long cmax[4] = {0, 0, 0, 0};
     for (long long c = 0; c < ncomp; ++c) {
       hpo[c + 1] = hpo[c] + (long long)hs[c] * hk[c];
-      long long need = (long long)hs[c] * ((long long)hs[c] + hk[c] + 1);   // [A'_BB | R], pivots
+      // band and right-hand sides of every row, pivot reciprocals
+      long long need = (long long)hs[c] * ((long long)hbw[2 * c] + hbw[2 * c + 1] + 2 + hk[c]);
       int q = need <= WARP_NEED ? 0 : need <= MID_NEED ? 1 : need * 8 + 1024 <= max_smem ? 2 : 3;
       cls[q].push_back((int)c);
       cmax[q] = std::max(cmax[q], need);
@@ -615,7 +636,7 @@ int phase_basis(Batch& b) {
     pool.col[s] = ocol;
     pool.val[s] = oval;
     CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col, b.val, b.TD, instage,
-                nullptr, 0, coff, members, pos, colptr, colbuf, pool_off, pstage, poff, plen,
+                nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};
     long long lo = 0;
     for (int q = 0; q < 4; ++q) {

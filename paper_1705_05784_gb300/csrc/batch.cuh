@@ -133,6 +133,8 @@ struct Batch {
   int* blk_ptr = nullptr;      // cells of each primal block (global coarse index)
   int* blk_cell = nullptr;
   std::vector<int> h_blk_ptr;  // host copy of blk_ptr (taken on the first reconstruction)
+  int* blk_bw = nullptr;       // per primal block: bandwidths of its local problem
+  std::vector<int> h_blk_bw;
   // ---- coarse system: [0] the iteration's restriction, [1] R^FV for the
   // flux reconstruction when the iteration uses R^FE ----
   CoarseSys cs[2];

@@ -106,20 +106,52 @@ struct LocalArgs {
   const int* node_cell;
   const double* pp;
   double* pt;
+  const int* bw;   // per primal block: lower and upper bandwidth in block order
   int* err;
 };
+
+// bandwidths of each primal block's local matrix in block order (cells in
+// ascending index): one thread per block
+__global__ void k_blk_band(const int* blk_ptr, const int* blk_cell, int nblk, const int* rowptr,
+                           const int* col, const int* primal, int* bw) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nblk) return;
+  const int a0 = blk_ptr[c], m = blk_ptr[c + 1] - a0;
+  int bl = 0, bu = 0;
+  for (int t = 0; t < m; ++t) {
+    const int i = blk_cell[a0 + t];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int j = col[p];
+      if (j == i || primal[j] != primal[i]) continue;
+      int lo = 0, hi = m - 1, pos = -1;
+      while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = blk_cell[a0 + mid];
+        if (v == j) { pos = mid; break; }
+        if (v < j) lo = mid + 1; else hi = mid - 1;
+      }
+      if (pos < 0) continue;
+      bl = max(bl, t - pos);
+      bu = max(bu, pos - t);
+    }
+  }
+  bw[2 * c] = bl;
+  bw[2 * c + 1] = bu;
+}
 
 template <class G>
 __device__ void flux_local(const LocalArgs& a, int c, double* K, int* red) {
   const int gr = G::rank(), gs = G::size();
   const Inst& I = a.inst[find_segment(a.off_nc, a.B + 1, c)];
   const int a0 = a.blk_ptr[c], m = a.blk_ptr[c + 1] - a0;
-  const int ld = m + 1;
+  // band storage: W band entries, then the right-hand side
+  const int bl = a.bw[2 * c], bu = a.bw[2 * c + 1], W = bl + bu + 1;
+  const int ld = W + 1;
+  (void)red;
   for (long long t = gr; t < (long long)m * ld; t += gs) K[t] = 0.0;
   G::sync();
   const int myblk = c - I.nc_off;
   bool hasD = false;
-  int bl = 0, bu = 0;   // bandwidths of K in block order
   for (int t = gr; t < m; t += gs) {
     int i = a.blk_cell[a0 + t];
     double* Kt = K + (long long)t * ld;
@@ -138,17 +170,15 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K, int* red) {
           if (v == j) { pos = mid; break; }
           if (v < j) lo = mid + 1; else hi = mid - 1;
         }
-        if (pos < 0) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
-        Kt[pos] -= T;
+        if (pos < 0 || t - pos > bl || pos - t > bu) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
+        Kt[pos - t + bl] -= T;
         d += T;
-        bl = max(bl, t - pos);
-        bu = max(bu, pos - t);
       } else {
         b -= T * (a.pp[i] - a.pp[j]);
       }
     }
-    Kt[t] += d;
-    Kt[m] = b;
+    Kt[bl] += d;
+    Kt[W] = b;
   }
   // pin the coarse node unless a Dirichlet face closes the block
   bool anyD = G::per_warp ? __any_sync(0xffffffffu, hasD) : __syncthreads_or(hasD);
@@ -163,16 +193,14 @@ __device__ void flux_local(const LocalArgs& a, int c, double* K, int* red) {
     }
     G::sync();
     double* Kp = K + (long long)pos * ld;
-    for (int j = gr; j <= m; j += gs) Kp[j] = j == pos ? 1.0 : (j == m ? a.pp[v] : 0.0);
+    for (int j = gr; j <= W; j += gs) Kp[j] = j == bl ? 1.0 : (j == W ? a.pp[v] : 0.0);
   }
-  bl = G::max(bl, red);
-  bu = G::max(bu, red);
   G::sync();
   if (!ge_solve<G>(K, ld, m, 1, bl, bu, K + (long long)m * ld)) {
     if (gr == 0) atomicCAS(a.err, 0, DERR_BREAKDOWN);
     return;
   }
-  for (int t = gr; t < m; t += gs) a.pt[a.blk_cell[a0 + t]] = K[(long long)t * ld + m];
+  for (int t = gr; t < m; t += gs) a.pt[a.blk_cell[a0 + t]] = K[(long long)t * ld + W];
 }
 
 // primal blocks of the listed instances: one warp each (WarpGroup, several
@@ -362,20 +390,29 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread
   // CTA in shared memory, or a 512-thread CTA on a bounded global workspace
-  if (b.h_blk_ptr.empty()) {   // primal-block sizes, fixed after setup: fetched once
+  if (b.h_blk_ptr.empty()) {   // primal-block sizes and bandwidths, fixed after setup: once
     b.h_blk_ptr.resize(b.tot_nc + 1);
+    b.h_blk_bw.resize(2 * (b.tot_nc + 1));
+    FAMS_TRY(b.alloc((void**)&b.blk_bw, sizeof(int) * 2 * (b.tot_nc + 1)));
+    if (b.tot_nc > 0)
+      fams::note_launch(), k_blk_band<<<grid_for(b.tot_nc, 128), 128, 0, st>>>(
+          b.blk_ptr, b.blk_cell, (int)b.tot_nc, b.rowptr, b.col, b.primal, b.blk_bw);
     FAMS_CUDA(cudaMemcpyAsync(b.h_blk_ptr.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
+                              cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaMemcpyAsync(b.h_blk_bw.data(), b.blk_bw, sizeof(int) * 2 * b.tot_nc,
                               cudaMemcpyDeviceToHost, st));
     FAMS_CUDA(cudaStreamSynchronize(st));
   }
   const std::vector<int>& hp = b.h_blk_ptr;
+  const std::vector<int>& hbw = b.h_blk_bw;
   std::vector<int> cls[4];
   long long cmax[4] = {0, 0, 0, 0};
   for (int ii : list) {
     const Inst& I = b.h[ii];
     for (int c = I.nc_off; c < I.nc_off + I.nc; ++c) {
       long long m = hp[c + 1] - hp[c];
-      long long need = m * (m + 2);   // [K | rhs], pivot reciprocals
+      // band and right-hand side of every row, pivot reciprocals
+      long long need = m * ((long long)hbw[2 * c] + hbw[2 * c + 1] + 3);
       int q = need <= LOCAL_WARP_NEED ? 0 : need <= LOCAL_MID_NEED ? 1
             : need * 8 <= max_smem ? 2 : 3;
       cls[q].push_back(c);
@@ -385,7 +422,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   int* lst = nullptr;
   FAMS_TRY(b.scratch((void**)&lst, sizeof(int) * (b.tot_nc + 1)));
   LocalArgs la{b.d_inst, b.B, b.off_nc, nullptr, 0, b.blk_ptr, b.blk_cell, b.rowptr, b.col,
-               b.val, b.TD, b.q, b.primal, b.node_cell, pp, pt, b.d_err};
+               b.val, b.TD, b.q, b.primal, b.node_cell, pp, pt, b.blk_bw, b.d_err};
   long long lo = 0;
   for (int q = 0; q < 4; ++q) {
     if (cls[q].empty()) continue;
