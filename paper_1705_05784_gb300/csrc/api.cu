@@ -265,6 +265,10 @@ void destroy_batch(Batch& b) {
   if (b.side_done) cudaEventDestroy(b.side_done);
   b.side = nullptr;
   b.side_done = nullptr;
+  for (int i = 0; i < 3; ++i)
+    if (b.fk_st[i]) cudaStreamDestroy(b.fk_st[i]);
+  for (int i = 0; i < 4; ++i)
+    if (b.fk_ev[i]) cudaEventDestroy(b.fk_ev[i]);
   if (b.aux) cudaStreamDestroy(b.aux);
   if (b.aux_ev) cudaEventDestroy(b.aux_ev);
   if (b.aux_done) cudaEventDestroy(b.aux_done);

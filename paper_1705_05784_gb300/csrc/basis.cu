@@ -638,41 +638,54 @@ int phase_basis(Batch& b) {
     CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col, b.val, b.TD, instage,
                 nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};
+    // the size classes are disjoint sets of blocks: lists and workspace on the
+    // main stream, then each class on its own stream so their tails overlap
+    int* lsts[4] = {nullptr, nullptr, nullptr, nullptr};
     long long lo = 0;
     for (int q = 0; q < 4; ++q) {
       if (cls[q].empty()) continue;
-      int* lst = clist + lo;
-      FAMS_CUDA(cudaMemcpyAsync(lst, cls[q].data(), sizeof(int) * cls[q].size(),
+      lsts[q] = clist + lo;
+      FAMS_CUDA(cudaMemcpyAsync(lsts[q], cls[q].data(), sizeof(int) * cls[q].size(),
                                 cudaMemcpyHostToDevice, st));
       lo += (long long)cls[q].size();
+    }
+    // bounded workspace of the global-memory class: at most ~1 GiB per launch
+    const long long per3 = std::max(1LL, (1LL << 27) / std::max(cmax[3], 1LL));
+    double* work = nullptr;
+    if (!cls[3].empty())
+      FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] *
+                                            std::min(per3, (long long)cls[3].size())));
+    cudaStream_t cst[4] = {st, st, st, st};
+    FAMS_TRY(fork_streams(b, 3, cst + 1));
+    for (int q = 0; q < 4; ++q) {
+      if (cls[q].empty()) continue;
+      int* lst = lsts[q];
       long long cnt = (long long)cls[q].size();
+      cudaStream_t qs = cst[q];
       if (q == 0) {
         long long slice = (cmax[0] + 3) & ~3LL;
         ca.comp_list = lst;
         ca.ncomp = cnt;
         fams::note_launch(),
             k_comp_solve<WarpGroup><<<(int)((cnt + CTA_WARPS - 1) / CTA_WARPS), 32 * CTA_WARPS,
-                                      sizeof(double) * slice * CTA_WARPS, st>>>(ca, slice, nullptr);
+                                      sizeof(double) * slice * CTA_WARPS, qs>>>(ca, slice, nullptr);
       } else if (q < 3) {
         ca.comp_list = lst;
         ca.ncomp = cnt;
         fams::note_launch(),
-            k_comp_solve<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], st>>>(
+            k_comp_solve<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], qs>>>(
                 ca, cmax[q], nullptr);
       } else {
-        // bounded workspace: at most ~1 GiB of dense blocks per launch
-        long long per = std::max(1LL, (1LL << 27) / std::max(cmax[3], 1LL));
-        double* work = nullptr;
-        FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] * std::min(per, cnt)));
-        for (long long o = 0; o < cnt; o += per) {
+        for (long long o = 0; o < cnt; o += per3) {
           ca.comp_list = lst + o;
-          ca.ncomp = std::min(per, cnt - o);
+          ca.ncomp = std::min(per3, cnt - o);
           fams::note_launch(),
-              k_comp_solve<CtaGroup><<<(int)ca.ncomp, 512, 0, st>>>(ca, cmax[3], work);
+              k_comp_solve<CtaGroup><<<(int)ca.ncomp, 512, 0, qs>>>(ca, cmax[3], work);
         }
       }
       FAMS_CUDA(cudaGetLastError());
     }
+    FAMS_TRY(join_streams(b, 3));
     FAMS_TRY(b.check_err("dual-block solves"));
   }
   // every row must have a basis row

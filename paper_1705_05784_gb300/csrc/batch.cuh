@@ -46,6 +46,8 @@ struct Batch {
   cudaEvent_t side_done = nullptr;
   cudaStream_t aux = nullptr;         // concurrent band LU passes of disjoint instance sets
   cudaEvent_t aux_ev = nullptr, aux_done = nullptr;
+  cudaStream_t fk_st[3] = {nullptr, nullptr, nullptr};   // size classes of local solves
+  cudaEvent_t fk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool prepare_flux = false;          // some instance asked for it (fams_opts.prepare_flux)
   int device = 0;
   std::vector<Inst> h;          // host copy of the descriptors
@@ -231,6 +233,10 @@ int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* to
 int take_ints(Batch& b, const int* src, const int* idx, int n, std::vector<int>& out);
 // whether any of v[0..n) is negative
 int any_negative(Batch& b, const int* v, long long n, bool* res);
+// k (<= 3) extra streams that start after the work queued on b.stream so far,
+// and the join that makes b.stream wait for them
+int fork_streams(Batch& b, int k, cudaStream_t* out);
+int join_streams(Batch& b, int k);
 int sort_segments(Batch& b, const int* ptr, int nseg, int* key, double* val, bool strict);
 int transpose(Batch& b, const int* rowptr, const int* col, const double* val, int nrows,
               int ncols, long long nnz, int** tptr, int** tcol, double** tval, bool keep);

@@ -423,13 +423,29 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_TRY(b.scratch((void**)&lst, sizeof(int) * (b.tot_nc + 1)));
   LocalArgs la{b.d_inst, b.B, b.off_nc, nullptr, 0, b.blk_ptr, b.blk_cell, b.rowptr, b.col,
                b.val, b.TD, b.q, b.primal, b.node_cell, pp, pt, b.blk_bw, b.d_err};
+  // disjoint size classes: lists and workspace on the main stream, then each
+  // class on its own stream so that their tails overlap
+  int* ls[4] = {nullptr, nullptr, nullptr, nullptr};
   long long lo = 0;
   for (int q = 0; q < 4; ++q) {
     if (cls[q].empty()) continue;
+    ls[q] = lst + lo;
+    lo += (long long)cls[q].size();
+    FAMS_CUDA(cudaMemcpyAsync(ls[q], cls[q].data(), sizeof(int) * cls[q].size(),
+                              cudaMemcpyHostToDevice, st));
+  }
+  const long long per3 = std::max(1LL, (1LL << 26) / std::max(cmax[3], 1LL));
+  double* work = nullptr;
+  if (!cls[3].empty())
+    FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] *
+                                          std::min(per3, (long long)cls[3].size())));
+  cudaStream_t cst[4] = {st, st, st, st};
+  FAMS_TRY(fork_streams(b, 3, cst + 1));
+  for (int q = 0; q < 4; ++q) {
+    if (cls[q].empty()) continue;
     long long cnt = (long long)cls[q].size();
-    int* l = lst + lo;
-    lo += cnt;
-    FAMS_CUDA(cudaMemcpyAsync(l, cls[q].data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
+    int* l = ls[q];
+    cudaStream_t qs = cst[q];
     la.blk_list = l;
     la.nblk = cnt;
     if (q == 0) {
@@ -437,25 +453,23 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
       fams::note_launch(),
           k_flux_local<WarpGroup><<<(int)((cnt + LOCAL_CTA_WARPS - 1) / LOCAL_CTA_WARPS),
                                     32 * LOCAL_CTA_WARPS,
-                                    sizeof(double) * slice * LOCAL_CTA_WARPS, st>>>(la, slice,
+                                    sizeof(double) * slice * LOCAL_CTA_WARPS, qs>>>(la, slice,
                                                                                   nullptr);
     } else if (q < 3) {
       fams::note_launch(),
-          k_flux_local<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], st>>>(
+          k_flux_local<CtaGroup><<<(int)cnt, q == 1 ? 128 : 256, sizeof(double) * cmax[q], qs>>>(
               la, cmax[q], nullptr);
     } else {
-      long long per = std::max(1LL, (1LL << 26) / std::max(cmax[3], 1LL));
-      double* work = nullptr;
-      FAMS_TRY(b.scratch((void**)&work, sizeof(double) * cmax[3] * std::min(per, cnt)));
-      for (long long o = 0; o < cnt; o += per) {
+      for (long long o = 0; o < cnt; o += per3) {
         la.blk_list = l + o;
-        la.nblk = std::min(per, cnt - o);
+        la.nblk = std::min(per3, cnt - o);
         fams::note_launch(),
-            k_flux_local<CtaGroup><<<(int)la.nblk, 512, 0, st>>>(la, cmax[3], work);
+            k_flux_local<CtaGroup><<<(int)la.nblk, 512, 0, qs>>>(la, cmax[3], work);
       }
     }
     FAMS_CUDA(cudaGetLastError());
   }
+  FAMS_TRY(join_streams(b, 3));
   FAMS_CUDA(cudaGetLastError());
   long long* dfo = nullptr;
   long long* dno = nullptr;

@@ -132,6 +132,28 @@ int any_negative(Batch& b, const int* v, long long n, bool* res) {
   return FAMS_OK;
 }
 
+int fork_streams(Batch& b, int k, cudaStream_t* out) {
+  if (!b.fk_ev[3]) FAMS_CUDA(cudaEventCreateWithFlags(&b.fk_ev[3], cudaEventDisableTiming));
+  FAMS_CUDA(cudaEventRecord(b.fk_ev[3], b.stream));
+  for (int i = 0; i < k; ++i) {
+    if (!b.fk_st[i]) {
+      FAMS_CUDA(cudaStreamCreateWithFlags(&b.fk_st[i], cudaStreamNonBlocking));
+      FAMS_CUDA(cudaEventCreateWithFlags(&b.fk_ev[i], cudaEventDisableTiming));
+    }
+    FAMS_CUDA(cudaStreamWaitEvent(b.fk_st[i], b.fk_ev[3], 0));
+    out[i] = b.fk_st[i];
+  }
+  return FAMS_OK;
+}
+
+int join_streams(Batch& b, int k) {
+  for (int i = 0; i < k; ++i) {
+    FAMS_CUDA(cudaEventRecord(b.fk_ev[i], b.fk_st[i]));
+    FAMS_CUDA(cudaStreamWaitEvent(b.stream, b.fk_ev[i], 0));
+  }
+  return FAMS_OK;
+}
+
 int exclusive_scan(Batch& b, const int* in, int* out, long long n, long long* total) {
   if (n <= 0) {
     FAMS_CUDA(cudaMemsetAsync(out, 0, sizeof(int), b.stream));
