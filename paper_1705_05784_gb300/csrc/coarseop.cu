@@ -628,7 +628,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   if (ldl_smem > 0) {
     FAMS_CUDA(cudaFuncSetAttribute(k_band_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    max_smem));
-    fams::note_launch(), k_band_ldl<<<B, 256, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu);
+    fams::note_launch(), k_band_ldl<<<B, 512, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu);
     FAMS_CUDA(cudaGetLastError());
     std::vector<int> failed(B, 0);
     FAMS_CUDA(cudaMemcpyAsync(failed.data(), d_lu, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
