@@ -306,9 +306,31 @@ __global__ void k_flux_nnc(const Inst* inst, const int* list, int nlist, const l
 
 }  // namespace
 
+// primal-block sizes and the bandwidths of their local problems, fixed after
+// setup: computed once, kept on the host for the size classes
+int local_bands(Batch& b) {
+  if (!b.h_blk_ptr.empty()) return FAMS_OK;
+  cudaStream_t st = b.stream;
+  std::vector<int> hp(b.tot_nc + 1), hbw(2 * (b.tot_nc + 1), 0);
+  FAMS_TRY(b.alloc((void**)&b.blk_bw, sizeof(int) * 2 * (b.tot_nc + 1)));
+  if (b.tot_nc > 0)
+    fams::note_launch(), k_blk_band<<<grid_for(b.tot_nc, 128), 128, 0, st>>>(
+        b.blk_ptr, b.blk_cell, (int)b.tot_nc, b.rowptr, b.col, b.primal, b.blk_bw);
+  FAMS_CUDA(cudaGetLastError());
+  FAMS_CUDA(cudaMemcpyAsync(hp.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
+                            cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaMemcpyAsync(hbw.data(), b.blk_bw, sizeof(int) * 2 * b.tot_nc,
+                            cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  b.h_blk_bw.swap(hbw);
+  b.h_blk_ptr.swap(hp);
+  return FAMS_OK;
+}
+
 // The R^FV coarse system of the reconstruction: the iteration's own when every
 // instance iterates with R^FV, otherwise a second one built on first use.
 int flux_prepare(Batch& b, const CoarseHost** ch) {
+  FAMS_TRY(local_bands(b));
   bool all_fv = true;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
   if (all_fv) {
@@ -336,7 +358,7 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
 int flux_beside(Batch& b, cudaEvent_t ready) {
   bool all_fv = true;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
-  if (all_fv || b.fv_ready) return FAMS_OK;
+  if ((all_fv || b.fv_ready) && !b.h_blk_ptr.empty()) return FAMS_OK;
   if (!b.side) {
     FAMS_CUDA(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
     FAMS_CUDA(cudaEventCreateWithFlags(&b.side_done, cudaEventDisableTiming));
@@ -390,20 +412,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread
   // CTA in shared memory, or a 512-thread CTA on a bounded global workspace
-  if (b.h_blk_ptr.empty()) {   // primal-block sizes and bandwidths, fixed after setup: once
-    b.h_blk_ptr.resize(b.tot_nc + 1);
-    b.h_blk_bw.resize(2 * (b.tot_nc + 1));
-    FAMS_TRY(b.alloc((void**)&b.blk_bw, sizeof(int) * 2 * (b.tot_nc + 1)));
-    if (b.tot_nc > 0)
-      fams::note_launch(), k_blk_band<<<grid_for(b.tot_nc, 128), 128, 0, st>>>(
-          b.blk_ptr, b.blk_cell, (int)b.tot_nc, b.rowptr, b.col, b.primal, b.blk_bw);
-    FAMS_CUDA(cudaMemcpyAsync(b.h_blk_ptr.data(), b.blk_ptr, sizeof(int) * (b.tot_nc + 1),
-                              cudaMemcpyDeviceToHost, st));
-    FAMS_CUDA(cudaMemcpyAsync(b.h_blk_bw.data(), b.blk_bw, sizeof(int) * 2 * b.tot_nc,
-                              cudaMemcpyDeviceToHost, st));
-    FAMS_CUDA(cudaStreamSynchronize(st));
-  }
-  const std::vector<int>& hp = b.h_blk_ptr;
+  const std::vector<int>& hp = b.h_blk_ptr;   // filled by flux_prepare
   const std::vector<int>& hbw = b.h_blk_bw;
   std::vector<int> cls[4];
   long long cmax[4] = {0, 0, 0, 0};
