@@ -268,26 +268,43 @@ def sizes_of(ctx, i):
                 nc=sz["n_coarse"], ldab=int(2 * kl + ku + 1), faces=sz["n_faces"], nnc=sz["n_nnc"])
 
 
-def cpu_baseline(sample):
-    """The FP64 oracle on `sample` instances of the same workload, one core."""
-    code = f"""
-import sys, time, json, numpy as np, warnings
-warnings.simplefilter('ignore')
-sys.path.insert(0, {ROOT!r})
-import bench, oracle
-from oracle import solver as osolver
-probs = bench.problems({sample}, 9000)
-t = time.perf_counter()
-for p in probs:
+ORACLE_SEED = 9000   # instances of the oracle baseline (same workload recipe)
+
+
+def _oracle_one(i, keep=False):
+    """The oracle on instance i of the baseline sample: setup, solve to TOL,
+    flux reconstruction.  Returns (seconds, x, connection fluxes) or seconds."""
+    import warnings
+    warnings.simplefilter("ignore")
+    import oracle
+    from oracle import solver as osolver
+    p = problems(i + 1, ORACLE_SEED)[i]
+    t = time.perf_counter()
     g, sysm, c, P, st = oracle.build(p)
     if p.krylov == 1:
-        x, it, rr, ok, _ = osolver.gmres_solve(st, tol={TOL}, max_iter=p.max_iter,
-                                               restart=p.restart)
+        x, it, rr, ok, _ = osolver.gmres_solve(st, tol=TOL, max_iter=p.max_iter, restart=p.restart)
     else:
-        x, it, rr, ok, _ = osolver.two_stage_solve(st, tol={TOL}, max_iter=p.max_iter)
+        x, it, rr, ok, _ = osolver.two_stage_solve(st, tol=TOL, max_iter=p.max_iter)
     st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
-    osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
-print(json.dumps({{"seconds": time.perf_counter() - t}}))
+    flux, dflux, _, _ = osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
+    sec = time.perf_counter() - t
+    return (sec, x, flux) if keep else sec
+
+
+def cpu_baseline(sample, all_cores=True):
+    """The FP64 oracle on `sample` instances of the same workload, one core;
+    then one instance per host core at once (the throughput of the host).  The
+    single-core run keeps its solutions and fluxes for the error of the GPU
+    path against the oracle (`out["_ref"]`, an .npz path)."""
+    import tempfile
+    ref = os.path.join(tempfile.gettempdir(), f"fams_oracle_ref_{os.getpid()}.npz")
+    code = f"""
+import sys, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+import bench
+res = [bench._oracle_one(i, keep=True) for i in range({sample})]
+np.savez({ref!r}, **{{f"x{{i}}": r[1] for i, r in enumerate(res)}}, **{{f"f{{i}}": r[2] for i, r in enumerate(res)}})
+print(json.dumps({{"seconds": sum(r[0] for r in res)}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
@@ -295,22 +312,88 @@ print(json.dumps({{"seconds": time.perf_counter() - t}}))
         return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                 "sample": f"failed: {r.stderr[-300:]}"}
     sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
-    return {"value": sample / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample} instance(s) of the workload (setup + solve to 1e-8 + flux), "
-                      f"{sec:.1f} s single-threaded"}
+    out = {"value": sample / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "sample": f"{sample} instance(s) of the workload (setup + solve to 1e-8 + flux), "
+                     f"{sec:.1f} s single-threaded", "_ref": ref}
+    ncores = os.cpu_count() or 1
+    if all_cores and ncores > 1:
+        code = f"""
+import sys, json, time, multiprocessing as mp
+sys.path.insert(0, {ROOT!r})
+import bench
+if __name__ == "__main__":
+    with mp.get_context("spawn").Pool({ncores}) as pool:
+        pool.map(bench._oracle_one, [0] * {ncores})   # imports and page-in
+        t = time.perf_counter()
+        pool.map(bench._oracle_one, list(range({ncores})))
+        print(json.dumps({{"seconds": time.perf_counter() - t}}))
+"""
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        if r.returncode == 0:
+            wall = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+            out["all_cores"] = {"value": ncores / wall, "unit": "solves/s", "cores": ncores,
+                                "sample": f"{ncores} instances, one per process, {wall:.1f} s wall"}
+    return out
+
+
+def conn_fluxes(p, face, nnc):
+    """GPU face and NNC fluxes in the oracle's connection order: interior x,
+    y (and z) faces, then the matrix-fracture and fracture-fracture links."""
+    import numpy as np
+    nz = p.nz if p.dim == 3 else 1
+    nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
+    parts = [face[:nfx].reshape(nz, p.ny, p.nx + 1)[:, :, 1:-1].ravel(),
+             face[nfx:nfx + nfy].reshape(nz, p.ny + 1, p.nx)[:, 1:-1, :].ravel()]
+    if p.dim == 3:
+        parts.append(face[nfx + nfy:].reshape(nz + 1, p.ny, p.nx)[1:-1].ravel())
+    return np.concatenate(parts + [nnc])
+
+
+def oracle_error(fams, cpu, sample):
+    """The GPU path on the oracle baseline's instances against the oracle's
+    results (both converged to TOL): relative L2 error of the pressure and
+    largest flux difference relative to the largest flux."""
+    import numpy as np
+    ref = cpu.pop("_ref", None) if cpu else None
+    if not ref or not os.path.exists(ref):
+        return None
+    try:
+        d = np.load(ref)
+        probs = problems(sample, ORACLE_SEED)
+        ex, ef = 0.0, 0.0
+        with fams.Context(probs) as c:
+            xs, st = c.solve(tol=TOL)
+            for i, p in enumerate(probs):
+                face, nnc = c.flux(xs[i], i)
+                xo, fo = d[f"x{i}"], d[f"f{i}"]
+                ex = max(ex, float(np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo)))
+                ef = max(ef, float(np.abs(conn_fluxes(p, face, nnc) - fo).max() / np.abs(fo).max()))
+        return {"instances": sample, "pressure_rel_l2": ex, "flux_rel_max": ef,
+                "note": "GPU and oracle each converged to rel. residual 1e-8"}
+    except Exception as e:   # a failed comparison is reported, not fatal
+        return {"error": str(e)[:200]}
+    finally:
+        os.remove(ref)
 
 
 def run_reference(args, rank):
     """--impl reference: the oracle, as it stands, on the host cores."""
     if rank != 0:
         return
+
+    def step():
+        # seconds of one instance inside the oracle process (its start-up excluded)
+        out = cpu_baseline(1, all_cores=False)
+        ref = out.pop("_ref", None)
+        if ref and os.path.exists(ref):
+            os.remove(ref)
+        if not out.get("value"):
+            raise RuntimeError(out.get("sample", "oracle run failed"))
+        return 1.0 / out["value"]
+
     for _ in range(args.warmup):
-        cpu_baseline(1)
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        cpu_baseline(1)
-        times.append(time.perf_counter() - t)
+        step()
+    times = [step() for _ in range(args.steps)]
     tot = sum(times)
     v = args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
@@ -465,6 +548,8 @@ def main():
     achieved = byts / (k_ms / 1000.0) / 1e9
     if rank != 0:
         return
+    oracle_err = oracle_error(fams, cpu, args.cpu_sample) if cpu else None
+    cells = sum(S[i]["n"] for i, s in enumerate(stats) if s["converged"])
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -493,10 +578,12 @@ def main():
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else
                                     "fallback 6800 GB/s"},
         "cpu_baseline": cpu,
+        "oracle_error": oracle_err,
         "e2e": {"value": converged * args.steps / (e2e_ms / 1000.0), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "cells_per_s": cells * world * args.steps / (total_ms / 1000.0),
     }
     if args.serve > 0:
         sv = serving(fams, args.serve, args.plain, 7000, args.pipelines, args.max_batch)
