@@ -43,3 +43,19 @@ def test_binding_loads_and_reports_missing_gpu_loudly():
     with pytest.raises(fams.FamsError) as e:
         fams.Context(inputs.config_2d_small())
     assert e.value.status == fams.ECUDA
+
+
+def test_argument_checks_need_no_gpu():
+    """Null and empty arguments are rejected before any CUDA call."""
+    from paper_1705_05784_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(f"no CUDA toolkit: {e}")
+    lib = ctypes.CDLL(path)
+    ctx = ctypes.c_void_p()
+    assert lib.fams_setup_batch(0, None, None, None, None, ctypes.byref(ctx)) == -1   # FAMS_EINVAL
+    assert lib.fams_setup(None, None, None, None, ctypes.byref(ctx)) == -1
+    assert lib.fams_solve(None, None, None, ctypes.c_double(1e-8), None) == -1
+    assert lib.fams_flux(None, 0, None, None, None) == -1
+    assert lib.fams_update(None, None) == -1

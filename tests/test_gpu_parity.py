@@ -527,6 +527,52 @@ def test_flux_reports_a_singular_fv_coarse_system():
         assert e.value.status == fams.EBREAKDOWN
 
 
+def _degenerate(dim, nx, ny, nz, coarsen, seed=3):
+    shape = (nx, ny) if dim == 2 else (nx, ny, nz)
+    perm = (10 ** inputs.gaussian_field(shape, 1.0, 3.0, seed)).reshape(-1)
+    return inputs.Problem(dim=dim, nx=nx, ny=ny, nz=nz, perm=perm,
+                          fracs=np.zeros((0, 4 if dim == 2 else 6)), kf=np.zeros(0),
+                          coarsen=coarsen, frac_dmin=5, basis=0, restriction=1, alpha=0.0)
+
+
+@pytest.mark.parametrize("args", [(2, 16, 16, 1, (4, 4, 1)),    # no fractures
+                                  (2, 16, 16, 1, (1, 1, 1)),    # every cell a coarse node
+                                  (2, 1, 12, 1, (4, 4, 1)),     # one column of cells
+                                  (2, 5, 3, 1, (8, 8, 1)),      # one partial primal block
+                                  (3, 6, 5, 4, (2, 2, 2))])     # 3D without plates
+def test_degenerate_inputs_match_the_oracle(args):
+    """Inputs at the edges of the method: the GMRES trajectory, the converged
+    pressure and the conservative fluxes equal the oracle's."""
+    fams = _fams()
+    p = _gmres(_degenerate(*args), 30, 200)
+    g, sysm, c, P, st = oracle.build(p)
+    xo, ito, _, oko, _ = osolver.gmres_solve(st, tol=1e-10, max_iter=200, restart=30)
+    with fams.Context(p) as ctx:
+        assert ctx.sizes()["n_coarse"] == c.n_coarse
+        Pg = _gpu_P(ctx, P.shape)
+        np.testing.assert_array_equal(Pg.indptr, P.indptr)
+        np.testing.assert_array_equal(Pg.indices, P.indices)
+        np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
+        xs, stats = ctx.solve(tol=1e-10)
+        assert stats[0]["converged"] and oko
+        assert abs(stats[0]["iterations"] - ito) <= 1
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-8
+        face, nnc = ctx.flux(xs[0])
+    sfv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    flux, dflux, _, _ = osolver.reconstruct_flux(sysm, p, sfv, xs[0], c.primal, c.node_cell)
+    nz = p.nz if p.dim == 3 else 1
+    nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
+    parts = [face[:nfx].reshape(nz, p.ny, p.nx + 1)[:, :, 1:-1].ravel(),
+             face[nfx:nfx + nfy].reshape(nz, p.ny + 1, p.nx)[:, 1:-1, :].ravel()]
+    if p.dim == 3:
+        parts.append(face[nfx + nfy:].reshape(nz + 1, p.ny, p.nx)[1:-1].ravel())
+    conn = np.concatenate(parts + [nnc])
+    # scale: the largest flux including the Dirichlet faces (in a single
+    # column every internal flux is rounding noise)
+    scale = max(np.abs(flux).max(), np.abs(dflux).max())
+    np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-9 * scale)
+
+
 def test_rejects_bad_input():
     fams = _fams()
     p = _case("2d32")
