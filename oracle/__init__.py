@@ -46,18 +46,25 @@ class OracleResult:
     history: list
 
 
-def build(prob, route="staged"):
-    """Geometry, system, coarse grids, P (truncated) and the solver setup."""
-    g = _geom.build_geometry(prob)
-    sysm = _asm.assemble(prob, g)
-    c = _coarsen.build_coarse(prob, g)
+def prolongation(prob, g, sysm, c, route="staged"):
+    """P (truncated) from the basis operator A0 of `sysm` (Sec. 3.1, App. A;
+    truncation Sec. 4.3).  Called with an updated system it rebuilds the basis
+    functions for new mobilities on the same coarse grids."""
     plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
     if route == "staged":
         P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate)
     else:
         P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
                                          plate)
-    P = _basis.truncate(P, prob.alpha)
+    return _basis.truncate(P, prob.alpha)
+
+
+def build(prob, route="staged"):
+    """Geometry, system, coarse grids, P (truncated) and the solver setup."""
+    g = _geom.build_geometry(prob)
+    sysm = _asm.assemble(prob, g)
+    c = _coarsen.build_coarse(prob, g)
+    P = prolongation(prob, g, sysm, c, route)
     st = _solver.setup(sysm, P, c.primal, c.n_coarse, prob.restriction)
     return g, sysm, c, P, st
 

@@ -291,3 +291,34 @@ def test_sealed_node_makes_the_fv_coarse_system_singular():
     q.alpha = 1e-2
     _, _, _, _, sq = oracle.build(q)
     assert solver.singular_step(sq.Ac) == -1
+
+
+def test_basis_rebuilt_for_new_mobilities():
+    """Rebuilding the basis from the updated operator: a uniform mobility
+    scale leaves P unchanged (A0 scales, its local solutions do not); a
+    non-uniform one changes it, keeps the partition of unity and the vertex
+    rows, and (fracture-free, no truncation) the rebuilt P solves the updated
+    operator's rows at the interior cells exactly: those rows keep all their
+    links, so (A0' P) vanishes there."""
+    p = _small(0, restriction=1)
+    g, sysm, c, P, st = oracle.build(p)
+    u = assemble.update_mobility(sysm, np.full(sysm.n, 3.0))
+    Pu = oracle.prolongation(p, g, u, c)
+    assert abs(Pu - P).max() < 1e-12
+    sc = np.random.default_rng(5).uniform(0.25, 4.0, sysm.n)
+    u = assemble.update_mobility(sysm, sc)
+    Pu = oracle.prolongation(p, g, u, c)
+    assert abs(Pu - P).max() > 1e-3
+    assert np.abs(np.asarray(Pu.sum(axis=1)).ravel() - 1).max() < 1e-12
+    for J, cell in enumerate(c.node_cell):
+        row = Pu.getrow(cell)
+        assert row.nnz == 1 and row.indices[0] == J and row.data[0] == 1.0
+    q = inputs.config_2d(24, 1.0, 4.0, 0, (6, 16), 1e2, 4, 4, seed=7, basis=0, restriction=1)
+    q.alpha = 0.0
+    gq, sq, cq, Pq, _ = oracle.build(q)
+    uq = assemble.update_mobility(sq, np.random.default_rng(6).uniform(0.5, 2.0, sq.n))
+    Pr = oracle.prolongation(q, gq, uq, cq)
+    interior = cq.rank == cq.rank.min()
+    R = (uq.A0 @ Pr).toarray()[interior]
+    assert np.abs(R).max() < 1e-12 * abs(uq.A0).max()
+    assert abs(Pr - Pq).max() > 1e-3
