@@ -170,6 +170,19 @@ int fams_update(fams_ctx* ctx, const double* mobility_scale);
 /* the same for every instance of a batch context (scale[i] nullable) */
 int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);
 
+/* fams_update_basis - fams_update_batch, then, when the mobility has moved
+   far from the one the current basis functions were built with, the basis
+   functions rebuilt from the updated operator on the same coarse grids (the
+   paper keeps them across time steps unless properties change much, Sec.
+   3.1): P and P^T, R A P and its factors anew; ILU(0) as after the update.
+   Rebuilt when some cell's scale differs from its scale at the last build
+   (the setup until the first rebuild) by more than a factor 1 + eps; eps < 0
+   rebuilds always, +infinity never.  The decision covers the whole context
+   (the paper decides per local problem).  *rebuilt (nullable) is set to 1 or
+   0.  Errors as fams_update; FAMS_EINVAL for a NaN eps. */
+int fams_update_basis(fams_ctx* ctx, const double* const* mobility_scale, double eps,
+                      int* rebuilt);
+
 /* Limits of fams_solve_static (its fixed work array, about 13 MB per GPU). */
 #define FAMS_STATIC_MAX_ROWS 262144   /* n_matrix + n_frac of the instance */
 #define FAMS_STATIC_MAX_COARSE 16384  /* n_coarse of the instance */

@@ -489,6 +489,13 @@ int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale) {
   return phase_update(ctx->b, mobility_scale);
 }
 
+int fams_update_basis(fams_ctx* ctx, const double* const* mobility_scale, double eps,
+                      int* rebuilt) {
+  if (!ctx) { set_error("null argument"); return FAMS_EINVAL; }
+  if (eps != eps) { set_error("eps is NaN"); return FAMS_EINVAL; }
+  return phase_update_basis(ctx->b, mobility_scale, eps, rebuilt);
+}
+
 int fams_update(fams_ctx* ctx, const double* mobility_scale) {
   if (!ctx || ctx->b.B != 1) { set_error("fams_update needs a single-instance context"); return FAMS_EINVAL; }
   const double* s[1] = {mobility_scale};

@@ -2,6 +2,7 @@
 // is the concatenation of the instances' arrays (a block-diagonal system);
 // Inst::*_off give each instance's slice.
 #pragma once
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -109,6 +110,7 @@ struct Batch {
   // time-step update: mobility scale per row and the setup-time values it
   // scales (allocated by the first update)
   double* mob = nullptr;
+  double* mob_basis = nullptr;   // mobility scales the current P was built with (null: setup's)
   double* val0 = nullptr;
   double* TD0 = nullptr;
   double* qD0 = nullptr;
@@ -223,6 +225,15 @@ struct Batch {
     for (void* p : tmp) cudaFreeAsync(p, stream);
     tmp.clear();
   }
+  // free one owned array (stream-ordered) before it is built anew
+  template <class T>
+  void release(T*& p) {
+    if (!p) return;
+    void* v = static_cast<void*>(p);
+    cudaFreeAsync(v, stream);
+    owned.erase(std::remove(owned.begin(), owned.end(), v), owned.end());
+    p = nullptr;
+  }
   int upload_inst();
   int check_err(const char* phase);
 };
@@ -248,7 +259,8 @@ int phase_coarse(Batch& b);       // coarse.cu: matrix blocks, networks, BFS, ra
 int phase_basis(Batch& b);        // basis.cu: P
 int phase_coarse_op(Batch& b, int restriction);  // coarseop.cu: R A P, band LU
 int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse);
-int phase_update(Batch& b, const double* const* scale);   // system.cu
+int phase_update(Batch& b, const double* const* scale);
+int phase_update_basis(Batch& b, const double* const* scale, double eps, int* rebuilt);
 int ilu_refactor(Batch& b);                               // ilu.cu
 int refresh_mixed(Batch& b);                              // solve.cu
 int phase_ilu(Batch& b);          // ilu.cu

@@ -1016,6 +1016,8 @@ int refresh_mixed(Batch& b) {
   round(b.pk_lv, b.pk_lv32, PK * n1);
   round(b.pk_uv, b.pk_uv32, PK * n1);
   round(b.pk_ud, b.pk_ud32, n1);
+  round(b.p_val, b.p_val32, b.tot_pnnz);
+  round(b.pt_val, b.pt_val32, b.tot_pnnz);
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }

@@ -2,6 +2,8 @@
 // columns: two-point matrix stencil (harmonic face transmissibilities),
 // matrix-fracture connections T = CI k_m, fracture-fracture links, Dirichlet
 // faces through half-cell transmissibilities.  Row order [matrix; fracture].
+#include <cstring>
+
 #include "batch.cuh"
 
 namespace fams {
@@ -224,6 +226,83 @@ int phase_update(Batch& b, const double* const* scale) {
   FAMS_CUDA(cudaStreamSynchronize(st));
   b.free_tmp();
   return b.check_err("time-step update");
+}
+
+namespace {
+
+// largest relative change max(s/s0, s0/s) - 1 of the mobility scales since
+// the basis was built (s0 null: all 1), as the bits of a non-negative double,
+// which order like the integers
+__global__ void k_scale_change(long long n, const double* s, const double* s0,
+                               unsigned long long* out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = s[i], c = s0 ? s0[i] : 1.0;
+  double q = (a > c ? a / c : c / a) - 1.0;
+  if (!(q >= 0.0)) q = 1e300;   // not finite: treat as a large change
+  atomicMax(out, (unsigned long long)__double_as_longlong(q));
+}
+
+void release_coarse(Batch& b, CoarseSys& cs, CoarseHost& ch) {
+  b.release(cs.Ac); b.release(cs.ac_off); b.release(cs.band); b.release(cs.band_off);
+  b.release(cs.kl); b.release(cs.ku); b.release(cs.ipiv); b.release(cs.perm); b.release(cs.bad);
+  b.release(cs.nopiv); b.release(cs.binv); b.release(cs.binv_off);
+  ch = CoarseHost{};
+}
+
+}  // namespace
+
+// The time-step update, then -- when some cell's mobility scale moved by
+// more than a factor 1 + eps from the one the current basis functions were
+// built with (eps < 0: always) -- the basis functions, P and P^T, R A P and
+// its factors rebuilt from the updated basis operator on the same coarse
+// grids.  ILU(0) depends on A only and stays as the update left it.
+int phase_update_basis(Batch& b, const double* const* scale, double eps, int* rebuilt) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  const long long n = b.tot_row;
+  if (rebuilt) *rebuilt = 0;
+  FAMS_TRY(phase_update(b, scale));
+  bool again = eps < 0.0;
+  if (!again && n > 0) {
+    unsigned long long* d = nullptr;
+    FAMS_TRY(b.scratch((void**)&d, sizeof(unsigned long long)));
+    FAMS_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
+    fams::note_launch(), k_scale_change<<<grid_for(n, T), T, 0, st>>>(n, b.mob, b.mob_basis, d);
+    unsigned long long h = 0;
+    FAMS_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    FAMS_CUDA(cudaStreamSynchronize(st));
+    double q = 0.0;
+    std::memcpy(&q, &h, sizeof(q));
+    again = q > eps;
+  }
+  if (!again) {
+    b.free_tmp();
+    return FAMS_OK;
+  }
+  b.release(b.p_ptr); b.release(b.p_col); b.release(b.p_val);
+  b.release(b.pt_ptr); b.release(b.pt_col); b.release(b.pt_val);
+  FAMS_TRY(phase_basis(b));
+  release_coarse(b, b.cs[0], b.csh[0]);
+  FAMS_TRY(phase_coarse_op(b, -1));
+  if (b.fv_built) release_coarse(b, b.cs[1], b.csh[1]);
+  b.fv_built = false;
+  b.fv_ready = false;
+  if (b.p_val32) {   // FP32 copies of P and P^T at the new size
+    b.release(b.p_val32);
+    b.release(b.pt_val32);
+    FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (b.tot_pnnz + 1)));
+    FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (b.tot_pnnz + 1)));
+    FAMS_TRY(refresh_mixed(b));
+  }
+  if (!b.mob_basis) FAMS_TRY(b.alloc((void**)&b.mob_basis, sizeof(double) * (n + 1)));
+  if (n > 0)
+    FAMS_CUDA(cudaMemcpyAsync(b.mob_basis, b.mob, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  b.free_tmp();
+  FAMS_TRY(b.check_err("basis rebuild"));
+  if (rebuilt) *rebuilt = 1;
+  return FAMS_OK;
 }
 
 int phase_system(Batch& b) {

@@ -82,6 +82,7 @@ def _load():
     lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fams_update.argtypes = [C.c_void_p, C.c_void_p]
     lib.fams_update_batch.argtypes = [C.c_void_p, P(C.c_void_p)]
+    lib.fams_update_basis.argtypes = [C.c_void_p, P(C.c_void_p), C.c_double, P(C.c_int)]
     lib.fams_flux_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), P(C.c_void_p),
                                     P(C.c_int)]
     lib.fams_query.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong]
@@ -234,6 +235,18 @@ class Context:
         arrs = [None if sc is None else np.ascontiguousarray(sc, np.float64) for sc in scales]
         ptrs = (C.c_void_p * self.n)(*[0 if a is None else a.ctypes.data for a in arrs])
         _check(lib.fams_update_batch(self.h, ptrs))
+
+    def update_basis(self, scales, eps):
+        """fams_update_basis: the update of `update`, then the basis functions
+        rebuilt when some scale moved by more than a factor 1 + eps since the
+        last build (eps < 0: always).  Returns whether they were rebuilt."""
+        if not isinstance(scales, (list, tuple)):
+            scales = [scales]
+        arrs = [None if sc is None else np.ascontiguousarray(sc, np.float64) for sc in scales]
+        ptrs = (C.c_void_p * self.n)(*[0 if a is None else a.ctypes.data for a in arrs])
+        r = C.c_int(0)
+        _check(lib.fams_update_basis(self.h, ptrs, float(eps), C.byref(r)))
+        return bool(r.value)
 
     def solve_device(self, rhs_ptrs, x_ptrs, tol):
         """The same call with caller-owned buffers given as raw pointers (host

@@ -635,3 +635,49 @@ def test_time_step_update_matches_oracle(name, restriction):
         ctx.update(None)
         np.testing.assert_allclose(ctx.query("A_VAL"), sysm.A.data, rtol=1e-13,
                                    atol=1e-15 * abs(sysm.A).max())
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3dcross"])
+def test_basis_rebuild_matches_oracle(name, restriction):
+    """fams_update_basis: below its threshold P stays the setup's; above it
+    P, R A P, a GMRES trajectory and the conservative fluxes equal the
+    oracle's for the basis rebuilt from the updated operator; the same scales
+    again are no change; eps < 0 always rebuilds."""
+    from oracle import assemble as oasm
+    fams = _fams()
+    p = _gmres(_case(name, 0, restriction), 8, 13)
+    g, sysm, c, P, st0 = oracle.build(p)
+    sc = np.random.default_rng(7).uniform(0.5, 2.0, sysm.n)
+    with fams.Context(p) as ctx:
+        assert not ctx.update_basis(sc, 10.0)
+        Pg = _gpu_P(ctx, P.shape)
+        np.testing.assert_array_equal(Pg.indices, P.indices)
+        np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
+        assert ctx.update_basis(sc, 0.01)
+        ur = oasm.update_mobility(sysm, sc)
+        Pu = oracle.prolongation(p, g, ur, c)
+        Pg = _gpu_P(ctx, Pu.shape)
+        np.testing.assert_array_equal(Pg.indptr, Pu.indptr)
+        np.testing.assert_array_equal(Pg.indices, Pu.indices)
+        np.testing.assert_allclose(Pg.data, Pu.data, rtol=0, atol=1e-12)
+        su = osolver.setup(ur, Pu, c.primal, c.n_coarse, p.restriction)
+        Ac = ctx.query("AC").reshape(c.n_coarse, c.n_coarse)
+        np.testing.assert_allclose(Ac, su.Ac, rtol=0, atol=1e-11 * np.abs(su.Ac).max())
+        xo, ito, _, _, _ = osolver.gmres_solve(su, tol=0.0, max_iter=13, restart=8)
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 13 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+        face, nnc = ctx.flux(xs[0])
+        sfv = osolver.setup(ur, Pu, c.primal, c.n_coarse, osolver.R_FV)
+        flux, dflux, _, _ = osolver.reconstruct_flux(ur, p, sfv, xs[0], c.primal, c.node_cell)
+        nz = p.nz if p.dim == 3 else 1
+        nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
+        parts = [face[:nfx].reshape(nz, p.ny, p.nx + 1)[:, :, 1:-1].ravel(),
+                 face[nfx:nfx + nfy].reshape(nz, p.ny + 1, p.nx)[:, 1:-1, :].ravel()]
+        if p.dim == 3:
+            parts.append(face[nfx + nfy:].reshape(nz + 1, p.ny, p.nx)[1:-1].ravel())
+        conn = np.concatenate(parts + [nnc])
+        np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
+        assert not ctx.update_basis(sc, 0.01)
+        assert ctx.update_basis(sc, -1.0)
