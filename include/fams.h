@@ -34,7 +34,10 @@ extern "C" {
 /* coupling strategy of the basis functions (Sec. 3.1, Eqs. 19-22) */
 enum { FAMS_DECOUPLED = 0, FAMS_FRAC = 1, FAMS_ROCK = 2, FAMS_COUPLED = 3 };
 /* restriction operator (Sec. 3.2): finite volume (R^FV) or finite element (R^FE = P^T) */
-enum { FAMS_R_FV = 0, FAMS_R_FE = 1 };
+/* restriction (Sec. 3.2): finite volume (primal-block indicators), finite
+   element (P^T), or MSMIX: P^T rows for the matrix coarse nodes and
+   indicator rows for the fracture coarse nodes */
+enum { FAMS_R_FV = 0, FAMS_R_FE = 1, FAMS_R_MIX = 2 };
 /* arithmetic of the iteration: FP64 throughout, or FP32 inner stages with
    FP64 outer residual, coarse solve and refinement */
 enum { FAMS_FP64 = 0, FAMS_MIXED = 1 };

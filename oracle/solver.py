@@ -4,7 +4,8 @@ iteration (Sec. 3.2, Table 1), and conservative flux reconstruction.
 TEST INFRASTRUCTURE ONLY (see oracle/geometry.py).
 
 * R^FV: R[I, i] = 1 when fine cell i lies in primal block I (Sec. 3.2);
-  R^FE = P^T (MSFE).
+  R^FE = P^T (MSFE); MSMIX: P^T rows for matrix coarse nodes, R^FV rows for
+  fracture coarse nodes (the paper's example of the hybrid, Sec. 3.2).
 * coarse operator A_c = R A P, solved by LU with partial pivoting (the paper
   uses a direct LU solver, Sec. 4).
 * ILU(0) of the complete fine A in natural order (matrix cells then fracture
@@ -30,14 +31,24 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-R_FV, R_FE = 0, 1
+R_FV, R_FE, R_MIX = 0, 1, 2
 
 
-def restriction(P, primal, n_coarse, kind):
+def restriction(P, primal, n_coarse, kind, n_matrix=None):
+    """R^FV (primal-block indicators), R^FE = P^T, or MSMIX (Sec. 3.2): the
+    rows of matrix coarse nodes from P^T, the rows of fracture coarse nodes
+    (indices from the first fracture block on) from the indicators."""
     n = P.shape[0]
+    fv = sp.csr_matrix((np.ones(n), (primal, np.arange(n))), shape=(n_coarse, n))
+    if kind == R_FV:
+        return fv
+    fe = sp.csr_matrix(P.T)
     if kind == R_FE:
-        return sp.csr_matrix(P.T)
-    return sp.csr_matrix((np.ones(n), (primal, np.arange(n))), shape=(n_coarse, n))
+        return fe
+    nm = n if n_matrix is None else n_matrix
+    ncm = int(primal[:nm].max()) + 1 if nm > 0 else 0
+    frac_row = (np.arange(n_coarse) >= ncm).astype(np.float64)
+    return sp.csr_matrix(sp.diags(1.0 - frac_row) @ fe + sp.diags(frac_row) @ fv)
 
 
 def coarse_operator(R, A, P):
@@ -121,7 +132,7 @@ def setup(sysm, P, primal, n_coarse, kind):
     s.A = sysm.A
     s.q = sysm.q
     s.P = P
-    s.R = restriction(P, primal, n_coarse, kind)
+    s.R = restriction(P, primal, n_coarse, kind, sysm.n_matrix)
     s.Ac = coarse_operator(s.R, sysm.A, P)
     s.lu = sla.lu_factor(s.Ac)
     s.F = ilu0(sysm.A)

@@ -81,7 +81,8 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   for (int a = 0; a < g.dim; ++a)
     if (o.coarsen[a] < 1) return bad("coarsening ratios must be >= 1");
   if (o.basis < 0 || o.basis > 3) return bad("basis must be 0..3");
-  if (o.restriction != FAMS_R_FV && o.restriction != FAMS_R_FE) return bad("restriction must be FV or FE");
+  if (o.restriction != FAMS_R_FV && o.restriction != FAMS_R_FE && o.restriction != FAMS_R_MIX)
+    return bad("restriction must be FAMS_R_FV, FAMS_R_FE or FAMS_R_MIX");
   if (!(o.alpha >= 0.0) || !(o.alpha < 1.0)) return bad("alpha must be in [0, 1)");
   if (o.max_iter < 0) return bad("max_iter must be >= 0");
   if (o.precision != FAMS_FP64 && o.precision != FAMS_MIXED)

@@ -38,6 +38,21 @@ __global__ void k_rap(const Inst* inst, int B, const int* off_row, long long nnz
   double a = val[p];
   double* Ac = cs.Ac + cs.ac_off[ii];
   int nc = I.nc;
+  if (mode < 0 && I.restriction == FAMS_R_MIX) {
+    // MSMIX: the fracture coarse rows as R^FV, the matrix coarse rows as R^FE
+    int Ib = primal[i];
+    if (Ib >= I.ncm)
+      for (int q = p_ptr[j]; q < p_ptr[j + 1]; ++q)
+        atomicAdd(&Ac[(long long)Ib * nc + p_col[q]], a * p_val[q]);
+    for (int t = p_ptr[i]; t < p_ptr[i + 1]; ++t) {
+      int Ie = p_col[t];
+      if (Ie >= I.ncm) continue;
+      double u = p_val[t] * a;
+      for (int q = p_ptr[j]; q < p_ptr[j + 1]; ++q)
+        atomicAdd(&Ac[(long long)Ie * nc + p_col[q]], u * p_val[q]);
+    }
+    return;
+  }
   if (!fe) {
     int Ib = primal[i];
     for (int q = p_ptr[j]; q < p_ptr[j + 1]; ++q)

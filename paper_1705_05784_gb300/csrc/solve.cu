@@ -428,7 +428,8 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
     for (int k = threadIdx.x >> 5; k < nc; k += nw) {
       const int c = co + perm[k];
       T s = 0;
-      if (I.restriction == FAMS_R_FE) {
+      // MSMIX: P^T rows for the matrix coarse nodes, indicators for the fracture ones
+      if (I.restriction == FAMS_R_FE || (I.restriction == FAMS_R_MIX && perm[k] < I.ncm)) {
         for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += ptv[p] * r[a.pt_col[p]];
       } else {
         for (int p = a.blk_ptr[c] + lane; p < a.blk_ptr[c + 1]; p += 32) s += r[a.blk_cell[p]];

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libfams.so")
 
 DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
-R_FV, R_FE = 0, 1
+R_FV, R_FE, R_MIX = 0, 1, 2
 FP64, MIXED = 0, 1
 KRYLOV_NONE, KRYLOV_GMRES = 0, 1
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ETIMEOUT, ECUDA, ECAPACITY = 0, -1, -2, -3, -4, -5, -6, -7

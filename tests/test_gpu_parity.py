@@ -681,3 +681,27 @@ def test_basis_rebuild_matches_oracle(name, restriction):
         np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
         assert not ctx.update_basis(sc, 0.01)
         assert ctx.update_basis(sc, -1.0)
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3dcross"])
+def test_msmix_matches_oracle(name, variant):
+    """MSMIX restriction (P^T rows for matrix coarse nodes, indicators for
+    fracture coarse nodes): R A P, a GMRES trajectory and the converged
+    solution equal the oracle's."""
+    fams = _fams()
+    p = _gmres(_case(name, variant, osolver.R_MIX), 8, 13)
+    g, sysm, c, P, st = oracle.build(p)
+    with fams.Context(p) as ctx:
+        Ac = ctx.query("AC").reshape(c.n_coarse, c.n_coarse)
+        np.testing.assert_allclose(Ac, st.Ac, rtol=0, atol=1e-11 * np.abs(st.Ac).max())
+        xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=13, restart=8)
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 13 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+    q = _gmres(_case(name, variant, osolver.R_MIX), 30, 300)
+    with fams.Context(q) as ctx:
+        xs, stats = ctx.solve(tol=1e-8)
+        assert stats[0]["converged"]
+    xd, _, _, okd, _ = osolver.gmres_solve(st, tol=1e-8, max_iter=300, restart=30)
+    assert okd and np.linalg.norm(xs[0] - xd) / np.linalg.norm(xd) < 1e-6

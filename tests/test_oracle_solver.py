@@ -322,3 +322,25 @@ def test_basis_rebuilt_for_new_mobilities():
     R = (uq.A0 @ Pr).toarray()[interior]
     assert np.abs(R).max() < 1e-12 * abs(uq.A0).max()
     assert abs(Pr - Pq).max() > 1e-3
+
+
+def test_msmix_restriction():
+    """MSMIX: matrix coarse rows of R A P are the R^FE ones, fracture coarse
+    rows the R^FV ones; without fractures MSMIX is R^FE; the GMRES iteration
+    with it reaches the direct solution."""
+    p = _small(1, restriction=solver.R_MIX)
+    g, sysm, c, P, st = oracle.build(p)
+    fe = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FE)
+    fv = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FV)
+    ncm = c.n_coarse_matrix
+    assert c.n_coarse > ncm
+    np.testing.assert_array_equal(st.Ac[:ncm], fe.Ac[:ncm])
+    np.testing.assert_array_equal(st.Ac[ncm:], fv.Ac[ncm:])
+    x, it, rr, ok, _ = solver.gmres_solve(st, tol=1e-10, max_iter=200, restart=30)
+    xd = spla.spsolve(sysm.A.tocsc(), sysm.q)
+    assert ok and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+    q = inputs.config_2d(24, 1.0, 4.0, 0, (6, 16), 1e2, 4, 4, seed=7, basis=0,
+                         restriction=solver.R_MIX)
+    gq, sq, cq, Pq, stq = oracle.build(q)
+    feq = solver.setup(sq, Pq, cq.primal, cq.n_coarse, solver.R_FE)
+    assert abs(stq.R - feq.R).max() == 0.0
