@@ -166,9 +166,9 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
    two cells' mobility scales, a Dirichlet half-cell's the setup-time value
    times its cell's scale.  The coarse grids and P (Sec. 3.1) are kept; R A P
    and its factors, the ILU(0) smoother and the fluxes' transmissibilities
-   follow.  mobility_scale: n_matrix + n_frac positive values, relative to
-   the setup (nullable: all 1, i.e. back to the setup values); host or
-   device. */
+   follow.  mobility_scale: n_matrix + n_frac positive finite values (not
+   checked), relative to the setup (nullable: all 1, i.e. back to the setup
+   values); host or device. */
 int fams_update(fams_ctx* ctx, const double* mobility_scale);
 /* the same for every instance of a batch context (scale[i] nullable) */
 int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);

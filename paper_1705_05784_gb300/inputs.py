@@ -48,7 +48,7 @@ class Problem:
     frac_dmin: int = 5
     frac_cz: int = 1
     basis: int = 0                   # 0 Decoupled, 1 Frac, 2 Rock, 3 Coupled
-    restriction: int = 0             # 0 FV, 1 FE
+    restriction: int = 0             # 0 FV, 1 FE, 2 MSMIX
     alpha: float = 0.0
     tol: float = 1e-8
     max_iter: int = 200
