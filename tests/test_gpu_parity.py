@@ -705,3 +705,26 @@ def test_msmix_matches_oracle(name, variant):
         assert stats[0]["converged"]
     xd, _, _, okd, _ = osolver.gmres_solve(st, tol=1e-8, max_iter=300, restart=30)
     assert okd and np.linalg.norm(xs[0] - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def test_bench_workload_instances_match_the_oracle():
+    """The bench workload at full size (256x256, GMRES(30), R^FE, reconstruction
+    prepared beside the solve) in a batch of 16: two sampled instances against
+    the oracle, both converged to 1e-8 -- pressure and conservative fluxes."""
+    import bench
+    fams = _fams()
+    probs = bench.problems(16, bench.ORACLE_SEED)
+    with fams.Context(probs) as c:
+        xs, st = c.solve(tol=bench.TOL)
+        assert all(s["converged"] for s in st)
+        for i in (0, 1):
+            p = probs[i]
+            g, sysm, co, P, so = oracle.build(p)
+            xo, _, _, oko, _ = osolver.gmres_solve(so, tol=bench.TOL, max_iter=p.max_iter,
+                                                   restart=p.restart)
+            assert oko
+            assert np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo) < 1e-6
+            sfv = osolver.setup(sysm, P, co.primal, co.n_coarse, osolver.R_FV)
+            fo, _, _, _ = osolver.reconstruct_flux(sysm, p, sfv, xo, co.primal, co.node_cell)
+            face, nnc = c.flux(xs[i], i)
+            assert np.abs(bench.conn_fluxes(p, face, nnc) - fo).max() < 1e-6 * np.abs(fo).max()
