@@ -89,7 +89,9 @@ typedef struct {
 /* Method options.  coarsen[] = matrix coarsening ratio per axis; frac_dmin =
    d_min of the distance-based fracture coarsening (Table 2; <= 0 means
    infinity, one coarse node per network); frac_cz = vertical coarsening of 3D
-   fracture plates; alpha = truncation threshold of P (Sec. 4.3, 0 = none);
+   fracture plates; alpha = truncation threshold of P (Sec. 4.3, 0 = none;
+   a basis function none of whose entries outside its node cell reaches alpha
+   keeps all of them, so none is reduced to its node cell);
    max_iter bounds the Table 1 loop (or the GMRES iterations); precision =
    FAMS_FP64 or FAMS_MIXED.  krylov = FAMS_KRYLOV_GMRES runs the two-stage
    step as the right preconditioner of GMRES(restart), the paper's benchmark
@@ -235,9 +237,11 @@ int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, doubl
    numerically singular gets FAMS_EBREAKDOWN and its buffers are left
    untouched while the others are reconstructed.  Numerically singular: a
    pivot of its band LU is at most 1e-13 times the largest entry of its row as
-   assembled (e.g. a coarse node whose truncated basis function is its own
-   cell inside its own primal block: its R^FV column sums to zero).  Returns
-   FAMS_EBREAKDOWN if any instance failed that way. */
+   assembled (e.g. a node cell 1e-300 times as permeable as its neighbours:
+   its basis function is 1e-300 outside the node cell, and its R^FV column is
+   that small).  Truncation never reduces a basis function to its own node
+   cell, which would make that column exactly zero.  Returns FAMS_EBREAKDOWN
+   if any instance failed that way. */
 int fams_flux_batch(fams_ctx* ctx, const double* const* x, double* const* face_flux,
                     double* const* nnc_flux, int* status);
 

@@ -52,11 +52,12 @@ def prolongation(prob, g, sysm, c, route="staged"):
     functions for new mobilities on the same coarse grids."""
     plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
     if route == "staged":
-        P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate)
+        P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate,
+                                       c.row_net)
     else:
         P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
-                                         plate)
-    return _basis.truncate(P, prob.alpha)
+                                         plate, c.row_net)
+    return _basis.truncate(P, prob.alpha, c.node_cell)
 
 
 def build(prob, route="staged"):

@@ -41,10 +41,16 @@ DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
 M, F = 0, 1
 
 
-def keep_link(variant, med_r, rank_r, med_c, rank_c, cross=False):
-    """cross: the link joins cells of two different fractures (a crossing).
-    Two fracture faces never share a link: faces of different fractures meet
-    only along edges, so a face-face link across a crossing is dropped."""
+def keep_link(variant, med_r, rank_r, med_c, rank_c, cross=0):
+    """cross: 1 if the link joins cells of two different fractures of one
+    coarsening network (a crossing), 2 if of two different networks.  Two
+    fracture faces never share a link: faces of different fractures meet only
+    along edges, so a face-face link across a crossing is dropped.  Networks
+    are coarsened apart (3D plates of other layer ranges that cross), so
+    their wirebaskets are unrelated and no link between two of them is
+    kept: each network's basis functions are built on that network alone."""
+    if cross == 2 and med_r == F and med_c == F:
+        return False
     if cross and med_r == F and med_c == F and rank_r == RANK_F and rank_c == RANK_F:
         return False
     if variant == DECOUPLED:
@@ -77,7 +83,17 @@ def _plate_of(n, plate):
     return np.full(n, -1, np.int64) if plate is None else np.asarray(plate, np.int64)
 
 
-def stage_blocks(A0, rank, medium, node_cell, variant, plate=None):
+def _cross(plate, net, r, c):
+    """0: not two fractures' cells; 1: two fractures of one network; 2: two
+    networks (net None: one network)."""
+    if plate[r] < 0 or plate[c] < 0 or plate[r] == plate[c]:
+        return 0
+    if net is not None and net[r] != net[c]:
+        return 2
+    return 1
+
+
+def stage_blocks(A0, rank, medium, node_cell, variant, plate=None, net=None):
     """The dual blocks of every stage (lists of rows), in solve order."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
@@ -100,9 +116,8 @@ def stage_blocks(A0, rank, medium, node_cell, variant, plate=None):
         for r in S:
             for p in range(ip[r], ip[r + 1]):
                 c = ix[p]
-                cross = plate[r] >= 0 and plate[c] >= 0 and plate[r] != plate[c]
                 if c != r and in_stage[c] and keep_link(variant, medium[r], rank[r], medium[c],
-                                                        rank[c], cross):
+                                                        rank[c], _cross(plate, net, r, c)):
                     er.append(loc[r])
                     ec.append(loc[c])
         G = sp.csr_matrix((np.ones(len(er)), (er, ec)), shape=(S.size, S.size))
@@ -115,16 +130,16 @@ def stage_blocks(A0, rank, medium, node_cell, variant, plate=None):
     return out
 
 
-def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None):
+def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=None):
     """P (CSR, n x n_coarse) by the staged wirebasket rule.  plate[r]: input
-    fracture of fracture row r (-1 for matrix rows; None: no crossings)."""
+    fracture of fracture row r (-1 for matrix rows; None: no crossings);
+    net[r]: coarsening network of fracture row r (None: a single network)."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
 
     def keep(r, c):
-        cross = plate[r] >= 0 and plate[c] >= 0 and plate[r] != plate[c]
-        return keep_link(variant, medium[r], rank[r], medium[c], rank[c], cross)
+        return keep_link(variant, medium[r], rank[r], medium[c], rank[c], _cross(plate, net, r, c))
 
     nc = len(node_cell)
     rows = [dict() for _ in range(n)]
@@ -221,19 +236,22 @@ def _solve(Ablk, R):
     return sp.csr_matrix(lu.solve(Rd))
 
 
-def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None):
+def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None, net=None):
     """P from the printed block formulas of Appendix A (regular wirebasket:
     the blocks that the TPFA stencil makes zero are taken as zero).  Face-face
-    links across fracture crossings are dropped from A0 first (removed from
-    the diagonal), as in keep_link."""
+    links across fracture crossings, and every link between two coarsening
+    networks, are dropped from A0 first (removed from the diagonal), as in
+    keep_link."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
     A0 = A0.tolil()
-    ff = np.nonzero((medium == F) & (rank == RANK_F))[0]
-    for r in ff:
+    for r in np.nonzero(medium == F)[0]:
         for c in list(A0.rows[r]):
-            if c != r and medium[c] == F and rank[c] == RANK_F and plate[c] != plate[r]:
+            if c == r or medium[c] != F:
+                continue
+            x = _cross(plate, net, r, c)
+            if x == 2 or (x == 1 and rank[r] == RANK_F and rank[c] == RANK_F):
                 A0[r, r] = A0[r, r] + A0[r, c]
                 A0[r, c] = 0.0
     A0 = sp.csr_matrix(A0)
@@ -367,19 +385,39 @@ def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None):
     return P
 
 
-def truncate(P, alpha):
+def truncate(P, alpha, node_cell=None):
     """Sec. 4.3: drop entries with |P_ij| < alpha and divide each row by its new
     sum.  A row that would lose every entry keeps its largest one (lowest
-    column on ties).  alpha = 0 leaves P unchanged."""
+    column on ties).  alpha = 0 leaves P unchanged.
+
+    node_cell (the node cell of every coarse column), when given, adds the
+    rule that truncation never reduces a basis function to its own node cell:
+    a column j none of whose entries outside row node_cell[j] reaches alpha
+    keeps all of its entries.  Without it, a node cell much less permeable
+    than its neighbours has a basis function that is the unit vector of its
+    cell after truncation; that column of R^FV A P is A's column summed over
+    the node's own primal block, zero, and the finite-volume stage of the flux
+    reconstruction (Sec. 3.2) would have no solution."""
     P = sp.csr_matrix(P, copy=True)
     if alpha <= 0.0:
         return P
+    n, nc = P.shape
+    keep_all = np.zeros(nc, bool)
+    if node_cell is not None:
+        node_cell = np.asarray(node_cell, np.int64)
+        survives = np.zeros(nc, bool)
+        for r in range(n):
+            for p in range(P.indptr[r], P.indptr[r + 1]):
+                j = P.indices[p]
+                if r != node_cell[j] and abs(P.data[p]) >= alpha:
+                    survives[j] = True
+        keep_all = ~survives
     ri, ci, vv = [], [], []
-    for r in range(P.shape[0]):
+    for r in range(n):
         a, b = P.indptr[r], P.indptr[r + 1]
         cols = P.indices[a:b]
         vals = P.data[a:b]
-        keep = np.abs(vals) >= alpha
+        keep = (np.abs(vals) >= alpha) | keep_all[cols]
         if not keep.any() and b > a:
             keep = np.zeros(b - a, bool)
             keep[int(np.argmax(np.abs(vals)))] = True

@@ -14,15 +14,18 @@ Readings where the paper is silent:
   node line: 3D ranks V=3, E=2, F=1, I=0; in 2D the same count plus one, so the
   matrix has V, E and F (faces are the lowest class in 2D);
 * fracture networks are the connected components of the fracture graph (along
-  strike and through intersections; in 3D of its x-y projection).  Table 2 is
+  strike and through intersections; in 3D of its x-y projection, where two
+  crossing plates join one network only when they span the same layers: the
+  vertical coarse grid of a network is one uniform extrusion, Sec. 4.3, and
+  plates of other layer ranges that cross are coarsened as separate networks
+  while their fracture-fracture connections stay in A).  Table 2 is
   run per network with: start cell = lowest-index cell of degree 1 (lowest
   index if none), neighbours visited in ascending index, FIFO queues, and a
   candidate removed from Q_vertex whenever its level is lowered;
 * 2D fracture cells are V (coarse nodes) or E; 3D fracture cells are V on a
   vertex column and a node layer, E on exactly one of the two, F otherwise;
   the vertical coarse grid of a network starts at its lowest layer with
-  frac_cz layers per block (uniform extrusion, Sec. 4.3), so all plates that
-  meet must share their layer range;
+  frac_cz layers per block (uniform extrusion, Sec. 4.3);
 * coarse numbering: matrix blocks lexicographically, then the fracture blocks
   network by network (networks in order of their lowest cell), strike block
   fastest, then vertical block.
@@ -196,8 +199,7 @@ def build_coarse(prob, geom):
         else:
             fr = sorted({int(s_frac[s]) for s in cells})
             k0s = {(int(g.frac_k0[f]), int(g.frac_nk[f])) for f in fr}
-            if len(k0s) != 1:
-                raise ValueError("plates of one fracture network must share their layer range")
+            assert len(k0s) == 1, "a network joins plates of different layer ranges"
             k0, nk = k0s.pop()
             c.net_layers.append((k0, nk))
             cz = max(1, prob.frac_cz)
@@ -217,6 +219,15 @@ def build_coarse(prob, geom):
                     f = s_frac[v]
                     node_cell.append(nm + g.frac_first[f] + s_loc[v] + g.frac_ns[f] * vnode[vb])
             base += npr * nvb
+    # coarsening network of every fracture row (-1 for matrix rows)
+    row_net = np.full(nm + nf, -1, np.int64)
+    for f in range(len(g.frac_ns)):
+        ns = g.frac_ns[f]
+        nk = g.frac_nk[f] if prob.dim == 3 else 1
+        for kk in range(nk):
+            for s in range(ns):
+                row_net[nm + g.frac_first[f] + s + ns * kk] = lab[g.strike_first[f] + s]
+    c.row_net = row_net
     c.rank = rank
     c.primal = primal
     c.node_cell = np.array(node_cell, np.int64)

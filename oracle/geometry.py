@@ -309,7 +309,9 @@ def build_geometry(prob):
     g.ff_T = np.array([t[2] for t in ff], np.float64)
     g.ff_kind = np.array([t[3] for t in ff], np.int64)
 
-    # --- the x-y projection ("strike") graph used by the fracture coarsening ---
+    # --- the x-y projection ("strike") graph used by the fracture coarsening:
+    # along-strike neighbours, and the crossing cells of two fractures (in 3D
+    # of two plates with the same layer range) ---
     n_strike = int(g.frac_ns.sum())
     g.n_strike = n_strike
     sfirst = np.concatenate([[0], np.cumsum(g.frac_ns)[:-1]]) if nf else np.zeros(0, np.int64)
@@ -325,9 +327,12 @@ def build_geometry(prob):
         sa = min(int(math.floor(t * na)), na - 1)
         sb = min(int(math.floor(u * nb)), nb - 1)
         if dim == 3:
-            lo = max(g.frac_k0[fa], g.frac_k0[fb])
-            hi = min(g.frac_k0[fa] + g.frac_nk[fa], g.frac_k0[fb] + g.frac_nk[fb])
-            if hi <= lo:
+            # plates are coarsened together only where they share their layer
+            # range (uniform vertical extrusion of the network, Sec. 4.3);
+            # crossing plates of other ranges stay connected in A
+            if g.frac_k0[fa] != g.frac_k0[fb] or g.frac_nk[fa] != g.frac_nk[fb]:
+                continue
+            if g.frac_nk[fa] <= 0:
                 continue
         a, b = sfirst[fa] + sa, sfirst[fb] + sb
         if a != b:

@@ -48,10 +48,14 @@ __device__ inline int stage_of(int variant, int med, int rank) {
   }
 }
 
-// cross: the link joins fracture cells of two different input fractures.
-// Faces of different fractures meet only along edges: a face-face link across
-// a crossing is never kept.
-__device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc, bool cross) {
+// cross: 1 if the link joins fracture cells of two different input fractures
+// of one coarsening network, 2 if of two networks.  Faces of different
+// fractures meet only along edges: a face-face link across a crossing is never
+// kept.  Networks are coarsened apart (3D plates of other layer ranges that
+// cross), so no link between two networks is kept: each network's basis
+// functions are built on that network alone.
+__device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc, int cross) {
+  if (cross == 2 && mr == 1 && mc == 1) return false;
   if (cross && mr == 1 && mc == 1 && rr == RANK_F && rc == RANK_F) return false;
   switch (variant) {
     case 0: return mr == mc && rc >= rr;
@@ -61,19 +65,31 @@ __device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc, bo
   }
 }
 
-__device__ inline bool crossing(const int* plate, int r, int c) {
+// plate[r]: input fracture of row r (-1 for matrix rows); plate[nrow + r]:
+// its coarsening network
+__device__ inline int crossing(const int* plate, long long nrow, int r, int c) {
   int a = plate[r], b = plate[c];
-  return a >= 0 && b >= 0 && a != b;
+  if (a < 0 || b < 0 || a == b) return 0;
+  return plate[nrow + r] != plate[nrow + c] ? 2 : 1;
 }
 
-// input fracture of every unknown (-1 for matrix cells)
+// input fracture and coarsening network of every unknown (-1 for matrix cells)
 __global__ void k_row_plate(const Inst* inst, int B, const int* off_row, long long nrow,
-                            const int* f_cfirst, long long nfr, int* plate) {
+                            const int* f_cfirst, const int* f_sfirst, const int* f_ns,
+                            const int* s_net, long long nfr, int* plate) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst[find_segment(off_row, B + 1, r)];
   long long loc = r - I.row_off;
-  plate[r] = loc < I.nm ? -1 : find_segment(f_cfirst, (int)nfr + 1, I.fc_off + (loc - I.nm));
+  if (loc < I.nm) {
+    plate[r] = -1;
+    plate[nrow + r] = -1;
+    return;
+  }
+  int gc = (int)(I.fc_off + (loc - I.nm));
+  int gf = find_segment(f_cfirst, (int)nfr + 1, gc);
+  plate[r] = gf;
+  plate[nrow + r] = s_net[f_sfirst[gf] + (gc - f_cfirst[gf]) % f_ns[gf]];
 }
 
 struct RowCtx {
@@ -147,7 +163,7 @@ __global__ void k_stage_union(const Inst* inst, int B, const int* off_row, long 
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
     int c = col[p];
     if (c <= r || !instage[c]) continue;
-    if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, (int)r, c))) continue;
+    if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, nrow, (int)r, c))) continue;
     int a = uf_find(parent, (int)r), b = uf_find(parent, c);
     while (a != b) {
       if (a < b) { int t = a; a = b; b = t; }   // link the larger root a under b
@@ -213,7 +229,7 @@ __device__ void bitonic_sort_int(int* a, int m) {
 // Mode 0 needs a power of two >= the largest block of ints of dynamic shared
 // memory.
 __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
-                            const int* plate, const int* rowptr, const int* col,
+                            const int* plate, long long nrow, const int* rowptr, const int* col,
                             const int* instage,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
@@ -255,13 +271,13 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
       if (cc == r) continue;
       if (instage[cc]) {
         if (mode == 0 &&
-            keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) {
+            keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) {
           bl = max(bl, i - pos[cc]);
           bu = max(bu, pos[cc] - i);
         }
         continue;
       }
-      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) continue;
       ++links;
       if (pstage[cc] < 0) { over = true; continue; }
       cand += plen[cc];
@@ -289,7 +305,7 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
     for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
       int cc = col[p];
       if (cc == r || instage[cc]) continue;
-      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, r, cc))) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) continue;
       int st = pstage[cc];
       if (st < 0) continue;
       const int* pc = pool.col[st] + poff[cc];
@@ -338,7 +354,8 @@ struct CompArgs {
   int B;
   const int* off_row;
   const int* rank;
-  const int* plate;
+  const int* plate;          // input fracture per row, then coarsening network per row
+  long long nrow;
   const int* rowptr;
   const int* col;
   const double* val;
@@ -388,7 +405,7 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
       double av = a.val[p];
       if (cc == r) { d += av - a.TD[r]; continue; }
       double T = -av;
-      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, r, cc))) {
+      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, a.nrow, r, cc))) {
         if (a.instage[cc]) {
           int pc = a.pos[cc];
           if (pc < 0 || pc >= n || i - pc > bl || pc - i > bu) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
@@ -442,16 +459,23 @@ __global__ void k_comp_solve(CompArgs a, long long slice, double* gwork) {
   comp_solve<G>(a, a.comp_list[idx], M, red);
 }
 
-// truncation (Sec. 4.3) and CSR of P
+// truncation (Sec. 4.3) and CSR of P.  keep_all[c] (instance-local column c)
+// marks a basis function none of whose entries outside its node cell reaches
+// alpha: truncation keeps all of its entries, so no basis function is reduced
+// to its own node cell (a zero column of R^FV A P otherwise).
+__device__ inline bool trunc_keep(double v, int c, double alpha, const int* keep_all) {
+  return alpha <= 0.0 || fabs(v) >= alpha || keep_all[c];
+}
+
 __device__ inline void trunc_row(const int* pc, const double* pv, int len, double alpha,
-                                 int* cnt, double* sum, int* only) {
+                                 const int* keep_all, int* cnt, double* sum, int* only) {
   int c = 0, amax = -1;
   double s = 0.0, vmax = -1.0;
   for (int q = 0; q < len; ++q) {
     double v = pv[q];
     if (v == 0.0) continue;
     if (fabs(v) > vmax) { vmax = fabs(v); amax = q; }
-    if (alpha <= 0.0 || fabs(v) >= alpha) { ++c; s += v; }
+    if (trunc_keep(v, pc[q], alpha, keep_all)) { ++c; s += v; }
   }
   *only = -1;
   if (c == 0 && amax >= 0) { c = 1; s = pv[amax]; *only = amax; }
@@ -459,31 +483,56 @@ __device__ inline void trunc_row(const int* pc, const double* pv, int len, doubl
   *sum = s;
 }
 
+// survives[nc_off + c] = 1 when column c has an entry of magnitude >= alpha
+// outside its node cell's row (vertex rows are the pool's last stage)
+__global__ void k_p_survive(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* pstage, const int* poff, const int* plen, Pool pool,
+                            int* survives) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  int st = pstage[r];
+  if (st == NSTAGE) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  if (I.alpha <= 0.0) return;
+  const int* pc = pool.col[st] + poff[r];
+  const double* pv = pool.val[st] + poff[r];
+  for (int q = 0; q < plen[r]; ++q)
+    if (fabs(pv[q]) >= I.alpha) survives[I.nc_off + pc[q]] = 1;
+}
+
+// keep_all = 1 - survives, in place
+__global__ void k_p_keep_all(long long nct, int* flag) {
+  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nct) flag[j] = flag[j] ? 0 : 1;
+}
+
 __global__ void k_p_count(const Inst* inst, int B, const int* off_row, long long nrow,
                           const int* pstage, const int* poff, const int* plen, Pool pool,
-                          int* cnt) {
+                          const int* keep_all, int* cnt) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
   int st = pstage[r];
   int c = 0, only;
   double s;
-  trunc_row(pool.col[st] + poff[r], pool.val[st] + poff[r], plen[r], I.alpha, &c, &s, &only);
+  trunc_row(pool.col[st] + poff[r], pool.val[st] + poff[r], plen[r], I.alpha, keep_all + I.nc_off,
+            &c, &s, &only);
   cnt[r] = c;
 }
 
 __global__ void k_p_fill(const Inst* inst, int B, const int* off_row, long long nrow,
                          const int* pstage, const int* poff, const int* plen, Pool pool,
-                         const int* p_ptr, int* p_col, double* p_val) {
+                         const int* keep_all, const int* p_ptr, int* p_col, double* p_val) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
   int st = pstage[r];
   const int* pc = pool.col[st] + poff[r];
   const double* pv = pool.val[st] + poff[r];
+  const int* ka = keep_all + I.nc_off;
   int c, only;
   double s;
-  trunc_row(pc, pv, plen[r], I.alpha, &c, &s, &only);
+  trunc_row(pc, pv, plen[r], I.alpha, ka, &c, &s, &only);
   int o = p_ptr[r];
   if (only >= 0) {
     p_col[o] = pc[only];
@@ -494,7 +543,7 @@ __global__ void k_p_fill(const Inst* inst, int B, const int* off_row, long long 
   for (int q = 0; q < plen[r]; ++q) {
     double v = pv[q];
     if (v == 0.0) continue;
-    if (I.alpha <= 0.0 || fabs(v) >= I.alpha) {
+    if (trunc_keep(v, pc[q], I.alpha, ka)) {
       p_col[o] = pc[q];
       p_val[o] = scale ? v / s : v;
       ++o;
@@ -533,9 +582,9 @@ int phase_basis(Batch& b) {
     fams::note_launch(), k_vertex_rows<<<grid_for(nct, T), T, 0, st>>>(b.d_inst, b.B, b.off_nc, nct, b.node_cell, vcol,
                                                   vval, pstage, poff, plen);
   int* plate = nullptr;
-  FAMS_TRY(b.scratch((void**)&plate, sizeof(int) * (nrow + 1)));
-  fams::note_launch(), k_row_plate<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow,
-                                                                     b.f_cfirst, b.tot_fr, plate);
+  FAMS_TRY(b.scratch((void**)&plate, sizeof(int) * (2 * nrow + 1)));
+  fams::note_launch(), k_row_plate<<<grid_for(nrow, T), T, 0, st>>>(
+      b.d_inst, b.B, b.off_row, nrow, b.f_cfirst, b.f_sfirst, b.f_ns, b.s_net, b.tot_fr, plate);
   int *label = nullptr, *instage = nullptr, *flag = nullptr, *rscan = nullptr;
   int *comp_of = nullptr, *pos = nullptr;
   FAMS_TRY(b.scratch((void**)&label, sizeof(int) * (nrow + 1)));
@@ -590,7 +639,7 @@ int phase_basis(Batch& b) {
                 std::to_string(MEMBER_SORT_MAX) + " are supported");
       return FAMS_ECAPACITY;
     }
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 0, ncols, nullptr, nullptr, bw, b.d_err);
     FAMS_CUDA(cudaGetLastError());
@@ -598,7 +647,7 @@ int phase_basis(Batch& b) {
     long long totc = 0;
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col,
+    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
                                             instage, coff, members, pos, pstage, poff, plen, pool,
                                             s, 1, ncols, colptr, colbuf, nullptr, b.d_err);
     // host plan: pool offsets, and the blocks by size class (doubles of
@@ -635,7 +684,7 @@ int phase_basis(Batch& b) {
     }
     pool.col[s] = ocol;
     pool.val[s] = oval;
-    CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, b.rowptr, b.col, b.val, b.TD, instage,
+    CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col, b.val, b.TD, instage,
                 nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};
     // the size classes are disjoint sets of blocks: lists and workspace on the
@@ -701,15 +750,21 @@ int phase_basis(Batch& b) {
       return FAMS_EINVAL;
     }
   }
+  int* keep_all = nullptr;
+  FAMS_TRY(b.scratch((void**)&keep_all, sizeof(int) * (nct + 1)));
+  FAMS_CUDA(cudaMemsetAsync(keep_all, 0, sizeof(int) * (nct + 1), st));
+  fams::note_launch(), k_p_survive<<<grid_for(nrow, T), T, 0, st>>>(
+      b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen, pool, keep_all);
+  if (nct > 0) fams::note_launch(), k_p_keep_all<<<grid_for(nct, T), T, 0, st>>>(nct, keep_all);
   fams::note_launch(), k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
-                                             pool, cnt);
+                                             pool, keep_all, cnt);
   long long pnnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.p_ptr, nrow, &pnnz));
   b.tot_pnnz = pnnz;
   FAMS_TRY(b.alloc((void**)&b.p_col, sizeof(int) * (pnnz + 1)));
   FAMS_TRY(b.alloc((void**)&b.p_val, sizeof(double) * (pnnz + 1)));
   fams::note_launch(), k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
-                                            pool, b.p_ptr, b.p_col, b.p_val);
+                                            pool, keep_all, b.p_ptr, b.p_col, b.p_val);
   // P^T with global coarse rows (restriction R^FE and the coarse operator)
   int* gcol = nullptr;
   FAMS_TRY(b.scratch((void**)&gcol, sizeof(int) * (pnnz + 1)));

@@ -9,7 +9,8 @@
 // Table 2 runs on each network (start = lowest-index cell of degree 1, else
 // the lowest cell; neighbours in ascending index; FIFO queues; a candidate is
 // dropped from Q_vertex when its level is lowered).  3D plates of a network
-// share one vertical grid of frac_cz layers per block.
+// share one vertical grid of frac_cz layers per block; crossing plates join a
+// network only when their layer ranges are equal.
 #include <algorithm>
 #include <climits>
 
@@ -67,9 +68,16 @@ __global__ void k_strike_deg(const int* f_sfirst, const int* f_ns, long long nfr
   deg[gs] = (s > 0) + (s + 1 < f_ns[gf]);
 }
 
+// plates of a 3D network share one uniform vertical coarse grid (Sec. 4.3):
+// two crossing plates join the strike graph only when their layer ranges are
+// equal (their fracture-fracture connections stay in A either way)
+__device__ inline bool same_layers(const Inst& I, const int* f_k0, const int* f_nk, int fa, int fb) {
+  return I.dim != 3 || (f_k0[fa] == f_k0[fb] && f_nk[fa] == f_nk[fb] && f_nk[fa] > 0);
+}
+
 __global__ void k_strike_inter_deg(const Inst* inst, int B, const int* off_pair, long long npair,
                                    const int* hit, const int* sa, const int* sb,
-                                   const int* f_sfirst, int* deg) {
+                                   const int* f_sfirst, const int* f_k0, const int* f_nk, int* deg) {
   long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= npair || !hit[gp]) return;
   int ii = find_segment(off_pair, B + 1, gp);
@@ -80,6 +88,7 @@ __global__ void k_strike_inter_deg(const Inst* inst, int B, const int* off_pair,
     if (q < off + cnt) { a = i; b = i + 1 + (q - off); break; }
     off += cnt;
   }
+  if (!same_layers(I, f_k0, f_nk, I.fr_off + a, I.fr_off + b)) return;
   atomicAdd(&deg[f_sfirst[I.fr_off + a] + sa[gp]], 1);
   atomicAdd(&deg[f_sfirst[I.fr_off + b] + sb[gp]], 1);
 }
@@ -98,7 +107,8 @@ __global__ void k_strike_fill(const int* f_sfirst, const int* f_ns, long long nf
 
 __global__ void k_strike_inter_fill(const Inst* inst, int B, const int* off_pair, long long npair,
                                     const int* hit, const int* sa, const int* sb,
-                                    const int* f_sfirst, const int* ptr, int* cursor, int* adj) {
+                                    const int* f_sfirst, const int* f_k0, const int* f_nk,
+                                    const int* ptr, int* cursor, int* adj) {
   long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= npair || !hit[gp]) return;
   int ii = find_segment(off_pair, B + 1, gp);
@@ -109,6 +119,7 @@ __global__ void k_strike_inter_fill(const Inst* inst, int B, const int* off_pair
     if (q < off + cnt) { a = i; b = i + 1 + (q - off); break; }
     off += cnt;
   }
+  if (!same_layers(I, f_k0, f_nk, I.fr_off + a, I.fr_off + b)) return;
   int u = f_sfirst[I.fr_off + a] + sa[gp];
   int v = f_sfirst[I.fr_off + b] + sb[gp];
   adj[ptr[u] + atomicAdd(&cursor[u], 1)] = v;
@@ -350,7 +361,8 @@ int phase_coarse(Batch& b) {
   if (ns > 0) fams::note_launch(), k_strike_deg<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, deg);
   if (np > 0)
     fams::note_launch(), k_strike_inter_deg<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
-                                                      b.inter_sa, b.inter_sb, b.f_sfirst, deg);
+                                                      b.inter_sa, b.inter_sb, b.f_sfirst, b.f_k0,
+                                                      b.f_nk, deg);
   long long nadj = 0;
   FAMS_TRY(exclusive_scan(b, deg, sptr, ns, &nadj));
   FAMS_TRY(b.scratch((void**)&adj, sizeof(int) * (nadj + 1)));
@@ -358,8 +370,8 @@ int phase_coarse(Batch& b) {
     fams::note_launch(), k_strike_fill<<<grid_for(ns, T), T, 0, st>>>(b.f_sfirst, b.f_ns, nfr, ns, sptr, cursor, adj);
   if (np > 0)
     fams::note_launch(), k_strike_inter_fill<<<grid_for(np, T), T, 0, st>>>(b.d_inst, b.B, b.off_pair, np, b.inter_hit,
-                                                       b.inter_sa, b.inter_sb, b.f_sfirst, sptr,
-                                                       cursor, adj);
+                                                       b.inter_sa, b.inter_sb, b.f_sfirst, b.f_k0,
+                                                       b.f_nk, sptr, cursor, adj);
   FAMS_TRY(sort_segments(b, sptr, (int)ns, adj, nullptr, true));
   // networks
   int *lab = nullptr, *flag = nullptr, *rscan = nullptr;
@@ -437,7 +449,7 @@ int phase_coarse(Batch& b) {
       h_dmin[n] = I.dmin;
       h_netinst[n] = i;
       if (I.dim == 3 && (h_k0min[n] != h_k0max[n] || h_nkmin[n] != h_nkmax[n])) {
-        set_error("fracture plates that meet must share their layer range (uniform extrusion)");
+        set_error("internal: a fracture network joins plates of different layer ranges");
         return FAMS_EINVAL;
       }
     }

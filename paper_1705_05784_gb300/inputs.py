@@ -135,12 +135,12 @@ def config_2d_small(seed=1, basis=0, restriction=0):
                    alpha=0.0, name="2d-32x32-1frac")
 
 
-def config_2d_sealed_node(basis=0, restriction=1):
+def config_2d_sealed_node(basis=0, restriction=1, factor=1e-10):
     """config_2d_small with truncation (alpha 1e-2) and the cell at (22, 6), the
-    coarse node of primal block (5, 1), 1e-10 times as permeable as before."""
+    coarse node of primal block (5, 1), `factor` times as permeable as before."""
     p = config_2d_small(basis=basis, restriction=restriction)
     p.perm = p.perm.copy()
-    p.perm[22 + 32 * 6] *= 1e-10
+    p.perm[22 + 32 * 6] *= factor
     p.alpha = 1e-2
     p.name = "2d-32x32-sealed-node"
     return p

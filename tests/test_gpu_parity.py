@@ -53,12 +53,21 @@ def _case(name, variant=0, restriction=1):
         p.fracs = np.array([[1.5, 8.3, 14.5, 8.3, 0.0, 8.0], [8.3, 1.5, 8.3, 14.5, 0.0, 8.0],
                             [2.2, 2.7, 13.6, 12.9, 0.0, 8.0]])
         p.kf = np.array([1e3, 1e4, 1e3])
+    elif name == "3dlayers":
+        # five plates of their own layer ranges: two cross with different
+        # ranges (separate networks), two with the same range (one network)
+        p = inputs.config_3d(16, 16, 10, 1.0, (4, 4, 2), 0, (4, 9), 1e3, (4, 4, 4), 4, 3, seed=6,
+                             basis=variant, restriction=restriction)
+        p.fracs = np.array([[1.5, 4.3, 14.5, 4.3, 0.0, 7.0], [6.3, 1.5, 6.3, 14.5, 3.0, 10.0],
+                            [2.2, 9.7, 13.6, 12.9, 2.0, 8.0], [11.7, 7.1, 10.1, 15.2, 2.0, 8.0],
+                            [3.1, 14.4, 7.9, 14.1, 5.0, 9.0]])
+        p.kf = np.array([1e3, 1e4, 1e3, 1e2, 1e3])
     else:
         raise KeyError(name)
     return p
 
 
-CASES = ["2d32", "2d64", "2d50ragged", "3d", "3dcross"]
+CASES = ["2d32", "2d64", "2d50ragged", "3d", "3dcross", "3dlayers"]
 
 
 @pytest.fixture(scope="module")
@@ -378,6 +387,37 @@ def test_gmres_and_richardson_instances_share_a_batch(built):
     assert np.linalg.norm(xs[1] - xb[0]) / np.linalg.norm(xb[0]) < 1e-10
 
 
+def _interior_connections(p, face, nnc):
+    """The device's fluxes in the oracle's connection order: interior x, y (z)
+    faces, then the matrix-fracture and fracture-fracture connections."""
+    nx, ny = p.nx, p.ny
+    nz = p.nz if p.dim == 3 else 1
+    nfx, nfy = (nx + 1) * ny * nz, nx * (ny + 1) * nz
+    fx = face[:nfx].reshape(nz, ny, nx + 1)
+    fy = face[nfx:nfx + nfy].reshape(nz, ny + 1, nx)
+    parts = [fx[:, :, 1:-1].ravel(), fy[:, 1:-1, :].ravel()]
+    if p.dim == 3:
+        fz = face[nfx + nfy:].reshape(nz + 1, ny, nx)
+        parts.append(fz[1:-1].ravel())
+    return np.concatenate(parts + [nnc])
+
+
+def _balance(sysm, p, face, conn):
+    """Net outflow of every cell of a W/E problem without sources, from the
+    device's face fluxes and connection fluxes."""
+    nx, ny = p.nx, p.ny
+    nz = p.nz if p.dim == 3 else 1
+    fx = face[:(nx + 1) * ny * nz].reshape(nz, ny, nx + 1)
+    ci, cj, _ = osolver.connections(sysm, p)
+    out = np.zeros(sysm.n)
+    np.add.at(out, ci, conn)
+    np.subtract.at(out, cj, conn)
+    xm = np.arange(sysm.n_matrix) % nx
+    out[np.nonzero(xm == 0)[0]] -= fx[:, :, 0].ravel()
+    out[np.nonzero(xm == nx - 1)[0]] += fx[:, :, -1].ravel()
+    return out
+
+
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("name", ["2d32", "2d64", "3d"])
 def test_flux_conservative_and_matches_oracle(built, name, restriction):
@@ -389,36 +429,20 @@ def test_flux_conservative_and_matches_oracle(built, name, restriction):
     # oracle reconstruction from the same iterate
     st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
     flux, dflux, pp, pt = osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
-    nm = g.n_matrix
-    nx, ny = p.nx, p.ny
-    nz = p.nz if p.dim == 3 else 1
-    nfx, nfy = (nx + 1) * ny * nz, nx * (ny + 1) * nz
-    fx = face[:nfx].reshape(nz, ny, nx + 1)
-    fy = face[nfx:nfx + nfy].reshape(nz, ny + 1, nx)
-    parts = [fx[:, :, 1:-1].ravel(), fy[:, 1:-1, :].ravel()]
-    if p.dim == 3:
-        fz = face[nfx + nfy:].reshape(nz + 1, ny, nx)
-        parts.append(fz[1:-1].ravel())
-    gpu_conn = np.concatenate(parts + [nnc])
+    gpu_conn = _interior_connections(p, face, nnc)
     scale = np.abs(flux).max()
     np.testing.assert_allclose(gpu_conn, flux, rtol=0, atol=1e-8 * scale)
-    # cell-by-cell mass balance of the GPU field
-    ci, cj, _ = osolver.connections(sysm, p)
-    out = np.zeros(sysm.n)
-    np.add.at(out, ci, gpu_conn)
-    np.subtract.at(out, cj, gpu_conn)
-    xm = np.arange(nm) % nx
-    west = fx[:, :, 0].ravel()
-    east = fx[:, :, -1].ravel()
-    out[np.nonzero(xm == 0)[0]] -= west
-    out[np.nonzero(xm == nx - 1)[0]] += east
-    # conservative to round-off: every flux is T (p_i - p_j), so a balance
-    # carries errors of order eps T_max |p|_max (the oracle's own imbalance
-    # is of the same size)
+    # cell-by-cell mass balance of the GPU field: conservative to round-off
+    # (every flux is T (p_i - p_j), so a balance carries errors of order
+    # eps T_max |p|_max; the oracle's own imbalance is of the same size)
+    out = _balance(sysm, p, face, gpu_conn)
     _, _, cT = osolver.connections(sysm, p)
     bound = 64 * np.finfo(float).eps * cT.max() * max(np.abs(pt).max(), 1.0)
     assert np.abs(out).max() < bound
-    assert abs(west.sum() - east.sum()) < sysm.n * bound
+    nx, ny = p.nx, p.ny
+    nz = p.nz if p.dim == 3 else 1
+    fx = face[:(nx + 1) * ny * nz].reshape(nz, ny, nx + 1)
+    assert abs(fx[:, :, 0].sum() - fx[:, :, -1].sum()) < sysm.n * bound
 
 
 def test_batch_matches_single(built):
@@ -491,18 +515,16 @@ def test_flux_prepared_beside_the_solve():
             np.testing.assert_allclose(na, nb, rtol=0, atol=1e-9 * sc)
 
 
-def test_flux_reports_a_singular_fv_coarse_system():
-    """The sealed-node instance's R^FV A P is singular by the oracle's scaled
-    pivot test: its reconstruction reports FAMS_EBREAKDOWN, the regular
-    instance of the same batch is reconstructed as alone, and both R^FE
-    solves converge; an R^FV iteration on the sealed instance reports
-    FAMS_EBREAKDOWN from the solve."""
+def test_flux_of_a_sealed_node_instance_is_conservative():
+    """A node cell 1e-10 times less permeable than its neighbours: truncation
+    keeps its whole basis function (none of its off-node entries reaches
+    alpha), so R^FV A P is regular; the batch reconstruction of that
+    instance and of a regular one succeeds, matches the oracle's
+    reconstruction from the same iterate and conserves mass in every cell."""
     fams = _fams()
     sealed = inputs.config_2d_sealed_node(restriction=0)
     plain = inputs.config_2d_small(restriction=0)
     plain.alpha = 1e-2
-    assert osolver.singular_step(oracle.build(sealed)[4].Ac) >= 0
-    assert osolver.singular_step(oracle.build(plain)[4].Ac) == -1
     probs = []
     for q in (sealed, plain):
         q = _gmres(copy.copy(q), 30, 200)
@@ -516,15 +538,50 @@ def test_flux_reports_a_singular_fv_coarse_system():
         N = [np.full(max(1, s["n_nnc"]), 7.0) for s in S]
         status = c.flux_batch_ptr([x.ctypes.data for x in xs], [f.ctypes.data for f in F],
                                   [m.ctypes.data for m in N])
-        assert status == [fams.EBREAKDOWN, 0]
-        assert (F[0] == 7.0).all() and (N[0] == 7.0).all()
-        f1, n1 = c.flux(xs[1], 1)
-        np.testing.assert_array_equal(F[1], f1)
-        np.testing.assert_array_equal(N[1][: S[1]["n_nnc"]], n1)
+        assert status == [0, 0]
+        for i, q in enumerate(probs):
+            g, sysm, co, P, _ = oracle.build(q)
+            st_fv = osolver.setup(sysm, P, co.primal, co.n_coarse, osolver.R_FV)
+            assert osolver.singular_step(st_fv.Ac) == -1
+            flux, dflux, pp, pt = osolver.reconstruct_flux(sysm, q, st_fv, xs[i], co.primal,
+                                                           co.node_cell)
+            gpu_conn = _interior_connections(q, F[i], N[i][: S[i]["n_nnc"]])
+            np.testing.assert_allclose(gpu_conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
+            _, _, cT = osolver.connections(sysm, q)
+            bound = 64 * np.finfo(float).eps * cT.max() * max(np.abs(pt).max(), 1.0)
+            assert np.abs(_balance(sysm, q, F[i], gpu_conn)).max() < bound
+
+
+def test_flux_reports_a_singular_fv_coarse_system():
+    """A node cell sealed to 1e-300: its basis function is 1e-300 outside the
+    node cell and R^FV A P is singular by the oracle's scaled pivot test.  The
+    R^FV iteration reports FAMS_EBREAKDOWN from the solve, and the
+    reconstruction of that instance reports FAMS_EBREAKDOWN and leaves its
+    buffers untouched, while a regular instance of the same batch is
+    reconstructed as alone."""
+    fams = _fams()
+    sealed = inputs.config_2d_sealed_node(restriction=0, factor=1e-300)
+    plain = inputs.config_2d_small(restriction=0)
+    plain.alpha = 1e-2
+    assert osolver.singular_step(oracle.build(sealed)[4].Ac) >= 0
+    assert osolver.singular_step(oracle.build(plain)[4].Ac) == -1
     with fams.Context(sealed) as c:
         with pytest.raises(fams.FamsError) as e:
             c.solve(tol=1e-8)
         assert e.value.status == fams.EBREAKDOWN
+    x_plain = oracle.run(plain).p
+    with fams.Context([sealed, plain]) as c:
+        S = [c.sizes(i) for i in range(2)]
+        xs = [np.zeros(S[0]["n_matrix"] + S[0]["n_frac"]), x_plain]
+        F = [np.full(s["n_faces"], 7.0) for s in S]
+        N = [np.full(max(1, s["n_nnc"]), 7.0) for s in S]
+        status = c.flux_batch_ptr([x.ctypes.data for x in xs], [f.ctypes.data for f in F],
+                                  [m.ctypes.data for m in N])
+        assert status == [fams.EBREAKDOWN, 0]
+        assert (F[0] == 7.0).all() and (N[0] == 7.0).all()
+        f1, n1 = c.flux(x_plain, 1)
+        np.testing.assert_array_equal(F[1], f1)
+        np.testing.assert_array_equal(N[1][: S[1]["n_nnc"]], n1)
 
 
 def _degenerate(dim, nx, ny, nz, coarsen, seed=3):

@@ -110,20 +110,63 @@ def test_matrix_rank_counts_2d():
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("dim", [2, 3, "3layers"])
 def test_staged_equals_appendix_formulas(variant, dim):
+    """dim "3layers": plates of random heights, some crossing with other
+    layer ranges (separate networks that stay connected in A)."""
     if dim == 2:
         p = inputs.config_2d(24, 1.0, 4.0, 4, (6, 16), 1e3, 4, 4, seed=7, basis=variant)
-    else:
+    elif dim == 3:
         p = inputs.config_3d(12, 12, 8, 1.0, (4, 4, 2), 3, (4, 9), 1e3, (4, 4, 4), 4, 4,
                              seed=3, basis=variant)
         p.fracs[:, 4] = 0.0
         p.fracs[:, 5] = 8.0
+    else:
+        p = _layered_plates(variant)
     g, s, c = _setup(p)
     plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
-    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
-    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant, plate)
+    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, variant, plate,
+                                   c.row_net)
+    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, variant, plate,
+                                     c.row_net)
     assert abs(P1 - P2).max() < 1e-12
+    assert np.abs(np.asarray(P1.sum(axis=1)).ravel() - 1).max() < 1e-12
+
+
+def _layered_plates(variant):
+    """16x16x10 box, five plates of random layer ranges; plates 0 and 1 cross
+    with different ranges, plates 2 and 3 cross with the same range."""
+    p = inputs.config_3d(16, 16, 10, 1.0, (4, 4, 2), 0, (4, 9), 1e3, (4, 4, 4), 4, 3, seed=6,
+                         basis=variant)
+    p.fracs = np.array([[1.5, 4.3, 14.5, 4.3, 0.0, 7.0], [6.3, 1.5, 6.3, 14.5, 3.0, 10.0],
+                        [2.2, 9.7, 13.6, 12.9, 2.0, 8.0], [11.7, 7.1, 10.1, 15.2, 2.0, 8.0],
+                        [3.1, 14.4, 7.9, 14.1, 5.0, 9.0]])
+    p.kf = np.array([1e3, 1e4, 1e3, 1e2, 1e3])
+    return p
+
+
+def test_crossing_plates_of_other_layer_ranges_are_separate_networks():
+    p = _layered_plates(0)
+    g, s, c = _setup(p)
+    crossings = {(fa, fb) for fa, fb, _, _ in g.intersections}
+    assert (0, 1) in crossings and (2, 3) in crossings
+    lab, nets = coarsen.fracture_networks(g.strike_adj)
+    sf = g.strike_first
+    net_of = [int(lab[sf[f]]) for f in range(len(p.fracs))]
+    assert net_of[0] != net_of[1] and net_of[2] == net_of[3]
+    # the crossing still couples the two plates in A (through the f-f links)
+    ff = set(zip(g.cell_frac[g.ff_a], g.cell_frac[g.ff_b]))
+    assert (0, 1) in ff
+    # ... but no dual block of a fracture stage spans two networks (Coupled
+    # blocks may still join two networks through matrix cells)
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    for variant in range(3):
+        for cells in basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, variant, plate,
+                                        c.row_net):
+            assert len({int(c.row_net[r]) for r in cells if c.row_net[r] >= 0}) <= 1
+    merged = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, 0, plate, None)
+    assert any(len({int(c.row_net[r]) for r in cells if c.row_net[r] >= 0}) > 1
+               for cells in merged)
 
 
 def _crossing_plates(variant):
@@ -243,3 +286,108 @@ def test_truncation_example():
     # a row whose every entry is below alpha keeps its largest one
     R = basis.truncate(sp.csr_matrix(np.array([[0.3, 0.3, 0.4]])), 0.5).toarray()
     np.testing.assert_allclose(R, [[0.0, 0.0, 1.0]])
+
+
+def test_truncation_never_reduces_a_basis_function_to_its_node_cell():
+    """Columns 0..2 have node cells 0..2.  Every entry of column 2 outside its
+    node row is below alpha, so column 2 keeps all of them (rows rescaled as
+    usual); columns 0 and 1 are truncated as before.  Worked by hand."""
+    P = sp.csr_matrix(np.array([[1.0, 0.0, 0.0],
+                                [0.0, 1.0, 0.0],
+                                [0.0, 0.0, 1.0],
+                                [0.6, 0.39, 0.005],
+                                [0.004, 0.988, 0.008]]))
+    Q = basis.truncate(P, 1e-2, node_cell=[0, 1, 2]).toarray()
+    np.testing.assert_allclose(Q[:3], np.eye(3), rtol=0, atol=0)
+    np.testing.assert_allclose(Q[3], [0.6 / 0.995, 0.39 / 0.995, 0.005 / 0.995], rtol=1e-15)
+    np.testing.assert_allclose(Q[4], [0.0, 0.988 / 0.996, 0.008 / 0.996], rtol=1e-15)
+    # without the node cells column 2 would vanish outside its node row
+    Q0 = basis.truncate(P, 1e-2).toarray()
+    np.testing.assert_allclose(Q0[3], [0.6 / 0.99, 0.39 / 0.99, 0.0], rtol=1e-15)
+    np.testing.assert_allclose(Q0[4], [0.0, 1.0, 0.0], rtol=1e-15)
+    # one off-node entry at alpha is enough for the column to be truncated
+    P2 = P.toarray()
+    P2[4] = [0.0, 0.99, 0.01]
+    Q2 = basis.truncate(sp.csr_matrix(P2), 1e-2, node_cell=[0, 1, 2]).toarray()
+    np.testing.assert_allclose(Q2[3], [0.6 / 0.99, 0.39 / 0.99, 0.0], rtol=1e-15)
+    np.testing.assert_allclose(Q2[4], [0.0, 0.99, 0.01], rtol=1e-15)
+
+
+def _plate_cases():
+    cases, cur = [], None
+    for line in open(os.path.join(GOLDEN, "coarse3d_plates.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, _, val = line.partition(" ")
+        if key == "case":
+            cur = {"name": val, "plates": [], "rank": [], "block": []}
+        elif key == "end":
+            cases.append(cur)
+        elif key == "plate":
+            cur["plates"].append([float(t) for t in val.split()])
+        elif key in ("rank", "block"):
+            cur[key].extend(int(t) for t in val.split())
+        elif key in ("grid", "coarsen", "nodes"):
+            cur[key] = [int(t) for t in val.split()]
+        else:
+            cur[key] = int(val)
+    return cases
+
+
+@pytest.mark.parametrize("case", _plate_cases(), ids=lambda c: c["name"])
+def test_3d_plate_coarsening_golden(case):
+    """Ranks, fracture coarse blocks and node cells of every plate cell
+    against hand-worked cases (a wrong vertical node layer, an E/F swap or a
+    misnumbered block turns this red)."""
+    nx, ny, nz = case["grid"]
+    pl = np.array(case["plates"])
+    p = inputs.Problem(dim=3, nx=nx, ny=ny, nz=nz, perm=np.ones(nx * ny * nz), fracs=pl,
+                       kf=np.full(len(pl), 1e3), coarsen=tuple(case["coarsen"]),
+                       frac_dmin=case["dmin"], frac_cz=case["cz"])
+    g = geometry.build_geometry(p)
+    c = coarsen.build_coarse(p, g)
+    nm = g.n_matrix
+    assert g.n_frac == len(case["rank"])
+    assert c.n_coarse == case["ncoarse"]
+    assert list(c.rank[nm:]) == case["rank"]
+    assert list(c.primal[nm:] - c.n_coarse_matrix) == case["block"]
+    assert list(c.node_cell[c.n_coarse_matrix:] - nm) == case["nodes"]
+
+
+def _piece_cases():
+    out, cur = [], None
+    for line in open(os.path.join(GOLDEN, "oblique_pieces.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, _, val = line.partition(" ")
+        if key == "case":
+            cur = {"name": val, "pieces": {}}
+        elif key == "end":
+            out.append(cur)
+        elif key == "seg":
+            cur["seg"] = [float(t) for t in val.split()]
+        elif key == "piece":
+            s, ix, iy, num, den = (int(t) for t in val.split())
+            cur["pieces"].setdefault(s, []).append((ix, iy, num / den))
+        else:
+            cur[key] = [int(t) for t in val.split()]
+    return out
+
+
+@pytest.mark.parametrize("case", _piece_cases(), ids=lambda c: c["name"])
+def test_oblique_pieces_golden(case):
+    """Matrix cells and lengths of the pieces of oblique fracture cells (Eqs.
+    4-6: A_ij is the overlap length times the depth) against hand-worked
+    parameter crossings."""
+    ax, ay, bx, by = case["seg"]
+    n = case["n"][0]
+    nx, ny = case["grid"]
+    L = float(np.hypot(bx - ax, by - ay))
+    for s in range(n):
+        got = geometry.piece_overlaps(ax, ay, bx, by, n, s, 1.0, 1.0, nx, ny)
+        want = case["pieces"][s]
+        assert [(i, j) for i, j, _ in got] == [(i, j) for i, j, _ in want]
+        np.testing.assert_allclose([ln for _, _, ln in got], [f * L for _, _, f in want],
+                                   rtol=1e-14, atol=0)

@@ -271,22 +271,47 @@ def test_singular_step_pins():
     assert solver.singular_step(np.zeros((0, 0))) == -1
 
 
-def test_sealed_node_makes_the_fv_coarse_system_singular():
-    """A node cell 1e-10 times less permeable than its neighbours: its basis
-    function truncates to the node cell alone, so its R^FV column sums A's
-    column over its own primal block (zero); the R^FE system stays regular."""
+def test_sealed_node_keeps_its_basis_function_and_a_conservative_field():
+    """A node cell 1e-10 times less permeable than its neighbours: every entry
+    of its basis function outside the node cell is below alpha, so truncation
+    keeps the whole column (it is not reduced to the node cell).  R^FV A P is
+    then regular and the reconstruction conserves mass in every cell to
+    round-off (every flux is T (p_i - p_j): 64 eps T_max |p|_max, 1.4e-10 with
+    the fracture's T of 1e4, 3e-16 relative); with the node reduced to its
+    cell (truncation without the node cells) the column of R^FV A P vanishes
+    and the system is singular."""
     p = inputs.config_2d_sealed_node(restriction=solver.R_FV)
     g, sysm, c, P, st = oracle.build(p)
     node = 22 + 32 * 6
     J = int(np.nonzero(c.node_cell == node)[0][0])
     col = P.tocsc()[:, J]
-    assert col.nnz == 1 and col.indices[0] == node and col.data[0] == 1.0
-    Afv = st.Ac
-    assert np.abs(Afv[:, J]).max() <= 1e-14 * np.abs(Afv).max()
-    assert solver.singular_step(Afv) >= 0
-    sfe = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FE)
-    assert solver.singular_step(sfe.Ac) == -1
-    # the same inputs without the sealed cell: both regular
+    assert col.nnz > 1 and np.abs(col.data[col.indices != node]).max() < p.alpha
+    assert solver.singular_step(st.Ac) == -1
+    x = oracle.run(p).p
+    flux, dflux, _, _ = solver.reconstruct_flux(sysm, p, st, x, c.primal, c.node_cell)
+    bal = solver.cell_balance(sysm, p, flux, dflux)
+    _, _, cT = solver.connections(sysm, p)
+    assert np.abs(bal).max() < 64 * np.finfo(float).eps * cT.max() * max(np.abs(x).max(), 1.0)
+    # the column reduced to its node cell: R^FV column J sums A's column over
+    # the node's own primal block, zero
+    P_old = basis.truncate(basis.prolongation_staged(
+        sysm.A0, c.rank, c.medium, c.node_cell, p.basis,
+        np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])), p.alpha)
+    colo = P_old.tocsc()[:, J]
+    assert colo.nnz == 1 and colo.indices[0] == node and colo.data[0] == 1.0
+    Aold = solver.coarse_operator(solver.restriction(P_old, c.primal, c.n_coarse, solver.R_FV),
+                                  sysm.A, P_old)
+    assert np.abs(Aold[:, J]).max() <= 1e-14 * np.abs(Aold).max()
+    assert solver.singular_step(Aold) >= 0
+
+
+def test_a_node_sealed_to_underflow_still_makes_the_fv_system_singular():
+    """A node cell 1e-300 times as permeable: its basis function is 1e-300
+    outside the node cell, so R^FV A P is singular by the scaled pivot test
+    (and so is R^FE A P, whose diagonal entry of that node is 1e-300)."""
+    p = inputs.config_2d_sealed_node(restriction=solver.R_FV, factor=1e-300)
+    g, sysm, c, P, st = oracle.build(p)
+    assert solver.singular_step(st.Ac) >= 0
     q = inputs.config_2d_small(restriction=solver.R_FV)
     q.alpha = 1e-2
     _, _, _, _, sq = oracle.build(q)
