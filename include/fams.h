@@ -205,10 +205,11 @@ int fams_update_basis(fams_ctx* ctx, const double* const* mobility_scale, double
    and ILU corrections, the coarse vectors, status words and residual
    history) live in one device array compiled into the library, of fixed size
    (the FAMS_STATIC_MAX_* limits; every GPU that loads the library holds it
-   until the process exits).  The first call on a device looks up that
-   array's address on the context's device (which also loads the library's
-   kernels there): make the first call on each device before any stream
-   capture starts.
+   until the process exits).  Every call looks up that array's address on the
+   context's device (cudaGetSymbolAddress, a host query), so the address
+   stays right if the device's context is recreated; the first call on a
+   device also loads the library's kernels there: make the first call on each
+   device before any stream capture starts.
    ctx must be a single-instance context; x (in initial guess, out pressure)
    and rhs (nullable) may be host or device memory.  Instances above a limit
    are rejected with FAMS_ECAPACITY before anything runs.  Every call, from any
@@ -343,6 +344,11 @@ void fams_server_destroy(fams_server* s);
 /* Number of CUDA kernels the library has launched since it was loaded (all
    contexts, all threads); the difference across a call counts its launches. */
 long long fams_launch_count(void);
+
+/* Number of device allocations the library has made since it was loaded (all
+   contexts, all threads); the difference across a call counts its
+   allocations (0 across fams_solve_static). */
+long long fams_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -20,10 +20,12 @@ constexpr uint64_t POOL_KEEP = 32ull << 30;   // bytes of freed device memory th
 namespace {
 thread_local std::string g_err;
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 int Batch::upload_inst() {
   std::vector<int> o(8 * (B + 1));
@@ -636,5 +638,7 @@ const char* fams_strerror(int s) {
 const char* fams_last_error(void) { return g_err.c_str(); }
 
 long long fams_launch_count(void) { return g_launches.load(); }
+
+long long fams_alloc_count(void) { return g_allocs.load(); }
 
 }  // extern "C"

@@ -208,6 +208,7 @@ struct Batch {
       set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       return FAMS_ENOMEM;
     }
+    note_alloc();
     owned.push_back(*p);
     return FAMS_OK;
   }
@@ -218,6 +219,7 @@ struct Batch {
       set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
       return FAMS_ENOMEM;
     }
+    note_alloc();
     tmp.push_back(*p);
     return FAMS_OK;
   }

@@ -83,6 +83,7 @@ struct Dev;  // device arrays of a batch (defined in batch.cuh)
 
 void set_error(const std::string& msg);
 void note_launch();  // counts every kernel launch of the library (fams_launch_count)
+void note_alloc();   // counts every device allocation of the library (fams_alloc_count)
 
 inline int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;

@@ -18,7 +18,6 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <mutex>
 
 #include "batch.cuh"
 
@@ -1109,36 +1108,25 @@ constexpr long long STATIC_DOUBLES = 6 * STATIC_ROWS + 2 * STATIC_COARSE + STATI
 static_assert(STATIC_ROWS % 32 == 0 && STATIC_COARSE % 32 == 0 && STATIC_STAT % 32 == 0,
               "parts of the static work array must stay 256-byte aligned");
 static_assert(STATIC_STAT >= STAT_W, "status words do not fit");
-constexpr int MAX_DEVICES = 64;
 }  // namespace
 
 // In host code this name only stands for the device array: its device address
-// comes from cudaGetSymbolAddress, once per device.
+// comes from cudaGetSymbolAddress.
 static __device__ __align__(256) double g_solve_static_work[STATIC_DOUBLES];
 
 namespace {
-std::mutex g_static_mu;
-double* g_static_ptr[MAX_DEVICES] = {};
-
-// device address of the work array on `dev` (current device); looked up on
-// the first call on each device
-int static_work(int dev, double** out) {
-  if (dev < 0 || dev >= MAX_DEVICES) {
-    set_error("device ordinal beyond the static work table");
-    return FAMS_EINVAL;
+// device address of the work array in the current device's context, looked
+// up on every call (a cheap host query): a cached address would go stale when
+// the context is recreated (cudaDeviceReset) and the module loads elsewhere
+int static_work(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_solve_static_work);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("cudaGetSymbolAddress of the static work array: ") +
+              cudaGetErrorString(e));
+    return FAMS_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_solve_static_work);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("cudaGetSymbolAddress of the static work array: ") +
-                cudaGetErrorString(e));
-      return FAMS_ECUDA;
-    }
-    g_static_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_static_ptr[dev];
+  *out = static_cast<double*>(p);
   return FAMS_OK;
 }
 
@@ -1171,7 +1159,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
     return FAMS_ECAPACITY;
   }
   double* w = nullptr;
-  FAMS_TRY(static_work(b.device, &w));
+  FAMS_TRY(static_work(&w));
   double* q = w;
   double* xs = w + STATIC_ROWS;
   double* dp = w + 3 * STATIC_ROWS;

@@ -95,6 +95,8 @@ def _load():
     lib.fams_last_error.restype = C.c_char_p
     lib.fams_launch_count.argtypes = []
     lib.fams_launch_count.restype = C.c_longlong
+    lib.fams_alloc_count.argtypes = []
+    lib.fams_alloc_count.restype = C.c_longlong
     lib.fams_server_create.argtypes = [P(fams_server_opts), P(C.c_void_p)]
     lib.fams_server_submit.argtypes = [C.c_void_p, P(fams_grid), P(C.c_double), P(fams_fracs),
                                        P(fams_opts), P(C.c_double), P(C.c_longlong)]
@@ -144,6 +146,11 @@ def _args(prob):
 def launch_count():
     """Kernels launched by the library since it was loaded."""
     return int(lib.fams_launch_count())
+
+
+def alloc_count():
+    """Device allocations made by the library since it was loaded."""
+    return int(lib.fams_alloc_count())
 
 
 class Context:
@@ -271,7 +278,7 @@ class Context:
         st = fams_stats()
         s = lib.fams_solve_static(self.h, None if r is None else r.ctypes.data_as(C.c_void_p),
                                   x.ctypes.data_as(C.c_void_p), tol, C.byref(st))
-        _check(s, allow=(ENOCONV,))
+        _check(s, allow=(ENOCONV, EBREAKDOWN))
         return x, dict(iterations=st.iterations, rel_residual=st.rel_residual,
                        converged=bool(st.converged), solve_ms=st.solve_ms, status=s)
 

@@ -36,7 +36,9 @@ def test_static_matches_solve_on_consecutive_calls():
         rhs = np.random.default_rng(5).standard_normal(na) * 1e-3
         ref_a = ca.solve(rhs=rhs, tol=1e-8)
         ref_b = cb.solve(tol=1e-8)
-        # three calls in a row through the shared array: a, b (larger), a again
+        # three calls in a row through the shared array: a, b (larger), a
+        # again; none of them allocates device memory
+        n_alloc = fams.alloc_count()
         xa1, sa1 = ca.solve_static(rhs=rhs, tol=1e-8)
         _agree(xa1, sa1, ref_a[0][0], ref_a[1][0])
         xb, sb = cb.solve_static(tol=1e-8)
@@ -44,6 +46,10 @@ def test_static_matches_solve_on_consecutive_calls():
         xa2, sa2 = ca.solve_static(rhs=rhs, tol=1e-8)
         _agree(xa2, sa2, ref_a[0][0], ref_a[1][0])
         assert sa1["converged"] and sb["converged"]
+        assert fams.alloc_count() == n_alloc
+        # the allocating entry point does allocate (the counter works)
+        ca.solve(rhs=rhs, tol=1e-8)
+        assert fams.alloc_count() > n_alloc
 
 
 def test_static_from_a_warm_start_and_device_buffers():
@@ -85,3 +91,45 @@ def test_static_rejects_batch_and_oversize():
         s = fams.lib.fams_solve_static(cbig.h, None, x.ctypes.data_as(fams.C.c_void_p), 1e-8, None)
         assert s == fams.ECAPACITY
         assert b"max_iter" in fams.lib.fams_last_error()
+
+
+def _line(n, cx):
+    """A one-row 2D grid of n cells, coarsening cx along it (cheap to set up
+    at the sizes of the static limits)."""
+    perm = 10.0 ** inputs.gaussian_field((n, 1), 1.0, 8.0, 11)
+    return inputs.Problem(dim=2, nx=n, ny=1, nz=1, perm=perm, fracs=np.zeros((0, 4)),
+                          kf=np.zeros(0), coarsen=(cx, 1, 1), frac_dmin=5, basis=0,
+                          restriction=1, alpha=0.0)
+
+
+def test_static_rejects_instances_above_its_limits():
+    """One unknown above FAMS_STATIC_MAX_ROWS, and one coarse unknown above
+    FAMS_STATIC_MAX_COARSE: FAMS_ECAPACITY with the limit named, nothing run."""
+    from paper_1705_05784_gb300 import fams
+    cases = [(_line(262144 + 1, 64), b"unknowns; fams_solve_static holds at most 262144"),
+             (_line(2 * 16384 + 2, 2), b"coarse unknowns; fams_solve_static holds at most 16384")]
+    for p, msg in cases:
+        with fams.Context(p) as c:
+            S = c.sizes()
+            assert (S["n_matrix"] > 262144) == (b"at most 262144" in msg)
+            x = np.zeros(S["n_matrix"] + S["n_frac"])
+            n_launch = fams.launch_count()
+            s = fams.lib.fams_solve_static(c.h, None, x.ctypes.data_as(fams.C.c_void_p), 1e-8,
+                                           None)
+            assert s == fams.ECAPACITY
+            assert msg in fams.lib.fams_last_error()
+            assert fams.launch_count() == n_launch
+
+
+def test_static_reports_a_singular_coarse_system_like_the_solve():
+    """A node cell sealed to 1e-300 makes R^FV A P singular: fams_solve_static
+    returns FAMS_EBREAKDOWN (the binding hands back the status, as for the
+    batch solve) and fams_solve reports the same."""
+    from paper_1705_05784_gb300 import fams
+    p = inputs.config_2d_sealed_node(restriction=0, factor=1e-300)
+    with fams.Context(p) as c:
+        x, st = c.solve_static(tol=1e-8)
+        assert st["status"] == fams.EBREAKDOWN
+        with pytest.raises(fams.FamsError) as e:
+            c.solve(tol=1e-8)
+        assert e.value.status == fams.EBREAKDOWN
