@@ -287,7 +287,7 @@ def _oracle_one(i, keep=False):
         x, it, rr, ok, _ = osolver.gmres_solve(st, tol=TOL, max_iter=p.max_iter, restart=p.restart)
     else:
         x, it, rr, ok, _ = osolver.two_stage_solve(st, tol=TOL, max_iter=p.max_iter)
-    st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    st_fv = oracle.reconstruction_setup(p, g, sysm, c)
     flux, dflux, _, _ = osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
     sec = time.perf_counter() - t
     return (sec, x, flux) if keep else sec

@@ -90,8 +90,8 @@ typedef struct {
    d_min of the distance-based fracture coarsening (Table 2; <= 0 means
    infinity, one coarse node per network); frac_cz = vertical coarsening of 3D
    fracture plates; alpha = truncation threshold of P (Sec. 4.3, 0 = none;
-   a basis function none of whose entries outside its node cell reaches alpha
-   keeps all of them, so none is reduced to its node cell);
+   the iteration's P only: the flux reconstruction uses the basis functions
+   before truncation);
    max_iter bounds the Table 1 loop (or the GMRES iterations); precision =
    FAMS_FP64 or FAMS_MIXED.  krylov = FAMS_KRYLOV_GMRES runs the two-stage
    step as the right preconditioner of GMRES(restart), the paper's benchmark
@@ -223,7 +223,8 @@ int fams_solve_static(fams_ctx* ctx, const double* rhs, double* x, double tol, f
 /* fams_flux - conservative fine-scale flux field from an iterate x of
    instance `inst`: one finite-volume multiscale stage, then a local TPFA
    problem per primal block with the block-boundary fluxes as Neumann data
-   (Sec. 3.2; after any iteration, Sec. 1).  face_flux: n_faces values, x faces
+   (Sec. 3.2; after any iteration, Sec. 1); the finite-volume stage uses the
+   basis functions before truncation.  face_flux: n_faces values, x faces
    ((nx+1) ny nz, x fastest), then y faces, then z faces, positive along +axis
    (no-flow boundary faces are 0).  nnc_flux: n_nnc values, matrix-fracture
    connections (positive matrix -> fracture) in fams_query(FAMS_Q_NNC_*) order,
@@ -240,9 +241,10 @@ int fams_flux(fams_ctx* ctx, int inst, const double* x, double* face_flux, doubl
    pivot of its band LU is at most 1e-13 times the largest entry of its row as
    assembled (e.g. a node cell 1e-300 times as permeable as its neighbours:
    its basis function is 1e-300 outside the node cell, and its R^FV column is
-   that small).  Truncation never reduces a basis function to its own node
-   cell, which would make that column exactly zero.  Returns FAMS_EBREAKDOWN
-   if any instance failed that way. */
+   that small).  The reconstruction's R^FV A P is built with the basis
+   functions before truncation (a truncated basis function can lie inside
+   its own primal block, which makes its column of R^FV A P zero).  Returns
+   FAMS_EBREAKDOWN if any instance failed that way. */
 int fams_flux_batch(fams_ctx* ctx, const double* const* x, double* const* face_flux,
                     double* const* nnc_flux, int* status);
 

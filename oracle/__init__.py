@@ -46,10 +46,11 @@ class OracleResult:
     history: list
 
 
-def prolongation(prob, g, sysm, c, route="staged"):
-    """P (truncated) from the basis operator A0 of `sysm` (Sec. 3.1, App. A;
-    truncation Sec. 4.3).  Called with an updated system it rebuilds the basis
-    functions for new mobilities on the same coarse grids."""
+def prolongation(prob, g, sysm, c, route="staged", truncated=True):
+    """P (truncated unless `truncated` is False) from the basis operator A0 of
+    `sysm` (Sec. 3.1, App. A; truncation Sec. 4.3).  Called with an updated
+    system it rebuilds the basis functions for new mobilities on the same
+    coarse grids."""
     plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
     if route == "staged":
         P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate,
@@ -57,7 +58,18 @@ def prolongation(prob, g, sysm, c, route="staged"):
     else:
         P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
                                          plate, c.row_net)
-    return _basis.truncate(P, prob.alpha, c.node_cell)
+    return _basis.truncate(P, prob.alpha) if truncated else P
+
+
+def reconstruction_setup(prob, g, sysm, c):
+    """The finite-volume coarse system of the flux reconstruction (Sec. 3.2):
+    R^FV A P with the basis functions before truncation.  Reading: truncation
+    (Sec. 4.3) cuts the iteration's cost, and a truncated basis function can
+    lie inside its own primal block, where its column of R^FV A P vanishes and
+    the finite-volume stage has no solution; the reconstruction's single stage
+    therefore uses the untruncated basis functions."""
+    P = prolongation(prob, g, sysm, c, truncated=False)
+    return _solver.setup(sysm, P, c.primal, c.n_coarse, _solver.R_FV)
 
 
 def build(prob, route="staged"):

@@ -385,39 +385,19 @@ def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None, net=
     return P
 
 
-def truncate(P, alpha, node_cell=None):
+def truncate(P, alpha):
     """Sec. 4.3: drop entries with |P_ij| < alpha and divide each row by its new
     sum.  A row that would lose every entry keeps its largest one (lowest
-    column on ties).  alpha = 0 leaves P unchanged.
-
-    node_cell (the node cell of every coarse column), when given, adds the
-    rule that truncation never reduces a basis function to its own node cell:
-    a column j none of whose entries outside row node_cell[j] reaches alpha
-    keeps all of its entries.  Without it, a node cell much less permeable
-    than its neighbours has a basis function that is the unit vector of its
-    cell after truncation; that column of R^FV A P is A's column summed over
-    the node's own primal block, zero, and the finite-volume stage of the flux
-    reconstruction (Sec. 3.2) would have no solution."""
+    column on ties).  alpha = 0 leaves P unchanged."""
     P = sp.csr_matrix(P, copy=True)
     if alpha <= 0.0:
         return P
-    n, nc = P.shape
-    keep_all = np.zeros(nc, bool)
-    if node_cell is not None:
-        node_cell = np.asarray(node_cell, np.int64)
-        survives = np.zeros(nc, bool)
-        for r in range(n):
-            for p in range(P.indptr[r], P.indptr[r + 1]):
-                j = P.indices[p]
-                if r != node_cell[j] and abs(P.data[p]) >= alpha:
-                    survives[j] = True
-        keep_all = ~survives
     ri, ci, vv = [], [], []
-    for r in range(n):
+    for r in range(P.shape[0]):
         a, b = P.indptr[r], P.indptr[r + 1]
         cols = P.indices[a:b]
         vals = P.data[a:b]
-        keep = (np.abs(vals) >= alpha) | keep_all[cols]
+        keep = np.abs(vals) >= alpha
         if not keep.any() and b > a:
             keep = np.zeros(b - a, bool)
             keep[int(np.argmax(np.abs(vals)))] = True

@@ -459,23 +459,17 @@ __global__ void k_comp_solve(CompArgs a, long long slice, double* gwork) {
   comp_solve<G>(a, a.comp_list[idx], M, red);
 }
 
-// truncation (Sec. 4.3) and CSR of P.  keep_all[c] (instance-local column c)
-// marks a basis function none of whose entries outside its node cell reaches
-// alpha: truncation keeps all of its entries, so no basis function is reduced
-// to its own node cell (a zero column of R^FV A P otherwise).
-__device__ inline bool trunc_keep(double v, int c, double alpha, const int* keep_all) {
-  return alpha <= 0.0 || fabs(v) >= alpha || keep_all[c];
-}
-
-__device__ inline void trunc_row(const int* pc, const double* pv, int len, double alpha,
-                                 const int* keep_all, int* cnt, double* sum, int* only) {
+// truncation (Sec. 4.3) and CSR of P.  full = true: the basis functions
+// before truncation (the flux reconstruction's P).
+__device__ inline void trunc_row(const double* pv, int len, double alpha, int* cnt, double* sum,
+                                 int* only) {
   int c = 0, amax = -1;
   double s = 0.0, vmax = -1.0;
   for (int q = 0; q < len; ++q) {
     double v = pv[q];
     if (v == 0.0) continue;
     if (fabs(v) > vmax) { vmax = fabs(v); amax = q; }
-    if (trunc_keep(v, pc[q], alpha, keep_all)) { ++c; s += v; }
+    if (alpha <= 0.0 || fabs(v) >= alpha) { ++c; s += v; }
   }
   *only = -1;
   if (c == 0 && amax >= 0) { c = 1; s = pv[amax]; *only = amax; }
@@ -483,67 +477,43 @@ __device__ inline void trunc_row(const int* pc, const double* pv, int len, doubl
   *sum = s;
 }
 
-// survives[nc_off + c] = 1 when column c has an entry of magnitude >= alpha
-// outside its node cell's row (vertex rows are the pool's last stage)
-__global__ void k_p_survive(const Inst* inst, int B, const int* off_row, long long nrow,
-                            const int* pstage, const int* poff, const int* plen, Pool pool,
-                            int* survives) {
-  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrow) return;
-  int st = pstage[r];
-  if (st == NSTAGE) return;
-  const Inst& I = inst_of(inst, B, off_row, (int)r);
-  if (I.alpha <= 0.0) return;
-  const int* pc = pool.col[st] + poff[r];
-  const double* pv = pool.val[st] + poff[r];
-  for (int q = 0; q < plen[r]; ++q)
-    if (fabs(pv[q]) >= I.alpha) survives[I.nc_off + pc[q]] = 1;
-}
-
-// keep_all = 1 - survives, in place
-__global__ void k_p_keep_all(long long nct, int* flag) {
-  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nct) flag[j] = flag[j] ? 0 : 1;
-}
-
 __global__ void k_p_count(const Inst* inst, int B, const int* off_row, long long nrow,
                           const int* pstage, const int* poff, const int* plen, Pool pool,
-                          const int* keep_all, int* cnt) {
+                          bool full, int* cnt) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
   int st = pstage[r];
   int c = 0, only;
   double s;
-  trunc_row(pool.col[st] + poff[r], pool.val[st] + poff[r], plen[r], I.alpha, keep_all + I.nc_off,
-            &c, &s, &only);
+  trunc_row(pool.val[st] + poff[r], plen[r], full ? 0.0 : I.alpha, &c, &s, &only);
   cnt[r] = c;
 }
 
 __global__ void k_p_fill(const Inst* inst, int B, const int* off_row, long long nrow,
                          const int* pstage, const int* poff, const int* plen, Pool pool,
-                         const int* keep_all, const int* p_ptr, int* p_col, double* p_val) {
+                         bool full, const int* p_ptr, int* p_col, double* p_val) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst_of(inst, B, off_row, (int)r);
+  const double alpha = full ? 0.0 : I.alpha;
   int st = pstage[r];
   const int* pc = pool.col[st] + poff[r];
   const double* pv = pool.val[st] + poff[r];
-  const int* ka = keep_all + I.nc_off;
   int c, only;
   double s;
-  trunc_row(pc, pv, plen[r], I.alpha, ka, &c, &s, &only);
+  trunc_row(pv, plen[r], alpha, &c, &s, &only);
   int o = p_ptr[r];
   if (only >= 0) {
     p_col[o] = pc[only];
     p_val[o] = 1.0;
     return;
   }
-  bool scale = I.alpha > 0.0;
+  bool scale = alpha > 0.0;
   for (int q = 0; q < plen[r]; ++q) {
     double v = pv[q];
     if (v == 0.0) continue;
-    if (trunc_keep(v, pc[q], I.alpha, ka)) {
+    if (alpha <= 0.0 || fabs(v) >= alpha) {
       p_col[o] = pc[q];
       p_val[o] = scale ? v / s : v;
       ++o;
@@ -750,21 +720,36 @@ int phase_basis(Batch& b) {
       return FAMS_EINVAL;
     }
   }
-  int* keep_all = nullptr;
-  FAMS_TRY(b.scratch((void**)&keep_all, sizeof(int) * (nct + 1)));
-  FAMS_CUDA(cudaMemsetAsync(keep_all, 0, sizeof(int) * (nct + 1), st));
-  fams::note_launch(), k_p_survive<<<grid_for(nrow, T), T, 0, st>>>(
-      b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen, pool, keep_all);
-  if (nct > 0) fams::note_launch(), k_p_keep_all<<<grid_for(nct, T), T, 0, st>>>(nct, keep_all);
   fams::note_launch(), k_p_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
-                                             pool, keep_all, cnt);
+                                             pool, false, cnt);
   long long pnnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.p_ptr, nrow, &pnnz));
   b.tot_pnnz = pnnz;
   FAMS_TRY(b.alloc((void**)&b.p_col, sizeof(int) * (pnnz + 1)));
   FAMS_TRY(b.alloc((void**)&b.p_val, sizeof(double) * (pnnz + 1)));
   fams::note_launch(), k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen,
-                                            pool, keep_all, b.p_ptr, b.p_col, b.p_val);
+                                            pool, false, b.p_ptr, b.p_col, b.p_val);
+  // the flux reconstruction's P: the basis functions before truncation (the
+  // same array when no instance truncates)
+  bool any_trunc = false;
+  for (auto& I : b.h) any_trunc = any_trunc || I.alpha > 0.0;
+  if (any_trunc) {
+    FAMS_TRY(b.alloc((void**)&b.pf_ptr, sizeof(int) * (nrow + 1)));
+    fams::note_launch(), k_p_count<<<grid_for(nrow, T), T, 0, st>>>(
+        b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen, pool, true, cnt);
+    long long fnnz = 0;
+    FAMS_TRY(exclusive_scan(b, cnt, b.pf_ptr, nrow, &fnnz));
+    FAMS_TRY(b.alloc((void**)&b.pf_col, sizeof(int) * (fnnz + 1)));
+    FAMS_TRY(b.alloc((void**)&b.pf_val, sizeof(double) * (fnnz + 1)));
+    fams::note_launch(), k_p_fill<<<grid_for(nrow, T), T, 0, st>>>(
+        b.d_inst, b.B, b.off_row, nrow, pstage, poff, plen, pool, true, b.pf_ptr, b.pf_col,
+        b.pf_val);
+  } else {
+    b.pf_ptr = b.p_ptr;
+    b.pf_col = b.p_col;
+    b.pf_val = b.p_val;
+  }
+  b.pf_alias = !any_trunc;
   // P^T with global coarse rows (restriction R^FE and the coarse operator)
   int* gcol = nullptr;
   FAMS_TRY(b.scratch((void**)&gcol, sizeof(int) * (pnnz + 1)));

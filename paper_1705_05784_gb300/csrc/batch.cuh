@@ -134,6 +134,13 @@ struct Batch {
   int* pt_ptr = nullptr;       // CSR of P^T (rows = global coarse index)
   int* pt_col = nullptr;       // global fine rows
   double* pt_val = nullptr;
+  // the flux reconstruction's P: the basis functions before truncation (its
+  // finite-volume stage, Sec. 3.2); the same arrays as P when no instance
+  // truncates (pf_alias)
+  int* pf_ptr = nullptr;
+  int* pf_col = nullptr;
+  double* pf_val = nullptr;
+  bool pf_alias = true;
   int* blk_ptr = nullptr;      // cells of each primal block (global coarse index)
   int* blk_cell = nullptr;
   std::vector<int> h_blk_ptr;  // host copy of blk_ptr (taken on the first reconstruction)
@@ -260,7 +267,9 @@ int phase_system(Batch& b);       // system.cu: CSR of A, q_D
 int phase_coarse(Batch& b);       // coarse.cu: matrix blocks, networks, BFS, ranks
 int phase_basis(Batch& b);        // basis.cu: P
 int phase_coarse_op(Batch& b, int restriction);  // coarseop.cu: R A P, band LU
-int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse);
+// R A P with the prolongation (p_ptr, p_col, p_val): P, or the reconstruction's
+int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse,
+                        const int* p_ptr, const int* p_col, const double* p_val);
 int phase_update(Batch& b, const double* const* scale);
 int phase_update_basis(Batch& b, const double* const* scale, double eps, int* rebuilt);
 int ilu_refactor(Batch& b);                               // ilu.cu

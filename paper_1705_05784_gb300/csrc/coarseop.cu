@@ -537,7 +537,8 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
 // reuse: the system was built before and the fine operator kept its pattern
 // (a time-step update): A_c is summed again and refactored with the same
 // ordering, bandwidths and band layout
-int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse) {
+int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse,
+                        const int* p_ptr, const int* p_col, const double* p_val) {
   const int T = 256;
   cudaStream_t st = b.stream;
   long long nct = b.tot_nc;
@@ -568,8 +569,8 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   FAMS_CUDA(cudaMemsetAsync(cs.Ac, 0, sizeof(double) * (tot + 1), st));
   if (b.tot_nnz > 0)
     fams::note_launch(), k_rap<<<grid_for(b.tot_nnz, T), T, 0, st>>>(b.d_inst, B, b.off_row, b.tot_nnz, b.rowptr, b.col,
-                                                b.val, b.tot_row, b.primal, b.p_ptr, b.p_col,
-                                                b.p_val, cs, mode);
+                                                b.val, b.tot_row, b.primal, p_ptr, p_col,
+                                                p_val, cs, mode);
   int* ip = nullptr;
   FAMS_TRY(b.scratch((void**)&ip, sizeof(int) * (nct + 1)));
   if (!reuse) {
@@ -793,7 +794,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
 }
 
 int phase_coarse_op(Batch& b, int mode) {
-  return build_coarse_system(b, b.cs[0], mode, b.csh[0], false);
+  return build_coarse_system(b, b.cs[0], mode, b.csh[0], false, b.p_ptr, b.p_col, b.p_val);
 }
 
 }  // namespace fams

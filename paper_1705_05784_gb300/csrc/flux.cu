@@ -1,6 +1,9 @@
 // Conservative fine-scale flux reconstruction after any iterate (Sec. 1 and
 // Sec. 3.2: possible after an MSFV stage).
-//   1. p' = x + P (R^FV A P)^-1 R^FV (q - A x)          (one FV stage)
+//   1. p' = x + P (R^FV A P)^-1 R^FV (q - A x)          (one FV stage; P here
+//      holds the basis functions before truncation: a truncated basis
+//      function can lie inside its own primal block, where its column of
+//      R^FV A P vanishes)
 //   2. every connection between two primal blocks carries T (p'_i - p'_j);
 //   3. each primal block solves its own TPFA problem with those fluxes as
 //      Neumann data (Dirichlet faces stay Dirichlet; a block without one is
@@ -327,11 +330,13 @@ int local_bands(Batch& b) {
   return FAMS_OK;
 }
 
-// The R^FV coarse system of the reconstruction: the iteration's own when every
-// instance iterates with R^FV, otherwise a second one built on first use.
+// The R^FV coarse system of the reconstruction, R^FV A P with the basis
+// functions before truncation: the iteration's own when every instance
+// iterates with R^FV and none truncates, otherwise a second one built on
+// first use.
 int flux_prepare(Batch& b, const CoarseHost** ch) {
   FAMS_TRY(local_bands(b));
-  bool all_fv = true;
+  bool all_fv = b.pf_alias;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
   if (all_fv) {
     *ch = &b.csh[0];
@@ -339,7 +344,8 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
   }
   if (!b.fv_ready) {
     // built once; a time-step update (fv_built, !fv_ready) refactors it in place
-    FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1], b.fv_built));
+    FAMS_TRY(build_coarse_system(b, b.cs[1], 0, b.csh[1], b.fv_built, b.pf_ptr, b.pf_col,
+                                 b.pf_val));
     b.fv_ready = true;
     b.fv_built = true;
     b.free_tmp();
@@ -356,7 +362,7 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
 // system stays unbuilt and the reconstruction builds it (and reports the
 // error) on its first call.
 int flux_beside(Batch& b, cudaEvent_t ready) {
-  bool all_fv = true;
+  bool all_fv = b.pf_alias;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
   if ((all_fv || b.fv_ready) && !b.h_blk_ptr.empty()) return FAMS_OK;
   if (!b.side) {
@@ -406,8 +412,8 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_TRY(b.scratch((void**)&dlist, sizeof(int) * nl));
   FAMS_CUDA(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
   fams::note_launch(), k_flux_stage<<<nl, 512, smem, st>>>(
-      b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.p_ptr, b.p_col,
-      b.p_val, b.q, x, res, pp);
+      b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.pf_ptr, b.pf_col,
+      b.pf_val, b.q, x, res, pp);
   FAMS_CUDA(cudaGetLastError());
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread

@@ -219,7 +219,7 @@ int phase_update(Batch& b, const double* const* scale) {
         b.ff_T);
   FAMS_CUDA(cudaGetLastError());
   // P stays; R A P, its factors, ILU(0) and the FP32 copies follow A
-  FAMS_TRY(build_coarse_system(b, b.cs[0], -1, b.csh[0], true));
+  FAMS_TRY(build_coarse_system(b, b.cs[0], -1, b.csh[0], true, b.p_ptr, b.p_col, b.p_val));
   b.fv_ready = false;
   FAMS_TRY(ilu_refactor(b));
   FAMS_TRY(refresh_mixed(b));
@@ -280,6 +280,10 @@ int phase_update_basis(Batch& b, const double* const* scale, double eps, int* re
     b.free_tmp();
     return FAMS_OK;
   }
+  if (!b.pf_alias) {
+    b.release(b.pf_ptr); b.release(b.pf_col); b.release(b.pf_val);
+  }
+  b.pf_ptr = nullptr; b.pf_col = nullptr; b.pf_val = nullptr;
   b.release(b.p_ptr); b.release(b.p_col); b.release(b.p_val);
   b.release(b.pt_ptr); b.release(b.pt_col); b.release(b.pt_val);
   FAMS_TRY(phase_basis(b));

@@ -427,7 +427,7 @@ def test_flux_conservative_and_matches_oracle(built, name, restriction):
     x = xs[0]
     face, nnc = ctx.flux(x)
     # oracle reconstruction from the same iterate
-    st_fv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    st_fv = oracle.reconstruction_setup(p, g, sysm, c)
     flux, dflux, pp, pt = osolver.reconstruct_flux(sysm, p, st_fv, x, c.primal, c.node_cell)
     gpu_conn = _interior_connections(p, face, nnc)
     scale = np.abs(flux).max()
@@ -515,33 +515,40 @@ def test_flux_prepared_beside_the_solve():
             np.testing.assert_allclose(na, nb, rtol=0, atol=1e-9 * sc)
 
 
-def test_flux_of_a_sealed_node_instance_is_conservative():
-    """A node cell 1e-10 times less permeable than its neighbours: truncation
-    keeps its whole basis function (none of its off-node entries reaches
-    alpha), so R^FV A P is regular; the batch reconstruction of that
-    instance and of a regular one succeeds, matches the oracle's
+def test_flux_of_instances_with_a_singular_truncated_fv_system():
+    """Instances whose R^FV A P with the truncated P is singular (a sealed
+    node cell whose truncated basis function is its own cell; a 64 x 64
+    instance with a numerically singular pivot) next to a regular one: the
+    reconstruction's finite-volume stage uses the basis functions before
+    truncation, so every instance is reconstructed, matches the oracle's
     reconstruction from the same iterate and conserves mass in every cell."""
     fams = _fams()
     sealed = inputs.config_2d_sealed_node(restriction=0)
     plain = inputs.config_2d_small(restriction=0)
     plain.alpha = 1e-2
+    # truncation makes this instance's R^FV A P numerically singular
+    bound = inputs.config_2d(64, 2.0, 8.0, 4, (10, 30), 1e4, 8, 8, seed=86, basis=2,
+                             restriction=1, alpha=1e-2)
     probs = []
-    for q in (sealed, plain):
+    for q in (sealed, plain, bound):
         q = _gmres(copy.copy(q), 30, 200)
         q.restriction = 1
         probs.append(q)
     with fams.Context(probs) as c:
         xs, st = c.solve(tol=1e-8)
         assert all(s["converged"] for s in st)
-        S = [c.sizes(i) for i in range(2)]
+        S = [c.sizes(i) for i in range(3)]
         F = [np.full(s["n_faces"], 7.0) for s in S]
         N = [np.full(max(1, s["n_nnc"]), 7.0) for s in S]
         status = c.flux_batch_ptr([x.ctypes.data for x in xs], [f.ctypes.data for f in F],
                                   [m.ctypes.data for m in N])
-        assert status == [0, 0]
+        assert status == [0, 0, 0]
         for i, q in enumerate(probs):
             g, sysm, co, P, _ = oracle.build(q)
-            st_fv = osolver.setup(sysm, P, co.primal, co.n_coarse, osolver.R_FV)
+            trunc = osolver.coarse_operator(
+                osolver.restriction(P, co.primal, co.n_coarse, osolver.R_FV), sysm.A, P)
+            assert (osolver.singular_step(trunc) >= 0) == (i != 1)
+            st_fv = oracle.reconstruction_setup(q, g, sysm, co)
             assert osolver.singular_step(st_fv.Ac) == -1
             flux, dflux, pp, pt = osolver.reconstruct_flux(sysm, q, st_fv, xs[i], co.primal,
                                                            co.node_cell)
@@ -615,7 +622,7 @@ def test_degenerate_inputs_match_the_oracle(args):
         assert abs(stats[0]["iterations"] - ito) <= 1
         assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-8
         face, nnc = ctx.flux(xs[0])
-    sfv = osolver.setup(sysm, P, c.primal, c.n_coarse, osolver.R_FV)
+    sfv = oracle.reconstruction_setup(p, g, sysm, c)
     flux, dflux, _, _ = osolver.reconstruct_flux(sysm, p, sfv, xs[0], c.primal, c.node_cell)
     nz = p.nz if p.dim == 3 else 1
     nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
@@ -660,6 +667,7 @@ def test_time_step_update_matches_oracle(name, restriction):
     fams = _fams()
     p = _gmres(_case(name, 0, restriction), 8, 13)
     g, sysm, c, P, st0 = oracle.build(p)
+    Pf = oracle.prolongation(p, g, sysm, c, truncated=False)   # the reconstruction's P
     n = sysm.n
     with fams.Context(p) as ctx:
         for seed in (3, 4):
@@ -678,7 +686,7 @@ def test_time_step_update_matches_oracle(name, restriction):
             assert stats[0]["iterations"] == 13 == ito
             assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
             face, nnc = ctx.flux(xs[0])
-            sfv = osolver.setup(ur, P, c.primal, c.n_coarse, osolver.R_FV)
+            sfv = osolver.setup(ur, Pf, c.primal, c.n_coarse, osolver.R_FV)
             flux, dflux, _, _ = osolver.reconstruct_flux(ur, p, sfv, xs[0], c.primal, c.node_cell)
             nz = p.nz if p.dim == 3 else 1
             nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
@@ -726,7 +734,7 @@ def test_basis_rebuild_matches_oracle(name, restriction):
         assert stats[0]["iterations"] == 13 == ito
         assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
         face, nnc = ctx.flux(xs[0])
-        sfv = osolver.setup(ur, Pu, c.primal, c.n_coarse, osolver.R_FV)
+        sfv = oracle.reconstruction_setup(p, g, ur, c)
         flux, dflux, _, _ = osolver.reconstruct_flux(ur, p, sfv, xs[0], c.primal, c.node_cell)
         nz = p.nz if p.dim == 3 else 1
         nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
@@ -781,7 +789,7 @@ def test_bench_workload_instances_match_the_oracle():
                                                    restart=p.restart)
             assert oko
             assert np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo) < 1e-6
-            sfv = osolver.setup(sysm, P, co.primal, co.n_coarse, osolver.R_FV)
+            sfv = oracle.reconstruction_setup(p, g, sysm, co)
             fo, _, _, _ = osolver.reconstruct_flux(sysm, p, sfv, xo, co.primal, co.node_cell)
             face, nnc = c.flux(xs[i], i)
             assert np.abs(bench.conn_fluxes(p, face, nnc) - fo).max() < 1e-6 * np.abs(fo).max()

@@ -288,31 +288,6 @@ def test_truncation_example():
     np.testing.assert_allclose(R, [[0.0, 0.0, 1.0]])
 
 
-def test_truncation_never_reduces_a_basis_function_to_its_node_cell():
-    """Columns 0..2 have node cells 0..2.  Every entry of column 2 outside its
-    node row is below alpha, so column 2 keeps all of them (rows rescaled as
-    usual); columns 0 and 1 are truncated as before.  Worked by hand."""
-    P = sp.csr_matrix(np.array([[1.0, 0.0, 0.0],
-                                [0.0, 1.0, 0.0],
-                                [0.0, 0.0, 1.0],
-                                [0.6, 0.39, 0.005],
-                                [0.004, 0.988, 0.008]]))
-    Q = basis.truncate(P, 1e-2, node_cell=[0, 1, 2]).toarray()
-    np.testing.assert_allclose(Q[:3], np.eye(3), rtol=0, atol=0)
-    np.testing.assert_allclose(Q[3], [0.6 / 0.995, 0.39 / 0.995, 0.005 / 0.995], rtol=1e-15)
-    np.testing.assert_allclose(Q[4], [0.0, 0.988 / 0.996, 0.008 / 0.996], rtol=1e-15)
-    # without the node cells column 2 would vanish outside its node row
-    Q0 = basis.truncate(P, 1e-2).toarray()
-    np.testing.assert_allclose(Q0[3], [0.6 / 0.99, 0.39 / 0.99, 0.0], rtol=1e-15)
-    np.testing.assert_allclose(Q0[4], [0.0, 1.0, 0.0], rtol=1e-15)
-    # one off-node entry at alpha is enough for the column to be truncated
-    P2 = P.toarray()
-    P2[4] = [0.0, 0.99, 0.01]
-    Q2 = basis.truncate(sp.csr_matrix(P2), 1e-2, node_cell=[0, 1, 2]).toarray()
-    np.testing.assert_allclose(Q2[3], [0.6 / 0.99, 0.39 / 0.99, 0.0], rtol=1e-15)
-    np.testing.assert_allclose(Q2[4], [0.0, 0.99, 0.01], rtol=1e-15)
-
-
 def _plate_cases():
     cases, cur = [], None
     for line in open(os.path.join(GOLDEN, "coarse3d_plates.txt")):

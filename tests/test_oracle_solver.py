@@ -1,5 +1,7 @@
 """Pins of the oracle's coarse system, ILU(0), Table 1 iteration and flux
 reconstruction (Sec. 3.2)."""
+import copy
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -114,7 +116,7 @@ def test_flux_reconstruction_is_conservative(variant):
     p.tol = 1e-3          # stop early: the reconstruction works after any iteration
     r = oracle.run(p)
     g, sysm, c, P, st = oracle.build(p)
-    st_fv = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FV)
+    st_fv = oracle.reconstruction_setup(p, g, sysm, c)
     flux, dflux, pp, pt = solver.reconstruct_flux(sysm, p, st_fv, r.p, c.primal, c.node_cell)
     bal = solver.cell_balance(sysm, p, flux, dflux)
     scale = np.abs(flux).max()
@@ -271,51 +273,89 @@ def test_singular_step_pins():
     assert solver.singular_step(np.zeros((0, 0))) == -1
 
 
-def test_sealed_node_keeps_its_basis_function_and_a_conservative_field():
-    """A node cell 1e-10 times less permeable than its neighbours: every entry
-    of its basis function outside the node cell is below alpha, so truncation
-    keeps the whole column (it is not reduced to the node cell).  R^FV A P is
-    then regular and the reconstruction conserves mass in every cell to
-    round-off (every flux is T (p_i - p_j): 64 eps T_max |p|_max, 1.4e-10 with
-    the fracture's T of 1e4, 3e-16 relative); with the node reduced to its
-    cell (truncation without the node cells) the column of R^FV A P vanishes
-    and the system is singular."""
+def _block_bound_basis():
+    """A 64 x 64 instance (sigma 2, Rock-AMS, alpha 1e-2) in which a truncated
+    basis function lies inside its own primal block."""
+    return inputs.config_2d(64, 2.0, 8.0, 4, (10, 30), 1e4, 8, 8, seed=86, basis=2,
+                            restriction=1, alpha=1e-2)
+
+
+def test_truncated_fv_system_singular_and_the_reconstruction():
+    """Truncation can make R^FV A P singular: a basis function whose
+    truncated support stays inside its own primal block, off the block's
+    boundary, sends no flux out of any block (a zero column; 13 of the 304
+    instances of the 256 x 256 workload), and here a numerically singular
+    pivot appears.  The reconstruction's finite-volume stage uses the basis
+    functions before truncation: regular, and the reconstructed field
+    conserves mass in every cell to round-off (64 eps T_max |p|_max)."""
+    p = _block_bound_basis()
+    g, sysm, c, P, st = oracle.build(p)
+    Afv = solver.coarse_operator(solver.restriction(P, c.primal, c.n_coarse, solver.R_FV),
+                                 sysm.A, P)
+    assert solver.singular_step(Afv) >= 0
+    rs = oracle.reconstruction_setup(p, g, sysm, c)
+    assert rs.P.nnz > P.nnz
+    assert solver.singular_step(rs.Ac) == -1
+    x = oracle.run(p).p
+    flux, dflux, _, _ = solver.reconstruct_flux(sysm, p, rs, x, c.primal, c.node_cell)
+    bal = solver.cell_balance(sysm, p, flux, dflux)
+    _, _, cT = solver.connections(sysm, p)
+    assert np.abs(bal).max() < 64 * np.finfo(float).eps * cT.max() * max(np.abs(x).max(), 1.0)
+
+
+def test_a_basis_function_inside_its_block_gives_a_zero_fv_column():
+    """The structural case by hand: on a homogeneous 24 x 24 grid with 8 x 8
+    coarsening, replace column j of P by the unit vector of its node cell
+    (a support inside the block, off its boundary): the column of R^FV A P
+    is zero (A0 has zero row sums, so A's column summed over the block is
+    the flux out of the block, zero); with the untruncated column it is not."""
+    p = inputs.config_2d(24, 0.0, 4.0, 0, (1, 2), 1.0, 8, 8, seed=1, restriction=0)
+    p.coarsen = (8, 8, 1)
+    g, sysm, c, P, st = oracle.build(p)
+    nodes = c.node_cell
+    # the node cell of an interior-ish block: one not on the domain boundary
+    nx = p.nx
+    j = next(k for k, v in enumerate(nodes) if 0 < v % nx < nx - 1 and 0 < v // nx < p.ny - 1)
+    Q = P.tolil()
+    Q[:, j] = 0.0
+    Q[nodes[j], j] = 1.0
+    Q = sp.csr_matrix(Q)
+    R = solver.restriction(Q, c.primal, c.n_coarse, solver.R_FV)
+    A0c = solver.coarse_operator(R, sysm.A0, Q)
+    assert np.abs(A0c[:, j]).max() == 0.0
+    Ac = solver.coarse_operator(R, sysm.A0, P)
+    assert np.abs(Ac[:, j]).max() > 0.0
+
+
+def test_sealed_node_and_the_reconstruction():
+    """A node cell 1e-10 times less permeable than its neighbours: truncation
+    reduces its basis function to the node cell, whose R^FV column is then
+    zero.  Before truncation its basis function is about 1e-10 outside the
+    node cell: the reconstruction's system is regular and its field
+    conservative.  Sealed to 1e-300, even that system is singular by the
+    scaled pivot test."""
     p = inputs.config_2d_sealed_node(restriction=solver.R_FV)
     g, sysm, c, P, st = oracle.build(p)
     node = 22 + 32 * 6
     J = int(np.nonzero(c.node_cell == node)[0][0])
     col = P.tocsc()[:, J]
-    assert col.nnz > 1 and np.abs(col.data[col.indices != node]).max() < p.alpha
-    assert solver.singular_step(st.Ac) == -1
-    x = oracle.run(p).p
-    flux, dflux, _, _ = solver.reconstruct_flux(sysm, p, st, x, c.primal, c.node_cell)
+    assert col.nnz == 1 and col.indices[0] == node and col.data[0] == 1.0
+    assert np.abs(st.Ac[:, J]).max() <= 1e-14 * np.abs(st.Ac).max()
+    assert solver.singular_step(st.Ac) >= 0
+    sfe = solver.setup(sysm, P, c.primal, c.n_coarse, solver.R_FE)
+    assert solver.singular_step(sfe.Ac) == -1
+    rs = oracle.reconstruction_setup(p, g, sysm, c)
+    assert solver.singular_step(rs.Ac) == -1
+    q = copy.copy(p)
+    q.restriction = solver.R_FE
+    x = oracle.run(q).p
+    flux, dflux, _, _ = solver.reconstruct_flux(sysm, p, rs, x, c.primal, c.node_cell)
     bal = solver.cell_balance(sysm, p, flux, dflux)
     _, _, cT = solver.connections(sysm, p)
     assert np.abs(bal).max() < 64 * np.finfo(float).eps * cT.max() * max(np.abs(x).max(), 1.0)
-    # the column reduced to its node cell: R^FV column J sums A's column over
-    # the node's own primal block, zero
-    P_old = basis.truncate(basis.prolongation_staged(
-        sysm.A0, c.rank, c.medium, c.node_cell, p.basis,
-        np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])), p.alpha)
-    colo = P_old.tocsc()[:, J]
-    assert colo.nnz == 1 and colo.indices[0] == node and colo.data[0] == 1.0
-    Aold = solver.coarse_operator(solver.restriction(P_old, c.primal, c.n_coarse, solver.R_FV),
-                                  sysm.A, P_old)
-    assert np.abs(Aold[:, J]).max() <= 1e-14 * np.abs(Aold).max()
-    assert solver.singular_step(Aold) >= 0
-
-
-def test_a_node_sealed_to_underflow_still_makes_the_fv_system_singular():
-    """A node cell 1e-300 times as permeable: its basis function is 1e-300
-    outside the node cell, so R^FV A P is singular by the scaled pivot test
-    (and so is R^FE A P, whose diagonal entry of that node is 1e-300)."""
-    p = inputs.config_2d_sealed_node(restriction=solver.R_FV, factor=1e-300)
-    g, sysm, c, P, st = oracle.build(p)
-    assert solver.singular_step(st.Ac) >= 0
-    q = inputs.config_2d_small(restriction=solver.R_FV)
-    q.alpha = 1e-2
-    _, _, _, _, sq = oracle.build(q)
-    assert solver.singular_step(sq.Ac) == -1
+    s300 = inputs.config_2d_sealed_node(restriction=solver.R_FV, factor=1e-300)
+    g3, sys3, c3, _, _ = oracle.build(s300)
+    assert solver.singular_step(oracle.reconstruction_setup(s300, g3, sys3, c3).Ac) >= 0
 
 
 def test_basis_rebuilt_for_new_mobilities():

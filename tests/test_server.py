@@ -65,10 +65,10 @@ def test_a_rejected_problem_fails_alone():
     from paper_1705_05784_gb300 import fams
     good = _mix()[:3]
     bad = inputs.config_3d(20, 18, 12, 1.0, (5, 5, 2), 2, (6, 14), 1e3, (5, 6, 4), 5, 4, seed=8)
-    # two crossing plates with different layer ranges: one network cannot be
-    # extruded uniformly, which setup rejects
-    bad.fracs = np.array([[2.0, 9.0, 18.0, 9.0, 0.0, 12.0], [10.0, 1.0, 10.0, 17.0, 3.0, 9.0]])
-    bad.kf = np.array([1e3, 1e3])
+    # a negative permeability: the device's input check rejects the instance
+    # during setup, inside the micro-batch
+    bad.perm = bad.perm.copy()
+    bad.perm[37] = -1.0
     with fams.Server(max_batch=8, pipelines=1, hbm_budget=8 << 30) as srv:
         tg = [srv.submit(p) for p in good]
         tb = srv.submit(bad)
