@@ -284,9 +284,15 @@ enum {
   FAMS_Q_LAST_EC = 29,     /* double coarse solution (R A P)^-1 R r of the last sweep */
   FAMS_Q_STAGE_CYCLES = 30, /* double SM cycles of the last solve per phase: residual,
                                restriction, band solve, prolongation + r1, L sweep, U sweep */
-  FAMS_Q_SETUP_MS = 31     /* double wall ms of the setup phases of the whole context:
+  FAMS_Q_SETUP_MS = 31,    /* double wall ms of the setup phases of the whole context:
                               geometry, fine system, coarse grids, basis, coarse operator,
                               ILU(0) */
+  FAMS_Q_CLASS_COUNTS = 32 /* int32  local problems of the whole context solved per size
+                              class (one warp; a 128-thread CTA; a 256-thread CTA in shared
+                              memory; a 512-thread CTA on a global-memory workspace): the
+                              basis functions' dual blocks (4 values, all setups and
+                              rebuilds), then the flux reconstruction's primal blocks (4
+                              values, all calls) */
 };
 int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap);
 

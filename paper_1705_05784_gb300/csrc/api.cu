@@ -594,6 +594,7 @@ int fams_query(const fams_ctx* ctx, int inst, int what, void* out, long long cap
       break;
     case FAMS_Q_STAGE_CYCLES: FAMS_TRY(dbls(b.stat + STAT_W * inst + 4, 6)); break;
     case FAMS_Q_SETUP_MS: isint = false; vd.assign(b.setup_ms, b.setup_ms + 6); break;
+    case FAMS_Q_CLASS_COUNTS: vi.assign(b.class_cnt, b.class_cnt + 8); break;
     case FAMS_Q_LAST_DP1: FAMS_TRY(dbls(b.dp + I.row_off, I.n)); break;
     case FAMS_Q_LAST_DP2: FAMS_TRY(dbls(b.y + I.row_off, I.n)); break;
     case FAMS_Q_LAST_RC: FAMS_TRY(dbls(b.rc + I.nc_off, I.nc)); break;

@@ -636,6 +636,7 @@ int phase_basis(Batch& b) {
       long long need = (long long)hs[c] * ((long long)hbw[2 * c] + hbw[2 * c + 1] + 2 + hk[c]);
       int q = need <= WARP_NEED ? 0 : need <= MID_NEED ? 1 : need * 8 + 1024 <= max_smem ? 2 : 3;
       cls[q].push_back((int)c);
+      ++b.class_cnt[q];
       cmax[q] = std::max(cmax[q], need);
     }
     long long* pool_off = nullptr;

@@ -199,6 +199,10 @@ struct Batch {
   bool fv_ready = false;       // R^FV coarse system current
   bool fv_built = false;       // ... and allocated (a time-step update only refactors it)
   double setup_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per setup phase, wall time
+  // local problems solved per size class (one warp, 128-thread CTA, 256-thread
+  // CTA in shared memory, 512-thread CTA on a global workspace): dual blocks
+  // of the basis stages [0..3], primal blocks of the flux reconstruction [4..7]
+  int class_cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // flux reconstruction buffers (allocated on first use): iterates and outputs
   double* fx = nullptr;
   double* fface = nullptr;

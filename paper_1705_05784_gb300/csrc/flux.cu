@@ -431,6 +431,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
       int q = need <= LOCAL_WARP_NEED ? 0 : need <= LOCAL_MID_NEED ? 1
             : need * 8 <= max_smem ? 2 : 3;
       cls[q].push_back(c);
+      ++b.class_cnt[4 + q];
       cmax[q] = std::max(cmax[q], need);
     }
   }

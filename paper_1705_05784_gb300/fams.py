@@ -24,8 +24,9 @@ Q = dict(NNC_FRAC=1, NNC_MATRIX=2, NNC_AREA=3, NNC_DIST=4, FF_A=5, FF_B=6, FF_T=
          A_ROWPTR=8, A_COL=9, A_VAL=10, Q=11, RANK=12, PRIMAL=13, NODE_CELL=14,
          P_ROWPTR=15, P_COL=16, P_VAL=17, AC=18, ILU_VAL=19, LEVELS=20,
          COARSE_PERM=21, COARSE_IPIV=22, BAND_KLKU=23, BAND=24, HISTORY=25,
-         LAST_DP1=26, LAST_DP2=27, LAST_RC=28, LAST_EC=29, STAGE_CYCLES=30, SETUP_MS=31)
-_INT_QUERIES = {1, 2, 5, 6, 8, 9, 12, 13, 14, 15, 16, 20, 21, 22, 23}
+         LAST_DP1=26, LAST_DP2=27, LAST_RC=28, LAST_EC=29, STAGE_CYCLES=30, SETUP_MS=31,
+         CLASS_COUNTS=32)
+_INT_QUERIES = {1, 2, 5, 6, 8, 9, 12, 13, 14, 15, 16, 20, 21, 22, 23, 32}
 
 
 class fams_grid(C.Structure):

@@ -793,3 +793,108 @@ def test_bench_workload_instances_match_the_oracle():
             fo, _, _, _ = osolver.reconstruct_flux(sysm, p, sfv, xo, co.primal, co.node_cell)
             face, nnc = c.flux(xs[i], i)
             assert np.abs(bench.conn_fluxes(p, face, nnc) - fo).max() < 1e-6 * np.abs(fo).max()
+
+
+def _bench_oracle(i):
+    """Pool worker: the oracle on instance i of the 16-instance bench batch --
+    its GMRES(30) iteration count to 1e-8 and the iterate after exactly that
+    many iterations."""
+    import warnings
+    warnings.simplefilter("ignore")
+    import bench
+    p = bench.problems(16, bench.ORACLE_SEED)[i]
+    g, sysm, co, P, so = oracle.build(p)
+    xo, ito, rro, oko, _ = osolver.gmres_solve(so, tol=bench.TOL, max_iter=p.max_iter,
+                                               restart=p.restart)
+    return i, xo, ito, oko
+
+
+def _bench_oracle_flux(args):
+    """Pool worker: the oracle's reconstruction of bench instance i from an
+    iterate x."""
+    import warnings
+    warnings.simplefilter("ignore")
+    import bench
+    i, x = args
+    p = bench.problems(16, bench.ORACLE_SEED)[i]
+    g, sysm, co, P, so = oracle.build(p)
+    sfv = oracle.reconstruction_setup(p, g, sysm, co)
+    fo, _, _, _ = osolver.reconstruct_flux(sysm, p, sfv, x, co.primal, co.node_cell)
+    return i, fo
+
+
+def test_bench_workload_trajectories_at_full_size():
+    """Every kind of instance of the bench workload at full size (256x256,
+    the four coupling strategies x T_ratio 1e2, 1e4, 1e6, 1e8: a batch of
+    16 with the bench's options): each instance converges in the oracle's
+    iteration count, after exactly that many GMRES iterations its pressure
+    equals the oracle's to 1e-10 relative L2, and its conservative fluxes
+    from that iterate equal the oracle's reconstruction to 1e-8 of the
+    largest flux.  The oracle runs on the host cores in spawned processes."""
+    import multiprocessing as mp
+    import bench
+    fams = _fams()
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
+        ref = {i: (xo, ito, oko) for i, xo, ito, oko in pool.imap_unordered(_bench_oracle,
+                                                                          range(16))}
+        assert all(ref[i][2] for i in range(16))
+        probs = bench.problems(16, bench.ORACLE_SEED)
+        with fams.Context(probs) as c:
+            xs, st = c.solve(tol=bench.TOL)
+        its = [s["iterations"] for s in st]
+        assert all(s["converged"] for s in st)
+        assert its == [ref[i][1] for i in range(16)], (its, [ref[i][1] for i in range(16)])
+        # the same batch with each instance stopped after the oracle's count
+        for i, p in enumerate(probs):
+            p.max_iter = ref[i][1]
+        with fams.Context(probs) as c:
+            xk, stk = c.solve(tol=0.0)
+            assert [s["iterations"] for s in stk] == [ref[i][1] for i in range(16)]
+            errs = [np.linalg.norm(xk[i] - ref[i][0]) / np.linalg.norm(ref[i][0])
+                    for i in range(16)]
+            assert max(errs) < 1e-10, errs
+            fl = [c.flux(xk[i], i) for i in range(16)]
+        for i, fo in pool.imap_unordered(_bench_oracle_flux, [(i, xk[i]) for i in range(16)]):
+            got = bench.conn_fluxes(probs[i], *fl[i])
+            assert np.abs(got - fo).max() < 1e-8 * np.abs(fo).max(), i
+
+
+def _class_case(variant):
+    """3D, coarsening 8 x 8 x 8: interior dual blocks of 343 cells and primal
+    blocks of 512 cells exceed shared memory as banded systems, so both the
+    basis and the reconstruction take the global-workspace size class."""
+    p = inputs.config_3d(24, 24, 16, 1.0, (6, 6, 3), 0, (6, 14), 1e3, (8, 8, 8), 8, 8, seed=12,
+                         basis=variant, restriction=1)
+    p.fracs = np.array([[2.5, 9.3, 21.5, 14.1, 0.0, 16.0], [12.3, 1.5, 11.1, 22.5, 0.0, 16.0]])
+    p.kf = np.array([1e3, 1e4])
+    return p
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_global_workspace_size_class_matches_the_oracle(variant):
+    """The size class that solves local problems on a global-memory
+    workspace: the query shows it was taken for dual blocks and primal
+    blocks; P, a fixed-count GMRES trajectory and the fluxes equal the
+    oracle's."""
+    fams = _fams()
+    p = _gmres(_class_case(variant), 30, 12)
+    g, sysm, c, P, st = oracle.build(p)
+    with fams.Context(p) as ctx:
+        Pg = _gpu_P(ctx, P.shape)
+        np.testing.assert_array_equal(Pg.indptr, P.indptr)
+        np.testing.assert_array_equal(Pg.indices, P.indices)
+        np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
+        xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=12, restart=30)
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 12 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+        face, nnc = ctx.flux(xs[0])
+        cc = ctx.query("CLASS_COUNTS")
+        assert cc[3] > 0 and cc[7] > 0, cc
+    sfv = oracle.reconstruction_setup(p, g, sysm, c)
+    flux, _, _, pt = osolver.reconstruct_flux(sysm, p, sfv, xs[0], c.primal, c.node_cell)
+    conn = _interior_connections(p, face, nnc)
+    np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
+    _, _, cT = osolver.connections(sysm, p)
+    bound = 64 * np.finfo(float).eps * cT.max() * max(np.abs(pt).max(), 1.0)
+    assert np.abs(_balance(sysm, p, face, conn)).max() < bound
