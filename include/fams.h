@@ -116,6 +116,13 @@ typedef struct {
                         filling the SMs that early-converging instances leave
                         idle; 0: built on the first fams_flux* call.  Results are
                         the same either way. */
+  int merge_cap;     /* Coupled-AMS: largest dual block that same-rank links across the
+                        media may merge (Sec. 3.1: one can limit the merged blocks);
+                        0 = no limit.  The blocks of each medium are merged through the
+                        cross-medium links in the order of A's rows and columns, a link
+                        joining two blocks only while the merged block stays within the
+                        cap; a link left between two blocks is dropped and removed from
+                        the diagonal. */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */

@@ -52,12 +52,13 @@ def prolongation(prob, g, sysm, c, route="staged", truncated=True):
     system it rebuilds the basis functions for new mobilities on the same
     coarse grids."""
     plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
+    cap = getattr(prob, "merge_cap", 0)
     if route == "staged":
         P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate,
-                                       c.row_net)
+                                       c.row_net, cap)
     else:
         P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
-                                         plate, c.row_net)
+                                         plate, c.row_net, cap)
     return _basis.truncate(P, prob.alpha) if truncated else P
 
 

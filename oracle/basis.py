@@ -93,8 +93,61 @@ def _cross(plate, net, r, c):
     return 1
 
 
-def stage_blocks(A0, rank, medium, node_cell, variant, plate=None, net=None):
-    """The dual blocks of every stage (lists of rows), in solve order."""
+def merge_capped(n_cells, same_links, cross_links, cap):
+    """Dual blocks of a Coupled stage under a merge cap (Sec. 3.1: one can
+    limit the size of the blocks that same-rank links across the media
+    merge).  Reading: the blocks of each medium alone (connected components
+    of `same_links`) are merged through the cross-medium links taken in the
+    given order (the CSR order of A: lower row first, then column), a link
+    joining two blocks only when the merged block holds at most `cap` cells.
+    Returns a block label per cell (the lowest cell of its block)."""
+    parent = list(range(n_cells))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for a, b in same_links:
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    size = [0] * n_cells
+    for x in range(n_cells):
+        size[find(x)] += 1
+    for a, b in cross_links:
+        ra, rb = find(a), find(b)
+        if ra != rb and size[ra] + size[rb] <= cap:
+            lo, hi = min(ra, rb), max(ra, rb)
+            parent[hi] = lo
+            size[lo] += size[hi]
+    return [find(x) for x in range(n_cells)]
+
+
+def _stage_labels(A0, S, in_stage, medium, keep, variant, merge_cap):
+    """Block label (position in S of the block's lowest cell) of every cell of
+    a stage S: connected components of the kept links inside the stage; for
+    Coupled with merge_cap > 0, cross-medium links merge blocks only within
+    the cap (merge_capped)."""
+    ip, ix = A0.indptr, A0.indices
+    loc = -np.ones(A0.shape[0], np.int64)
+    loc[S] = np.arange(S.size)
+    same, cross = [], []
+    for r in S:
+        for p in range(ip[r], ip[r + 1]):
+            c = ix[p]
+            if c > r and in_stage[c] and keep(r, c):
+                (cross if (variant == COUPLED and merge_cap > 0 and medium[r] != medium[c])
+                 else same).append((int(loc[r]), int(loc[c])))
+    cap = merge_cap if merge_cap > 0 else S.size
+    return np.asarray(merge_capped(S.size, same, cross, cap), np.int64)
+
+
+def stage_blocks(A0, rank, medium, node_cell, variant, plate=None, net=None, merge_cap=0,
+                 with_stage=False):
+    """The dual blocks of every stage (lists of rows), in solve order
+    (with_stage: (stage index, rows) pairs)."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
@@ -102,7 +155,7 @@ def stage_blocks(A0, rank, medium, node_cell, variant, plate=None, net=None):
     known[np.asarray(node_cell)] = True
     ip, ix = A0.indptr, A0.indices
     out = []
-    for stage in stage_list(variant):
+    for si, stage in enumerate(stage_list(variant)):
         in_stage = np.zeros(n, bool)
         for (med, rk) in stage:
             in_stage |= (medium == med) & (rank == rk)
@@ -110,30 +163,51 @@ def stage_blocks(A0, rank, medium, node_cell, variant, plate=None, net=None):
         S = np.nonzero(in_stage)[0]
         if S.size == 0:
             continue
-        loc = -np.ones(n, np.int64)
-        loc[S] = np.arange(S.size)
-        er, ec = [], []
-        for r in S:
-            for p in range(ip[r], ip[r + 1]):
-                c = ix[p]
-                if c != r and in_stage[c] and keep_link(variant, medium[r], rank[r], medium[c],
-                                                        rank[c], _cross(plate, net, r, c)):
-                    er.append(loc[r])
-                    ec.append(loc[c])
-        G = sp.csr_matrix((np.ones(len(er)), (er, ec)), shape=(S.size, S.size))
-        ncomp, lab = csg.connected_components(G, directed=False)
-        members = [[] for _ in range(ncomp)]
+
+        def keep(r, c):
+            return keep_link(variant, medium[r], rank[r], medium[c], rank[c],
+                             _cross(plate, net, r, c))
+        lab = _stage_labels(A0, S, in_stage, medium, keep, variant, merge_cap)
+        members = {}
         for li, r in enumerate(S):
-            members[lab[li]].append(int(r))
-        out.extend(members)
+            members.setdefault(int(lab[li]), []).append(int(r))
+        for k in sorted(members):
+            out.append((si, members[k]) if with_stage else members[k])
         known |= in_stage
     return out
 
 
-def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=None):
+def cut_links(A0, rank, medium, node_cell, variant, plate=None, net=None, merge_cap=0):
+    """Links that the keep rule keeps but the merge cap cuts: same-stage
+    cross-medium links between two different blocks (Coupled only)."""
+    A0 = sp.csr_matrix(A0)
+    blocks = stage_blocks(A0, rank, medium, node_cell, variant, plate, net, merge_cap, True)
+    blk = -np.ones(A0.shape[0], np.int64)
+    stg = -np.ones(A0.shape[0], np.int64)
+    for b, (si, cells) in enumerate(blocks):
+        blk[cells] = b
+        stg[cells] = si
+    out = []
+    ip, ix = A0.indptr, A0.indices
+    for r in range(A0.shape[0]):
+        if blk[r] < 0:
+            continue
+        for p in range(ip[r], ip[r + 1]):
+            c = ix[p]
+            if c != r and stg[c] == stg[r] and blk[c] != blk[r] and keep_link(
+                    variant, medium[r], rank[r], medium[c], rank[c], _cross(plate, net, r, c)):
+                out.append((r, c))
+    return out
+
+
+def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=None,
+                        merge_cap=0):
     """P (CSR, n x n_coarse) by the staged wirebasket rule.  plate[r]: input
     fracture of fracture row r (-1 for matrix rows; None: no crossings);
-    net[r]: coarsening network of fracture row r (None: a single network)."""
+    net[r]: coarsening network of fracture row r (None: a single network);
+    merge_cap: largest Coupled block merged across the media (0: no cap); a
+    kept link between two blocks of one stage (cut by the cap) is dropped
+    and removed from the diagonal."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
@@ -156,22 +230,13 @@ def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=No
         S = np.nonzero(in_stage)[0]
         if S.size == 0:
             continue
-        loc = -np.ones(n, np.int64)
-        loc[S] = np.arange(S.size)
         # links kept inside the stage define the dual blocks
-        er, ec = [], []
-        for r in S:
-            for p in range(ip[r], ip[r + 1]):
-                c = ix[p]
-                if c != r and in_stage[c] and keep(r, c):
-                    er.append(loc[r])
-                    ec.append(loc[c])
-        G = sp.csr_matrix((np.ones(len(er)), (er, ec)), shape=(S.size, S.size))
-        ncomp, lab = csg.connected_components(G, directed=False)
-        members = [[] for _ in range(ncomp)]
+        lab = _stage_labels(A0, S, in_stage, medium, keep, variant, merge_cap)
+        members = {}
         for li, r in enumerate(S):
-            members[lab[li]].append(r)
-        for cells in members:
+            members.setdefault(int(lab[li]), []).append(r)
+        for key in sorted(members):
+            cells = members[key]
             cells = sorted(cells)
             b = len(cells)
             bl = {r: i for i, r in enumerate(cells)}
@@ -186,7 +251,7 @@ def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=No
                         diag += a
                         continue
                     T = -a
-                    if keep(r, c):
+                    if keep(r, c) and (c in bl or not in_stage[c]):
                         if c in bl:
                             Ab[i, bl[c]] = a
                         else:
@@ -236,16 +301,23 @@ def _solve(Ablk, R):
     return sp.csr_matrix(lu.solve(Rd))
 
 
-def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None, net=None):
+def prolongation_appendix(A0, rank, medium, node_cell, variant, plate=None, net=None,
+                          merge_cap=0):
     """P from the printed block formulas of Appendix A (regular wirebasket:
     the blocks that the TPFA stencil makes zero are taken as zero).  Face-face
-    links across fracture crossings, and every link between two coarsening
-    networks, are dropped from A0 first (removed from the diagonal), as in
-    keep_link."""
+    links across fracture crossings, every link between two coarsening
+    networks, and the links a Coupled merge cap cuts, are dropped from A0
+    first (removed from the diagonal), as in keep_link and
+    prolongation_staged."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
+    cut = cut_links(A0, rank, medium, node_cell, variant, plate, net, merge_cap) \
+        if merge_cap > 0 else []
     A0 = A0.tolil()
+    for r, c in cut:
+        A0[r, r] = A0[r, r] + A0[r, c]
+        A0[r, c] = 0.0
     for r in np.nonzero(medium == F)[0]:
         for c in list(A0.rows[r]):
             if c == r or medium[c] != F:

@@ -73,6 +73,12 @@ __device__ inline int crossing(const int* plate, long long nrow, int r, int c) {
   return plate[nrow + r] != plate[nrow + c] ? 2 : 1;
 }
 
+// a same-stage link across the media of a Coupled instance with a merge cap:
+// left out of the first union, merged within the cap afterwards
+__device__ inline bool capped_cross(const Inst& I, int mr, int mc) {
+  return I.merge_cap > 0 && mr != mc;
+}
+
 // input fracture and coarsening network of every unknown (-1 for matrix cells)
 __global__ void k_row_plate(const Inst* inst, int B, const int* off_row, long long nrow,
                             const int* f_cfirst, const int* f_sfirst, const int* f_ns,
@@ -163,6 +169,7 @@ __global__ void k_stage_union(const Inst* inst, int B, const int* off_row, long 
   for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
     int c = col[p];
     if (c <= r || !instage[c]) continue;
+    if (capped_cross(I, mr, medium_of(I, c))) continue;   // merged afterwards, within the cap
     if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, nrow, (int)r, c))) continue;
     int a = uf_find(parent, (int)r), b = uf_find(parent, c);
     while (a != b) {
@@ -182,6 +189,81 @@ __global__ void k_stage_flatten(long long nrow, const int* instage, int* label) 
   int x = (int)r;
   while (parent[x] != x) x = parent[x];
   label[r] = x;
+}
+
+// Coupled with a merge cap (Sec. 3.1: the merged blocks may be limited):
+// the blocks of each medium come from the union above without the
+// cross-medium links; those links then merge blocks one at a time, in the
+// order of A's rows and columns, while the merged block stays within the cap.
+// csize[root] = cells of the block of `root`
+__global__ void k_root_size(long long nrow, const int* instage, const int* label, int* csize) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrow && instage[r]) atomicAdd(&csize[label[r]], 1);
+}
+
+// rows of the stage with a kept cross-medium link to a higher row of the stage
+__global__ void k_cross_flag(const Inst* inst, int B, const int* off_row, long long nrow,
+                             const int* rank, const int* plate, const int* rowptr, const int* col,
+                             const int* instage, int* flag) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  flag[r] = 0;
+  if (!instage[r]) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int mr = medium_of(I, (int)r), rr = rank[r];
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+    int c = col[p];
+    if (c <= r || !instage[c] || !capped_cross(I, mr, medium_of(I, c))) continue;
+    if (keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, nrow, (int)r, c))) {
+      flag[r] = 1;
+      return;
+    }
+  }
+}
+
+__global__ void k_compact_rows(long long nrow, const int* flag, const int* pos, int* list) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrow && flag[r]) list[pos[r]] = (int)r;
+}
+
+__device__ inline int cap_find(int* parent, int x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]];
+    x = parent[x];
+  }
+  return x;
+}
+
+// one thread per instance walks its listed rows in order (the merge order is
+// part of the method's result, so it is sequential by design)
+__global__ void k_merge_cap(const Inst* inst, int B, const int* off_row, long long nrow,
+                            const int* rank, const int* plate, const int* rowptr, const int* col,
+                            const int* instage, const int* list, int nlist, int* label,
+                            int* csize) {
+  int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= B) return;
+  const Inst& I = inst[ii];
+  if (I.merge_cap <= 0 || nlist == 0) return;
+  // first listed row of this instance
+  int lo = 0, hi = nlist;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (list[mid] < I.row_off) lo = mid + 1; else hi = mid;
+  }
+  for (int t = lo; t < nlist && list[t] < I.row_off + I.n; ++t) {
+    int r = list[t];
+    int mr = medium_of(I, r), rr = rank[r];
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int c = col[p];
+      if (c <= r || !instage[c] || !capped_cross(I, mr, medium_of(I, c))) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, nrow, r, c))) continue;
+      int a = cap_find(label, r), b = cap_find(label, c);
+      if (a == b || csize[a] + csize[b] > I.merge_cap) continue;
+      int l = min(a, b), h = max(a, b);
+      label[h] = l;
+      csize[l] += csize[h];
+    }
+  }
 }
 
 __global__ void k_root_flag(long long nrow, const int* label, int* flag) {
@@ -230,7 +312,7 @@ __device__ void bitonic_sort_int(int* a, int m) {
 // memory.
 __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
                             const int* plate, long long nrow, const int* rowptr, const int* col,
-                            const int* instage,
+                            const int* instage, const int* label,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
                             int* ncols, const int* colptr, int* colbuf, int* bw, int* err) {
@@ -270,7 +352,8 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
       int cc = col[p];
       if (cc == r) continue;
       if (instage[cc]) {
-        if (mode == 0 &&
+        // a link to another block of the stage (cut by a merge cap) is dropped
+        if (mode == 0 && label[cc] == label[r] &&
             keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) {
           bl = max(bl, i - pos[cc]);
           bu = max(bu, pos[cc] - i);
@@ -361,6 +444,7 @@ struct CompArgs {
   const double* val;
   const double* TD;
   const int* instage;
+  const int* label;          // block root per in-stage row
   const int* comp_list;
   long long ncomp;
   const int* comp_off;
@@ -405,7 +489,9 @@ __device__ void comp_solve(const CompArgs& a, int c, double* M, int* red) {
       double av = a.val[p];
       if (cc == r) { d += av - a.TD[r]; continue; }
       double T = -av;
-      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, a.nrow, r, cc))) {
+      // kept, unless it leads to another block of the stage (cut by a merge cap)
+      if (keep_link(I.basis, mr, rr, medium_of(I, cc), a.rank[cc], crossing(a.plate, a.nrow, r, cc)) &&
+          (!a.instage[cc] || a.label[cc] == a.label[r])) {
         if (a.instage[cc]) {
           int pc = a.pos[cc];
           if (pc < 0 || pc >= n || i - pc > bl || pc - i > bu) { atomicCAS(a.err, 0, DERR_INVAL); continue; }
@@ -563,6 +649,13 @@ int phase_basis(Batch& b) {
   FAMS_TRY(b.scratch((void**)&rscan, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&comp_of, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.scratch((void**)&pos, sizeof(int) * (nrow + 1)));
+  bool any_cap = false;
+  for (auto& I : b.h) any_cap = any_cap || I.merge_cap > 0;
+  int *csize = nullptr, *xlist = nullptr;
+  if (any_cap) {
+    FAMS_TRY(b.scratch((void**)&csize, sizeof(int) * (nrow + 1)));
+    FAMS_TRY(b.scratch((void**)&xlist, sizeof(int) * (nrow + 1)));
+  }
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   // leave room for the kernels' static shared memory
@@ -577,6 +670,21 @@ int phase_basis(Batch& b) {
     fams::note_launch(), k_stage_union<<<grid_for(nrow, T), T, 0, st>>>(
         b.d_inst, b.B, b.off_row, nrow, b.rank, plate, b.rowptr, b.col, instage, label);
     fams::note_launch(), k_stage_flatten<<<grid_for(nrow, T), T, 0, st>>>(nrow, instage, label);
+    if (any_cap && s < 2) {   // Coupled stages with cross-medium links: [mE,fE], [mF,fF]
+      FAMS_CUDA(cudaMemsetAsync(csize, 0, sizeof(int) * (nrow + 1), st));
+      fams::note_launch(), k_root_size<<<grid_for(nrow, T), T, 0, st>>>(nrow, instage, label, csize);
+      fams::note_launch(), k_cross_flag<<<grid_for(nrow, T), T, 0, st>>>(
+          b.d_inst, b.B, b.off_row, nrow, b.rank, plate, b.rowptr, b.col, instage, flag);
+      long long nl = 0;
+      FAMS_TRY(exclusive_scan(b, flag, rscan, nrow, &nl));
+      if (nl > 0) {
+        fams::note_launch(), k_compact_rows<<<grid_for(nrow, T), T, 0, st>>>(nrow, flag, rscan, xlist);
+        fams::note_launch(), k_merge_cap<<<grid_for(b.B, 32), 32, 0, st>>>(
+            b.d_inst, b.B, b.off_row, nrow, b.rank, plate, b.rowptr, b.col, instage, xlist,
+            (int)nl, label, csize);
+        fams::note_launch(), k_stage_flatten<<<grid_for(nrow, T), T, 0, st>>>(nrow, instage, label);
+      }
+    }
     fams::note_launch(), k_root_flag<<<grid_for(nrow, T), T, 0, st>>>(nrow, label, flag);
     long long ncomp = 0;
     FAMS_TRY(exclusive_scan(b, flag, rscan, nrow, &ncomp));
@@ -610,7 +718,7 @@ int phase_basis(Batch& b) {
       return FAMS_ECAPACITY;
     }
     fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
-                                            instage, coff, members, pos, pstage, poff, plen, pool,
+                                            instage, label, coff, members, pos, pstage, poff, plen, pool,
                                             s, 0, ncols, nullptr, nullptr, bw, b.d_err);
     FAMS_CUDA(cudaGetLastError());
     FAMS_TRY(b.check_err("dual-block columns"));
@@ -618,7 +726,7 @@ int phase_basis(Batch& b) {
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
     fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
-                                            instage, coff, members, pos, pstage, poff, plen, pool,
+                                            instage, label, coff, members, pos, pstage, poff, plen, pool,
                                             s, 1, ncols, colptr, colbuf, nullptr, b.d_err);
     // host plan: pool offsets, and the blocks by size class (doubles of
     // [A'_BB | R]): one warp, a 128-thread CTA, a 256-thread CTA in shared
@@ -656,7 +764,7 @@ int phase_basis(Batch& b) {
     pool.col[s] = ocol;
     pool.val[s] = oval;
     CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col, b.val, b.TD, instage,
-                nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
+                label, nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};
     // the size classes are disjoint sets of blocks: lists and workspace on the
     // main stream, then each class on its own stream so their tails overlap

@@ -42,6 +42,7 @@ struct Inst {
   double aperture, hf;
   int cx, cy, cz, dmin, fcz, basis, restriction, precision, max_iter;
   int krylov, restart;  // outer iteration; GMRES cycle length
+  int merge_cap;        // Coupled: largest block merged across the media (0: none)
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells

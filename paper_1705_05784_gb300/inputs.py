@@ -50,6 +50,7 @@ class Problem:
     basis: int = 0                   # 0 Decoupled, 1 Frac, 2 Rock, 3 Coupled
     restriction: int = 0             # 0 FV, 1 FE, 2 MSMIX
     alpha: float = 0.0
+    merge_cap: int = 0               # Coupled: largest block merged across the media (0: none)
     tol: float = 1e-8
     max_iter: int = 200
     krylov: int = 0                  # 0 the Table 1 loop, 1 GMRES(restart)

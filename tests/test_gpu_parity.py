@@ -797,8 +797,11 @@ def test_bench_workload_instances_match_the_oracle():
 
 def _bench_oracle(i):
     """Pool worker: the oracle on instance i of the 16-instance bench batch --
-    its GMRES(30) iteration count to 1e-8 and the iterate after exactly that
-    many iterations."""
+    its GMRES(30) iteration count to 1e-8, the iterate after exactly that many
+    iterations, and the trajectory's own rounding sensitivity: the relative
+    change of that iterate when the initial guess 0 is replaced by 1e-14
+    times a seeded normal vector (a perturbation at the rounding level of a
+    pressure of order one)."""
     import warnings
     warnings.simplefilter("ignore")
     import bench
@@ -806,7 +809,10 @@ def _bench_oracle(i):
     g, sysm, co, P, so = oracle.build(p)
     xo, ito, rro, oko, _ = osolver.gmres_solve(so, tol=bench.TOL, max_iter=p.max_iter,
                                                restart=p.restart)
-    return i, xo, ito, oko
+    x0 = 1e-14 * np.random.default_rng(100 + i).standard_normal(sysm.n)
+    x1, _, _, _, _ = osolver.gmres_solve(so, x0=x0, tol=0.0, max_iter=ito, restart=p.restart)
+    sens = np.linalg.norm(x1 - xo) / np.linalg.norm(xo)
+    return i, xo, ito, oko, sens
 
 
 def _bench_oracle_flux(args):
@@ -828,15 +834,18 @@ def test_bench_workload_trajectories_at_full_size():
     the four coupling strategies x T_ratio 1e2, 1e4, 1e6, 1e8: a batch of
     16 with the bench's options): each instance converges in the oracle's
     iteration count, after exactly that many GMRES iterations its pressure
-    equals the oracle's to 1e-10 relative L2, and its conservative fluxes
-    from that iterate equal the oracle's reconstruction to 1e-8 of the
+    equals the oracle's to 1e-10 relative L2 -- or, where the oracle's own
+    trajectory moves by more under a rounding-level change of its initial
+    guess (T_ratio 1e6 and 1e8 reach 1e-9..3e-7: the systems' conditioning
+    amplifies rounding), to 10 times that sensitivity -- and its conservative
+    fluxes from that iterate equal the oracle's reconstruction to 1e-8 of the
     largest flux.  The oracle runs on the host cores in spawned processes."""
     import multiprocessing as mp
     import bench
     fams = _fams()
     with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
-        ref = {i: (xo, ito, oko) for i, xo, ito, oko in pool.imap_unordered(_bench_oracle,
-                                                                          range(16))}
+        ref = {i: (xo, ito, oko, sens) for i, xo, ito, oko, sens in
+               pool.imap_unordered(_bench_oracle, range(16))}
         assert all(ref[i][2] for i in range(16))
         probs = bench.problems(16, bench.ORACLE_SEED)
         with fams.Context(probs) as c:
@@ -852,7 +861,8 @@ def test_bench_workload_trajectories_at_full_size():
             assert [s["iterations"] for s in stk] == [ref[i][1] for i in range(16)]
             errs = [np.linalg.norm(xk[i] - ref[i][0]) / np.linalg.norm(ref[i][0])
                     for i in range(16)]
-            assert max(errs) < 1e-10, errs
+            bounds = [max(1e-10, 10.0 * ref[i][3]) for i in range(16)]
+            assert all(e <= b for e, b in zip(errs, bounds)), list(zip(errs, bounds))
             fl = [c.flux(xk[i], i) for i in range(16)]
         for i, fo in pool.imap_unordered(_bench_oracle_flux, [(i, xk[i]) for i in range(16)]):
             got = bench.conn_fluxes(probs[i], *fl[i])
@@ -895,6 +905,34 @@ def test_global_workspace_size_class_matches_the_oracle(variant):
     flux, _, _, pt = osolver.reconstruct_flux(sysm, p, sfv, xs[0], c.primal, c.node_cell)
     conn = _interior_connections(p, face, nnc)
     np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
+    # conservative to the rounding of the local solves: their residual grows
+    # with the block size m (Wilkinson's n eps bound of a backward-stable
+    # elimination), so the per-cell bound is max(64, 4 m) eps T_max |p|_max
     _, _, cT = osolver.connections(sysm, p)
-    bound = 64 * np.finfo(float).eps * cT.max() * max(np.abs(pt).max(), 1.0)
+    m = np.bincount(c.primal).max()
+    bound = max(64, 4 * m) * np.finfo(float).eps * cT.max() * max(np.abs(pt).max(), 1.0)
     assert np.abs(_balance(sysm, p, face, conn)).max() < bound
+
+
+@pytest.mark.parametrize("cap", [8, 16])
+@pytest.mark.parametrize("name", ["3dcross", "3dlayers"])
+def test_coupled_merge_cap_matches_the_oracle(name, cap):
+    """Coupled-AMS with a merge cap (fams_opts.merge_cap): P bit-for-bit in
+    pattern and to 1e-12 in value, and a fixed-count GMRES trajectory to
+    1e-10, against the oracle's capped merge."""
+    fams = _fams()
+    p = _gmres(_case(name, 3, 1), 30, 12)
+    p.merge_cap = cap
+    g, sysm, c, P, st = oracle.build(p)
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    from oracle import basis as obasis
+    assert obasis.cut_links(sysm.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, cap)
+    with fams.Context(p) as ctx:
+        Pg = _gpu_P(ctx, P.shape)
+        np.testing.assert_array_equal(Pg.indptr, P.indptr)
+        np.testing.assert_array_equal(Pg.indices, P.indices)
+        np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
+        xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=12, restart=30)
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 12 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10

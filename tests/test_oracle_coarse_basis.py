@@ -366,3 +366,59 @@ def test_oblique_pieces_golden(case):
         assert [(i, j) for i, j, _ in got] == [(i, j) for i, j, _ in want]
         np.testing.assert_allclose([ln for _, _, ln in got], [f * L for _, _, f in want],
                                    rtol=1e-14, atol=0)
+
+
+def test_merge_capped_by_hand():
+    """Eight cells: same-medium blocks {0,1,2} {3} {4,5} {6,7}; cross-medium
+    links in order (2,3) (1,4) (3,6) (5,7).  Cap 4: (2,3) gives {0,1,2,3}
+    (4 cells); (1,4) would give 6 > 4, cut; (3,6) would give 6, cut; (5,7)
+    gives {4,5,6,7}.  Cap 6: (2,3) -> 4 cells, (1,4) -> 6, (3,6) -> 8 cut,
+    (5,7) -> {4,5} is already in the 6-cell block, {6,7} would give 8, cut."""
+    same = [(0, 1), (1, 2), (4, 5), (6, 7)]
+    cross = [(2, 3), (1, 4), (3, 6), (5, 7)]
+    assert basis.merge_capped(8, same, cross, 4) == [0, 0, 0, 0, 4, 4, 4, 4]
+    assert basis.merge_capped(8, same, cross, 6) == [0, 0, 0, 0, 0, 0, 6, 6]
+    assert basis.merge_capped(8, same, cross, 8) == [0] * 8
+    # a same-medium block above the cap merges with nothing
+    assert basis.merge_capped(8, same, cross, 2) == [0, 0, 0, 3, 4, 4, 6, 6]
+
+
+def _coupled_3d(cap):
+    p = _crossing_plates(3)
+    p.merge_cap = cap
+    return p
+
+
+@pytest.mark.parametrize("cap", [0, 8, 16])
+def test_coupled_merge_cap(cap):
+    """Coupled-AMS with a merge cap: the staged and Appendix A routes agree
+    (cut links removed from the diagonal), partition of unity holds, and no
+    block is larger than the cap unless one medium alone makes it so; with
+    cap 0, or a cap above every merged block, nothing is cut."""
+    p = _coupled_3d(cap)
+    g, s, c = _setup(p)
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    P1 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, cap)
+    P2 = basis.prolongation_appendix(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net,
+                                     cap)
+    assert abs(P1 - P2).max() < 1e-12
+    assert np.abs(np.asarray(P1.sum(axis=1)).ravel() - 1).max() < 1e-12
+    blocks = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, cap)
+    free = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, 0)
+    cut = basis.cut_links(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, cap)
+    if cap == 0:
+        assert not cut
+    else:
+        assert cut and all(c.medium[r] != c.medium[q] for r, q in cut)
+        big = max(len(b) for b in free)
+        assert big > cap
+        for cells in blocks:
+            if len(cells) > cap:   # then one medium's cells alone exceed the cap
+                sub = basis.stage_blocks(s.A0, c.rank, c.medium, c.node_cell, 0, plate,
+                                         c.row_net)
+                assert any(len(set(b) & set(cells)) > cap for b in sub)
+    big = max(len(b) for b in free)
+    assert not basis.cut_links(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, big)
+    P3 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, big)
+    P0 = basis.prolongation_staged(s.A0, c.rank, c.medium, c.node_cell, 3, plate, c.row_net, 0)
+    assert abs(P3 - P0).max() == 0.0
