@@ -123,6 +123,11 @@ typedef struct {
                         joining two blocks only while the merged block stays within the
                         cap; a link left between two blocks is dropped and removed from
                         the diagonal. */
+  int grid_solve;    /* the iteration of a single-instance context on every SM of the GPU
+                        (one cooperative kernel; GMRES in FP64): 0 = when the instance
+                        has at least 2^18 unknowns, 1 = always, -1 = never (one CTA per
+                        instance, as for batches).  The same arithmetic either way, up to
+                        the order of the sums. */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */

@@ -17,8 +17,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libfams.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["util", "geometry", "system", "coarse", "basis", "coarseop", "ilu", "solve", "flux", "api",
-         "server"]
+UNITS = ["util", "geometry", "system", "coarse", "basis", "coarseop", "ilu", "solve", "solve_grid",
+         "flux", "api", "server"]
 NOFMA = {"geometry"}
 
 

@@ -96,6 +96,7 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
     return bad("GMRES restart must be in 1..FAMS_MAX_RESTART");
   if (o.prepare_flux != 0 && o.prepare_flux != 1) return bad("prepare_flux must be 0 or 1");
   if (o.merge_cap < 0) return bad("merge_cap must be >= 0");
+  if (o.grid_solve < -1 || o.grid_solve > 1) return bad("grid_solve must be -1, 0 or 1");
   return FAMS_OK;
 }
 
@@ -162,6 +163,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.max_iter = o.max_iter; I.alpha = o.alpha;
     I.krylov = o.krylov; I.restart = o.krylov == FAMS_KRYLOV_GMRES ? o.restart : 0;
     I.merge_cap = o.basis == FAMS_COUPLED ? o.merge_cap : 0;
+    I.grid_solve = o.grid_solve;
     b.prepare_flux = b.prepare_flux || o.prepare_flux == 1;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;

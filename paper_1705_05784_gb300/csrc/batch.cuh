@@ -178,6 +178,14 @@ struct Batch {
   double* stat = nullptr;      // per instance: 4 doubles (iters, relres, converged, qnorm)
   double* hist = nullptr;      // per instance: relative residual after each sweep
   double* krylov = nullptr;    // GMRES bases of the instances that use GMRES
+  // whole-GPU solve of a single large instance (solve_grid.cu): A_c^-1 of
+  // the iteration's coarse system (nc x nc, row-major), its validity, the
+  // grid barrier and the partial sums of the grid reductions
+  double* ainv = nullptr;
+  bool ainv_ready = false;
+  void* gbar = nullptr;
+  double* gpart = nullptr;
+  int gpart_n = 0;
   // mixed precision: FP32 copies of A, P, P^T and the ILU(0) factors (plain
   // and level-ordered), FP32 work vectors and GMRES bases
   float* val32 = nullptr;
@@ -281,6 +289,13 @@ int refresh_mixed(Batch& b);                              // solve.cu
 int phase_ilu(Batch& b);          // ilu.cu
 int phase_alloc_work(Batch& b);   // solve.cu
 int run_solve(Batch& b, double tol, float* ms);   // solve.cu
+// solve_grid.cu: a single-instance context whose iteration runs on every SM
+constexpr long long GRID_SOLVE_ROWS = 1LL << 18;
+bool whole_gpu(const Batch& b);       // single instance, large or asked for: every SM
+bool solve_on_grid(const Batch& b);   // ... and its iteration is FP64 GMRES
+int run_solve_grid(Batch& b, double tol, float* ms);
+int ilu_factor_grid(Batch& b);        // ILU(0) factorisation on every SM
+int band_lu_grid(Batch& b, CoarseSys& cs, CoarseHost& ch);   // coarse band LU on every SM
 // flux.cu
 int flux_prepare(Batch& b, const CoarseHost** ch);
 int flux_beside(Batch& b, cudaEvent_t ready);   // flux.cu: flux_prepare on the side stream

@@ -235,7 +235,6 @@ constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choi
 // a pivot at most this fraction of the largest entry of its row (as assembled)
 // is numerically zero: the rounding the elimination leaves in that row, a few
 // eps times its scale, is then within three decimal digits of the pivot
-constexpr double SING_EPS = 1e-13;
 
 // Symmetric positive definite coarse systems (R^FE = P^T: A_c = P^T A P):
 // band LDL^T without pivoting, about a quarter of the band LU's work.  The
@@ -617,6 +616,18 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   FAMS_CUDA(cudaMemsetAsync(cs.band, 0, sizeof(double) * (ch.band_tot + 1), st));
   fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip,
                                                                    nullptr);
+  if (whole_gpu(b)) {
+    // one large instance: band LU with partial pivoting on every SM (its
+    // iteration solves with A_c^-1 formed from these factors)
+    FAMS_TRY(band_lu_grid(b, cs, ch));
+    if (!reuse) {
+      ch.binv_off.assign(B, 0);
+      FAMS_TRY(b.alloc((void**)&cs.binv, sizeof(double)));
+      FAMS_CUDA(cudaMemcpyAsync(cs.binv_off, ch.binv_off.data(), sizeof(long long) * B,
+                                cudaMemcpyHostToDevice, st));
+    }
+    return b.check_err("coarse LU");
+  }
   // factorisation: LDL^T for the symmetric positive definite (R^FE) systems
   // whose active triangle fits in shared memory, band LU for the others and
   // for any LDL^T that meets a non-positive pivot

@@ -31,6 +31,9 @@ constexpr int PK = 4;  // factor entries per row kept inline in the level-ordere
 constexpr int MAX_OVERLAP = 8;        // matrix columns one fracture cell may cross
 constexpr double ZERO_PIECE = 1e-12;  // x h_f
 constexpr double DIST_FLOOR = 1e-3;   // x h_f
+// a pivot at most this fraction of the largest entry of its row (as
+// assembled) is numerically zero: the coarse system is singular
+constexpr double SING_EPS = 1e-13;
 
 // Per-instance description, mirrored on the device.  Offsets index the
 // concatenated (block-diagonal) arrays of a batch.
@@ -43,6 +46,7 @@ struct Inst {
   int cx, cy, cz, dmin, fcz, basis, restriction, precision, max_iter;
   int krylov, restart;  // outer iteration; GMRES cycle length
   int merge_cap;        // Coupled: largest block merged across the media (0: none)
+  int grid_solve;       // single instance on every SM: 0 auto, 1 always, -1 never
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells

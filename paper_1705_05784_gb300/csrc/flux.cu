@@ -362,6 +362,9 @@ int flux_prepare(Batch& b, const CoarseHost** ch) {
 // system stays unbuilt and the reconstruction builds it (and reports the
 // error) on its first call.
 int flux_beside(Batch& b, cudaEvent_t ready) {
+  // a whole-GPU context builds it on its own stream when first needed: its
+  // cooperative kernels take every SM and never run beside another kernel
+  if (whole_gpu(b)) return FAMS_OK;
   bool all_fv = b.pf_alias;
   for (auto& I : b.h) all_fv = all_fv && I.restriction == FAMS_R_FV;
   if ((all_fv || b.fv_ready) && !b.h_blk_ptr.empty()) return FAMS_OK;

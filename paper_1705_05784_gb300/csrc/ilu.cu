@@ -187,8 +187,13 @@ int phase_ilu(Batch& b) {
   FAMS_TRY(sort_segments(b, b.lev_ptr, tl, b.lev_rows, nullptr, false));
   FAMS_TRY(b.alloc((void**)&b.ilu, sizeof(double) * (b.tot_nnz + 1)));
   FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
-  fams::note_launch(), k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag, b.lev_off, b.lev_ptr,
-                                  b.lev_rows, b.ilu, b.d_err);
+  if (whole_gpu(b)) {
+    FAMS_TRY(ilu_factor_grid(b));
+  } else {
+    fams::note_launch(), k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag,
+                                                          b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
+                                                          b.d_err);
+  }
   FAMS_CUDA(cudaGetLastError());
   FAMS_TRY(b.check_err("ILU(0)"));
   long long n1 = nrow + 1;
@@ -218,9 +223,13 @@ int ilu_refactor(Batch& b) {
   cudaStream_t st = b.stream;
   long long nrow = b.tot_row;
   FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
-  fams::note_launch(), k_ilu_factor<<<b.B, 512, 0, st>>>(b.d_inst, b.B, b.rowptr, b.col, b.diag,
-                                                          b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
-                                                          b.d_err);
+  if (whole_gpu(b)) {
+    FAMS_TRY(ilu_factor_grid(b));
+  } else {
+    fams::note_launch(), k_ilu_factor<<<b.B, 512, 0, st>>>(b.d_inst, b.B, b.rowptr, b.col, b.diag,
+                                                            b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
+                                                            b.d_err);
+  }
   FAMS_CUDA(cudaGetLastError());
   FAMS_TRY(b.check_err("ILU(0)"));
   if (nrow > 0)

@@ -1030,6 +1030,7 @@ int make_q(Batch& b, const double* rhs_dev) {
 }
 
 int run_solve(Batch& b, double tol, float* ms) {
+  if (solve_on_grid(b)) return run_solve_grid(b, tol, ms);
   SolveArgs a{};
   a.inst = b.d_inst;
   a.cs = b.cs[0];

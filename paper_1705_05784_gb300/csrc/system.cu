@@ -221,6 +221,7 @@ int phase_update(Batch& b, const double* const* scale) {
   // P stays; R A P, its factors, ILU(0) and the FP32 copies follow A
   FAMS_TRY(build_coarse_system(b, b.cs[0], -1, b.csh[0], true, b.p_ptr, b.p_col, b.p_val));
   b.fv_ready = false;
+  b.ainv_ready = false;
   FAMS_TRY(ilu_refactor(b));
   FAMS_TRY(refresh_mixed(b));
   FAMS_CUDA(cudaStreamSynchronize(st));
@@ -292,6 +293,7 @@ int phase_update_basis(Batch& b, const double* const* scale, double eps, int* re
   if (b.fv_built) release_coarse(b, b.cs[1], b.csh[1]);
   b.fv_built = false;
   b.fv_ready = false;
+  b.ainv_ready = false;
   if (b.p_val32) {   // FP32 copies of P and P^T at the new size
     b.release(b.p_val32);
     b.release(b.pt_val32);

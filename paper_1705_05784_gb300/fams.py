@@ -45,7 +45,8 @@ class fams_opts(C.Structure):
                 ("basis", C.c_int), ("restriction", C.c_int), ("alpha", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
                 ("restart", C.c_int),
-                ("prepare_flux", C.c_int), ("merge_cap", C.c_int)]
+                ("prepare_flux", C.c_int), ("merge_cap", C.c_int),
+                ("grid_solve", C.c_int)]
 
 
 class fams_stats(C.Structure):
@@ -141,7 +142,7 @@ def _args(prob):
                   max(1, prob.frac_cz), prob.basis, prob.restriction, prob.alpha,
                   prob.max_iter, getattr(prob, "precision", FP64), getattr(prob, "krylov", 0),
                   getattr(prob, "restart", 30), getattr(prob, "prepare_flux", 0),
-                  getattr(prob, "merge_cap", 0))
+                  getattr(prob, "merge_cap", 0), getattr(prob, "grid_solve", 0))
     return g, perm, f, o, (xy, kf)
 
 

@@ -936,3 +936,32 @@ def test_coupled_merge_cap_matches_the_oracle(name, cap):
         xs, stats = ctx.solve(tol=0.0)
         assert stats[0]["iterations"] == 12 == ito
         assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3d", "3dlayers"])
+def test_whole_gpu_solve_matches_the_oracle(name, restriction):
+    """The iteration of a single instance on every SM (fams_opts.grid_solve =
+    1: one cooperative kernel, A_c^-1 formed from the band factors, grid
+    barriers per ILU level): a fixed-count GMRES trajectory to 1e-10 against
+    the oracle, and the converged solve in the same iteration count (+-1) as
+    the one-CTA kernel."""
+    fams = _fams()
+    p = _gmres(_case(name, 3 if name.startswith("3d") else 1, restriction), 10, 17)
+    p.grid_solve = 1
+    g, sysm, c, P, st = oracle.build(p)
+    xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=17, restart=10)
+    with fams.Context(p) as ctx:
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 17 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+    q = _gmres(p, 30, 300)
+    res = []
+    for mode in (1, -1):
+        q.grid_solve = mode
+        with fams.Context(q) as ctx:
+            xs, stats = ctx.solve(tol=1e-9)
+            assert stats[0]["converged"]
+            res.append((xs[0], stats[0]["iterations"]))
+    assert abs(res[0][1] - res[1][1]) <= 1
+    assert np.linalg.norm(res[0][0] - res[1][0]) / np.linalg.norm(res[1][0]) < 1e-6
