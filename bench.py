@@ -272,6 +272,76 @@ def sizes_of(ctx, i):
 
 ORACLE_SEED = 9000   # instances of the oracle baseline (same workload recipe)
 
+LARGE_WORKLOAD = ("3D 128x128x64 (1.05M matrix cells): layered log10 k std 2 corr (16,16,4), "
+                  "100 vertical plates (sides U[10,60] cells, random layer ranges), k_f 1e4, "
+                  "coarsening 8x8x8, fracture d_min 8 x 8 layers, Coupled-AMS (merge cap {cap}), "
+                  "R^FE, alpha 1e-2, ILU(0), GMRES(30), tol 1e-8, + flux reconstruction; "
+                  "one instance on every SM")
+
+
+def large_problem(cap, seed=3):
+    """The 3D scale case: one instance of about 1.2M unknowns."""
+    from paper_1705_05784_gb300 import inputs
+    p = inputs.config_3d(128, 128, 64, 2.0, (16, 16, 4), 100, (10, 60), 1e4, (8, 8, 8), 8, 8,
+                         seed=seed, basis=3, restriction=1, alpha=1e-2)
+    p.krylov, p.restart, p.max_iter, p.merge_cap = 1, 30, 400, cap
+    return p
+
+
+def large_instance(fams, steps, warmup, cap):
+    """Setup + solve + flux of the 3D scale case on the whole GPU (the
+    cooperative path), timed with CUDA events; the iteration kernel's HBM
+    roofline from its algorithmic bytes."""
+    import numpy as np
+    import torch
+    p = large_problem(cap)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    perm = torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev)
+
+    def one():
+        c = fams.Context(p, device_perm=[perm.data_ptr()])
+        S = sizes_of(c, 0)
+        x = torch.zeros(S["n"], dtype=torch.float64, device=dev)
+        f = torch.zeros(S["faces"], dtype=torch.float64, device=dev)
+        m = torch.zeros(max(S["nnc"], 1), dtype=torch.float64, device=dev)
+        st = c.solve_device([None], [x.data_ptr()], TOL)
+        fl = c.flux_batch_ptr([x.data_ptr()], [f.data_ptr()], [m.data_ptr()])
+        setup = [float(v) for v in c.query("SETUP_MS")]
+        c.close()
+        return S, st[0], fl[0], setup
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    runs = [one() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    S, st, fl, setup = runs[-1]
+    k_ms = statistics.median(r[1]["solve_ms"] for r in runs)
+    byts = gmres_bytes(S, st["iterations"], p.restart)
+    pk = peaks()
+    peak = pk.get("hbm_gbs", 6800.0)
+    ok = st["converged"] and fl == 0
+    return {"workload": LARGE_WORKLOAD.format(cap=cap), "unknowns": S["n"], "coarse": S["nc"],
+            "steps": steps, "ms_per_solve": ms, "solves_per_s": (1000.0 / ms) if ok else 0.0,
+            "cells_per_s": S["n"] * 1000.0 / ms if ok else 0.0,
+            "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+            "converged": st["converged"], "flux_status": fl,
+            "setup_ms": {k: round(v, 1) for k, v in zip(
+                ("geometry", "fine_system", "coarse_grids", "basis", "coarse_operator", "ilu0"),
+                setup)},
+            "solve_ms": k_ms,
+            "roofline": {"kernel": "k_gmres_grid (cooperative GMRES(30) over every SM)",
+                         "bound": "hbm", "achieved": byts / (k_ms / 1000.0) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": byts / (k_ms / 1000.0) / 1e9 / peak,
+                         "algorithmic_bytes": byts,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else
+                                        "fallback 6800 GB/s"}}
+
 
 def _oracle_one(i, keep=False):
     """The oracle on instance i of the baseline sample: setup, solve to TOL,
@@ -450,6 +520,10 @@ def main():
     ap.add_argument("--max-batch", type=int, default=64, help="server: requests per micro-batch")
     ap.add_argument("--plain", type=int, default=32,
                     help="requests of the stream solved one by one for the plain comparison")
+    ap.add_argument("--large", type=int, default=2,
+                    help="timed solves of the 3D 128x128x64 scale case (0: skip)")
+    ap.add_argument("--merge-cap", type=int, default=256,
+                    help="Coupled-AMS merge cap of the 3D scale case")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -606,6 +680,8 @@ def main():
         "clocks": clk.summary(),
         "cells_per_s": value * cells / max(converged_here, 1),
     }
+    if args.large > 0:
+        line["large_instance"] = large_instance(fams, args.large, 1, args.merge_cap)
     if args.serve > 0:
         sv = serving(fams, args.serve, args.plain, 7000, args.pipelines, args.max_batch)
         line["serving"] = sv

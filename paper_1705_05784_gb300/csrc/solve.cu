@@ -354,13 +354,15 @@ template <class T>
 struct SweepRow {
   int t, i, cnt, p;
   T base, diag;
+  T xo, dpo;   // U sweep: the row's base and multiscale correction, loaded ahead too
   int c[PK];
   T f[PK];
 };
 
 template <class T>
 __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int nlev, bool lower,
-                                  SweepRow<T>& s) {
+                                  SweepRow<T>& s, const T* dpv = nullptr,
+                                  const T* bv = nullptr) {
   s.t = -1;
   if (l < 0 || l >= nlev) return;
   int t = lp[l] + threadIdx.x;
@@ -375,6 +377,8 @@ __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int 
   } else {
     s.cnt = a.pk_nu[t];
     s.diag = Prec<T>::ud(a)[t];
+    s.dpo = dpv[s.i];
+    s.xo = bv ? bv[s.i] : T(0);
   }
   const int* pc = lower ? a.pk_lc : a.pk_uc;
   const T* pv = lower ? Prec<T>::lv(a) : Prec<T>::uv(a);
@@ -394,6 +398,21 @@ struct SolveSmem {
   double* buf;
   int* pbuf;
 };
+
+// SM cycles per phase, kept by thread 0 in shared memory: cyc[0..5] the six
+// phases, cyc[6] the time stamp of the last mark (no registers held across
+// the phases)
+constexpr int NCYC = 7;
+__device__ inline void stamp(long long* cyc) {
+  if (threadIdx.x == 0) cyc[6] = clock64();
+}
+__device__ inline void mark(long long* cyc, int k) {
+  if (threadIdx.x == 0) {
+    const long long now = clock64();
+    cyc[k] += now - cyc[6];
+    cyc[6] = now;
+  }
+}
 
 // Steps 5-7 of Table 1 on a residual r, in the arithmetic T of the vectors
 // (the coarse solve is FP64 in both; SM cycles of the phases are added to
@@ -418,7 +437,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   const T* F = Prec<T>::F(a);
   T* y = Prec<T>::y(a);
   T* ylev = Prec<T>::ylev(a);
-  long long t1 = clock64();
+  stamp(cyc);
   // step 5: coarse right-hand side R r, in band order: one warp per coarse
   // row (a row of P^T or a primal block holds hundreds of cells), lanes
   // along the row, then a fixed butterfly sum
@@ -442,7 +461,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
     }
   }
   __syncthreads();
-  long long t1b = clock64();
+  mark(cyc, 1);
   if (a.cs.nopiv[ii] && 4 * (COARSE_NB + kl) <= 2 * BAND_BUF)
     coarse_solve_blocked(AB, a.cs.binv + a.cs.binv_off[ii], nc, kl, ku, S.yb, S.buf);
   else
@@ -452,7 +471,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
     a.csol[co + perm[k]] = S.yb[k];
   }
   __syncthreads();
-  long long t2 = clock64();
+  mark(cyc, 2);
   // dp1 = P e_c
   for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
 #pragma unroll
@@ -469,7 +488,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
   rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
   __syncthreads();
-  long long t3 = clock64();
+  mark(cyc, 3);
   // step 7, L sweep: y_i = r1_i - sum_{j<i} L_ij y_j, by level position t.
   // Results also go to a shared-memory ring of the last SWEEP_RING
   // positions (the band buffer, idle during the sweeps): a neighbour from a
@@ -502,17 +521,17 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
     __syncthreads();
     cur = nxt;
   }
-  long long t4 = clock64();
+  mark(cyc, 4);
   // U sweep and step 8: out = (base + dp1) + dp2; the ring now holds the
   // upper neighbours, valid while tc < lp[l] + SWEEP_RING
-  sweep_load<T>(a, lp, nlev - 1, nlev, false, cur);
+  sweep_load<T>(a, lp, nlev - 1, nlev, false, cur, dp, base);
   for (int l = nlev - 1; l >= 0; --l) {
-    sweep_load<T>(a, lp, l - 1, nlev, false, nxt);
+    sweep_load<T>(a, lp, l - 1, nlev, false, nxt, dp, base);
     const int lim = lp[l] + SWEEP_RING;
     auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
     if (cur.t >= 0) {
       T s = cur.base;
-      T xo = base ? base[cur.i] : T(0), dpo = dp[cur.i];
+      const T xo = cur.xo, dpo = cur.dpo;
 #pragma unroll
       for (int k = 0; k < PK; ++k)
         if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
@@ -540,14 +559,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
     __syncthreads();
     cur = nxt;
   }
-  long long t5 = clock64();
-  if (cyc) {
-    cyc[1] += t1b - t1;
-    cyc[2] += t2 - t1b;
-    cyc[3] += t3 - t2;
-    cyc[4] += t4 - t3;
-    cyc[5] += t5 - t4;
-  }
+  mark(cyc, 5);
 }
 
 __device__ inline SolveSmem solve_smem(double* sm, int nc, int* pbuf) {
@@ -594,9 +606,11 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   double rel = 0.0, prev = INFINITY;
   // SM cycles per phase (thread 0, between barriers): residual, restriction,
   // band solve, prolongation + r1, L sweep, U sweep
-  long long cyc[6] = {0, 0, 0, 0, 0, 0};
+  __shared__ long long cyc[NCYC];
+  if (threadIdx.x < NCYC) cyc[threadIdx.x] = 0;
+  __syncthreads();
   for (;;) {
-    long long t0 = clock64();
+    stamp(cyc);
     // step 3: r = q - A p (FP64)
     acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
     rel = sqrt(block_sum(acc, red)) / qn;
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
       s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii]);
     }
     __syncthreads();
-    cyc[0] += clock64() - t0;
+    mark(cyc, 0);
     if (s_done) break;
     // steps 5-8: p = p + dp1 + dp2
     if (!use32) {
@@ -737,11 +751,11 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
   const long long ld = a.ntot;
   const int NT = blockDim.x;
   // V_0 = r / beta, g = beta e_1
-  long long t0 = clock64();
+  stamp(cyc);
   for (int i = ro + threadIdx.x; i < ro + n; i += NT) V[i] = a.r[i] / beta;
   for (int k = threadIdx.x; k <= m; k += NT) G.g[k] = k == 0 ? beta : 0.0;
   __syncthreads();
-  cyc[0] += clock64() - t0;
+  mark(cyc, 0);
   int k = 0;
   for (;;) {
     // z = M^-1 V_k, w = A z (in V_{k+1})
@@ -753,11 +767,11 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
       for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)Vk[i];
       __syncthreads();
       two_stage<float>(a, I, ii, a.rf, a.dpf, Zk, nullptr, S, cyc);
-      t0 = clock64();
+      stamp(cyc);
       acc = rows_apply_wide(a, ro, n, Zk, w);
     } else {
       two_stage<double>(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
-      t0 = clock64();
+      stamp(cyc);
       acc = rows_apply<double>(a, ro, n, a.r, w);
     }
     (void)acc;
@@ -832,13 +846,13 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
       *G.done = (est <= a.tol || k + 1 >= m || it + 1 >= I.max_iter || !isfinite(est));
     }
     __syncthreads();
-    cyc[0] += clock64() - t0;
+    mark(cyc, 0);
     ++k;
     ++it;
     if (*G.done) break;
   }
   // y = H^-1 g (upper triangular k x k)
-  t0 = clock64();
+  stamp(cyc);
   if (threadIdx.x == 0) {
     for (int i = k - 1; i >= 0; --i) {
       double s = G.g[i];
@@ -855,7 +869,7 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
       a.x[i] += s;
     }
     __syncthreads();
-    cyc[0] += clock64() - t0;
+    mark(cyc, 0);
   } else {
     // u = V y (in V_k), x += M^-1 u
     double* u = V + (long long)k * ld;
@@ -865,7 +879,7 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
       u[i] = s;
     }
     __syncthreads();
-    cyc[0] += clock64() - t0;
+    mark(cyc, 0);
     two_stage<double>(a, I, ii, u, a.dp, a.x, a.x, S, cyc);
   }
 }
@@ -906,14 +920,16 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
   for (int i = ro + threadIdx.x; i < ro + n; i += NT) acc += a.q[i] * a.q[i];
   double qn = sqrt(block_sum(acc, red));
   if (!(qn > 0.0)) qn = 1.0;
-  long long cyc[6] = {0, 0, 0, 0, 0, 0};
-  long long t0 = clock64();
+  __shared__ long long cyc[NCYC];
+  if (threadIdx.x < NCYC) cyc[threadIdx.x] = 0;
+  __syncthreads();
+  stamp(cyc);
   int it = 0;
   acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
   double beta = sqrt(block_sum(acc, red));
   double rel = beta / qn;
   if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len] = rel;
-  cyc[0] += clock64() - t0;
+  mark(cyc, 0);
   for (;;) {
     if (threadIdx.x == 0)
       s_done = (rel <= a.tol || it >= I.max_iter || !isfinite(rel) || a.cs.bad[ii] || !(beta > 0.0));
@@ -926,7 +942,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
     } else {
       gmres_cycle<false>(a, I, ii, kry64, nullptr, beta, qn, it, S, G, cyc);
     }
-    t0 = clock64();
+    stamp(cyc);
     acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
     double beta1 = sqrt(block_sum(acc, red));
     if (use32 && !(beta1 <= MIXED_MIN_GAIN * beta)) {
@@ -941,7 +957,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
     beta = beta1;
     rel = beta / qn;
     if (threadIdx.x == 0) a.hist[(long long)ii * a.hist_len + it] = rel;
-    cyc[0] += clock64() - t0;
+    mark(cyc, 0);
   }
   write_stats(a, ii, it, rel, qn, cyc);
 }
