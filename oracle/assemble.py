@@ -17,8 +17,16 @@ transmissibility T to both of its cells and A is symmetric:
 * fracture-fracture: along strike k_f a_f depth / h_s, vertically
   k_f a_f h_s / dz, intersections as built in geometry.py.
 
-Unknown order: matrix cells (x fastest, then y, then z) then fracture cells
-(Eq. 8 block order [m; f]).
+* wells (Sec. 2, q^mw = PI lambda^m (p^w - p^m) / V, volume-integrated): a
+  perforation of matrix cell i connects it to its well with
+  beta_i = PI_i k_i.  A rate-controlled well is one more unknown p^w (the
+  paper gives each well a single fine-scale DOF, Sec. 3) with the equation
+  sum_i beta_i (p^w - p_i) = Q_w; a pressure-controlled well (p^w fixed)
+  acts on its perforated cells like a Dirichlet half-cell: beta_i (p_i -
+  p_bhp), kept out of A0 like the Dirichlet faces.
+
+Unknown order: matrix cells (x fastest, then y, then z), then fracture cells,
+then the rate-controlled wells in input order (Eq. 8 block order [m; f; w]).
 """
 from __future__ import annotations
 
@@ -89,11 +97,32 @@ def dirichlet_terms(prob):
             np.concatenate(fids))
 
 
+WELL_RATE, WELL_PRESSURE = 0, 1
+
+
+def well_terms(prob):
+    """(rate-well connections (cell, well k, beta), pressure-well terms (cell,
+    beta, p_bhp, well index)) in input order; beta = PI k of the cell."""
+    perm = np.asarray(prob.perm, np.float64)
+    rate, pres = [], []
+    nw = 0
+    for w, wl in enumerate(getattr(prob, "wells", None) or []):
+        cells = np.asarray(wl.cells, np.int64)
+        beta = np.asarray(wl.pi, np.float64) * perm[cells]
+        if wl.control == WELL_RATE:
+            rate.append((cells, np.full(len(cells), nw), beta))
+            nw += 1
+        else:
+            pres.append((cells, beta, np.full(len(cells), float(wl.value)), np.full(len(cells), w)))
+    return rate, pres, nw
+
+
 def assemble(prob, geom=None):
     """Build A (with Dirichlet terms), A0 (without them) and the total rhs."""
     g = build_geometry(prob) if geom is None else geom
     nm, nf = g.n_matrix, g.n_frac
-    n = nm + nf
+    rate, pres, nw = well_terms(prob)
+    n = nm + nf + nw
     perm = np.asarray(prob.perm, np.float64)
     rows, cols, vals = [], [], []
     conns = []  # (i, j, T) for every connection, i < j
@@ -104,6 +133,9 @@ def assemble(prob, geom=None):
     Tmf = g.nnc_area / g.nnc_dist * perm[g.nnc_m]
     conns.append((g.nnc_m, nm + g.nnc_f, Tmf))
     conns.append((nm + g.ff_a, nm + g.ff_b, g.ff_T))
+    # rate-controlled wells: perforated cell - well DOF
+    for cells, wk, beta in rate:
+        conns.append((cells, nm + nf + wk, beta))
 
     for i, j, T in conns:
         rows += [i, j, i, j]
@@ -114,6 +146,12 @@ def assemble(prob, geom=None):
     A0.sum_duplicates()
     A0.sort_indices()
     dc, dT, dp, dfid = dirichlet_terms(prob)
+    # pressure-controlled wells join the Dirichlet terms (face id 6 + well)
+    for cells, beta, pb, w in pres:
+        dc = np.concatenate([dc, cells])
+        dT = np.concatenate([dT, beta])
+        dp = np.concatenate([dp, pb])
+        dfid = np.concatenate([dfid, 6 + w])
     D = np.zeros(n)
     np.add.at(D, dc, dT)
     qD = np.zeros(n)
@@ -126,11 +164,21 @@ def assemble(prob, geom=None):
     s.n = n
     s.n_matrix = nm
     s.n_frac = nf
+    s.n_well = nw
+    s.well_conn = rate
     s.A = A
     s.A0 = A0
     s.T_D = D
     s.q_dirichlet = qD
-    src = np.zeros(n) if prob.rhs is None else np.asarray(prob.rhs, np.float64)
+    src = np.zeros(n)
+    if prob.rhs is not None:
+        r = np.asarray(prob.rhs, np.float64)
+        src[:len(r)] = r
+    k = 0
+    for wl in getattr(prob, "wells", None) or []:
+        if wl.control == WELL_RATE:
+            src[nm + nf + k] += wl.value   # total injection rate Q_w
+            k += 1
     s.q = src + qD
     s.dirichlet = (dc, dT, dp, dfid)
     s.Tmf = Tmf

@@ -38,7 +38,7 @@ import scipy.sparse.linalg as spla
 from .coarsen import RANK_E, RANK_F, RANK_I, RANK_V
 
 DECOUPLED, FRAC, ROCK, COUPLED = 0, 1, 2, 3
-M, F = 0, 1
+M, F, W = 0, 1, 2   # media: matrix, fractures, wells
 
 
 def keep_link(variant, med_r, rank_r, med_c, rank_c, cross=0):
@@ -49,6 +49,10 @@ def keep_link(variant, med_r, rank_r, med_c, rank_c, cross=0):
     are coarsened apart (3D plates of other layer ranges that cross), so
     their wirebaskets are unrelated and no link between two of them is
     kept: each network's basis functions are built on that network alone."""
+    if med_c == W:
+        return True    # a well's value is known (P^ww = I): the beta term of Eq. 18
+    if med_r == W:
+        return False   # well rows are coarse nodes
     if cross == 2 and med_r == F and med_c == F:
         return False
     if cross and med_r == F and med_c == F and rank_r == RANK_F and rank_c == RANK_F:

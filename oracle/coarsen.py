@@ -219,8 +219,16 @@ def build_coarse(prob, geom):
                     f = s_frac[v]
                     node_cell.append(nm + g.frac_first[f] + s_loc[v] + g.frac_ns[f] * vnode[vb])
             base += npr * nvb
-    # coarsening network of every fracture row (-1 for matrix rows)
-    row_net = np.full(nm + nf, -1, np.int64)
+    # each rate-controlled well: one fine DOF, its own coarse node and primal
+    # block (Sec. 3: mapped to the coarse scale by the identity), rank V
+    nw = sum(1 for wl in (getattr(prob, "wells", None) or []) if wl.control == 0)
+    if nw:
+        rank = np.concatenate([rank, np.full(nw, RANK_V, np.int64)])
+        primal = np.concatenate([primal, base + np.arange(nw)])
+        node_cell.extend(nm + nf + np.arange(nw))
+        base += nw
+    # coarsening network of every fracture row (-1 for matrix and well rows)
+    row_net = np.full(nm + nf + nw, -1, np.int64)
     for f in range(len(g.frac_ns)):
         ns = g.frac_ns[f]
         nk = g.frac_nk[f] if prob.dim == 3 else 1
@@ -233,5 +241,7 @@ def build_coarse(prob, geom):
     c.node_cell = np.array(node_cell, np.int64)
     c.n_coarse = base
     c.n_coarse_matrix = ncm
-    c.medium = np.concatenate([np.zeros(nm, np.int64), np.ones(nf, np.int64)])
+    c.n_well = nw
+    c.medium = np.concatenate([np.zeros(nm, np.int64), np.ones(nf, np.int64),
+                               np.full(nw, 2, np.int64)])
     return c

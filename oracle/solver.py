@@ -246,8 +246,8 @@ def multiscale_stage(s, x):
 
 def connections(sysm, prob):
     """Every connection (i, j, T) with i < j, in a fixed order: matrix x, y, z
-    faces, then matrix-fracture, then fracture-fracture.  Also returns the
-    Dirichlet face list."""
+    faces, then matrix-fracture, then fracture-fracture, then the
+    perforations of the rate-controlled wells (cell - well, wells in order)."""
     from .assemble import matrix_faces
     nm = sysm.n_matrix
     g = sysm.geom
@@ -256,6 +256,8 @@ def connections(sysm, prob):
         out.append((lo, hi, T))
     out.append((g.nnc_m, nm + g.nnc_f, sysm.Tmf))
     out.append((nm + g.ff_a, nm + g.ff_b, g.ff_T))
+    for cells, wk, beta in getattr(sysm, "well_conn", []):   # rate-controlled wells
+        out.append((cells, nm + sysm.n_frac + wk, beta))
     ci = np.concatenate([o[0] for o in out]).astype(np.int64)
     cj = np.concatenate([o[1] for o in out]).astype(np.int64)
     cT = np.concatenate([o[2] for o in out]).astype(np.float64)

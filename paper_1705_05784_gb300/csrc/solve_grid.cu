@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "batch.cuh"
 
@@ -84,7 +86,8 @@ struct GArgs {
   double* hist;
   long long hist_len;
   double* part;          // 2 x gridDim.x partial sums
-  GridBar* bar;
+  GridBar* bar;          // bar[0]: the grid; bar[1]: the CTAs of the ILU(0) sweeps
+  int sweep_ctas;        // CTAs that run the sweeps (enough threads for the widest level)
   double tol;
 };
 
@@ -94,17 +97,21 @@ __device__ inline long long gthreads() { return (long long)gridDim.x * blockDim.
 // loads of vectors written by other CTAs during the kernel: from L2
 __device__ inline double ldv(const double* p) { return __ldcg(p); }
 
-// false: the kernel must return (a barrier gave up, here or in another CTA)
-__device__ bool grid_sync(GridBar* bar) {
+// false: the kernel must return (a barrier gave up, here or in another CTA).
+// `parties` CTAs take part (the whole grid by default); the error word of
+// the grid's barrier (err) is shared by every barrier of the launch
+__device__ bool grid_sync(GridBar* bar, unsigned int parties = 0, int* err_word = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &bar->gen;
-    volatile int* verr = &bar->err;
+    int* ew = err_word ? err_word : &bar->err;
+    volatile int* verr = ew;
+    const unsigned int np = parties ? parties : gridDim.x;
     const unsigned int g = *vgen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&bar->count, 1u) == np - 1) {
       atomicExch(&bar->count, 0u);
       __threadfence();
       atomicAdd(&bar->gen, 1u);
@@ -113,7 +120,7 @@ __device__ bool grid_sync(GridBar* bar) {
       while (*vgen == g) {
         if (*verr) { ok = 0; break; }
         if (++polls > GRID_SPIN) {
-          atomicCAS(&bar->err, 0, DERR_TIMEOUT);
+          atomicCAS(ew, 0, DERR_TIMEOUT);
           ok = 0;
           break;
         }
@@ -205,41 +212,109 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
     a.ylev[a.pk_pos[i]] = s;
   }
   if (!grid_sync(a.bar)) return false;
-  // L sweep, level by level: y_t = r1_t - sum_{j<t} L_tj y_j
-  const long long nt = a.ntot;
-  for (int l = 0; l < a.nlev; ++l) {
-    for (long long t = a.lev_ptr[l] + t0; t < a.lev_ptr[l + 1]; t += T) {
-      double s = ldv(a.ylev + t);
-      const int cnt = a.pk_nl[t];
+  // the ILU(0) sweeps on the first sweep_ctas CTAs, level by level with a
+  // barrier among them (a level holds at most their threads' rows at once
+  // in 3D wavefronts; fewer parties make each barrier cheaper); each thread
+  // loads its row of the next level before the barrier.  The other CTAs wait
+  // at the grid barrier after the sweeps.
+  if ((int)blockIdx.x < a.sweep_ctas) {
+    const long long nt = a.ntot;
+    const long long ST = (long long)a.sweep_ctas * blockDim.x;
+    GridBar* sb = a.bar + 1;
+    int* ew = &a.bar->err;
+    // L sweep: y_t = r1_t - sum_{j<t} L_tj y_j
+    long long t = a.nlev > 0 ? a.lev_ptr[0] + t0 : 0;
+    int cnt = 0, p0 = 0, c[PK];
+    double yb = 0.0, f[PK];
+    auto load_l = [&](int l) {
+      t = a.lev_ptr[l] + t0;
+      if (t < a.lev_ptr[l + 1]) {
+        yb = ldv(a.ylev + t);
+        cnt = a.pk_nl[t];
+        p0 = a.pk_lp[t];
 #pragma unroll
-      for (int k = 0; k < PK; ++k)
-        if (k < cnt) s -= a.pk_lv[k * nt + t] * ldv(a.ylev + a.pk_lc[k * nt + t]);
-      const int p0 = a.pk_lp[t];
-      for (int p = p0 + PK; p < p0 + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
-      a.ylev[t] = s;
-    }
-    if (!grid_sync(a.bar)) return false;
-  }
-  // U sweep and the update: out = (base + dp) + x_t, x_t = (y_t - sum_{j>t} U_tj x_j) / U_tt
-  for (int l = a.nlev - 1; l >= 0; --l) {
-    for (long long t = a.lev_ptr[l] + t0; t < a.lev_ptr[l + 1]; t += T) {
-      const int i = a.lev_rows[t];
-      double s = ldv(a.ylev + t);
-      const int cnt = a.pk_nu[t];
-#pragma unroll
-      for (int k = 0; k < PK; ++k)
-        if (k < cnt) s -= a.pk_uv[k * nt + t] * ldv(a.ylev + a.pk_uc[k * nt + t]);
-      if (cnt > PK) {
-        const int d = a.diag[i];
-        for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+        for (int k = 0; k < PK; ++k) {
+          c[k] = a.pk_lc[k * nt + t];
+          f[k] = a.pk_lv[k * nt + t];
+        }
       }
-      const double xi = s * a.pk_ud[t];
-      a.ylev[t] = xi;
-      a.y[i] = xi;
-      out[i] = ((base ? ldv(base + i) : 0.0) + ldv(a.dp + i)) + xi;
+    };
+    if (a.nlev > 0) load_l(0);
+    for (int l = 0; l < a.nlev; ++l) {
+      const long long te = a.lev_ptr[l + 1];
+      if (t < te) {
+        double s = yb;
+#pragma unroll
+        for (int k = 0; k < PK; ++k)
+          if (k < cnt) s -= f[k] * ldv(a.ylev + c[k]);
+        for (int p = p0 + PK; p < p0 + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+        a.ylev[t] = s;
+        for (long long u = t + ST; u < te; u += ST) {   // rows beyond one per thread
+          double s2 = ldv(a.ylev + u);
+          const int c2 = a.pk_nl[u], q0 = a.pk_lp[u];
+          for (int k = 0; k < PK && k < c2; ++k) s2 -= a.pk_lv[k * nt + u] * ldv(a.ylev + a.pk_lc[k * nt + u]);
+          for (int p = q0 + PK; p < q0 + c2; ++p) s2 -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+          a.ylev[u] = s2;
+        }
+      }
+      if (l + 1 < a.nlev) load_l(l + 1);
+      if (!grid_sync(sb, (unsigned)a.sweep_ctas, ew)) return false;
     }
-    if (!grid_sync(a.bar)) return false;
+    // U sweep and the update: out = (base + dp) + x_t, x_t = (y_t - sum_{j>t} U_tj x_j) / U_tt
+    double ud = 0.0, xo = 0.0, dpo = 0.0;
+    int row = 0;
+    auto load_u = [&](int l) {
+      t = a.lev_ptr[l] + t0;
+      if (t < a.lev_ptr[l + 1]) {
+        row = a.lev_rows[t];
+        yb = ldv(a.ylev + t);
+        cnt = a.pk_nu[t];
+        ud = a.pk_ud[t];
+        dpo = ldv(a.dp + row);
+        xo = base ? ldv(base + row) : 0.0;
+#pragma unroll
+        for (int k = 0; k < PK; ++k) {
+          c[k] = a.pk_uc[k * nt + t];
+          f[k] = a.pk_uv[k * nt + t];
+        }
+      }
+    };
+    if (a.nlev > 0) load_u(a.nlev - 1);
+    for (int l = a.nlev - 1; l >= 0; --l) {
+      const long long te = a.lev_ptr[l + 1];
+      if (t < te) {
+        double s = yb;
+#pragma unroll
+        for (int k = 0; k < PK; ++k)
+          if (k < cnt) s -= f[k] * ldv(a.ylev + c[k]);
+        if (cnt > PK) {
+          const int d = a.diag[row];
+          for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+        }
+        const double xi = s * ud;
+        a.ylev[t] = xi;
+        a.y[row] = xi;
+        out[row] = (xo + dpo) + xi;
+        for (long long u = t + ST; u < te; u += ST) {   // rows beyond one per thread
+          const int i = a.lev_rows[u];
+          double s2 = ldv(a.ylev + u);
+          const int c2 = a.pk_nu[u];
+          for (int k = 0; k < PK && k < c2; ++k) s2 -= a.pk_uv[k * nt + u] * ldv(a.ylev + a.pk_uc[k * nt + u]);
+          if (c2 > PK) {
+            const int d = a.diag[i];
+            for (int p = d + 1 + PK; p <= d + c2; ++p) s2 -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+          }
+          const double x2 = s2 * a.pk_ud[u];
+          a.ylev[u] = x2;
+          a.y[i] = x2;
+          out[i] = ((base ? ldv(base + i) : 0.0) + ldv(a.dp + i)) + x2;
+        }
+      }
+      if (l > 0) load_u(l - 1);
+      if (!grid_sync(sb, (unsigned)a.sweep_ctas, ew)) return false;
+    }
   }
+  if (!grid_sync(a.bar)) return false;
   return true;
 }
 
@@ -623,13 +698,13 @@ bool solve_on_grid(const Batch& b) {
 
 namespace {
 int grid_bar(Batch& b, int nblk) {
-  if (!b.gbar) FAMS_TRY(b.alloc((void**)&b.gbar, sizeof(GridBar)));
+  if (!b.gbar) FAMS_TRY(b.alloc((void**)&b.gbar, 2 * sizeof(GridBar)));
   if (b.gpart_n < nblk) {
     b.release(b.gpart);
     FAMS_TRY(b.alloc((void**)&b.gpart, sizeof(double) * (2 * (size_t)nblk + 16)));
     b.gpart_n = nblk;
   }
-  FAMS_CUDA(cudaMemsetAsync(b.gbar, 0, sizeof(GridBar), b.stream));
+  FAMS_CUDA(cudaMemsetAsync(b.gbar, 0, 2 * sizeof(GridBar), b.stream));
   return FAMS_OK;
 }
 
@@ -735,6 +810,16 @@ int run_solve_grid(Batch& b, double tol, float* ms) {
   a.part = static_cast<double*>(b.gpart);
   a.bar = static_cast<GridBar*>(b.gbar);
   a.tol = tol;
+  // CTAs of the sweeps: enough threads for the widest level at one row each
+  {
+    std::vector<int> lp(I.nlev + 1);
+    FAMS_CUDA(cudaMemcpyAsync(lp.data(), b.lev_ptr, sizeof(int) * (I.nlev + 1),
+                              cudaMemcpyDeviceToHost, b.stream));
+    FAMS_CUDA(cudaStreamSynchronize(b.stream));
+    int widest = 1;
+    for (int l = 0; l < I.nlev; ++l) widest = std::max(widest, lp[l + 1] - lp[l]);
+    a.sweep_ctas = std::max(1, std::min(nblk, (widest + GT - 1) / GT));
+  }
   cudaEvent_t e0, e1;
   FAMS_CUDA(cudaEventCreate(&e0));
   FAMS_CUDA(cudaEventCreate(&e1));

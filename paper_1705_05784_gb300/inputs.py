@@ -26,6 +26,21 @@ import numpy as np
 BC_WEST, BC_EAST, BC_SOUTH, BC_NORTH, BC_BOTTOM, BC_TOP = 1, 2, 4, 8, 16, 32
 
 
+WELL_RATE, WELL_PRESSURE = 0, 1
+
+
+@dataclass
+class Well:
+    """A vertical (or any) well: the matrix cells it perforates, the geometric
+    productivity index of each perforation, and its control: a total
+    injection rate (the well pressure is an unknown) or a bottom-hole
+    pressure."""
+    cells: np.ndarray
+    pi: np.ndarray
+    control: int = WELL_RATE
+    value: float = 0.0
+
+
 @dataclass
 class Problem:
     """One F-AMS problem instance (all arrays host numpy, float64 / int32)."""
@@ -59,6 +74,7 @@ class Problem:
     prepare_flux: int = 0            # 1: build the reconstruction's coarse system beside the solve
     precision: int = 0               # 0 FP64, 1 FP32 inner stages
     rhs: np.ndarray = None           # sources, length N (matrix then fracture); None = 0
+    wells: list = None               # Well objects (None: no wells)
     name: str = ""
     meta: dict = field(default_factory=dict)
 
@@ -182,3 +198,11 @@ def config_3d(nx, ny, nz, sigma, corr, n_plates, side, tratio, coarsen, dmin, cz
                    kf=np.full(len(fr), float(tratio)), coarsen=tuple(coarsen),
                    frac_dmin=dmin, frac_cz=cz, basis=basis, restriction=restriction,
                    alpha=alpha, name=f"3d-{nx}x{ny}x{nz}-{n_plates}pl-s{seed}")
+
+
+def column_well(nx, ny, nz, ix, iy, pi, control, value, k0=0, k1=None):
+    """A vertical well through the matrix column (ix, iy), layers k0..k1-1
+    (all layers by default), the same productivity index per perforation."""
+    k1 = nz if k1 is None else k1
+    cells = np.array([ix + nx * (iy + ny * k) for k in range(k0, k1)], np.int64)
+    return Well(cells=cells, pi=np.full(len(cells), float(pi)), control=control, value=value)
