@@ -86,6 +86,26 @@ typedef struct {
   double h_f;
 } fams_fracs;
 
+/* Peaceman wells (Sec. 2: q^mw = PI lambda^m (p^w - p^m) per perforated matrix
+   cell, volume-integrated; lambda^m = k).  Well w perforates the matrix cells
+   perf_cell[perf_ptr[w] .. perf_ptr[w+1]) (natural index, strictly ascending
+   within a well) with geometric productivity indices perf_pi (> 0).  A
+   FAMS_WELL_RATE well injects value[w] in total (negative: produces); its
+   pressure is one more unknown with the equation sum_i PI_i k_i (p^w - p_i) =
+   value[w], and it is one coarse node with P^ww = I and its own basis
+   function (Sec. 3.1).  A FAMS_WELL_PRESSURE well holds p^w = value[w]: its
+   perforations act like Dirichlet half-cells PI_i k_i (p_i - p^w).  All
+   arrays host or device memory, copied during setup. */
+enum { FAMS_WELL_RATE = 0, FAMS_WELL_PRESSURE = 1 };
+typedef struct {
+  int n;
+  const int* perf_ptr;
+  const int* perf_cell;
+  const double* perf_pi;
+  const int* control;
+  const double* value;
+} fams_wells;
+
 /* Method options.  coarsen[] = matrix coarsening ratio per axis; frac_dmin =
    d_min of the distance-based fracture coarsening (Table 2; <= 0 means
    infinity, one coarse node per network); frac_cz = vertical coarsening of 3D
@@ -128,6 +148,12 @@ typedef struct {
                         has at least 2^18 unknowns, 1 = always, -1 = never (one CTA per
                         instance, as for batches).  The same arithmetic either way, up to
                         the order of the sums. */
+  int subblock;      /* 1: after the ILU(0) stage, a sub-block smoothing stage (Sec. 3.2:
+                        iterations on the sub-block systems of each medium): r2 = r1 -
+                        A dp2, dp3 = ILU(0) of A without its cross-medium entries (the
+                        blocks A^mm, A^ff and the wells') applied to r2, p += dp3; once
+                        per Table 1 sweep or GMRES preconditioner application.  FP64
+                        only (FAMS_EINVAL with FAMS_MIXED). */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */
@@ -154,17 +180,39 @@ int fams_setup(const fams_grid* grid, const double* perm, const fams_fracs* frac
 int fams_setup_batch(int n, const fams_grid* grids, const double* const* perms,
                      const fams_fracs* fracs, const fams_opts* opts, fams_ctx** out);
 
+/* fams_setup_wells / fams_setup_batch_wells - the same with Peaceman wells
+   (wells nullable, or wells[i] per instance; fams_wells above).  Unknown
+   order [matrix; fractures; rate-controlled wells in input order]: every
+   vector of the instance (rhs, x) holds n_matrix + n_frac + n_well values
+   (fams_sizes_wells).  Errors as fams_setup; FAMS_EINVAL for a perforation
+   outside the matrix, perforations of a well not strictly ascending, a
+   non-positive or non-finite PI, an unknown control or a non-finite value. */
+int fams_setup_wells(const fams_grid* grid, const double* perm, const fams_fracs* fracs,
+                     const fams_wells* wells, const fams_opts* opts, fams_ctx** out);
+int fams_setup_batch_wells(int n, const fams_grid* grids, const double* const* perms,
+                           const fams_fracs* fracs, const fams_wells* wells,
+                           const fams_opts* opts, fams_ctx** out);
+
+/* fams_sizes_wells - rate-controlled wells (unknowns after the fracture
+   cells) and perforations of instance `inst`.  The fluxes of fams_flux follow
+   the fracture connections with one value per perforation (rate-controlled
+   wells first, then pressure-controlled, each in input order; positive from
+   the cell into the well), included in n_nnc of fams_sizes.  Null pointers
+   are skipped. */
+int fams_sizes_wells(const fams_ctx* ctx, int inst, int* n_well, int* n_perf);
+
 /* fams_sizes - counts of instance `inst`: fine unknowns of the matrix and the
    fractures, coarse unknowns, matrix faces (x, y then z faces including the
    boundary faces), and fracture connections (matrix-fracture then
-   fracture-fracture).  Null pointers are skipped. */
+   fracture-fracture, then well perforations).  Null pointers are skipped. */
 int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n_coarse,
                int* n_faces, int* n_nnc);
 
 /* fams_solve - Table 1 (steps 3, 5-8) on instance 0 of ctx from the initial
    guess in x until ||q - A x||_2 <= tol ||q||_2, q = rhs + Dirichlet terms.
-   rhs: n_matrix + n_frac sources (nullable = 0); x: in initial guess, out
-   pressure.  FAMS_ENOCONV leaves the last iterate in x; FAMS_EBREAKDOWN
+   rhs: n_matrix + n_frac sources (+ n_well values added to the rate wells'
+   rates; nullable = 0); x: in initial guess, out pressure (n_matrix + n_frac
+   + n_well values: the rate wells' pressures last).  FAMS_ENOCONV leaves the last iterate in x; FAMS_EBREAKDOWN
    reports a numerically singular coarse system (the test of fams_flux_batch). */
 int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st);
 
@@ -182,7 +230,9 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
    and its factors, the ILU(0) smoother and the fluxes' transmissibilities
    follow.  mobility_scale: n_matrix + n_frac positive finite values (not
    checked), relative to the setup (nullable: all 1, i.e. back to the setup
-   values); host or device. */
+   values); host or device.  A perforation scales like a connection whose
+   well side keeps scale 1 (rate well) or like a Dirichlet half-cell
+   (pressure well). */
 int fams_update(fams_ctx* ctx, const double* mobility_scale);
 /* the same for every instance of a batch context (scale[i] nullable) */
 int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);

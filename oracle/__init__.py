@@ -79,7 +79,8 @@ def build(prob, route="staged"):
     sysm = _asm.assemble(prob, g)
     c = _coarsen.build_coarse(prob, g)
     P = prolongation(prob, g, sysm, c, route)
-    st = _solver.setup(sysm, P, c.primal, c.n_coarse, prob.restriction)
+    st = _solver.setup(sysm, P, c.primal, c.n_coarse, prob.restriction,
+                       c.medium if getattr(prob, "subblock", 0) else None)
     return g, sysm, c, P, st
 
 

@@ -14,6 +14,12 @@ TEST INFRASTRUCTURE ONLY (see oracle/geometry.py).
     r = q - A p;  dp1 = P (R A P)^-1 R r;  r1 = r - A dp1;
     dp2 = (LU)^-1 r1;  p = p + dp1 + dp2
   iterated until ||q - A p||_2 <= tol ||q||_2 (q including Dirichlet terms).
+* optional sub-block smoothing stage (Sec. 3.2: iterations on the sub-block
+  systems of each medium, A^mm and A^ff): after step 7,
+    r2 = r1 - A dp2;  dp3 = (L_B U_B)^-1 r2;  p = p + dp3
+  with L_B U_B the ILU(0) of A without its cross-medium entries (the media's
+  diagonal blocks, wells a block of their own), one application per sweep
+  (reading: the paper leaves the stage's iterations open).
 * numerically singular coarse system (a reading; the paper is silent):
   Gaussian elimination with partial pivoting meets a pivot at most SING_EPS
   times the largest entry of its row as assembled (`singular_step`).
@@ -87,6 +93,15 @@ def ilu0(A):
     return F
 
 
+def block_matrix(A, medium):
+    """A with every entry that couples two media removed, its pattern kept:
+    the diagonal blocks A^mm, A^ff (and the wells') in place."""
+    C = sp.csr_matrix(A, copy=True)
+    rows = np.repeat(np.arange(C.shape[0]), np.diff(C.indptr))
+    C.data[np.asarray(medium)[rows] != np.asarray(medium)[C.indices]] = 0.0
+    return C
+
+
 def ilu0_apply(F, r):
     """Solve L U x = r with the factors from ilu0()."""
     L = sp.tril(F, k=-1, format="csr") + sp.identity(F.shape[0], format="csr")
@@ -127,7 +142,8 @@ def singular_step(M):
     return -1
 
 
-def setup(sysm, P, primal, n_coarse, kind):
+def setup(sysm, P, primal, n_coarse, kind, medium=None):
+    """medium (per unknown), when given, adds the sub-block smoothing stage."""
     s = Setup()
     s.A = sysm.A
     s.q = sysm.q
@@ -136,6 +152,7 @@ def setup(sysm, P, primal, n_coarse, kind):
     s.Ac = coarse_operator(s.R, sysm.A, P)
     s.lu = sla.lu_factor(s.Ac)
     s.F = ilu0(sysm.A)
+    s.Fb = None if medium is None else ilu0(block_matrix(sysm.A, medium))
     return s
 
 
@@ -156,6 +173,8 @@ def two_stage_solve(s, x0=None, tol=1e-8, max_iter=200, smoother=True, history=F
             r1 = r - A @ dp1                              # step 6
             dp2 = ilu0_apply(s.F, r1)                     # step 7
             p = p + dp2                                   # step 8
+            if getattr(s, "Fb", None) is not None:        # sub-block smoothing
+                p = p + ilu0_apply(s.Fb, r1 - A @ dp2)
         it += 1
         r = q - A @ p                                     # step 3 of the next sweep
         hist.append(np.linalg.norm(r) / qn)
@@ -169,7 +188,10 @@ def precondition(s, r, smoother=True):
     dp1 = s.P @ sla.lu_solve(s.lu, s.R @ r)
     if not smoother:
         return dp1
-    return dp1 + ilu0_apply(s.F, r - s.A @ dp1)
+    z = dp1 + ilu0_apply(s.F, r - s.A @ dp1)
+    if getattr(s, "Fb", None) is not None:
+        z = z + ilu0_apply(s.Fb, r - s.A @ z)
+    return z
 
 
 def gmres_solve(s, x0=None, tol=1e-8, max_iter=200, restart=30, history=False):

@@ -97,6 +97,8 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   if (o.prepare_flux != 0 && o.prepare_flux != 1) return bad("prepare_flux must be 0 or 1");
   if (o.merge_cap < 0) return bad("merge_cap must be >= 0");
   if (o.grid_solve < -1 || o.grid_solve > 1) return bad("grid_solve must be -1, 0 or 1");
+  if (o.subblock != 0 && o.subblock != 1) return bad("subblock must be 0 or 1");
+  if (o.subblock && o.precision != FAMS_FP64) return bad("subblock needs precision FAMS_FP64");
   return FAMS_OK;
 }
 
@@ -127,8 +129,136 @@ int copy_to_host(void* dst, const void* src, size_t bytes) {
   return FAMS_OK;
 }
 
+// wells of the batch to host arrays in the perforation order of the flux
+// output (per instance: rate wells' perforations, then pressure wells', each
+// in input order), with their checks
+struct HostWells {
+  std::vector<int> inst, cell, wloc;   // wloc: rate-well index in the instance, -1 pressure
+  std::vector<double> pi, bhp;
+  std::vector<int> nw, nperf;          // per instance
+  std::vector<double> rate;            // per rate well of the batch, in order
+};
+
+int read_wells(int n, const fams_grid* grids, const fams_wells* wells, HostWells& hw) {
+  hw.nw.assign(n, 0);
+  hw.nperf.assign(n, 0);
+  if (!wells) return FAMS_OK;
+  for (int i = 0; i < n; ++i) {
+    const fams_wells& W = wells[i];
+    if (W.n < 0) { set_error("wells.n must be >= 0"); return FAMS_EINVAL; }
+    if (W.n == 0) continue;
+    if (!W.perf_ptr || !W.control || !W.value) { set_error("wells arrays are null"); return FAMS_EINVAL; }
+    std::vector<int> ptr(W.n + 1), ctl(W.n);
+    std::vector<double> val(W.n);
+    FAMS_TRY(copy_to_host(ptr.data(), W.perf_ptr, sizeof(int) * (W.n + 1)));
+    FAMS_TRY(copy_to_host(ctl.data(), W.control, sizeof(int) * W.n));
+    FAMS_TRY(copy_to_host(val.data(), W.value, sizeof(double) * W.n));
+    if (ptr[0] != 0) { set_error("wells.perf_ptr[0] must be 0"); return FAMS_EINVAL; }
+    for (int w = 0; w < W.n; ++w)
+      if (ptr[w + 1] < ptr[w]) { set_error("wells.perf_ptr must not decrease"); return FAMS_EINVAL; }
+    const int np = ptr[W.n];
+    if (np > 0 && (!W.perf_cell || !W.perf_pi)) { set_error("wells arrays are null"); return FAMS_EINVAL; }
+    std::vector<int> cells(np);
+    std::vector<double> pis(np);
+    FAMS_TRY(copy_to_host(cells.data(), W.perf_cell, sizeof(int) * np));
+    FAMS_TRY(copy_to_host(pis.data(), W.perf_pi, sizeof(double) * np));
+    const fams_grid& g = grids[i];
+    const long long nm = (long long)g.nx * g.ny * (g.dim == 3 ? g.nz : 1);
+    for (int w = 0; w < W.n; ++w) {
+      if (ctl[w] != FAMS_WELL_RATE && ctl[w] != FAMS_WELL_PRESSURE) {
+        set_error("well control must be FAMS_WELL_RATE or FAMS_WELL_PRESSURE");
+        return FAMS_EINVAL;
+      }
+      if (!std::isfinite(val[w])) { set_error("well value must be finite"); return FAMS_EINVAL; }
+      if (ctl[w] == FAMS_WELL_RATE && ptr[w + 1] == ptr[w]) {
+        set_error("a rate-controlled well needs a perforation");
+        return FAMS_EINVAL;
+      }
+      for (int k = ptr[w]; k < ptr[w + 1]; ++k) {
+        if (cells[k] < 0 || cells[k] >= nm) { set_error("perforation outside the matrix"); return FAMS_EINVAL; }
+        if (k > ptr[w] && cells[k] <= cells[k - 1]) {
+          set_error("perforations of a well must be strictly ascending");
+          return FAMS_EINVAL;
+        }
+        if (!(pis[k] > 0.0) || !std::isfinite(pis[k])) {
+          set_error("productivity index must be positive and finite");
+          return FAMS_EINVAL;
+        }
+      }
+    }
+    for (int pass = 0; pass < 2; ++pass) {   // rate wells, then pressure wells
+      for (int w = 0; w < W.n; ++w) {
+        if ((ctl[w] == FAMS_WELL_RATE) != (pass == 0)) continue;
+        for (int k = ptr[w]; k < ptr[w + 1]; ++k) {
+          hw.inst.push_back(i);
+          hw.cell.push_back(cells[k]);
+          hw.wloc.push_back(pass == 0 ? hw.nw[i] : -1);
+          hw.pi.push_back(pis[k]);
+          hw.bhp.push_back(pass == 0 ? 0.0 : val[w]);
+          ++hw.nperf[i];
+        }
+        if (pass == 0) {
+          hw.rate.push_back(val[w]);
+          ++hw.nw[i];
+        }
+      }
+    }
+  }
+  return FAMS_OK;
+}
+
+int upload_wells(Batch& b, const HostWells& hw) {
+  b.tot_perf = (long long)hw.cell.size();
+  b.tot_w = (long long)hw.rate.size();
+  if (b.tot_perf == 0 && b.tot_w == 0) return FAMS_OK;
+  const long long np = b.tot_perf, nw = b.tot_w;
+  std::vector<int> mcell(np), mptr(b.tot_m + 1, 0), midx(np);
+  for (long long k = 0; k < np; ++k) {
+    mcell[k] = b.h[hw.inst[k]].m_off + hw.cell[k];
+    ++mptr[mcell[k] + 1];
+  }
+  for (long long c = 0; c < b.tot_m; ++c) mptr[c + 1] += mptr[c];
+  {
+    std::vector<int> cur(mptr.begin(), mptr.end() - 1);
+    for (long long k = 0; k < np; ++k) midx[cur[mcell[k]]++] = (int)k;
+  }
+  // [first, end) perforation of each rate well (contiguous: a rate well's
+  // perforations follow each other in the perforation order)
+  std::vector<int> wrange(2 * (nw + 1), 0);
+  for (long long k = 0; k < np; ++k) {
+    if (hw.wloc[k] < 0) continue;
+    const long long gw = b.h[hw.inst[k]].w_off + hw.wloc[k];
+    if (wrange[2 * gw + 1] == 0) wrange[2 * gw] = (int)k;
+    wrange[2 * gw + 1] = (int)k + 1;
+  }
+  std::vector<int> pcell(hw.cell.begin(), hw.cell.end()), pw(hw.wloc.begin(), hw.wloc.end());
+  FAMS_TRY(b.alloc((void**)&b.perf_row, sizeof(int) * (np + 1)));
+  FAMS_TRY(b.alloc((void**)&b.perf_wrow, sizeof(int) * (np + 1)));
+  FAMS_TRY(b.alloc((void**)&b.perf_beta, sizeof(double) * (np + 1)));
+  FAMS_TRY(b.alloc((void**)&b.perf_bhp, sizeof(double) * (np + 1)));
+  FAMS_TRY(b.alloc((void**)&b.mperf_ptr, sizeof(int) * (b.tot_m + 1)));
+  FAMS_TRY(b.alloc((void**)&b.mperf_idx, sizeof(int) * (np + 1)));
+  FAMS_TRY(b.alloc((void**)&b.wperf_range, sizeof(int) * 2 * (nw + 1)));
+  FAMS_TRY(b.alloc((void**)&b.w_rate, sizeof(double) * (nw + 1)));
+  // staged on the device in the rows' and beta's places; k_perf_rows
+  // turns them into global rows and PI k
+  FAMS_CUDA(cudaMemcpyAsync(b.perf_row, pcell.data(), sizeof(int) * np, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.perf_wrow, pw.data(), sizeof(int) * np, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.perf_beta, hw.pi.data(), sizeof(double) * np, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.perf_bhp, hw.bhp.data(), sizeof(double) * np, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.mperf_ptr, mptr.data(), sizeof(int) * (b.tot_m + 1), cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.mperf_idx, midx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.wperf_range, wrange.data(), sizeof(int) * 2 * (nw + 1),
+                            cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaMemcpyAsync(b.w_rate, hw.rate.data(), sizeof(double) * nw, cudaMemcpyHostToDevice, b.stream));
+  FAMS_CUDA(cudaStreamSynchronize(b.stream));   // host vectors go out of scope
+  return FAMS_OK;
+}
+
 int setup_batch(int n, const fams_grid* grids, const double* const* perms, const fams_fracs* fracs,
-                const fams_opts* opts, Batch& b) {
+                const fams_wells* wells, const fams_opts* opts, Batch& b) {
+  HostWells hw;
+  FAMS_TRY(read_wells(n, grids, wells, hw));
   b.B = n;
   FAMS_CUDA(cudaGetDevice(&b.device));
   FAMS_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
@@ -164,9 +294,14 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.krylov = o.krylov; I.restart = o.krylov == FAMS_KRYLOV_GMRES ? o.restart : 0;
     I.merge_cap = o.basis == FAMS_COUPLED ? o.merge_cap : 0;
     I.grid_solve = o.grid_solve;
+    I.subblock = o.subblock;
     b.prepare_flux = b.prepare_flux || o.prepare_flux == 1;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;
+    I.nw = hw.nw[i];
+    I.w_off = i ? b.h[i - 1].w_off + b.h[i - 1].nw : 0;
+    I.nperf = hw.nperf[i];
+    I.perf_off = i ? b.h[i - 1].perf_off + b.h[i - 1].nperf : 0;
     I.nfr = nf;
     I.fr_off = (int)fr;
     m += I.nm;
@@ -226,6 +361,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
         return FAMS_EINVAL;
       }
   }
+  FAMS_TRY(upload_wells(b, hw));
   FAMS_TRY(b.upload_inst());
   // wall time of each setup phase (every phase ends synchronised with the
   // device): geometry, system, coarse grids, basis, coarse operator, ILU(0)
@@ -316,7 +452,7 @@ int flux_some(Batch& b, const std::vector<int>& want, const double* const* x,
     }
   if (!b.fx) {
     long long nf = 0, nn = 0;
-    for (auto& I : b.h) nf += faces_host(I), nn += (long long)I.nnc + I.nff;
+    for (auto& I : b.h) nf += faces_host(I), nn += (long long)I.nnc + I.nff + I.nperf;
     FAMS_TRY(b.alloc((void**)&b.fx, sizeof(double) * (b.tot_row + 1)));
     FAMS_TRY(b.alloc((void**)&b.fface, sizeof(double) * (nf + 1)));
     FAMS_TRY(b.alloc((void**)&b.fnnc, sizeof(double) * (nn + 1)));
@@ -345,7 +481,7 @@ int flux_some(Batch& b, const std::vector<int>& want, const double* const* x,
   for (size_t k = 0; k < list.size(); ++k) {
     const Inst& I = b.h[list[k]];
     foff[k + 1] = foff[k] + faces_host(I);
-    noff[k + 1] = noff[k] + I.nnc + I.nff;
+    noff[k + 1] = noff[k] + I.nnc + I.nff + I.nperf;
     FAMS_CUDA(cudaMemcpyAsync(b.fx + I.row_off, x[slot[k]], sizeof(double) * I.n,
                               cudaMemcpyDefault, b.stream));
   }
@@ -373,6 +509,12 @@ extern "C" {
 
 int fams_setup_batch(int n, const fams_grid* grids, const double* const* perms,
                      const fams_fracs* fracs, const fams_opts* opts, fams_ctx** out) {
+  return fams_setup_batch_wells(n, grids, perms, fracs, nullptr, opts, out);
+}
+
+int fams_setup_batch_wells(int n, const fams_grid* grids, const double* const* perms,
+                           const fams_fracs* fracs, const fams_wells* wells,
+                           const fams_opts* opts, fams_ctx** out) {
   if (!out || n < 1 || !grids || !perms || !opts) {
     set_error("null argument or n < 1");
     return FAMS_EINVAL;
@@ -383,7 +525,7 @@ int fams_setup_batch(int n, const fams_grid* grids, const double* const* perms,
     if (!perms[i]) { set_error("perm is null"); return FAMS_EINVAL; }
   }
   fams_ctx* c = new fams_ctx();
-  int s = setup_batch(n, grids, perms, fracs, opts, c->b);
+  int s = setup_batch(n, grids, perms, fracs, wells, opts, c->b);
   if (s != FAMS_OK) {
     destroy_batch(c->b);
     delete c;
@@ -403,6 +545,23 @@ int fams_setup(const fams_grid* grid, const double* perm, const fams_fracs* frac
   return fams_setup_batch(1, grid, perms, fracs, opts, out);
 }
 
+int fams_setup_wells(const fams_grid* grid, const double* perm, const fams_fracs* fracs,
+                     const fams_wells* wells, const fams_opts* opts, fams_ctx** out) {
+  if (!grid || !perm || !opts) {
+    set_error("null argument");
+    return FAMS_EINVAL;
+  }
+  const double* perms[1] = {perm};
+  return fams_setup_batch_wells(1, grid, perms, fracs, wells, opts, out);
+}
+
+int fams_sizes_wells(const fams_ctx* ctx, int inst, int* n_well, int* n_perf) {
+  if (!ctx || inst < 0 || inst >= ctx->b.B) { set_error("bad context or instance"); return FAMS_EINVAL; }
+  if (n_well) *n_well = ctx->b.h[inst].nw;
+  if (n_perf) *n_perf = ctx->b.h[inst].nperf;
+  return FAMS_OK;
+}
+
 int fams_num_instances(const fams_ctx* ctx) { return ctx ? ctx->b.B : 0; }
 
 int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n_coarse,
@@ -415,7 +574,7 @@ int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n
   if (n_coarse) *n_coarse = I.nc;
   if (n_faces)
     *n_faces = (I.nx + 1) * I.ny * nz + I.nx * (I.ny + 1) * nz + (I.dim == 3 ? I.nx * I.ny * (nz + 1) : 0);
-  if (n_nnc) *n_nnc = I.nnc + I.nff;
+  if (n_nnc) *n_nnc = I.nnc + I.nff + I.nperf;
   return FAMS_OK;
 }
 

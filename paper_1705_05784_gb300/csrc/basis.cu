@@ -55,6 +55,8 @@ __device__ inline int stage_of(int variant, int med, int rank) {
 // cross), so no link between two networks is kept: each network's basis
 // functions are built on that network alone.
 __device__ inline bool keep_link(int variant, int mr, int rr, int mc, int rc, int cross) {
+  if (mc == 2) return true;    // a well's value is known (P^ww = I): Eq. 18's beta term
+  if (mr == 2) return false;   // well rows are coarse nodes
   if (cross == 2 && mr == 1 && mc == 1) return false;
   if (cross && mr == 1 && mc == 1 && rr == RANK_F && rc == RANK_F) return false;
   switch (variant) {
@@ -87,7 +89,7 @@ __global__ void k_row_plate(const Inst* inst, int B, const int* off_row, long lo
   if (r >= nrow) return;
   const Inst& I = inst[find_segment(off_row, B + 1, r)];
   long long loc = r - I.row_off;
-  if (loc < I.nm) {
+  if (loc < I.nm || loc >= I.nm + I.nf) {   // matrix and well rows
     plate[r] = -1;
     plate[nrow + r] = -1;
     return;
@@ -109,7 +111,11 @@ __device__ inline const Inst& inst_of(const Inst* inst, int B, const int* off_ro
   return inst[find_segment(off_row, B + 1, r)];
 }
 
-__device__ inline int medium_of(const Inst& I, int r) { return (r - I.row_off) < I.nm ? 0 : 1; }
+// 0 matrix, 1 fracture, 2 well
+__device__ inline int medium_of(const Inst& I, int r) {
+  const int loc = r - I.row_off;
+  return loc < I.nm ? 0 : (loc < I.nm + I.nf ? 1 : 2);
+}
 
 // P staging: each known row points into the pool of the stage that built it
 struct Pool {

@@ -71,6 +71,16 @@ struct Batch {
   long long tot_m = 0, tot_fr = 0, tot_fc = 0, tot_s = 0, tot_row = 0, tot_pair = 0,
             tot_nnc = 0, tot_ff = 0, tot_nc = 0, tot_net = 0, tot_nnz = 0, tot_pnnz = 0;
 
+  // ---- wells (none: all null, tot_perf = 0) ----
+  long long tot_w = 0, tot_perf = 0;   // rate-controlled wells, perforations
+  int* perf_row = nullptr;     // per perforation: global row of the perforated matrix cell
+  int* perf_wrow = nullptr;    // ... global row of its rate well, -1 for a pressure well
+  double* perf_beta = nullptr; // ... PI k of the cell
+  double* perf_bhp = nullptr;  // ... bottom-hole pressure (pressure wells)
+  int* mperf_ptr = nullptr;    // per global matrix cell: its perforations (tot_m + 1)
+  int* mperf_idx = nullptr;
+  int* wperf_range = nullptr;  // per rate well: [first, end) of its perforations
+  double* w_rate = nullptr;    // per rate well: total injection rate
   // ---- inputs ----
   double* perm = nullptr;      // tot_m
   double* fracs = nullptr;     // 6 per input fracture
@@ -167,6 +177,12 @@ struct Batch {
   double* pk_uv = nullptr;
   double* pk_ud = nullptr;     // reciprocal of the U diagonal
   double* ylev = nullptr;      // sweep right-hand side in level order
+  // the sub-block smoothing stage (instances with fams_opts.subblock): ILU(0)
+  // of A without its cross-medium entries, in A's pattern and level order
+  double* ilu_b = nullptr;
+  double* pk_lv_b = nullptr;
+  double* pk_uv_b = nullptr;
+  double* pk_ud_b = nullptr;
   // ---- iteration work vectors ----
   double* q = nullptr;
   double* x = nullptr;
@@ -294,7 +310,7 @@ constexpr long long GRID_SOLVE_ROWS = 1LL << 18;
 bool whole_gpu(const Batch& b);       // single instance, large or asked for: every SM
 bool solve_on_grid(const Batch& b);   // ... and its iteration is FP64 GMRES
 int run_solve_grid(Batch& b, double tol, float* ms);
-int ilu_factor_grid(Batch& b);        // ILU(0) factorisation on every SM
+int ilu_factor_grid(Batch& b, double* F);   // ILU(0) factorisation (values in F) on every SM
 int band_lu_grid(Batch& b, CoarseSys& cs, CoarseHost& ch);   // coarse band LU on every SM
 // flux.cu
 int flux_prepare(Batch& b, const CoarseHost** ch);

@@ -324,6 +324,22 @@ __global__ void k_frac_nodes(const Inst* inst, int B, const int* off_fr, const i
   }
 }
 
+// rate-controlled wells: one coarse node each after the fracture nodes
+// (Sec. 3: a well's DOF maps to the coarse scale by the identity), rank V,
+// its own primal block
+__global__ void k_well_coarse(const Inst* inst, int B, const int* off_row, long long nrow,
+                              int* rank, int* primal, int* node_cell) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  const int k = (int)(r - I.row_off) - I.nm - I.nf;
+  if (k < 0) return;
+  const int c = I.nc - I.nw + k;
+  rank[r] = RANK_V;
+  primal[r] = c;
+  node_cell[I.nc_off + c] = (int)r;
+}
+
 __global__ void k_primal_global(const Inst* inst, int B, const int* off_row, long long nrow,
                                 const int* primal, int* gprimal, int* iota) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,9 +511,9 @@ int phase_coarse(Batch& b) {
       }
       base += h_nv[n] * nvb;
     }
-    I.nc = base;
+    I.nc = base + I.nw;
     I.nc_off = (int)nc_tot;
-    nc_tot += base;
+    nc_tot += I.nc;
   }
   b.tot_nc = nc_tot;
   if (nnet > 0)
@@ -517,6 +533,9 @@ int phase_coarse(Batch& b) {
                                                   b.f_ns, b.f_k0, nfr, nnet, netoff, ninst,
                                                   b.net_nv, b.net_k0, b.net_nk, b.net_base, vlist,
                                                   b.node_cell);
+  if (b.tot_w > 0)
+    fams::note_launch(), k_well_coarse<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow,
+                                                                         b.rank, b.primal, b.node_cell);
   FAMS_CUDA(cudaGetLastError());
   // cells of each primal block (rows of R^FV), sorted
   int *gprim = nullptr, *iota = nullptr;

@@ -47,6 +47,7 @@ struct Inst {
   int krylov, restart;  // outer iteration; GMRES cycle length
   int merge_cap;        // Coupled: largest block merged across the media (0: none)
   int grid_solve;       // single instance on every SM: 0 auto, 1 always, -1 never
+  int subblock;         // 1: the sub-block smoothing stage after ILU(0)
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells
@@ -54,6 +55,8 @@ struct Inst {
   int nf, fc_off;     // fracture cells
   int ns, s_off;      // strike (x-y projection) cells
   int n, row_off;     // unknowns
+  int nw, w_off;      // rate-controlled wells (unknowns after the fracture cells)
+  int nperf, perf_off;  // well perforations (rate wells first, then pressure wells)
   int nnc, nnc_off;   // matrix-fracture connections
   int nff, ff_off;    // fracture-fracture connections
   int ninter, inter_off;  // fracture pairs examined for intersections

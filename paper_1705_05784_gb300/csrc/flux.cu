@@ -281,12 +281,25 @@ __global__ void k_flux_faces(const Inst* inst, const int* list, int nlist, const
   face[g] = out;
 }
 
+// perforations of the wells, for the flux output: global rows of the cell
+// and of its rate well (-1: pressure well), beta = PI k, bottom-hole pressure
+struct PerfArgs {
+  const int* row;
+  const int* wrow;
+  const double* beta;
+  const double* bhp;
+  const double* mob;   // nullable: mobility scales of a time-step update
+};
+
 // steps 2 and 4 on the fracture connections: matrix-fracture (positive
-// matrix -> fracture), then fracture-fracture (positive lower -> higher cell)
+// matrix -> fracture), then fracture-fracture (positive lower -> higher
+// cell), then the well perforations (positive cell -> well: a rate well
+// is its own primal block, so T (p'_cell - p'_well); a pressure well like a
+// Dirichlet face, from the local solution)
 __global__ void k_flux_nnc(const Inst* inst, const int* list, int nlist, const long long* noff,
                            long long ntot, const int* nrow_m, const int* nrow_f, const double* nT,
-                           const int* ffa, const int* ffb, const double* ffT, const int* primal,
-                           const double* pp, const double* pt, double* out) {
+                           const int* ffa, const int* ffb, const double* ffT, PerfArgs pf,
+                           const int* primal, const double* pp, const double* pt, double* out) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ntot) return;
   int li = 0, hi = nlist - 1;
@@ -299,11 +312,22 @@ __global__ void k_flux_nnc(const Inst* inst, const int* list, int nlist, const l
   if (t < I.nnc) {
     long long k = I.nnc_off + t;
     out[g] = nT[k] * (pp[nrow_m[k]] - pp[nrow_f[k]]);
-  } else {
+  } else if (t < I.nnc + I.nff) {
     long long k = I.ff_off + (t - I.nnc);
     int a = ffa[k], b = ffb[k];
     const double* p = primal[a] == primal[b] ? pt : pp;
     out[g] = ffT[k] * (p[a] - p[b]);
+  } else {
+    const long long k = I.perf_off + (t - I.nnc - I.nff);
+    const int c = pf.row[k], w = pf.wrow[k];
+    double T = pf.beta[k];
+    if (w >= 0) {
+      if (pf.mob) T *= 2.0 * pf.mob[c] * pf.mob[w] / (pf.mob[c] + pf.mob[w]);
+      out[g] = T * (pp[c] - pp[w]);
+    } else {
+      if (pf.mob) T *= pf.mob[c];
+      out[g] = T * (pt[c] - pf.bhp[k]);
+    }
   }
 }
 
@@ -502,7 +526,8 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   if (noff[nl] > 0)
     fams::note_launch(), k_flux_nnc<<<grid_for(noff[nl], 256), 256, 0, st>>>(
         b.d_inst, dlist, nl, dno, noff[nl], b.nnc_row_m, b.nnc_row_f, b.nnc_T, b.ff_a, b.ff_b,
-        b.ff_T, b.primal, pp, pt, nnc);
+        b.ff_T, PerfArgs{b.perf_row, b.perf_wrow, b.perf_beta, b.perf_bhp, b.mob}, b.primal, pp,
+        pt, nnc);
   FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaStreamSynchronize(st));
   b.free_tmp();

@@ -485,11 +485,11 @@ int phase_geometry(Batch& b) {
                             cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemcpyAsync(b.f_sfirst, sfirst.data(), sizeof(int) * (nfr + 1),
                             cudaMemcpyHostToDevice, st));
-  // rows: matrix then fracture cells per instance
+  // rows: matrix cells, fracture cells, then rate-controlled wells per instance
   long long row = 0, pairs = 0;
   for (int i = 0; i < b.B; ++i) {
     Inst& I = b.h[i];
-    I.n = I.nm + I.nf;
+    I.n = I.nm + I.nf + I.nw;
     I.row_off = (int)row;
     row += I.n;
     I.inter_off = (int)pairs;

@@ -120,6 +120,21 @@ __global__ void k_ilu_factor(const Inst* inst, int B, const int* rowptr, const i
   if (threadIdx.x == 0 && bad) atomicCAS(err, 0, DERR_BREAKDOWN);
 }
 
+// A without its cross-medium entries (matrix, fracture and well blocks), in
+// A's pattern: the sub-block smoothing stage's matrix
+__global__ void k_block_vals(const Inst* inst, int B, const int* off_row, long long nrow,
+                             const int* rowptr, const int* col, const double* val, double* out) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  const Inst& I = inst[find_segment(off_row, B + 1, r)];
+  auto med = [&](long long g) {
+    const long long loc = g - I.row_off;
+    return loc < I.nm ? 0 : (loc < I.nm + I.nf ? 1 : 2);
+  };
+  const int mr = med(r);
+  for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) out[p] = med(col[p]) == mr ? val[p] : 0.0;
+}
+
 __global__ void k_pos(long long nrow, const int* rows, int* pos) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nrow) pos[rows[t]] = (int)t;
@@ -149,6 +164,41 @@ __global__ void k_pack(long long nrow, const int* rows, const int* rowptr, const
 }
 
 }  // namespace
+
+// the factors of the sub-block stage (when an instance asks for it): A's
+// values without the cross-medium entries, factored on A's levels, packed
+// beside the main factors
+static int block_factors(Batch& b, bool alloc) {
+  const int T = 256;
+  cudaStream_t st = b.stream;
+  const long long nrow = b.tot_row, n1 = nrow + 1;
+  bool any = false;
+  for (auto& I : b.h) any = any || I.subblock;
+  if (!any) return FAMS_OK;
+  if (alloc) {
+    FAMS_TRY(b.alloc((void**)&b.ilu_b, sizeof(double) * (b.tot_nnz + 1)));
+    FAMS_TRY(b.alloc((void**)&b.pk_lv_b, sizeof(double) * PK * n1));
+    FAMS_TRY(b.alloc((void**)&b.pk_uv_b, sizeof(double) * PK * n1));
+    FAMS_TRY(b.alloc((void**)&b.pk_ud_b, sizeof(double) * n1));
+  }
+  if (nrow == 0) return FAMS_OK;
+  fams::note_launch(), k_block_vals<<<grid_for(nrow, T), T, 0, st>>>(
+      b.d_inst, b.B, b.off_row, nrow, b.rowptr, b.col, b.val, b.ilu_b);
+  if (whole_gpu(b)) {
+    FAMS_TRY(ilu_factor_grid(b, b.ilu_b));
+  } else {
+    fams::note_launch(), k_ilu_factor<<<b.B, 512, 0, st>>>(b.d_inst, b.B, b.rowptr, b.col, b.diag,
+                                                            b.lev_off, b.lev_ptr, b.lev_rows,
+                                                            b.ilu_b, b.d_err);
+  }
+  FAMS_CUDA(cudaGetLastError());
+  FAMS_TRY(b.check_err("ILU(0) of the media blocks"));
+  fams::note_launch(), k_pack<<<grid_for(nrow, T), T, 0, st>>>(
+      nrow, b.lev_rows, b.rowptr, b.col, b.diag, b.ilu_b, b.pk_pos, b.pk_nl, b.pk_lp, b.pk_lc,
+      b.pk_lv_b, b.pk_nu, b.pk_uc, b.pk_uv_b, b.pk_ud_b);
+  FAMS_CUDA(cudaGetLastError());
+  return FAMS_OK;
+}
 
 int phase_ilu(Batch& b) {
   const int T = 256;
@@ -188,7 +238,7 @@ int phase_ilu(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.ilu, sizeof(double) * (b.tot_nnz + 1)));
   FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
   if (whole_gpu(b)) {
-    FAMS_TRY(ilu_factor_grid(b));
+    FAMS_TRY(ilu_factor_grid(b, b.ilu));
   } else {
     fams::note_launch(), k_ilu_factor<<<B, 512, 0, st>>>(b.d_inst, B, b.rowptr, b.col, b.diag,
                                                           b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
@@ -214,7 +264,7 @@ int phase_ilu(Batch& b) {
         b.pk_lv, b.pk_nu, b.pk_uc, b.pk_uv, b.pk_ud);
   }
   FAMS_CUDA(cudaGetLastError());
-  return FAMS_OK;
+  return block_factors(b, true);
 }
 
 // new values, same pattern and levels (a time-step update)
@@ -224,7 +274,7 @@ int ilu_refactor(Batch& b) {
   long long nrow = b.tot_row;
   FAMS_CUDA(cudaMemcpyAsync(b.ilu, b.val, sizeof(double) * b.tot_nnz, cudaMemcpyDeviceToDevice, st));
   if (whole_gpu(b)) {
-    FAMS_TRY(ilu_factor_grid(b));
+    FAMS_TRY(ilu_factor_grid(b, b.ilu));
   } else {
     fams::note_launch(), k_ilu_factor<<<b.B, 512, 0, st>>>(b.d_inst, b.B, b.rowptr, b.col, b.diag,
                                                             b.lev_off, b.lev_ptr, b.lev_rows, b.ilu,
@@ -237,7 +287,7 @@ int ilu_refactor(Batch& b) {
         nrow, b.lev_rows, b.rowptr, b.col, b.diag, b.ilu, b.pk_pos, b.pk_nl, b.pk_lp, b.pk_lc,
         b.pk_lv, b.pk_nu, b.pk_uc, b.pk_uv, b.pk_ud);
   FAMS_CUDA(cudaGetLastError());
-  return FAMS_OK;
+  return block_factors(b, false);
 }
 
 }  // namespace fams

@@ -97,6 +97,12 @@ struct SolveArgs {
   const int* pk_uc;
   const double* pk_uv;
   const double* pk_ud;
+  // the sub-block smoothing stage: ILU(0) of A without its cross-medium
+  // entries, in the pattern of A and in level order (null: no instance has it)
+  const double* Fb;
+  const double* pk_lvb;
+  const double* pk_uvb;
+  const double* pk_udb;
   double* ylev;
   long long ntot;  // rows of the batch (stride of the PK arrays)
   double tol;
@@ -122,10 +128,10 @@ template <> struct Prec<double> {
   static __device__ const double* val(const SolveArgs& a) { return a.val; }
   static __device__ const double* pv(const SolveArgs& a) { return a.p_val; }
   static __device__ const double* ptv(const SolveArgs& a) { return a.pt_val; }
-  static __device__ const double* F(const SolveArgs& a) { return a.F; }
-  static __device__ const double* lv(const SolveArgs& a) { return a.pk_lv; }
-  static __device__ const double* uv(const SolveArgs& a) { return a.pk_uv; }
-  static __device__ const double* ud(const SolveArgs& a) { return a.pk_ud; }
+  static __device__ const double* F(const SolveArgs& a, int set = 0) { return set ? a.Fb : a.F; }
+  static __device__ const double* lv(const SolveArgs& a, int set = 0) { return set ? a.pk_lvb : a.pk_lv; }
+  static __device__ const double* uv(const SolveArgs& a, int set = 0) { return set ? a.pk_uvb : a.pk_uv; }
+  static __device__ const double* ud(const SolveArgs& a, int set = 0) { return set ? a.pk_udb : a.pk_ud; }
   static __device__ double* y(const SolveArgs& a) { return a.y; }
   static __device__ double* ylev(const SolveArgs& a) { return a.ylev; }
   static __device__ double* dp(const SolveArgs& a) { return a.dp; }
@@ -135,10 +141,11 @@ template <> struct Prec<float> {
   static __device__ const float* val(const SolveArgs& a) { return a.val32; }
   static __device__ const float* pv(const SolveArgs& a) { return a.p_val32; }
   static __device__ const float* ptv(const SolveArgs& a) { return a.pt_val32; }
-  static __device__ const float* F(const SolveArgs& a) { return a.F32; }
-  static __device__ const float* lv(const SolveArgs& a) { return a.pk_lv32; }
-  static __device__ const float* uv(const SolveArgs& a) { return a.pk_uv32; }
-  static __device__ const float* ud(const SolveArgs& a) { return a.pk_ud32; }
+  // (the sub-block stage runs in FP64 only: set 1 is never asked for here)
+  static __device__ const float* F(const SolveArgs& a, int = 0) { return a.F32; }
+  static __device__ const float* lv(const SolveArgs& a, int = 0) { return a.pk_lv32; }
+  static __device__ const float* uv(const SolveArgs& a, int = 0) { return a.pk_uv32; }
+  static __device__ const float* ud(const SolveArgs& a, int = 0) { return a.pk_ud32; }
   static __device__ float* y(const SolveArgs& a) { return a.yf; }
   static __device__ float* ylev(const SolveArgs& a) { return a.ylevf; }
   static __device__ float* dp(const SolveArgs& a) { return a.dpf; }
@@ -362,7 +369,7 @@ struct SweepRow {
 template <class T>
 __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int nlev, bool lower,
                                   SweepRow<T>& s, const T* dpv = nullptr,
-                                  const T* bv = nullptr) {
+                                  const T* bv = nullptr, int set = 0) {
   s.t = -1;
   if (l < 0 || l >= nlev) return;
   int t = lp[l] + threadIdx.x;
@@ -376,12 +383,12 @@ __device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int 
     s.diag = T(1);
   } else {
     s.cnt = a.pk_nu[t];
-    s.diag = Prec<T>::ud(a)[t];
-    s.dpo = dpv[s.i];
+    s.diag = Prec<T>::ud(a, set)[t];
+    s.dpo = dpv ? dpv[s.i] : T(0);
     s.xo = bv ? bv[s.i] : T(0);
   }
   const int* pc = lower ? a.pk_lc : a.pk_uc;
-  const T* pv = lower ? Prec<T>::lv(a) : Prec<T>::uv(a);
+  const T* pv = lower ? Prec<T>::lv(a, set) : Prec<T>::uv(a, set);
 #pragma unroll
   for (int k = 0; k < PK; ++k) {
     s.c[k] = pc[(long long)k * a.ntot + t];
@@ -434,7 +441,6 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   const int NT = blockDim.x;
   const T* ptv = Prec<T>::ptv(a);
   const T* pv = Prec<T>::pv(a);
-  const T* F = Prec<T>::F(a);
   T* y = Prec<T>::y(a);
   T* ylev = Prec<T>::ylev(a);
   stamp(cyc);
@@ -495,69 +501,84 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   // recent level is read there, older ones from ylev.  The current level
   // writes positions [lp[l], lp[l+1]), so a position tc is still in the ring
   // while tc >= lp[l+1] - SWEEP_RING.
+  // Pass 1 (instances with the sub-block smoothing stage): the same sweeps
+  // with the media blocks' factors on r2 = r - A (dp1 + dp2), added to out.
   T* ring = reinterpret_cast<T*>(S.buf);
-  SweepRow<T> cur, nxt;
-  sweep_load<T>(a, lp, 0, nlev, true, cur);
-  for (int l = 0; l < nlev; ++l) {
-    sweep_load<T>(a, lp, l + 1, nlev, true, nxt);
-    const int lim = lp[l + 1] - SWEEP_RING;
-    auto yv = [&](int tc) { return tc >= lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
-    if (cur.t >= 0) {
-      T s = cur.base;
-#pragma unroll
-      for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
-      for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
-      ring[cur.t & (SWEEP_RING - 1)] = s;
-      ylev[cur.t] = s;
+  const int npass = I.subblock ? 2 : 1;
+  for (int pass = 0; pass < npass; ++pass) {
+    if (pass == 1) {
+      for (int i = ro + threadIdx.x; i < ro + n; i += NT) dp[i] += y[i];
+      __syncthreads();
+      rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
+      __syncthreads();
     }
-    for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
-      int i = a.lev_rows[t];
-      T s = ylev[t];
-      for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
-      ring[t & (SWEEP_RING - 1)] = s;
-      ylev[t] = s;
-    }
-    __syncthreads();
-    cur = nxt;
-  }
-  mark(cyc, 4);
-  // U sweep and step 8: out = (base + dp1) + dp2; the ring now holds the
-  // upper neighbours, valid while tc < lp[l] + SWEEP_RING
-  sweep_load<T>(a, lp, nlev - 1, nlev, false, cur, dp, base);
-  for (int l = nlev - 1; l >= 0; --l) {
-    sweep_load<T>(a, lp, l - 1, nlev, false, nxt, dp, base);
-    const int lim = lp[l] + SWEEP_RING;
-    auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
-    if (cur.t >= 0) {
-      T s = cur.base;
-      const T xo = cur.xo, dpo = cur.dpo;
+    const T* Fs = Prec<T>::F(a, pass);
+    const T* uds = Prec<T>::ud(a, pass);
+    SweepRow<T> cur, nxt;
+    sweep_load<T>(a, lp, 0, nlev, true, cur, nullptr, nullptr, pass);
+    for (int l = 0; l < nlev; ++l) {
+      sweep_load<T>(a, lp, l + 1, nlev, true, nxt, nullptr, nullptr, pass);
+      const int lim = lp[l + 1] - SWEEP_RING;
+      auto yv = [&](int tc) { return tc >= lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
+      if (cur.t >= 0) {
+        T s = cur.base;
 #pragma unroll
-      for (int k = 0; k < PK; ++k)
-        if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
-      if (cur.cnt > PK) {
-        int d = a.diag[cur.i];
-        for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
+        for (int k = 0; k < PK; ++k)
+          if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
+        for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+        ring[cur.t & (SWEEP_RING - 1)] = s;
+        ylev[cur.t] = s;
       }
-      T xi = s * cur.diag;   // reciprocal of U's diagonal
-      ring[cur.t & (SWEEP_RING - 1)] = xi;
-      ylev[cur.t] = xi;
-      y[cur.i] = xi;
-      out[cur.i] = (xo + dpo) + xi;
+      for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
+        int i = a.lev_rows[t];
+        T s = ylev[t];
+        for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+        ring[t & (SWEEP_RING - 1)] = s;
+        ylev[t] = s;
+      }
+      __syncthreads();
+      cur = nxt;
     }
-    for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
-      int i = a.lev_rows[t];
-      int d = a.diag[i];
-      T s = ylev[t];
-      for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= F[p] * yv(a.pk_pos[a.col[p]]);
-      T xi = s * Prec<T>::ud(a)[t];
-      ring[t & (SWEEP_RING - 1)] = xi;
-      ylev[t] = xi;
-      y[i] = xi;
-      out[i] = ((base ? base[i] : T(0)) + dp[i]) + xi;
+    mark(cyc, 4);
+    // U sweep and step 8: out = (base + dp1) + dp2 (pass 1: out += dp3); the
+    // ring now holds the upper neighbours, valid while tc < lp[l] + SWEEP_RING
+    const T* bsrc = pass ? out : base;
+    const T* dsrc = pass ? nullptr : dp;
+    sweep_load<T>(a, lp, nlev - 1, nlev, false, cur, dsrc, bsrc, pass);
+    for (int l = nlev - 1; l >= 0; --l) {
+      sweep_load<T>(a, lp, l - 1, nlev, false, nxt, dsrc, bsrc, pass);
+      const int lim = lp[l] + SWEEP_RING;
+      auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
+      if (cur.t >= 0) {
+        T s = cur.base;
+        const T xo = cur.xo, dpo = cur.dpo;
+#pragma unroll
+        for (int k = 0; k < PK; ++k)
+          if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
+        if (cur.cnt > PK) {
+          int d = a.diag[cur.i];
+          for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+        }
+        T xi = s * cur.diag;   // reciprocal of U's diagonal
+        ring[cur.t & (SWEEP_RING - 1)] = xi;
+        ylev[cur.t] = xi;
+        y[cur.i] = xi;
+        out[cur.i] = (xo + dpo) + xi;
+      }
+      for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
+        int i = a.lev_rows[t];
+        int d = a.diag[i];
+        T s = ylev[t];
+        for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+        T xi = s * uds[t];
+        ring[t & (SWEEP_RING - 1)] = xi;
+        ylev[t] = xi;
+        y[i] = xi;
+        out[i] = ((bsrc ? bsrc[i] : T(0)) + (dsrc ? dsrc[i] : T(0))) + xi;
+      }
+      __syncthreads();
+      cur = nxt;
     }
-    __syncthreads();
-    cur = nxt;
   }
   mark(cyc, 5);
 }
@@ -1060,6 +1081,7 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.crhs = b.rc; a.csol = b.ec;
   a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
   a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
+  a.Fb = b.ilu_b; a.pk_lvb = b.pk_lv_b; a.pk_uvb = b.pk_uv_b; a.pk_udb = b.pk_ud_b;
   a.ylev = b.ylev;
   a.ntot = b.tot_row;
   a.tol = tol;
@@ -1197,6 +1219,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
   a.hist = stat + STATIC_STAT; a.hist_len = STATIC_HIST;
   a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
   a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
+  a.Fb = b.ilu_b; a.pk_lvb = b.pk_lv_b; a.pk_uvb = b.pk_uv_b; a.pk_udb = b.pk_ud_b;
   a.ntot = b.tot_row;
   a.tol = tol;
 

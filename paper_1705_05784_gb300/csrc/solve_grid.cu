@@ -71,6 +71,11 @@ struct GArgs {
   const int* pk_uc;
   const double* pk_uv;
   const double* pk_ud;
+  const double* Fb;      // the sub-block stage's factors (subblock: 1), same layout
+  const double* pk_lvb;
+  const double* pk_uvb;
+  const double* pk_udb;
+  int subblock;
   long long ntot;        // stride of the PK arrays
   const double* ainv;    // A_c^-1, nc x nc, row-major, coarse order
   const double* q;
@@ -217,6 +222,24 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
   // in 3D wavefronts; fewer parties make each barrier cheaper); each thread
   // loads its row of the next level before the barrier.  The other CTAs wait
   // at the grid barrier after the sweeps.
+  for (int pass = 0; pass < (a.subblock ? 2 : 1); ++pass) {
+  // pass 1, the sub-block smoothing stage: r2 = r - A (dp1 + dp2), swept
+  // with the media blocks' factors and added to out
+  if (pass == 1) {
+    for (long long i = t0; i < a.n; i += T) a.dp[i] = ldv(a.dp + i) + ldv(a.y + i);
+    if (!grid_sync(a.bar)) return false;
+    for (long long i = t0; i < a.n; i += T) {
+      double s = ldv(r + i);
+      for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) s -= a.val[p] * ldv(a.dp + a.col[p]);
+      a.y[i] = s;
+      a.ylev[a.pk_pos[i]] = s;
+    }
+    if (!grid_sync(a.bar)) return false;
+  }
+  const double* Fs = pass ? a.Fb : a.F;
+  const double* lvs = pass ? a.pk_lvb : a.pk_lv;
+  const double* uvs = pass ? a.pk_uvb : a.pk_uv;
+  const double* uds = pass ? a.pk_udb : a.pk_ud;
   if ((int)blockIdx.x < a.sweep_ctas) {
     const long long nt = a.ntot;
     const long long ST = (long long)a.sweep_ctas * blockDim.x;
@@ -235,7 +258,7 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
 #pragma unroll
         for (int k = 0; k < PK; ++k) {
           c[k] = a.pk_lc[k * nt + t];
-          f[k] = a.pk_lv[k * nt + t];
+          f[k] = lvs[k * nt + t];
         }
       }
     };
@@ -247,13 +270,13 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
 #pragma unroll
         for (int k = 0; k < PK; ++k)
           if (k < cnt) s -= f[k] * ldv(a.ylev + c[k]);
-        for (int p = p0 + PK; p < p0 + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+        for (int p = p0 + PK; p < p0 + cnt; ++p) s -= Fs[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
         a.ylev[t] = s;
         for (long long u = t + ST; u < te; u += ST) {   // rows beyond one per thread
           double s2 = ldv(a.ylev + u);
           const int c2 = a.pk_nl[u], q0 = a.pk_lp[u];
-          for (int k = 0; k < PK && k < c2; ++k) s2 -= a.pk_lv[k * nt + u] * ldv(a.ylev + a.pk_lc[k * nt + u]);
-          for (int p = q0 + PK; p < q0 + c2; ++p) s2 -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+          for (int k = 0; k < PK && k < c2; ++k) s2 -= lvs[k * nt + u] * ldv(a.ylev + a.pk_lc[k * nt + u]);
+          for (int p = q0 + PK; p < q0 + c2; ++p) s2 -= Fs[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
           a.ylev[u] = s2;
         }
       }
@@ -269,13 +292,13 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
         row = a.lev_rows[t];
         yb = ldv(a.ylev + t);
         cnt = a.pk_nu[t];
-        ud = a.pk_ud[t];
-        dpo = ldv(a.dp + row);
-        xo = base ? ldv(base + row) : 0.0;
+        ud = uds[t];
+        dpo = pass ? 0.0 : ldv(a.dp + row);
+        xo = pass ? ldv(out + row) : (base ? ldv(base + row) : 0.0);
 #pragma unroll
         for (int k = 0; k < PK; ++k) {
           c[k] = a.pk_uc[k * nt + t];
-          f[k] = a.pk_uv[k * nt + t];
+          f[k] = uvs[k * nt + t];
         }
       }
     };
@@ -289,7 +312,7 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
           if (k < cnt) s -= f[k] * ldv(a.ylev + c[k]);
         if (cnt > PK) {
           const int d = a.diag[row];
-          for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+          for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= Fs[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
         }
         const double xi = s * ud;
         a.ylev[t] = xi;
@@ -299,15 +322,15 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
           const int i = a.lev_rows[u];
           double s2 = ldv(a.ylev + u);
           const int c2 = a.pk_nu[u];
-          for (int k = 0; k < PK && k < c2; ++k) s2 -= a.pk_uv[k * nt + u] * ldv(a.ylev + a.pk_uc[k * nt + u]);
+          for (int k = 0; k < PK && k < c2; ++k) s2 -= uvs[k * nt + u] * ldv(a.ylev + a.pk_uc[k * nt + u]);
           if (c2 > PK) {
             const int d = a.diag[i];
-            for (int p = d + 1 + PK; p <= d + c2; ++p) s2 -= a.F[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
+            for (int p = d + 1 + PK; p <= d + c2; ++p) s2 -= Fs[p] * ldv(a.ylev + a.pk_pos[a.col[p]]);
           }
-          const double x2 = s2 * a.pk_ud[u];
+          const double x2 = s2 * uds[u];
           a.ylev[u] = x2;
           a.y[i] = x2;
-          out[i] = ((base ? ldv(base + i) : 0.0) + ldv(a.dp + i)) + x2;
+          out[i] = pass ? ldv(out + i) + x2 : ((base ? ldv(base + i) : 0.0) + ldv(a.dp + i)) + x2;
         }
       }
       if (l > 0) load_u(l - 1);
@@ -315,6 +338,7 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
     }
   }
   if (!grid_sync(a.bar)) return false;
+  }
   return true;
 }
 
@@ -724,7 +748,7 @@ int bar_status(Batch& b, const char* what) {
 }
 }  // namespace
 
-int ilu_factor_grid(Batch& b) {
+int ilu_factor_grid(Batch& b, double* F) {
   const Inst& I = b.h[0];
   int nblk = 0;
   FAMS_TRY(grid_blocks(b, (const void*)k_ilu_factor_grid, 0, &nblk));
@@ -735,7 +759,6 @@ int ilu_factor_grid(Batch& b) {
   const int* lev_ptr = b.lev_ptr;
   const int* rows = b.lev_rows;
   int nlev = I.nlev;
-  double* F = b.ilu;
   GridBar* bar = static_cast<GridBar*>(b.gbar);
   void* params[] = {&rowptr, &col, &diag, &lev_ptr, &rows, &nlev, &F, &bar};
   fams::note_launch();
@@ -802,6 +825,8 @@ int run_solve_grid(Batch& b, double tol, float* ms) {
   a.F = b.ilu; a.lev_ptr = b.lev_ptr; a.lev_rows = b.lev_rows;
   a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
   a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
+  a.Fb = b.ilu_b; a.pk_lvb = b.pk_lv_b; a.pk_uvb = b.pk_uv_b; a.pk_udb = b.pk_ud_b;
+  a.subblock = I.subblock;
   a.ntot = b.tot_row;
   a.ainv = b.ainv;
   a.q = b.q; a.x = b.x; a.r = b.r; a.dp = b.dp; a.y = b.y; a.ylev = b.ylev;

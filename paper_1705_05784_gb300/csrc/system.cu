@@ -1,7 +1,10 @@
 // Fine-scale EDFM system A p = q (Sec. 2, Eqs. 1-8) in CSR with sorted
 // columns: two-point matrix stencil (harmonic face transmissibilities),
 // matrix-fracture connections T = CI k_m, fracture-fracture links, Dirichlet
-// faces through half-cell transmissibilities.  Row order [matrix; fracture].
+// faces through half-cell transmissibilities, well perforations (a
+// rate-controlled well is one more row with sum_i beta_i (p^w - p_i) = Q_w; a
+// pressure-controlled well's perforations enter like Dirichlet half-cells).
+// Row order [matrix; fracture; well].
 #include <cstring>
 
 #include "batch.cuh"
@@ -32,9 +35,33 @@ __global__ void k_ff_bcell(const Inst* inst, int B, const int* off_row, long lon
   bcell[k] = I.fc_off + (r - I.row_off - I.nm);
 }
 
+// perforations: global matrix cell -> global row, global rate well -> its
+// row, productivity index -> beta = PI k of the cell (Sec. 2: lambda^m = k)
+__global__ void k_perf_rows(const Inst* inst, int B, const int* off_m, long long np,
+                            const double* perm, int* prow, int* pwrow, double* beta) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int gm = prow[k];
+  const Inst& I = inst[find_segment(off_m, B + 1, gm)];
+  prow[k] = I.row_off + (gm - I.m_off);
+  if (pwrow[k] >= 0) pwrow[k] = I.row_off + I.nm + I.nf + (pwrow[k] - I.w_off);
+  beta[k] *= perm[gm];
+}
+
+struct WellArgs {
+  const int* mperf_ptr;   // null: no wells in the batch
+  const int* mperf_idx;
+  const int* prow;
+  const int* pwrow;
+  const double* beta;
+  const double* bhp;
+  const int* wrange;
+  const double* rate;
+};
+
 __global__ void k_row_count(const Inst* inst, int B, const int* off_row, long long nrow,
                             const int* nnc_t_ptr, const int* nnc_first, const int* ffr_ptr,
-                            const int* ff_first, int* cnt) {
+                            const int* ff_first, WellArgs w, int* cnt) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst[find_segment(off_row, B + 1, r)];
@@ -46,11 +73,16 @@ __global__ void k_row_count(const Inst* inst, int B, const int* off_row, long lo
     if (I.dim == 3) c += (z > 0) + (z < I.nz - 1);
     int gm = I.m_off + loc;
     c += nnc_t_ptr[gm + 1] - nnc_t_ptr[gm];
-  } else {
+    if (w.mperf_ptr)
+      for (int q = w.mperf_ptr[gm]; q < w.mperf_ptr[gm + 1]; ++q) c += w.pwrow[w.mperf_idx[q]] >= 0;
+  } else if (loc < I.nm + I.nf) {
     int gc = I.fc_off + (loc - I.nm);
     c += nnc_first[gc + 1] - nnc_first[gc];
     c += ffr_ptr[gc + 1] - ffr_ptr[gc];
     c += ff_first[gc + 1] - ff_first[gc];
+  } else {
+    const int gw = I.w_off + (loc - I.nm - I.nf);
+    c += w.wrange[2 * gw + 1] - w.wrange[2 * gw];
   }
   cnt[r] = c;
 }
@@ -60,8 +92,8 @@ __global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long lon
                            const double* nnc_t_T, const int* nnc_first, const int* nrow_m,
                            const double* nT, const int* ffr_ptr, const int* ffr_a,
                            const double* ffr_T, const int* ff_first, const int* ffb,
-                           const double* ffT, const int* rowptr, int* col, double* val,
-                           int* diag, double* TD, double* qD) {
+                           const double* ffT, WellArgs w, const int* rowptr, int* col,
+                           double* val, int* diag, double* TD, double* qD) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrow) return;
   const Inst& I = inst[find_segment(off_row, B + 1, r)];
@@ -107,6 +139,19 @@ __global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long lon
       double t = nnc_t_T[q];
       col[p] = I.row_off + I.nm + (gc - I.fc_off); val[p++] = -t; sumT += t;
     }
+    // perforations: a rate well's row (after every fracture row), or a
+    // pressure well's Dirichlet-like term
+    if (w.mperf_ptr)
+      for (int q = w.mperf_ptr[gm]; q < w.mperf_ptr[gm + 1]; ++q) {
+        const int k = w.mperf_idx[q];
+        const double t = w.beta[k];
+        if (w.pwrow[k] >= 0) {
+          col[p] = w.pwrow[k]; val[p++] = -t; sumT += t;
+        } else {
+          td += t;
+          qd += t * w.bhp[k];
+        }
+      }
     // Dirichlet faces: T_D = 2 k A / h
     const int on[6] = {x == 0, x == nx - 1, y == 0, y == ny - 1, I.dim == 3 && z == 0,
                        I.dim == 3 && z == nz - 1};
@@ -119,7 +164,7 @@ __global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long lon
         qd += t * I.bc_val[f];
       }
     }
-  } else {
+  } else if (loc < I.nm + I.nf) {
     int gc = I.fc_off + (loc - I.nm);
     for (int q = nnc_first[gc]; q < nnc_first[gc + 1]; ++q) {
       double t = nT[q];
@@ -134,6 +179,16 @@ __global__ void k_row_fill(const Inst* inst, int B, const int* off_row, long lon
       double t = ffT[q];
       col[p] = ffb[q]; val[p++] = -t; sumT += t;
     }
+  } else {
+    // a rate-controlled well: its perforated cells (ascending), then the
+    // diagonal; its total rate is the row's source
+    const int gw = I.w_off + (loc - I.nm - I.nf);
+    for (int k = w.wrange[2 * gw]; k < w.wrange[2 * gw + 1]; ++k) {
+      const double t = w.beta[k];
+      col[p] = w.prow[k]; val[p++] = -t; sumT += t;
+    }
+    dpos = p++;
+    qd = w.rate[gw];
   }
   col[dpos] = (int)r;
   val[dpos] = sumT + td;
@@ -208,8 +263,8 @@ int phase_update(Batch& b, const double* const* scale) {
   if (n > 0) fams::note_launch(), k_fill<<<grid_for(n, T), T, 0, st>>>(n, 1.0, b.mob);
   for (int i = 0; i < b.B; ++i)
     if (scale && scale[i])
-      FAMS_CUDA(cudaMemcpyAsync(b.mob + b.h[i].row_off, scale[i], sizeof(double) * b.h[i].n,
-                                cudaMemcpyDefault, st));
+      FAMS_CUDA(cudaMemcpyAsync(b.mob + b.h[i].row_off, scale[i],
+                                sizeof(double) * (b.h[i].nm + b.h[i].nf), cudaMemcpyDefault, st));
   if (n > 0)
     fams::note_launch(), k_update_rows<<<grid_for(n, T), T, 0, st>>>(
         n, b.rowptr, b.col, b.diag, b.val0, b.TD0, b.qD0, b.mob, b.val, b.TD, b.qD, b.q);
@@ -335,12 +390,17 @@ int phase_system(Batch& b) {
   FAMS_TRY(transpose(b, b.ff_first, bcell, b.ff_T, (int)nfc, (int)nfc, nff, &ffr_ptr, &ffr_a,
                      &ffr_T, false));
   // ffr_a: for each higher cell, the lower cells (fracture-cell index) in order
+  if (b.tot_perf > 0)
+    fams::note_launch(), k_perf_rows<<<grid_for(b.tot_perf, T), T, 0, st>>>(
+        b.d_inst, b.B, b.off_m, b.tot_perf, b.perm, b.perf_row, b.perf_wrow, b.perf_beta);
+  const WellArgs wa{b.tot_perf > 0 ? b.mperf_ptr : nullptr, b.mperf_idx, b.perf_row, b.perf_wrow,
+                    b.perf_beta, b.perf_bhp, b.wperf_range, b.w_rate};
   int* cnt = nullptr;
   FAMS_TRY(b.scratch((void**)&cnt, sizeof(int) * (nrow + 1)));
   FAMS_TRY(b.alloc((void**)&b.rowptr, sizeof(int) * (nrow + 1)));
   if (nrow > 0)
     fams::note_launch(), k_row_count<<<grid_for(nrow, T), T, 0, st>>>(b.d_inst, b.B, b.off_row, nrow, nnc_t_ptr,
-                                                 b.nnc_first, ffr_ptr, b.ff_first, cnt);
+                                                 b.nnc_first, ffr_ptr, b.ff_first, wa, cnt);
   long long nnz = 0;
   FAMS_TRY(exclusive_scan(b, cnt, b.rowptr, nrow, &nnz));
   b.tot_nnz = nnz;
@@ -352,8 +412,8 @@ int phase_system(Batch& b) {
   if (nrow > 0)
     fams::note_launch(), k_row_fill<<<grid_for(nrow, T), T, 0, st>>>(
         b.d_inst, b.B, b.off_row, nrow, b.perm, nnc_t_ptr, nnc_t_fc, nnc_t_T, b.nnc_first,
-        b.nnc_row_m, b.nnc_T, ffr_ptr, ffr_a, ffr_T, b.ff_first, b.ff_b, b.ff_T, b.rowptr, b.col,
-        b.val, b.diag, b.TD, b.qD);
+        b.nnc_row_m, b.nnc_T, ffr_ptr, ffr_a, ffr_T, b.ff_first, b.ff_b, b.ff_T, wa, b.rowptr,
+        b.col, b.val, b.diag, b.TD, b.qD);
   FAMS_CUDA(cudaGetLastError());
   // row pointers at the instance boundaries (off_row: B + 1 row offsets)
   std::vector<int> hp;

@@ -46,7 +46,13 @@ class fams_opts(C.Structure):
                 ("max_iter", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
                 ("restart", C.c_int),
                 ("prepare_flux", C.c_int), ("merge_cap", C.c_int),
-                ("grid_solve", C.c_int)]
+                ("grid_solve", C.c_int), ("subblock", C.c_int)]
+
+
+class fams_wells(C.Structure):
+    _fields_ = [("n", C.c_int), ("perf_ptr", C.POINTER(C.c_int)),
+                ("perf_cell", C.POINTER(C.c_int)), ("perf_pi", C.POINTER(C.c_double)),
+                ("control", C.POINTER(C.c_int)), ("value", C.POINTER(C.c_double))]
 
 
 class fams_stats(C.Structure):
@@ -75,6 +81,9 @@ def _load():
                                      P(fams_opts), P(C.c_void_p)]
     lib.fams_setup.argtypes = [P(fams_grid), P(C.c_double), P(fams_fracs), P(fams_opts),
                                P(C.c_void_p)]
+    lib.fams_setup_batch_wells.argtypes = [C.c_int, P(fams_grid), P(P(C.c_double)), P(fams_fracs),
+                                           P(fams_wells), P(fams_opts), P(C.c_void_p)]
+    lib.fams_sizes_wells.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(C.c_int)]
     lib.fams_sizes.argtypes = [C.c_void_p, C.c_int] + [P(C.c_int)] * 5
     lib.fams_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, P(fams_stats)]
     lib.fams_solve_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double,
@@ -142,8 +151,26 @@ def _args(prob):
                   max(1, prob.frac_cz), prob.basis, prob.restriction, prob.alpha,
                   prob.max_iter, getattr(prob, "precision", FP64), getattr(prob, "krylov", 0),
                   getattr(prob, "restart", 30), getattr(prob, "prepare_flux", 0),
-                  getattr(prob, "merge_cap", 0), getattr(prob, "grid_solve", 0))
+                  getattr(prob, "merge_cap", 0), getattr(prob, "grid_solve", 0),
+                  getattr(prob, "subblock", 0))
     return g, perm, f, o, (xy, kf)
+
+
+def _wells(prob):
+    """fams_wells (and the arrays it points into) for the wells of a problem."""
+    ws = getattr(prob, "wells", None) or []
+    if not ws:
+        return fams_wells(0, None, None, None, None, None), ()
+    ptr = np.zeros(len(ws) + 1, np.int32)
+    for i, w in enumerate(ws):
+        ptr[i + 1] = ptr[i] + len(w.cells)
+    cells = np.ascontiguousarray(np.concatenate([np.asarray(w.cells) for w in ws]), np.int32)
+    pis = np.ascontiguousarray(np.concatenate([np.asarray(w.pi, np.float64) for w in ws]))
+    ctl = np.array([int(w.control) for w in ws], np.int32)
+    val = np.array([float(w.value) for w in ws], np.float64)
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+    out = fams_wells(len(ws), ip(ptr), ip(cells), _dptr(pis), ip(ctl), _dptr(val))
+    return out, (ptr, cells, pis, ctl, val)
 
 
 def launch_count():
@@ -176,9 +203,14 @@ class Context:
             perms = (C.POINTER(C.c_double) * n)(*[_dptr(p[1]) for p in parts])
         fracs = (fams_fracs * n)(*[p[2] for p in parts])
         opts = (fams_opts * n)(*[p[3] for p in parts])
-        self._keep = parts
+        wl = [_wells(p) for p in problems]
+        self._keep = (parts, wl)
         self.h = C.c_void_p()
-        _check(lib.fams_setup_batch(n, grids, perms, fracs, opts, C.byref(self.h)))
+        if any(w[0].n for w in wl):
+            wells = (fams_wells * n)(*[w[0] for w in wl])
+            _check(lib.fams_setup_batch_wells(n, grids, perms, fracs, wells, opts, C.byref(self.h)))
+        else:
+            _check(lib.fams_setup_batch(n, grids, perms, fracs, opts, C.byref(self.h)))
         self.n = n
         self.problems = problems
 
@@ -200,10 +232,15 @@ class Context:
         self.close()
 
     def sizes(self, inst=0):
-        v = [C.c_int() for _ in range(5)]
-        _check(lib.fams_sizes(self.h, inst, *[C.byref(x) for x in v]))
-        return dict(zip(("n_matrix", "n_frac", "n_coarse", "n_faces", "n_nnc"),
-                        [x.value for x in v]))
+        """Counts of an instance; "n" = every unknown (matrix, fracture and
+        rate-well pressures), the length of its rhs and x."""
+        v = [C.c_int() for _ in range(7)]
+        _check(lib.fams_sizes(self.h, inst, *[C.byref(x) for x in v[:5]]))
+        _check(lib.fams_sizes_wells(self.h, inst, C.byref(v[5]), C.byref(v[6])))
+        d = dict(zip(("n_matrix", "n_frac", "n_coarse", "n_faces", "n_nnc", "n_well", "n_perf"),
+                     [x.value for x in v]))
+        d["n"] = d["n_matrix"] + d["n_frac"] + d["n_well"]
+        return d
 
     def query(self, what, inst=0):
         code = Q[what] if isinstance(what, str) else what
@@ -218,7 +255,7 @@ class Context:
         single instance).  Returns (list of pressures, list of stats dicts)."""
         n = self.n
         sz = [self.sizes(i) for i in range(n)]
-        N = [s["n_matrix"] + s["n_frac"] for s in sz]
+        N = [s["n"] for s in sz]
         if rhs is not None and not isinstance(rhs, (list, tuple)):
             rhs = [rhs]
         if x0 is not None and not isinstance(x0, (list, tuple)):
@@ -275,7 +312,7 @@ class Context:
         """fams_solve_static on this single-instance context: the solve of
         fams_solve with the library's fixed work array instead of any
         allocation.  Returns (pressure, stats dict)."""
-        N = self.sizes(0)["n_matrix"] + self.sizes(0)["n_frac"]
+        N = self.sizes(0)["n"]
         x = np.ascontiguousarray(x0 if x0 is not None else np.zeros(N), np.float64).copy()
         r = None if rhs is None else np.ascontiguousarray(rhs, np.float64)
         st = fams_stats()

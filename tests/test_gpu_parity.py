@@ -971,3 +971,30 @@ def test_whole_gpu_solve_matches_the_oracle(name, restriction):
             res.append((xs[0], stats[0]["iterations"]))
     assert abs(res[0][1] - res[1][1]) <= 1
     assert np.linalg.norm(res[0][0] - res[1][0]) / np.linalg.norm(res[1][0]) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [-1, 1])
+@pytest.mark.parametrize("restriction", [0, 1])
+@pytest.mark.parametrize("name", ["2d64", "3dcross"])
+def test_sub_block_smoothing_stage_matches_the_oracle(name, restriction, grid):
+    """fams_opts.subblock: the extra smoothing stage on the media blocks
+    (Sec. 3.2) in the GMRES preconditioner, on one CTA and on every SM: a
+    fixed-count trajectory to 1e-10; the Table 1 loop with it too."""
+    fams = _fams()
+    p = _gmres(_case(name, 0, restriction), 10, 15)
+    p.subblock, p.grid_solve = 1, grid
+    g, sysm, c, P, st = oracle.build(p)
+    assert st.Fb is not None
+    xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=15, restart=10)
+    with fams.Context(p) as ctx:
+        xs, stats = ctx.solve(tol=0.0)
+        assert stats[0]["iterations"] == 15 == ito
+        assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
+    if grid < 0 and restriction == 1:
+        q = copy.copy(p)
+        q.krylov, q.max_iter = 0, 9
+        xt, itt, _, _, _ = osolver.two_stage_solve(st, tol=0.0, max_iter=9)
+        with fams.Context(q) as ctx:
+            xs, stats = ctx.solve(tol=0.0)
+            assert stats[0]["iterations"] == 9 == itt
+            assert np.linalg.norm(xs[0] - xt) / np.linalg.norm(xt) < 1e-10

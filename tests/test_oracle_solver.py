@@ -409,3 +409,36 @@ def test_msmix_restriction():
     gq, sq, cq, Pq, stq = oracle.build(q)
     feq = solver.setup(sq, Pq, cq.primal, cq.n_coarse, solver.R_FE)
     assert abs(stq.R - feq.R).max() == 0.0
+
+
+def test_sub_block_smoother_factors_are_the_media_blocks():
+    """The stage's ILU(0) is that of A^mm and A^ff apart (each factored on its
+    own, then placed in A's pattern), and zero on the cross-medium entries;
+    without fractures it is ILU(0) of A itself."""
+    p = _small(variant=0, restriction=1)
+    p.subblock = 1
+    g, sysm, c, P, st = oracle.build(p)
+    nm = g.n_matrix
+    A = sysm.A.tocsr()
+    Fm = solver.ilu0(A[:nm, :nm]).toarray()
+    Ff = solver.ilu0(A[nm:, nm:]).toarray()
+    Fb = st.Fb.toarray()
+    np.testing.assert_allclose(Fb[:nm, :nm], Fm, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(Fb[nm:, nm:], Ff, rtol=1e-14, atol=0)
+    assert not Fb[:nm, nm:].any() and not Fb[nm:, :nm].any()
+    q = inputs.config_2d(24, 1.0, 4.0, 0, (1, 2), 1.0, 4, 4, seed=3)
+    q.subblock = 1
+    _, _, _, _, sq = oracle.build(q)
+    assert abs(sq.Fb - sq.F).max() == 0.0
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_sub_block_smoother_converges_to_the_direct_solution(variant):
+    p = inputs.config_2d(32, 1.5, 6.0, 6, (8, 20), 1e6, 4, 5, seed=9, basis=variant,
+                         restriction=1)
+    p.subblock = 1
+    p.tol, p.max_iter = 1e-10, 500
+    r = oracle.run(p)
+    g, sysm, c, P, st = oracle.build(p)
+    xd = spla.spsolve(sysm.A.tocsc(), sysm.q)
+    assert r.converged and np.linalg.norm(r.p - xd) < 1e-6 * np.linalg.norm(xd)
