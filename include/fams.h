@@ -237,16 +237,18 @@ int fams_update(fams_ctx* ctx, const double* mobility_scale);
 /* the same for every instance of a batch context (scale[i] nullable) */
 int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);
 
-/* fams_update_basis - fams_update_batch, then, when the mobility has moved
-   far from the one the current basis functions were built with, the basis
-   functions rebuilt from the updated operator on the same coarse grids (the
-   paper keeps them across time steps unless properties change much, Sec.
-   3.1): P and P^T, R A P and its factors anew; ILU(0) as after the update.
-   Rebuilt when some cell's scale differs from its scale at the last build
-   (the setup until the first rebuild) by more than a factor 1 + eps; eps < 0
-   rebuilds always, +infinity never.  The decision covers the whole context
-   (the paper decides per local problem).  *rebuilt (nullable) is set to 1 or
-   0.  Errors as fams_update; FAMS_EINVAL for a NaN eps. */
+/* fams_update_basis - fams_update_batch, then the adaptive basis update of
+   Sec. 3.1 (basis functions recomputed only where the fine-scale properties
+   change beyond a threshold), per dual block: a cell is marked when its
+   mobility scale differs from the scale its basis row was last computed with
+   (the setup's, 1, until then) by more than a factor 1 + eps (eps < 0 marks
+   every cell, +infinity none); the dual blocks holding a marked cell, and,
+   stage by stage, the blocks that read a row solved again in an earlier
+   stage, are solved again from the updated operator on the same coarse
+   grids, the others keep their rows; truncation, P^T, R A P and its factors
+   follow (ILU(0) as after the update).  *rebuilt (nullable) receives the
+   number of dual blocks solved (0: P unchanged).  Errors as fams_update;
+   FAMS_EINVAL for a NaN eps. */
 int fams_update_basis(fams_ctx* ctx, const double* const* mobility_scale, double eps,
                       int* rebuilt);
 

@@ -51,7 +51,8 @@ def prolongation(prob, g, sysm, c, route="staged", truncated=True):
     `sysm` (Sec. 3.1, App. A; truncation Sec. 4.3).  Called with an updated
     system it rebuilds the basis functions for new mobilities on the same
     coarse grids."""
-    plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac])
+    plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac,
+                            np.full(getattr(sysm, "n_well", 0), -1, np.int64)])
     cap = getattr(prob, "merge_cap", 0)
     if route == "staged":
         P = _basis.prolongation_staged(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate,
@@ -60,6 +61,29 @@ def prolongation(prob, g, sysm, c, route="staged", truncated=True):
         P = _basis.prolongation_appendix(sysm.A0, c.rank, c.medium, c.node_cell, prob.basis,
                                          plate, c.row_net, cap)
     return _basis.truncate(P, prob.alpha) if truncated else P
+
+
+def prolongation_update(prob, g, sysm, c, P_full, ref, scale, eps):
+    """The adaptive basis update (Sec. 3.1: basis functions are recomputed
+    only where the fine-scale properties change beyond a threshold; Table 1
+    step 4): a cell is marked when its mobility scale moved by more than a
+    factor 1 + eps from `ref`, the scale its basis row was last computed
+    with (eps < 0 marks every cell); dual blocks holding a marked cell, and
+    the blocks that read rows recomputed in an earlier stage, are solved
+    again from the updated operator of `sysm`; the others keep their rows of
+    P_full (the untruncated P of the last build).  Returns (P truncated,
+    P untruncated, new ref, blocks solved)."""
+    scale = np.asarray(scale, np.float64)
+    ref = np.asarray(ref, np.float64)
+    marked = np.ones(len(scale), bool) if eps < 0 else (
+        (scale > (1.0 + eps) * ref) | (scale < ref / (1.0 + eps)))
+    plate = np.concatenate([np.full(g.n_matrix, -1, np.int64), g.cell_frac,
+                            np.full(getattr(sysm, "n_well", 0), -1, np.int64)])
+    Pf, rec, solved = _basis.prolongation_staged(
+        sysm.A0, c.rank, c.medium, c.node_cell, prob.basis, plate, c.row_net,
+        getattr(prob, "merge_cap", 0), old=P_full, marked=marked)
+    ref = np.where(rec, scale, ref)
+    return _basis.truncate(Pf, prob.alpha), Pf, ref, solved
 
 
 def reconstruction_setup(prob, g, sysm, c):

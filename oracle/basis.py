@@ -205,13 +205,19 @@ def cut_links(A0, rank, medium, node_cell, variant, plate=None, net=None, merge_
 
 
 def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=None,
-                        merge_cap=0):
+                        merge_cap=0, old=None, marked=None):
     """P (CSR, n x n_coarse) by the staged wirebasket rule.  plate[r]: input
     fracture of fracture row r (-1 for matrix rows; None: no crossings);
     net[r]: coarsening network of fracture row r (None: a single network);
     merge_cap: largest Coupled block merged across the media (0: no cap); a
     kept link between two blocks of one stage (cut by the cap) is dropped
-    and removed from the diagonal."""
+    and removed from the diagonal.
+
+    Adaptive update (old: the untruncated P of the last build, marked: the
+    cells whose mobility moved beyond the threshold): a dual block is solved
+    again, with this A0, only if it holds a marked cell or reads a row of a
+    block solved again in an earlier stage; the other blocks keep their rows
+    of `old`.  Returns (P, recomputed rows, blocks solved) then."""
     A0 = sp.csr_matrix(A0)
     n = A0.shape[0]
     plate = _plate_of(n, plate)
@@ -226,6 +232,11 @@ def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=No
         rows[v] = {j: 1.0}
         known[v] = True
     ip, ix, dv = A0.indptr, A0.indices, A0.data
+    adaptive = old is not None
+    recomputed = np.zeros(n, bool)
+    solved = 0
+    if adaptive:
+        old = sp.csr_matrix(old)
     for stage in stage_list(variant):
         in_stage = np.zeros(n, bool)
         for (med, rk) in stage:
@@ -242,6 +253,24 @@ def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=No
         for key in sorted(members):
             cells = members[key]
             cells = sorted(cells)
+            if adaptive:
+                dirty = bool(np.asarray(marked)[cells].any())
+                if not dirty:
+                    for r in cells:
+                        for p in range(ip[r], ip[r + 1]):
+                            c = ix[p]
+                            if c != r and recomputed[c] and keep(r, c) and not in_stage[c]:
+                                dirty = True
+                                break
+                        if dirty:
+                            break
+                if not dirty:
+                    for r in cells:
+                        a, e = old.indptr[r], old.indptr[r + 1]
+                        rows[r] = dict(zip(old.indices[a:e].tolist(), old.data[a:e].tolist()))
+                    continue
+                recomputed[cells] = True
+                solved += 1
             b = len(cells)
             bl = {r: i for i, r in enumerate(cells)}
             Ab = np.zeros((b, b))
@@ -282,6 +311,8 @@ def prolongation_staged(A0, rank, medium, node_cell, variant, plate=None, net=No
             vv.append(rows[r][col])
     P = sp.csr_matrix((vv, (ri, ci)), shape=(n, nc))
     P.sort_indices()
+    if adaptive:
+        return P, recomputed, solved
     return P
 
 

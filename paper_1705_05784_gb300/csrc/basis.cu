@@ -551,6 +551,61 @@ __global__ void k_comp_solve(CompArgs a, long long slice, double* gwork) {
   comp_solve<G>(a, a.comp_list[idx], M, red);
 }
 
+// Adaptive update (Sec. 3.1: basis functions recomputed only where the
+// fine-scale properties change beyond a threshold).  dirty[c] of a dual block
+// of the stage: it holds a marked cell, or one of its rows keeps a link to a
+// row of an earlier stage that was solved again (rec)
+__global__ void k_block_dirty(const Inst* inst, int B, const int* off_row, long long nrow,
+                              const int* rank, const int* plate, const int* rowptr,
+                              const int* col, const int* instage, const int* comp_of,
+                              const int* marked, const int* rec, int* dirty) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow || !instage[r]) return;
+  const Inst& I = inst_of(inst, B, off_row, (int)r);
+  int d = marked[r];
+  const int mr = medium_of(I, (int)r), rr = rank[r];
+  for (int p = rowptr[r]; p < rowptr[r + 1] && !d; ++p) {
+    const int c = col[p];
+    if (c == r || instage[c] || !rec[c]) continue;
+    if (keep_link(I.basis, mr, rr, medium_of(I, c), rank[c], crossing(plate, nrow, (int)r, c))) d = 1;
+  }
+  if (d) dirty[comp_of[r]] = 1;
+}
+
+// a block kept as it was: its rows' pool entries from the untruncated P of
+// the last build (each row's nonzeros at their columns in the block's
+// sorted column list, zeros elsewhere); one thread per row of such blocks
+__global__ void k_block_keep(long long nrow, const int* instage, const int* comp_of,
+                             const int* dirty, const int* pos, const int* colptr,
+                             const int* colbuf, const long long* pool_off, const int* comp_off,
+                             const int* oldp, const int* oldc, const double* oldv, int s,
+                             int* ocol, double* oval, int* pstage, int* poff, int* plen, int* rec,
+                             int* err) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow || !instage[r]) return;
+  const int c = comp_of[r];
+  if (dirty[c]) {
+    rec[r] = 1;
+    return;
+  }
+  const int k = colptr[c + 1] - colptr[c];
+  const int* cols = colbuf + colptr[c];
+  const long long base = pool_off[c] + (long long)pos[r] * k;
+  for (int q = 0; q < k; ++q) {
+    ocol[base + q] = cols[q];
+    oval[base + q] = 0.0;
+  }
+  for (int e = oldp[r]; e < oldp[r + 1]; ++e) {
+    const int j = find_col(cols, k, oldc[e]);
+    if (j < 0) { atomicCAS(err, 0, DERR_INVAL); continue; }
+    oval[base + j] = oldv[e];
+  }
+  pstage[r] = s;
+  poff[r] = (int)base;
+  plen[r] = k;
+  (void)comp_off;
+}
+
 // truncation (Sec. 4.3) and CSR of P.  full = true: the basis functions
 // before truncation (the flux reconstruction's P).
 __device__ inline void trunc_row(const double* pv, int len, double alpha, int* cnt, double* sum,
@@ -623,8 +678,10 @@ __global__ void k_p_global_cols(const Inst* inst, int B, const int* off_row, lon
 
 }  // namespace
 
-int phase_basis(Batch& b) {
+int phase_basis(Batch& b, const int* marked, int* rec, int* n_solved) {
   const int T = 256;
+  const bool adaptive = marked != nullptr;
+  if (n_solved) *n_solved = 0;
   cudaStream_t st = b.stream;
   long long nrow = b.tot_row, nct = b.tot_nc;
   int *pstage = nullptr, *poff = nullptr, *plen = nullptr;
@@ -753,6 +810,28 @@ int phase_basis(Batch& b) {
       ++b.class_cnt[q];
       cmax[q] = std::max(cmax[q], need);
     }
+    // adaptive update: only the dirty blocks are solved; the others keep the
+    // untruncated rows of the last build (pf_*)
+    std::vector<int> hdirty;
+    int* dirty = nullptr;
+    if (adaptive) {
+      FAMS_TRY(b.scratch((void**)&dirty, sizeof(int) * (ncomp + 1)));
+      FAMS_CUDA(cudaMemsetAsync(dirty, 0, sizeof(int) * (ncomp + 1), st));
+      fams::note_launch(), k_block_dirty<<<grid_for(nrow, T), T, 0, st>>>(
+          b.d_inst, b.B, b.off_row, nrow, b.rank, plate, b.rowptr, b.col, instage, comp_of,
+          marked, rec, dirty);
+      hdirty.resize(ncomp);
+      FAMS_CUDA(cudaMemcpyAsync(hdirty.data(), dirty, sizeof(int) * ncomp, cudaMemcpyDeviceToHost, st));
+      FAMS_CUDA(cudaStreamSynchronize(st));
+      for (int q = 0; q < 4; ++q) {
+        std::vector<int> keep;
+        for (int c : cls[q])
+          if (hdirty[c]) keep.push_back(c);
+        cls[q].swap(keep);
+      }
+      for (int q = 0; q < 4; ++q)
+        if (n_solved) *n_solved += (int)cls[q].size();
+    }
     long long* pool_off = nullptr;
     int* ocol = nullptr;
     double* oval = nullptr;
@@ -769,6 +848,10 @@ int phase_basis(Batch& b) {
     }
     pool.col[s] = ocol;
     pool.val[s] = oval;
+    if (adaptive)
+      fams::note_launch(), k_block_keep<<<grid_for(nrow, T), T, 0, st>>>(
+          nrow, instage, comp_of, dirty, pos, colptr, colbuf, pool_off, coff, b.pf_ptr, b.pf_col,
+          b.pf_val, s, ocol, oval, pstage, poff, plen, rec, b.d_err);
     CompArgs ca{b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col, b.val, b.TD, instage,
                 label, nullptr, 0, coff, members, pos, colptr, colbuf, bw, pool_off, pstage, poff, plen,
                 pool, s, ocol, oval, b.d_err};

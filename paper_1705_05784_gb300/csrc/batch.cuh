@@ -293,7 +293,11 @@ int transpose(Batch& b, const int* rowptr, const int* col, const double* val, in
 int phase_geometry(Batch& b);     // geometry.cu
 int phase_system(Batch& b);       // system.cu: CSR of A, q_D
 int phase_coarse(Batch& b);       // coarse.cu: matrix blocks, networks, BFS, ranks
-int phase_basis(Batch& b);        // basis.cu: P
+// basis.cu: P.  marked (device, per row; null: every block) selects the
+// adaptive update: only dual blocks holding a marked row, or reading a row
+// solved again in an earlier stage, are solved (rows flagged in rec); the
+// others keep their rows of the untruncated P of the last build (pf_*)
+int phase_basis(Batch& b, const int* marked = nullptr, int* rec = nullptr, int* n_solved = nullptr);
 int phase_coarse_op(Batch& b, int restriction);  // coarseop.cu: R A P, band LU
 // R A P with the prolongation (p_ptr, p_col, p_val): P, or the reconstruction's
 int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool reuse,

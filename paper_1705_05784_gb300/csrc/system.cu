@@ -286,19 +286,6 @@ int phase_update(Batch& b, const double* const* scale) {
 
 namespace {
 
-// largest relative change max(s/s0, s0/s) - 1 of the mobility scales since
-// the basis was built (s0 null: all 1), as the bits of a non-negative double,
-// which order like the integers
-__global__ void k_scale_change(long long n, const double* s, const double* s0,
-                               unsigned long long* out) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double a = s[i], c = s0 ? s0[i] : 1.0;
-  double q = (a > c ? a / c : c / a) - 1.0;
-  if (!(q >= 0.0)) q = 1e300;   // not finite: treat as a large change
-  atomicMax(out, (unsigned long long)__double_as_longlong(q));
-}
-
 void release_coarse(Batch& b, CoarseSys& cs, CoarseHost& ch) {
   b.release(cs.Ac); b.release(cs.ac_off); b.release(cs.band); b.release(cs.band_off);
   b.release(cs.kl); b.release(cs.ku); b.release(cs.ipiv); b.release(cs.perm); b.release(cs.bad);
@@ -306,63 +293,94 @@ void release_coarse(Batch& b, CoarseSys& cs, CoarseHost& ch) {
   ch = CoarseHost{};
 }
 
+// The time-step update, then the adaptive basis update (Sec. 3.1: basis
+// functions recomputed only where the fine-scale properties change beyond a
+// threshold): a row is marked when its mobility scale moved by more than a
+// factor 1 + eps from the scale its basis row was last computed with; the
+// dual blocks holding a marked row, and those reading a row solved again in
+// an earlier stage, are solved again from the updated operator; P, P^T, R A P
+// and its factors follow when any block was.  ILU(0) depends on A only and
+// stays as the update left it.
+// adaptive update: rows whose mobility scale moved by more than a factor
+// 1 + eps from the scale their basis row was last computed with (eps < 0:
+// every row)
+__global__ void k_mark_moved(long long n, const double* mob, const double* ref, double eps,
+                             int* marked) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = mob[i], r = ref ? ref[i] : 1.0;
+  marked[i] = eps < 0.0 || s > (1.0 + eps) * r || s < r / (1.0 + eps);
+}
+
+__global__ void k_ref_update(long long n, const int* rec, const double* mob, double* ref) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && rec[i]) ref[i] = mob[i];
+}
+
+__global__ void k_any(long long n, const int* v, int* out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && v[i]) *out = 1;
+}
+
 }  // namespace
 
-// The time-step update, then -- when some cell's mobility scale moved by
-// more than a factor 1 + eps from the one the current basis functions were
-// built with (eps < 0: always) -- the basis functions, P and P^T, R A P and
-// its factors rebuilt from the updated basis operator on the same coarse
-// grids.  ILU(0) depends on A only and stays as the update left it.
 int phase_update_basis(Batch& b, const double* const* scale, double eps, int* rebuilt) {
   const int T = 256;
   cudaStream_t st = b.stream;
   const long long n = b.tot_row;
   if (rebuilt) *rebuilt = 0;
   FAMS_TRY(phase_update(b, scale));
-  bool again = eps < 0.0;
-  if (!again && n > 0) {
-    unsigned long long* d = nullptr;
-    FAMS_TRY(b.scratch((void**)&d, sizeof(unsigned long long)));
-    FAMS_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), st));
-    fams::note_launch(), k_scale_change<<<grid_for(n, T), T, 0, st>>>(n, b.mob, b.mob_basis, d);
-    unsigned long long h = 0;
-    FAMS_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
-    FAMS_CUDA(cudaStreamSynchronize(st));
-    double q = 0.0;
-    std::memcpy(&q, &h, sizeof(q));
-    again = q > eps;
+  if (n == 0) return FAMS_OK;
+  if (!b.mob_basis) {   // the scales the current basis rows were computed with: the setup's
+    FAMS_TRY(b.alloc((void**)&b.mob_basis, sizeof(double) * (n + 1)));
+    fams::note_launch(), k_fill<<<grid_for(n, T), T, 0, st>>>(n, 1.0, b.mob_basis);
   }
-  if (!again) {
+  int *marked = nullptr, *rec = nullptr, *any = nullptr;
+  FAMS_TRY(b.scratch((void**)&marked, sizeof(int) * (n + 1)));
+  FAMS_TRY(b.scratch((void**)&rec, sizeof(int) * (n + 1)));
+  FAMS_TRY(b.scratch((void**)&any, sizeof(int)));
+  FAMS_CUDA(cudaMemsetAsync(rec, 0, sizeof(int) * (n + 1), st));
+  FAMS_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
+  fams::note_launch(), k_mark_moved<<<grid_for(n, T), T, 0, st>>>(n, b.mob, b.mob_basis, eps, marked);
+  fams::note_launch(), k_any<<<grid_for(n, T), T, 0, st>>>(n, marked, any);
+  int hany = 0;
+  FAMS_CUDA(cudaMemcpyAsync(&hany, any, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FAMS_CUDA(cudaStreamSynchronize(st));
+  if (!hany) {
     b.free_tmp();
     return FAMS_OK;
   }
-  if (!b.pf_alias) {
-    b.release(b.pf_ptr); b.release(b.pf_col); b.release(b.pf_val);
+  // the new P replaces the old once the stages have read the old rows
+  int *op = b.p_ptr, *oc = b.p_col, *opt = b.pt_ptr, *otc = b.pt_col;
+  double *ov = b.p_val, *otv = b.pt_val;
+  int *ofp = b.pf_ptr, *ofc = b.pf_col;
+  double* ofv = b.pf_val;
+  const bool oalias = b.pf_alias;
+  int solved = 0;
+  FAMS_TRY(phase_basis(b, marked, rec, &solved));
+  b.release(op); b.release(oc); b.release(ov);
+  b.release(opt); b.release(otc); b.release(otv);
+  if (!oalias) { b.release(ofp); b.release(ofc); b.release(ofv); }
+  fams::note_launch(), k_ref_update<<<grid_for(n, T), T, 0, st>>>(n, rec, b.mob, b.mob_basis);
+  if (solved > 0) {
+    release_coarse(b, b.cs[0], b.csh[0]);
+    FAMS_TRY(phase_coarse_op(b, -1));
+    if (b.fv_built) release_coarse(b, b.cs[1], b.csh[1]);
+    b.fv_built = false;
+    b.fv_ready = false;
+    b.ainv_ready = false;
+    if (b.p_val32) {   // FP32 copies of P and P^T at the new size
+      b.release(b.p_val32);
+      b.release(b.pt_val32);
+      FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (b.tot_pnnz + 1)));
+      FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (b.tot_pnnz + 1)));
+      FAMS_TRY(refresh_mixed(b));
+    }
   }
-  b.pf_ptr = nullptr; b.pf_col = nullptr; b.pf_val = nullptr;
-  b.release(b.p_ptr); b.release(b.p_col); b.release(b.p_val);
-  b.release(b.pt_ptr); b.release(b.pt_col); b.release(b.pt_val);
-  FAMS_TRY(phase_basis(b));
-  release_coarse(b, b.cs[0], b.csh[0]);
-  FAMS_TRY(phase_coarse_op(b, -1));
-  if (b.fv_built) release_coarse(b, b.cs[1], b.csh[1]);
-  b.fv_built = false;
-  b.fv_ready = false;
-  b.ainv_ready = false;
-  if (b.p_val32) {   // FP32 copies of P and P^T at the new size
-    b.release(b.p_val32);
-    b.release(b.pt_val32);
-    FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (b.tot_pnnz + 1)));
-    FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (b.tot_pnnz + 1)));
-    FAMS_TRY(refresh_mixed(b));
-  }
-  if (!b.mob_basis) FAMS_TRY(b.alloc((void**)&b.mob_basis, sizeof(double) * (n + 1)));
-  if (n > 0)
-    FAMS_CUDA(cudaMemcpyAsync(b.mob_basis, b.mob, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   FAMS_CUDA(cudaStreamSynchronize(st));
   b.free_tmp();
-  FAMS_TRY(b.check_err("basis rebuild"));
-  if (rebuilt) *rebuilt = 1;
+  FAMS_TRY(b.check_err("basis update"));
+  if (rebuilt) *rebuilt = solved;
   return FAMS_OK;
 }
 

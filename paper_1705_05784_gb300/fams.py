@@ -284,16 +284,18 @@ class Context:
         _check(lib.fams_update_batch(self.h, ptrs))
 
     def update_basis(self, scales, eps):
-        """fams_update_basis: the update of `update`, then the basis functions
-        rebuilt when some scale moved by more than a factor 1 + eps since the
-        last build (eps < 0: always).  Returns whether they were rebuilt."""
+        """fams_update_basis: the update of `update`, then the adaptive basis
+        update: dual blocks holding a cell whose scale moved by more than a
+        factor 1 + eps since its basis row was computed (eps < 0: every
+        block), and their downstream blocks, solved again.  Returns the number
+        of dual blocks solved (0: P unchanged)."""
         if not isinstance(scales, (list, tuple)):
             scales = [scales]
         arrs = [None if sc is None else np.ascontiguousarray(sc, np.float64) for sc in scales]
         ptrs = (C.c_void_p * self.n)(*[0 if a is None else a.ctypes.data for a in arrs])
         r = C.c_int(0)
         _check(lib.fams_update_basis(self.h, ptrs, float(eps), C.byref(r)))
-        return bool(r.value)
+        return int(r.value)
 
     def solve_device(self, rhs_ptrs, x_ptrs, tol):
         """The same call with caller-owned buffers given as raw pointers (host

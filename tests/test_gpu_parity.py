@@ -705,23 +705,36 @@ def test_time_step_update_matches_oracle(name, restriction):
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3dcross"])
 def test_basis_rebuild_matches_oracle(name, restriction):
-    """fams_update_basis: below its threshold P stays the setup's; above it
-    P, R A P, a GMRES trajectory and the conservative fluxes equal the
-    oracle's for the basis rebuilt from the updated operator; the same scales
-    again are no change; eps < 0 always rebuilds."""
+    """fams_update_basis, the adaptive update of Sec. 3.1 per dual block:
+    with a threshold above every change nothing is solved and P stays; with
+    scales moved in a patch only the blocks holding a moved cell and their
+    downstream blocks are solved again -- the same blocks as the oracle's
+    (count bit-exact) -- and P, R A P, a GMRES trajectory and the fluxes
+    equal the oracle's; the same scales again solve nothing; eps < 0 solves
+    every block."""
     from oracle import assemble as oasm
     fams = _fams()
     p = _gmres(_case(name, 0, restriction), 8, 13)
     g, sysm, c, P, st0 = oracle.build(p)
-    sc = np.random.default_rng(7).uniform(0.5, 2.0, sysm.n)
+    Pf = oracle.prolongation(p, g, sysm, c, truncated=False)
+    rng = np.random.default_rng(7)
+    sc = np.ones(sysm.n)
+    patch = rng.choice(g.n_matrix, size=max(8, g.n_matrix // 20), replace=False)
+    sc[patch] = rng.uniform(3.0, 6.0, len(patch))
+    sc[g.n_matrix:] = rng.uniform(0.9, 1.1, g.n_frac)      # below the threshold
     with fams.Context(p) as ctx:
-        assert not ctx.update_basis(sc, 10.0)
+        assert ctx.update_basis(sc, 10.0) == 0
         Pg = _gpu_P(ctx, P.shape)
         np.testing.assert_array_equal(Pg.indices, P.indices)
         np.testing.assert_allclose(Pg.data, P.data, rtol=0, atol=1e-12)
-        assert ctx.update_basis(sc, 0.01)
+        n_solved = ctx.update_basis(sc, 0.5)
         ur = oasm.update_mobility(sysm, sc)
-        Pu = oracle.prolongation(p, g, ur, c)
+        Pu, Puf, ref, solved = oracle.prolongation_update(p, g, ur, c, Pf, np.ones(sysm.n), sc,
+                                                          0.5)
+        total = len(oracle.basis.stage_blocks(
+            sysm.A0, c.rank, c.medium, c.node_cell, p.basis,
+            np.concatenate([np.full(g.n_matrix, -1), g.cell_frac]), c.row_net))
+        assert n_solved == solved and 0 < solved < total
         Pg = _gpu_P(ctx, Pu.shape)
         np.testing.assert_array_equal(Pg.indptr, Pu.indptr)
         np.testing.assert_array_equal(Pg.indices, Pu.indices)
@@ -734,18 +747,12 @@ def test_basis_rebuild_matches_oracle(name, restriction):
         assert stats[0]["iterations"] == 13 == ito
         assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
         face, nnc = ctx.flux(xs[0])
-        sfv = oracle.reconstruction_setup(p, g, ur, c)
+        sfv = osolver.setup(ur, Puf, c.primal, c.n_coarse, osolver.R_FV)
         flux, dflux, _, _ = osolver.reconstruct_flux(ur, p, sfv, xs[0], c.primal, c.node_cell)
-        nz = p.nz if p.dim == 3 else 1
-        nfx, nfy = (p.nx + 1) * p.ny * nz, p.nx * (p.ny + 1) * nz
-        parts = [face[:nfx].reshape(nz, p.ny, p.nx + 1)[:, :, 1:-1].ravel(),
-                 face[nfx:nfx + nfy].reshape(nz, p.ny + 1, p.nx)[:, 1:-1, :].ravel()]
-        if p.dim == 3:
-            parts.append(face[nfx + nfy:].reshape(nz + 1, p.ny, p.nx)[1:-1].ravel())
-        conn = np.concatenate(parts + [nnc])
+        conn = _interior_connections(p, face, nnc)
         np.testing.assert_allclose(conn, flux, rtol=0, atol=1e-8 * np.abs(flux).max())
-        assert not ctx.update_basis(sc, 0.01)
-        assert ctx.update_basis(sc, -1.0)
+        assert ctx.update_basis(sc, 0.5) == 0
+        assert ctx.update_basis(sc, -1.0) == total
 
 
 @pytest.mark.parametrize("variant", [0, 3])

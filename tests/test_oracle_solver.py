@@ -442,3 +442,81 @@ def test_sub_block_smoother_converges_to_the_direct_solution(variant):
     g, sysm, c, P, st = oracle.build(p)
     xd = spla.spsolve(sysm.A.tocsc(), sysm.q)
     assert r.converged and np.linalg.norm(r.p - xd) < 1e-6 * np.linalg.norm(xd)
+
+
+def _adaptive_case():
+    p = _small(3, restriction=1)
+    p.alpha = 0.0
+    g, sysm, c, P, st = oracle.build(p)
+    return p, g, sysm, c, P
+
+
+def test_adaptive_update_extremes():
+    """eps < 0 solves every dual block again: the full rebuild; eps = inf
+    solves none: P unchanged."""
+    p, g, sysm, c, P = _adaptive_case()
+    sc = np.random.default_rng(8).uniform(0.5, 2.0, sysm.n)
+    u = assemble.update_mobility(sysm, sc)
+    ref = np.ones(sysm.n)
+    Pa, Pf, ref2, solved = oracle.prolongation_update(p, g, u, c, P, ref, sc, -1.0)
+    assert abs(Pa - oracle.prolongation(p, g, u, c)).max() < 1e-13
+    assert solved == len(basis.stage_blocks(sysm.A0, c.rank, c.medium, c.node_cell, p.basis,
+                                            np.concatenate([np.full(g.n_matrix, -1),
+                                                            g.cell_frac]), c.row_net))
+    Pn, _, ref3, solved = oracle.prolongation_update(p, g, u, c, P, ref, sc, np.inf)
+    assert solved == 0 and abs(Pn - P).max() == 0.0 and (ref3 == 1.0).all()
+
+
+def test_adaptive_update_solves_the_marked_blocks_and_their_downstream():
+    """Scales moved by 10x in a 3x3 patch (eps 0.5): the recomputed rows are
+    exactly the blocks holding a marked cell plus, stage by stage, the blocks
+    that read a recomputed row (an independent closure over the dual-block
+    graph); every other row is the old one; every recomputed row solves its
+    local problem (Eq. 18 with the dropped links on the diagonal) against
+    the final values of the rows it reads; partition of unity holds."""
+    p, g, sysm, c, P = _adaptive_case()
+    nx = p.nx
+    sc = np.ones(sysm.n)
+    patch = [x + nx * y for x in range(9, 12) for y in range(13, 16)]
+    sc[patch] = 10.0
+    u = assemble.update_mobility(sysm, sc)
+    Pa, Pf, ref2, solved = oracle.prolongation_update(p, g, u, c, P, np.ones(sysm.n), sc, 0.5)
+    plate = np.concatenate([np.full(g.n_matrix, -1), g.cell_frac])
+    blocks = basis.stage_blocks(sysm.A0, c.rank, c.medium, c.node_cell, p.basis, plate,
+                                c.row_net, 0, True)
+    A0 = sysm.A0.tocsr()
+
+    def keep(r, q):
+        return basis.keep_link(p.basis, c.medium[r], c.rank[r], c.medium[q], c.rank[q],
+                               basis._cross(plate, c.row_net, r, q))
+    stage_of = {}
+    for si, cells in blocks:
+        for r in cells:
+            stage_of[r] = si
+    rec = np.zeros(sysm.n, bool)
+    for si, cells in blocks:
+        hit = any(r in patch for r in cells) or any(
+            rec[q] and keep(r, q) and stage_of.get(q, -1) != si
+            for r in cells for q in A0.indices[A0.indptr[r]:A0.indptr[r + 1]] if q != r)
+        if hit:
+            rec[cells] = True
+    assert solved > 0 and (ref2 == np.where(rec, sc, 1.0)).all()
+    Pd, Po = Pa.toarray(), P.toarray()
+    np.testing.assert_array_equal(Pd[~rec], Po[~rec])
+    assert abs(Pd[rec] - Po[rec]).max() > 1e-3
+    # each recomputed row solves its local equation with the updated operator
+    U = u.A0.tocsr()
+    for r in np.nonzero(rec)[0]:
+        acc = np.zeros(Pd.shape[1])
+        d = 0.0
+        for k in range(U.indptr[r], U.indptr[r + 1]):
+            q = U.indices[k]
+            a = U.data[k]
+            if q == r:
+                d += a
+            elif keep(r, q):
+                acc += a * Pd[q]
+            else:
+                d += a   # a dropped link leaves the diagonal: A0 row sums are zero
+        np.testing.assert_allclose(d * Pd[r] + acc, 0.0, atol=1e-12 * abs(U).max())
+    np.testing.assert_allclose(Pd.sum(axis=1), 1.0, atol=1e-12)
