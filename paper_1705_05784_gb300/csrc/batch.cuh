@@ -177,6 +177,7 @@ struct Batch {
   double* pk_uv = nullptr;
   double* pk_ud = nullptr;     // reciprocal of the U diagonal
   double* ylev = nullptr;      // sweep right-hand side in level order
+  double* xlev = nullptr;      // base + multiscale correction in level order (U sweep)
   // the sub-block smoothing stage (instances with fams_opts.subblock): ILU(0)
   // of A without its cross-medium entries, in A's pattern and level order
   double* ilu_b = nullptr;
@@ -217,6 +218,7 @@ struct Batch {
   float* dpf = nullptr;
   float* yf = nullptr;
   float* ylevf = nullptr;
+  float* xlevf = nullptr;
   float* krylov32 = nullptr;
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)

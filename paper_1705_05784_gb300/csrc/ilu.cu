@@ -257,6 +257,7 @@ int phase_ilu(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.pk_uv, sizeof(double) * PK * n1));
   FAMS_TRY(b.alloc((void**)&b.pk_ud, sizeof(double) * n1));
   FAMS_TRY(b.alloc((void**)&b.ylev, sizeof(double) * n1));
+  FAMS_TRY(b.alloc((void**)&b.xlev, sizeof(double) * n1));
   if (nrow > 0) {
     fams::note_launch(), k_pos<<<grid_for(nrow, T), T, 0, st>>>(nrow, b.lev_rows, b.pk_pos);
     fams::note_launch(), k_pack<<<grid_for(nrow, T), T, 0, st>>>(

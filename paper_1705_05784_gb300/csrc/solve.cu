@@ -29,8 +29,31 @@ constexpr int SOLVE_T = 512;
 constexpr int ROWS_ILP = 4;
 constexpr int BAND_BUF = 3072;   // doubles per staged chunk of band columns (24 KiB)
 constexpr int CH_MAX = 64;       // band columns per chunk
-constexpr int SWEEP_RING = 4096; // level positions of recent sweep results kept in shared memory
-static_assert(SWEEP_RING <= 2 * BAND_BUF, "the sweep ring lives in the band buffer");
+constexpr int SWEEP_RING = 1024; // level positions of recent sweep results kept in shared memory
+// Rows of the triangular sweeps are copied into shared memory STAGE_D - 1
+// levels ahead of their use (asynchronous copies, no registers held):
+// threads 0..STAGE_W-1 take the first STAGE_W rows of a level, the other
+// threads the rest of a wider level with plain loads.  Per staged row:
+// STAGE_V values (PK factor entries, right-hand side, reciprocal diagonal,
+// the part of the output the U sweep adds to) and STAGE_I integers (PK
+// neighbour positions, entry count, first CSR entry of L or the row of U).
+// Ring and stages fit in the band buffer, so two CTAs per SM still leave
+// about 90 KB of L1 to the sparse products: deeper staging (3 or 4 levels)
+// took the SM's L1 (or the second CTA) and was slower overall.
+constexpr int STAGE_D = 2;
+constexpr int STAGE_W = 256;
+constexpr int STAGE_V = PK + 3;
+constexpr int STAGE_I = PK + 2;
+constexpr int STAGE_SLOTS = STAGE_D * STAGE_W;
+static_assert(SOLVE_T > STAGE_W, "threads beyond the staged rows take the rest of a level");
+// shared memory behind the coarse vectors: the coarse solve's two band
+// chunks, or during the sweeps the ring followed by the staged rows
+constexpr size_t SWEEP_BYTES =
+    SWEEP_RING * sizeof(double) + (size_t)STAGE_SLOTS * (STAGE_V * sizeof(double) + STAGE_I * sizeof(int));
+constexpr size_t BUF_BYTES =
+    SWEEP_BYTES > 2 * BAND_BUF * sizeof(double) ? SWEEP_BYTES : 2 * BAND_BUF * sizeof(double);
+static_assert(BUF_BYTES % sizeof(double) == 0, "the buffer is counted in doubles");
+constexpr int BUF_DOUBLES = (int)(BUF_BYTES / sizeof(double));
 
 __device__ inline double block_sum(double v, double* red) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -104,6 +127,7 @@ struct SolveArgs {
   const double* pk_uvb;
   const double* pk_udb;
   double* ylev;
+  double* xlev;    // level order: the part of the two-stage output the U sweep adds to
   long long ntot;  // rows of the batch (stride of the PK arrays)
   double tol;
   // FP32 copies and work vectors of the mixed-precision inner stages
@@ -120,6 +144,7 @@ struct SolveArgs {
   float* dpf;
   float* yf;
   float* ylevf;
+  float* xlevf;
 };
 
 // the arrays of one arithmetic: FP64 throughout, or the FP32 copies
@@ -134,6 +159,7 @@ template <> struct Prec<double> {
   static __device__ const double* ud(const SolveArgs& a, int set = 0) { return set ? a.pk_udb : a.pk_ud; }
   static __device__ double* y(const SolveArgs& a) { return a.y; }
   static __device__ double* ylev(const SolveArgs& a) { return a.ylev; }
+  static __device__ double* xlev(const SolveArgs& a) { return a.xlev; }
   static __device__ double* dp(const SolveArgs& a) { return a.dp; }
   static __device__ double* z(const SolveArgs& a) { return a.r; }
 };
@@ -148,6 +174,7 @@ template <> struct Prec<float> {
   static __device__ const float* ud(const SolveArgs& a, int = 0) { return a.pk_ud32; }
   static __device__ float* y(const SolveArgs& a) { return a.yf; }
   static __device__ float* ylev(const SolveArgs& a) { return a.ylevf; }
+  static __device__ float* xlev(const SolveArgs& a) { return a.xlevf; }
   static __device__ float* dp(const SolveArgs& a) { return a.dpf; }
   static __device__ float* z(const SolveArgs& a) { return a.zf; }
 };
@@ -354,51 +381,70 @@ __device__ void coarse_solve_blocked(const double* AB, const double* binv, int n
   }
 }
 
-// one row of a triangular sweep, loaded from the level-ordered layout: every
-// address depends only on the position t, so the loads of a whole level are
-// coalesced and independent of the sweep's results
-template <class T>
-struct SweepRow {
-  int t, i, cnt, p;
-  T base, diag;
-  T xo, dpo;   // U sweep: the row's base and multiscale correction, loaded ahead too
-  int c[PK];
-  T f[PK];
-};
+// Asynchronous global -> shared copies of 4 or 8 bytes (cp.async): each
+// thread waits for its own groups only and reads only what it copied itself.
+template <int BYTES>
+__device__ inline void cp_async(void* dst, const void* src) {
+  static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte copies");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Staged rows of a triangular sweep in shared memory, [field][slot], slot =
+// stage * STAGE_W + thread.  v: PK factor entries, then right-hand side,
+// reciprocal diagonal (U) and output part (U); c: PK neighbour positions,
+// then entry count and first CSR entry (L) or row (U).
 template <class T>
-__device__ inline void sweep_load(const SolveArgs& a, const int* lp, int l, int nlev, bool lower,
-                                  SweepRow<T>& s, const T* dpv = nullptr,
-                                  const T* bv = nullptr, int set = 0) {
-  s.t = -1;
-  if (l < 0 || l >= nlev) return;
-  int t = lp[l] + threadIdx.x;
-  if (t >= lp[l + 1]) return;
-  s.t = t;
-  s.i = a.lev_rows[t];
-  s.base = Prec<T>::ylev(a)[t];
-  if (lower) {
-    s.cnt = a.pk_nl[t];
-    s.p = a.pk_lp[t];
-    s.diag = T(1);
-  } else {
-    s.cnt = a.pk_nu[t];
-    s.diag = Prec<T>::ud(a, set)[t];
-    s.dpo = dpv ? dpv[s.i] : T(0);
-    s.xo = bv ? bv[s.i] : T(0);
-  }
-  const int* pc = lower ? a.pk_lc : a.pk_uc;
-  const T* pv = lower ? Prec<T>::lv(a, set) : Prec<T>::uv(a, set);
+struct Stage {
+  T* v;
+  int* c;
+};
+template <class T>
+__device__ inline Stage<T> stage_of(double* buf) {
+  char* p = reinterpret_cast<char*>(buf) + SWEEP_RING * sizeof(double);
+  return Stage<T>{reinterpret_cast<T*>(p),
+                  reinterpret_cast<int*>(p + (size_t)STAGE_V * STAGE_SLOTS * sizeof(T))};
+}
+
+// Copies this thread's row of the level at positions [lo, hi) (none: lo ==
+// hi) into stage slot `stage` and commits one group (empty without a row).
+// Every address depends only on the level position t, so the copies of a
+// whole level are coalesced.
+template <class T, bool LOWER>
+__device__ inline void stage_rows(const SolveArgs& a, int lo, int hi, int set, const Stage<T>& sg,
+                                  int stage) {
+  const int tid = threadIdx.x;
+  const int t = lo + tid;
+  if (tid < STAGE_W && t < hi) {
+    const int sl = stage * STAGE_W + tid;
+    const int* pc = LOWER ? a.pk_lc : a.pk_uc;
+    const T* pv = LOWER ? Prec<T>::lv(a, set) : Prec<T>::uv(a, set);
 #pragma unroll
-  for (int k = 0; k < PK; ++k) {
-    s.c[k] = pc[(long long)k * a.ntot + t];
-    s.f[k] = pv[(long long)k * a.ntot + t];
+    for (int k = 0; k < PK; ++k) {
+      cp_async<4>(sg.c + k * STAGE_SLOTS + sl, pc + (long long)k * a.ntot + t);
+      cp_async<sizeof(T)>(sg.v + k * STAGE_SLOTS + sl, pv + (long long)k * a.ntot + t);
+    }
+    cp_async<sizeof(T)>(sg.v + PK * STAGE_SLOTS + sl, Prec<T>::ylev(a) + t);
+    if (LOWER) {
+      cp_async<4>(sg.c + PK * STAGE_SLOTS + sl, a.pk_nl + t);
+      cp_async<4>(sg.c + (PK + 1) * STAGE_SLOTS + sl, a.pk_lp + t);
+    } else {
+      cp_async<4>(sg.c + PK * STAGE_SLOTS + sl, a.pk_nu + t);
+      cp_async<4>(sg.c + (PK + 1) * STAGE_SLOTS + sl, a.lev_rows + t);
+      cp_async<sizeof(T)>(sg.v + (PK + 1) * STAGE_SLOTS + sl, Prec<T>::ud(a, set) + t);
+      cp_async<sizeof(T)>(sg.v + (PK + 2) * STAGE_SLOTS + sl, Prec<T>::xlev(a) + t);
+    }
   }
+  cp_commit();
 }
 
 // shared-memory layout of the solve kernels (doubles): the coarse vector in
-// band order, the coarse correction in coarse order, two staged chunks of
-// band columns; the GMRES kernel adds its small dense arrays after them
+// band order, the coarse correction in coarse order, BUF_DOUBLES for the
+// band chunks or the sweeps; the GMRES kernel adds its small dense arrays
+// after them
 struct SolveSmem {
   double* yb;
   double* ecs;
@@ -426,7 +472,8 @@ __device__ inline void mark(long long* cyc, int k) {
 // cyc by thread 0):
 //   dp = P A_c^-1 R r;  y = r - A dp (also in level order);
 //   out = (base + dp) + (LU)^-1 y   (base null: out = dp + (LU)^-1 y)
-// out may alias base; r, dp and out must not alias y or ylev.
+// base + dp is kept in level order (xlev) for the U sweep.
+// out may alias base; r, dp and out must not alias y, ylev or xlev.
 template <class T>
 __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const T* r,
                                           T* dp, T* out, const T* base, const SolveSmem& S,
@@ -478,7 +525,8 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   }
   __syncthreads();
   mark(cyc, 2);
-  // dp1 = P e_c
+  // dp1 = P e_c; base + dp1 in level order
+  T* xlev = Prec<T>::xlev(a);
   for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
@@ -487,6 +535,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
         T s = 0;
         for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += pv[p] * (T)S.ecs[a.p_col[p]];
         dp[i] = s;
+        xlev[a.pk_pos[i]] = (base ? base[i] : T(0)) + s;
       }
     }
   }
@@ -497,87 +546,130 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   mark(cyc, 3);
   // step 7, L sweep: y_i = r1_i - sum_{j<i} L_ij y_j, by level position t.
   // Results also go to a shared-memory ring of the last SWEEP_RING
-  // positions (the band buffer, idle during the sweeps): a neighbour from a
-  // recent level is read there, older ones from ylev.  The current level
-  // writes positions [lp[l], lp[l+1]), so a position tc is still in the ring
-  // while tc >= lp[l+1] - SWEEP_RING.
+  // positions: a neighbour from a recent level is read there, older ones
+  // from ylev.  The current level writes positions [lp[l], lp[l+1]), so a
+  // position tc is still in the ring while tc >= lp[l+1] - SWEEP_RING.
+  // Rows are staged STAGE_D - 1 levels ahead (stage_rows); the staging and
+  // the ring use the band buffer, idle during the sweeps.
   // Pass 1 (instances with the sub-block smoothing stage): the same sweeps
   // with the media blocks' factors on r2 = r - A (dp1 + dp2), added to out.
   T* ring = reinterpret_cast<T*>(S.buf);
+  const Stage<T> sg = stage_of<T>(S.buf);
+  const int tid = threadIdx.x;
   const int npass = I.subblock ? 2 : 1;
   for (int pass = 0; pass < npass; ++pass) {
     if (pass == 1) {
-      for (int i = ro + threadIdx.x; i < ro + n; i += NT) dp[i] += y[i];
+      for (int i = ro + tid; i < ro + n; i += NT) dp[i] += y[i];
       __syncthreads();
       rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
       __syncthreads();
     }
     const T* Fs = Prec<T>::F(a, pass);
     const T* uds = Prec<T>::ud(a, pass);
-    SweepRow<T> cur, nxt;
-    sweep_load<T>(a, lp, 0, nlev, true, cur, nullptr, nullptr, pass);
-    for (int l = 0; l < nlev; ++l) {
-      sweep_load<T>(a, lp, l + 1, nlev, true, nxt, nullptr, nullptr, pass);
-      const int lim = lp[l + 1] - SWEEP_RING;
-      auto yv = [&](int tc) { return tc >= lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
-      if (cur.t >= 0) {
-        T s = cur.base;
+    // level bounds in registers: lw[k] = lp[l + k] (clamped to lp[nlev]),
+    // the next one loaded a level ahead
+    int lw[STAGE_D + 1];
 #pragma unroll
-        for (int k = 0; k < PK; ++k)
-          if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
-        for (int p = cur.p + PK; p < cur.p + cur.cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
-        ring[cur.t & (SWEEP_RING - 1)] = s;
-        ylev[cur.t] = s;
-      }
-      for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
-        int i = a.lev_rows[t];
-        T s = ylev[t];
-        for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
-        ring[t & (SWEEP_RING - 1)] = s;
-        ylev[t] = s;
+    for (int k = 0; k <= STAGE_D; ++k) lw[k] = lp[min(k, nlev)];
+#pragma unroll
+    for (int j = 0; j < STAGE_D - 1; ++j) stage_rows<T, true>(a, lw[j], lw[j + 1], pass, sg, j);
+    for (int l = 0; l < nlev; ++l) {
+      const int lnext = lp[min(l + STAGE_D + 1, nlev)];
+      stage_rows<T, true>(a, lw[STAGE_D - 1], lw[STAGE_D], pass, sg, (l + STAGE_D - 1) % STAGE_D);
+      cp_wait<STAGE_D - 1>();
+      const int lo = lw[0], hi = lw[1];
+      const int lim = hi - SWEEP_RING;
+      auto yv = [&](int tc) { return tc >= lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
+      if (tid < STAGE_W) {
+        const int t = lo + tid;
+        if (t < hi) {
+          const int sl = (l % STAGE_D) * STAGE_W + tid;
+          const int cnt = sg.c[PK * STAGE_SLOTS + sl];
+          T s = sg.v[PK * STAGE_SLOTS + sl];
+#pragma unroll
+          for (int k = 0; k < PK; ++k)
+            if (k < cnt) s -= sg.v[k * STAGE_SLOTS + sl] * yv(sg.c[k * STAGE_SLOTS + sl]);
+          if (cnt > PK) {
+            const int p0 = sg.c[(PK + 1) * STAGE_SLOTS + sl];
+            for (int p = p0 + PK; p < p0 + cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+          }
+          ring[t & (SWEEP_RING - 1)] = s;
+          ylev[t] = s;
+        }
+      } else {
+        for (int t = lo + tid; t < hi; t += NT - STAGE_W) {
+          int i = a.lev_rows[t];
+          T s = ylev[t];
+          for (int p = a.rowptr[i]; p < a.diag[i]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+          ring[t & (SWEEP_RING - 1)] = s;
+          ylev[t] = s;
+        }
       }
       __syncthreads();
-      cur = nxt;
+#pragma unroll
+      for (int k = 0; k < STAGE_D; ++k) lw[k] = lw[k + 1];
+      lw[STAGE_D] = lnext;
     }
     mark(cyc, 4);
-    // U sweep and step 8: out = (base + dp1) + dp2 (pass 1: out += dp3); the
-    // ring now holds the upper neighbours, valid while tc < lp[l] + SWEEP_RING
-    const T* bsrc = pass ? out : base;
-    const T* dsrc = pass ? nullptr : dp;
-    sweep_load<T>(a, lp, nlev - 1, nlev, false, cur, dsrc, bsrc, pass);
-    for (int l = nlev - 1; l >= 0; --l) {
-      sweep_load<T>(a, lp, l - 1, nlev, false, nxt, dsrc, bsrc, pass);
-      const int lim = lp[l] + SWEEP_RING;
-      auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
-      if (cur.t >= 0) {
-        T s = cur.base;
-        const T xo = cur.xo, dpo = cur.dpo;
+    // U sweep and step 8: out = xlev + dp2 with xlev = base + dp1 (pass 1:
+    // xlev = pass 0's output).  The ring now holds the upper neighbours,
+    // valid while tc < lp[l] + SWEEP_RING.  Iteration j = nlev - 1 - l uses
+    // stage j % STAGE_D.
+    const bool keep = pass + 1 < npass;   // pass 0's output is pass 1's xlev
+    // uw[k] = lp[l + 1 - k] (clamped to lp[0]) for the current level l
+    int uw[STAGE_D + 1];
 #pragma unroll
-        for (int k = 0; k < PK; ++k)
-          if (k < cur.cnt) s -= cur.f[k] * yv(cur.c[k]);
-        if (cur.cnt > PK) {
-          int d = a.diag[cur.i];
-          for (int p = d + 1 + PK; p <= d + cur.cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+    for (int k = 0; k <= STAGE_D; ++k) uw[k] = lp[max(nlev - k, 0)];
+#pragma unroll
+    for (int j = 0; j < STAGE_D - 1; ++j) stage_rows<T, false>(a, uw[j + 1], uw[j], pass, sg, j);
+    for (int l = nlev - 1, j = 0; l >= 0; --l, ++j) {
+      const int unext = lp[max(l - STAGE_D, 0)];
+      stage_rows<T, false>(a, uw[STAGE_D], uw[STAGE_D - 1], pass, sg, (j + STAGE_D - 1) % STAGE_D);
+      cp_wait<STAGE_D - 1>();
+      const int lo = uw[1], hi = uw[0];
+      const int lim = lo + SWEEP_RING;
+      auto yv = [&](int tc) { return tc < lim ? ring[tc & (SWEEP_RING - 1)] : ylev[tc]; };
+      if (tid < STAGE_W) {
+        const int t = lo + tid;
+        if (t < hi) {
+          const int sl = (j % STAGE_D) * STAGE_W + tid;
+          const int cnt = sg.c[PK * STAGE_SLOTS + sl];
+          const int i = sg.c[(PK + 1) * STAGE_SLOTS + sl];
+          T s = sg.v[PK * STAGE_SLOTS + sl];
+#pragma unroll
+          for (int k = 0; k < PK; ++k)
+            if (k < cnt) s -= sg.v[k * STAGE_SLOTS + sl] * yv(sg.c[k * STAGE_SLOTS + sl]);
+          if (cnt > PK) {
+            const int d = a.diag[i];
+            for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+          }
+          const T xi = s * sg.v[(PK + 1) * STAGE_SLOTS + sl];   // reciprocal of U's diagonal
+          const T o = sg.v[(PK + 2) * STAGE_SLOTS + sl] + xi;
+          ring[t & (SWEEP_RING - 1)] = xi;
+          ylev[t] = xi;
+          y[i] = xi;
+          out[i] = o;
+          if (keep) xlev[t] = o;
         }
-        T xi = s * cur.diag;   // reciprocal of U's diagonal
-        ring[cur.t & (SWEEP_RING - 1)] = xi;
-        ylev[cur.t] = xi;
-        y[cur.i] = xi;
-        out[cur.i] = (xo + dpo) + xi;
-      }
-      for (int t = lp[l] + threadIdx.x + NT; t < lp[l + 1]; t += NT) {
-        int i = a.lev_rows[t];
-        int d = a.diag[i];
-        T s = ylev[t];
-        for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
-        T xi = s * uds[t];
-        ring[t & (SWEEP_RING - 1)] = xi;
-        ylev[t] = xi;
-        y[i] = xi;
-        out[i] = ((bsrc ? bsrc[i] : T(0)) + (dsrc ? dsrc[i] : T(0))) + xi;
+      } else {
+        for (int t = lo + tid; t < hi; t += NT - STAGE_W) {
+          int i = a.lev_rows[t];
+          int d = a.diag[i];
+          T s = ylev[t];
+          for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
+          const T xi = s * uds[t];
+          const T o = xlev[t] + xi;
+          ring[t & (SWEEP_RING - 1)] = xi;
+          ylev[t] = xi;
+          y[i] = xi;
+          out[i] = o;
+          if (keep) xlev[t] = o;
+        }
       }
       __syncthreads();
-      cur = nxt;
+#pragma unroll
+      for (int k = 0; k < STAGE_D; ++k) uw[k] = uw[k + 1];
+      uw[STAGE_D] = unext;
     }
   }
   mark(cyc, 5);
@@ -928,7 +1020,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
   const int n = I.n, ro = I.row_off, m = I.restart;
   const SolveSmem S = solve_smem(sm, I.nc, pbuf);
   GmresSmem G;
-  G.H = sm + 2 * I.nc + 2 * BAND_BUF;
+  G.H = sm + 2 * I.nc + BUF_DOUBLES;
   G.g = G.H + (m + 1) * m;
   G.cs = G.g + (m + 1);
   G.sn = G.cs + m;
@@ -1023,7 +1115,7 @@ int phase_alloc_work(Batch& b) {
     FAMS_TRY(b.alloc((void**)&b.pk_lv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_uv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_ud32, sizeof(float) * n1));
-    for (float** v : {&b.rf, &b.zf, &b.dpf, &b.yf, &b.ylevf})
+    for (float** v : {&b.rf, &b.zf, &b.dpf, &b.yf, &b.ylevf, &b.xlevf})
       FAMS_TRY(b.alloc((void**)v, sizeof(float) * n1));
     FAMS_TRY(b.alloc((void**)&b.xs, sizeof(double) * n1));
     auto round = [&](const double* src, float* dst, long long cnt) {
@@ -1082,12 +1174,13 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
   a.pk_nu = b.pk_nu; a.pk_uc = b.pk_uc; a.pk_uv = b.pk_uv; a.pk_ud = b.pk_ud;
   a.Fb = b.ilu_b; a.pk_lvb = b.pk_lv_b; a.pk_uvb = b.pk_uv_b; a.pk_udb = b.pk_ud_b;
-  a.ylev = b.ylev;
+  a.ylev = b.ylev; a.xlev = b.xlev;
   a.ntot = b.tot_row;
   a.tol = tol;
   a.val32 = b.val32; a.p_val32 = b.p_val32; a.pt_val32 = b.pt_val32; a.F32 = b.ilu32;
   a.pk_lv32 = b.pk_lv32; a.pk_uv32 = b.pk_uv32; a.pk_ud32 = b.pk_ud32;
   a.xs = b.xs; a.rf = b.rf; a.zf = b.zf; a.dpf = b.dpf; a.yf = b.yf; a.ylevf = b.ylevf;
+  a.xlevf = b.xlevf;
   int maxnc = 0;
   for (auto& I : b.h) maxnc = std::max(maxnc, I.nc);
   for (int i = 0; i < b.B; ++i)
@@ -1095,7 +1188,7 @@ int run_solve(Batch& b, double tol, float* ms) {
       set_error("coarse band wider than the staged band buffer");
       return FAMS_ECAPACITY;
     }
-  size_t smem = sizeof(double) * (2 * (size_t)maxnc + 2 * BAND_BUF);
+  size_t smem = sizeof(double) * (2 * (size_t)maxnc + BUF_DOUBLES);
   int mr = 0, nrich = 0, ngm = 0;
   for (auto& I : b.h) {
     mr = std::max(mr, I.restart);
@@ -1134,7 +1227,7 @@ int run_solve(Batch& b, double tol, float* ms) {
 // The same iteration with its work vectors in a fixed device array, for
 // callers that cannot allocate device memory when they solve.  Layout in
 // doubles, every part starting on a 256-byte boundary:
-//   q, x, r, dp, y, ylev   STATIC_ROWS each
+//   q, x, r, dp, y, ylev, xlev   STATIC_ROWS each
 //   crhs, csol             STATIC_COARSE each
 //   stat                   STATIC_STAT (STAT_W used)
 //   hist                   STATIC_HIST
@@ -1143,7 +1236,7 @@ constexpr long long STATIC_ROWS = FAMS_STATIC_MAX_ROWS;
 constexpr long long STATIC_COARSE = FAMS_STATIC_MAX_COARSE;
 constexpr long long STATIC_STAT = 32;
 constexpr long long STATIC_HIST = (long long)FAMS_STATIC_MAX_ITER + 1;
-constexpr long long STATIC_DOUBLES = 6 * STATIC_ROWS + 2 * STATIC_COARSE + STATIC_STAT + STATIC_HIST;
+constexpr long long STATIC_DOUBLES = 7 * STATIC_ROWS + 2 * STATIC_COARSE + STATIC_STAT + STATIC_HIST;
 static_assert(STATIC_ROWS % 32 == 0 && STATIC_COARSE % 32 == 0 && STATIC_STAT % 32 == 0,
               "parts of the static work array must stay 256-byte aligned");
 static_assert(STATIC_STAT >= STAT_W, "status words do not fit");
@@ -1190,7 +1283,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
     set_error("coarse band wider than the staged band buffer");
     return FAMS_ECAPACITY;
   }
-  size_t smem = sizeof(double) * (2 * (size_t)I.nc + 2 * BAND_BUF);
+  size_t smem = sizeof(double) * (2 * (size_t)I.nc + BUF_DOUBLES);
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   if ((long long)smem + 3072 > max_smem) {
@@ -1202,7 +1295,7 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
   double* q = w;
   double* xs = w + STATIC_ROWS;
   double* dp = w + 3 * STATIC_ROWS;
-  double* stat = w + 6 * STATIC_ROWS + 2 * STATIC_COARSE;
+  double* stat = w + 7 * STATIC_ROWS + 2 * STATIC_COARSE;
 
   SolveArgs a{};
   a.inst = b.d_inst;
@@ -1214,7 +1307,8 @@ int solve_static_on_device(Batch& b, const double* rhs, double* x, double tol, f
   a.F = b.ilu; a.lev_off = b.lev_off; a.lev_ptr = b.lev_ptr; a.lev_rows = b.lev_rows;
   a.q = q; a.x = xs; a.r = w + 2 * STATIC_ROWS; a.dp = dp; a.y = w + 4 * STATIC_ROWS;
   a.ylev = w + 5 * STATIC_ROWS;
-  a.crhs = w + 6 * STATIC_ROWS; a.csol = w + 6 * STATIC_ROWS + STATIC_COARSE;
+  a.xlev = w + 6 * STATIC_ROWS;
+  a.crhs = w + 7 * STATIC_ROWS; a.csol = w + 7 * STATIC_ROWS + STATIC_COARSE;
   a.stat = stat;
   a.hist = stat + STATIC_STAT; a.hist_len = STATIC_HIST;
   a.pk_pos = b.pk_pos; a.pk_nl = b.pk_nl; a.pk_lp = b.pk_lp; a.pk_lc = b.pk_lc; a.pk_lv = b.pk_lv;
