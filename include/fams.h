@@ -38,8 +38,11 @@ enum { FAMS_DECOUPLED = 0, FAMS_FRAC = 1, FAMS_ROCK = 2, FAMS_COUPLED = 3 };
    element (P^T), or MSMIX: P^T rows for the matrix coarse nodes and
    indicator rows for the fracture coarse nodes */
 enum { FAMS_R_FV = 0, FAMS_R_FE = 1, FAMS_R_MIX = 2 };
-/* arithmetic of the iteration: FP64 throughout, or FP32 inner stages with
-   FP64 outer residual, coarse solve and refinement */
+/* arithmetic of the iteration: FP64 throughout, or mixed: the two-stage
+   step's restriction, prolongation and ILU(0) sweeps in FP32 (FP32 copies of
+   P, P^T and the factors), with the residuals, r - A dp1, the coarse solve,
+   the GMRES basis and the iterate in FP64 (iterative refinement; flexible
+   GMRES with FP64 restart vectors) */
 enum { FAMS_FP64 = 0, FAMS_MIXED = 1 };
 /* outer iteration: the Table 1 loop, or GMRES with the two-stage step as
    right preconditioner (Sec. 4.5, 4.6) */

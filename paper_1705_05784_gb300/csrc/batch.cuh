@@ -203,9 +203,9 @@ struct Batch {
   void* gbar = nullptr;
   double* gpart = nullptr;
   int gpart_n = 0;
-  // mixed precision: FP32 copies of A, P, P^T and the ILU(0) factors (plain
-  // and level-ordered), FP32 work vectors and GMRES bases
-  float* val32 = nullptr;
+  // mixed precision: FP32 copies of P, P^T and the ILU(0) factors (plain and
+  // level-ordered), the saved iterate, the FP32 sweep vectors and the FP64
+  // restart vectors Z of flexible GMRES
   float* p_val32 = nullptr;
   float* pt_val32 = nullptr;
   float* ilu32 = nullptr;
@@ -213,13 +213,9 @@ struct Batch {
   float* pk_uv32 = nullptr;
   float* pk_ud32 = nullptr;
   double* xs = nullptr;
-  float* rf = nullptr;
-  float* zf = nullptr;
-  float* dpf = nullptr;
   float* yf = nullptr;
   float* ylevf = nullptr;
-  float* xlevf = nullptr;
-  float* krylov32 = nullptr;
+  double* krylov_z = nullptr;
   long long hist_len = 0;      // max_iter + 1 of the batch
   // flux (FV coarse factor built on first use)
   bool fv_ready = false;       // R^FV coarse system current

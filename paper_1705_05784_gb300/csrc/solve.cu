@@ -34,22 +34,23 @@ constexpr int SWEEP_RING = 1024; // level positions of recent sweep results kept
 // levels ahead of their use (asynchronous copies, no registers held):
 // threads 0..STAGE_W-1 take the first STAGE_W rows of a level, the other
 // threads the rest of a wider level with plain loads.  Per staged row:
-// STAGE_V values (PK factor entries, right-hand side, reciprocal diagonal,
-// the part of the output the U sweep adds to) and STAGE_I integers (PK
-// neighbour positions, entry count, first CSR entry of L or the row of U).
+// STAGE_V values in the sweep's arithmetic (PK factor entries, right-hand
+// side, reciprocal diagonal), the FP64 part of the output the U sweep adds
+// to, and STAGE_I integers (PK neighbour positions, entry count, first CSR
+// entry of L or the row of U).
 // Ring and stages fit in the band buffer, so two CTAs per SM still leave
 // about 90 KB of L1 to the sparse products: deeper staging (3 or 4 levels)
 // took the SM's L1 (or the second CTA) and was slower overall.
 constexpr int STAGE_D = 2;
 constexpr int STAGE_W = 256;
-constexpr int STAGE_V = PK + 3;
+constexpr int STAGE_V = PK + 2;
 constexpr int STAGE_I = PK + 2;
 constexpr int STAGE_SLOTS = STAGE_D * STAGE_W;
 static_assert(SOLVE_T > STAGE_W, "threads beyond the staged rows take the rest of a level");
 // shared memory behind the coarse vectors: the coarse solve's two band
 // chunks, or during the sweeps the ring followed by the staged rows
-constexpr size_t SWEEP_BYTES =
-    SWEEP_RING * sizeof(double) + (size_t)STAGE_SLOTS * (STAGE_V * sizeof(double) + STAGE_I * sizeof(int));
+constexpr size_t SWEEP_BYTES = SWEEP_RING * sizeof(double) +
+    (size_t)STAGE_SLOTS * ((STAGE_V + 1) * sizeof(double) + STAGE_I * sizeof(int));
 constexpr size_t BUF_BYTES =
     SWEEP_BYTES > 2 * BAND_BUF * sizeof(double) ? SWEEP_BYTES : 2 * BAND_BUF * sizeof(double);
 static_assert(BUF_BYTES % sizeof(double) == 0, "the buffer is counted in doubles");
@@ -131,7 +132,6 @@ struct SolveArgs {
   long long ntot;  // rows of the batch (stride of the PK arrays)
   double tol;
   // FP32 copies and work vectors of the mixed-precision inner stages
-  const float* val32;
   const float* p_val32;
   const float* pt_val32;
   const float* F32;
@@ -139,18 +139,13 @@ struct SolveArgs {
   const float* pk_uv32;
   const float* pk_ud32;
   double* xs;     // iterate saved before an FP32 cycle
-  float* rf;      // residual rounded to FP32
-  float* zf;      // preconditioned vector
-  float* dpf;
   float* yf;
   float* ylevf;
-  float* xlevf;
 };
 
 // the arrays of one arithmetic: FP64 throughout, or the FP32 copies
 template <class T> struct Prec;
 template <> struct Prec<double> {
-  static __device__ const double* val(const SolveArgs& a) { return a.val; }
   static __device__ const double* pv(const SolveArgs& a) { return a.p_val; }
   static __device__ const double* ptv(const SolveArgs& a) { return a.pt_val; }
   static __device__ const double* F(const SolveArgs& a, int set = 0) { return set ? a.Fb : a.F; }
@@ -159,12 +154,8 @@ template <> struct Prec<double> {
   static __device__ const double* ud(const SolveArgs& a, int set = 0) { return set ? a.pk_udb : a.pk_ud; }
   static __device__ double* y(const SolveArgs& a) { return a.y; }
   static __device__ double* ylev(const SolveArgs& a) { return a.ylev; }
-  static __device__ double* xlev(const SolveArgs& a) { return a.xlev; }
-  static __device__ double* dp(const SolveArgs& a) { return a.dp; }
-  static __device__ double* z(const SolveArgs& a) { return a.r; }
 };
 template <> struct Prec<float> {
-  static __device__ const float* val(const SolveArgs& a) { return a.val32; }
   static __device__ const float* pv(const SolveArgs& a) { return a.p_val32; }
   static __device__ const float* ptv(const SolveArgs& a) { return a.pt_val32; }
   // (the sub-block stage runs in FP64 only: set 1 is never asked for here)
@@ -174,22 +165,21 @@ template <> struct Prec<float> {
   static __device__ const float* ud(const SolveArgs& a, int = 0) { return a.pk_ud32; }
   static __device__ float* y(const SolveArgs& a) { return a.yf; }
   static __device__ float* ylev(const SolveArgs& a) { return a.ylevf; }
-  static __device__ float* xlev(const SolveArgs& a) { return a.xlevf; }
-  static __device__ float* dp(const SolveArgs& a) { return a.dpf; }
-  static __device__ float* z(const SolveArgs& a) { return a.zf; }
 };
 
-// y[i] = b[i] - sum_p val[p] v[col[p]] for the instance's rows, four rows per
-// thread in flight; returns this thread's sum of y^2 when `norm`
-template <class T>
-__device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const T* b, const T* v,
-                                       T* y, bool norm, T* ylev = nullptr) {
-  const T* val = Prec<T>::val(a);
-  T acc = 0;
+// y[i] = b[i] - sum_p val[p] v[col[p]] in FP64 for the instance's rows, four
+// rows per thread in flight; y (and ylev, in level order) are stored in the
+// arithmetic TO of their consumer.  Returns this thread's sum of y^2 when
+// `norm`.
+template <class TO>
+__device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const double* b,
+                                       const double* v, TO* y, bool norm, TO* ylev = nullptr) {
+  const double* val = a.val;
+  double acc = 0;
   const int NT = blockDim.x;
   for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
     int rs[ROWS_ILP], re[ROWS_ILP];
-    T s[ROWS_ILP];
+    double s[ROWS_ILP];
     int m = 0;
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
@@ -197,7 +187,7 @@ __device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const 
       bool ok = i < ro + n;
       rs[k] = ok ? a.rowptr[i] : 0;
       re[k] = ok ? a.rowptr[i + 1] : 0;
-      s[k] = ok ? b[i] : T(0);
+      s[k] = ok ? b[i] : 0.0;
       m = max(m, re[k] - rs[k]);
     }
     for (int e = 0; e < m; ++e) {
@@ -211,13 +201,13 @@ __device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const 
     for (int k = 0; k < ROWS_ILP; ++k) {
       int i = i0 + k * NT;
       if (i < ro + n) {
-        y[i] = s[k];
-        if (ylev) ylev[a.pk_pos[i]] = s[k];
+        y[i] = (TO)s[k];
+        if (ylev) ylev[a.pk_pos[i]] = (TO)s[k];
         if (norm) acc += s[k] * s[k];
       }
     }
   }
-  return (double)acc;
+  return acc;
 }
 
 // Coarse band solve (LAPACK gbtrs steps on the band factors).  Warps
@@ -394,19 +384,21 @@ template <int N>
 __device__ inline void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Staged rows of a triangular sweep in shared memory, [field][slot], slot =
-// stage * STAGE_W + thread.  v: PK factor entries, then right-hand side,
-// reciprocal diagonal (U) and output part (U); c: PK neighbour positions,
-// then entry count and first CSR entry (L) or row (U).
+// stage * STAGE_W + thread.  x: the FP64 output part (U); v: PK factor
+// entries, then right-hand side and reciprocal diagonal (U); c: PK neighbour
+// positions, then entry count and first CSR entry (L) or row (U).
 template <class T>
 struct Stage {
+  double* x;
   T* v;
   int* c;
 };
 template <class T>
 __device__ inline Stage<T> stage_of(double* buf) {
   char* p = reinterpret_cast<char*>(buf) + SWEEP_RING * sizeof(double);
-  return Stage<T>{reinterpret_cast<T*>(p),
-                  reinterpret_cast<int*>(p + (size_t)STAGE_V * STAGE_SLOTS * sizeof(T))};
+  char* pv = p + (size_t)STAGE_SLOTS * sizeof(double);
+  return Stage<T>{reinterpret_cast<double*>(p), reinterpret_cast<T*>(pv),
+                  reinterpret_cast<int*>(pv + (size_t)STAGE_V * STAGE_SLOTS * sizeof(T))};
 }
 
 // Copies this thread's row of the level at positions [lo, hi) (none: lo ==
@@ -435,7 +427,7 @@ __device__ inline void stage_rows(const SolveArgs& a, int lo, int hi, int set, c
       cp_async<4>(sg.c + PK * STAGE_SLOTS + sl, a.pk_nu + t);
       cp_async<4>(sg.c + (PK + 1) * STAGE_SLOTS + sl, a.lev_rows + t);
       cp_async<sizeof(T)>(sg.v + (PK + 1) * STAGE_SLOTS + sl, Prec<T>::ud(a, set) + t);
-      cp_async<sizeof(T)>(sg.v + (PK + 2) * STAGE_SLOTS + sl, Prec<T>::xlev(a) + t);
+      cp_async<8>(sg.x + sl, a.xlev + t);
     }
   }
   cp_commit();
@@ -475,9 +467,9 @@ __device__ inline void mark(long long* cyc, int k) {
 // base + dp is kept in level order (xlev) for the U sweep.
 // out may alias base; r, dp and out must not alias y, ylev or xlev.
 template <class T>
-__device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const T* r,
-                                          T* dp, T* out, const T* base, const SolveSmem& S,
-                                          long long* cyc) {
+__device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const double* r,
+                                          double* dp, double* out, const double* base,
+                                          const SolveSmem& S, long long* cyc) {
   const int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
   const double* AB = a.cs.band + a.cs.band_off[ii];
   const int* ipiv = a.cs.ipiv + co;
@@ -501,9 +493,9 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       T s = 0;
       // MSMIX: P^T rows for the matrix coarse nodes, indicators for the fracture ones
       if (I.restriction == FAMS_R_FE || (I.restriction == FAMS_R_MIX && perm[k] < I.ncm)) {
-        for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += ptv[p] * r[a.pt_col[p]];
+        for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += ptv[p] * (T)r[a.pt_col[p]];
       } else {
-        for (int p = a.blk_ptr[c] + lane; p < a.blk_ptr[c + 1]; p += 32) s += r[a.blk_cell[p]];
+        for (int p = a.blk_ptr[c] + lane; p < a.blk_ptr[c + 1]; p += 32) s += (T)r[a.blk_cell[p]];
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -525,8 +517,8 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   }
   __syncthreads();
   mark(cyc, 2);
-  // dp1 = P e_c; base + dp1 in level order
-  T* xlev = Prec<T>::xlev(a);
+  // dp1 = P e_c (arithmetic T, stored FP64); base + dp1 in level order
+  double* xlev = a.xlev;
   for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
@@ -534,13 +526,14 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       if (i < ro + n) {
         T s = 0;
         for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += pv[p] * (T)S.ecs[a.p_col[p]];
-        dp[i] = s;
-        xlev[a.pk_pos[i]] = (base ? base[i] : T(0)) + s;
+        dp[i] = (double)s;
+        xlev[a.pk_pos[i]] = (base ? base[i] : 0.0) + (double)s;
       }
     }
   }
   __syncthreads();
-  // step 6: r1 = r - A dp1, stored in y (natural order) and ylev (level order)
+  // step 6: r1 = r - A dp1 in FP64 (the difference of two nearly equal
+  // vectors), stored in y (natural order) and ylev (level order) in T
   rows_residual<T>(a, ro, n, r, dp, y, false, ylev);
   __syncthreads();
   mark(cyc, 3);
@@ -644,7 +637,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
             for (int p = d + 1 + PK; p <= d + cnt; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
           }
           const T xi = s * sg.v[(PK + 1) * STAGE_SLOTS + sl];   // reciprocal of U's diagonal
-          const T o = sg.v[(PK + 2) * STAGE_SLOTS + sl] + xi;
+          const double o = sg.x[sl] + (double)xi;
           ring[t & (SWEEP_RING - 1)] = xi;
           ylev[t] = xi;
           y[i] = xi;
@@ -658,7 +651,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
           T s = ylev[t];
           for (int p = d + 1; p < a.rowptr[i + 1]; ++p) s -= Fs[p] * yv(a.pk_pos[a.col[p]]);
           const T xi = s * uds[t];
-          const T o = xlev[t] + xi;
+          const double o = xlev[t] + (double)xi;
           ring[t & (SWEEP_RING - 1)] = xi;
           ylev[t] = xi;
           y[i] = xi;
@@ -737,15 +730,10 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     mark(cyc, 0);
     if (s_done) break;
     // steps 5-8: p = p + dp1 + dp2
-    if (!use32) {
+    if (!use32)
       two_stage<double>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
-    } else {
-      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)a.r[i];
-      __syncthreads();
-      two_stage<float>(a, I, ii, a.rf, a.dpf, a.zf, nullptr, S, cyc);
-      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.x[i] += (double)a.zf[i];
-      __syncthreads();
-    }
+    else
+      two_stage<float>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
     ++it;
   }
   write_stats(a, ii, it, rel, qn, cyc);
@@ -754,15 +742,14 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
 // GMRES helpers on the vectors of one instance (rows [ro, ro + n)); every
 // reduction has a fixed order, so results do not depend on the batch
 
-// y = A v; returns this thread's sum of y^2
-template <class T>
-__device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const T* v, T* y) {
-  const T* val = Prec<T>::val(a);
-  T acc = 0;
+// y = A v (FP64); returns this thread's sum of y^2
+__device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const double* v, double* y) {
+  const double* val = a.val;
+  double acc = 0;
   const int NT = blockDim.x;
   for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
     int rs[ROWS_ILP], re[ROWS_ILP];
-    T s[ROWS_ILP];
+    double s[ROWS_ILP];
     int m = 0;
 #pragma unroll
     for (int k = 0; k < ROWS_ILP; ++k) {
@@ -789,47 +776,8 @@ __device__ inline double rows_apply(const SolveArgs& a, int ro, int n, const T* 
       }
     }
   }
-  return (double)acc;
-}
-
-// y = A z for an FP32 vector z, in FP64 (z is widened exactly); returns this
-// thread's sum of y^2
-__device__ inline double rows_apply_wide(const SolveArgs& a, int ro, int n, const float* z,
-                                         double* y) {
-  double acc = 0.0;
-  const int NT = blockDim.x;
-  for (int i0 = ro + threadIdx.x; i0 < ro + n; i0 += ROWS_ILP * NT) {
-    int rs[ROWS_ILP], re[ROWS_ILP];
-    double s[ROWS_ILP];
-    int m = 0;
-#pragma unroll
-    for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * NT;
-      bool ok = i < ro + n;
-      rs[k] = ok ? a.rowptr[i] : 0;
-      re[k] = ok ? a.rowptr[i + 1] : 0;
-      s[k] = 0.0;
-      m = max(m, re[k] - rs[k]);
-    }
-    for (int e = 0; e < m; ++e) {
-#pragma unroll
-      for (int k = 0; k < ROWS_ILP; ++k) {
-        int p = rs[k] + e;
-        if (p < re[k]) s[k] += a.val[p] * (double)z[a.col[p]];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < ROWS_ILP; ++k) {
-      int i = i0 + k * NT;
-      if (i < ro + n) {
-        y[i] = s[k];
-        acc += s[k] * s[k];
-      }
-    }
-  }
   return acc;
 }
-
 
 constexpr double MIXED_MIN_GAIN = 0.1;   // FP32 cycle: least FP64 residual reduction kept
 
@@ -847,17 +795,17 @@ struct GmresSmem {
 // One GMRES(m) cycle from the residual in a.r (norm beta), ending with
 // x += M^-1 V y.  `it` counts preconditioner applications.
 //
-// mixed = true: flexible GMRES with the two-stage step in FP32.  The basis V,
-// w = A z and the Gram-Schmidt passes stay FP64; each V_k is rounded to FP32
-// for the two-stage step and its output z_k is kept (Z, FP32), so that
-// A Z = V H holds in FP64 whatever the FP32 rounding did to the
-// preconditioner, and the cycle ends with x += Z y (no further
-// preconditioner application).  FP32 vectors cannot hold smooth pressure
-// fields to more than a few digits of their cell-to-cell differences, which
-// is why only the preconditioner, whose output the residual never depends on
-// through FP32 arithmetic, runs there.
+// mixed = true: flexible GMRES with the two-stage step's restriction,
+// prolongation and ILU(0) sweeps in FP32 (two_stage<float>).  The basis V,
+// w = A z, the Gram-Schmidt passes, r1 = r - A dp1 and the coarse solve stay
+// FP64, and each output z_k is kept in FP64 (Z), so that A Z = V H holds in
+// FP64 whatever the FP32 rounding did to the preconditioner; the cycle ends
+// with x += Z y (no further preconditioner application).  Rounding z_k or r1
+// to FP32 would cost the high-contrast instances their convergence: with
+// k_f / k_m up to 1e8, A applied to an FP32 rounding error of z is as large
+// as A z itself.
 template <bool mixed>
-__device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V, float* Z,
+__device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V, double* Z,
                             double beta, double qn, int& it, const SolveSmem& S,
                             const GmresSmem& G, long long* cyc) {
   const int n = I.n, ro = I.row_off, m = I.restart;
@@ -876,16 +824,14 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
     double* w = V + (long long)(k + 1) * ld;
     double acc;
     if constexpr (mixed) {
-      float* Zk = Z + (long long)k * ld;
-      for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.rf[i] = (float)Vk[i];
-      __syncthreads();
-      two_stage<float>(a, I, ii, a.rf, a.dpf, Zk, nullptr, S, cyc);
+      double* Zk = Z + (long long)k * ld;
+      two_stage<float>(a, I, ii, Vk, a.dp, Zk, nullptr, S, cyc);
       stamp(cyc);
-      acc = rows_apply_wide(a, ro, n, Zk, w);
+      acc = rows_apply(a, ro, n, Zk, w);
     } else {
       two_stage<double>(a, I, ii, Vk, a.dp, a.r, nullptr, S, cyc);
       stamp(cyc);
-      acc = rows_apply<double>(a, ro, n, a.r, w);
+      acc = rows_apply(a, ro, n, a.r, w);
     }
     (void)acc;
     // modified Gram-Schmidt, as in the oracle: for i = 0..k, h_i = V_i . w,
@@ -978,7 +924,7 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
     // x += Z y
     for (int i = ro + threadIdx.x; i < ro + n; i += NT) {
       double s = 0.0;
-      for (int j = 0; j < k; ++j) s += G.yv[j] * (double)Z[(long long)j * ld + i];
+      for (int j = 0; j < k; ++j) s += G.yv[j] * Z[(long long)j * ld + i];
       a.x[i] += s;
     }
     __syncthreads();
@@ -1009,7 +955,7 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
 // MIXED_MIN_GAIN marks FP32 as too coarse for this instance: the cycle is
 // undone if the residual grew, and the instance continues with the FP64
 // two-stage step.
-__global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64, float* kry32) {
+__global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry, double* kryz) {
   extern __shared__ double sm[];
   __shared__ double red[40];
   __shared__ int s_done;
@@ -1051,9 +997,9 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry64
     if (use32) {
       for (int i = ro + threadIdx.x; i < ro + n; i += NT) a.xs[i] = a.x[i];
       __syncthreads();
-      gmres_cycle<true>(a, I, ii, kry64, kry32, beta, qn, it, S, G, cyc);
+      gmres_cycle<true>(a, I, ii, kry, kryz, beta, qn, it, S, G, cyc);
     } else {
-      gmres_cycle<false>(a, I, ii, kry64, nullptr, beta, qn, it, S, G, cyc);
+      gmres_cycle<false>(a, I, ii, kry, nullptr, beta, qn, it, S, G, cyc);
     }
     stamp(cyc);
     acc = rows_residual<double>(a, ro, n, a.q, a.x, a.r, true);
@@ -1091,37 +1037,34 @@ int phase_alloc_work(Batch& b) {
   FAMS_TRY(b.alloc((void**)&b.rc, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.ec, sizeof(double) * (b.tot_nc + 1)));
   FAMS_TRY(b.alloc((void**)&b.hist, sizeof(double) * b.hist_len * b.B));
-  // GMRES bases: (restart + 1) vectors indexed like the batch rows, in the
-  // arithmetic of the instances that use them
-  // (a mixed-precision instance may fall back to FP64 GMRES)
-  int mr64 = 0, mr32 = 0;
+  // GMRES bases: (restart + 1) vectors V indexed like the batch rows, and for
+  // the mixed-precision instances the restart vectors Z of flexible GMRES
+  int mr = 0, mrz = 0;
   bool mixed = false;
   for (auto& I : b.h) {
     bool m32 = I.precision == FAMS_MIXED;
     mixed |= m32;
-    mr64 = std::max(mr64, I.restart);
-    if (m32) mr32 = std::max(mr32, I.restart);
+    mr = std::max(mr, I.restart);
+    if (m32 && I.krylov == FAMS_KRYLOV_GMRES) mrz = std::max(mrz, I.restart);
   }
-  if (mr64 > 0)
-    FAMS_TRY(b.alloc((void**)&b.krylov, sizeof(double) * (size_t)(mr64 + 1) * (size_t)(n + 1)));
-  if (mr32 > 0)
-    FAMS_TRY(b.alloc((void**)&b.krylov32, sizeof(float) * (size_t)(mr32 + 1) * (size_t)(n + 1)));
+  if (mr > 0)
+    FAMS_TRY(b.alloc((void**)&b.krylov, sizeof(double) * (size_t)(mr + 1) * (size_t)(n + 1)));
+  if (mrz > 0)
+    FAMS_TRY(b.alloc((void**)&b.krylov_z, sizeof(double) * (size_t)mrz * (size_t)(n + 1)));
   if (mixed) {
     const long long n1 = n + 1, nnz = b.tot_nnz, pn = b.tot_pnnz;
-    FAMS_TRY(b.alloc((void**)&b.val32, sizeof(float) * (nnz + 1)));
     FAMS_TRY(b.alloc((void**)&b.ilu32, sizeof(float) * (nnz + 1)));
     FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (pn + 1)));
     FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (pn + 1)));
     FAMS_TRY(b.alloc((void**)&b.pk_lv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_uv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_ud32, sizeof(float) * n1));
-    for (float** v : {&b.rf, &b.zf, &b.dpf, &b.yf, &b.ylevf, &b.xlevf})
+    for (float** v : {&b.yf, &b.ylevf})
       FAMS_TRY(b.alloc((void**)v, sizeof(float) * n1));
     FAMS_TRY(b.alloc((void**)&b.xs, sizeof(double) * n1));
     auto round = [&](const double* src, float* dst, long long cnt) {
       if (cnt > 0) fams::note_launch(), k_round<<<grid_for(cnt, 256), 256, 0, b.stream>>>(cnt, src, dst);
     };
-    round(b.val, b.val32, nnz);
     round(b.ilu, b.ilu32, nnz);
     round(b.p_val, b.p_val32, pn);
     round(b.pt_val, b.pt_val32, pn);
@@ -1135,12 +1078,11 @@ int phase_alloc_work(Batch& b) {
 
 // FP32 copies of the operators after their FP64 values changed
 int refresh_mixed(Batch& b) {
-  if (!b.val32) return FAMS_OK;
+  if (!b.ilu32) return FAMS_OK;
   const long long n1 = b.tot_row + 1, nnz = b.tot_nnz;
   auto round = [&](const double* src, float* dst, long long cnt) {
     if (cnt > 0) fams::note_launch(), k_round<<<grid_for(cnt, 256), 256, 0, b.stream>>>(cnt, src, dst);
   };
-  round(b.val, b.val32, nnz);
   round(b.ilu, b.ilu32, nnz);
   round(b.pk_lv, b.pk_lv32, PK * n1);
   round(b.pk_uv, b.pk_uv32, PK * n1);
@@ -1177,10 +1119,9 @@ int run_solve(Batch& b, double tol, float* ms) {
   a.ylev = b.ylev; a.xlev = b.xlev;
   a.ntot = b.tot_row;
   a.tol = tol;
-  a.val32 = b.val32; a.p_val32 = b.p_val32; a.pt_val32 = b.pt_val32; a.F32 = b.ilu32;
+  a.p_val32 = b.p_val32; a.pt_val32 = b.pt_val32; a.F32 = b.ilu32;
   a.pk_lv32 = b.pk_lv32; a.pk_uv32 = b.pk_uv32; a.pk_ud32 = b.pk_ud32;
-  a.xs = b.xs; a.rf = b.rf; a.zf = b.zf; a.dpf = b.dpf; a.yf = b.yf; a.ylevf = b.ylevf;
-  a.xlevf = b.xlevf;
+  a.xs = b.xs; a.yf = b.yf; a.ylevf = b.ylevf;
   int maxnc = 0;
   for (auto& I : b.h) maxnc = std::max(maxnc, I.nc);
   for (int i = 0; i < b.B; ++i)
@@ -1210,7 +1151,7 @@ int run_solve(Batch& b, double tol, float* ms) {
   // each kernel leaves the other kind of instance alone
   if (nrich > 0) fams::note_launch(), k_solve<<<b.B, SOLVE_T, smem, b.stream>>>(a);
   if (ngm > 0)
-    fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov, b.krylov32);
+    fams::note_launch(), k_gmres<<<b.B, SOLVE_T, smem_g, b.stream>>>(a, b.krylov, b.krylov_z);
   FAMS_CUDA(cudaGetLastError());
   FAMS_CUDA(cudaEventRecord(e1, b.stream));
   if (b.prepare_flux) FAMS_TRY(flux_beside(b, e0));
