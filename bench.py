@@ -110,70 +110,115 @@ class Clocks:
                 "samples": len(sm)}
 
 
-SERVE_WORKLOAD = ("stream of independent requests, arrivals Poisson at 80% of the "
-                  "closed-loop rate: half 2D (side U{64..256}, 0-30 fractures L~U[20,120], "
-                  "log10 k std 2 corr 16, coarsening 8x8), half 3D (cube side U{24..48}, 0-10 "
-                  "full-height plates, log10 k std 1.5, coarsening U{4..8}^3); T_ratio "
-                  "1e2..1e8, the four coupling strategies, R^FE, GMRES(30), tol 1e-8, + flux")
+SERVE_WORKLOAD = ("stream of requests, Poisson arrivals at 80% of the closed-loop rate: half new "
+                  "realisations (full setup), half time-step updates of one of the 8 latest new "
+                  "realisations (mobility x U[0.5,2] per cell, basis functions of the base's setup "
+                  "reused, issued once the base's pressure is in); new realisations half 2D (side "
+                  "U{64..1024}, log10 k std 2 corr 16, coarsening 8x8, d_min 8), half 3D (cube side "
+                  "U{32..128}, log10 k std 1.5 corr (8,8,4), coarsening U{4..8}^3, plates with "
+                  "sides U[10,60] and random layer ranges), fractures U{0..200} (L~U[20,120] in 2D), "
+                  "T_ratio 1e2..1e8, the four coupling strategies (Coupled merge cap 256), R^FE, "
+                  "GMRES(30), tol 1e-8, + flux")
 
 
-def serve_problems(n, seed):
-    """The served stream's requests (see SERVE_WORKLOAD), seeded."""
+def serve_stream(n, seed):
+    """The served stream (see SERVE_WORKLOAD), seeded: a list of ("new",
+    problem) and ("update", index of the base event, scale seed) events."""
     import numpy as np
     from paper_1705_05784_gb300 import inputs
     rng = np.random.default_rng(seed)
-    out = []
+    events, news = [], []
     for i in range(n):
+        if news and rng.random() < 0.5:
+            b = news[-1 - int(rng.integers(0, min(8, len(news))))]
+            events.append(("update", b, seed * 100003 + i))
+            continue
         basis = int(rng.integers(0, 4))
         tr = float(TRATIOS[int(rng.integers(0, len(TRATIOS)))])
+        nfr = int(rng.integers(0, 201))
         if rng.random() < 0.5:
-            side = 8 * int(rng.integers(8, 33))
-            p = inputs.config_2d(side, 2.0, 16.0, int(rng.integers(0, 31)), (20.0, 120.0), tr, 8, 8,
-                                 seed=seed + i, basis=basis, restriction=1, alpha=1e-2)
+            side = int(rng.integers(64, 1025))
+            p = inputs.config_2d(side, 2.0, 16.0, nfr, (20.0, 120.0), tr, 8, 8, seed=seed + i,
+                                 basis=basis, restriction=1, alpha=1e-2)
         else:
-            side = int(rng.integers(24, 49))
+            side = int(rng.integers(32, 129))
             cr = int(rng.integers(4, 9))
-            npl = int(rng.integers(0, 11))
-            p = inputs.config_3d(side, side, side, 1.5, (8.0, 8.0, 4.0), npl, (4, max(5, side // 2)),
-                                 tr, (cr, cr, cr), cr, cr, seed=seed + i, basis=basis,
+            p = inputs.config_3d(side, side, side, 1.5, (8.0, 8.0, 4.0), nfr, (10, 60), tr,
+                                 (cr, cr, cr), cr, cr, seed=seed + i, basis=basis,
                                  restriction=1, alpha=1e-2)
-            if npl:
-                p.fracs[:, 4] = 0.0
-                p.fracs[:, 5] = float(side)
         p.krylov, p.restart, p.max_iter = 1, 30, 400
-        out.append(p)
-    return out
+        if basis == 3:
+            p.merge_cap = 256
+        news.append(i)
+        events.append(("new", p))
+    return events
+
+
+def _scale(seed, n):
+    import numpy as np
+    return np.random.default_rng(seed).uniform(0.5, 2.0, n)
 
 
 def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
-    """Served stream (continuous batching through fams_server_*) against the
-    plain path (one context per request, solved one after another)."""
+    """Served stream (continuous batching and resident setups through
+    fams_server_*) against the plain path (each request alone in a context of
+    its own, one after another)."""
     import numpy as np
-    probs = serve_problems(n_req, seed)
+    events = serve_stream(n_req, seed)
 
     def pct(v, q):
         v = sorted(v)
         return v[min(len(v) - 1, int(q * len(v)))] if v else None
 
-    def run(rate):
+    def run(evs, rate):
         lat, svc, ok, fails, done = [], [], 0, {}, []
         with fams.Server(max_batch=max_batch, pipelines=pipelines, hbm_budget=96 << 30,
                          tol=TOL) as srv:
             rng = np.random.default_rng(seed + 1)
-            arrive = np.cumsum(rng.exponential(1.0 / rate, len(probs))) if rate else None
+            arrive = np.cumsum(rng.exponential(1.0 / rate, len(evs))) if rate else None
             t0 = time.perf_counter()
-            tickets, t_sub = [], []
-            for k, p in enumerate(probs):
+            tickets = [None] * len(evs)
+            t_sub = [0.0] * len(evs)
+            size = {}                       # base event -> unknowns, once its result is in
+            deferred = []                   # updates waiting for their base's pressure
+
+            def base_ready(b):
+                if b in size:
+                    return True
+                if tickets[b] is not None and srv.wait(tickets[b], 0.0):
+                    size[b] = srv.sizes(tickets[b])[0]
+                    return True
+                return False
+
+            def submit_update(k):
+                _, b, sd = evs[k]
+                t_sub[k] = time.perf_counter() - t0
+                tickets[k] = srv.submit_update(tickets[b], _scale(sd, size[b]))
+
+            for k, ev in enumerate(evs):
                 if arrive is not None:
-                    dt = arrive[k] - (time.perf_counter() - t0)
-                    if dt > 0:
-                        time.sleep(dt)
-                t_sub.append(time.perf_counter() - t0)
-                tickets.append(srv.submit(p))
+                    while True:
+                        dt = arrive[k] - (time.perf_counter() - t0)
+                        deferred = [d for d in deferred if not (base_ready(evs[d][1]) and
+                                                                submit_update(d) is None)]
+                        if dt <= 0:
+                            break
+                        time.sleep(min(dt, 0.002))
+                if ev[0] == "new":
+                    t_sub[k] = time.perf_counter() - t0
+                    tickets[k] = srv.submit(ev[1])
+                elif base_ready(ev[1]):
+                    submit_update(k)
+                else:
+                    deferred.append(k)
+            for d in deferred:
+                srv.wait(tickets[evs[d][1]], 600000.0)
+                base_ready(evs[d][1])
+                submit_update(d)
             for t in tickets:
                 srv.wait(t, 600000.0)
             elapsed = time.perf_counter() - t0
-            for t, ts in zip(tickets, t_sub):
+            for k, (t, ts) in enumerate(zip(tickets, t_sub)):
                 x, face, nnc, st = srv.fetch(t)
                 good = st["status"] == 0 and st["converged"]
                 ok += good
@@ -184,6 +229,7 @@ def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
                 svc.append(st["service_ms"])
                 if good:
                     done.append(ts + st["latency_ms"] / 1000.0)
+            for t in tickets:
                 srv.release(t)
         # steady-state rate: completions between the 10th and 90th percentile
         # completion times (no ramp-up at the start, no drain at the end)
@@ -192,18 +238,21 @@ def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
         steady = (i90 - i10) / (done[i90] - done[i10]) if i90 > i10 and done[i90] > done[i10] else None
         return ok, elapsed, lat, fails, svc, steady
 
-    run(None)                                    # warm-up of the stream's code paths
-
-    ok_c, el_c, _, _, _, _ = run(None)           # closed loop: sustained served rate
-    rate = 0.8 * len(probs) / el_c
-    ok_s, el_s, lat, fails, svc, steady = run(rate)
-    # plain: the first n_plain requests, each alone, one after another
+    run(events[:8], None)                        # warm-up of the stream's code paths
+    ok_c, el_c, _, _, _, _ = run(events, None)   # closed loop: sustained served rate
+    rate = 0.8 * len(events) / el_c
+    ok_s, el_s, lat, fails, svc, steady = run(events, rate)
+    # plain: the first n_plain requests, each alone, one after another (an
+    # update: the base problem set up, fams_update, solve from zero, flux)
     times = []
     ok_p = 0
-    for p in probs[:n_plain]:
+    for k, ev in enumerate(events[:n_plain]):
+        p = ev[1] if ev[0] == "new" else events[ev[1]][1]
         t = time.perf_counter()
         try:
             with fams.Context(p) as c:
+                if ev[0] == "update":
+                    c.update([_scale(ev[2], c.sizes()["n"])])
                 xs, st = c.solve(tol=TOL)
                 if st[0]["converged"]:
                     c.flux(xs[0])
@@ -212,8 +261,9 @@ def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
             pass                                 # counted as not solved, as in the stream
         times.append(1000.0 * (time.perf_counter() - t))
     plain_rate = ok_p / (sum(times) / 1000.0) if times else None
-    return {"workload": SERVE_WORKLOAD, "requests": len(probs), "pipelines": pipelines,
-            "max_batch": max_batch,
+    n_upd = sum(1 for e in events if e[0] == "update")
+    return {"workload": SERVE_WORKLOAD, "requests": len(events), "updates": n_upd,
+            "pipelines": pipelines, "max_batch": max_batch,
             "sustained_solves_per_s": ok_c / el_c, "arrival_rate_per_s": rate,
             "served_solves_per_s": steady, "served_over_whole_run_per_s": ok_s / el_s,
             "converged": ok_s, "failed": fails,
@@ -222,7 +272,8 @@ def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
             "queue_p50_ms": pct([l - s for l, s in zip(lat, svc)], 0.50),
             "plain": {"requests": len(times), "solves_per_s": plain_rate,
                       "p50_ms": pct(times, 0.50), "p99_ms": pct(times, 0.99),
-                      "note": "one context per request, setup + solve + flux, sequential"},
+                      "note": "one context per request, setup (+ update) + solve + flux, "
+                              "sequential"},
             "served_vs_plain": steady / plain_rate if plain_rate and steady else None}
 
 
@@ -514,11 +565,11 @@ def main():
                     help="mixed: FP32 inner stages with FP64 residuals and refinement")
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
     ap.add_argument("--restart", type=int, default=30, help="GMRES cycle length")
-    ap.add_argument("--serve", type=int, default=400,
+    ap.add_argument("--serve", type=int, default=32,
                     help="requests in the served stream (0: skip the serving measurement)")
     ap.add_argument("--pipelines", type=int, default=4, help="server: micro-batches in flight")
     ap.add_argument("--max-batch", type=int, default=64, help="server: requests per micro-batch")
-    ap.add_argument("--plain", type=int, default=32,
+    ap.add_argument("--plain", type=int, default=8,
                     help="requests of the stream solved one by one for the plain comparison")
     ap.add_argument("--large", type=int, default=2,
                     help="timed solves of the 3D 128x128x64 scale case (0: skip)")
@@ -683,7 +734,7 @@ def main():
     if args.large > 0:
         line["large_instance"] = large_instance(fams, args.large, 1, args.merge_cap)
     if args.serve > 0:
-        sv = serving(fams, args.serve, args.plain, 7000, args.pipelines, args.max_batch)
+        sv = serving(fams, args.serve, args.plain, 4, args.pipelines, args.max_batch)
         line["serving"] = sv
         line["latency"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
                            "note": "served stream, submission to completion per request; "

@@ -224,6 +224,12 @@ int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_sta
    Returns FAMS_ENOCONV if any instance did not converge. */
 int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
                      fams_stats* st);
+/* fams_solve_subset - fams_solve_batch on the n_list distinct instances in
+   list only (the others keep their state and launch nothing); rhs, x and st
+   are indexed like list.  A whole-GPU context (one instance) takes list {0}.
+   FAMS_EINVAL for an index out of range or repeated. */
+int fams_solve_subset(fams_ctx* ctx, int n_list, const int* list, const double* const* rhs,
+                      double* const* x, double tol, fams_stats* st);
 
 /* fams_update - time-step update of instance 0: every connection's
    transmissibility (matrix faces, matrix-fracture and fracture-fracture) is
@@ -382,12 +388,14 @@ const char* fams_last_error(void);
    go to the next free worker.  A result does not depend on what the request
    was batched with (up to the rounding of the coarse operator's atomic
    sums).  rhs, if given, holds n_matrix matrix-cell sources (fracture sources
-   are zero).  Calls are thread-safe. */
+   are zero).  Finished micro-batches stay resident for time-step updates
+   (fams_server_submit_update) and count against hbm_budget until all their
+   requests are released or the memory is needed.  Calls are thread-safe. */
 typedef struct fams_server fams_server;
 typedef struct {
   int max_batch;         /* instances per micro-batch, >= 1 */
   int pipelines;         /* micro-batches in flight, 1..16 */
-  long long hbm_budget;  /* bytes the in-flight micro-batches may use */
+  long long hbm_budget;  /* bytes the in-flight micro-batches and resident setups may use */
   double tol;            /* relative residual of every solve */
   int with_flux;         /* also reconstruct the conservative fluxes */
 } fams_server_opts;
@@ -397,6 +405,21 @@ int fams_server_create(const fams_server_opts* opts, fams_server** out);
 int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm,
                        const fams_fracs* fracs, const fams_opts* opts, const double* rhs,
                        long long* ticket);
+/* fams_server_submit_update - a time-step update of the earlier new
+   realisation `base` (finished or not): its problem with every cell's
+   mobility scaled by mobility_scale (n_scale = n_matrix + n_frac values,
+   relative to the base's setup as in fams_update; copied), solved with the
+   basis functions of the base's setup (Sec. 3.1 end; the server keeps each
+   finished micro-batch's context resident for this) from the base's
+   pressure as initial guess.  rhs (n_rhs matrix-cell sources; nullable: the
+   base's).  Updates of one resident context are batched; an update of a
+   setup evicted for memory sets the base problem up again first.  The
+   result is collected like any request's; its status is FAMS_EINVAL when
+   the base failed, was released before the update ran, or n_scale does not
+   match its unknowns. */
+int fams_server_submit_update(fams_server* s, long long base, const double* mobility_scale,
+                              long long n_scale, const double* rhs, long long n_rhs,
+                              long long* ticket);
 /* waits up to timeout_ms (<= 0: no wait); *done = 1 once the result is ready */
 int fams_server_wait(fams_server* s, long long ticket, double timeout_ms, int* done);
 /* copies a finished request's pressure (n_matrix + n_frac values), fluxes (as

@@ -578,38 +578,61 @@ int fams_sizes(const fams_ctx* ctx, int inst, int* n_matrix, int* n_frac, int* n
   return FAMS_OK;
 }
 
-int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
-                     fams_stats* st) {
+}  // extern "C"
+
+namespace {
+
+// the iteration on the listed instances (rhs, x and st indexed like list);
+// instances not listed keep their state and launch nothing
+int solve_list(fams_ctx* ctx, const std::vector<int>& list, const double* const* rhs,
+               double* const* x, double tol, fams_stats* st) {
   if (!ctx || !x) { set_error("null argument"); return FAMS_EINVAL; }
   if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return FAMS_EINVAL; }
   Batch& b = ctx->b;
-  for (int i = 0; i < b.B; ++i)
-    if (!x[i]) { set_error("x is null"); return FAMS_EINVAL; }
+  const int nl = (int)list.size();
+  const bool all = nl == b.B;
+  std::vector<int> act(b.B, 0);
+  for (int k = 0; k < nl; ++k) {
+    const int i = list[k];
+    if (i < 0 || i >= b.B || act[i]) { set_error("bad or repeated instance in the list"); return FAMS_EINVAL; }
+    if (!x[k]) { set_error("x is null"); return FAMS_EINVAL; }
+    act[i] = 1;
+  }
+  if (nl == 0) return FAMS_OK;
+  int* d_act = nullptr;
+  if (!all) {
+    if (whole_gpu(b)) { set_error("a whole-GPU context has one instance"); return FAMS_EINVAL; }
+    if (!b.d_active) FAMS_TRY(b.alloc((void**)&b.d_active, sizeof(int) * b.B));
+    FAMS_CUDA(cudaMemcpyAsync(b.d_active, act.data(), sizeof(int) * b.B, cudaMemcpyHostToDevice,
+                              b.stream));
+    d_act = b.d_active;
+  }
   // rhs staged in the dp work vector
   FAMS_CUDA(cudaMemsetAsync(b.dp, 0, sizeof(double) * b.tot_row, b.stream));
-  for (int i = 0; i < b.B; ++i) {
-    const Inst& I = b.h[i];
-    if (rhs && rhs[i])
-      FAMS_CUDA(cudaMemcpyAsync(b.dp + I.row_off, rhs[i], sizeof(double) * I.n, cudaMemcpyDefault,
+  for (int k = 0; k < nl; ++k) {
+    const Inst& I = b.h[list[k]];
+    if (rhs && rhs[k])
+      FAMS_CUDA(cudaMemcpyAsync(b.dp + I.row_off, rhs[k], sizeof(double) * I.n, cudaMemcpyDefault,
                                 b.stream));
-    FAMS_CUDA(cudaMemcpyAsync(b.x + I.row_off, x[i], sizeof(double) * I.n, cudaMemcpyDefault,
+    FAMS_CUDA(cudaMemcpyAsync(b.x + I.row_off, x[k], sizeof(double) * I.n, cudaMemcpyDefault,
                               b.stream));
   }
   FAMS_TRY(make_q(b, b.dp));
   float ms = 0.f;
-  FAMS_TRY(run_solve(b, tol, &ms));
+  FAMS_TRY(run_solve(b, tol, &ms, d_act));
   std::vector<double> stat;
   FAMS_TRY(fetch(b, b.stat, (long long)STAT_W * b.B, stat));
   int status = FAMS_OK;
-  for (int i = 0; i < b.B; ++i) {
+  for (int k = 0; k < nl; ++k) {
+    const int i = list[k];
     const Inst& I = b.h[i];
-    FAMS_CUDA(cudaMemcpyAsync(x[i], b.x + I.row_off, sizeof(double) * I.n, cudaMemcpyDefault,
+    FAMS_CUDA(cudaMemcpyAsync(x[k], b.x + I.row_off, sizeof(double) * I.n, cudaMemcpyDefault,
                               b.stream));
     if (st) {
-      st[i].iterations = (int)stat[STAT_W * i];
-      st[i].rel_residual = stat[STAT_W * i + 1];
-      st[i].converged = stat[STAT_W * i + 2] > 0.5;
-      st[i].solve_ms = ms;
+      st[k].iterations = (int)stat[STAT_W * i];
+      st[k].rel_residual = stat[STAT_W * i + 1];
+      st[k].converged = stat[STAT_W * i + 2] > 0.5;
+      st[k].solve_ms = ms;
     }
     if (stat[STAT_W * i + STAT_BAD] > 0.5) {
       if (status != FAMS_EBREAKDOWN)
@@ -626,6 +649,24 @@ int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, 
   }
   FAMS_CUDA(cudaStreamSynchronize(b.stream));
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fams_solve_batch(fams_ctx* ctx, const double* const* rhs, double* const* x, double tol,
+                     fams_stats* st) {
+  if (!ctx) { set_error("null argument"); return FAMS_EINVAL; }
+  std::vector<int> all(ctx->b.B);
+  for (int i = 0; i < ctx->b.B; ++i) all[i] = i;
+  return solve_list(ctx, all, rhs, x, tol, st);
+}
+
+int fams_solve_subset(fams_ctx* ctx, int n_list, const int* list, const double* const* rhs,
+                      double* const* x, double tol, fams_stats* st) {
+  if (!ctx || n_list < 0 || (n_list > 0 && !list)) { set_error("null argument"); return FAMS_EINVAL; }
+  return solve_list(ctx, std::vector<int>(list, list + n_list), rhs, x, tol, st);
 }
 
 int fams_solve(fams_ctx* ctx, const double* rhs, double* x, double tol, fams_stats* st) {

@@ -53,6 +53,7 @@ struct Batch {
   int device = 0;
   std::vector<Inst> h;          // host copy of the descriptors
   Inst* d_inst = nullptr;       // device copy
+  int* d_active = nullptr;      // instances a subset solve runs (allocated on first use)
   int* d_err = nullptr;         // device status word
   std::vector<void*> owned;     // freed by fams_destroy
   std::vector<void*> tmp;       // freed at the end of setup
@@ -306,7 +307,8 @@ int ilu_refactor(Batch& b);                               // ilu.cu
 int refresh_mixed(Batch& b);                              // solve.cu
 int phase_ilu(Batch& b);          // ilu.cu
 int phase_alloc_work(Batch& b);   // solve.cu
-int run_solve(Batch& b, double tol, float* ms);   // solve.cu
+// active: device array, 1 per instance to solve (null: all)
+int run_solve(Batch& b, double tol, float* ms, const int* active = nullptr);   // solve.cu
 // solve_grid.cu: a single-instance context whose iteration runs on every SM
 constexpr long long GRID_SOLVE_ROWS = 1LL << 18;
 bool whole_gpu(const Batch& b);       // single instance, large or asked for: every SM

@@ -32,13 +32,14 @@ __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, co
                              const int* col, const double* val, const int* blk_ptr,
                              const int* blk_cell, const int* p_ptr, const int* p_col,
                              const double* p_val, const double* q, const double* x, double* r,
-                             double* pp) {
+                             double* pp, double* gws, long long gstride) {
   extern __shared__ double sm[];
   int ii = list[blockIdx.x];
   const Inst& I = inst[ii];
   int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
-  double* yb = sm;
-  double* ecs = sm + nc;
+  // the two coarse vectors: shared memory, or global scratch when they do not fit
+  double* yb = gws ? gws + (long long)blockIdx.x * gstride : sm;
+  double* ecs = yb + nc;
   for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
     double s = q[i];
     for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s -= val[p] * x[col[p]];
@@ -430,6 +431,11 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;  // static shared memory of the kernels
+  double* gws = nullptr;   // coarse vectors in global memory (above ~14k coarse unknowns)
+  if (smem > (size_t)max_smem) {
+    FAMS_TRY(b.scratch((void**)&gws, smem * (size_t)nl));
+    smem = 0;
+  }
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_local<CtaGroup>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
@@ -440,7 +446,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_CUDA(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
   fams::note_launch(), k_flux_stage<<<nl, 512, smem, st>>>(
       b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.pf_ptr, b.pf_col,
-      b.pf_val, b.q, x, res, pp);
+      b.pf_val, b.q, x, res, pp, gws, 2 * (long long)maxnc);
   FAMS_CUDA(cudaGetLastError());
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread

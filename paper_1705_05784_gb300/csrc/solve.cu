@@ -84,6 +84,7 @@ __global__ void k_make_q(long long n, const double* rhs, const double* qD, doubl
 
 struct SolveArgs {
   const Inst* inst;
+  const int* active;   // per instance: 1 to solve (null: every instance)
   CoarseSys cs;
   const int* rowptr;
   const int* col;
@@ -698,7 +699,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   __shared__ int pbuf[2 * CH_MAX];
   int ii = blockIdx.x;
   const Inst& I = a.inst[ii];
-  if (I.krylov != FAMS_KRYLOV_NONE) return;
+  if (I.krylov != FAMS_KRYLOV_NONE || (a.active && !a.active[ii])) return;
   const int n = I.n, ro = I.row_off;
   const SolveSmem S = solve_smem(sm, I.nc, pbuf);
   const int NT = blockDim.x;
@@ -962,7 +963,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry, 
   __shared__ int pbuf[2 * CH_MAX];
   int ii = blockIdx.x;
   const Inst& I = a.inst[ii];
-  if (I.krylov != FAMS_KRYLOV_GMRES) return;
+  if (I.krylov != FAMS_KRYLOV_GMRES || (a.active && !a.active[ii])) return;
   const int n = I.n, ro = I.row_off, m = I.restart;
   const SolveSmem S = solve_smem(sm, I.nc, pbuf);
   GmresSmem G;
@@ -1100,10 +1101,11 @@ int make_q(Batch& b, const double* rhs_dev) {
   return FAMS_OK;
 }
 
-int run_solve(Batch& b, double tol, float* ms) {
+int run_solve(Batch& b, double tol, float* ms, const int* active) {
   if (solve_on_grid(b)) return run_solve_grid(b, tol, ms);
   SolveArgs a{};
   a.inst = b.d_inst;
+  a.active = active;
   a.cs = b.cs[0];
   a.rowptr = b.rowptr; a.col = b.col; a.val = b.val; a.diag = b.diag;
   a.p_ptr = b.p_ptr; a.p_col = b.p_col; a.p_val = b.p_val;

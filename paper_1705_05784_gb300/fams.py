@@ -88,6 +88,8 @@ def _load():
     lib.fams_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, P(fams_stats)]
     lib.fams_solve_batch.argtypes = [C.c_void_p, P(C.c_void_p), P(C.c_void_p), C.c_double,
                                      P(fams_stats)]
+    lib.fams_solve_subset.argtypes = [C.c_void_p, C.c_int, P(C.c_int), P(C.c_void_p),
+                                      P(C.c_void_p), C.c_double, P(fams_stats)]
     lib.fams_solve_static.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                       P(fams_stats)]
     lib.fams_flux.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -111,6 +113,9 @@ def _load():
     lib.fams_server_create.argtypes = [P(fams_server_opts), P(C.c_void_p)]
     lib.fams_server_submit.argtypes = [C.c_void_p, P(fams_grid), P(C.c_double), P(fams_fracs),
                                        P(fams_opts), P(C.c_double), P(C.c_longlong)]
+    lib.fams_server_submit_update.argtypes = [C.c_void_p, C.c_longlong, P(C.c_double),
+                                              C.c_longlong, P(C.c_double), C.c_longlong,
+                                              P(C.c_longlong)]
     lib.fams_server_wait.argtypes = [C.c_void_p, C.c_longlong, C.c_double, P(C.c_int)]
     lib.fams_server_result.argtypes = [C.c_void_p, C.c_longlong, P(C.c_double), C.c_longlong,
                                        P(C.c_double), C.c_longlong, P(C.c_double), C.c_longlong,
@@ -274,6 +279,26 @@ class Context:
                  for i in range(n)]
         return xs, stats
 
+    def solve_subset(self, insts, rhs=None, x0=None, tol=1e-8):
+        """fams_solve_subset: solve only the listed instances (the others keep
+        their state).  rhs/x0: lists indexed like insts.  Returns (pressures,
+        stats dicts) indexed like insts."""
+        m = len(insts)
+        N = [self.sizes(i)["n"] for i in insts]
+        xs = [np.ascontiguousarray(x0[k] if x0 is not None else np.zeros(N[k]), np.float64).copy()
+              for k in range(m)]
+        rs = [None if rhs is None or rhs[k] is None else np.ascontiguousarray(rhs[k], np.float64)
+              for k in range(m)]
+        li = (C.c_int * max(m, 1))(*insts)
+        xp = (C.c_void_p * max(m, 1))(*[x.ctypes.data for x in xs])
+        rp = (C.c_void_p * max(m, 1))(*[0 if r is None else r.ctypes.data for r in rs])
+        st = (fams_stats * max(m, 1))()
+        s = lib.fams_solve_subset(self.h, m, li, rp, xp, tol, st)
+        _check(s, allow=(ENOCONV,))
+        return xs, [dict(iterations=st[k].iterations, rel_residual=st[k].rel_residual,
+                         converged=bool(st[k].converged), solve_ms=st[k].solve_ms, status=s)
+                    for k in range(m)]
+
     def update(self, scales):
         """fams_update_batch: scales is a list per instance (None: all 1) or
         one array for a single instance."""
@@ -366,6 +391,17 @@ class Server:
         r = None if rhs is None else np.ascontiguousarray(rhs, np.float64)
         _check(lib.fams_server_submit(self.h, C.byref(g), _dptr(perm), C.byref(f), C.byref(o),
                                       None if r is None else _dptr(r), C.byref(t)))
+        return t.value
+
+    def submit_update(self, base, scale, rhs=None):
+        """Time-step update of the new realisation `base`: mobility scale per
+        cell (n_matrix + n_frac values), basis functions of the base's setup."""
+        sc = np.ascontiguousarray(scale, np.float64)
+        r = None if rhs is None else np.ascontiguousarray(rhs, np.float64)
+        t = C.c_longlong()
+        _check(lib.fams_server_submit_update(self.h, base, _dptr(sc), len(sc),
+                                             None if r is None else _dptr(r),
+                                             0 if r is None else len(r), C.byref(t)))
         return t.value
 
     def wait(self, ticket, timeout_ms=60000.0):

@@ -87,3 +87,75 @@ def test_small_budget_still_serves_one_at_a_time():
         for t in ts:
             assert srv.wait(t, 120000.0)
             assert srv.status(t) == fams.OK
+
+
+def _update_alone(fams, p, x_base, scale):
+    """The reference of a served time-step update: the base problem's own
+    context, fams_update with the scale, solved from the base's pressure."""
+    with fams.Context(p) as c:
+        c.update([scale])
+        xs, st = c.solve(tol=1e-8, x0=[x_base])
+        face, nnc = c.flux(xs[0])
+    assert st[0]["converged"]
+    return xs[0], face, nnc, st[0]
+
+
+@pytest.mark.parametrize("budget", [8 << 30, 1])
+def test_time_step_updates_match_standalone_updates(budget):
+    """fams_server_submit_update against a resident setup (budget 8 GiB) and,
+    with a budget of 1 byte, after the base's setup was evicted (set up again
+    first): each updated result -- pressure, fluxes, iterations -- equals
+    fams_update + solve from the base's pressure in a context of its own."""
+    from paper_1705_05784_gb300 import fams
+    probs = _mix()[:6]
+    rng = np.random.default_rng(7)
+    with fams.Server(max_batch=4, pipelines=2, hbm_budget=budget, tol=1e-8) as srv:
+        base = [srv.submit(p) for p in probs]
+        xb = []
+        for t in base:
+            assert srv.wait(t, 120000.0)
+            x, face, nnc, st = srv.fetch(t)
+            assert st["status"] == 0
+            xb.append(x)
+        picks = [0, 2, 3, 3, 5]          # two updates of one base, in one stream
+        scales = [rng.uniform(0.5, 2.0, len(xb[i])) for i in picks]
+        ups = [srv.submit_update(base[i], sc) for i, sc in zip(picks, scales)]
+        for t, i, sc in zip(ups, picks, scales):
+            assert srv.wait(t, 120000.0)
+            x, face, nnc, st = srv.fetch(t)
+            assert st["status"] == 0 and st["converged"], st["error"]
+            x0, f0, n0, s0 = _update_alone(fams, probs[i], xb[i], sc)
+            assert abs(st["iterations"] - s0["iterations"]) <= 1
+            assert np.linalg.norm(x - x0) / np.linalg.norm(x0) < 1e-9
+            fs = max(np.abs(f0).max(), 1e-300)
+            np.testing.assert_allclose(face, f0, rtol=0, atol=1e-8 * fs)
+            np.testing.assert_allclose(nnc, n0, rtol=0, atol=1e-8 * fs)
+        # an update whose scale does not match its base fails alone
+        bad = srv.submit_update(base[1], np.ones(3))
+        assert srv.wait(bad, 60000.0)
+        assert srv.status(bad) == fams.EINVAL
+        # releasing the base first: its later update fails
+        srv.release(base[4])
+        late = None
+        try:
+            late = srv.submit_update(base[4], np.ones(len(xb[4])))
+        except fams.FamsError:
+            pass                         # unknown ticket at submission
+        if late is not None:
+            assert srv.wait(late, 60000.0)
+            assert srv.status(late) == fams.EINVAL
+
+
+def test_subset_solve_leaves_the_other_instances_alone():
+    """fams_solve_subset: the listed instances are solved exactly as in a
+    full batch solve; the others launch nothing and keep their state."""
+    from paper_1705_05784_gb300 import fams
+    probs = _mix()[:4]
+    with fams.Context(probs) as c:
+        xs_all, st_all = c.solve(tol=1e-8)
+        xs, st = c.solve_subset([3, 1], tol=1e-8)
+        for k, i in enumerate([3, 1]):
+            assert st[k]["iterations"] == st_all[i]["iterations"]
+            assert np.linalg.norm(xs[k] - xs_all[i]) / np.linalg.norm(xs_all[i]) < 1e-12
+        with pytest.raises(fams.FamsError):
+            c.solve_subset([1, 1])
