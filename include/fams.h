@@ -261,7 +261,7 @@ int fams_update_batch(fams_ctx* ctx, const double* const* mobility_scale);
 int fams_update_basis(fams_ctx* ctx, const double* const* mobility_scale, double eps,
                       int* rebuilt);
 
-/* Limits of fams_solve_static (its fixed work array, about 13 MB per GPU). */
+/* Limits of fams_solve_static (its fixed work array, about 15 MB per GPU). */
 #define FAMS_STATIC_MAX_ROWS 262144   /* n_matrix + n_frac of the instance */
 #define FAMS_STATIC_MAX_COARSE 16384  /* n_coarse of the instance */
 #define FAMS_STATIC_MAX_ITER 16383    /* the instance's max_iter */

@@ -312,6 +312,7 @@ int run_solve(Batch& b, double tol, float* ms, const int* active = nullptr);   /
 // solve_grid.cu: a single-instance context whose iteration runs on every SM
 constexpr long long GRID_SOLVE_ROWS = 1LL << 18;
 bool whole_gpu(const Batch& b);       // single instance, large or asked for: every SM
+bool one_cta_fits(const Batch& b, int nc, int kl, int ku, int m);   // solve.cu
 bool solve_on_grid(const Batch& b);   // ... and its iteration is FP64 GMRES
 int run_solve_grid(Batch& b, double tol, float* ms);
 int ilu_factor_grid(Batch& b, double* F);   // ILU(0) factorisation (values in F) on every SM

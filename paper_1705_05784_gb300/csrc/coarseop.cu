@@ -616,6 +616,15 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   FAMS_CUDA(cudaMemsetAsync(cs.band, 0, sizeof(double) * (ch.band_tot + 1), st));
   fams::note_launch(), k_band_fill<<<grid_for(nct, 64), 64, 0, st>>>(b.d_inst, B, b.off_nc, nct, cs, ip,
                                                                    nullptr);
+  // a single instance whose coarse system the one-CTA iteration cannot hold
+  // (a band wider than its shared-memory chunks) goes to the whole GPU when
+  // the caller left the choice to the library (grid_solve = 0)
+  if (!reuse && mode < 0 && B == 1 && b.h[0].grid_solve == 0 && !whole_gpu(b) &&
+      !one_cta_fits(b, b.h[0].nc, ch.kl[0], ch.ku[0],
+                    b.h[0].krylov == FAMS_KRYLOV_GMRES ? b.h[0].restart : 0)) {
+    b.h[0].grid_solve = 1;
+    FAMS_CUDA(cudaMemcpyAsync(b.d_inst, b.h.data(), sizeof(Inst), cudaMemcpyHostToDevice, st));
+  }
   if (whole_gpu(b)) {
     // one large instance: band LU with partial pivoting on every SM (its
     // iteration solves with A_c^-1 formed from these factors)

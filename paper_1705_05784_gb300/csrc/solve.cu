@@ -1101,6 +1101,20 @@ int make_q(Batch& b, const double* rhs_dev) {
   return FAMS_OK;
 }
 
+// whether the one-CTA iteration kernels hold a coarse system of nc unknowns
+// and band kl + ku + 1 (the band chunks and the coarse vectors in shared
+// memory), for an instance of GMRES restart m (0: the Table 1 loop)
+bool one_cta_fits(const Batch& b, int nc, int kl, int ku, int m) {
+  if (kl + ku + 1 > BAND_BUF) return false;
+  size_t smem = sizeof(double) * (2 * (size_t)nc + BUF_DOUBLES);
+  if (m > 0) smem += sizeof(double) * ((size_t)m * m + 5 * (size_t)m + 1);
+  int max_smem = 0;
+  if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device) !=
+      cudaSuccess)
+    return true;   // (the launch reports it)
+  return (long long)smem + 3072 <= max_smem;
+}
+
 int run_solve(Batch& b, double tol, float* ms, const int* active) {
   if (solve_on_grid(b)) return run_solve_grid(b, tol, ms);
   SolveArgs a{};

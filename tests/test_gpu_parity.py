@@ -1005,3 +1005,34 @@ def test_sub_block_smoothing_stage_matches_the_oracle(name, restriction, grid):
             xs, stats = ctx.solve(tol=0.0)
             assert stats[0]["iterations"] == 9 == itt
             assert np.linalg.norm(xs[0] - xt) / np.linalg.norm(xt) < 1e-10
+
+
+def test_oversize_coarse_band_goes_to_the_whole_gpu():
+    """A single instance below the automatic whole-GPU size whose coarse
+    band is wider than the one-CTA kernels' band chunks (a 40^3 cube with
+    189 plates at coarsening 4-8) is solved on the whole GPU when the caller
+    leaves the choice to the library, as when it asks for it; with the
+    one-CTA path forced it fails with FAMS_ECAPACITY."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    fams = _fams()
+    p = bench.serve_stream(7, 4)[6][1]
+    assert p.dim == 3 and p.nx == 40 and len(p.fracs) == 189
+    with fams.Context(p) as c:
+        kl, ku = c.query("BAND_KLKU")
+        assert kl + ku + 1 > 3072 and c.sizes()["n"] < (1 << 18)
+        xa, sa = c.solve(tol=1e-8)
+        assert sa[0]["converged"]
+    q = copy.copy(p)
+    q.grid_solve = 1
+    with fams.Context(q) as c:
+        xg, sg = c.solve(tol=1e-8)
+    assert sg[0]["iterations"] == sa[0]["iterations"]
+    assert np.linalg.norm(xa[0] - xg[0]) / np.linalg.norm(xg[0]) < 1e-10
+    q.grid_solve = -1
+    with fams.Context(q) as c:
+        with pytest.raises(fams.FamsError) as e:
+            c.solve(tol=1e-8)
+        assert e.value.status == fams.ECAPACITY
