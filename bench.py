@@ -330,6 +330,89 @@ LARGE_WORKLOAD = ("3D 128x128x64 (1.05M matrix cells): layered log10 k std 2 cor
                   "one instance on every SM")
 
 
+BATCH3D_WORKLOAD = ("512 independent 3D instances in one context: cube side U{24..64}, log10 k std "
+                    "1.5 corr (8,8,4), Poisson(15) vertical plates clipped to 40 with sides U[4, side/2] "
+                    "and random layer ranges, coarsening U{4..8}^3 (fracture d_min and layer blocks "
+                    "alike), T_ratio 1e2..1e8, the four coupling strategies (Coupled merge cap 256), "
+                    "R^FE, alpha 1e-2, GMRES(30) with FP32 inner stages and FP64 refinement, tol 1e-8, "
+                    "+ flux reconstruction; seeds 1000+i")
+
+
+def batch3d_problems(n=512, seed0=1000):
+    """The batched 3D workload (see BATCH3D_WORKLOAD), seeded."""
+    import numpy as np
+    from paper_1705_05784_gb300 import inputs
+    rng = np.random.default_rng(seed0)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(24, 65))
+        cr = int(rng.integers(4, 9))
+        npl = int(min(40, rng.poisson(15)))
+        basis = i % 4
+        p = inputs.config_3d(side, side, side, 1.5, (8.0, 8.0, 4.0), npl, (4, max(5, side // 2)),
+                             TRATIOS[(i // 4) % len(TRATIOS)], (cr, cr, cr), cr, cr, seed=seed0 + i,
+                             basis=basis, restriction=1, alpha=1e-2)
+        p.krylov, p.restart, p.max_iter, p.precision = 1, 30, 400, 1
+        p.prepare_flux = 1
+        if basis == 3:
+            p.merge_cap = 256
+        out.append(p)
+    return out
+
+
+def batched_3d(fams, n, steps, warmup):
+    """The batched 3D workload: setup + solve + flux of all instances in one
+    context per step, inputs in GPU memory, timed with CUDA events."""
+    import numpy as np
+    import torch
+    probs = batch3d_problems(n)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    perm_d = [torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev) for p in probs]
+    ctx = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+    S = [sizes_of(ctx, i) for i in range(n)]
+    ctx.close()
+    x_d = [torch.zeros(s["n"], dtype=torch.float64, device=dev) for s in S]
+    f_d = [torch.zeros(s["faces"], dtype=torch.float64, device=dev) for s in S]
+    n_d = [torch.zeros(max(s["nnc"], 1), dtype=torch.float64, device=dev) for s in S]
+
+    def step():
+        for x in x_d:
+            x.zero_()
+        c = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+        st = c.solve_device([None] * n, [x.data_ptr() for x in x_d], TOL)
+        fl = c.flux_batch_ptr([x.data_ptr() for x in x_d], [f.data_ptr() for f in f_d],
+                              [m.data_ptr() for m in n_d])
+        setup = [float(v) for v in c.query("SETUP_MS")]
+        c.close()
+        return st, fl, setup
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    runs = [step() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st, fl, setup = runs[-1]
+    ok = [s["converged"] and f == 0 for s, f in zip(st, fl)]
+    its = [s["iterations"] for s in st]
+    return {"workload": BATCH3D_WORKLOAD, "instances": n, "unknowns": sum(s["n"] for s in S),
+            "steps": steps, "ms_per_step": ms, "solves_per_s": sum(ok) * 1000.0 / ms,
+            "cells_per_s": sum(s["n"] for s, k in zip(S, ok) if k) * 1000.0 / ms,
+            "converged": sum(ok), "flux_failed": sum(1 for f in fl if f != 0),
+            "iterations_median": statistics.median(its), "iterations_max": max(its),
+            "max_rel_residual": max(s["rel_residual"] for s in st),
+            "kernel_ms": statistics.median(r[0][0]["solve_ms"] for r in runs),
+            "setup_ms": {k: round(v, 1) for k, v in zip(
+                ("geometry", "fine_system", "coarse_grids", "basis", "coarse_operator", "ilu0"),
+                setup)},
+            "dtype": "f32+f64 (FP32 restriction, prolongation and ILU(0) sweeps; FP64 residual, "
+                     "coarse solve, Krylov basis and refinement)"}
+
+
 def large_problem(cap, seed=3):
     """The 3D scale case: one instance of about 1.2M unknowns."""
     from paper_1705_05784_gb300 import inputs
@@ -472,27 +555,38 @@ def conn_fluxes(p, face, nnc):
     return np.concatenate(parts + [nnc])
 
 
+PRECISIONS = (("fp64", 0, 0), ("mixed", 1, 0), ("mixed_bf16p", 1, 1))
+
+
 def oracle_error(fams, cpu, sample):
     """The GPU path on the oracle baseline's instances against the oracle's
     results (both converged to TOL): relative L2 error of the pressure and
-    largest flux difference relative to the largest flux."""
+    largest flux difference relative to the largest flux, for FP64 (top
+    level) and for each precision variant (`by_precision`)."""
     import numpy as np
     ref = cpu.pop("_ref", None) if cpu else None
     if not ref or not os.path.exists(ref):
         return None
     try:
         d = np.load(ref)
-        probs = problems(sample, ORACLE_SEED)
-        ex, ef = 0.0, 0.0
-        with fams.Context(probs) as c:
-            xs, st = c.solve(tol=TOL)
-            for i, p in enumerate(probs):
-                face, nnc = c.flux(xs[i], i)
-                xo, fo = d[f"x{i}"], d[f"f{i}"]
-                ex = max(ex, float(np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo)))
-                ef = max(ef, float(np.abs(conn_fluxes(p, face, nnc) - fo).max() / np.abs(fo).max()))
-        return {"instances": sample, "pressure_rel_l2": ex, "flux_rel_max": ef,
-                "note": "GPU and oracle each converged to rel. residual 1e-8"}
+        out = {"instances": sample, "note": "GPU and oracle each converged to rel. residual 1e-8",
+               "by_precision": {}}
+        for name, prec, bf in PRECISIONS:
+            probs = problems(sample, ORACLE_SEED, precision=prec)
+            for p in probs:
+                p.bf16_p = bf
+            ex, ef = 0.0, 0.0
+            with fams.Context(probs) as c:
+                xs, st = c.solve(tol=TOL)
+                for i, p in enumerate(probs):
+                    face, nnc = c.flux(xs[i], i)
+                    xo, fo = d[f"x{i}"], d[f"f{i}"]
+                    ex = max(ex, float(np.linalg.norm(xs[i] - xo) / np.linalg.norm(xo)))
+                    ef = max(ef, float(np.abs(conn_fluxes(p, face, nnc) - fo).max() /
+                                       np.abs(fo).max()))
+            out["by_precision"][name] = {"pressure_rel_l2": ex, "flux_rel_max": ef}
+        out.update(out["by_precision"]["fp64"])
+        return out
     except Exception as e:   # a failed comparison is reported, not fatal
         return {"error": str(e)[:200]}
     finally:
@@ -573,6 +667,11 @@ def main():
                     help="requests of the stream solved one by one for the plain comparison")
     ap.add_argument("--large", type=int, default=2,
                     help="timed solves of the 3D 128x128x64 scale case (0: skip)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: run the schedule autotuner (precision variant x GMRES restart) on "
+                         "the batch and report its table")
+    ap.add_argument("--batch3d", type=int, default=512,
+                    help="instances of the batched 3D workload (0: skip)")
     ap.add_argument("--merge-cap", type=int, default=256,
                     help="Coupled-AMS merge cap of the 3D scale case")
     args = ap.parse_args()
@@ -733,6 +832,16 @@ def main():
     }
     if args.large > 0:
         line["large_instance"] = large_instance(fams, args.large, 1, args.merge_cap)
+    if args.tune:
+        # the schedule autotuner on the bench batch: arithmetic of the
+        # two-stage step x GMRES restart, each held to the FP64 residual
+        from paper_1705_05784_gb300 import tune
+        best, table = tune.tune(problems(args.batch, rank_seed(rank)), tol=TOL)
+        line["autotune"] = {"best": best, "table": table,
+                            "note": "setup + solve + flux of the batch, host buffers, wall time "
+                                    "after one untimed run per candidate"}
+    if args.batch3d > 0:
+        line["batched_3d"] = batched_3d(fams, args.batch3d, 1, 1)
     if args.serve > 0:
         sv = serving(fams, args.serve, args.plain, 4, args.pipelines, args.max_batch)
         line["serving"] = sv

@@ -157,6 +157,10 @@ typedef struct {
                         blocks A^mm, A^ff and the wells') applied to r2, p += dp3; once
                         per Table 1 sweep or GMRES preconditioner application.  FP64
                         only (FAMS_EINVAL with FAMS_MIXED). */
+  int bf16_p;        /* 1 (with FAMS_MIXED only): P and P^T values of the FP32 restriction
+                        and prolongation stored in BF16 (8-bit mantissa, FP32 arithmetic);
+                        R A P keeps the FP64 P.  A trial of the storage precision: the
+                        FP64 residual still decides convergence. */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */

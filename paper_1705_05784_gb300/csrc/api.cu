@@ -99,6 +99,8 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   if (o.grid_solve < -1 || o.grid_solve > 1) return bad("grid_solve must be -1, 0 or 1");
   if (o.subblock != 0 && o.subblock != 1) return bad("subblock must be 0 or 1");
   if (o.subblock && o.precision != FAMS_FP64) return bad("subblock needs precision FAMS_FP64");
+  if (o.bf16_p != 0 && o.bf16_p != 1) return bad("bf16_p must be 0 or 1");
+  if (o.bf16_p && o.precision != FAMS_MIXED) return bad("bf16_p needs precision FAMS_MIXED");
   return FAMS_OK;
 }
 
@@ -295,6 +297,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.merge_cap = o.basis == FAMS_COUPLED ? o.merge_cap : 0;
     I.grid_solve = o.grid_solve;
     I.subblock = o.subblock;
+    I.bf16_p = o.bf16_p;
     b.prepare_flux = b.prepare_flux || o.prepare_flux == 1;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;

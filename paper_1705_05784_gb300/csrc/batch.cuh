@@ -209,6 +209,8 @@ struct Batch {
   // restart vectors Z of flexible GMRES
   float* p_val32 = nullptr;
   float* pt_val32 = nullptr;
+  unsigned short* p_val16 = nullptr;    // BF16 storage of P and P^T (fams_opts.bf16_p)
+  unsigned short* pt_val16 = nullptr;
   float* ilu32 = nullptr;
   float* pk_lv32 = nullptr;
   float* pk_uv32 = nullptr;

@@ -230,6 +230,10 @@ __global__ void k_inverse_perm(const Inst* inst, int B, const int* off_nc, long 
 
 __device__ inline int wrap(int x, int k) { return x >= k ? x - k : x; }
 
+// values of the row (and column) entering a factorisation ring that each
+// thread loads one step ahead
+constexpr int LU_PF = 4;
+
 constexpr int LU_EXTRA = 32;      // narrow LU ring: columns of fill past the upper band
 constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choice
 // a pivot at most this fraction of the largest entry of its row (as assembled)
@@ -263,9 +267,21 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
     S[e] = (i < n && c <= i && i - c <= kl) ? BEL(i, c) : 0.0;
   }
   __syncthreads();
+  // the row entering the ring at the end of step j (row j + K, columns
+  // j + 1 .. j + K) is still as assembled: loaded when the step starts
+  const bool pf = K <= LU_PF * T;
   for (int j = 0; j < n; ++j) {
     const int km = min(kl, n - 1 - j);
     const int js = j % K, base = wrap(js + 1, K);
+    const int inew = j + K;
+    double pr[LU_PF];
+    if (pf) {
+#pragma unroll
+      for (int q = 0; q < LU_PF; ++q) {
+        const int c = inew - kl + threadIdx.x + q * T;
+        pr[q] = (inew < n && c <= inew) ? BEL(inew, c) : 0.0;
+      }
+    }
     const double d = S[js * K + js];
     const long long db = __double_as_longlong(d);   // positive and finite, tested on the bits
     if (!(db > 0 && db < 0x7ff0000000000000LL)) {
@@ -296,9 +312,15 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
     }
     __syncthreads();
     // row j + K of the original matrix takes row j's slot
-    const int i = j + K;
-    if (i < n)
-      for (int c = i - kl + threadIdx.x; c <= i; c += T) S[js * K + c % K] = BEL(i, c);
+    if (pf) {
+#pragma unroll
+      for (int q = 0; q < LU_PF; ++q) {
+        const int c = inew - kl + threadIdx.x + q * T;
+        if (inew < n && c <= inew) S[js * K + c % K] = pr[q];
+      }
+    } else if (inew < n) {
+      for (int c = inew - kl + threadIdx.x; c <= inew; c += T) S[js * K + c % K] = BEL(inew, c);
+    }
     __syncthreads();
   }
 #undef BEL
@@ -382,7 +404,13 @@ __global__ void k_band_binv(const Inst* inst, int B, CoarseSys cs) {
 // scale in `sc` through the interchanges); an exactly zero column is the
 // extreme case.  A coarse node whose truncated basis function is a single
 // cell inside its own primal block has an R^FV column that sums to zero.
-__global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* only, int* err,
+//
+// The row and the column that enter the ring at the end of step j are still
+// as assembled, so each thread loads its share of them (up to LU_PF values
+// of each) when step j starts, and they arrive while the step eliminates;
+// the entering row's scale is reduced per warp into `scw` and combined by
+// thread 0 when the next step chooses its pivot.
+__global__ void __launch_bounds__(1024) k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* only, int* err,
                               double* gws, long long gstride, int extra, double tau, int* failed) {
   extern __shared__ double dyn[];
   int ii = blockIdx.x;
@@ -397,6 +425,11 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   double* ur = lj + K1;                                // pivot row j
   double* sc = ur + kv + 1;                            // scale of the row in each slot
   double* AB = cs.band + cs.band_off[ii];
+  // the entering row spans columns j+1 .. j+kl+ku+1 (its scale), the ring
+  // takes the first K2 of them; prefetch when every thread holds its share
+  const int RW = kl + ku + 1;
+  const bool pf = RW <= LU_PF * T && kl <= LU_PF * T;
+  __shared__ double scw[32];
   int* ipiv = cs.ipiv + I.nc_off;
   __shared__ double sv[32];
   __shared__ int si[32];
@@ -421,6 +454,17 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
   for (int j = 0; j < n; ++j) {
     const int km = min(kl, n - 1 - j);
     const int jr = j % K1, jc = j % K2;
+    const int inew = j + K1, cnew = j + K2;
+    // entering row inew (columns j+1..) and column cnew (rows j+1..j+kl)
+    double prow[LU_PF], pcol[LU_PF];
+    if (pf) {
+#pragma unroll
+      for (int q = 0; q < LU_PF; ++q) {
+        const int cc = 1 + threadIdx.x + q * T, t = 1 + threadIdx.x + q * T;
+        prow[q] = (cc <= RW && INBAND(inew, j + cc)) ? BEL(inew, j + cc) : 0.0;
+        pcol[q] = (t < K1 && INBAND(j + t, cnew)) ? BEL(j + t, cnew) : 0.0;
+      }
+    }
     double best = -1.0;
     int bi = 0;
     for (int t = threadIdx.x; t <= km; t += T) {
@@ -435,6 +479,11 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
     if (lane == 0) { sv[w] = best; si[w] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (pf && j > 0) {   // scale of the row that entered slot (j-1) % K1 at the last step
+        double m = 0.0;
+        for (int q = 0; q < nw; ++q) m = fmax(m, scw[q]);
+        sc[(j - 1) % K1] = m;
+      }
       double b0 = -1.0;
       int i0 = 0;
       for (int q = 0; q < nw; ++q)
@@ -500,21 +549,33 @@ __global__ void k_band_lu_act(const Inst* inst, int B, CoarseSys cs, const int* 
     __syncthreads();
     // column slot jc becomes column j + K2 (still original in the band: no
     // step so far reached it), row slot jr becomes row j + K1
-    const int inew = j + K1, cnew = j + K2;
-    for (int t = 1 + threadIdx.x; t < K1; t += T) {
-      int i = j + t;
-      SEL(wrap(jr + t, K1), jc) = INBAND(i, cnew) ? BEL(i, cnew) : 0.0;
-    }
-    for (int cc = 1 + threadIdx.x; cc <= K2; cc += T) {
-      int c = j + cc;
-      SEL(jr, wrap(jc + cc, K2)) = INBAND(inew, c) ? BEL(inew, c) : 0.0;
-    }
-    if (w == nw - 1) {   // scale of the entering row, still as assembled in the band
+    if (pf) {
       double m = 0.0;
-      if (inew < n)
-        for (int c = inew - kl + lane; c <= min(n - 1, inew + ku); c += 32) m = fmax(m, fabs(BEL(inew, c)));
+#pragma unroll
+      for (int q = 0; q < LU_PF; ++q) {
+        const int cc = 1 + threadIdx.x + q * T, t = 1 + threadIdx.x + q * T;
+        if (t < K1) SEL(wrap(jr + t, K1), jc) = pcol[q];
+        if (cc <= K2) SEL(jr, wrap(jc + cc, K2)) = prow[q];
+        m = fmax(m, fabs(prow[q]));
+      }
       for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) sc[jr] = m;
+      if (lane == 0) scw[w] = m;
+    } else {
+      for (int t = 1 + threadIdx.x; t < K1; t += T) {
+        int i = j + t;
+        SEL(wrap(jr + t, K1), jc) = INBAND(i, cnew) ? BEL(i, cnew) : 0.0;
+      }
+      for (int cc = 1 + threadIdx.x; cc <= K2; cc += T) {
+        int c = j + cc;
+        SEL(jr, wrap(jc + cc, K2)) = INBAND(inew, c) ? BEL(inew, c) : 0.0;
+      }
+      if (w == nw - 1) {   // scale of the entering row, still as assembled in the band
+        double m = 0.0;
+        if (inew < n)
+          for (int c = inew - kl + lane; c <= min(n - 1, inew + ku); c += 32) m = fmax(m, fabs(BEL(inew, c)));
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) sc[jr] = m;
+      }
     }
     __syncthreads();
   }

@@ -48,6 +48,7 @@ struct Inst {
   int merge_cap;        // Coupled: largest block merged across the media (0: none)
   int grid_solve;       // single instance on every SM: 0 auto, 1 always, -1 never
   int subblock;         // 1: the sub-block smoothing stage after ILU(0)
+  int bf16_p;           // mixed precision: P and P^T values stored in BF16
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells

@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "batch.cuh"
 
 namespace fams {
@@ -75,6 +77,11 @@ __device__ inline double block_sum(double v, double* red) {
 __global__ void k_round(long long n, const double* src, float* dst) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = (float)src[i];
+}
+
+__global__ void k_round_bf16(long long n, const double* src, __nv_bfloat16* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __double2bfloat16(src[i]);
 }
 
 __global__ void k_make_q(long long n, const double* rhs, const double* qD, double* q) {
@@ -135,6 +142,8 @@ struct SolveArgs {
   // FP32 copies and work vectors of the mixed-precision inner stages
   const float* p_val32;
   const float* pt_val32;
+  const __nv_bfloat16* p_val16;    // BF16 storage of P and P^T (fams_opts.bf16_p)
+  const __nv_bfloat16* pt_val16;
   const float* F32;
   const float* pk_lv32;
   const float* pk_uv32;
@@ -147,8 +156,6 @@ struct SolveArgs {
 // the arrays of one arithmetic: FP64 throughout, or the FP32 copies
 template <class T> struct Prec;
 template <> struct Prec<double> {
-  static __device__ const double* pv(const SolveArgs& a) { return a.p_val; }
-  static __device__ const double* ptv(const SolveArgs& a) { return a.pt_val; }
   static __device__ const double* F(const SolveArgs& a, int set = 0) { return set ? a.Fb : a.F; }
   static __device__ const double* lv(const SolveArgs& a, int set = 0) { return set ? a.pk_lvb : a.pk_lv; }
   static __device__ const double* uv(const SolveArgs& a, int set = 0) { return set ? a.pk_uvb : a.pk_uv; }
@@ -157,8 +164,6 @@ template <> struct Prec<double> {
   static __device__ double* ylev(const SolveArgs& a) { return a.ylev; }
 };
 template <> struct Prec<float> {
-  static __device__ const float* pv(const SolveArgs& a) { return a.p_val32; }
-  static __device__ const float* ptv(const SolveArgs& a) { return a.pt_val32; }
   // (the sub-block stage runs in FP64 only: set 1 is never asked for here)
   static __device__ const float* F(const SolveArgs& a, int = 0) { return a.F32; }
   static __device__ const float* lv(const SolveArgs& a, int = 0) { return a.pk_lv32; }
@@ -166,6 +171,22 @@ template <> struct Prec<float> {
   static __device__ const float* ud(const SolveArgs& a, int = 0) { return a.pk_ud32; }
   static __device__ float* y(const SolveArgs& a) { return a.yf; }
   static __device__ float* ylev(const SolveArgs& a) { return a.ylevf; }
+};
+
+// where the restriction and prolongation read P's values: FP64, the FP32
+// copies, or their BF16 storage (widened to FP32 on load)
+template <class TP> struct PVals;
+template <> struct PVals<double> {
+  static __device__ const double* pv(const SolveArgs& a) { return a.p_val; }
+  static __device__ const double* ptv(const SolveArgs& a) { return a.pt_val; }
+};
+template <> struct PVals<float> {
+  static __device__ const float* pv(const SolveArgs& a) { return a.p_val32; }
+  static __device__ const float* ptv(const SolveArgs& a) { return a.pt_val32; }
+};
+template <> struct PVals<__nv_bfloat16> {
+  static __device__ const __nv_bfloat16* pv(const SolveArgs& a) { return a.p_val16; }
+  static __device__ const __nv_bfloat16* ptv(const SolveArgs& a) { return a.pt_val16; }
 };
 
 // y[i] = b[i] - sum_p val[p] v[col[p]] in FP64 for the instance's rows, four
@@ -467,7 +488,7 @@ __device__ inline void mark(long long* cyc, int k) {
 //   out = (base + dp) + (LU)^-1 y   (base null: out = dp + (LU)^-1 y)
 // base + dp is kept in level order (xlev) for the U sweep.
 // out may alias base; r, dp and out must not alias y, ylev or xlev.
-template <class T>
+template <class T, class TP = T>
 __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int ii, const double* r,
                                           double* dp, double* out, const double* base,
                                           const SolveSmem& S, long long* cyc) {
@@ -479,8 +500,8 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   const int* lp = a.lev_ptr + a.lev_off[ii];
   const int nlev = I.nlev;
   const int NT = blockDim.x;
-  const T* ptv = Prec<T>::ptv(a);
-  const T* pv = Prec<T>::pv(a);
+  const TP* ptv = PVals<TP>::ptv(a);
+  const TP* pv = PVals<TP>::pv(a);
   T* y = Prec<T>::y(a);
   T* ylev = Prec<T>::ylev(a);
   stamp(cyc);
@@ -494,7 +515,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       T s = 0;
       // MSMIX: P^T rows for the matrix coarse nodes, indicators for the fracture ones
       if (I.restriction == FAMS_R_FE || (I.restriction == FAMS_R_MIX && perm[k] < I.ncm)) {
-        for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += ptv[p] * (T)r[a.pt_col[p]];
+        for (int p = a.pt_ptr[c] + lane; p < a.pt_ptr[c + 1]; p += 32) s += (T)ptv[p] * (T)r[a.pt_col[p]];
       } else {
         for (int p = a.blk_ptr[c] + lane; p < a.blk_ptr[c + 1]; p += 32) s += (T)r[a.blk_cell[p]];
       }
@@ -526,7 +547,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
       int i = i0 + k * NT;
       if (i < ro + n) {
         T s = 0;
-        for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += pv[p] * (T)S.ecs[a.p_col[p]];
+        for (int p = a.p_ptr[i]; p < a.p_ptr[i + 1]; ++p) s += (T)pv[p] * (T)S.ecs[a.p_col[p]];
         dp[i] = (double)s;
         xlev[a.pk_pos[i]] = (base ? base[i] : 0.0) + (double)s;
       }
@@ -734,7 +755,10 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
     if (!use32)
       two_stage<double>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
     else
-      two_stage<float>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
+      if (I.bf16_p)
+        two_stage<float, __nv_bfloat16>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
+      else
+        two_stage<float>(a, I, ii, a.r, a.dp, a.x, a.x, S, cyc);
     ++it;
   }
   write_stats(a, ii, it, rel, qn, cyc);
@@ -826,7 +850,10 @@ __device__ void gmres_cycle(const SolveArgs& a, const Inst& I, int ii, double* V
     double acc;
     if constexpr (mixed) {
       double* Zk = Z + (long long)k * ld;
-      two_stage<float>(a, I, ii, Vk, a.dp, Zk, nullptr, S, cyc);
+      if (I.bf16_p)
+        two_stage<float, __nv_bfloat16>(a, I, ii, Vk, a.dp, Zk, nullptr, S, cyc);
+      else
+        two_stage<float>(a, I, ii, Vk, a.dp, Zk, nullptr, S, cyc);
       stamp(cyc);
       acc = rows_apply(a, ro, n, Zk, w);
     } else {
@@ -1057,6 +1084,12 @@ int phase_alloc_work(Batch& b) {
     FAMS_TRY(b.alloc((void**)&b.ilu32, sizeof(float) * (nnz + 1)));
     FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (pn + 1)));
     FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (pn + 1)));
+    bool bf = false;
+    for (auto& I : b.h) bf = bf || I.bf16_p;
+    if (bf) {
+      FAMS_TRY(b.alloc((void**)&b.p_val16, sizeof(unsigned short) * (pn + 1)));
+      FAMS_TRY(b.alloc((void**)&b.pt_val16, sizeof(unsigned short) * (pn + 1)));
+    }
     FAMS_TRY(b.alloc((void**)&b.pk_lv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_uv32, sizeof(float) * PK * n1));
     FAMS_TRY(b.alloc((void**)&b.pk_ud32, sizeof(float) * n1));
@@ -1069,6 +1102,12 @@ int phase_alloc_work(Batch& b) {
     round(b.ilu, b.ilu32, nnz);
     round(b.p_val, b.p_val32, pn);
     round(b.pt_val, b.pt_val32, pn);
+    if (b.p_val16 && pn > 0) {
+      fams::note_launch(), k_round_bf16<<<grid_for(pn, 256), 256, 0, b.stream>>>(
+          pn, b.p_val, reinterpret_cast<__nv_bfloat16*>(b.p_val16));
+      fams::note_launch(), k_round_bf16<<<grid_for(pn, 256), 256, 0, b.stream>>>(
+          pn, b.pt_val, reinterpret_cast<__nv_bfloat16*>(b.pt_val16));
+    }
     round(b.pk_lv, b.pk_lv32, PK * n1);
     round(b.pk_uv, b.pk_uv32, PK * n1);
     round(b.pk_ud, b.pk_ud32, n1);
@@ -1090,6 +1129,12 @@ int refresh_mixed(Batch& b) {
   round(b.pk_ud, b.pk_ud32, n1);
   round(b.p_val, b.p_val32, b.tot_pnnz);
   round(b.pt_val, b.pt_val32, b.tot_pnnz);
+  if (b.p_val16 && b.tot_pnnz > 0) {
+    fams::note_launch(), k_round_bf16<<<grid_for(b.tot_pnnz, 256), 256, 0, b.stream>>>(
+        b.tot_pnnz, b.p_val, reinterpret_cast<__nv_bfloat16*>(b.p_val16));
+    fams::note_launch(), k_round_bf16<<<grid_for(b.tot_pnnz, 256), 256, 0, b.stream>>>(
+        b.tot_pnnz, b.pt_val, reinterpret_cast<__nv_bfloat16*>(b.pt_val16));
+  }
   FAMS_CUDA(cudaGetLastError());
   return FAMS_OK;
 }
@@ -1136,6 +1181,8 @@ int run_solve(Batch& b, double tol, float* ms, const int* active) {
   a.ntot = b.tot_row;
   a.tol = tol;
   a.p_val32 = b.p_val32; a.pt_val32 = b.pt_val32; a.F32 = b.ilu32;
+  a.p_val16 = reinterpret_cast<const __nv_bfloat16*>(b.p_val16);
+  a.pt_val16 = reinterpret_cast<const __nv_bfloat16*>(b.pt_val16);
   a.pk_lv32 = b.pk_lv32; a.pk_uv32 = b.pk_uv32; a.pk_ud32 = b.pk_ud32;
   a.xs = b.xs; a.yf = b.yf; a.ylevf = b.ylevf;
   int maxnc = 0;

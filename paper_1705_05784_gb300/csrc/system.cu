@@ -374,6 +374,12 @@ int phase_update_basis(Batch& b, const double* const* scale, double eps, int* re
       b.release(b.pt_val32);
       FAMS_TRY(b.alloc((void**)&b.p_val32, sizeof(float) * (b.tot_pnnz + 1)));
       FAMS_TRY(b.alloc((void**)&b.pt_val32, sizeof(float) * (b.tot_pnnz + 1)));
+      if (b.p_val16) {
+        b.release(b.p_val16);
+        b.release(b.pt_val16);
+        FAMS_TRY(b.alloc((void**)&b.p_val16, sizeof(unsigned short) * (b.tot_pnnz + 1)));
+        FAMS_TRY(b.alloc((void**)&b.pt_val16, sizeof(unsigned short) * (b.tot_pnnz + 1)));
+      }
       FAMS_TRY(refresh_mixed(b));
     }
   }

@@ -68,6 +68,7 @@ class Problem:
     merge_cap: int = 0               # Coupled: largest block merged across the media (0: none)
     grid_solve: int = 0              # single instance on every SM: 0 auto (>= 2^18 unknowns), 1, -1
     subblock: int = 0                # 1: the sub-block smoothing stage after ILU(0)
+    bf16_p: int = 0                  # mixed precision: P and P^T values stored in BF16
     tol: float = 1e-8
     max_iter: int = 200
     krylov: int = 0                  # 0 the Table 1 loop, 1 GMRES(restart)

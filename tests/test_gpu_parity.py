@@ -373,6 +373,31 @@ def test_mixed_precision_reaches_the_fp64_tolerance(built, name, variant, krylov
     assert stats[0]["iterations"] <= ito + max(3, ito // 4)
 
 
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3d"])
+def test_bf16_stored_p_reaches_the_fp64_tolerance(built, name, variant):
+    """fams_opts.bf16_p (P and P^T values of the FP32 restriction and
+    prolongation stored in BF16): GMRES still reaches the FP64 tolerance, the
+    solution matches the FP64 oracle's to tol x cond, and BF16 storage may
+    cost iterations but not convergence; bf16_p without FAMS_MIXED is
+    rejected."""
+    p, g, sysm, c, P, st, ctx = built(name, variant)
+    xo, ito, _, oko, _ = osolver.gmres_solve(st, tol=1e-8, max_iter=p.max_iter, restart=30)
+    q = _mixed(p, 1)
+    q.bf16_p, q.max_iter = 1, 400
+    with _fams().Context(q) as cm:
+        xs, stats = cm.solve(tol=1e-8)
+    x = xs[0]
+    rr = np.linalg.norm(sysm.q - sysm.A @ x) / np.linalg.norm(sysm.q)
+    assert oko and stats[0]["converged"] and rr <= 1e-8
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+    assert stats[0]["iterations"] <= 2 * ito + 10
+    r = copy.copy(p)
+    r.bf16_p = 1
+    with pytest.raises(_fams().FamsError):
+        _fams().Context(r)
+
+
 def test_gmres_and_richardson_instances_share_a_batch(built):
     """A batch mixing both outer iterations gives each instance its own result."""
     pa = _gmres(built("2d32", 0)[0], 30, 200)
