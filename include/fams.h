@@ -161,6 +161,11 @@ typedef struct {
                         and prolongation stored in BF16 (8-bit mantissa, FP32 arithmetic);
                         R A P keeps the FP64 P.  A trial of the storage precision: the
                         FP64 residual still decides convergence. */
+  int coarse_mode;   /* the whole-GPU iteration's coarse solve: 0 automatic (A_c^-1 while
+                        it takes at most 8 GiB, else the band factors), 1 A_c^-1 formed
+                        once (a product per iteration on every SM), 2 the band factors
+                        solved by one CTA per iteration.  The same solution up to
+                        rounding. */
 } fams_opts;
 
 /* Per-solve statistics (nullable argument). */

@@ -101,6 +101,7 @@ int validate(const fams_grid& g, const fams_fracs* f, const fams_opts& o) {
   if (o.subblock && o.precision != FAMS_FP64) return bad("subblock needs precision FAMS_FP64");
   if (o.bf16_p != 0 && o.bf16_p != 1) return bad("bf16_p must be 0 or 1");
   if (o.bf16_p && o.precision != FAMS_MIXED) return bad("bf16_p needs precision FAMS_MIXED");
+  if (o.coarse_mode < 0 || o.coarse_mode > 2) return bad("coarse_mode must be 0, 1 or 2");
   return FAMS_OK;
 }
 
@@ -298,6 +299,7 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
     I.grid_solve = o.grid_solve;
     I.subblock = o.subblock;
     I.bf16_p = o.bf16_p;
+    I.coarse_mode = o.coarse_mode;
     b.prepare_flux = b.prepare_flux || o.prepare_flux == 1;
     I.nm = g.nx * g.ny * I.nz;
     I.m_off = (int)m;

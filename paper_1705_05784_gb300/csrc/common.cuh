@@ -49,6 +49,7 @@ struct Inst {
   int grid_solve;       // single instance on every SM: 0 auto, 1 always, -1 never
   int subblock;         // 1: the sub-block smoothing stage after ILU(0)
   int bf16_p;           // mixed precision: P and P^T values stored in BF16
+  int coarse_mode;      // whole-GPU coarse solve: 0 auto, 1 A_c^-1, 2 band factors
   double alpha;
   // sizes and offsets
   int nm, m_off;      // matrix cells

@@ -21,6 +21,7 @@
 
 #include <cuda_bf16.h>
 
+#include "band_solve.cuh"
 #include "batch.cuh"
 
 namespace fams {
@@ -30,7 +31,6 @@ namespace {
 constexpr int SOLVE_T = 512;
 constexpr int ROWS_ILP = 4;
 constexpr int BAND_BUF = 3072;   // doubles per staged chunk of band columns (24 KiB)
-constexpr int CH_MAX = 64;       // band columns per chunk
 constexpr int SWEEP_RING = 1024; // level positions of recent sweep results kept in shared memory
 // Rows of the triangular sweeps are copied into shared memory STAGE_D - 1
 // levels ahead of their use (asynchronous copies, no registers held):
@@ -230,102 +230,6 @@ __device__ inline double rows_residual(const SolveArgs& a, int ro, int n, const 
     }
   }
   return acc;
-}
-
-// Coarse band solve (LAPACK gbtrs steps on the band factors).  Warps
-// 0..CS_WARPS-1 run the recurrences column by column, splitting each
-// column's rows among them and meeting at a named barrier; the other warps
-// stage the next chunk of band columns into shared memory meanwhile (double
-// buffer, one CTA barrier per chunk).  The staging warps also turn U's
-// diagonal into its reciprocal, so the recurrences never divide.
-constexpr int CS_WARPS = 4;
-constexpr int CS_T = 32 * CS_WARPS;
-
-__device__ inline void cs_sync() { asm volatile("bar.sync 1, %0;" ::"n"(CS_T) : "memory"); }
-
-__device__ void coarse_solve(const double* AB, const int* ipiv, int n, int kl, int ku, double* yb,
-                             double* buf, int* pbuf) {
-  const int kv = kl + ku, ldab = 2 * kl + ku + 1, stride = kv + 1;
-  int ch = BAND_BUF / stride;
-  ch = max(1, min(CH_MAX, ch));
-  const int nch = (n + ch - 1) / ch;
-  const int tid = threadIdx.x;
-  const bool comp = tid < CS_T;
-  const int T = blockDim.x;
-  // forward (L with row interchanges), chunk c holds columns [c ch, (c+1) ch)
-  auto load_fwd = [&](int c, double* dst, int* pdst, int t0, int nt) {
-    int j0 = c * ch;
-    for (int idx = t0; idx < ch * kl; idx += nt) {
-      int jj = idx / kl, t = idx % kl + 1, j = j0 + jj;
-      dst[jj * stride + t - 1] = (j < n && t <= n - 1 - j) ? AB[(long long)(kv + t) + (long long)ldab * j] : 0.0;
-    }
-    for (int jj = t0; jj < ch; jj += nt) pdst[jj] = (j0 + jj < n) ? ipiv[j0 + jj] : 0;
-  };
-  load_fwd(0, buf, pbuf, tid, T);
-  __syncthreads();
-  for (int c = 0; c < nch; ++c) {
-    double* cur = buf + (c & 1) * BAND_BUF;
-    int* pcur = pbuf + (c & 1) * CH_MAX;
-    if (comp) {
-      int j0 = c * ch;
-      for (int jj = 0; jj < ch && j0 + jj < n; ++jj) {
-        int j = j0 + jj;
-        int km = min(kl, n - 1 - j);
-        int pj = pcur[jj];
-        if (pj != j) {
-          if (tid == 0) {
-            double t = yb[j];
-            yb[j] = yb[pj];
-            yb[pj] = t;
-          }
-          cs_sync();
-        }
-        double yj = yb[j];
-        for (int t = 1 + tid; t <= km; t += CS_T) yb[j + t] -= cur[jj * stride + t - 1] * yj;
-        cs_sync();
-      }
-    } else if (c + 1 < nch) {
-      load_fwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, pbuf + ((c + 1) & 1) * CH_MAX, tid - CS_T,
-               T - CS_T);
-    }
-    __syncthreads();
-  }
-  // backward (U, kv superdiagonals, reciprocal diagonal); chunk c holds
-  // columns [n-(c+1)ch, n-c ch).  Rows are updated with x_j = y_j / U_jj
-  // while y_j itself is overwritten one column later, when nothing reads it.
-  auto load_bwd = [&](int c, double* dst, int t0, int nt) {
-    int jhi = n - c * ch, jlo = max(0, jhi - ch);
-    for (int idx = t0; idx < (jhi - jlo) * stride; idx += nt) {
-      int jj = idx / stride, rr = idx % stride, j = jlo + jj;
-      int i = j - kv + rr;
-      double v = (i >= 0) ? AB[(long long)rr + (long long)ldab * j] : 0.0;
-      dst[jj * stride + rr] = rr == kv ? 1.0 / v : v;
-    }
-  };
-  load_bwd(0, buf, tid, T);
-  __syncthreads();
-  int prev = -1;
-  double xprev = 0.0;
-  for (int c = 0; c < nch; ++c) {
-    double* cur = buf + (c & 1) * BAND_BUF;
-    if (comp) {
-      int jhi = n - c * ch, jlo = max(0, jhi - ch);
-      for (int j = jhi - 1; j >= jlo; --j) {
-        const double* colj = cur + (j - jlo) * stride;
-        double xj = yb[j] * colj[kv];
-        if (tid == 0 && prev >= 0) yb[prev] = xprev;
-        for (int i = max(0, j - kv) + tid; i < j; i += CS_T) yb[i] -= colj[kv + i - j] * xj;
-        prev = j;
-        xprev = xj;
-        cs_sync();
-      }
-    } else if (c + 1 < nch) {
-      load_bwd(c + 1, buf + ((c + 1) & 1) * BAND_BUF, tid - CS_T, T - CS_T);
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && prev >= 0) yb[prev] = xprev;
-  __syncthreads();
 }
 
 // Band solve of factors without row interchanges (LDL^T, stored as unit L and
@@ -532,7 +436,7 @@ __device__ __forceinline__ void two_stage(const SolveArgs& a, const Inst& I, int
   if (a.cs.nopiv[ii] && 4 * (COARSE_NB + kl) <= 2 * BAND_BUF)
     coarse_solve_blocked(AB, a.cs.binv + a.cs.binv_off[ii], nc, kl, ku, S.yb, S.buf);
   else
-    coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf);
+    band::coarse_solve(AB, ipiv, nc, kl, ku, S.yb, S.buf, S.pbuf, BAND_BUF);
   for (int k = threadIdx.x; k < nc; k += NT) {
     S.ecs[perm[k]] = S.yb[k];
     a.csol[co + perm[k]] = S.yb[k];
@@ -717,7 +621,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_solve(SolveArgs a) {
   extern __shared__ double sm[];
   __shared__ double red[40];
   __shared__ int s_done;
-  __shared__ int pbuf[2 * CH_MAX];
+  __shared__ int pbuf[2 * band::CH_MAX];
   int ii = blockIdx.x;
   const Inst& I = a.inst[ii];
   if (I.krylov != FAMS_KRYLOV_NONE || (a.active && !a.active[ii])) return;
@@ -987,7 +891,7 @@ __global__ void __launch_bounds__(SOLVE_T, 2) k_gmres(SolveArgs a, double* kry, 
   extern __shared__ double sm[];
   __shared__ double red[40];
   __shared__ int s_done;
-  __shared__ int pbuf[2 * CH_MAX];
+  __shared__ int pbuf[2 * band::CH_MAX];
   int ii = blockIdx.x;
   const Inst& I = a.inst[ii];
   if (I.krylov != FAMS_KRYLOV_GMRES || (a.active && !a.active[ii])) return;

@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "band_solve.cuh"
 #include "batch.cuh"
 
 namespace fams {
@@ -37,6 +38,14 @@ namespace {
 constexpr int GT = 512;                     // threads per CTA
 constexpr long long GRID_SPIN = 1LL << 24;  // polls of a barrier (~2-3 s with the back-off)
 constexpr int INV_NR = 8;                   // right-hand sides per CTA pass of the inverse
+// The iteration's coarse solve: A_c^-1 formed once (about 2.5 nc^2 kl FMAs
+// on every SM, then a product per iteration), or the band factors solved by
+// one CTA per iteration (band mode).  Measured on 14k and 16k coarse
+// unknowns the one-CTA band solve takes 26-240 ms per iteration (a
+// synchronisation per band column), so the inverse stays the automatic
+// choice while it fits in GRID_INV_BYTES of device memory.
+constexpr long long GRID_INV_BYTES = 8LL << 30;
+constexpr int GRID_BAND_BUF = 3072;         // doubles per band chunk (at least kl + ku + 1)
 
 struct GridBar {
   unsigned int count;
@@ -77,7 +86,13 @@ struct GArgs {
   const double* pk_udb;
   int subblock;
   long long ntot;        // stride of the PK arrays
-  const double* ainv;    // A_c^-1, nc x nc, row-major, coarse order
+  const double* ainv;    // A_c^-1, nc x nc, row-major, coarse order (null: band mode)
+  // band mode: the band LU factors, pivots and band order; CTA 0 solves with
+  // them in shared memory (hsm doubles of Hessenberg data, then nc + 2 bb)
+  const double* band;
+  const int* ipiv;
+  const int* perm;
+  int kl, ku, bb, hsm;
   const double* q;
   double* x;
   double* r;
@@ -193,13 +208,27 @@ __device__ bool two_stage_grid(const GArgs& a, const double* r, double* out, con
     if (lane == 0) a.rc[k] = s;
   }
   if (!grid_sync(a.bar)) return false;
-  // e_c = A_c^-1 r_c: a warp per coarse row of the inverse
-  for (long long k = gw; k < a.nc; k += nw) {
-    const double* row = a.ainv + k * a.nc;
-    double s = 0.0;
-    for (int j = lane; j < a.nc; j += 32) s += row[j] * ldv(a.rc + j);
-    s = warp_sum(s);
-    if (lane == 0) a.ec[k] = s;
+  if (a.ainv) {
+    // e_c = A_c^-1 r_c: a warp per coarse row of the inverse
+    for (long long k = gw; k < a.nc; k += nw) {
+      const double* row = a.ainv + k * a.nc;
+      double s = 0.0;
+      for (int j = lane; j < a.nc; j += 32) s += row[j] * ldv(a.rc + j);
+      s = warp_sum(s);
+      if (lane == 0) a.ec[k] = s;
+    }
+  } else if (blockIdx.x == 0) {
+    // e_c by the band factors on CTA 0 (the others wait at the barrier): r_c
+    // gathered into band order in shared memory, the gbtrs steps, scattered
+    // back in coarse order
+    extern __shared__ double sm[];
+    __shared__ int pbuf[2 * band::CH_MAX];
+    double* yb = sm + a.hsm;
+    double* bbuf = yb + a.nc;
+    for (int k = threadIdx.x; k < a.nc; k += blockDim.x) yb[k] = ldv(a.rc + a.perm[k]);
+    __syncthreads();
+    band::coarse_solve(a.band, a.ipiv, a.nc, a.kl, a.ku, yb, bbuf, pbuf, a.bb);
+    for (int k = threadIdx.x; k < a.nc; k += blockDim.x) a.ec[a.perm[k]] = yb[k];
   }
   if (!grid_sync(a.bar)) return false;
   // dp = P e_c
@@ -809,9 +838,26 @@ int run_solve_grid(Batch& b, double tol, float* ms) {
     if (ms) *ms = 0.f;
     return FAMS_OK;
   }
-  FAMS_TRY(coarse_inverse(b));
   const int m = I.restart;
-  const size_t smem = sizeof(double) * ((size_t)(m + 1) * m + 4 * (size_t)m + 2);
+  const size_t hsm = (size_t)(m + 1) * m + 4 * (size_t)m + 2;
+  size_t smem = sizeof(double) * hsm;
+  // large coarse systems: band mode when CTA 0 holds the right-hand side and
+  // two band chunks in shared memory; otherwise A_c^-1
+  const int kl = b.csh[0].kl[0], ku = b.csh[0].ku[0];
+  const int bb = std::max(GRID_BAND_BUF, kl + ku + 1);
+  int max_smem = 0;
+  FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
+  const size_t smem_band = sizeof(double) * (hsm + (size_t)I.nc + 2 * (size_t)bb);
+  const bool fits = (long long)smem_band + 2048 <= max_smem;
+  const bool big = (long long)I.nc * I.nc * (long long)sizeof(double) > GRID_INV_BYTES;
+  const bool band_mode = fits && (I.coarse_mode == 2 || (I.coarse_mode == 0 && big));
+  if (band_mode) {
+    smem = smem_band;
+    FAMS_CUDA(cudaFuncSetAttribute(k_gmres_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  } else {
+    FAMS_TRY(coarse_inverse(b));
+  }
   int nblk = 0;
   FAMS_TRY(grid_blocks(b, (const void*)k_gmres_grid, smem, &nblk));
   FAMS_TRY(grid_bar(b, nblk));
@@ -828,7 +874,11 @@ int run_solve_grid(Batch& b, double tol, float* ms) {
   a.Fb = b.ilu_b; a.pk_lvb = b.pk_lv_b; a.pk_uvb = b.pk_uv_b; a.pk_udb = b.pk_ud_b;
   a.subblock = I.subblock;
   a.ntot = b.tot_row;
-  a.ainv = b.ainv;
+  a.ainv = band_mode ? nullptr : b.ainv;
+  a.band = b.cs[0].band + b.csh[0].band_off[0];
+  a.ipiv = b.cs[0].ipiv;
+  a.perm = b.cs[0].perm;
+  a.kl = kl; a.ku = ku; a.bb = bb; a.hsm = (int)hsm;
   a.q = b.q; a.x = b.x; a.r = b.r; a.dp = b.dp; a.y = b.y; a.ylev = b.ylev;
   a.rc = b.rc; a.ec = b.ec; a.V = b.krylov;
   a.stat = b.stat; a.hist = b.hist; a.hist_len = b.hist_len;

@@ -46,7 +46,8 @@ class fams_opts(C.Structure):
                 ("max_iter", C.c_int), ("precision", C.c_int), ("krylov", C.c_int),
                 ("restart", C.c_int),
                 ("prepare_flux", C.c_int), ("merge_cap", C.c_int),
-                ("grid_solve", C.c_int), ("subblock", C.c_int), ("bf16_p", C.c_int)]
+                ("grid_solve", C.c_int), ("subblock", C.c_int), ("bf16_p", C.c_int),
+                ("coarse_mode", C.c_int)]
 
 
 class fams_wells(C.Structure):
@@ -157,7 +158,8 @@ def _args(prob):
                   prob.max_iter, getattr(prob, "precision", FP64), getattr(prob, "krylov", 0),
                   getattr(prob, "restart", 30), getattr(prob, "prepare_flux", 0),
                   getattr(prob, "merge_cap", 0), getattr(prob, "grid_solve", 0),
-                  getattr(prob, "subblock", 0), getattr(prob, "bf16_p", 0))
+                  getattr(prob, "subblock", 0), getattr(prob, "bf16_p", 0),
+                  getattr(prob, "coarse_mode", 0))
     return g, perm, f, o, (xy, kf)
 
 

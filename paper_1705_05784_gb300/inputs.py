@@ -69,6 +69,7 @@ class Problem:
     grid_solve: int = 0              # single instance on every SM: 0 auto (>= 2^18 unknowns), 1, -1
     subblock: int = 0                # 1: the sub-block smoothing stage after ILU(0)
     bf16_p: int = 0                  # mixed precision: P and P^T values stored in BF16
+    coarse_mode: int = 0             # whole-GPU coarse solve: 0 auto, 1 A_c^-1, 2 band factors
     tol: float = 1e-8
     max_iter: int = 200
     krylov: int = 0                  # 0 the Table 1 loop, 1 GMRES(restart)

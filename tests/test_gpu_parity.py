@@ -976,17 +976,18 @@ def test_coupled_merge_cap_matches_the_oracle(name, cap):
         assert np.linalg.norm(xs[0] - xo) / np.linalg.norm(xo) < 1e-10
 
 
+@pytest.mark.parametrize("coarse_mode", [1, 2])
 @pytest.mark.parametrize("restriction", [0, 1])
 @pytest.mark.parametrize("name", ["2d64", "2d50ragged", "3d", "3dlayers"])
-def test_whole_gpu_solve_matches_the_oracle(name, restriction):
+def test_whole_gpu_solve_matches_the_oracle(name, restriction, coarse_mode):
     """The iteration of a single instance on every SM (fams_opts.grid_solve =
-    1: one cooperative kernel, A_c^-1 formed from the band factors, grid
-    barriers per ILU level): a fixed-count GMRES trajectory to 1e-10 against
-    the oracle, and the converged solve in the same iteration count (+-1) as
-    the one-CTA kernel."""
+    1: one cooperative kernel, grid barriers per ILU level; the coarse solve
+    by A_c^-1 formed from the band factors or by the band factors on one CTA):
+    a fixed-count GMRES trajectory to 1e-10 against the oracle, and the
+    converged solve in the same iteration count (+-1) as the one-CTA kernel."""
     fams = _fams()
     p = _gmres(_case(name, 3 if name.startswith("3d") else 1, restriction), 10, 17)
-    p.grid_solve = 1
+    p.grid_solve, p.coarse_mode = 1, coarse_mode
     g, sysm, c, P, st = oracle.build(p)
     xo, ito, _, _, _ = osolver.gmres_solve(st, tol=0.0, max_iter=17, restart=10)
     with fams.Context(p) as ctx:
@@ -1061,3 +1062,23 @@ def test_oversize_coarse_band_goes_to_the_whole_gpu():
         with pytest.raises(fams.FamsError) as e:
             c.solve(tol=1e-8)
         assert e.value.status == fams.ECAPACITY
+
+
+def test_whole_gpu_coarse_modes_agree_on_a_large_coarse_system():
+    """7396 coarse unknowns (256^2 cells at coarsening 3): solving with the
+    band factors on one CTA and with A_c^-1 gives the same iterations and
+    solution to 1e-10."""
+    fams = _fams()
+    p = inputs.config_2d(256, 2.0, 16.0, 20, (20, 80), 1e4, 3, 6, seed=12, basis=1, restriction=1,
+                         alpha=1e-2, krylov=1, restart=30, max_iter=200)
+    p.grid_solve = 1
+    res = []
+    for mode in (2, 1):
+        p.coarse_mode = mode
+        with fams.Context(p) as c:
+            assert c.sizes()["n_coarse"] > 6000
+            xs, st = c.solve(tol=1e-9)
+            assert st[0]["converged"]
+            res.append((xs[0], st[0]["iterations"]))
+    assert res[0][1] == res[1][1]
+    assert np.linalg.norm(res[0][0] - res[1][0]) / np.linalg.norm(res[1][0]) < 1e-10
