@@ -313,6 +313,51 @@ def gmres_bytes(s, iters, restart):
     return total
 
 
+STAGES = ("residual_spmv_gram_schmidt", "restriction", "coarse_band_solve",
+          "prolongation_r1", "ilu_L_sweep", "ilu_U_sweep")
+
+
+def stage_bytes(s):
+    """Algorithmic bytes of one GMRES step's phases for one instance (FP64
+    values 8 B, int32 indices 4 B; the phases of fams_query(STAGE_CYCLES)),
+    the Gram-Schmidt part at the cycle's average basis size."""
+    n, nnz, nnzp, nc, ldab = s["n"], s["nnz"], s["nnzp"], s["nc"], s["ldab"]
+    a_pass = 12 * nnz + 4 * (n + 1)
+    return {"restriction": 12 * nnzp + 4 * (nc + 1) + 8 * n,
+            "coarse_band_solve": 8 * ldab * nc + 16 * 32 * nc,
+            "prolongation_r1": 12 * nnzp + 4 * (n + 1) + a_pass + 8 * n * 7 + 8 * n,
+            "ilu_L_sweep": 72 * n,
+            "ilu_U_sweep": 104 * n}
+
+
+def stage_roofline(fams, probs, S, peak, sm_mhz):
+    """Per-phase HBM rate of the GMRES kernel: a phase's algorithmic bytes
+    per step of every instance over the phase's SM cycles per step of the
+    median instance (fams_query(FAMS_Q_STAGE_CYCLES)), i.e. the rate the
+    resident instances reach while all run that phase."""
+    import numpy as np
+    with fams.Context(probs) as c:
+        _, st = c.solve(tol=TOL)
+        cyc = np.array([c.query("STAGE_CYCLES", i) for i in range(len(probs))])
+    its = np.array([max(x["iterations"], 1) for x in st], dtype=float)
+    per = np.median(cyc / its[:, None], axis=0)
+    hz = (sm_mhz or 2070.0) * 1e6
+    out = {}
+    sb = [stage_bytes(s) for s in S]
+    for k, name in enumerate(STAGES):
+        if k == 0:
+            # w = A z, the fused Gram-Schmidt passes and the scaling at the average basis size
+            byts = sum(gmres_bytes(s, int(i), probs[j].restart) - (int(i) + 1) * _passes(s)[1]
+                       for j, (s, i) in enumerate(zip(S, its)))
+            byts /= float(its.mean())
+        else:
+            byts = sum(b[name] for b in sb)
+        gbs = byts / (per[k] / hz) / 1e9
+        out[name] = {"mcycles_per_step": round(per[k] / 1e6, 3), "gb_per_step": round(byts / 1e9, 3),
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    return out
+
+
 def sizes_of(ctx, i):
     sz = ctx.sizes(i)
     n = sz["n_matrix"] + sz["n_frac"]
@@ -832,6 +877,11 @@ def main():
     }
     if args.large > 0:
         line["large_instance"] = large_instance(fams, args.large, 1, args.merge_cap)
+    line["stage_roofline"] = {
+        "phases": stage_roofline(fams, probs, S, peak, line["clocks"].get("sm_mhz")),
+        "note": "per phase of k_gmres: algorithmic bytes of one step of every instance / SM "
+                "cycles of one step of the median instance (fams_query STAGE_CYCLES), of measured "
+                "HBM; phases of different instances overlap in the kernel"}
     if args.tune:
         # the schedule autotuner on the bench batch: arithmetic of the
         # two-stage step x GMRES restart, each held to the FP64 residual
