@@ -248,9 +248,12 @@ constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choi
 // the solves need no second code path: unit lower multipliers
 // L'(i,j) = S(i,j) / d_j, upper row U(j,c) = S(c,j) (= d_j L'(c,j)), pivot
 // rows ipiv[j] = j.  A non-positive or non-finite pivot sets failed[ii]; the
-// host then refactors that instance with the band LU.
-__global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* only, int* failed) {
-  extern __shared__ double S[];
+// host then refactors that instance with the band LU.  A ring too large for
+// shared memory lives in a global slice (gws + gslot[ii] gstride; the
+// column below the pivot stays in shared memory).
+__global__ void __launch_bounds__(1024) k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* only, int* failed,
+                           double* gws, const int* gslot, long long gstride) {
+  extern __shared__ double dyn[];
   int ii = blockIdx.x;
   if (!only[ii]) return;
   const Inst& I = inst[ii];
@@ -259,7 +262,8 @@ __global__ void k_band_ldl(const Inst* inst, int B, CoarseSys cs, const int* onl
   const int nw = T >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* AB = cs.band + cs.band_off[ii];
   int* ipiv = cs.ipiv + I.nc_off;
-  double* colj = S + (long long)K * K;   // column j below the pivot
+  double* S = gws ? gws + (long long)gslot[ii] * gstride : dyn;
+  double* colj = gws ? dyn : S + (long long)K * K;   // column j below the pivot
   __shared__ double s_inv;
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
   for (int e = threadIdx.x; e < K * K; e += T) {
@@ -704,28 +708,53 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;   // static shared memory of the kernels
-  std::vector<int> spd(B, 0), lu(B, 0), ldl_ok(B, 0);
-  size_t ldl_smem = 0;
+  // (rings too large for shared memory in global slices: LDL^T on a global
+  // ring has half the band LU's work and no pivot search)
+  std::vector<int> spd(B, 0), lu(B, 0), ldl_ok(B, 0), spd_s(B, 0), spd_g(B, 0), gslot(B, -1);
+  size_t ldl_smem = 0, ldl_gsmem = 0;
+  long long gstride = 0;
+  int ng = 0;
   for (int i = 0; i < B; ++i) {
     bool fe = mode == 1 || (mode < 0 && b.h[i].restriction == FAMS_R_FE);
-    size_t need = sizeof(double) * ((size_t)(ch.kl[i] + 1) * (ch.kl[i] + 1) + ch.kl[i] + 1);
-    if (fe && ch.kl[i] == ch.ku[i] && need <= (size_t)max_smem) {
+    const size_t K = (size_t)ch.kl[i] + 1;
+    size_t need = sizeof(double) * (K * K + K);
+    if (fe && ch.kl[i] == ch.ku[i]) {
       spd[i] = 1;
-      ldl_smem = std::max(ldl_smem, need);
+      if (need <= (size_t)max_smem) {
+        spd_s[i] = 1;
+        ldl_smem = std::max(ldl_smem, need);
+      } else {
+        spd_g[i] = 1;
+        gslot[i] = ng++;
+        gstride = std::max(gstride, (long long)(K * K));
+        ldl_gsmem = std::max(ldl_gsmem, sizeof(double) * K);
+      }
     } else {
       lu[i] = 1;
     }
   }
-  int *d_spd = nullptr, *d_lu = nullptr;
+  int *d_spd = nullptr, *d_lu = nullptr, *d_spdg = nullptr, *d_gslot = nullptr;
   FAMS_TRY(b.scratch((void**)&d_spd, sizeof(int) * B));
   FAMS_TRY(b.scratch((void**)&d_lu, sizeof(int) * B));
-  FAMS_CUDA(cudaMemcpyAsync(d_spd, spd.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  FAMS_CUDA(cudaMemcpyAsync(d_spd, spd_s.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   FAMS_CUDA(cudaMemsetAsync(d_lu, 0, sizeof(int) * B, st));
   FAMS_CUDA(cudaMemsetAsync(cs.bad, 0, sizeof(int) * B, st));
-  if (ldl_smem > 0) {
+  if (ldl_smem > 0 || ng > 0) {
     FAMS_CUDA(cudaFuncSetAttribute(k_band_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    max_smem));
-    fams::note_launch(), k_band_ldl<<<B, 512, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu);
+    if (ldl_smem > 0)
+      fams::note_launch(), k_band_ldl<<<B, 512, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu,
+                                                               nullptr, nullptr, 0);
+    if (ng > 0) {
+      double* gws = nullptr;
+      FAMS_TRY(b.scratch((void**)&d_spdg, sizeof(int) * B));
+      FAMS_TRY(b.scratch((void**)&d_gslot, sizeof(int) * B));
+      FAMS_TRY(b.scratch((void**)&gws, sizeof(double) * (size_t)gstride * ng));
+      FAMS_CUDA(cudaMemcpyAsync(d_spdg, spd_g.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+      FAMS_CUDA(cudaMemcpyAsync(d_gslot, gslot.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+      fams::note_launch(), k_band_ldl<<<B, 1024, ldl_gsmem, st>>>(b.d_inst, B, cs, d_spdg, d_lu,
+                                                                 gws, d_gslot, gstride);
+    }
     FAMS_CUDA(cudaGetLastError());
     std::vector<int> failed(B, 0);
     FAMS_CUDA(cudaMemcpyAsync(failed.data(), d_lu, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
