@@ -881,7 +881,9 @@ def main():
         "phases": stage_roofline(fams, probs, S, peak, line["clocks"].get("sm_mhz")),
         "note": "per phase of k_gmres: algorithmic bytes of one step of every instance / SM "
                 "cycles of one step of the median instance (fams_query STAGE_CYCLES), of measured "
-                "HBM; phases of different instances overlap in the kernel"}
+                "HBM; phases of different instances overlap in the kernel, and the Gram-Schmidt "
+                "passes re-read w (0.5 MB per instance) from L2, so that phase's algorithmic rate "
+                "exceeds HBM"}
     if args.tune:
         # the schedule autotuner on the bench batch: arithmetic of the
         # two-stage step x GMRES restart, each held to the FP64 residual
