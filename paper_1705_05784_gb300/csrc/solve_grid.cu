@@ -595,22 +595,26 @@ __global__ void __launch_bounds__(GT) k_ilu_factor_grid(const int* rowptr, const
 
 // Band LU with partial pivoting (LAPACK gbtf2 steps) of one coarse system on
 // the whole GPU, in place in the band storage (ldab = 2 kl + ku + 1, the fill
-// rows zero on entry).  Step j: CTA 0 picks the pivot of column j (largest
+// rows zero on entry).  Step j: the owner of column j picks its pivot (largest
 // magnitude, lowest row on ties), applies the scaled singularity test of the
 // one-CTA factorisations (pivot at most SING_EPS times the largest entry of
 // its row as assembled; row scales follow the interchanges), stores the pivot
-// row and the multipliers (column j of L) and publishes the multipliers; after
-// a grid barrier each CTA interchanges and updates its own columns (column c
-// belongs to CTA c mod gridDim) among j + 1 .. j + kl + ku; a second barrier
-// ends the step.  ctl[0]: pivot offset of the step, ctl[1]: 1 + the step of a
-// singular pivot (0: none).
+// row and the multipliers (column j of L) and publishes the multipliers; each
+// CTA then interchanges and updates its own columns (column c belongs to CTA
+// c mod gridDim) among j + 1 .. j + kl + ku, and the owner of column j + 1
+// chooses step j + 1's pivot as soon as that column is updated, so a step
+// ends with one grid barrier.  ctl[1]: 1 + the step of a singular pivot (0:
+// none); ctl[2 + (j & 1)]: pivot offset of step j.
 __global__ void __launch_bounds__(GT) k_band_lu_grid(double* AB, int* ipiv, int n, int kl, int ku,
                                                    double* sc, double* mult, int* ctl,
                                                    GridBar* bar) {
   const int kv = kl + ku, ldab = 2 * kl + ku + 1;
   const long long T = gthreads(), t0 = gtid();
+  const int G = (int)gridDim.x;
   __shared__ double sv[32];
   __shared__ int si[32];
+  __shared__ int s_p;
+  __shared__ double s_piv;
 #define BEL(i, c) AB[(long long)(kv + (i) - (c)) + (long long)ldab * (c)]
   // row scales of the matrix as assembled
   for (long long i = t0; i < n; i += T) {
@@ -619,63 +623,70 @@ __global__ void __launch_bounds__(GT) k_band_lu_grid(double* AB, int* ipiv, int 
       m = fmax(m, fabs(BEL(i, c)));
     sc[i] = m;
   }
-  if (!grid_sync(bar)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = 0; j < n; ++j) {
+  // Step j's pivot, by the CTA that owns column j (c mod G = blockIdx): the
+  // largest entry of the column below the diagonal, the row interchange of
+  // the scales, the multipliers (into the half of `mult` for j's parity)
+  // and the interchange for the other CTAs (ctl[2 + parity]); a numerically
+  // singular column sets ctl[1] = 1 + j.
+  auto pivot = [&](int j) {
     const int km = min(kl, n - 1 - j);
-    if (blockIdx.x == 0) {
-      double best = -1.0;
-      int bi = 0;
-      for (int t = threadIdx.x; t <= km; t += blockDim.x) {
-        const double v = fabs(ldv(&BEL(j + t, j)));
-        if (v > best) { best = v; bi = t; }
-      }
-      for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) { sv[w] = best; si[w] = bi; }
-      __syncthreads();
-      __shared__ int s_p;
-      __shared__ double s_piv;
-      if (threadIdx.x == 0) {
-        double b0 = -1.0;
-        int i0 = 0;
-        for (int q = 0; q < nw; ++q)
-          if (sv[q] > b0 || (sv[q] == b0 && si[q] < i0)) { b0 = sv[q]; i0 = si[q]; }
-        const double p0 = ldv(&BEL(j + i0, j));
-        if (!(b0 > 0.0) || !isfinite(b0) || !(fabs(p0) > SING_EPS * ldv(sc + j + i0))) {
-          ctl[1] = 1 + j;
-        } else {
-          ipiv[j] = j + i0;
-          const double t = ldv(sc + j);
-          sc[j] = ldv(sc + j + i0);
-          sc[j + i0] = t;
-        }
-        ctl[0] = i0;
-        s_p = i0;
-        s_piv = p0;
-      }
-      __syncthreads();
-      const int p = s_p;
-      const double inv = 1.0 / s_piv;
-      // multipliers of the interchanged column j: row j + p holds the old row j
-      const double ajj = ldv(&BEL(j, j));
-      for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) {
-        const double v = (t == p ? ajj : ldv(&BEL(j + t, j))) * inv;
-        mult[t] = v;
-      }
-      __syncthreads();
-      for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) BEL(j + t, j) = mult[t];
-      if (threadIdx.x == 0) BEL(j, j) = s_piv;
+    double best = -1.0;
+    int bi = 0;
+    for (int t = threadIdx.x; t <= km; t += blockDim.x) {
+      const double v = fabs(ldv(&BEL(j + t, j)));
+      if (v > best) { best = v; bi = t; }
     }
-    if (!grid_sync(bar)) return;
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[w] = best; si[w] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = 0;
+      for (int q = 0; q < nw; ++q)
+        if (sv[q] > b0 || (sv[q] == b0 && si[q] < i0)) { b0 = sv[q]; i0 = si[q]; }
+      const double p0 = ldv(&BEL(j + i0, j));
+      if (!(b0 > 0.0) || !isfinite(b0) || !(fabs(p0) > SING_EPS * ldv(sc + j + i0))) {
+        ctl[1] = 1 + j;
+      } else {
+        ipiv[j] = j + i0;
+        const double t = ldv(sc + j);
+        sc[j] = ldv(sc + j + i0);
+        sc[j + i0] = t;
+      }
+      ctl[2 + (j & 1)] = i0;
+      s_p = i0;
+      s_piv = p0;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const double inv = 1.0 / s_piv;
+    double* mj = mult + (long long)(j & 1) * (kl + 2);
+    // multipliers of the interchanged column j: row j + p holds the old row j
+    const double ajj = ldv(&BEL(j, j));
+    for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) {
+      const double v = (t == p ? ajj : ldv(&BEL(j + t, j))) * inv;
+      mj[t] = v;
+    }
+    __syncthreads();
+    for (int t = 1 + threadIdx.x; t <= km; t += blockDim.x) BEL(j + t, j) = mj[t];
+    if (threadIdx.x == 0) BEL(j, j) = s_piv;
+  };
+  if (!grid_sync(bar)) return;
+  if (n > 0 && blockIdx.x == 0) pivot(0);
+  if (!grid_sync(bar)) return;
+  for (int j = 0; j < n; ++j) {
     if (*(volatile int*)(ctl + 1)) return;
-    const int p = *(volatile int*)ctl;
+    const int km = min(kl, n - 1 - j);
+    const int p = *(volatile int*)(ctl + 2 + (j & 1));
+    const double* mj = mult + (long long)(j & 1) * (kl + 2);
     // interchange and update the columns (j, j + kl + ku] this CTA owns (c mod
-    // gridDim = blockIdx), a warp per column
-    const int cend = min(n - 1, j + kv), G = (int)gridDim.x;
+    // G = blockIdx), a warp per column; the owner's first column is j + 1
+    const int cend = min(n - 1, j + kv);
     const int c0 = j + 1 + (((int)blockIdx.x - (j + 1) % G) % G + G) % G;
     int idx = 0;
     for (int c = c0; c <= cend; c += G, ++idx) {
@@ -690,8 +701,15 @@ __global__ void __launch_bounds__(GT) k_band_lu_grid(double* AB, int* ipiv, int 
       }
       const double ujc = BEL(j, c);
       if (ujc != 0.0)
-        for (int t = 1 + lane; t <= km; t += 32) BEL(j + t, c) -= ldv(mult + t) * ujc;
+        for (int t = 1 + lane; t <= km; t += 32) BEL(j + t, c) -= ldv(mj + t) * ujc;
       __syncwarp();
+    }
+    // look-ahead: the owner of column j + 1, whose warp 0 has just updated
+    // it, chooses step j + 1's pivot before the barrier (one grid barrier
+    // per step; the search overlaps the other CTAs' updates)
+    if (j + 1 < n && (int)blockIdx.x == (j + 1) % G) {
+      __syncthreads();
+      pivot(j + 1);
     }
     if (!grid_sync(bar)) return;
   }
@@ -804,7 +822,7 @@ int band_lu_grid(Batch& b, CoarseSys& cs, CoarseHost& ch) {
   double *sc = nullptr, *mult = nullptr;
   int* ctl = nullptr;
   FAMS_TRY(b.scratch((void**)&sc, sizeof(double) * (n + 1)));
-  FAMS_TRY(b.scratch((void**)&mult, sizeof(double) * (kl + 2)));
+  FAMS_TRY(b.scratch((void**)&mult, sizeof(double) * 2 * (kl + 2)));
   FAMS_TRY(b.scratch((void**)&ctl, sizeof(int) * 4));
   FAMS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(int) * 4, b.stream));
   double* AB = cs.band + ch.band_off[0];
