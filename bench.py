@@ -246,7 +246,7 @@ def serving(fams, n_req, n_plain, seed, pipelines=4, max_batch=64):
     # update: the base problem set up, fams_update, solve from zero, flux)
     times = []
     ok_p = 0
-    for k, ev in enumerate(events[:n_plain]):
+    for k, ev in enumerate(events[:n_plain] if n_plain >= 0 else events):
         p = ev[1] if ev[0] == "new" else events[ev[1]][1]
         t = time.perf_counter()
         try:
@@ -704,12 +704,13 @@ def main():
                     help="mixed: FP32 inner stages with FP64 residuals and refinement")
     ap.add_argument("--krylov", choices=["gmres", "none"], default="gmres")
     ap.add_argument("--restart", type=int, default=30, help="GMRES cycle length")
-    ap.add_argument("--serve", type=int, default=32,
+    ap.add_argument("--serve", type=int, default=24,
                     help="requests in the served stream (0: skip the serving measurement)")
     ap.add_argument("--pipelines", type=int, default=4, help="server: micro-batches in flight")
     ap.add_argument("--max-batch", type=int, default=64, help="server: requests per micro-batch")
-    ap.add_argument("--plain", type=int, default=8,
-                    help="requests of the stream solved one by one for the plain comparison")
+    ap.add_argument("--plain", type=int, default=-1,
+                    help="requests of the stream solved one by one for the plain comparison "
+                         "(-1: all of them, the same requests as the served stream)")
     ap.add_argument("--large", type=int, default=2,
                     help="timed solves of the 3D 128x128x64 scale case (0: skip)")
     ap.add_argument("--tune", type=int, default=1,
