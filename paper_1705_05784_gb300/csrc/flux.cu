@@ -16,6 +16,7 @@
 // steps 2 and 4.
 #include <algorithm>
 
+#include "band_solve.cuh"
 #include "batch.cuh"
 #include "dense.cuh"
 
@@ -32,14 +33,17 @@ __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, co
                              const int* col, const double* val, const int* blk_ptr,
                              const int* blk_cell, const int* p_ptr, const int* p_col,
                              const double* p_val, const double* q, const double* x, double* r,
-                             double* pp, double* gws, long long gstride) {
+                             double* pp, double* gws, long long gstride, int bb) {
   extern __shared__ double sm[];
+  __shared__ int pbuf[2 * band::CH_MAX];
   int ii = list[blockIdx.x];
   const Inst& I = inst[ii];
   int n = I.n, ro = I.row_off, nc = I.nc, co = I.nc_off;
-  // the two coarse vectors: shared memory, or global scratch when they do not fit
+  // the two coarse vectors: shared memory, or global scratch when they do not
+  // fit; then two chunks of bb doubles for the band solve's staged columns
   double* yb = gws ? gws + (long long)blockIdx.x * gstride : sm;
   double* ecs = yb + nc;
+  double* bbuf = gws ? sm : sm + 2 * (long long)nc;
   for (int i = ro + threadIdx.x; i < ro + n; i += blockDim.x) {
     double s = q[i];
     for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) s -= val[p] * x[col[p]];
@@ -54,30 +58,10 @@ __global__ void k_flux_stage(const Inst* inst, const int* list, CoarseSys cs, co
     yb[k] = s;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const double* AB = cs.band + cs.band_off[ii];
-    const int* ipiv = cs.ipiv + co;
-    int kl = cs.kl[ii], ku = cs.ku[ii], kv = kl + ku, ldab = 2 * kl + ku + 1;
-    int lane = threadIdx.x;
-    for (int j = 0; j < nc; ++j) {
-      int km = min(kl, nc - 1 - j);
-      int pj = ipiv[j];
-      if (lane == 0 && pj != j) { double t = yb[j]; yb[j] = yb[pj]; yb[pj] = t; }
-      __syncwarp();
-      double yj = yb[j];
-      for (int t = 1 + lane; t <= km; t += 32)
-        yb[j + t] -= AB[(long long)(kv + t) + (long long)ldab * j] * yj;
-      __syncwarp();
-    }
-    for (int j = nc - 1; j >= 0; --j) {
-      double yj = yb[j] / AB[(long long)kv + (long long)ldab * j];
-      __syncwarp();
-      if (lane == 0) yb[j] = yj;
-      for (int i = max(0, j - kv) + lane; i < j; i += 32)
-        yb[i] -= AB[(long long)(kv + i - j) + (long long)ldab * j] * yj;
-      __syncwarp();
-    }
-  }
+  // the R^FV band factors (gbtrs steps on four warps, the others staging
+  // band columns)
+  band::coarse_solve(cs.band + cs.band_off[ii], cs.ipiv + co, nc, cs.kl[ii], cs.ku[ii], yb, bbuf,
+                     pbuf, bb);
   __syncthreads();
   for (int k = threadIdx.x; k < nc; k += blockDim.x) ecs[perm[k]] = yb[k];
   __syncthreads();
@@ -427,14 +411,23 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   double* res = b.dp;
   int maxnc = 0;
   for (int ii : list) maxnc = std::max(maxnc, b.h[ii].nc);
-  size_t smem = sizeof(double) * 2 * (size_t)maxnc;
+  // band chunks of the staged band solve: at least one column of the
+  // widest listed band
+  int bb = 3072;
+  for (int ii : list) bb = std::max(bb, chh->kl[ii] + chh->ku[ii] + 1);
+  const size_t band_smem = sizeof(double) * 2 * (size_t)bb;
+  size_t smem = sizeof(double) * 2 * (size_t)maxnc + band_smem;
   int max_smem = 0;
   FAMS_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   max_smem -= 1024;  // static shared memory of the kernels
-  double* gws = nullptr;   // coarse vectors in global memory (above ~14k coarse unknowns)
+  if (band_smem > (size_t)max_smem) {
+    set_error("reconstruction's coarse band too wide for the staged band solve");
+    return FAMS_ECAPACITY;
+  }
+  double* gws = nullptr;   // coarse vectors in global memory when they do not fit beside
   if (smem > (size_t)max_smem) {
-    FAMS_TRY(b.scratch((void**)&gws, smem * (size_t)nl));
-    smem = 0;
+    FAMS_TRY(b.scratch((void**)&gws, sizeof(double) * 2 * (size_t)maxnc * (size_t)nl));
+    smem = band_smem;
   }
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
   FAMS_CUDA(cudaFuncSetAttribute(k_flux_local<CtaGroup>,
@@ -446,7 +439,7 @@ int run_flux(Batch& b, const std::vector<int>& list, const double* x, double* fa
   FAMS_CUDA(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
   fams::note_launch(), k_flux_stage<<<nl, 512, smem, st>>>(
       b.d_inst, dlist, *cs, b.rowptr, b.col, b.val, b.blk_ptr, b.blk_cell, b.pf_ptr, b.pf_col,
-      b.pf_val, b.q, x, res, pp, gws, 2 * (long long)maxnc);
+      b.pf_val, b.q, x, res, pp, gws, 2 * (long long)maxnc, bb);
   FAMS_CUDA(cudaGetLastError());
   // local problems of every primal block of the listed instances, by size
   // class (doubles of [K | rhs]): one warp, a 128-thread CTA, a 256-thread
