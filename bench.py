@@ -336,8 +336,12 @@ def stage_roofline(fams, probs, S, peak, sm_mhz):
     """Per-phase HBM rate of the GMRES kernel: a phase's algorithmic bytes
     per step of every instance over the phase's SM cycles per step of the
     median instance (fams_query(FAMS_Q_STAGE_CYCLES)), i.e. the rate the
-    resident instances reach while all run that phase."""
+    resident instances reach while all run that phase.  A batch larger than
+    the resident slots (two CTAs per SM) counts only the resident share."""
     import numpy as np
+    import torch
+    slots = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    share = min(1.0, slots / float(len(probs)))
     with fams.Context(probs) as c:
         _, st = c.solve(tol=TOL)
         cyc = np.array([c.query("STAGE_CYCLES", i) for i in range(len(probs))])
@@ -354,6 +358,7 @@ def stage_roofline(fams, probs, S, peak, sm_mhz):
             byts /= float(its.mean())
         else:
             byts = sum(b[name] for b in sb)
+        byts *= share
         gbs = byts / (per[k] / hz) / 1e9
         out[name] = {"mcycles_per_step": round(per[k] / 1e6, 3), "gb_per_step": round(byts / 1e9, 3),
                      "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}

@@ -15,7 +15,7 @@ struct fams_ctx {
 
 namespace fams {
 
-constexpr uint64_t POOL_KEEP = 32ull << 30;   // bytes of freed device memory the pool keeps
+constexpr uint64_t POOL_KEEP = 32ull << 30;   // least freed device memory the pool keeps
 
 namespace {
 thread_local std::string g_err;
@@ -267,10 +267,15 @@ int setup_batch(int n, const fams_grid* grids, const double* const* perms, const
   FAMS_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
   {
     // keep freed blocks in this process's pool for the next context (up to
-    // POOL_KEEP bytes) instead of returning them at every synchronisation
+    // half of the device's memory, at least POOL_KEEP bytes) instead of
+    // returning them at every synchronisation (unmapping the memory of a
+    // large batch, and mapping it again for the next context, cost tens of
+    // milliseconds each)
     cudaMemPool_t pool;
     FAMS_CUDA(cudaDeviceGetDefaultMemPool(&pool, b.device));
-    uint64_t keep = POOL_KEEP;
+    size_t dev_free = 0, dev_total = 0;
+    FAMS_CUDA(cudaMemGetInfo(&dev_free, &dev_total));
+    uint64_t keep = std::max<uint64_t>(POOL_KEEP, dev_total / 2);
     FAMS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
     // reuse across streams only once the free has completed: the pool then
     // never makes one context's stream wait for another's

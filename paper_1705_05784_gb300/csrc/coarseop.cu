@@ -234,6 +234,9 @@ __device__ inline int wrap(int x, int k) { return x >= k ? x - k : x; }
 // thread loads one step ahead
 constexpr int LU_PF = 4;
 
+constexpr int LDL_T = 512;       // threads of the band LDL^T (ring in shared memory)
+constexpr int LU_SMEM_T = 256;   // threads of the band LU with its ring in shared memory
+
 constexpr int LU_EXTRA = 32;      // narrow LU ring: columns of fill past the upper band
 constexpr double LU_TAU = 0.1;    // narrow LU ring: threshold of the pivot choice
 // a pivot at most this fraction of the largest entry of its row (as assembled)
@@ -528,23 +531,53 @@ __global__ void __launch_bounds__(1024) k_band_lu_act(const Inst* inst, int B, C
     for (int t = 1 + threadIdx.x; t <= km; t += T) lj[t] = SEL(wrap(jr + t, K1), jc) * inv;
     for (int cc = 1 + threadIdx.x; cc <= wd; cc += T) ur[cc] = SEL(jr, wrap(jc + cc, K2));
     __syncthreads();
-    // rank-1 update: a warp per row, lanes along the pivot row, four
-    // independent loads in flight per lane (the ring may sit in global memory)
-    for (int t = 1 + w; t <= km; t += nw) {
-      const int rs = wrap(jr + t, K1);
-      const double l = lj[t];
-      for (int c0 = 1 + lane; c0 <= wd; c0 += 128) {
-        double v[4];
-        int cs_[4];
+    // rank-1 update.  Ring in shared memory: a thread per (column, group of
+    // rows), the column's ring slot and pivot-row value in registers; the
+    // thread walks its rows one ring row (K2 doubles) at a time, the ring's
+    // wrap split out of the walk, two rows per pass.  Adjacent threads take
+    // adjacent columns.
+    if (gws) {
+      // ring in global memory: a warp per row, lanes along the pivot row,
+      // four independent loads in flight per lane
+      for (int t = 1 + w; t <= km; t += nw) {
+        const int rs = wrap(jr + t, K1);
+        const double l = lj[t];
+        for (int c0 = 1 + lane; c0 <= wd; c0 += 128) {
+          double v[4];
+          int cs_[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int cc = c0 + 32 * u;
-          cs_[u] = cc <= wd ? wrap(jc + cc, K2) : -1;
-          v[u] = cs_[u] >= 0 ? SEL(rs, cs_[u]) : 0.0;
+          for (int u = 0; u < 4; ++u) {
+            int cc = c0 + 32 * u;
+            cs_[u] = cc <= wd ? wrap(jc + cc, K2) : -1;
+            v[u] = cs_[u] >= 0 ? SEL(rs, cs_[u]) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (cs_[u] >= 0) SEL(rs, cs_[u]) = v[u] - l * ur[c0 + 32 * u];
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (cs_[u] >= 0) SEL(rs, cs_[u]) = v[u] - l * ur[c0 + 32 * u];
+      }
+    } else if (wd > 0 && km > 0) {
+      const int G = wd >= T ? 1 : T / wd;   // row groups
+      const int per = (km + G - 1) / G;
+      for (int e = threadIdx.x; e < G * wd; e += T) {
+        const int g = e / wd, cc = 1 + e - g * wd;
+        const int t1 = min(km, (g + 1) * per);
+        const double u = ur[cc];
+        const int c = wrap(jc + cc, K2);
+        for (int t = 1 + g * per; t <= t1;) {
+          const int rs = wrap(jr + t, K1);
+          const int run = min(t1 - t + 1, K1 - rs);   // rows before the ring wraps
+          double* q = S + (long long)rs * K2 + c;
+          const double* l = lj + t;
+          int k = 0;
+          for (; k + 2 <= run; k += 2, q += 2 * K2) {
+            const double a0 = q[0], a1 = q[K2];
+            q[0] = a0 - l[k] * u;
+            q[K2] = a1 - l[k + 1] * u;
+          }
+          for (; k < run; ++k, q += K2) q[0] -= l[k] * u;
+          t += run;
+        }
       }
     }
     // finished pivot row and multipliers back to the band (temporaries only)
@@ -743,7 +776,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
     FAMS_CUDA(cudaFuncSetAttribute(k_band_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    max_smem));
     if (ldl_smem > 0)
-      fams::note_launch(), k_band_ldl<<<B, 512, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu,
+      fams::note_launch(), k_band_ldl<<<B, LDL_T, ldl_smem, st>>>(b.d_inst, B, cs, d_spd, d_lu,
                                                                nullptr, nullptr, 0);
     if (ng > 0) {
       double* gws = nullptr;
@@ -806,7 +839,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
       FAMS_TRY(b.scratch((void**)&d_f, sizeof(int) * B));
       FAMS_CUDA(cudaMemcpyAsync(d_n, lu_n.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
       FAMS_CUDA(cudaMemsetAsync(d_f, 0, sizeof(int) * B, st));
-      fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_n + temps, st>>>(
+      fams::note_launch(), k_band_lu_act<<<B, LU_SMEM_T, sizeof(double) * act_n + temps, st>>>(
           b.d_inst, B, cs, d_n, b.d_err, nullptr, 0, LU_EXTRA, LU_TAU, d_f);
       FAMS_CUDA(cudaGetLastError());
       std::vector<int> failed(B, 0);
@@ -864,7 +897,7 @@ int build_coarse_system(Batch& b, CoarseSys& cs, int mode, CoarseHost& ch, bool 
     gst = b.aux;
   }
   if (act_s > 0)
-    fams::note_launch(), k_band_lu_act<<<B, 256, sizeof(double) * act_s + temps, st>>>(
+    fams::note_launch(), k_band_lu_act<<<B, LU_SMEM_T, sizeof(double) * act_s + temps, st>>>(
         b.d_inst, B, cs, d_lu, b.d_err, nullptr, 0, -1, 1.0, nullptr);
   if (act_g > 0)
     fams::note_launch(), k_band_lu_act<<<B, 1024, temps, gst>>>(b.d_inst, B, cs, d_lg, b.d_err, gws,
