@@ -52,7 +52,7 @@ def test_ranks_take_disjoint_instances():
     import sys
     sys.path.insert(0, ROOT)
     import bench
-    seeds = [set(range(bench.rank_seed(r), bench.rank_seed(r) + 304)) for r in range(8)]
+    seeds = [set(range(bench.rank_seed(r), bench.rank_seed(r) + 1216)) for r in range(8)]
     for a in range(8):
         for b in range(a + 1, 8):
             assert not seeds[a] & seeds[b]
