@@ -33,7 +33,7 @@ METRIC = "solves/s to rel. residual 1e-8 (served vs plain F-AMS, one GB300); p50
 # 32 instances, 10 iterations (profiles/k_gmres_traffic_2d256_batch32_10its.md;
 # there the Krylov bases, 0.5 GB, already exceed L2, so the traffic grows with
 # the instances and iterations; None once the kernel has changed since)
-TRAFFIC_RATIO = 0.9175
+TRAFFIC_RATIO = 0.9170
 WORKLOAD = ("2D 256x256: log10 k std 2 corr 16, 30 fractures L~U[20,120], coarsening 8x8, "
             "d_min 8, 4 coupling strategies x T_ratio {1e2,1e4,1e6,1e8}, R^FE, alpha 1e-2, "
             "ILU(0), GMRES(30) with the two-stage preconditioner, tol 1e-8, + flux reconstruction")
