@@ -312,20 +312,21 @@ __device__ void bitonic_sort_int(int* a, int m) {
   }
 }
 
-// one CTA per dual block: sort its members, then find the coarse columns its
-// known neighbours carry.  mode 0 counts them, mode 1 writes them sorted.
-// Mode 0 needs a power of two >= the largest block of ints of dynamic shared
-// memory.
+// one CTA per dual block (list[blockIdx.x]): sort its members, then find the
+// coarse columns its known neighbours carry.  mode 0 counts them, mode 1
+// writes them sorted.  Mode 0 needs a power of two >= the largest block of
+// ints of dynamic shared memory.
 __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const int* rank,
                             const int* plate, long long nrow, const int* rowptr, const int* col,
                             const int* instage, const int* label,
                             const int* comp_off, int* members, int* pos, const int* pstage,
                             const int* poff, const int* plen, Pool pool, int s, int mode,
-                            int* ncols, const int* colptr, int* colbuf, int* bw, int* err) {
+                            const int* list, int* ncols, const int* colptr, int* colbuf, int* bw,
+                            int* err) {
   extern __shared__ int sm[];   // member sort buffer (mode 0), sized by the launch
   __shared__ int hs[HASH_CAP];
   __shared__ int nuniq, known_links, ncand, s_bl, s_bu;
-  int c = blockIdx.x;
+  int c = list[blockIdx.x];
   int a = comp_off[c], n = comp_off[c + 1] - a;
   if (n > MEMBER_SORT_MAX) {
     if (threadIdx.x == 0) atomicCAS(err, 0, DERR_CAPACITY);
@@ -425,6 +426,146 @@ __global__ void k_comp_cols(const Inst* inst, int B, const int* off_row, const i
   __syncthreads();
   bitonic_sort_int(hs, H);
   for (int i = threadIdx.x; i < nuniq; i += blockDim.x) colbuf[colptr[c] + i] = hs[i];
+}
+
+// bitonic sort of a[0..m) (m a power of two) by one warp
+__device__ void warp_bitonic_sort(int* a, int m) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < m; i += 32) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          if ((a[i] > a[l]) == up) { int t = a[i]; a[i] = a[l]; a[l] = t; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// The column search of k_comp_cols for dual blocks of at most WCOL_N members,
+// one warp per block (list[]), CTA_WARPS blocks per CTA: most dual blocks are
+// the 7-cell edges and 49-cell faces of a 2D coarse grid, which left most of
+// a 128-thread CTA idle.  The same results: members sorted, the same
+// bandwidths and the same sorted column set.  A block with more candidate
+// columns than a warp's table holds is flagged in mode 0 (ovf_flag, appended
+// to ovf_list) for k_comp_cols, and skipped in mode 1.
+constexpr int WCOL_N = 64;    // members of a block on one warp
+constexpr int WCOL_H = 512;   // hash slots per warp
+
+__global__ void __launch_bounds__(32 * CTA_WARPS) k_comp_cols_warp(
+    const Inst* inst, int B, const int* off_row, const int* rank, const int* plate, long long nrow,
+    const int* rowptr, const int* col, const int* instage, const int* label, const int* comp_off,
+    int* members, int* pos, const int* pstage, const int* poff, const int* plen, Pool pool,
+    int mode, const int* list, int nlist, int* ncols, const int* colptr, int* colbuf, int* bw,
+    int* ovf_flag, int* ovf_list, int* ovf_n, int* err) {
+  __shared__ int tab[CTA_WARPS][WCOL_H];
+  const unsigned FULL = 0xffffffffu;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = blockIdx.x * CTA_WARPS + wi;
+  if (li >= nlist) return;
+  const int c = list[li];
+  if (mode == 1 && ovf_flag[c]) return;
+  int* hs = tab[wi];
+  const int a = comp_off[c], n = comp_off[c + 1] - a;   // 1 <= n <= WCOL_N
+  if (mode == 0) {
+    int m = 32;
+    while (m < n) m <<= 1;
+    for (int i = lane; i < m; i += 32) hs[i] = i < n ? members[a + i] : 0x7fffffff;
+    __syncwarp();
+    warp_bitonic_sort(hs, m);
+    for (int i = lane; i < n; i += 32) {
+      members[a + i] = hs[i];
+      pos[hs[i]] = i;
+    }
+    __syncwarp();
+  }
+  const Inst& I = inst_of(inst, B, off_row, members[a]);
+  int cand = 0, links = 0, bl = 0, bu = 0;
+  bool over = false;
+  for (int i = lane; i < n; i += 32) {
+    int r = members[a + i];
+    int mr = medium_of(I, r), rr = rank[r];
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int cc = col[p];
+      if (cc == r) continue;
+      if (instage[cc]) {
+        if (mode == 0 && label[cc] == label[r] &&
+            keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) {
+          bl = max(bl, i - pos[cc]);
+          bu = max(bu, pos[cc] - i);
+        }
+        continue;
+      }
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) continue;
+      ++links;
+      if (pstage[cc] < 0) { over = true; continue; }
+      cand += plen[cc];
+    }
+  }
+  links = __reduce_add_sync(FULL, links);
+  const int ncand = __reduce_add_sync(FULL, cand);
+  if (__any_sync(FULL, over) && lane == 0) atomicCAS(err, 0, DERR_INVAL);
+  if (mode == 0) {
+    bl = __reduce_max_sync(FULL, bl);
+    bu = __reduce_max_sync(FULL, bu);
+    if (lane == 0) {
+      bw[2 * c] = bl;
+      bw[2 * c + 1] = bu;
+    }
+  }
+  int H = 32;
+  while (H < 2 * ncand && H < HASH_CAP) H <<= 1;
+  if (H > WCOL_H) {   // mode 0 only: mode 1 skips the flagged blocks
+    if (lane == 0) {
+      ovf_flag[c] = 1;
+      ovf_list[atomicAdd(ovf_n, 1)] = c;
+    }
+    return;
+  }
+  for (int i = lane; i < H; i += 32) hs[i] = -1;
+  __syncwarp();
+  int mine = 0;
+  for (int i = lane; i < n; i += 32) {
+    int r = members[a + i];
+    int mr = medium_of(I, r), rr = rank[r];
+    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+      int cc = col[p];
+      if (cc == r || instage[cc]) continue;
+      if (!keep_link(I.basis, mr, rr, medium_of(I, cc), rank[cc], crossing(plate, nrow, r, cc))) continue;
+      int st = pstage[cc];
+      if (st < 0) continue;
+      const int* pc = pool.col[st] + poff[cc];
+      for (int q = 0; q < plen[cc]; ++q) {
+        int key = pc[q];
+        unsigned h = ((unsigned)key * 2654435761u) & (H - 1);
+        for (int probe = 0; probe < H; ++probe) {
+          int prev = atomicCAS(&hs[h], -1, key);
+          if (prev == -1) { ++mine; break; }
+          if (prev == key) break;
+          h = (h + 1) & (H - 1);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  const int nuniq = __reduce_add_sync(FULL, mine);
+  if (lane == 0 && links == 0) atomicCAS(err, 0, DERR_FLOATING);
+  if (nuniq > H / 2) {
+    if (lane == 0) atomicCAS(err, 0, DERR_CAPACITY);
+    return;
+  }
+  if (mode == 0) {
+    if (lane == 0) ncols[c] = nuniq;
+    return;
+  }
+  for (int i = lane; i < H; i += 32)
+    if (hs[i] == -1) hs[i] = 0x7fffffff;
+  __syncwarp();
+  warp_bitonic_sort(hs, H);
+  for (int i = lane; i < nuniq; i += 32) colbuf[colptr[c] + i] = hs[i];
 }
 
 __device__ inline int find_col(const int* cols, int k, int key) {
@@ -780,17 +921,59 @@ int phase_basis(Batch& b, const int* marked, int* rec, int* n_solved) {
                 std::to_string(MEMBER_SORT_MAX) + " are supported");
       return FAMS_ECAPACITY;
     }
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
+    // column search: blocks of at most WCOL_N members one warp each, the
+    // others (and small blocks whose candidates overflow a warp's table) one
+    // CTA each
+    std::vector<int> lsmall, lbig;
+    for (long long c = 0; c < ncomp; ++c) (hs[c] <= WCOL_N ? lsmall : lbig).push_back((int)c);
+    const int nsmall = (int)lsmall.size();
+    int nbig = (int)lbig.size();
+    int *d_small = nullptr, *d_big = nullptr, *ovf_flag = nullptr, *ovf_n = nullptr;
+    FAMS_TRY(b.scratch((void**)&d_small, sizeof(int) * (nsmall + 1)));
+    FAMS_TRY(b.scratch((void**)&d_big, sizeof(int) * (ncomp + 1)));   // big, then overflowed small
+    FAMS_TRY(b.scratch((void**)&ovf_flag, sizeof(int) * (ncomp + 1)));
+    FAMS_TRY(b.scratch((void**)&ovf_n, sizeof(int)));
+    if (nsmall)
+      FAMS_CUDA(cudaMemcpyAsync(d_small, lsmall.data(), sizeof(int) * nsmall, cudaMemcpyHostToDevice, st));
+    if (nbig)
+      FAMS_CUDA(cudaMemcpyAsync(d_big, lbig.data(), sizeof(int) * nbig, cudaMemcpyHostToDevice, st));
+    FAMS_CUDA(cudaMemsetAsync(ovf_flag, 0, sizeof(int) * (ncomp + 1), st));
+    FAMS_CUDA(cudaMemsetAsync(ovf_n, 0, sizeof(int), st));
+    if (nsmall)
+      fams::note_launch(), k_comp_cols_warp<<<(nsmall + CTA_WARPS - 1) / CTA_WARPS, 32 * CTA_WARPS, 0, st>>>(
+          b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col, instage, label, coff,
+          members, pos, pstage, poff, plen, pool, 0, d_small, nsmall, ncols, nullptr, nullptr, bw,
+          ovf_flag, d_big + nbig, ovf_n, b.d_err);
+    if (nbig)
+      fams::note_launch(), k_comp_cols<<<nbig, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
                                             instage, label, coff, members, pos, pstage, poff, plen, pool,
-                                            s, 0, ncols, nullptr, nullptr, bw, b.d_err);
+                                            s, 0, d_big, ncols, nullptr, nullptr, bw, b.d_err);
     FAMS_CUDA(cudaGetLastError());
+    {
+      int h_ovf = 0;
+      FAMS_CUDA(cudaMemcpyAsync(&h_ovf, ovf_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FAMS_CUDA(cudaStreamSynchronize(st));
+      if (h_ovf > 0) {
+        fams::note_launch(), k_comp_cols<<<h_ovf, 128, sizeof(int) * sort_cap, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
+                                              instage, label, coff, members, pos, pstage, poff, plen, pool,
+                                              s, 0, d_big + nbig, ncols, nullptr, nullptr, bw, b.d_err);
+        FAMS_CUDA(cudaGetLastError());
+        nbig += h_ovf;
+      }
+    }
     FAMS_TRY(b.check_err("dual-block columns"));
     long long totc = 0;
     FAMS_TRY(exclusive_scan(b, ncols, colptr, ncomp, &totc));
     FAMS_TRY(b.scratch((void**)&colbuf, sizeof(int) * (totc + 1)));
-    fams::note_launch(), k_comp_cols<<<(int)ncomp, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
-                                            instage, label, coff, members, pos, pstage, poff, plen, pool,
-                                            s, 1, ncols, colptr, colbuf, nullptr, b.d_err);
+    if (nsmall)
+      fams::note_launch(), k_comp_cols_warp<<<(nsmall + CTA_WARPS - 1) / CTA_WARPS, 32 * CTA_WARPS, 0, st>>>(
+          b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col, instage, label, coff,
+          members, pos, pstage, poff, plen, pool, 1, d_small, nsmall, ncols, colptr, colbuf, nullptr,
+          ovf_flag, nullptr, nullptr, b.d_err);
+    if (nbig)
+      fams::note_launch(), k_comp_cols<<<nbig, 128, 0, st>>>(b.d_inst, b.B, b.off_row, b.rank, plate, nrow, b.rowptr, b.col,
+                                              instage, label, coff, members, pos, pstage, poff, plen, pool,
+                                              s, 1, d_big, ncols, colptr, colbuf, nullptr, b.d_err);
     // host plan: pool offsets, and the blocks by size class (doubles of
     // [A'_BB | R]): one warp, a 128-thread CTA, a 256-thread CTA in shared
     // memory, or a 512-thread CTA on a bounded global workspace
