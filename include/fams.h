@@ -16,7 +16,11 @@
  *    in input order, within a fracture along-strike index fastest, then layer.
  *  - A context owns all device memory of its instances (fine system, coarse
  *    grids, P, R, coarse factors, ILU(0) factors, work vectors); it is freed
- *    by fams_destroy().  All work is issued on the context's own CUDA stream
+ *    by fams_destroy().  Memory comes from the device's default memory pool
+ *    (stream-ordered allocation); setup raises the pool's release threshold
+ *    to half of the device's memory (at least 32 GiB), so freed memory stays
+ *    in this process for the next context instead of being unmapped and
+ *    mapped again (other allocators of the process see it as in use).  All work is issued on the context's own CUDA stream
  *    and every call returns only after that work has finished.
  *  - A batch context holds several independent instances (a block-diagonal
  *    system): kernels process all instances together and one CTA per instance
