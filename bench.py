@@ -688,9 +688,13 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "batch": 1},
+            # the same workload and batch as the GPU arm; each step times a
+            # bounded sample of it (one instance), the rate scales to the batch
+            "config": {"workload": WORKLOAD, "batch": args.batch, "solver": "GMRES(30), FP64",
+                       "parallelism": "oracle, one host core"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "1 instance per step, single-threaded FP64 oracle"},
+                             "sample": "1 instance of the workload per step (setup + solve to "
+                                       "1e-8 + flux), single-threaded FP64 oracle"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
