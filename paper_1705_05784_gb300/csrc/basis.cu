@@ -925,6 +925,8 @@ int phase_basis(Batch& b, const int* marked, int* rec, int* n_solved) {
     // others (and small blocks whose candidates overflow a warp's table) one
     // CTA each
     std::vector<int> lsmall, lbig;
+    lsmall.reserve(ncomp);
+    lbig.reserve(ncomp);
     for (long long c = 0; c < ncomp; ++c) (hs[c] <= WCOL_N ? lsmall : lbig).push_back((int)c);
     const int nsmall = (int)lsmall.size();
     int nbig = (int)lbig.size();
