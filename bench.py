@@ -5,14 +5,21 @@ residual 1e-8.
 One step = one pass of the whole path over a batch of independent 2D
 256 x 256 instances shaped like the paper's 2D test (log10 k Gaussian field,
 std 2, correlation 16 cells; 30 random fractures of 20-120 cells; coarsening
-8 x 8, d_min = 8; the four coupling strategies and T_ratio 1e2 / 1e4 in
-rotation; R^FE, alpha = 1e-2): EDFM geometry, assembly, coarse grids, basis
-functions, truncation, R A P and its LU, ILU(0), the Table 1 iteration to
-1e-8 and the conservative flux reconstruction of every instance.
+8 x 8, d_min = 8; the four coupling strategies x T_ratio 1e2 / 1e4 / 1e6 /
+1e8 in rotation; R^FE, alpha = 1e-2): EDFM geometry, assembly, coarse grids,
+basis functions, truncation, R A P and its factors, ILU(0), GMRES(30) with
+the two-stage step as preconditioner to 1e-8 (--krylov none: the Table 1
+iteration) and the conservative flux reconstruction of every instance.  The
+default batch is 1216 instances: four waves of the solve's resident slots.
 
 value: inputs (permeability, initial guess, flux buffers) resident in GPU
 memory; e2e: the same through the C ABI with host buffers (host-to-device and
-device-to-host copies inside the timed region).
+device-to-host copies inside the timed region).  Further keys of the line:
+the solve kernel's HBM roofline and its per-phase rates, the error against
+the oracle per precision variant, the oracle's own rate on the host cores,
+the schedule autotuner's table, the large single instance (3D 128x128x64 on
+the whole GPU), the batched 3D workload, and the served request stream
+against plain one-at-a-time solves.  --impl reference times the oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl fams|reference]
 """
