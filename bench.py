@@ -707,6 +707,53 @@ def run_reference(args, rank):
     print(json.dumps(line))
 
 
+def phases(fams, batch, reps=2):
+    """Wall time of each part of one step at `batch` instances, the
+    reconstruction's coarse system built beside the solve (prepare_flux 1)
+    and in the first flux call (0): setup (with the library's per-phase
+    setup times), solve (and the solve kernel's own time), flux, destroy.
+    The last of `reps` repetitions is reported (the first warms the pool)."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = []
+    for pf in (1, 0):
+        probs = problems(batch, rank_seed(0))
+        for p in probs:
+            p.prepare_flux = pf
+        perm_d = [torch.from_numpy(np.ascontiguousarray(p.perm)).to(dev) for p in probs]
+        ctx = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+        S = [sizes_of(ctx, i) for i in range(len(probs))]
+        ctx.close()
+        x_d = [torch.zeros(s["n"], dtype=torch.float64, device=dev) for s in S]
+        f_d = [torch.zeros(s["faces"], dtype=torch.float64, device=dev) for s in S]
+        n_d = [torch.zeros(max(s["nnc"], 1), dtype=torch.float64, device=dev) for s in S]
+        for _ in range(reps):
+            for x in x_d:
+                x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c = fams.Context(probs, device_perm=[t.data_ptr() for t in perm_d])
+            t1 = time.perf_counter()
+            st = c.solve_device([None] * batch, [x.data_ptr() for x in x_d], TOL)
+            t2 = time.perf_counter()
+            c.flux_batch_ptr([x.data_ptr() for x in x_d], [f.data_ptr() for f in f_d],
+                             [m.data_ptr() for m in n_d])
+            t3 = time.perf_counter()
+            setup = [round(float(v), 1) for v in c.query("SETUP_MS")]
+            c.close()
+            torch.cuda.synchronize()
+            t4 = time.perf_counter()
+        out.append({"prepare_flux": pf, "setup_ms": round(1e3 * (t1 - t0), 1),
+                    "setup_phases_ms": dict(zip(("geometry", "fine_system", "coarse_grids", "basis",
+                                                 "coarse_operator", "ilu0"), setup)),
+                    "solve_ms": round(1e3 * (t2 - t1), 1), "kernel_ms": round(st[0]["solve_ms"], 1),
+                    "flux_ms": round(1e3 * (t3 - t2), 1), "destroy_ms": round(1e3 * (t4 - t3), 1),
+                    "step_ms": round(1e3 * (t4 - t0), 1)})
+    return {"batch": batch, "workload": WORKLOAD, "note": "host wall times with synchronisation "
+            "after each call; kernel_ms: the solve kernel's device time", "runs": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,6 +788,9 @@ def main():
                     help="instances of the batched 3D workload (0: skip)")
     ap.add_argument("--merge-cap", type=int, default=256,
                     help="Coupled-AMS merge cap of the 3D scale case")
+    ap.add_argument("--phases", type=int, default=0,
+                    help="print the wall time of each part of one step at this batch size "
+                         "(one JSON line) instead of the bench line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -751,6 +801,11 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    if args.phases > 0:
+        from paper_1705_05784_gb300 import fams
+        if rank == 0:
+            print(json.dumps(phases(fams, args.phases)))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
