@@ -812,7 +812,8 @@ def main():
         dist.init_process_group("nccl")
     # the oracle baseline runs first, in a spawned process, before any GPU work
     cpu = None
-    if rank == 0 and not args.no_cpu and args.cpu_sample > 0:
+    # (rank 0 at one GPU only: under torchrun the other GPUs would wait for it)
+    if rank == 0 and world == 1 and not args.no_cpu and args.cpu_sample > 0:
         cpu = cpu_baseline(args.cpu_sample)
     from paper_1705_05784_gb300 import fams
     probs = problems(args.batch, rank_seed(rank), args.max_iter,
@@ -952,6 +953,11 @@ def main():
         "clocks": clk.summary(),
         "cells_per_s": value * cells / max(converged_here, 1),
     }
+    if world > 1:
+        # the single-GPU legs below run at N = 1 only: the other ranks have
+        # exited and their GPUs would sit idle meanwhile
+        print(json.dumps(line))
+        return
     if args.large > 0:
         line["large_instance"] = large_instance(fams, args.large, 1, args.merge_cap)
     line["stage_roofline"] = {
