@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -41,6 +42,27 @@ namespace {
 double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// a caller array of n doubles (host or device memory) into a host vector
+int copy_in(std::vector<double>& dst, const double* src, size_t n) {
+  dst.resize(n);
+  if (n == 0) return FAMS_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    cudaError_t e = cudaMemcpy(dst.data(), src, sizeof(double) * n, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+      fams::set_error(std::string("copying a request's array: ") + cudaGetErrorString(e));
+      return FAMS_ECUDA;
+    }
+  } else {
+    std::memcpy(dst.data(), src, sizeof(double) * n);
+  }
+  return FAMS_OK;
 }
 
 struct Resident;
@@ -525,7 +547,11 @@ int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm
   auto* r = new Request();
   r->grid = *grid;
   long long cells = (long long)grid->nx * grid->ny * (grid->dim == 3 ? grid->nz : 1);
-  r->perm.assign(perm, perm + cells);
+  int cs = copy_in(r->perm, perm, (size_t)cells);
+  if (cs != FAMS_OK) {
+    delete r;
+    return cs;
+  }
   int nf = fracs ? fracs->n : 0;
   if (nf > 0) {
     if (!fracs->xy || !fracs->kf) {
@@ -534,8 +560,12 @@ int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm
       return FAMS_EINVAL;
     }
     int w = grid->dim == 3 ? 6 : 4;
-    r->xy.assign(fracs->xy, fracs->xy + (size_t)nf * w);
-    r->kf.assign(fracs->kf, fracs->kf + nf);
+    cs = copy_in(r->xy, fracs->xy, (size_t)nf * w);
+    if (cs == FAMS_OK) cs = copy_in(r->kf, fracs->kf, (size_t)nf);
+    if (cs != FAMS_OK) {
+      delete r;
+      return cs;
+    }
   }
   if (fracs) r->fr = *fracs;
   r->fr.n = nf;
@@ -543,7 +573,11 @@ int fams_server_submit(fams_server* s, const fams_grid* grid, const double* perm
   r->fr.kf = nullptr;
   if (nf == 0) { r->fr.aperture = 1.0; r->fr.h_f = 1.0; }
   r->opts = *opts;
-  if (rhs) r->rhs.assign(rhs, rhs + cells);   // matrix sources; fracture sources default to 0
+  // matrix sources; fracture sources default to 0
+  if (rhs && (cs = copy_in(r->rhs, rhs, (size_t)cells)) != FAMS_OK) {
+    delete r;
+    return cs;
+  }
   r->mem = estimate_bytes(*r);
   r->heavy = estimate_heavy(*r);
   if (r->heavy && r->opts.grid_solve == 0) r->opts.grid_solve = 1;
@@ -574,8 +608,12 @@ int fams_server_submit_update(fams_server* s, long long base, const double* mobi
   auto* r = new Request();
   r->update = true;
   r->base = base;
-  r->scale.assign(mobility_scale, mobility_scale + n_scale);
-  if (rhs) r->rhs.assign(rhs, rhs + n_rhs);
+  int cs = copy_in(r->scale, mobility_scale, (size_t)n_scale);
+  if (cs == FAMS_OK && rhs) cs = copy_in(r->rhs, rhs, (size_t)n_rhs);
+  if (cs != FAMS_OK) {
+    delete r;
+    return cs;
+  }
   r->t_submit = now_ms();
   {
     std::lock_guard<std::mutex> lk(s->mu);
