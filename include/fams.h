@@ -436,7 +436,7 @@ int fams_server_submit_update(fams_server* s, long long base, const double* mobi
 /* waits up to timeout_ms (<= 0: no wait); *done = 1 once the result is ready */
 int fams_server_wait(fams_server* s, long long ticket, double timeout_ms, int* done);
 /* copies a finished request's pressure (n_matrix + n_frac values), fluxes (as
-   fams_flux; with_flux only) and statistics (st->solve_ms: from the start of
+   fams_flux; with_flux only; host or device memory) and statistics (st->solve_ms: from the start of
    the request's micro-batch to its completion); latency_ms = completion minus
    submission time.  Returns the request's status.  Null outputs are skipped;
    a capacity below the result's size is FAMS_EINVAL. */

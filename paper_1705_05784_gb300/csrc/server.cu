@@ -44,16 +44,35 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// a result vector into a caller array (host or device memory)
+int copy_out(double* dst, const std::vector<double>& src) {
+  if (src.empty()) return FAMS_OK;
+  if (on_device(dst)) {
+    cudaError_t e = cudaMemcpy(dst, src.data(), sizeof(double) * src.size(), cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+      fams::set_error(std::string("copying a result: ") + cudaGetErrorString(e));
+      return FAMS_ECUDA;
+    }
+  } else {
+    std::memcpy(dst, src.data(), sizeof(double) * src.size());
+  }
+  return FAMS_OK;
+}
+
 // a caller array of n doubles (host or device memory) into a host vector
 int copy_in(std::vector<double>& dst, const double* src, size_t n) {
   dst.resize(n);
   if (n == 0) return FAMS_OK;
-  cudaPointerAttributes at{};
-  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
-    cudaGetLastError();
-    at.type = cudaMemoryTypeUnregistered;
-  }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+  if (on_device(src)) {
     cudaError_t e = cudaMemcpy(dst.data(), src, sizeof(double) * n, cudaMemcpyDefault);
     if (e != cudaSuccess) {
       fams::set_error(std::string("copying a request's array: ") + cudaGetErrorString(e));
@@ -660,15 +679,15 @@ int fams_server_result(fams_server* s, long long ticket, double* x, long long x_
   if (!r->done) { set_error("request not finished"); return FAMS_EINVAL; }
   if (x) {
     if (x_cap < (long long)r->x.size()) { set_error("x buffer too small"); return FAMS_EINVAL; }
-    std::copy(r->x.begin(), r->x.end(), x);
+    if (int c = copy_out(x, r->x)) return c;
   }
   if (face_flux && !r->face.empty()) {
     if (face_cap < (long long)r->face.size()) { set_error("face buffer too small"); return FAMS_EINVAL; }
-    std::copy(r->face.begin(), r->face.end(), face_flux);
+    if (int c = copy_out(face_flux, r->face)) return c;
   }
   if (nnc_flux && !r->nnc.empty()) {
     if (nnc_cap < (long long)r->nnc.size()) { set_error("nnc buffer too small"); return FAMS_EINVAL; }
-    std::copy(r->nnc.begin(), r->nnc.end(), nnc_flux);
+    if (int c = copy_out(nnc_flux, r->nnc)) return c;
   }
   if (st) {
     *st = r->st;
